@@ -1,0 +1,391 @@
+"""Pins of the CPU oracle to facts the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: a closed form, a value
+printed in the paper, a theorem of the paper, an invariant, or a second construction that
+shares no code with the first.  A plausible slip in the oracle (a dropped term, a sign, a
+transposed operand, a wrong coefficient) breaks at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import sgn_oracle as O
+from paper_2506_16045_gb300 import inputs as I
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+# ---------------------------------------------------------------------------- D (§6.1)
+
+@pytest.mark.parametrize("n,L", [(8, 1.0), (16, 3.7), (64, 100.0), (128, 2 * math.pi)])
+def test_derivative_fft_equals_cotangent_matrix(n, L):
+    """D built from the DFT definition equals the closed-form periodic cotangent matrix."""
+    Df = O.diff_matrix_fft(n, L)
+    Dc = O.diff_matrix_cot(n, L)
+    assert np.abs(Df - Dc).max() <= 1e-14 * np.abs(Dc).max() * n
+    assert np.abs(Dc + Dc.T).max() == 0.0           # real antisymmetric
+
+
+@pytest.mark.parametrize("n,L", [(16, 1.0), (64, 7.5)])
+def test_derivative_exact_on_trig_and_nyquist(n, L):
+    x = I.grid_1d(n, L)
+    for m in range(1, n // 2):
+        f = np.sin(2 * np.pi * m * x / L)
+        np.testing.assert_allclose(O.deriv(f, L), (2 * np.pi * m / L) * np.cos(2 * np.pi * m * x / L),
+                                   atol=1e-12 * (2 * np.pi * m / L))
+    nyq = np.cos(np.pi * n * x / L)                    # the n/2 mode: its derivative is 0 (§6.1)
+    assert np.abs(O.deriv(nyq, L)).max() < 1e-12
+    assert np.abs(O.deriv(np.ones(n), L)).max() < 1e-14
+
+
+def test_derivative_2d_tensor_product():
+    X, Y = I.grid_2d(16, 8, 2.0, 3.0)
+    f = np.sin(2 * np.pi * 3 * X / 2.0) * np.cos(2 * np.pi * 2 * Y / 3.0)
+    g = O.grad(f, (2.0, 3.0))
+    np.testing.assert_allclose(g[0], (2 * np.pi * 3 / 2.0) * np.cos(2 * np.pi * 3 * X / 2.0)
+                               * np.cos(2 * np.pi * 2 * Y / 3.0), atol=1e-12)
+    np.testing.assert_allclose(g[1], -(2 * np.pi * 2 / 3.0) * np.sin(2 * np.pi * 3 * X / 2.0)
+                               * np.sin(2 * np.pi * 2 * Y / 3.0), atol=1e-12)
+
+
+# ---------------------------------------------------------------------------- G (Def:G)
+
+@pytest.mark.parametrize("eta0,hvar", [(1.0, 1.0), (4.0, 0.5), (0.5, 4.0)])
+def test_G_matrix_free_equals_dense_weak_form_1d(eta0, hvar):
+    """Def:G term by term (FFT derivatives) equals W^T M W (Def:MatrixM, cotangent D)."""
+    n = 48
+    _, h, eta, _ = I.testproblem_1d(n, eta0, hvar)
+    hx = O.deriv(h, 1.0)
+    Gd = O.dense_G_1d(eta, hx, 1.0)
+    U = np.random.default_rng(3).standard_normal((n, 5))
+    mf = np.stack([O.apply_G_1d(eta, hx, U[:, i], 1.0) for i in range(5)], axis=1)
+    assert np.abs(Gd @ U - mf).max() <= 1e-13 * np.abs(Gd @ U).max()
+    assert np.abs(Gd - Gd.T).max() <= 1e-14 * np.abs(Gd).max()
+    np.linalg.cholesky(Gd)                              # SPD (§6.1)
+
+
+@pytest.mark.parametrize("a,b", [(1.0, 1.0), (1.0, 20.0)])
+def test_G_matrix_free_equals_dense_weak_form_2d(a, b):
+    n = 10
+    _, _, h, eta, _ = I.elliptical_bump_2d(n, a, b)
+    gh = O.grad(h, (1.0, 1.0))
+    grid = O.make_grid(2, n, 1.0, 1.0, ny=n, Ly=1.0)
+    Gd = O.dense_G_2d(eta, gh, 1.0, 1.0)
+    u = np.random.default_rng(4).standard_normal((2, n, n))
+    ref = Gd @ u.ravel()
+    assert np.abs(ref - O.apply_G(eta, gh, u, grid).ravel()).max() <= 1e-13 * np.abs(ref).max()
+    assert np.abs(Gd - Gd.T).max() <= 1e-14 * np.abs(Gd).max()
+    np.linalg.cholesky(Gd)
+
+
+def test_G_2d_reduces_to_1d_on_y_constant_fields():
+    """§6.3: extending 1d data as constants in y with v = 0 reproduces the 1d operator."""
+    n, ny = 32, 4
+    _, h, eta, b = I.testproblem_1d(n, 1.0, 1.0)
+    hx = O.deriv(h, 1.0)
+    u1 = np.random.default_rng(5).standard_normal(n)
+    g1 = O.apply_G_1d(eta, hx, u1, 1.0)
+    E = np.tile(eta, (ny, 1))
+    H = np.tile(h, (ny, 1))
+    gh = O.grad(H, (1.0, 0.7))
+    U2 = np.stack([np.tile(u1, (ny, 1)), np.zeros((ny, n))])
+    g2 = O.apply_G(E, gh, U2, O.make_grid(2, n, 1.0, 1.0, ny=ny, Ly=0.7))
+    np.testing.assert_allclose(g2[0], np.tile(g1, (ny, 1)), atol=1e-12 * np.abs(g1).max())
+    assert np.abs(g2[1]).max() < 1e-12 * np.abs(g1).max()
+
+
+def test_flat_constant_depth_gives_A_equal_G_and_one_iteration():
+    """Eq:FlatbathCoeff with constant eta: A = G, kappa_ub = 1, PCG stops after 1 iteration."""
+    n, L, eta0 = 64, 10.0, 1.7
+    eta = np.full(n, eta0)
+    hx = np.zeros(n)
+    c = O.precond_coeffs(eta, hx)
+    gold = GOLDEN["flat_optimality"]
+    assert c["flat"] and c["kappa_ub"] == gold["kappa_ub"]
+    assert c["sigma"] == eta0 and abs(c["alpha"] - eta0 ** 3 / 3) < 1e-15
+    Gd = O.dense_G_1d(eta, hx, L)
+    Ad = O.dense_A_1d(c["sigma"], c["alpha"], n, L)
+    assert np.abs(Gd - Ad).max() <= 1e-13 * np.abs(Ad).max()
+    b = np.random.default_rng(6).standard_normal(n)
+    grid = O.make_grid(1, n, L, 9.81)
+    x, it, ratio, _ = O.solve_G(eta, hx, b, grid, rtol=1e-12)
+    assert it == gold["pcg_iterations"]
+    np.testing.assert_allclose(Gd @ x, b, atol=1e-12 * np.abs(b).max())
+
+
+# ---------------------------------------------------------------------------- A (Def:A)
+
+def test_Ainv_inverts_dense_A_1d_and_2d():
+    n, L = 32, 2.5
+    r = np.random.default_rng(7).standard_normal(n)
+    z = O.apply_Ainv(r, 1.3, 0.4, O.make_grid(1, n, L, 1.0))
+    np.testing.assert_allclose(O.dense_A_1d(1.3, 0.4, n, L) @ z, r, atol=1e-12)
+    nx, ny = 8, 6
+    r2 = np.random.default_rng(8).standard_normal((2, ny, nx))
+    grid = O.make_grid(2, nx, 1.5, 1.0, ny=ny, Ly=2.0)
+    z2 = O.apply_Ainv(r2, 0.9, 0.3, grid)
+    np.testing.assert_allclose(O.dense_A_2d(0.9, 0.3, nx, ny, 1.5, 2.0) @ z2.ravel(), r2.ravel(),
+                               atol=1e-12)
+    np.testing.assert_allclose(O.apply_A(z2, 0.9, 0.3, grid), r2, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------- Theorem 4.1
+
+def test_lambda_pm_printed_values():
+    gold = GOLDEN["lambda_pm"]
+    ev = np.linalg.eigvalsh(np.array([[1.0, 0.5], [0.5, 1.0 / 3.0]]))
+    assert abs(ev[1] - O.LAMBDA_PLUS) < 1e-15 and abs(ev[0] - O.LAMBDA_MINUS) < 1e-15
+    assert abs(O.LAMBDA_PLUS - eval(gold["plus_formula"], {"sqrt": math.sqrt})) < 1e-15
+    assert abs(O.LAMBDA_PLUS / O.LAMBDA_MINUS - 19.28147006790397) < 1e-12
+
+
+@pytest.mark.parametrize("eta0", [0.5, 1.0, 4.0])
+@pytest.mark.parametrize("hvar", [0.0, 0.5, 1.0, 4.0])
+@pytest.mark.parametrize("n", [16, 64])
+def test_theorem_4_1_eigenvalue_interval_1d(n, eta0, hvar):
+    """Generalized eigenvalues of (G, A) lie in [1/kappa_ub, 1] (Eq:EigValueBound)."""
+    _, h, eta, _ = I.testproblem_1d(n, eta0, hvar)
+    hx = O.deriv(h, 1.0) if hvar else np.zeros(n)
+    c = O.precond_coeffs(eta, hx)
+    ev = O.generalized_eigenvalues(O.dense_G_1d(eta, hx, 1.0),
+                                   O.dense_A_1d(c["sigma"], c["alpha"], n, 1.0))
+    assert ev.min() >= (1.0 - 1e-12) / c["kappa_ub"]
+    assert ev.max() <= 1.0 + 1e-12
+    cr = O.precond_coeffs(eta, hx, "replacement")
+    assert cr["kappa_ub"] >= c["kappa_ub"] * (1 - 1e-14)
+    evr = O.generalized_eigenvalues(O.dense_G_1d(eta, hx, 1.0),
+                                    O.dense_A_1d(cr["sigma"], cr["alpha"], n, 1.0))
+    assert evr.min() >= (1.0 - 1e-12) / cr["kappa_ub"] and evr.max() <= 1.0 + 1e-12
+
+
+@pytest.mark.parametrize("a,b", [(1.0, 1.0), (1.0, 20.0)])
+def test_theorem_4_1_eigenvalue_interval_2d(a, b):
+    n = 12
+    _, _, h, eta, _ = I.elliptical_bump_2d(n, a, b)
+    gh = O.grad(h, (1.0, 1.0))
+    c = O.precond_coeffs(eta, gh)
+    ev = O.generalized_eigenvalues(O.dense_G_2d(eta, gh, 1.0, 1.0),
+                                   O.dense_A_2d(c["sigma"], c["alpha"], n, n, 1.0, 1.0))
+    assert ev.min() >= (1.0 - 1e-12) / c["kappa_ub"]
+    assert ev.max() <= 1.0 + 1e-12
+
+
+def test_flat_bottom_coefficients_are_the_sharp_ones():
+    """On a flat bottom the bound (eta_max/eta_min)^3 is attained up to discretisation."""
+    n = 64
+    _, _, eta, _ = I.testproblem_1d(n, 1.0, 0.0)
+    hx = np.zeros(n)
+    c = O.precond_coeffs(eta, hx)
+    ev = O.generalized_eigenvalues(O.dense_G_1d(eta, hx, 1.0),
+                                   O.dense_A_1d(c["sigma"], c["alpha"], n, 1.0))
+    assert abs(c["kappa_ub"] - 8.0) < 1e-12
+    assert ev.max() > 0.95 and ev.min() < 1.2 / c["kappa_ub"]
+
+
+def test_printed_testproblem_values():
+    """|h_x|_max ~ 17.2 |h0| and the eigenvalue bulk ~[3e-2, 3e-1] with ~6 outliers (§6.2)."""
+    g = GOLDEN["hx_max_testproblem"]
+    assert abs(20 * math.sqrt(2) / math.exp(0.5) - g["exact"]) < 1e-12
+    assert round(g["exact"], 1) == g["printed"]
+    gb = GOLDEN["eigen_bulk_testproblem"]
+    for n in gb["n"]:
+        _, h, eta, _ = I.testproblem_1d(n, 1.0, 1.0)
+        hx = O.deriv(h, 1.0)
+        assert abs(np.abs(hx).max() - g["exact"]) < (0.3 if n == 64 else 1e-3)
+        c = O.precond_coeffs(eta, hx)
+        ev = O.generalized_eigenvalues(O.dense_G_1d(eta, hx, 1.0),
+                                       O.dense_A_1d(c["sigma"], c["alpha"], n, 1.0))
+        outside = int(np.sum((ev < gb["bulk_lo"]) | (ev > gb["bulk_hi"])))
+        assert 3 <= outside <= 10
+        assert ev.min() >= 1.0 / c["kappa_ub"]
+
+
+# ---------------------------------------------------------------------------- PCG (§3.2)
+
+@pytest.mark.parametrize("eta0,hvar", [(1.0, 1.0), (4.0, 1.0)])
+def test_pcg_error_monotone_and_within_cg_bound(eta0, hvar):
+    """epsilon(u_j) is non-increasing (§6.1) and <= 2 rho^j epsilon(0) (Eq:pcg_upperbound)."""
+    n = 64
+    _, h, eta, b = I.testproblem_1d(n, eta0, hvar)
+    hx = O.deriv(h, 1.0)
+    grid = O.make_grid(1, n, 1.0, 1.0)
+    Gd = O.dense_G_1d(eta, hx, 1.0)
+    ustar = np.linalg.solve(Gd, b)
+    c = O.precond_coeffs(eta, hx)
+    x, it, ratio, hist = O.pcg(lambda v: O.apply_G(eta, hx, v, grid),
+                               lambda v: O.apply_Ainv(v, c["sigma"], c["alpha"], grid),
+                               b, None, 1e-13, 500, history=True)
+    eps = [O.g_error(u, ustar, Gd, b) for u in hist]
+    rho = (math.sqrt(c["kappa_ub"]) - 1) / (math.sqrt(c["kappa_ub"]) + 1)
+    for j in range(1, len(eps)):
+        assert eps[j] <= eps[j - 1] * (1 + 1e-9) + 1e-15
+        assert eps[j] <= 2 * rho ** j * eps[0] * (1 + 1e-9) + 1e-15
+    assert eps[-1] < 1e-12
+    # reading R7: stopping at sqrt(r.A^-1 r) <= rtol sqrt(b.A^-1 b) gives
+    # eps <= sqrt(kappa_ub) rtol sqrt(b.A^-1 b)/||b||, since G^-1 <= kappa_ub A^-1
+    bAb = float(b @ O.apply_Ainv(b, c["sigma"], c["alpha"], grid))
+    for rtol in (1e-4, 1e-7):
+        x, _, _ = O.pcg(lambda v: O.apply_G(eta, hx, v, grid),
+                        lambda v: O.apply_Ainv(v, c["sigma"], c["alpha"], grid), b, None, rtol, 500)
+        bound = math.sqrt(c["kappa_ub"]) * rtol * math.sqrt(bAb) / np.linalg.norm(b)
+        assert O.g_error(x, ustar, Gd, b) <= bound * 1.01
+
+
+def test_pcg_zero_rhs_and_exact_warm_start():
+    n = 32
+    _, h, eta, b = I.testproblem_1d(n, 1.0, 1.0)
+    hx = O.deriv(h, 1.0)
+    grid = O.make_grid(1, n, 1.0, 1.0)
+    x, it, _, _ = O.solve_G(eta, hx, np.zeros(n), grid, x0=np.ones(n))
+    assert it == 0 and np.all(x == 0)
+    ustar = np.linalg.solve(O.dense_G_1d(eta, hx, 1.0), b)
+    x, it, _, _ = O.solve_G(eta, hx, b, grid, x0=ustar, rtol=1e-10)
+    assert it == 0
+
+
+def test_pcg_2d_elliptical_bump_converges_to_dense_solution():
+    n = 12
+    _, _, h, eta, rhs = I.elliptical_bump_2d(n, 1.0, 20.0)
+    gh = O.grad(h, (1.0, 1.0))
+    grid = O.make_grid(2, n, 1.0, 1.0, ny=n, Ly=1.0)
+    x, it, ratio, c = O.solve_G(eta, gh, rhs, grid, rtol=1e-13)
+    ref = np.linalg.solve(O.dense_G_2d(eta, gh, 1.0, 1.0), rhs.ravel())
+    np.testing.assert_allclose(x.ravel(), ref, atol=1e-10 * np.abs(ref).max())
+
+
+# ---------------------------------------------------------------------------- time stepping
+
+def test_solitary_wave_closed_form_rk4():
+    """Flat bottom, L=100, n=256, a=0.2, g=9.81: RK4 follows the exact translating wave."""
+    case = I.solitary_case()
+    grid = O.make_grid(1, case.n, case.L, case.g)
+    st = O.init_state(case.eta, case.u, case.h, grid)
+    O.run_rk4(st, 0.01, 60)
+    x = I.grid_1d(case.n, case.L)
+    ee, ue = I.solitary_wave_1d(x, case.L, 1.0, 0.2, 25.0, case.g, t=st.t)
+    assert np.abs(st.eta - ee).max() < 1e-8
+    assert np.abs(st.u - ue).max() < 1e-8
+
+
+def _order_errors(run, dts, T=1.0):
+    case = I.solitary_case(n=128, L=60.0, a=0.3, x0=30.0, g=1.0)
+    x = I.grid_1d(case.n, case.L)
+    errs = []
+    for dt in dts:
+        grid = O.make_grid(1, case.n, case.L, case.g)
+        st = O.init_state(case.eta, case.u, case.h, grid)
+        run(st, dt, int(round(T / dt)))
+        ee, _ = I.solitary_wave_1d(x, case.L, 1.0, 0.3, 30.0, case.g, t=st.t)
+        errs.append(np.abs(st.eta - ee).max())
+    return [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+
+
+@pytest.mark.parametrize("name,order,run,dts", [
+    ("rk4", 4, lambda s, d, k: O.run_rk4(s, d, k, 1e-13), (0.2, 0.1)),
+    ("ab2", 2, lambda s, d, k: O.run_ab(s, 2, d, k, 1e-13), (0.04, 0.02)),
+    ("ab3", 3, lambda s, d, k: O.run_ab(s, 3, d, k, 1e-13), (0.04, 0.02)),
+    ("ab4", 4, lambda s, d, k: O.run_ab(s, 4, d, k, 1e-13), (0.04, 0.02)),
+    ("sbdf2", 2, lambda s, d, k: O.run_sbdf2(s, d, k, 1e-13), (0.04, 0.02)),
+])
+def test_observed_order(name, order, run, dts):
+    """Table 1 / Eq:ERK coefficients give the expected convergence order."""
+    (p,) = _order_errors(run, dts)
+    assert abs(p - order) < 0.35, (name, p)
+
+
+def test_multistep_tables_consistency():
+    for s in (2, 3, 4):
+        a, b = O.AB_A[s], O.AB_B[s]
+        assert abs(sum(a)) < 1e-15
+        assert abs(sum(j * a[j] for j in range(s + 1)) - sum(b)) < 1e-14
+    a, b, c = O.SBDF2_A, O.SBDF2_B, O.SBDF2_C
+    assert abs(sum(a)) < 1e-15 and abs(sum(j * a[j] for j in range(3)) - sum(b)) < 1e-15
+    assert sum(c) == sum(b)      # extrapolation of A p is consistent
+
+
+def _shelf_state(n=256):
+    case = I.shelf_case(n=n, L=200.0, a=0.3, x0=40.0, r=0.5, xs=45.0, w=5.0)
+    grid = O.make_grid(1, case.n, case.L, case.g)
+    return case, O.init_state(case.eta, case.u, case.h, grid)
+
+
+def test_mass_conserved_to_roundoff_all_schemes():
+    """m = integral zeta is invariant for every scheme (spectral divergence has zero mean)."""
+    for run in (lambda s: O.run_rk4(s, 0.05, 4), lambda s: O.run_ab(s, 3, 0.05, 6),
+                lambda s: O.run_sbdf2(s, 0.02, 6)):
+        case, st = _shelf_state()
+        cell = case.L / case.n
+        m0 = O.mass(st.eta, st.h, cell)
+        run(st)
+        assert abs(O.mass(st.eta, st.h, cell) - m0) < 1e-12 * np.abs(st.eta - st.h).sum() * cell
+
+
+def test_energy_conserved_over_shelf_pins_forcing():
+    """E = 1/2 int [g zeta^2 + u.G u] (the flat-bottom energy of the conservation remark
+    with the kinetic energy 1/2 B[u,u]) is conserved by the SGN equations with bathymetry;
+    RK4's drift vanishes at 4th order.  A wrong term or sign in F, or the other reading of
+    (u.grad)^2 h, leaves an O(1e-3) drift."""
+    drifts = []
+    for dt in (0.04, 0.02):
+        case, st = _shelf_state()
+        E0 = O.energy(st)
+        O.run_rk4(st, dt, int(round(1.2 / dt)), 1e-13)
+        drifts.append(abs(O.energy(st) - E0) / E0)
+    assert drifts[0] < 2e-6 and drifts[1] < drifts[0] / 10
+
+
+def test_planted_forcing_mistake_breaks_energy_pin(monkeypatch):
+    """The energy pin is sensitive: dropping the eta*m*s term of F leaves a visible drift."""
+    def rhs_bad(eta, u, h, hx, L, g):
+        d = O.deriv(u, L)
+        m = O.deriv(eta * u, L)
+        s = hx * u
+        S = u * O.deriv(s, L)
+        Q = u * O.deriv(d, L) - d * d
+        Phi = eta ** 3 * Q / 3 + eta ** 2 * m * d + eta ** 2 * S / 2          # eta m s dropped
+        Psi = eta ** 2 * Q / 2 + eta * m * d + eta * S + m * s
+        F = O.deriv(Phi, L) - hx * Psi
+        return -m, -g * eta * O.deriv(eta - h, L) - O.deriv(eta * u * u, L) + F
+    monkeypatch.setattr(O, "rhs_1d", rhs_bad)
+    case, st = _shelf_state()
+    E0 = O.energy(st)
+    O.run_rk4(st, 0.04, 30, 1e-13)
+    assert abs(O.energy(st) - E0) / E0 > 1e-5
+
+
+def test_2d_plane_wave_matches_1d_evolution():
+    """A y-independent 2d solitary wave evolves like the 1d one (§6.5 sanity check)."""
+    n, ny, L = 64, 4, 40.0
+    case = I.solitary_case(n=n, L=L, a=0.2, x0=20.0, g=9.81)
+    g1 = O.make_grid(1, n, L, 9.81)
+    s1 = O.init_state(case.eta, case.u, case.h, g1)
+    O.run_rk4(s1, 0.02, 5, 1e-13)
+    g2 = O.make_grid(2, n, L, 9.81, ny=ny, Ly=5.0)
+    E = np.tile(case.eta, (ny, 1))
+    U = np.stack([np.tile(case.u, (ny, 1)), np.zeros((ny, n))])
+    s2 = O.init_state(E, U, np.ones((ny, n)), g2)
+    O.run_rk4(s2, 0.02, 5, 1e-13)
+    np.testing.assert_allclose(s2.eta, np.tile(s1.eta, (ny, 1)), atol=1e-11)
+    np.testing.assert_allclose(s2.u[0], np.tile(s1.u, (ny, 1)), atol=1e-11)
+    assert np.abs(s2.u[1]).max() < 1e-11
+
+
+def test_sbdf2_zero_stability_region():
+    """Eq:ZeroS3 for SBDF2 is bounded iff the eigenvalues of A^{-1}G lie in (0, 4/3)."""
+    lam_max = GOLDEN["sbdf2_zero_stability"]["lambda_max_stable"]
+    for lam, stable in ((0.05, True), (1.0, True), (1.3, True), (1.36, False), (2.0, False)):
+        roots = np.roots([1.0, -2.0 * (1.0 - lam), 1.0 - lam])
+        assert (np.abs(roots).max() < 1.0) == stable == (lam < lam_max)
+    n = 32
+    _, h, eta, _ = I.testproblem_1d(n, 1.0, 1.0)
+    hx = O.deriv(h, 1.0)
+    c = O.precond_coeffs(eta, hx)
+    Gd = O.dense_G_1d(eta, hx, 1.0)
+    lam_top = O.generalized_eigenvalues(Gd, O.dense_A_1d(c["sigma"], c["alpha"], n, 1.0)).max()
+    assert O.sbdf2_zero_stability_growth(Gd, O.dense_A_1d(c["sigma"], c["alpha"], n, 1.0)) < 10
+    s = 0.7 * lam_top / lam_max                     # pushes the top eigenvalue past 4/3
+    assert O.sbdf2_zero_stability_growth(
+        Gd, O.dense_A_1d(s * c["sigma"], s * c["alpha"], n, 1.0), nsteps=400) > 1e3
