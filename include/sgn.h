@@ -1,0 +1,209 @@
+/*
+ * sgn.h — C ABI of the GB300 (sm_103a) library for the preconditioned constraint solve of
+ * the Serre-Green-Naghdi (SGN) equations and the time integrators built on it.
+ *
+ * Paper: L. Feng, D. Shirokoff, W. Choi, "Preconditioning and Linearly Implicit Time
+ * Integration for the Serre-Green-Naghdi Equations" (arXiv 2506.16045).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns sgn_status; no C++ exception crosses this boundary and the
+ *    library never aborts the process.  sgn_last_error() gives a message for the last
+ *    failure on a context.
+ *  - Array arguments are DEVICE pointers owned by the caller (for example the data_ptr of
+ *    a CUDA tensor), contiguous, float64.  The library owns only the workspace inside
+ *    sgn_ctx, sgn_layout and sgn_state objects.
+ *  - Calls are asynchronous on the given stream (a cudaStream_t passed as void*; NULL is
+ *    the legacy default stream).  A call that returns host-side information (info/out
+ *    arrays) synchronises that stream first and says so.
+ *  - Batches: a layout packs `count` independent periodic instances.  The real fields of
+ *    instance i occupy [off_i, off_i + N_i) of every packed scalar array, with
+ *    off_i = N_0 + ... + N_{i-1} and N_i = nx*ny.  A 1d vector field is one packed array;
+ *    a 2d vector field is two packed planes: x components of all instances first, then y
+ *    components (the plane stride is the layout's total point count P).  A 2d scalar field
+ *    is row-major [ny][nx] (x fastest).
+ *  - Grid (§6.1): x_j = j Lx/nx; spectral derivatives D = F^{-1}(iK)F with
+ *    k_j = 2 pi j/L, j = -n/2+1..n/2-1, and the n/2 wavenumber set to 0.
+ *    nx, ny must be powers of two; 1d needs 8 <= nx <= 8192.
+ */
+#ifndef SGN_H
+#define SGN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SGN_OK = 0,
+  SGN_ERR_INVALID_ARG = 1,        /* null pointer, bad count, inconsistent grids */
+  SGN_ERR_UNSUPPORTED_SIZE = 2,   /* n not a power of two or outside the supported range */
+  SGN_ERR_NOMEM = 3,              /* device allocation failed */
+  SGN_ERR_CUDA = 4,               /* a CUDA runtime call failed (message in sgn_last_error) */
+  SGN_ERR_NOT_CONVERGED = 5,      /* PCG hit maxit (or the refinement cap) before rtol */
+  SGN_ERR_BREAKDOWN = 6,          /* NaN/Inf or p.Gp <= 0 inside PCG */
+  SGN_ERR_NONPOSITIVE_DEPTH = 7,  /* eta_min <= 0 (or NaN): the theorem needs eta > 0 */
+  SGN_ERR_PENDING = 8,            /* serving: request not finished */
+  SGN_ERR_TIMEOUT = 9,            /* a bounded device wait gave up */
+  SGN_ERR_REJECTED = 10           /* serving: request footprint above the memory budget */
+} sgn_status;
+
+typedef struct sgn_ctx sgn_ctx;
+typedef struct sgn_layout sgn_layout;
+typedef struct sgn_state sgn_state;
+typedef void* sgn_stream;         /* cudaStream_t */
+
+/* One periodic grid.  dim = 1: ny must be 1 and Ly is ignored.  g is the gravity constant
+ * (the paper sets g = 1 after non-dimensionalising, §2.1; it is kept explicit here). */
+typedef struct {
+  int dim;
+  int nx, ny;
+  double Lx, Ly;
+  double g;
+} sgn_grid;
+
+/* Preconditioner A = sigma I - alpha grad(div) (Def:A, §4) and the bound kappa_ub on the
+ * condition number of A^{-1}G (Theorem 4.1).  flat = 1 when max|grad h| <= 1e-12. */
+typedef struct {
+  double sigma, alpha, kappa_ub;
+  int flat;
+} sgn_precond;
+
+typedef enum {
+  SGN_COEF_OPT = 0,               /* Eq:FlatbathCoeff / Eq:Optcoeff / Eq:Optcoeffb (§4) */
+  SGN_COEF_REPLACEMENT = 1        /* sigma**, alpha** of the replacement remark (§4) */
+} sgn_coef_kind;
+
+typedef enum {
+  SGN_PREC_FP64 = 0,              /* every operation in float64 */
+  SGN_PREC_MIXED = 1              /* float32 inner PCG (matvecs, FFTs, vectors) with float64
+                                     dot accumulation, inside float64 iterative refinement */
+} sgn_precision;
+
+typedef struct {
+  int iters;                      /* PCG iterations (summed over refinements when mixed) */
+  int refinements;                /* float32 inner solves (mixed), 0 for FP64 */
+  double rel_resid_Ainv;          /* sqrt(r.A^{-1}r)/sqrt(b.A^{-1}b) at exit (float64 residual) */
+  int status;                     /* sgn_status of this instance */
+} sgn_pcg_info;
+
+/* ---------------------------------------------------------------------------------- */
+/* Context and layouts                                                                 */
+/* ---------------------------------------------------------------------------------- */
+
+/* Creates a context on `device` (made current for the call).  Allocates the twiddle
+ * tables (~384 KB).  workspace_bytes is a hint (0 = grow on demand). */
+sgn_status sgn_create(sgn_ctx** ctx, int device, size_t workspace_bytes);
+void sgn_destroy(sgn_ctx* ctx);
+const char* sgn_last_error(const sgn_ctx* ctx);
+const char* sgn_status_string(sgn_status s);
+
+/* Packs `count` instances (host array `grids`).  count > 1 needs dim = 1 for every grid;
+ * 2d layouts hold exactly one instance.  Allocates the layout's device descriptors and
+ * spectral workspace. */
+sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid* grids, sgn_layout** out);
+void sgn_layout_destroy(sgn_layout* lay);
+/* Total packed points P (per component). */
+long long sgn_layout_points(const sgn_layout* lay);
+/* offsets[0..count]: start of each instance in a packed scalar array (host array). */
+sgn_status sgn_layout_offsets(const sgn_layout* lay, long long* offsets);
+
+/* ---------------------------------------------------------------------------------- */
+/* Hot-path operations                                                                 */
+/* ---------------------------------------------------------------------------------- */
+
+/* Spectral gradient (§6.1): gradf = D f.  f: packed scalar [P]; gradf: packed vector
+ * ([P] in 1d, [2P] in 2d).  Used for grad h (the discrete bathymetry slope). */
+sgn_status sgn_spectral_grad(sgn_ctx* ctx, const sgn_layout* lay, const double* f, double* gradf,
+                             sgn_stream stream);
+
+/* Preconditioner coefficients (Eq:MaxMinWaveFields, Eq:FlatbathCoeff, Eq:Optcoeff,
+ * Eq:Optcoeffb; replacement coefficients of §4).  eta: [P]; gradh: vector.  out: HOST
+ * array [count]; the call synchronises the stream.  Returns SGN_ERR_NONPOSITIVE_DEPTH if
+ * some instance has eta_min <= 0. */
+sgn_status sgn_precond_coeffs(sgn_ctx* ctx, const sgn_layout* lay, const double* eta,
+                              const double* gradh, sgn_coef_kind kind, sgn_precond* out,
+                              sgn_stream stream);
+
+/* Constraint operator (Def:G, §2.2):
+ *   Gu = eta u - grad(eta^3/3 div u) - grad(eta^2/2 grad h.u) + eta^2/2 grad h (div u)
+ *        + eta grad h (grad h.u).
+ * eta: [P]; gradh, u, Gu: vectors.  float64. */
+sgn_status sgn_apply_operator(sgn_ctx* ctx, const sgn_layout* lay, const double* eta,
+                              const double* gradh, const double* u, double* Gu, sgn_stream stream);
+
+/* Preconditioner solve z = A^{-1} r with A = sigma I - alpha grad(div) (Def:A): per
+ * Fourier mode 1/(sigma + alpha k^2) in 1d, (sigma I + alpha k k^T)^{-1} in 2d.  P: HOST
+ * array [count] of coefficients (from sgn_precond_coeffs or the caller). */
+sgn_status sgn_precond_solve(sgn_ctx* ctx, const sgn_layout* lay, const sgn_precond* P,
+                             const double* r, double* z, sgn_stream stream);
+
+/* Preconditioned conjugate gradients for G_{eta,h} x = b with preconditioner A (§3.2,
+ * Eq:PCGLinSyst; §4).  x holds the initial guess on entry and the solution on exit.
+ * Stops when sqrt(r.A^{-1}r) <= rtol sqrt(b.A^{-1}b).  P: HOST array [count] or NULL to
+ * compute the optimal coefficients per instance on the device.  prec = SGN_PREC_MIXED runs
+ * float32 PCG inner solves inside float64 iterative refinement (the refinement residual
+ * b - Gx, the dot accumulations and x are float64).  info: HOST array [count] or NULL;
+ * when non-NULL the call synchronises the stream and returns the worst instance status. */
+sgn_status sgn_pcg(sgn_ctx* ctx, const sgn_layout* lay, const double* eta, const double* gradh,
+                   const sgn_precond* P, const double* b, double* x, double rtol, int maxit,
+                   sgn_precision prec, sgn_pcg_info* info, sgn_stream stream);
+
+/* Right-hand side of the DAE form (Eq:DAE_DSWE, §5): f_eta = -div(eta u),
+ * f_U = -g eta grad(zeta) - div(eta u (x) u) + F(eta, u, h) with F from Def:bigF and
+ * (u.grad)^2 h read as u.grad(u.grad h).  zeta = eta - h.  float64. */
+sgn_status sgn_rhs(sgn_ctx* ctx, const sgn_layout* lay, const double* eta, const double* u,
+                   const double* h, const double* gradh, double* f_eta, double* f_U,
+                   sgn_stream stream);
+
+/* ---------------------------------------------------------------------------------- */
+/* Time integration (§5)                                                               */
+/* ---------------------------------------------------------------------------------- */
+
+typedef struct {
+  double rtol;                    /* constraint-solve tolerance (stopping rule of sgn_pcg) */
+  int maxit;                      /* PCG iteration cap per solve */
+  sgn_precision prec;             /* FP64 or MIXED constraint solves */
+  sgn_coef_kind coef;             /* preconditioner coefficients for the PCG solves */
+  double rtol_inner;              /* mixed: float32 inner tolerance (0 = 1e-5) */
+  int max_refine;                 /* mixed: refinement cap (0 = 12) */
+} sgn_opts;
+
+typedef struct {
+  long long solves;               /* constraint solves since init */
+  long long iterations;           /* PCG iterations since init */
+  int max_iters;                  /* largest iteration count of one solve */
+  int status;                     /* worst status seen (sticky) */
+  double t;                       /* simulated time of instance 0 */
+  long long step;                 /* steps taken */
+} sgn_state_stats;
+
+/* Binds caller-owned packed arrays: eta [P], U (vector), u (vector), h [P], gradh (vector,
+ * written by sgn_state_init).  Allocates the library-owned stage/history workspace. */
+sgn_status sgn_state_create(sgn_ctx* ctx, const sgn_layout* lay, double* eta, double* U,
+                            double* u, const double* h, double* gradh, sgn_state** out);
+/* gradh = D h, U = G_{eta,h} u (Eq:DSWEcf4), clears history and counters. */
+sgn_status sgn_state_init(sgn_state* st, sgn_stream stream);
+/* Classical RK4 with one constraint solve per stage 2..4 and one for u_{n+1} (Eq:ERK,
+ * §5.1); U stages start from U_n.  dt: HOST array [count] (per-instance step). */
+sgn_status sgn_step_rk4(sgn_state* st, const double* dt, int nsteps, const sgn_opts* opts,
+                        sgn_stream stream);
+/* Adams-Bashforth of order 2..4 (Eq:AB, Table 1, §5.2), one solve per step; the first
+ * order-1 steps after init are RK4 steps of the same dt. */
+sgn_status sgn_step_abk(sgn_state* st, int order, const double* dt, int nsteps,
+                        const sgn_opts* opts, sgn_stream stream);
+/* Linearly implicit SBDF2 (Eq:MM with Table 1's SBDF2 row, §5.3): one A-solve per step,
+ * no Krylov iteration; A fixed from the state at init (§6.5).  The first step after init
+ * is an RK4 step. */
+sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nsteps, const sgn_opts* opts,
+                           sgn_stream stream);
+/* Synchronises the stream used by the last step call and reports counters. */
+sgn_status sgn_state_get_stats(sgn_state* st, sgn_state_stats* out);
+void sgn_state_free(sgn_state* st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGN_H */

@@ -1,0 +1,48 @@
+// Internal interface of the 2d (doubly periodic) kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "sgn_internal.h"
+
+namespace sgn {
+
+// One 2d instance: fields [ny][nx] row-major; vector fields are two planes of P = nx ny.
+struct Layout2d {
+  int nx = 0, ny = 0, lx = 0, ly = 0;
+  double Lx = 0.0, Ly = 0.0;
+  long long P = 0;
+  void* work = nullptr;      // device workspace (complex planes and reduction scratch)
+  size_t work_bytes = 0;
+};
+
+cudaError_t layout2d_create(Layout2d& L, const sgn_grid& g);
+void layout2d_destroy(Layout2d& L);
+size_t layout2d_res_bytes(const Layout2d& L);
+
+cudaError_t launch_grad2d(const Layout2d& L, const void* tw64, const double* f, double* gradf,
+                          cudaStream_t s);
+cudaError_t launch_coeffs2d(const Layout2d& L, const double* eta, const double* gradh, int kind,
+                            SolveRec* rec, cudaStream_t s);
+cudaError_t launch_apply_G2d(const Layout2d& L, const void* tw64, const double* eta,
+                             const double* gradh, const double* u, double* Gu, cudaStream_t s);
+cudaError_t launch_precond2d(const Layout2d& L, const void* tw64, const SolveRec* rec,
+                             const double* r, double* z, cudaStream_t s);
+cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, int precision,
+                         const double* eta, const double* gradh, const double* b, double* x,
+                         const SolveRec* given, int kind, double rtol, double rtol_inner,
+                         int maxit, int max_refine, SolveRec* rec, cudaStream_t s);
+cudaError_t launch_rhs2d(const Layout2d& L, const void* tw64, double g, const double* eta,
+                         const double* u, const double* h, const double* gradh, double* f_eta,
+                         double* f_U, cudaStream_t s);
+cudaError_t launch_lincomb2d(const Layout2d& L, const double* dt, double* out,
+                             const double* const* x, const double* a, int nx,
+                             const double* const* f, const double* c, int nf, int components,
+                             cudaStream_t s);
+cudaError_t launch_linimp_res2d(const Layout2d& L, const void* tw64, const SolveRec* A,
+                                const double* eta, const double* gradh, const double* u,
+                                const double* U, void* res_hat, cudaStream_t s);
+cudaError_t launch_linimp_solve2d(const Layout2d& L, const void* tw64, const SolveRec* A,
+                                  const void* res1_hat, const void* res0_hat, double c1,
+                                  double c0, double* u, cudaStream_t s);
+
+}  // namespace sgn

@@ -1,0 +1,898 @@
+// C ABI of the SGN library: contexts, batch layouts, the hot-path entry points and the
+// time integrators (host orchestration of the kernels in sgn_1d.cu / sgn_2d.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <initializer_list>
+#include <utility>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/sgn.h"
+#include "sgn_internal.h"
+#include "sgn_2d.h"
+
+using sgn::Inst1d;
+using sgn::Layout1d;
+using sgn::SolveRec;
+
+struct sgn_ctx {
+  int device = 0;
+  void* tw64 = nullptr;
+  void* tw32 = nullptr;
+  std::string err;
+};
+
+struct sgn_layout {
+  sgn_ctx* ctx = nullptr;
+  int count = 0;
+  int dim = 1;
+  std::vector<sgn_grid> grids;
+  std::vector<long long> offsets;
+  long long points = 0;
+  Layout1d l1;
+  sgn::Layout2d l2;
+  void* ws = nullptr;               // spectral workspace
+  double* scratch = nullptr;        // 5 P doubles (rhs intermediates)
+  SolveRec* rec = nullptr;          // [count] per-instance solve reports
+  SolveRec* given = nullptr;        // [count] caller-provided coefficients
+};
+
+namespace {
+
+struct DevStats {
+  long long solves;
+  long long iterations;
+  int max_iters;
+  int status;
+};
+
+__global__ void k_accum(const SolveRec* __restrict__ rec, int count, DevStats* st) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    for (int i = 0; i < count; ++i) {
+      st->solves += 1;
+      st->iterations += rec[i].iters;
+      st->max_iters = max(st->max_iters, rec[i].iters);
+      if (rec[i].status > st->status) st->status = rec[i].status;
+    }
+  }
+}
+
+// out = sum_t a_t x_t + dt_i sum_t c_t f_t over the points of each instance
+struct LinComb {
+  const double* x[4];
+  double a[4];
+  int nx;
+  const double* f[4];
+  double c[4];
+  int nf;
+};
+
+__global__ void k_lincomb(const Inst1d* __restrict__ insts, const double* __restrict__ dt,
+                          double* __restrict__ out, LinComb lc, long long plane,
+                          int components) {
+  const Inst1d I = insts[blockIdx.x];
+  const double d = dt[blockIdx.x];
+  for (int comp = 0; comp < components; ++comp) {
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+      const long long q = comp * plane + I.off + j;
+      double acc = 0.0, accf = 0.0;
+      for (int t = 0; t < lc.nx; ++t) acc += lc.a[t] * lc.x[t][q];
+      for (int t = 0; t < lc.nf; ++t) accf += lc.c[t] * lc.f[t][q];
+      out[q] = acc + d * accf;
+    }
+  }
+}
+
+sgn_status fail(sgn_ctx* ctx, sgn_status s, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return s;
+}
+
+sgn_status cuda_fail(sgn_ctx* ctx, cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(ctx, SGN_ERR_NOMEM, std::string(where) + ": out of device memory");
+  }
+  return fail(ctx, SGN_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define SGN_CUDA(ctx, expr)                                   \
+  do {                                                        \
+    cudaError_t e_ = (expr);                                  \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #expr); \
+  } while (0)
+
+inline cudaStream_t as_stream(sgn_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int ilog2_exact(int n) {
+  if (n <= 0 || (n & (n - 1))) return -1;
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+sgn_status check_layout(const sgn_layout* lay) {
+  if (!lay || !lay->ctx) return SGN_ERR_INVALID_ARG;
+  return SGN_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+// =======================================================================================
+// Context
+// =======================================================================================
+
+extern "C" const char* sgn_status_string(sgn_status s) {
+  switch (s) {
+    case SGN_OK: return "ok";
+    case SGN_ERR_INVALID_ARG: return "invalid argument";
+    case SGN_ERR_UNSUPPORTED_SIZE: return "unsupported size";
+    case SGN_ERR_NOMEM: return "out of device memory";
+    case SGN_ERR_CUDA: return "CUDA error";
+    case SGN_ERR_NOT_CONVERGED: return "not converged";
+    case SGN_ERR_BREAKDOWN: return "PCG breakdown";
+    case SGN_ERR_NONPOSITIVE_DEPTH: return "non-positive depth";
+    case SGN_ERR_PENDING: return "pending";
+    case SGN_ERR_TIMEOUT: return "timeout";
+    case SGN_ERR_REJECTED: return "rejected";
+  }
+  return "unknown status";
+}
+
+extern "C" sgn_status sgn_create(sgn_ctx** out, int device, size_t workspace_bytes) {
+  (void)workspace_bytes;
+  if (!out) return SGN_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return SGN_ERR_CUDA;
+  }
+  sgn_ctx* ctx = new (std::nothrow) sgn_ctx();
+  if (!ctx) return SGN_ERR_NOMEM;
+  ctx->device = device;
+  DeviceGuard g(device);
+  if (cudaMalloc(&ctx->tw64, sizeof(double) * 2 * sgn::kTwiddleN) != cudaSuccess ||
+      cudaMalloc(&ctx->tw32, sizeof(float) * 2 * sgn::kTwiddleN) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(ctx->tw64);
+    delete ctx;
+    return SGN_ERR_NOMEM;
+  }
+  if (sgn::twiddles_init(ctx->tw64, ctx->tw32, 0) != cudaSuccess ||
+      cudaStreamSynchronize(0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(ctx->tw64);
+    cudaFree(ctx->tw32);
+    delete ctx;
+    return SGN_ERR_CUDA;
+  }
+  *out = ctx;
+  return SGN_OK;
+}
+
+extern "C" void sgn_destroy(sgn_ctx* ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaFree(ctx->tw64);
+  cudaFree(ctx->tw32);
+  delete ctx;
+}
+
+extern "C" const char* sgn_last_error(const sgn_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : "null context";
+}
+
+// =======================================================================================
+// Layouts
+// =======================================================================================
+
+extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid* grids,
+                                        sgn_layout** out) {
+  if (!ctx || !grids || !out || count <= 0) return fail(ctx, SGN_ERR_INVALID_ARG, "layout args");
+  *out = nullptr;
+  const int dim = grids[0].dim;
+  if (dim != 1 && dim != 2) return fail(ctx, SGN_ERR_INVALID_ARG, "dim must be 1 or 2");
+  if (dim == 2 && count != 1) return fail(ctx, SGN_ERR_INVALID_ARG, "2d layouts hold one instance");
+  for (int i = 0; i < count; ++i) {
+    const sgn_grid& g = grids[i];
+    if (g.dim != dim || !(g.Lx > 0.0) || (dim == 2 && !(g.Ly > 0.0)))
+      return fail(ctx, SGN_ERR_INVALID_ARG, "grid fields");
+    if (dim == 1 && g.ny != 1) return fail(ctx, SGN_ERR_INVALID_ARG, "1d grid needs ny = 1");
+    const int lx = ilog2_exact(g.nx);
+    if (dim == 1 && (lx < 3 || lx > 13))
+      return fail(ctx, SGN_ERR_UNSUPPORTED_SIZE, "1d nx must be a power of two in [8, 8192]");
+    if (dim == 2) {
+      const int ly = ilog2_exact(g.ny);
+      if (lx < 3 || ly < 3 || lx > 10 || ly > 10)
+        return fail(ctx, SGN_ERR_UNSUPPORTED_SIZE, "2d nx, ny must be powers of two in [8, 1024]");
+    }
+  }
+  sgn_layout* lay = new (std::nothrow) sgn_layout();
+  if (!lay) return SGN_ERR_NOMEM;
+  lay->ctx = ctx;
+  lay->count = count;
+  lay->dim = dim;
+  lay->grids.assign(grids, grids + count);
+  lay->offsets.resize(count + 1);
+  long long off = 0;
+  for (int i = 0; i < count; ++i) {
+    lay->offsets[i] = off;
+    off += (long long)grids[i].nx * grids[i].ny;
+  }
+  lay->offsets[count] = off;
+  lay->points = off;
+  DeviceGuard gd(ctx->device);
+  auto cleanup = [&](sgn_status s, const char* msg) {
+    sgn_layout_destroy(lay);
+    return fail(ctx, s, msg);
+  };
+  if (dim == 1) {
+    Layout1d& L = lay->l1;
+    L.count = count;
+    L.points = off;
+    L.h_inst = new Inst1d[count];
+    long long ws = 0;
+    std::vector<int> ids;
+    for (int l = 3; l <= 13; ++l) {
+      L.class_begin[l] = (int)ids.size();
+      for (int i = 0; i < count; ++i)
+        if (ilog2_exact(grids[i].nx) == l) ids.push_back(i);
+      L.class_end[l] = (int)ids.size();
+    }
+    for (int i = 0; i < count; ++i) {
+      Inst1d& I = L.h_inst[i];
+      I.n = grids[i].nx;
+      I.log2n = ilog2_exact(I.n);
+      I.L = grids[i].Lx;
+      I.off = lay->offsets[i];
+      I.ws = ws;
+      ws += (long long)sgn::kWsVectors * (I.n / 2 + 1);
+    }
+    L.ws_cplx = ws;
+    if (cudaMalloc(&L.d_inst, sizeof(Inst1d) * count) != cudaSuccess ||
+        cudaMalloc(&L.d_ids, sizeof(int) * count) != cudaSuccess ||
+        cudaMalloc(&lay->ws, sizeof(double) * 2 * ws) != cudaSuccess ||
+        cudaMalloc(&lay->scratch, sizeof(double) * 5 * off) != cudaSuccess ||
+        cudaMalloc(&lay->rec, sizeof(SolveRec) * count) != cudaSuccess ||
+        cudaMalloc(&lay->given, sizeof(SolveRec) * count) != cudaSuccess) {
+      cudaGetLastError();
+      return cleanup(SGN_ERR_NOMEM, "layout allocation");
+    }
+    if (cudaMemcpy(L.d_inst, L.h_inst, sizeof(Inst1d) * count, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(L.d_ids, ids.data(), sizeof(int) * count, cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return cleanup(SGN_ERR_CUDA, "layout upload");
+    }
+  } else {
+    cudaError_t e = sgn::layout2d_create(lay->l2, grids[0]);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cleanup(e == cudaErrorMemoryAllocation ? SGN_ERR_NOMEM : SGN_ERR_CUDA, "2d layout");
+    }
+    if (cudaMalloc(&lay->rec, sizeof(SolveRec)) != cudaSuccess ||
+        cudaMalloc(&lay->given, sizeof(SolveRec)) != cudaSuccess) {
+      cudaGetLastError();
+      return cleanup(SGN_ERR_NOMEM, "layout allocation");
+    }
+  }
+  *out = lay;
+  return SGN_OK;
+}
+
+extern "C" void sgn_layout_destroy(sgn_layout* lay) {
+  if (!lay) return;
+  DeviceGuard g(lay->ctx->device);
+  cudaFree(lay->l1.d_inst);
+  cudaFree(lay->l1.d_ids);
+  delete[] lay->l1.h_inst;
+  sgn::layout2d_destroy(lay->l2);
+  cudaFree(lay->ws);
+  cudaFree(lay->scratch);
+  cudaFree(lay->rec);
+  cudaFree(lay->given);
+  delete lay;
+}
+
+extern "C" long long sgn_layout_points(const sgn_layout* lay) { return lay ? lay->points : -1; }
+
+extern "C" sgn_status sgn_layout_offsets(const sgn_layout* lay, long long* offsets) {
+  if (!lay || !offsets) return SGN_ERR_INVALID_ARG;
+  std::copy(lay->offsets.begin(), lay->offsets.end(), offsets);
+  return SGN_OK;
+}
+
+// =======================================================================================
+// Hot-path operations
+// =======================================================================================
+
+namespace {
+
+sgn_status upload_given(sgn_layout* lay, const sgn_precond* P, cudaStream_t s) {
+  std::vector<SolveRec> h(lay->count);
+  for (int i = 0; i < lay->count; ++i) {
+    SolveRec r = {};
+    r.sigma = P[i].sigma;
+    r.alpha = P[i].alpha;
+    r.kappa_ub = P[i].kappa_ub;
+    r.flat = P[i].flat;
+    if (!(r.sigma > 0.0) || !(r.alpha > 0.0))
+      return fail(lay->ctx, SGN_ERR_INVALID_ARG, "preconditioner sigma, alpha must be > 0");
+    h[i] = r;
+  }
+  SGN_CUDA(lay->ctx, cudaMemcpyAsync(lay->given, h.data(), sizeof(SolveRec) * lay->count,
+                                     cudaMemcpyHostToDevice, s));
+  // pageable source: the copy is staged before return, but keep `h` alive until it lands
+  SGN_CUDA(lay->ctx, cudaStreamSynchronize(s));
+  return SGN_OK;
+}
+
+sgn_status fetch_recs(sgn_layout* lay, std::vector<SolveRec>& h, cudaStream_t s) {
+  h.resize(lay->count);
+  SGN_CUDA(lay->ctx, cudaMemcpyAsync(h.data(), lay->rec, sizeof(SolveRec) * lay->count,
+                                     cudaMemcpyDeviceToHost, s));
+  SGN_CUDA(lay->ctx, cudaStreamSynchronize(s));
+  return SGN_OK;
+}
+
+}  // namespace
+
+extern "C" sgn_status sgn_spectral_grad(sgn_ctx* ctx, const sgn_layout* lay, const double* f,
+                                        double* gradf, sgn_stream stream) {
+  if (!ctx || check_layout(lay) || !f || !gradf) return fail(ctx, SGN_ERR_INVALID_ARG, "grad");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = lay->dim == 1
+                      ? sgn::launch_deriv1d(lay->l1, ctx->tw64, f, gradf, as_stream(stream))
+                      : sgn::launch_grad2d(lay->l2, ctx->tw64, f, gradf, as_stream(stream));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sgn_spectral_grad");
+  return SGN_OK;
+}
+
+extern "C" sgn_status sgn_precond_coeffs(sgn_ctx* ctx, const sgn_layout* lay_c, const double* eta,
+                                         const double* gradh, sgn_coef_kind kind,
+                                         sgn_precond* out, sgn_stream stream) {
+  sgn_layout* lay = const_cast<sgn_layout*>(lay_c);
+  if (!ctx || check_layout(lay) || !eta || !gradh || !out)
+    return fail(ctx, SGN_ERR_INVALID_ARG, "coeffs");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e = lay->dim == 1
+                      ? sgn::launch_coeffs1d(lay->l1, eta, gradh, kind, lay->rec, s)
+                      : sgn::launch_coeffs2d(lay->l2, eta, gradh, kind, lay->rec, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sgn_precond_coeffs");
+  std::vector<SolveRec> h;
+  sgn_status st = fetch_recs(lay, h, s);
+  if (st) return st;
+  sgn_status worst = SGN_OK;
+  for (int i = 0; i < lay->count; ++i) {
+    out[i].sigma = h[i].sigma;
+    out[i].alpha = h[i].alpha;
+    out[i].kappa_ub = h[i].kappa_ub;
+    out[i].flat = h[i].flat;
+    if (h[i].status != SGN_OK) worst = (sgn_status)h[i].status;
+  }
+  if (worst != SGN_OK) return fail(ctx, worst, "non-positive depth in some instance");
+  return SGN_OK;
+}
+
+extern "C" sgn_status sgn_apply_operator(sgn_ctx* ctx, const sgn_layout* lay, const double* eta,
+                                         const double* gradh, const double* u, double* Gu,
+                                         sgn_stream stream) {
+  if (!ctx || check_layout(lay) || !eta || !gradh || !u || !Gu)
+    return fail(ctx, SGN_ERR_INVALID_ARG, "apply_operator");
+  DeviceGuard g(ctx->device);
+  cudaError_t e =
+      lay->dim == 1
+          ? sgn::launch_apply_G1d(lay->l1, ctx->tw64, eta, gradh, u, Gu, as_stream(stream))
+          : sgn::launch_apply_G2d(lay->l2, ctx->tw64, eta, gradh, u, Gu, as_stream(stream));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sgn_apply_operator");
+  return SGN_OK;
+}
+
+extern "C" sgn_status sgn_precond_solve(sgn_ctx* ctx, const sgn_layout* lay_c,
+                                        const sgn_precond* P, const double* r, double* z,
+                                        sgn_stream stream) {
+  sgn_layout* lay = const_cast<sgn_layout*>(lay_c);
+  if (!ctx || check_layout(lay) || !P || !r || !z)
+    return fail(ctx, SGN_ERR_INVALID_ARG, "precond_solve");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  sgn_status st = upload_given(lay, P, s);
+  if (st) return st;
+  cudaError_t e = lay->dim == 1
+                      ? sgn::launch_precond1d(lay->l1, ctx->tw64, lay->given, r, z, s)
+                      : sgn::launch_precond2d(lay->l2, ctx->tw64, lay->given, r, z, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sgn_precond_solve");
+  return SGN_OK;
+}
+
+namespace {
+
+sgn_status run_pcg(sgn_layout* lay, const double* eta, const double* gradh, const SolveRec* given,
+                   sgn_coef_kind kind, const double* b, double* x, double rtol, int maxit,
+                   sgn_precision prec, double rtol_inner, int max_refine, cudaStream_t s) {
+  sgn_ctx* ctx = lay->ctx;
+  if (rtol_inner <= 0.0) rtol_inner = 1e-5;
+  if (max_refine <= 0) max_refine = 12;
+  cudaError_t e;
+  if (lay->dim == 1) {
+    e = sgn::launch_pcg1d(lay->l1, ctx->tw64, ctx->tw32, prec, eta, gradh, b, x, given, kind, rtol,
+                          rtol_inner, maxit, max_refine, lay->rec, lay->ws, s);
+  } else {
+    e = sgn::launch_pcg2d(lay->l2, ctx->tw64, ctx->tw32, prec, eta, gradh, b, x, given, kind, rtol,
+                          rtol_inner, maxit, max_refine, lay->rec, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "pcg launch");
+  return SGN_OK;
+}
+
+}  // namespace
+
+extern "C" sgn_status sgn_pcg(sgn_ctx* ctx, const sgn_layout* lay_c, const double* eta,
+                              const double* gradh, const sgn_precond* P, const double* b,
+                              double* x, double rtol, int maxit, sgn_precision prec,
+                              sgn_pcg_info* info, sgn_stream stream) {
+  sgn_layout* lay = const_cast<sgn_layout*>(lay_c);
+  if (!ctx || check_layout(lay) || !eta || !gradh || !b || !x || !(rtol > 0.0) || maxit < 0 ||
+      (prec != SGN_PREC_FP64 && prec != SGN_PREC_MIXED))
+    return fail(ctx, SGN_ERR_INVALID_ARG, "pcg args");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  const SolveRec* given = nullptr;
+  if (P) {
+    sgn_status st = upload_given(lay, P, s);
+    if (st) return st;
+    given = lay->given;
+  }
+  sgn_status st = run_pcg(lay, eta, gradh, given, SGN_COEF_OPT, b, x, rtol, maxit, prec, 0.0, 0, s);
+  if (st) return st;
+  if (!info) return SGN_OK;
+  std::vector<SolveRec> h;
+  st = fetch_recs(lay, h, s);
+  if (st) return st;
+  sgn_status worst = SGN_OK;
+  for (int i = 0; i < lay->count; ++i) {
+    info[i].iters = h[i].iters;
+    info[i].refinements = h[i].refinements;
+    info[i].rel_resid_Ainv = h[i].ratio;
+    info[i].status = h[i].status;
+    if (h[i].status > worst) worst = (sgn_status)h[i].status;
+  }
+  if (worst != SGN_OK) return fail(ctx, worst, "pcg: some instance did not finish cleanly");
+  return SGN_OK;
+}
+
+extern "C" sgn_status sgn_rhs(sgn_ctx* ctx, const sgn_layout* lay, const double* eta,
+                              const double* u, const double* h, const double* gradh,
+                              double* f_eta, double* f_U, sgn_stream stream) {
+  if (!ctx || check_layout(lay) || !eta || !u || !h || !gradh || !f_eta || !f_U)
+    return fail(ctx, SGN_ERR_INVALID_ARG, "rhs args");
+  DeviceGuard g(ctx->device);
+  const double grav = lay->grids[0].g;
+  cudaError_t e =
+      lay->dim == 1
+          ? sgn::launch_rhs1d(lay->l1, ctx->tw64, grav, eta, u, h, gradh, f_eta, f_U, lay->scratch,
+                              as_stream(stream))
+          : sgn::launch_rhs2d(lay->l2, ctx->tw64, grav, eta, u, h, gradh, f_eta, f_U,
+                              as_stream(stream));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sgn_rhs");
+  return SGN_OK;
+}
+
+// =======================================================================================
+// Time integration
+// =======================================================================================
+
+enum HistKind { HIST_NONE = 0, HIST_AB = 1, HIST_SBDF2 = 2 };
+
+struct sgn_state {
+  sgn_layout* lay = nullptr;
+  double* eta = nullptr;
+  double* U = nullptr;
+  double* u = nullptr;
+  const double* h = nullptr;
+  double* gradh = nullptr;
+  int d = 1;                        // components of a vector field
+  long long P = 0;
+  // library-owned workspace (each array d*P or P doubles)
+  std::vector<double*> bufs;
+  double* fe[4] = {nullptr};        // RK4 stage right-hand sides
+  double* fU[4] = {nullptr};
+  double* he[4] = {nullptr};        // multistep history (oldest first)
+  double* hU[4] = {nullptr};
+  double* eta_s = nullptr;
+  double* U_s = nullptr;
+  double* u_s = nullptr;
+  double* eta_p = nullptr;          // SBDF2 previous level
+  double* U_p = nullptr;
+  double* u_p = nullptr;
+  void* res0 = nullptr;             // SBDF2 residual spectra (previous / current)
+  void* res1 = nullptr;
+  double* dt_dev = nullptr;
+  SolveRec* A_fixed = nullptr;      // SBDF2 preconditioner, fixed at init
+  DevStats* stats = nullptr;
+  int hist = HIST_NONE;
+  int levels = 0;                   // valid multistep levels
+  std::vector<double> dt_last;
+  double t = 0.0;
+  long long step = 0;
+  cudaStream_t last = nullptr;
+};
+
+namespace {
+
+sgn_status alloc_state(sgn_state* st) {
+  const long long P = st->P;
+  const long long V = st->d * P;
+  auto get = [&](long long n) -> double* {
+    double* p = nullptr;
+    if (cudaMalloc(&p, sizeof(double) * (size_t)std::max<long long>(n, 1)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    st->bufs.push_back(p);
+    return p;
+  };
+  for (int i = 0; i < 4; ++i) {
+    if (!(st->fe[i] = get(P)) || !(st->fU[i] = get(V)) || !(st->he[i] = get(P)) ||
+        !(st->hU[i] = get(V)))
+      return SGN_ERR_NOMEM;
+  }
+  if (!(st->eta_s = get(P)) || !(st->U_s = get(V)) || !(st->u_s = get(V)) ||
+      !(st->eta_p = get(P)) || !(st->U_p = get(V)) || !(st->u_p = get(V)) ||
+      !(st->dt_dev = get(st->lay->count)))
+    return SGN_ERR_NOMEM;
+  const size_t res_bytes = st->lay->dim == 1 ? sizeof(double) * 2 * (size_t)(st->lay->l1.ws_cplx /
+                                                                            sgn::kWsVectors)
+                                             : sgn::layout2d_res_bytes(st->lay->l2);
+  if (cudaMalloc(&st->res0, res_bytes) != cudaSuccess ||
+      cudaMalloc(&st->res1, res_bytes) != cudaSuccess ||
+      cudaMalloc(&st->A_fixed, sizeof(SolveRec) * st->lay->count) != cudaSuccess ||
+      cudaMalloc(&st->stats, sizeof(DevStats)) != cudaSuccess) {
+    cudaGetLastError();
+    return SGN_ERR_NOMEM;
+  }
+  return SGN_OK;
+}
+
+sgn_status upload_dt(sgn_state* st, const double* dt, cudaStream_t s) {
+  for (int i = 0; i < st->lay->count; ++i)
+    if (!(dt[i] > 0.0)) return fail(st->lay->ctx, SGN_ERR_INVALID_ARG, "dt must be > 0");
+  bool same = (int)st->dt_last.size() == st->lay->count &&
+              std::equal(st->dt_last.begin(), st->dt_last.end(), dt);
+  if (!same) {
+    st->dt_last.assign(dt, dt + st->lay->count);
+    SGN_CUDA(st->lay->ctx, cudaMemcpyAsync(st->dt_dev, st->dt_last.data(),
+                                           sizeof(double) * st->lay->count,
+                                           cudaMemcpyHostToDevice, s));
+    SGN_CUDA(st->lay->ctx, cudaStreamSynchronize(s));
+  }
+  return SGN_OK;
+}
+
+// out = sum a_t x_t + dt sum c_t f_t for scalar (components=1) or vector fields
+sgn_status lincomb(sgn_state* st, double* out, std::initializer_list<std::pair<const double*, double>> xs,
+                   std::initializer_list<std::pair<const double*, double>> fs, int components,
+                   cudaStream_t s) {
+  LinComb lc{};
+  for (auto& p : xs) {
+    lc.x[lc.nx] = p.first;
+    lc.a[lc.nx] = p.second;
+    ++lc.nx;
+  }
+  for (auto& p : fs) {
+    lc.f[lc.nf] = p.first;
+    lc.c[lc.nf] = p.second;
+    ++lc.nf;
+  }
+  if (st->lay->dim == 1) {
+    k_lincomb<<<st->lay->count, 256, 0, s>>>(st->lay->l1.d_inst, st->dt_dev, out, lc, st->P,
+                                             components);
+  } else {
+    sgn::launch_lincomb2d(st->lay->l2, st->dt_dev, out, lc.x, lc.a, lc.nx, lc.f, lc.c, lc.nf,
+                          components, s);
+  }
+  SGN_CUDA(st->lay->ctx, cudaGetLastError());
+  return SGN_OK;
+}
+
+sgn_status rhs_at(sgn_state* st, const double* eta, const double* u, double* fe, double* fU,
+                  cudaStream_t s) {
+  return sgn_rhs(st->lay->ctx, st->lay, eta, u, st->h, st->gradh, fe, fU, s);
+}
+
+sgn_status solve_at(sgn_state* st, const double* eta, const double* U, double* u,
+                    const sgn_opts* o, cudaStream_t s) {
+  sgn_status r = run_pcg(st->lay, eta, st->gradh, nullptr, o->coef, U, u, o->rtol, o->maxit,
+                         o->prec, o->rtol_inner, o->max_refine, s);
+  if (r) return r;
+  k_accum<<<1, 32, 0, s>>>(st->lay->rec, st->lay->count, st->stats);
+  SGN_CUDA(st->lay->ctx, cudaGetLastError());
+  return SGN_OK;
+}
+
+sgn_status copy_field(sgn_state* st, double* dst, const double* src, long long n, cudaStream_t s) {
+  SGN_CUDA(st->lay->ctx, cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  return SGN_OK;
+}
+
+#define SGN_TRY(expr)            \
+  do {                           \
+    sgn_status s_ = (expr);      \
+    if (s_ != SGN_OK) return s_; \
+  } while (0)
+
+// One RK4 step (Eq:ERK): stages with a_{i,i-1} = 1/2, 1/2, 1 and weights 1/6, 1/3, 1/3, 1/6.
+sgn_status rk4_once(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
+  const int d = st->d;
+  const long long P = st->P, V = d * P;
+  static const double a[4] = {0.0, 0.5, 0.5, 1.0};
+  SGN_TRY(rhs_at(st, st->eta, st->u, st->fe[0], st->fU[0], s));
+  SGN_TRY(copy_field(st, st->u_s, st->u, V, s));
+  for (int i = 1; i < 4; ++i) {
+    SGN_TRY(lincomb(st, st->eta_s, {{st->eta, 1.0}}, {{st->fe[i - 1], a[i]}}, 1, s));
+    SGN_TRY(lincomb(st, st->U_s, {{st->U, 1.0}}, {{st->fU[i - 1], a[i]}}, d, s));
+    SGN_TRY(solve_at(st, st->eta_s, st->U_s, st->u_s, o, s));
+    SGN_TRY(rhs_at(st, st->eta_s, st->u_s, st->fe[i], st->fU[i], s));
+  }
+  const double b0 = 1.0 / 6.0, b1 = 1.0 / 3.0;
+  SGN_TRY(lincomb(st, st->eta, {{st->eta, 1.0}},
+                  {{st->fe[0], b0}, {st->fe[1], b1}, {st->fe[2], b1}, {st->fe[3], b0}}, 1, s));
+  SGN_TRY(lincomb(st, st->U, {{st->U, 1.0}},
+                  {{st->fU[0], b0}, {st->fU[1], b1}, {st->fU[2], b1}, {st->fU[3], b0}}, d, s));
+  SGN_TRY(copy_field(st, st->u, st->u_s, V, s));
+  SGN_TRY(solve_at(st, st->eta, st->U, st->u, o, s));
+  (void)P;
+  st->t += st->dt_last[0];
+  st->step += 1;
+  return SGN_OK;
+}
+
+sgn_status check_opts(sgn_state* st, const sgn_opts* o) {
+  if (!o || !(o->rtol > 0.0) || o->maxit <= 0 ||
+      (o->prec != SGN_PREC_FP64 && o->prec != SGN_PREC_MIXED))
+    return fail(st->lay->ctx, SGN_ERR_INVALID_ARG, "opts");
+  return SGN_OK;
+}
+
+}  // namespace
+
+extern "C" sgn_status sgn_state_create(sgn_ctx* ctx, const sgn_layout* lay, double* eta, double* U,
+                                       double* u, const double* h, double* gradh,
+                                       sgn_state** out) {
+  if (!ctx || check_layout(lay) || !eta || !U || !u || !h || !gradh || !out)
+    return fail(ctx, SGN_ERR_INVALID_ARG, "state args");
+  *out = nullptr;
+  DeviceGuard g(ctx->device);
+  sgn_state* st = new (std::nothrow) sgn_state();
+  if (!st) return SGN_ERR_NOMEM;
+  st->lay = const_cast<sgn_layout*>(lay);
+  st->eta = eta;
+  st->U = U;
+  st->u = u;
+  st->h = h;
+  st->gradh = gradh;
+  st->d = lay->dim;
+  st->P = lay->points;
+  sgn_status r = alloc_state(st);
+  if (r) {
+    sgn_state_free(st);
+    return fail(ctx, r, "state allocation");
+  }
+  *out = st;
+  return SGN_OK;
+}
+
+extern "C" sgn_status sgn_state_init(sgn_state* st, sgn_stream stream) {
+  if (!st) return SGN_ERR_INVALID_ARG;
+  sgn_ctx* ctx = st->lay->ctx;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  SGN_TRY(sgn_spectral_grad(ctx, st->lay, st->h, st->gradh, stream));
+  SGN_TRY(sgn_apply_operator(ctx, st->lay, st->eta, st->gradh, st->u, st->U, stream));
+  cudaError_t e = st->lay->dim == 1
+                      ? sgn::launch_coeffs1d(st->lay->l1, st->eta, st->gradh, SGN_COEF_OPT,
+                                             st->A_fixed, s)
+                      : sgn::launch_coeffs2d(st->lay->l2, st->eta, st->gradh, SGN_COEF_OPT,
+                                             st->A_fixed, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "state init coefficients");
+  SGN_CUDA(ctx, cudaMemsetAsync(st->stats, 0, sizeof(DevStats), s));
+  st->hist = HIST_NONE;
+  st->levels = 0;
+  st->t = 0.0;
+  st->step = 0;
+  st->last = s;
+  return SGN_OK;
+}
+
+extern "C" sgn_status sgn_step_rk4(sgn_state* st, const double* dt, int nsteps,
+                                   const sgn_opts* opts, sgn_stream stream) {
+  if (!st || !dt || nsteps < 0) return SGN_ERR_INVALID_ARG;
+  DeviceGuard g(st->lay->ctx->device);
+  cudaStream_t s = as_stream(stream);
+  SGN_TRY(check_opts(st, opts));
+  SGN_TRY(upload_dt(st, dt, s));
+  st->last = s;
+  for (int k = 0; k < nsteps; ++k) SGN_TRY(rk4_once(st, opts, s));
+  st->hist = HIST_NONE;
+  st->levels = 0;
+  return SGN_OK;
+}
+
+// Adams-Bashforth (Eq:AB, Table 1): w_{n+s} = w_{n+s-1} + dt sum_j b_j f_{n+j}
+extern "C" sgn_status sgn_step_abk(sgn_state* st, int order, const double* dt, int nsteps,
+                                   const sgn_opts* opts, sgn_stream stream) {
+  static const double B[5][4] = {{0, 0, 0, 0},
+                                 {0, 0, 0, 0},
+                                 {-0.5, 1.5, 0, 0},
+                                 {5.0 / 12, -16.0 / 12, 23.0 / 12, 0},
+                                 {-9.0 / 24, 37.0 / 24, -59.0 / 24, 55.0 / 24}};
+  if (!st || !dt || nsteps < 0 || order < 2 || order > 4) return SGN_ERR_INVALID_ARG;
+  DeviceGuard g(st->lay->ctx->device);
+  cudaStream_t s = as_stream(stream);
+  SGN_TRY(check_opts(st, opts));
+  const bool same_dt = (int)st->dt_last.size() == st->lay->count &&
+                       std::equal(st->dt_last.begin(), st->dt_last.end(), dt);
+  if (st->hist != HIST_AB || !same_dt) st->levels = 0;
+  SGN_TRY(upload_dt(st, dt, s));
+  st->last = s;
+  const int d = st->d;
+  auto push = [&]() -> sgn_status {
+    // rotate so that he[levels-1] is the newest
+    if (st->levels == 4) {
+      std::rotate(st->he, st->he + 1, st->he + 4);
+      std::rotate(st->hU, st->hU + 1, st->hU + 4);
+      st->levels = 3;
+    }
+    SGN_TRY(rhs_at(st, st->eta, st->u, st->he[st->levels], st->hU[st->levels], s));
+    st->levels += 1;
+    return SGN_OK;
+  };
+  if (st->levels == 0) SGN_TRY(push());
+  st->hist = HIST_AB;
+  for (int k = 0; k < nsteps; ++k) {
+    if (st->levels < order) {
+      SGN_TRY(rk4_once(st, opts, s));
+    } else {
+      const int L0 = st->levels - order;   // oldest level used
+      const double* const* he = st->he + L0;
+      const double* const* hU = st->hU + L0;
+      if (order == 2) {
+        SGN_TRY(lincomb(st, st->eta, {{st->eta, 1.0}}, {{he[0], B[2][0]}, {he[1], B[2][1]}}, 1, s));
+        SGN_TRY(lincomb(st, st->U, {{st->U, 1.0}}, {{hU[0], B[2][0]}, {hU[1], B[2][1]}}, d, s));
+      } else if (order == 3) {
+        SGN_TRY(lincomb(st, st->eta, {{st->eta, 1.0}},
+                        {{he[0], B[3][0]}, {he[1], B[3][1]}, {he[2], B[3][2]}}, 1, s));
+        SGN_TRY(lincomb(st, st->U, {{st->U, 1.0}},
+                        {{hU[0], B[3][0]}, {hU[1], B[3][1]}, {hU[2], B[3][2]}}, d, s));
+      } else {
+        SGN_TRY(lincomb(st, st->eta, {{st->eta, 1.0}},
+                        {{he[0], B[4][0]}, {he[1], B[4][1]}, {he[2], B[4][2]}, {he[3], B[4][3]}},
+                        1, s));
+        SGN_TRY(lincomb(st, st->U, {{st->U, 1.0}},
+                        {{hU[0], B[4][0]}, {hU[1], B[4][1]}, {hU[2], B[4][2]}, {hU[3], B[4][3]}},
+                        d, s));
+      }
+      SGN_TRY(solve_at(st, st->eta, st->U, st->u, opts, s));
+      st->t += st->dt_last[0];
+      st->step += 1;
+    }
+    SGN_TRY(push());
+  }
+  return SGN_OK;
+}
+
+// Linearly implicit SBDF2 (Eq:MM):
+//   w_{n+2} = (4 w_{n+1} - w_n + 2 dt (2 f_{n+1} - f_n)) / 3
+//   u_{n+2} = A^{-1} [2 res_{n+1} - res_n],  res_j = A u_j - G_j u_j + U_j
+extern "C" sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nsteps,
+                                      const sgn_opts* opts, sgn_stream stream) {
+  if (!st || !dt || nsteps < 0) return SGN_ERR_INVALID_ARG;
+  sgn_ctx* ctx = st->lay->ctx;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  SGN_TRY(check_opts(st, opts));
+  const bool same_dt = (int)st->dt_last.size() == st->lay->count &&
+                       std::equal(st->dt_last.begin(), st->dt_last.end(), dt);
+  if (st->hist != HIST_SBDF2 || !same_dt) st->levels = 0;
+  SGN_TRY(upload_dt(st, dt, s));
+  st->last = s;
+  const int d = st->d;
+  const long long P = st->P, V = d * P;
+  auto res_of = [&](const double* eta, const double* u, const double* U, void* out) -> sgn_status {
+    cudaError_t e =
+        st->lay->dim == 1
+            ? sgn::launch_linimp_res1d(st->lay->l1, ctx->tw64, st->A_fixed, eta, st->gradh, u, U,
+                                       out, st->lay->ws, s)
+            : sgn::launch_linimp_res2d(st->lay->l2, ctx->tw64, st->A_fixed, eta, st->gradh, u, U,
+                                       out, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "linimp residual");
+    return SGN_OK;
+  };
+  for (int k = 0; k < nsteps; ++k) {
+    if (st->levels == 0) {
+      // start-up: keep level n, take one RK4 step to level n+1
+      SGN_TRY(copy_field(st, st->eta_p, st->eta, P, s));
+      SGN_TRY(copy_field(st, st->U_p, st->U, V, s));
+      SGN_TRY(copy_field(st, st->u_p, st->u, V, s));
+      SGN_TRY(rhs_at(st, st->eta, st->u, st->he[0], st->hU[0], s));
+      SGN_TRY(res_of(st->eta, st->u, st->U, st->res0));
+      SGN_TRY(rk4_once(st, opts, s));
+      st->levels = 2;
+      st->hist = HIST_SBDF2;
+      continue;
+    }
+    // f_{n+1} into he[1], res_{n+1} into res1
+    SGN_TRY(rhs_at(st, st->eta, st->u, st->he[1], st->hU[1], s));
+    SGN_TRY(res_of(st->eta, st->u, st->U, st->res1));
+    SGN_TRY(lincomb(st, st->eta_s, {{st->eta, 4.0 / 3.0}, {st->eta_p, -1.0 / 3.0}},
+                    {{st->he[1], 4.0 / 3.0}, {st->he[0], -2.0 / 3.0}}, 1, s));
+    SGN_TRY(lincomb(st, st->U_s, {{st->U, 4.0 / 3.0}, {st->U_p, -1.0 / 3.0}},
+                    {{st->hU[1], 4.0 / 3.0}, {st->hU[0], -2.0 / 3.0}}, d, s));
+    cudaError_t e =
+        st->lay->dim == 1
+            ? sgn::launch_linimp_solve1d(st->lay->l1, ctx->tw64, st->A_fixed, st->res1, st->res0,
+                                         2.0, -1.0, st->u_s, s)
+            : sgn::launch_linimp_solve2d(st->lay->l2, ctx->tw64, st->A_fixed, st->res1, st->res0,
+                                         2.0, -1.0, st->u_s, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "linimp solve");
+    SGN_TRY(copy_field(st, st->eta_p, st->eta, P, s));
+    SGN_TRY(copy_field(st, st->U_p, st->U, V, s));
+    SGN_TRY(copy_field(st, st->u_p, st->u, V, s));
+    SGN_TRY(copy_field(st, st->eta, st->eta_s, P, s));
+    SGN_TRY(copy_field(st, st->U, st->U_s, V, s));
+    SGN_TRY(copy_field(st, st->u, st->u_s, V, s));
+    std::swap(st->he[0], st->he[1]);
+    std::swap(st->hU[0], st->hU[1]);
+    std::swap(st->res0, st->res1);
+    st->t += st->dt_last[0];
+    st->step += 1;
+  }
+  return SGN_OK;
+}
+
+extern "C" sgn_status sgn_state_get_stats(sgn_state* st, sgn_state_stats* out) {
+  if (!st || !out) return SGN_ERR_INVALID_ARG;
+  sgn_ctx* ctx = st->lay->ctx;
+  DeviceGuard g(ctx->device);
+  DevStats h{};
+  SGN_CUDA(ctx, cudaMemcpyAsync(&h, st->stats, sizeof(DevStats), cudaMemcpyDeviceToHost, st->last));
+  SGN_CUDA(ctx, cudaStreamSynchronize(st->last));
+  out->solves = h.solves;
+  out->iterations = h.iterations;
+  out->max_iters = h.max_iters;
+  out->status = h.status;
+  out->t = st->t;
+  out->step = st->step;
+  return SGN_OK;
+}
+
+extern "C" void sgn_state_free(sgn_state* st) {
+  if (!st) return;
+  DeviceGuard g(st->lay->ctx->device);
+  for (double* p : st->bufs) cudaFree(p);
+  cudaFree(st->res0);
+  cudaFree(st->res1);
+  cudaFree(st->A_fixed);
+  cudaFree(st->stats);
+  delete st;
+}

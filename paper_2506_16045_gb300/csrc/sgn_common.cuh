@@ -1,0 +1,191 @@
+// Device building blocks shared by the SGN kernels: complex arithmetic, the twiddle
+// table, an in-shared-memory Stockham FFT run by one CTA, and deterministic block
+// reductions with FP64 accumulation.
+//
+// Spectral convention (§6.1 of the paper): forward transform X_m = sum_j x_j e^{-2 pi i jm/n},
+// inverse without the 1/n factor (callers scale); wavenumber k_m = 2 pi m / L for
+// m < n/2, k_m = 2 pi (m - n) / L for m > n/2, and k_{n/2} = 0.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sgn_internal.h"
+
+namespace sgn {
+
+template <typename T>
+struct alignas(2 * sizeof(T)) cplx {
+  T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> mk(T a, T b) { cplx<T> r; r.x = a; r.y = b; return r; }
+template <typename T>
+__device__ __forceinline__ cplx<T> operator+(cplx<T> a, cplx<T> b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename T>
+__device__ __forceinline__ cplx<T> operator-(cplx<T> a, cplx<T> b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename T>
+__device__ __forceinline__ cplx<T> operator*(cplx<T> a, T s) { return mk(a.x * s, a.y * s); }
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b) when conj_b, else a * b (used for forward/inverse twiddles from one table)
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul_tw(cplx<T> a, cplx<T> w, bool inverse) {
+  T wy = inverse ? -w.y : w.y;
+  return mk(a.x * w.x - a.y * wy, a.x * wy + a.y * w.x);
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> conj(cplx<T> a) { return mk(a.x, -a.y); }
+// multiply by i (inverse=false -> -i for the forward 4-point kernel's sign)
+template <typename T>
+__device__ __forceinline__ cplx<T> mul_pi(cplx<T> a) { return mk(-a.y, a.x); }   // * (+i)
+template <typename T>
+__device__ __forceinline__ cplx<T> mul_mi(cplx<T> a) { return mk(a.y, -a.x); }   // * (-i)
+
+// Signed integer wavenumber index of mode m for length n, with the n/2 mode mapped to 0.
+__device__ __forceinline__ int wave_index(int m, int n) {
+  int h = n >> 1;
+  return m < h ? m : (m == h ? 0 : m - n);
+}
+
+// -------------------------------------------------------------------------------------
+// In-shared-memory complex FFT (Stockham autosort, one radix-2 stage when log2 n is odd,
+// then radix-4 stages).  Stage with current sub-transform length p: butterfly i takes the
+// R inputs buf[i + r n/R], twiddles them by w^{r k}, w = e^{-+2 pi i/(p R)}, k = i mod p,
+// and writes the R outputs to ((i - k) R + k) + s p.  Each thread keeps its butterflies'
+// outputs in registers between a barrier after all reads and the writes, so the transform
+// is in place.  MAXB bounds butterflies per thread per radix-4 stage: n/4 <= MAXB*NT.
+// All NT threads must call; returns after a barrier.
+// -------------------------------------------------------------------------------------
+template <typename T, int NT, int MAXB>
+__device__ __forceinline__ void cta_fft(cplx<T>* buf, int n, int log2n, bool inverse,
+                                        const cplx<T>* __restrict__ tw) {
+  const int t = threadIdx.x;
+  int p = 1;
+  int lp = 0;                                    // log2 p
+  if (log2n & 1) {
+    const int h = n >> 1;
+    cplx<T> y0[2 * MAXB], y1[2 * MAXB];
+    int dst[2 * MAXB];
+#pragma unroll
+    for (int b = 0; b < 2 * MAXB; ++b) {
+      int i = t + b * NT;
+      if (i < h) {
+        cplx<T> a0 = buf[i];
+        cplx<T> a1 = buf[i + h];
+        // p = 1 here: k = 0, no twiddle
+        y0[b] = a0 + a1;
+        y1[b] = a0 - a1;
+        dst[b] = i * 2;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < 2 * MAXB; ++b) {
+      int i = t + b * NT;
+      if (i < h) {
+        buf[dst[b]] = y0[b];
+        buf[dst[b] + 1] = y1[b];
+      }
+    }
+    __syncthreads();
+    p = 2;
+    lp = 1;
+  }
+  const int q = n >> 2;
+  while (p < n) {
+    cplx<T> y[MAXB][4];
+    int dst[MAXB];
+    const int tshift = kTwiddleLog2 - lp - 2;    // table stride NMAX/(4p) as a shift
+#pragma unroll
+    for (int b = 0; b < MAXB; ++b) {
+      int i = t + b * NT;
+      if (i < q) {
+        int k = i & (p - 1);
+        cplx<T> a0 = buf[i];
+        cplx<T> a1 = buf[i + q];
+        cplx<T> a2 = buf[i + 2 * q];
+        cplx<T> a3 = buf[i + 3 * q];
+        if (p > 1) {
+          int e = k << tshift;
+          a1 = cmul_tw(a1, tw[e], inverse);
+          a2 = cmul_tw(a2, tw[2 * e], inverse);
+          a3 = cmul_tw(a3, tw[3 * e], inverse);
+        }
+        cplx<T> s02 = a0 + a2, d02 = a0 - a2;
+        cplx<T> s13 = a1 + a3, d13 = a1 - a3;
+        // 4-point DFT: y1 = d02 + s d13 with s = -i (forward) or +i (inverse)
+        cplx<T> r13 = inverse ? mul_pi(d13) : mul_mi(d13);
+        y[b][0] = s02 + s13;
+        y[b][1] = d02 + r13;
+        y[b][2] = s02 - s13;
+        y[b][3] = d02 - r13;
+        dst[b] = ((i - k) << 2) + k;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < MAXB; ++b) {
+      int i = t + b * NT;
+      if (i < q) {
+        buf[dst[b]] = y[b][0];
+        buf[dst[b] + p] = y[b][1];
+        buf[dst[b] + 2 * p] = y[b][2];
+        buf[dst[b] + 3 * p] = y[b][3];
+      }
+    }
+    __syncthreads();
+    p <<= 2;
+    lp += 2;
+  }
+}
+
+// -------------------------------------------------------------------------------------
+// Block reduction of a double (deterministic: fixed shuffle tree, then warp 0 over the
+// per-warp partials).  scratch must hold NT/32 doubles.  Result broadcast to all threads.
+// -------------------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();                                 // scratch may still be read by a previous call
+  if (l == 0) scratch[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = (l < NT / 32) ? scratch[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (l == 0) scratch[NT / 32] = r;
+  }
+  __syncthreads();
+  return scratch[NT / 32];
+}
+
+template <int NT>
+__device__ __forceinline__ double block_max(double v, double* scratch) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) scratch[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double r = (l < NT / 32) ? scratch[l] : -1.0e308;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if (l == 0) scratch[NT / 32] = r;
+  }
+  __syncthreads();
+  return scratch[NT / 32];
+}
+
+template <int NT>
+__device__ __forceinline__ double block_min(double v, double* scratch) {
+  return -block_max<NT>(-v, scratch);
+}
+
+}  // namespace sgn

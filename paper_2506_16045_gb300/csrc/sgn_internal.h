@@ -1,0 +1,80 @@
+// Internal (C++) interface between the C ABI layer and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sgn.h"
+
+namespace sgn {
+
+constexpr int kTwiddleLog2 = 14;                 // twiddle table resolution: n <= 16384 per axis
+constexpr int kTwiddleN = 1 << kTwiddleLog2;
+
+// One 1d periodic instance inside a packed batch.  Real fields of instance i occupy
+// [off, off + n) of every packed array; the spectral workspace of the instance starts at
+// ws (in units of complex doubles) and holds kWsVectors half spectra of n/2 + 1 modes.
+struct Inst1d {
+  int n;
+  int log2n;
+  double L;
+  long long off;
+  long long ws;
+};
+
+// Preconditioner coefficients and solve report per instance (device resident).
+struct SolveRec {
+  double sigma, alpha, kappa_ub, eta_min, eta_max;
+  double ratio;          // final sqrt(r.A^{-1}r)/sqrt(b.A^{-1}b) (FP64 residual in the mixed path)
+  int flat;
+  int iters;             // PCG iterations (inner iterations summed over refinements)
+  int refinements;       // FP32 inner solves (mixed) or 0 (FP64)
+  int status;            // sgn_status of this instance
+};
+
+constexpr int kWsVectors = 6;          // half-spectrum vectors per instance in the workspace
+
+struct Layout1d {
+  int count = 0;
+  long long points = 0;                // sum of n
+  long long ws_cplx = 0;               // workspace size in complex doubles
+  Inst1d* d_inst = nullptr;            // device copy
+  Inst1d* h_inst = nullptr;            // host copy
+  int* d_ids = nullptr;                // instance ids grouped by size class
+  int class_begin[16] = {0};           // per log2n: [begin, end) into ids
+  int class_end[16] = {0};
+};
+
+// Launchers (all asynchronous on `stream`; return cudaError_t of the launch).
+cudaError_t twiddles_init(void* tw64, void* tw32, cudaStream_t s);
+
+cudaError_t launch_deriv1d(const Layout1d& lay, const void* tw64, const double* f, double* fx,
+                           cudaStream_t s);
+cudaError_t launch_apply_G1d(const Layout1d& lay, const void* tw64, const double* eta,
+                             const double* hx, const double* u, double* Gu, cudaStream_t s);
+cudaError_t launch_coeffs1d(const Layout1d& lay, const double* eta, const double* hx, int kind,
+                            SolveRec* rec, cudaStream_t s);
+cudaError_t launch_precond1d(const Layout1d& lay, const void* tw64, const SolveRec* rec,
+                             const double* r, double* z, cudaStream_t s);
+// precision: SGN_PREC_FP64 or SGN_PREC_MIXED.  `given` (nullable) holds preconditioner
+// coefficients per instance; otherwise they are computed from eta and hx (kind).
+cudaError_t launch_pcg1d(const Layout1d& lay, const void* tw64, const void* tw32, int precision,
+                         const double* eta, const double* hx, const double* b, double* x,
+                         const SolveRec* given, int kind, double rtol, double rtol_inner,
+                         int maxit, int max_refine, SolveRec* rec, void* ws, cudaStream_t s);
+cudaError_t launch_rhs1d(const Layout1d& lay, const void* tw64, double g, const double* eta,
+                         const double* u, const double* h, const double* hx, double* f_eta,
+                         double* f_U, double* scratch, cudaStream_t s);
+// out = base + sum_j c_j dt_i f_j over up to 4 terms (per-instance dt from `dt`)
+cudaError_t launch_axpy1d(const Layout1d& lay, const double* dt, double* out, const double* base,
+                          int nterms, const double* const* f, const double* c, double scale,
+                          cudaStream_t s);
+// SBDF2 pieces: res_hat = (sigma + alpha k^2) u_hat - (G u)_hat + U_hat, stored as half spectra
+cudaError_t launch_linimp_res1d(const Layout1d& lay, const void* tw64, const SolveRec* A,
+                                const double* eta, const double* hx, const double* u,
+                                const double* U, void* res_hat, void* ws, cudaStream_t s);
+// u = A^{-1} iFFT(c1 res1_hat + c0 res0_hat)
+cudaError_t launch_linimp_solve1d(const Layout1d& lay, const void* tw64, const SolveRec* A,
+                                  const void* res1_hat, const void* res0_hat, double c1,
+                                  double c0, double* u, cudaStream_t s);
+
+}  // namespace sgn

@@ -1,0 +1,310 @@
+"""Thin Python binding of the C ABI in include/sgn.h (argument marshalling only).
+
+Every numerical step runs in libsgn.so.  Arrays are CUDA float64 tensors (device
+pointers are passed through); streams are the current torch CUDA stream unless given.
+If the library is missing or no GPU is present, load() raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libsgn.so")
+
+SGN_OK = 0
+STATUS_NAMES = {
+    0: "SGN_OK", 1: "SGN_ERR_INVALID_ARG", 2: "SGN_ERR_UNSUPPORTED_SIZE", 3: "SGN_ERR_NOMEM",
+    4: "SGN_ERR_CUDA", 5: "SGN_ERR_NOT_CONVERGED", 6: "SGN_ERR_BREAKDOWN",
+    7: "SGN_ERR_NONPOSITIVE_DEPTH", 8: "SGN_ERR_PENDING", 9: "SGN_ERR_TIMEOUT",
+    10: "SGN_ERR_REJECTED",
+}
+PREC_FP64, PREC_MIXED = 0, 1
+COEF_OPT, COEF_REPLACEMENT = 0, 1
+
+
+class SgnGrid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("Lx", C.c_double),
+                ("Ly", C.c_double), ("g", C.c_double)]
+
+
+class SgnPrecond(C.Structure):
+    _fields_ = [("sigma", C.c_double), ("alpha", C.c_double), ("kappa_ub", C.c_double),
+                ("flat", C.c_int)]
+
+
+class SgnPcgInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("rel_resid_Ainv", C.c_double),
+                ("status", C.c_int)]
+
+
+class SgnOpts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("maxit", C.c_int), ("prec", C.c_int), ("coef", C.c_int),
+                ("rtol_inner", C.c_double), ("max_refine", C.c_int)]
+
+
+class SgnStateStats(C.Structure):
+    _fields_ = [("solves", C.c_longlong), ("iterations", C.c_longlong), ("max_iters", C.c_int),
+                ("status", C.c_int), ("t", C.c_double), ("step", C.c_longlong)]
+
+
+# (name, restype, argtypes) of every exported entry point declared in include/sgn.h
+_VP = C.c_void_p
+_DP = C.c_void_p       # device pointers travel as integers
+SIGNATURES = [
+    ("sgn_create", C.c_int, [C.POINTER(_VP), C.c_int, C.c_size_t]),
+    ("sgn_destroy", None, [_VP]),
+    ("sgn_last_error", C.c_char_p, [_VP]),
+    ("sgn_status_string", C.c_char_p, [C.c_int]),
+    ("sgn_layout_create", C.c_int, [_VP, C.c_int, C.POINTER(SgnGrid), C.POINTER(_VP)]),
+    ("sgn_layout_destroy", None, [_VP]),
+    ("sgn_layout_points", C.c_longlong, [_VP]),
+    ("sgn_layout_offsets", C.c_int, [_VP, C.POINTER(C.c_longlong)]),
+    ("sgn_spectral_grad", C.c_int, [_VP, _VP, _DP, _DP, _VP]),
+    ("sgn_precond_coeffs", C.c_int, [_VP, _VP, _DP, _DP, C.c_int, C.POINTER(SgnPrecond), _VP]),
+    ("sgn_apply_operator", C.c_int, [_VP, _VP, _DP, _DP, _DP, _DP, _VP]),
+    ("sgn_precond_solve", C.c_int, [_VP, _VP, C.POINTER(SgnPrecond), _DP, _DP, _VP]),
+    ("sgn_pcg", C.c_int, [_VP, _VP, _DP, _DP, C.POINTER(SgnPrecond), _DP, _DP, C.c_double,
+                          C.c_int, C.c_int, C.POINTER(SgnPcgInfo), _VP]),
+    ("sgn_rhs", C.c_int, [_VP, _VP, _DP, _DP, _DP, _DP, _DP, _DP, _VP]),
+    ("sgn_state_create", C.c_int, [_VP, _VP, _DP, _DP, _DP, _DP, _DP, C.POINTER(_VP)]),
+    ("sgn_state_init", C.c_int, [_VP, _VP]),
+    ("sgn_step_rk4", C.c_int, [_VP, C.POINTER(C.c_double), C.c_int, C.POINTER(SgnOpts), _VP]),
+    ("sgn_step_abk", C.c_int, [_VP, C.c_int, C.POINTER(C.c_double), C.c_int, C.POINTER(SgnOpts),
+                               _VP]),
+    ("sgn_step_linimp", C.c_int, [_VP, C.POINTER(C.c_double), C.c_int, C.POINTER(SgnOpts), _VP]),
+    ("sgn_state_get_stats", C.c_int, [_VP, C.POINTER(SgnStateStats)]),
+    ("sgn_state_free", None, [_VP]),
+]
+
+_lib = None
+
+
+def load(path: str = LIBPATH):
+    """Load libsgn.so and declare its signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsgn.so not found at {path}: build it with "
+                           "`python -m paper_2506_16045_gb300.build` (no CPU fallback exists)")
+    lib = C.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class SgnError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+
+
+def _ptr(t):
+    import torch
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA float64 tensor")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+@dataclass
+class Grid:
+    dim: int
+    nx: int
+    Lx: float
+    g: float = 9.81
+    ny: int = 1
+    Ly: float = 1.0
+
+    def c(self):
+        return SgnGrid(self.dim, self.nx, self.ny, self.Lx, self.Ly, self.g)
+
+    @property
+    def points(self):
+        return self.nx * self.ny
+
+
+class Context:
+    """Owns an sgn_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = C.c_void_p()
+        s = self.lib.sgn_create(C.byref(h), device, 0)
+        if s != SGN_OK:
+            raise SgnError(s, "sgn_create")
+        self.h = h
+        self.device = device
+
+    def check(self, s, what=""):
+        if s != SGN_OK:
+            msg = self.lib.sgn_last_error(self.h)
+            raise SgnError(s, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if self.h:
+            self.lib.sgn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Layout:
+    """A packed batch of instances (sgn_layout)."""
+
+    def __init__(self, ctx: Context, grids: Sequence[Grid]):
+        self.ctx = ctx
+        self.grids = list(grids)
+        arr = (SgnGrid * len(self.grids))(*[g.c() for g in self.grids])
+        h = C.c_void_p()
+        ctx.check(ctx.lib.sgn_layout_create(ctx.h, len(self.grids), arr, C.byref(h)),
+                  "sgn_layout_create")
+        self.h = h
+        self.count = len(self.grids)
+        self.points = ctx.lib.sgn_layout_points(h)
+        offs = (C.c_longlong * (self.count + 1))()
+        ctx.check(ctx.lib.sgn_layout_offsets(h, offs), "sgn_layout_offsets")
+        self.offsets = list(offs)
+        self.dim = self.grids[0].dim
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.sgn_layout_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spectral_grad(lay: Layout, f, gradf, stream=None):
+    lay.ctx.check(lay.ctx.lib.sgn_spectral_grad(lay.ctx.h, lay.h, _ptr(f), _ptr(gradf),
+                                                _stream(stream)), "sgn_spectral_grad")
+
+
+def precond_coeffs(lay: Layout, eta, gradh, kind=COEF_OPT, stream=None):
+    out = (SgnPrecond * lay.count)()
+    lay.ctx.check(lay.ctx.lib.sgn_precond_coeffs(lay.ctx.h, lay.h, _ptr(eta), _ptr(gradh), kind,
+                                                 out, _stream(stream)), "sgn_precond_coeffs")
+    return [dict(sigma=p.sigma, alpha=p.alpha, kappa_ub=p.kappa_ub, flat=bool(p.flat)) for p in out]
+
+
+def apply_operator(lay: Layout, eta, gradh, u, Gu, stream=None):
+    lay.ctx.check(lay.ctx.lib.sgn_apply_operator(lay.ctx.h, lay.h, _ptr(eta), _ptr(gradh), _ptr(u),
+                                                 _ptr(Gu), _stream(stream)), "sgn_apply_operator")
+
+
+def _precond_array(lay, P):
+    arr = (SgnPrecond * lay.count)()
+    for i, p in enumerate(P):
+        arr[i] = SgnPrecond(p["sigma"], p["alpha"], p.get("kappa_ub", 0.0), int(p.get("flat", 0)))
+    return arr
+
+
+def precond_solve(lay: Layout, P, r, z, stream=None):
+    lay.ctx.check(lay.ctx.lib.sgn_precond_solve(lay.ctx.h, lay.h, _precond_array(lay, P), _ptr(r),
+                                                _ptr(z), _stream(stream)), "sgn_precond_solve")
+
+
+def pcg(lay: Layout, eta, gradh, b, x, rtol=1e-12, maxit=1000, prec=PREC_FP64, P=None,
+        info=True, stream=None, check=True):
+    """Solve G x = b (x holds the initial guess).  Returns per-instance info dicts (or None)."""
+    inf = (SgnPcgInfo * lay.count)() if info else None
+    parr = _precond_array(lay, P) if P is not None else None
+    s = lay.ctx.lib.sgn_pcg(lay.ctx.h, lay.h, _ptr(eta), _ptr(gradh), parr, _ptr(b), _ptr(x), rtol,
+                            maxit, prec, inf, _stream(stream))
+    if check:
+        lay.ctx.check(s, "sgn_pcg")
+    if not info:
+        return None
+    return [dict(iters=i.iters, refinements=i.refinements, ratio=i.rel_resid_Ainv,
+                 status=i.status) for i in inf]
+
+
+def rhs(lay: Layout, eta, u, h, gradh, f_eta, f_U, stream=None):
+    lay.ctx.check(lay.ctx.lib.sgn_rhs(lay.ctx.h, lay.h, _ptr(eta), _ptr(u), _ptr(h), _ptr(gradh),
+                                      _ptr(f_eta), _ptr(f_U), _stream(stream)), "sgn_rhs")
+
+
+class State:
+    """sgn_state bound to caller-owned tensors eta, U, u, h, gradh (packed)."""
+
+    def __init__(self, lay: Layout, eta, U, u, h, gradh):
+        self.lay = lay
+        self.tensors = (eta, U, u, h, gradh)
+        hh = C.c_void_p()
+        lay.ctx.check(lay.ctx.lib.sgn_state_create(lay.ctx.h, lay.h, _ptr(eta), _ptr(U), _ptr(u),
+                                                   _ptr(h), _ptr(gradh), C.byref(hh)),
+                      "sgn_state_create")
+        self.h = hh
+
+    def init(self, stream=None):
+        self.lay.ctx.check(self.lay.ctx.lib.sgn_state_init(self.h, _stream(stream)),
+                           "sgn_state_init")
+
+    @staticmethod
+    def _opts(rtol, maxit, prec, coef, rtol_inner, max_refine):
+        return SgnOpts(rtol, maxit, prec, coef, rtol_inner, max_refine)
+
+    def _dt(self, dt):
+        n = self.lay.count
+        vals = [float(dt)] * n if not hasattr(dt, "__len__") else [float(v) for v in dt]
+        return (C.c_double * n)(*vals)
+
+    def rk4(self, dt, nsteps, rtol=1e-12, maxit=2000, prec=PREC_FP64, coef=COEF_OPT,
+            rtol_inner=0.0, max_refine=0, stream=None):
+        o = self._opts(rtol, maxit, prec, coef, rtol_inner, max_refine)
+        self.lay.ctx.check(self.lay.ctx.lib.sgn_step_rk4(self.h, self._dt(dt), nsteps, C.byref(o),
+                                                         _stream(stream)), "sgn_step_rk4")
+
+    def abk(self, order, dt, nsteps, rtol=1e-12, maxit=2000, prec=PREC_FP64, coef=COEF_OPT,
+            rtol_inner=0.0, max_refine=0, stream=None):
+        o = self._opts(rtol, maxit, prec, coef, rtol_inner, max_refine)
+        self.lay.ctx.check(self.lay.ctx.lib.sgn_step_abk(self.h, order, self._dt(dt), nsteps,
+                                                         C.byref(o), _stream(stream)),
+                           "sgn_step_abk")
+
+    def linimp(self, dt, nsteps, rtol=1e-12, maxit=2000, prec=PREC_FP64, coef=COEF_OPT,
+               rtol_inner=0.0, max_refine=0, stream=None):
+        o = self._opts(rtol, maxit, prec, coef, rtol_inner, max_refine)
+        self.lay.ctx.check(self.lay.ctx.lib.sgn_step_linimp(self.h, self._dt(dt), nsteps,
+                                                            C.byref(o), _stream(stream)),
+                           "sgn_step_linimp")
+
+    def stats(self):
+        st = SgnStateStats()
+        self.lay.ctx.check(self.lay.ctx.lib.sgn_state_get_stats(self.h, C.byref(st)),
+                           "sgn_state_get_stats")
+        return dict(solves=st.solves, iterations=st.iterations, max_iters=st.max_iters,
+                    status=st.status, t=st.t, step=st.step)
+
+    def close(self):
+        if self.h:
+            self.lay.ctx.lib.sgn_state_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
