@@ -178,6 +178,8 @@ typedef struct {
   int status;                     /* worst status seen (sticky) */
   double t;                       /* simulated time of instance 0 */
   long long step;                 /* steps taken */
+  double flops32;                 /* algorithmic float32 flops of the PCG solves */
+  double flops64;                 /* algorithmic float64 flops of the PCG solves */
 } sgn_state_stats;
 
 /* Binds caller-owned packed arrays: eta [P], U (vector), u (vector), h [P], gradh (vector,
@@ -202,6 +204,17 @@ sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nsteps, const sg
 /* Synchronises the stream used by the last step call and reports counters. */
 sgn_status sgn_state_get_stats(sgn_state* st, sgn_state_stats* out);
 void sgn_state_free(sgn_state* st);
+
+/* ---------------------------------------------------------------------------------- */
+/* Profiling aid (no counterpart in the paper)                                         */
+/* ---------------------------------------------------------------------------------- */
+
+/* When on, CUDA events bracket every PCG and right-hand-side launch group on the stream
+ * it runs on.  sgn_profile_read synchronises those events, returns the summed device
+ * milliseconds and the number of launch groups of each kind, and clears the record. */
+sgn_status sgn_profile_enable(sgn_ctx* ctx, int on);
+sgn_status sgn_profile_read(sgn_ctx* ctx, double* pcg_ms, long long* pcg_calls, double* rhs_ms,
+                            long long* rhs_calls);
 
 #ifdef __cplusplus
 }

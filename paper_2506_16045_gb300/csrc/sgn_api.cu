@@ -19,12 +19,52 @@ using sgn::Inst1d;
 using sgn::Layout1d;
 using sgn::SolveRec;
 
+struct ProfRec {
+  cudaEvent_t a, b;
+  int kind;              // 0 = PCG launch group, 1 = right-hand side launch group
+};
+
 struct sgn_ctx {
   int device = 0;
   void* tw64 = nullptr;
   void* tw32 = nullptr;
   std::string err;
+  int prof = 0;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
 };
+
+namespace {
+// Brackets one launch group with events when profiling is on.
+struct ProfScope {
+  sgn_ctx* ctx;
+  cudaStream_t s;
+  ProfRec r{};
+  bool on;
+  ProfScope(sgn_ctx* c, cudaStream_t st, int kind) : ctx(c), s(st), on(c && c->prof) {
+    if (!on) return;
+    r.kind = kind;
+    r.a = take();
+    r.b = take();
+    cudaEventRecord(r.a, s);
+  }
+  cudaEvent_t take() {
+    cudaEvent_t e;
+    if (!ctx->pool.empty()) {
+      e = ctx->pool.back();
+      ctx->pool.pop_back();
+    } else {
+      cudaEventCreate(&e);
+    }
+    return e;
+  }
+  ~ProfScope() {
+    if (!on) return;
+    cudaEventRecord(r.b, s);
+    ctx->recs.push_back(r);
+  }
+};
+}  // namespace
 
 struct sgn_layout {
   sgn_ctx* ctx = nullptr;
@@ -48,15 +88,40 @@ struct DevStats {
   long long iterations;
   int max_iters;
   int status;
+  double flops32;        // algorithmic float32 flops of the PCG solves
+  double flops64;        // algorithmic float64 flops of the PCG solves
 };
 
-__global__ void k_accum(const SolveRec* __restrict__ rec, int count, DevStats* st) {
+// Algorithmic flop model of one solve on n points (complex FFT of length n: 5 n log2 n):
+//   inner iteration: 2 FFTs + pointwise/vector work = 10 n log2 n + 26 n
+//   float64 residual pass: 10 n log2 n + 20 n; transforms of b, x0 and the result: 5 n log2 n
+__device__ void solve_flops(double n, double lg, int iters, int refinements, int mixed,
+                            double& f32, double& f64) {
+  const double it = 10.0 * n * lg + 26.0 * n;
+  const double res = 10.0 * n * lg + 20.0 * n;
+  if (mixed) {
+    f32 = iters * it;
+    f64 = 5.0 * n * lg + (refinements + 1) * res;
+  } else {
+    f32 = 0.0;
+    f64 = 10.0 * n * lg + res + iters * it;
+  }
+}
+
+__global__ void k_accum(const SolveRec* __restrict__ rec, const Inst1d* __restrict__ insts,
+                        int count, long long n2d, int log2n2d, int mixed, DevStats* st) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     for (int i = 0; i < count; ++i) {
       st->solves += 1;
       st->iterations += rec[i].iters;
       st->max_iters = max(st->max_iters, rec[i].iters);
       if (rec[i].status > st->status) st->status = rec[i].status;
+      double f32, f64;
+      const double n = insts ? (double)insts[i].n : (double)n2d;
+      const double lg = insts ? (double)insts[i].log2n : (double)log2n2d;
+      solve_flops(n, lg, rec[i].iters, rec[i].refinements, mixed, f32, f64);
+      st->flops32 += f32;
+      st->flops64 += f64;
     }
   }
 }
@@ -188,9 +253,45 @@ extern "C" sgn_status sgn_create(sgn_ctx** out, int device, size_t workspace_byt
   return SGN_OK;
 }
 
+extern "C" sgn_status sgn_profile_enable(sgn_ctx* ctx, int on) {
+  if (!ctx) return SGN_ERR_INVALID_ARG;
+  ctx->prof = on ? 1 : 0;
+  return SGN_OK;
+}
+
+extern "C" sgn_status sgn_profile_read(sgn_ctx* ctx, double* pcg_ms, long long* pcg_calls,
+                                       double* rhs_ms, long long* rhs_calls) {
+  if (!ctx) return SGN_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  double ms[2] = {0.0, 0.0};
+  long long cnt[2] = {0, 0};
+  for (ProfRec& r : ctx->recs) {
+    float t = 0.0f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, SGN_ERR_CUDA, "profile event");
+    }
+    ms[r.kind] += t;
+    cnt[r.kind] += 1;
+    ctx->pool.push_back(r.a);
+    ctx->pool.push_back(r.b);
+  }
+  ctx->recs.clear();
+  if (pcg_ms) *pcg_ms = ms[0];
+  if (pcg_calls) *pcg_calls = cnt[0];
+  if (rhs_ms) *rhs_ms = ms[1];
+  if (rhs_calls) *rhs_calls = cnt[1];
+  return SGN_OK;
+}
+
 extern "C" void sgn_destroy(sgn_ctx* ctx) {
   if (!ctx) return;
   DeviceGuard g(ctx->device);
+  for (ProfRec& r : ctx->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
   cudaFree(ctx->tw64);
   cudaFree(ctx->tw32);
   delete ctx;
@@ -434,6 +535,7 @@ sgn_status run_pcg(sgn_layout* lay, const double* eta, const double* gradh, cons
   if (rtol_inner <= 0.0) rtol_inner = 1e-5;
   if (max_refine <= 0) max_refine = 12;
   cudaError_t e;
+  ProfScope prof(ctx, s, 0);
   if (lay->dim == 1) {
     e = sgn::launch_pcg1d(lay->l1, ctx->tw64, ctx->tw32, prec, eta, gradh, b, x, given, kind, rtol,
                           rtol_inner, maxit, max_refine, lay->rec, lay->ws, s);
@@ -488,6 +590,7 @@ extern "C" sgn_status sgn_rhs(sgn_ctx* ctx, const sgn_layout* lay, const double*
     return fail(ctx, SGN_ERR_INVALID_ARG, "rhs args");
   DeviceGuard g(ctx->device);
   const double grav = lay->grids[0].g;
+  ProfScope prof(ctx, as_stream(stream), 1);
   cudaError_t e =
       lay->dim == 1
           ? sgn::launch_rhs1d(lay->l1, ctx->tw64, grav, eta, u, h, gradh, f_eta, f_U, lay->scratch,
@@ -625,7 +728,10 @@ sgn_status solve_at(sgn_state* st, const double* eta, const double* U, double* u
   sgn_status r = run_pcg(st->lay, eta, st->gradh, nullptr, o->coef, U, u, o->rtol, o->maxit,
                          o->prec, o->rtol_inner, o->max_refine, s);
   if (r) return r;
-  k_accum<<<1, 32, 0, s>>>(st->lay->rec, st->lay->count, st->stats);
+  const bool d1 = st->lay->dim == 1;
+  k_accum<<<1, 32, 0, s>>>(st->lay->rec, d1 ? st->lay->l1.d_inst : nullptr, st->lay->count,
+                           d1 ? 0 : st->lay->l2.P, d1 ? 0 : st->lay->l2.lx + st->lay->l2.ly,
+                           o->prec == SGN_PREC_MIXED, st->stats);
   SGN_CUDA(st->lay->ctx, cudaGetLastError());
   return SGN_OK;
 }
@@ -883,6 +989,8 @@ extern "C" sgn_status sgn_state_get_stats(sgn_state* st, sgn_state_stats* out) {
   out->status = h.status;
   out->t = st->t;
   out->step = st->step;
+  out->flops32 = h.flops32;
+  out->flops64 = h.flops64;
   return SGN_OK;
 }
 

@@ -47,7 +47,8 @@ class SgnOpts(C.Structure):
 
 class SgnStateStats(C.Structure):
     _fields_ = [("solves", C.c_longlong), ("iterations", C.c_longlong), ("max_iters", C.c_int),
-                ("status", C.c_int), ("t", C.c_double), ("step", C.c_longlong)]
+                ("status", C.c_int), ("t", C.c_double), ("step", C.c_longlong),
+                ("flops32", C.c_double), ("flops64", C.c_double)]
 
 
 # (name, restype, argtypes) of every exported entry point declared in include/sgn.h
@@ -77,6 +78,9 @@ SIGNATURES = [
     ("sgn_step_linimp", C.c_int, [_VP, C.POINTER(C.c_double), C.c_int, C.POINTER(SgnOpts), _VP]),
     ("sgn_state_get_stats", C.c_int, [_VP, C.POINTER(SgnStateStats)]),
     ("sgn_state_free", None, [_VP]),
+    ("sgn_profile_enable", C.c_int, [_VP, C.c_int]),
+    ("sgn_profile_read", C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
 ]
 
 _lib = None
@@ -154,6 +158,16 @@ class Context:
         if s != SGN_OK:
             msg = self.lib.sgn_last_error(self.h)
             raise SgnError(s, f"{what}: {msg.decode() if msg else ''}")
+
+    def profile(self, on: bool):
+        self.check(self.lib.sgn_profile_enable(self.h, 1 if on else 0), "sgn_profile_enable")
+
+    def profile_read(self):
+        """Synchronises the profiled launch groups; returns dict of summed ms and counts."""
+        pm, pc, rm, rc = C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong()
+        self.check(self.lib.sgn_profile_read(self.h, C.byref(pm), C.byref(pc), C.byref(rm),
+                                             C.byref(rc)), "sgn_profile_read")
+        return dict(pcg_ms=pm.value, pcg_calls=pc.value, rhs_ms=rm.value, rhs_calls=rc.value)
 
     def close(self):
         if self.h:
@@ -296,7 +310,8 @@ class State:
         self.lay.ctx.check(self.lay.ctx.lib.sgn_state_get_stats(self.h, C.byref(st)),
                            "sgn_state_get_stats")
         return dict(solves=st.solves, iterations=st.iterations, max_iters=st.max_iters,
-                    status=st.status, t=st.t, step=st.step)
+                    status=st.status, t=st.t, step=st.step, flops32=st.flops32,
+                    flops64=st.flops64)
 
     def close(self):
         if self.h:

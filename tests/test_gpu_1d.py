@@ -223,8 +223,16 @@ def test_rhs_shelf_and_flat(S):
     sgn.rhs(lay, dev(pack(etas)), dev(pack(us)), dev(pack(hs)), dev(pack(hxs)), fe, fU)
     for i, (n, L, _) in enumerate(cases):
         re, rU = O.rhs_1d(etas[i], us[i], hs[i], hxs[i], L, 9.81)
-        assert rel(unpack(host(fe), lay.offsets)[i], re) < 1e-12
-        assert rel(unpack(host(fU), lay.offsets)[i], rU) < 1e-11
+        # F holds third derivatives: float64 rounding is amplified ~k_max^3.  The bound is
+        # the oracle's own change under a last-bit relative perturbation of its inputs.
+        rng = np.random.default_rng(i)
+        jig = lambda a: a * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], a.size))
+        pe, pU = O.rhs_1d(jig(etas[i]), jig(us[i]), hs[i], jig(hxs[i]), L, 9.81)
+        tol_e = max(1e-13, 20 * rel(pe, re))
+        tol_U = max(1e-13, 20 * rel(pU, rU))
+        assert rel(unpack(host(fe), lay.offsets)[i], re) < tol_e, (n, tol_e)
+        assert rel(unpack(host(fU), lay.offsets)[i], rU) < tol_U, (n, tol_U)
+        assert tol_U < 1e-9
 
 
 def _run_gpu(sgn, ctx, insts, scheme, nsteps, prec, rtol, order=4):
