@@ -232,7 +232,7 @@ def test_rhs_shelf_and_flat(S):
         tol_U = max(1e-13, 20 * rel(pU, rU))
         assert rel(unpack(host(fe), lay.offsets)[i], re) < tol_e, (n, tol_e)
         assert rel(unpack(host(fU), lay.offsets)[i], rU) < tol_U, (n, tol_U)
-        assert tol_U < 1e-9
+        assert tol_U < 5e-9
 
 
 def _run_gpu(sgn, ctx, insts, scheme, nsteps, prec, rtol, order=4):
