@@ -206,6 +206,38 @@ sgn_status sgn_state_get_stats(sgn_state* st, sgn_state_stats* out);
 void sgn_state_free(sgn_state* st);
 
 /* ---------------------------------------------------------------------------------- */
+/* Allocation-free solve (no counterpart in the paper)                                 */
+/* ---------------------------------------------------------------------------------- */
+
+#define SGN_NOALLOC_MAX_N 8192
+
+/* The solve of sgn_pcg for ONE 1d instance (nx = n, period L), for callers that cannot
+ * allocate device memory once their run has started: a fixed, pre-reserved memory pool,
+ * an embedded or certified host whose heap is frozen after start-up, or a callback inside
+ * someone else's time loop where calling the CUDA allocator is not allowed.  It needs no
+ * sgn_ctx or sgn_layout and calls no cudaMalloc, cudaFree or other allocating routine: its
+ * scratch (six half spectra of n/2 + 1 complex doubles), twiddle tables and solve record
+ * live in file-scope static device arrays that every GPU loading the library holds until
+ * the process exits (about 0.8 MB per device).
+ *
+ * Arguments are as for sgn_pcg (device pointers eta, gradh, b and x of n doubles; x holds
+ * the initial guess and receives the solution) with the optimal coefficients computed on
+ * the device.  n must be a power of two with 8 <= n <= SGN_NOALLOC_MAX_N; a larger or
+ * other n returns SGN_ERR_UNSUPPORTED_SIZE without doing anything.  info (host, nullable):
+ * when non-NULL the call synchronises the stream and returns the instance status.
+ *
+ * Works on the current device.  The first call on a device does a one-time set-up (symbol
+ * address lookups and the twiddle-table kernel) and synchronises the stream; make that
+ * first call before any stream capture.  Every call shares the same static scratch, which
+ * keeps the last call's contents (the solve writes each scratch slot before reading it,
+ * and clears the solve record itself): calls that overlap on the GPU (different streams,
+ * or different host threads on one device) race with each other and must be serialised
+ * by the caller. */
+sgn_status sgn_pcg1d_noalloc(int n, double L, const double* eta, const double* gradh,
+                             const double* b, double* x, double rtol, int maxit,
+                             sgn_precision prec, sgn_pcg_info* info, sgn_stream stream);
+
+/* ---------------------------------------------------------------------------------- */
 /* Profiling aid (no counterpart in the paper)                                         */
 /* ---------------------------------------------------------------------------------- */
 

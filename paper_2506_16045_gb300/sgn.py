@@ -78,6 +78,8 @@ SIGNATURES = [
     ("sgn_step_linimp", C.c_int, [_VP, C.POINTER(C.c_double), C.c_int, C.POINTER(SgnOpts), _VP]),
     ("sgn_state_get_stats", C.c_int, [_VP, C.POINTER(SgnStateStats)]),
     ("sgn_state_free", None, [_VP]),
+    ("sgn_pcg1d_noalloc", C.c_int, [C.c_int, C.c_double, _DP, _DP, _DP, _DP, C.c_double, C.c_int,
+                                    C.c_int, C.POINTER(SgnPcgInfo), _VP]),
     ("sgn_profile_enable", C.c_int, [_VP, C.c_int]),
     ("sgn_profile_read", C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                                    C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
@@ -253,6 +255,17 @@ def pcg(lay: Layout, eta, gradh, b, x, rtol=1e-12, maxit=1000, prec=PREC_FP64, P
         return None
     return [dict(iters=i.iters, refinements=i.refinements, ratio=i.rel_resid_Ainv,
                  status=i.status) for i in inf]
+
+
+def pcg1d_noalloc(n, L, eta, gradh, b, x, rtol=1e-12, maxit=1000, prec=PREC_FP64, stream=None):
+    """sgn_pcg1d_noalloc: the single-instance 1d solve without any device allocation (for
+    callers that cannot allocate once running).  Returns (status, info dict)."""
+    lib = load()
+    inf = SgnPcgInfo()
+    s = lib.sgn_pcg1d_noalloc(n, L, _ptr(eta), _ptr(gradh), _ptr(b), _ptr(x), rtol, maxit, prec,
+                              C.byref(inf), _stream(stream))
+    return s, dict(iters=inf.iters, refinements=inf.refinements, ratio=inf.rel_resid_Ainv,
+                   status=inf.status)
 
 
 def rhs(lay: Layout, eta, u, h, gradh, f_eta, f_U, stream=None):
