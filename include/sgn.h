@@ -94,7 +94,7 @@ typedef struct {
 /* ---------------------------------------------------------------------------------- */
 
 /* Creates a context on `device` (made current for the call).  Allocates the twiddle
- * tables (~384 KB).  workspace_bytes is a hint (0 = grow on demand). */
+ * tables (~640 KB).  workspace_bytes is a hint (0 = grow on demand). */
 sgn_status sgn_create(sgn_ctx** ctx, int device, size_t workspace_bytes);
 void sgn_destroy(sgn_ctx* ctx);
 const char* sgn_last_error(const sgn_ctx* ctx);
@@ -218,7 +218,7 @@ void sgn_state_free(sgn_state* st);
  * sgn_ctx or sgn_layout and calls no cudaMalloc, cudaFree or other allocating routine: its
  * scratch (six half spectra of n/2 + 1 complex doubles), twiddle tables and solve record
  * live in file-scope static device arrays that every GPU loading the library holds until
- * the process exits (about 0.8 MB per device).
+ * the process exits (about 1 MB per device).
  *
  * Arguments are as for sgn_pcg (device pointers eta, gradh, b and x of n doubles; x holds
  * the initial guess and receives the solution) with the optimal coefficients computed on

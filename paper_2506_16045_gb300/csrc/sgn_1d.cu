@@ -27,13 +27,14 @@ using namespace d1;
 // Kernels
 // ---------------------------------------------------------------------------------------
 
-__global__ void k_twiddles(cplx<double>* tw64, cplx<float>* tw32) {
+__global__ void k_twiddles(cplx<double>* tw64, cplx<float>* tw32, cplx<df>* twdf) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < kTwiddleN) {
     double s, c;
     sincospi(-2.0 * (double)j / (double)kTwiddleN, &s, &c);
     tw64[j] = mk(c, s);
     tw32[j] = mk((float)c, (float)s);
+    twdf[j] = mk(df(c), df(s));
   }
 }
 
@@ -80,14 +81,15 @@ __global__ void __launch_bounds__(NT) k_apply_G1d(const Inst1d* __restrict__ ins
   __syncthreads();
   cta_fft<double, NT, MAXB>(buf, n, I.log2n, false, tw);
   CoefGlobal64 coef{eta + I.off, hx + I.off};
-  spectral_matvec<double, NT, MAXB>(buf, n, I.log2n, kunit, [&](int m) { return buf[m]; }, coef,
+  const Spec<double> sp = make_spec<double>(n, I.L, 0.0, 0.0);
+  spectral_matvec<double, NT, MAXB>(buf, sp, I.log2n, [&](int m) { return buf[m]; }, coef,
                                     nullptr, tw);
   // (G u)_m for m in [0, n/2]; the field is real, so (G u)_{n-m} = conj((G u)_m).
   cplx<double> g[2 * MAXB + 1];
 #pragma unroll
   for (int b = 0; b < 2 * MAXB + 1; ++b) {
     int m = threadIdx.x + b * NT;
-    if (m <= h) g[b] = gv_mode(buf, m, n, mode_k(m, n, kunit));
+    if (m <= h) g[b] = gv_mode(buf, m, n, sp.k(m));
   }
   __syncthreads();
 #pragma unroll
@@ -145,10 +147,16 @@ __global__ void __launch_bounds__(NT) k_precond1d(const Inst1d* __restrict__ ins
   for (int j = threadIdx.x; j < n; j += NT) z[I.off + j] = buf[j].x;
 }
 
-template <int NT, int MAXB>
+// a7: right-hand side of Eq:DAE_DSWE with F from Def:bigF, in number type T (float64 for
+// the float64 path, double-float for the mixed path): four derivative pairs
+// (u, eta u) -> (d, m); (zeta, s) -> (zeta_x, s_x); d -> d_x; Phi' -> Phi'_x with
+// Phi' = eta^3 Q/3 + eta^2 m d + eta^2 S/2 + eta m s - eta u^2 (the flux -(eta u^2)_x folded
+// in), Q = u d_x - d^2, S = u s_x (reading R6), and
+// f_eta = -m, f_U = -g eta zeta_x + Phi'_x - h_x Psi, Psi = eta^2 Q/2 + eta m d + eta S + m s.
+template <typename T, int NT, int MAXB>
 __global__ void __launch_bounds__(NT) k_rhs1d(const Inst1d* __restrict__ insts,
                                               const int* __restrict__ ids,
-                                              const cplx<double>* __restrict__ tw, double g,
+                                              const cplx<T>* __restrict__ tw, double g,
                                               const double* __restrict__ eta_all,
                                               const double* __restrict__ u_all,
                                               const double* __restrict__ h_all,
@@ -157,51 +165,58 @@ __global__ void __launch_bounds__(NT) k_rhs1d(const Inst1d* __restrict__ insts,
                                               double* __restrict__ fU_all,
                                               double* __restrict__ scratch, long long P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  cplx<double>* buf = reinterpret_cast<cplx<double>*>(smem);
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem);
   const Inst1d I = insts[ids[blockIdx.x]];
   const int n = I.n, log2n = I.log2n;
-  const double kunit = 2.0 * kPi / I.L;
+  const T kn = num<T>(2.0 * kPi / I.L / (double)n);
+  const T third = num<T>(1.0 / 3.0);
+  const T gT = num<T>(g);
   const double* eta = eta_all + I.off;
   const double* u = u_all + I.off;
   const double* hh = h_all + I.off;
   const double* hx = hx_all + I.off;
-  double* sd = scratch + I.off;            // d = u_x
-  double* sm = scratch + P + I.off;        // m = (eta u)_x
-  double* szx = scratch + 2 * P + I.off;   // zeta_x
-  double* ssx = scratch + 3 * P + I.off;   // s_x, s = h_x u
-  double* spsi = scratch + 4 * P + I.off;  // Psi
-  // d, m
-  deriv_pair<NT, MAXB>(buf, n, log2n, kunit, [&](int j) { return mk(u[j], eta[j] * u[j]); }, tw);
+  // scratch planes hold T values (8 bytes each for double and double-float)
+  T* sd = reinterpret_cast<T*>(scratch + I.off);           // d = u_x
+  T* sm = reinterpret_cast<T*>(scratch + P + I.off);       // m = (eta u)_x
+  T* szx = reinterpret_cast<T*>(scratch + 2 * P + I.off);  // zeta_x
+  T* ssx = reinterpret_cast<T*>(scratch + 3 * P + I.off);  // s_x, s = h_x u
+  T* spsi = reinterpret_cast<T*>(scratch + 4 * P + I.off); // Psi
+  deriv_pair<T, NT, MAXB>(buf, n, log2n, kn, [&](int j) {
+    T uj = num<T>(u[j]);
+    return mk(uj, num<T>(eta[j]) * uj);
+  }, tw);
   for (int j = threadIdx.x; j < n; j += NT) {
     sd[j] = buf[j].x;
     sm[j] = buf[j].y;
   }
   __syncthreads();
-  // zeta_x, s_x
-  deriv_pair<NT, MAXB>(buf, n, log2n, kunit,
-                       [&](int j) { return mk(eta[j] - hh[j], hx[j] * u[j]); }, tw);
+  deriv_pair<T, NT, MAXB>(buf, n, log2n, kn, [&](int j) {
+    return mk(num<T>(eta[j] - hh[j]), num<T>(hx[j]) * num<T>(u[j]));
+  }, tw);
   for (int j = threadIdx.x; j < n; j += NT) {
     szx[j] = buf[j].x;
     ssx[j] = buf[j].y;
   }
   __syncthreads();
-  // d_x
-  deriv_pair<NT, MAXB>(buf, n, log2n, kunit, [&](int j) { return mk(sd[j], 0.0); }, tw);
-  // Q = u d_x - d^2, S = u s_x; Phi' = Phi - eta u^2; Psi
+  deriv_pair<T, NT, MAXB>(buf, n, log2n, kn, [&](int j) { return mk(sd[j], from_int<T>(0)); },
+                          tw);
   for (int j = threadIdx.x; j < n; j += NT) {
-    double e = eta[j], uj = u[j], d = sd[j], m = sm[j], s = hx[j] * uj;
-    double Q = uj * buf[j].x - d * d;
-    double Sv = uj * ssx[j];
-    double e2 = e * e;
-    double Phi = e2 * e * Q * (1.0 / 3.0) + e2 * m * d + 0.5 * e2 * Sv + e * m * s - e * uj * uj;
-    spsi[j] = 0.5 * e2 * Q + e * m * d + e * Sv + m * s;
-    buf[j] = mk(Phi, 0.0);
+    T e = num<T>(eta[j]), uj = num<T>(u[j]), d = sd[j], m = sm[j];
+    T s = num<T>(hx[j]) * uj;
+    T Q = uj * buf[j].x - d * d;
+    T Sv = uj * ssx[j];
+    T e2 = e * e;
+    T md = m * d;
+    T Phi = e2 * e * Q * third + e2 * md + half(e2 * Sv) + e * m * s - e * uj * uj;
+    spsi[j] = half(e2 * Q) + e * md + e * Sv + m * s;
+    buf[j] = mk(Phi, from_int<T>(0));
   }
   __syncthreads();
-  deriv_pair<NT, MAXB>(buf, n, log2n, kunit, [&](int j) { return buf[j]; }, tw);
+  deriv_pair<T, NT, MAXB>(buf, n, log2n, kn, [&](int j) { return buf[j]; }, tw);
   for (int j = threadIdx.x; j < n; j += NT) {
-    fe_all[I.off + j] = -sm[j];
-    fU_all[I.off + j] = -g * eta[j] * szx[j] + buf[j].x - hx[j] * spsi[j];
+    fe_all[I.off + j] = -to_f64(sm[j]);
+    T fU = buf[j].x - gT * num<T>(eta[j]) * szx[j] - num<T>(hx[j]) * spsi[j];
+    fU_all[I.off + j] = to_f64(fU);
   }
 }
 
@@ -257,10 +272,11 @@ __global__ void __launch_bounds__(NT) k_linimp_res1d(const Inst1d* __restrict__ 
     Uh[m] = mul_mi(z - zc) * 0.5;
   }
   __syncthreads();
-  spectral_matvec<double, NT, MAXB>(buf, n, I.log2n, kunit, [&](int m) { return uh[m]; },
+  const Spec<double> sp = make_spec<double>(n, I.L, sigma, alpha);
+  spectral_matvec<double, NT, MAXB>(buf, sp, I.log2n, [&](int m) { return uh[m]; },
                                     CoefGlobal64{eta_all + I.off, hx_all + I.off}, nullptr, tw);
   for (int m = threadIdx.x; m <= h; m += NT) {
-    double k = mode_k(m, n, kunit);
+    double k = sp.k(m);
     cplx<double> gu = gv_mode(buf, m, n, k);
     out[m] = uh[m] * (sigma + alpha * k * k) - gu + Uh[m];
   }
@@ -285,7 +301,7 @@ __global__ void __launch_bounds__(NT) k_linimp_solve1d(const Inst1d* __restrict_
   const double sigma = A[id].sigma, alpha = A[id].alpha;
   const long long hs = I.ws / kWsVectors;
   for (int m = threadIdx.x; m <= h; m += NT) {
-    double k = mode_k(m, n, kunit);
+    double k = (m == h) ? 0.0 : kunit * (double)m;
     cplx<double> v = (res1[hs + m] * c1 + res0[hs + m] * c0) * (1.0 / (sigma + alpha * k * k));
     buf[m] = v;
     if (m > 0 && m < h) buf[n - m] = conj(v);
@@ -303,15 +319,16 @@ __global__ void __launch_bounds__(NT) k_linimp_solve1d(const Inst1d* __restrict_
 // =======================================================================================
 
 cudaError_t twiddles_init(void* tw64, void* tw32, cudaStream_t s) {
-  k_twiddles<<<kTwiddleN / 256, 256, 0, s>>>(static_cast<cplx<double>*>(tw64),
-                                            static_cast<cplx<float>*>(tw32));
+  k_twiddles<<<kTwiddleN / 256, 256, 0, s>>>(
+      static_cast<cplx<double>*>(tw64), static_cast<cplx<float>*>(tw32),
+      reinterpret_cast<cplx<df>*>(static_cast<char*>(tw32) + kTw32Bytes));
   return cudaGetLastError();
 }
 
 cudaError_t launch_deriv1d(const Layout1d& lay, const void* tw64, const double* f, double* fx,
                            cudaStream_t s) {
   auto tw = static_cast<const cplx<double>*>(tw64);
-  return for_each_class(lay, [&](auto NTc, auto MBc, int l, int first, int num) {
+  return for_each_class(lay, s, [&](auto NTc, auto MBc, int l, int first, int num, cudaStream_t s) {
     constexpr int NT = decltype(NTc)::value, MB = decltype(MBc)::value;
     size_t sm = (size_t)16 << l;
     auto k = k_deriv1d<NT, MB>;
@@ -325,7 +342,7 @@ cudaError_t launch_deriv1d(const Layout1d& lay, const void* tw64, const double* 
 cudaError_t launch_apply_G1d(const Layout1d& lay, const void* tw64, const double* eta,
                              const double* hx, const double* u, double* Gu, cudaStream_t s) {
   auto tw = static_cast<const cplx<double>*>(tw64);
-  return for_each_class(lay, [&](auto NTc, auto MBc, int l, int first, int num) {
+  return for_each_class(lay, s, [&](auto NTc, auto MBc, int l, int first, int num, cudaStream_t s) {
     constexpr int NT = decltype(NTc)::value, MB = decltype(MBc)::value;
     size_t sm = (size_t)16 << l;
     auto k = k_apply_G1d<NT, MB>;
@@ -345,7 +362,7 @@ cudaError_t launch_coeffs1d(const Layout1d& lay, const double* eta, const double
 cudaError_t launch_precond1d(const Layout1d& lay, const void* tw64, const SolveRec* rec,
                              const double* r, double* z, cudaStream_t s) {
   auto tw = static_cast<const cplx<double>*>(tw64);
-  return for_each_class(lay, [&](auto NTc, auto MBc, int l, int first, int num) {
+  return for_each_class(lay, s, [&](auto NTc, auto MBc, int l, int first, int num, cudaStream_t s) {
     constexpr int NT = decltype(NTc)::value, MB = decltype(MBc)::value;
     size_t sm = (size_t)16 << l;
     auto k = k_precond1d<NT, MB>;
@@ -356,18 +373,28 @@ cudaError_t launch_precond1d(const Layout1d& lay, const void* tw64, const SolveR
   });
 }
 
-cudaError_t launch_rhs1d(const Layout1d& lay, const void* tw64, double g, const double* eta,
-                         const double* u, const double* h, const double* hx, double* f_eta,
-                         double* f_U, double* scratch, cudaStream_t s) {
-  auto tw = static_cast<const cplx<double>*>(tw64);
-  return for_each_class(lay, [&](auto NTc, auto MBc, int l, int first, int num) {
+cudaError_t launch_rhs1d(const Layout1d& lay, const void* tw64, const void* tw32, int precision,
+                         double g, const double* eta, const double* u, const double* h,
+                         const double* hx, double* f_eta, double* f_U, double* scratch,
+                         cudaStream_t s) {
+  auto t64 = static_cast<const cplx<double>*>(tw64);
+  auto tdf = reinterpret_cast<const cplx<df>*>(static_cast<const char*>(tw32) + kTw32Bytes);
+  return for_each_class(lay, s, [&](auto NTc, auto MBc, int l, int first, int num, cudaStream_t s) {
     constexpr int NT = decltype(NTc)::value, MB = decltype(MBc)::value;
     size_t sm = (size_t)16 << l;
-    auto k = k_rhs1d<NT, MB>;
-    cudaError_t e = set_smem(k, sm);
-    if (e) return e;
-    k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, tw, g, eta, u, h, hx, f_eta, f_U,
-                          scratch, lay.points);
+    if (precision == SGN_PREC_MIXED) {
+      auto k = k_rhs1d<df, NT, MB>;
+      cudaError_t e = set_smem(k, sm);
+      if (e) return e;
+      k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, tdf, g, eta, u, h, hx, f_eta, f_U,
+                            scratch, lay.points);
+    } else {
+      auto k = k_rhs1d<double, NT, MB>;
+      cudaError_t e = set_smem(k, sm);
+      if (e) return e;
+      k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, t64, g, eta, u, h, hx, f_eta, f_U,
+                            scratch, lay.points);
+    }
     return cudaGetLastError();
   });
 }
@@ -389,7 +416,7 @@ cudaError_t launch_linimp_res1d(const Layout1d& lay, const void* tw64, const Sol
                                    const double* eta, const double* hx, const double* u,
                                    const double* U, void* res_hat, void* ws, cudaStream_t s) {
   auto tw = static_cast<const cplx<double>*>(tw64);
-  return for_each_class(lay, [&](auto NTc, auto MBc, int l, int first, int num) {
+  return for_each_class(lay, s, [&](auto NTc, auto MBc, int l, int first, int num, cudaStream_t s) {
     constexpr int NT = decltype(NTc)::value, MB = decltype(MBc)::value;
     size_t sm = (size_t)16 << l;
     auto k = k_linimp_res1d<NT, MB>;
@@ -405,7 +432,7 @@ cudaError_t launch_linimp_solve1d(const Layout1d& lay, const void* tw64, const S
                                   const void* res1_hat, const void* res0_hat, double c1,
                                   double c0, double* u, cudaStream_t s) {
   auto tw = static_cast<const cplx<double>*>(tw64);
-  return for_each_class(lay, [&](auto NTc, auto MBc, int l, int first, int num) {
+  return for_each_class(lay, s, [&](auto NTc, auto MBc, int l, int first, int num, cudaStream_t s) {
     constexpr int NT = decltype(NTc)::value, MB = decltype(MBc)::value;
     size_t sm = (size_t)16 << l;
     auto k = k_linimp_solve1d<NT, MB>;

@@ -70,44 +70,77 @@ __device__ __forceinline__ void coeffs_block(const double* __restrict__ eta, con
 }
 
 // ---------------------------------------------------------------------------------------
+// Spectral constants of one instance in the working precision T, so that per-mode work
+// never leaves T (on this part one stray float64 op costs ~62 float32 ops).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+struct Spec {
+  T kunit;     // 2 pi / L
+  T sigma;     // preconditioner A = sigma I - alpha d^2/dx^2
+  T alpha;
+  int n, h;
+  __device__ __forceinline__ T k(int m) const {        // m in [0, n/2], Nyquist -> 0
+    return m == h ? from_int<T>(0) : kunit * from_int<T>(m);
+  }
+  __device__ __forceinline__ T weight(int m) const {   // Parseval weight on half spectra
+    return (m == 0 || m == h) ? from_int<T>(1) : from_int<T>(2);
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ Spec<T> make_spec(int n, double L, double sigma, double alpha) {
+  Spec<T> s;
+  s.kunit = num<T>(2.0 * kPi / L);
+  s.sigma = num<T>(sigma);
+  s.alpha = num<T>(alpha);
+  s.n = n;
+  s.h = n >> 1;
+  return s;
+}
+
+// ---------------------------------------------------------------------------------------
 // Matvec in spectral form.  `get(m)` returns the half-spectrum coefficient of the input
 // for m in [0, n/2] (it may read buf[m]: each thread writes only buf[m] and buf[n-m] of
 // the modes it read).  On return buf holds Y = FFT(w + i q); extract (G v)_m with gv_mode.
 // ---------------------------------------------------------------------------------------
 template <typename T, int NT, int MAXB, typename Get, typename Coef>
-__device__ __forceinline__ void spectral_matvec(cplx<T>* buf, int n, int log2n, double kunit,
+__device__ __forceinline__ void spectral_matvec(cplx<T>* buf, const Spec<T>& sp, int log2n,
                                                 Get get, Coef coef, double* __restrict__ vout,
                                                 const cplx<T>* __restrict__ tw) {
-  const int h = n >> 1;
+  const int n = sp.n, h = sp.h;
+  const T one = from_int<T>(1);
   for (int m = threadIdx.x; m <= h; m += NT) {
     cplx<T> v = get(m);
-    T k = (T)mode_k(m, n, kunit);
-    buf[m] = v * ((T)1 - k);
-    if (m > 0 && m < h) buf[n - m] = conj(v) * ((T)1 + k);
+    const T k = sp.k(m);
+    buf[m] = v * (one - k);
+    if (m > 0 && m < h) buf[n - m] = conj(v) * (one + k);
   }
   __syncthreads();
   cta_fft<T, NT, MAXB>(buf, n, log2n, true, tw);
-  const T inv_n = (T)1 / (T)n;
+  const T inv_n = num<T>(1.0 / (double)n);
   for (int j = threadIdx.x; j < n; j += NT) {
     cplx<T> z = buf[j];
     T v = z.x * inv_n, vx = z.y * inv_n;
     T c1, c2, c3;
     coef(j, c1, c2, c3);
-    if (vout) vout[j] = (double)v;
+    if (vout) vout[j] = to_f64(v);
     buf[j] = mk(c1 * v + c2 * vx, c2 * v + c3 * vx);
   }
   __syncthreads();
   cta_fft<T, NT, MAXB>(buf, n, log2n, false, tw);
 }
 
+// (G v)_m = w_m - i k_m q_m = ((1 - k) Y_m + (1 + k) conj(Y_{n-m})) / 2
 template <typename T>
 __device__ __forceinline__ cplx<T> gv_mode(const cplx<T>* buf, int m, int n, T k) {
+  const T one = from_int<T>(1);
   cplx<T> y = buf[m];
   cplx<T> yc = conj(buf[(n - m) & (n - 1)]);
-  return (y * ((T)1 - k) + yc * ((T)1 + k)) * (T)0.5;
+  cplx<T> s = y * (one - k) + yc * (one + k);
+  return mk(half(s.x), half(s.y));
 }
 
-// FP64 coefficients of Def:MatrixM (1d) computed from eta and h_x on the fly
+// float64 coefficients of Def:MatrixM (1d) computed from eta and h_x on the fly
 struct CoefGlobal64 {
   const double* eta;
   const double* hx;
@@ -119,6 +152,7 @@ struct CoefGlobal64 {
   }
 };
 
+// float32 coefficients: c1 = eta (1 + h_x^2), c2 = eta^2 h_x / 2, c3 = eta^3 / 3 in smem
 struct CoefSmem32 {
   const float* c;     // [3][n]
   int n;
@@ -129,22 +163,52 @@ struct CoefSmem32 {
   }
 };
 
+// double-float coefficients: the float32 parts in smem, the remainders in global memory
+struct CoefDF {
+  const float* hi;    // [3][n] shared
+  const float* lo;    // [3][n] global
+  int n;
+  __device__ __forceinline__ void operator()(int j, df& c1, df& c2, df& c3) const {
+    c1 = df(hi[j], lo[j]);
+    c2 = df(hi[n + j], lo[n + j]);
+    c3 = df(hi[2 * n + j], lo[2 * n + j]);
+  }
+};
+
+// Splits the float64 coefficients into float32 parts (smem) and remainders (global).
+template <int NT>
+__device__ __forceinline__ void split_coefficients(const double* __restrict__ eta,
+                                                   const double* __restrict__ hx, int n,
+                                                   float* __restrict__ c_hi,
+                                                   float* __restrict__ c_lo) {
+  for (int j = threadIdx.x; j < n; j += NT) {
+    double e = eta[j], g = hx[j];
+    double c[3] = {e * (1.0 + g * g), 0.5 * e * e * g, e * e * e * (1.0 / 3.0)};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      float hi = (float)c[q];
+      c_hi[q * n + j] = hi;
+      if (c_lo) c_lo[q * n + j] = (float)(c[q] - (double)hi);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------
-// a7: right-hand side f(w, p) of Eq:DAE_DSWE with F from Def:bigF, float64.
+// Derivative pair: buf <- load(j) = f + i g, forward FFT, times i k_m (Nyquist 0) / n,
+// inverse FFT; on return buf[j] = f_x + i g_x (D is real, so it acts on both parts).
 // ---------------------------------------------------------------------------------------
-template <int NT, int MAXB, typename Load>
-__device__ __forceinline__ void deriv_pair(cplx<double>* buf, int n, int log2n, double kunit,
-                                           Load load, const cplx<double>* __restrict__ tw) {
+template <typename T, int NT, int MAXB, typename Load>
+__device__ __forceinline__ void deriv_pair(cplx<T>* buf, int n, int log2n, T kunit_over_n,
+                                           Load load, const cplx<T>* __restrict__ tw) {
   for (int j = threadIdx.x; j < n; j += NT) buf[j] = load(j);
   __syncthreads();
-  cta_fft<double, NT, MAXB>(buf, n, log2n, false, tw);
-  const double inv_n = 1.0 / n;
+  cta_fft<T, NT, MAXB>(buf, n, log2n, false, tw);
   for (int m = threadIdx.x; m < n; m += NT) {
-    double k = kunit * (double)wave_index(m, n) * inv_n;
+    T k = kunit_over_n * from_int<T>(wave_index(m, n));
     buf[m] = mul_pi(buf[m]) * k;
   }
   __syncthreads();
-  cta_fft<double, NT, MAXB>(buf, n, log2n, true, tw);
+  cta_fft<T, NT, MAXB>(buf, n, log2n, true, tw);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -154,23 +218,42 @@ __device__ __forceinline__ void deriv_pair(cplx<double>* buf, int n, int log2n, 
 template <int V>
 using IC = std::integral_constant<int, V>;
 
+// One launch per size class.  When a layout holds several classes they run concurrently on
+// the layout's side streams (event fork from `s`, join back into `s`; largest class first),
+// so a class that occupies few SMs does not leave the rest of the GPU idle.
 template <typename Fn>
-cudaError_t for_each_class(const Layout1d& lay, Fn&& fn) {
-  for (int l = 3; l <= 13; ++l) {
+cudaError_t for_each_class(const Layout1d& lay, cudaStream_t s, Fn&& fn) {
+  int ncls = 0;
+  for (int l = 3; l <= 13; ++l) ncls += lay.class_end[l] > lay.class_begin[l];
+  const bool fan = ncls > 1 && lay.side[0] != nullptr;
+  if (fan && cudaEventRecord(lay.fork, s) != cudaSuccess) return cudaGetLastError();
+  int ci = 0;
+  for (int l = 13; l >= 3; --l) {
     const int b = lay.class_begin[l], e = lay.class_end[l];
     if (e <= b) continue;
+    cudaStream_t cs = s;
+    if (fan) {
+      cs = lay.side[ci];
+      if (cudaStreamWaitEvent(cs, lay.fork, 0) != cudaSuccess) return cudaGetLastError();
+    }
     cudaError_t err = cudaSuccess;
     switch (l) {
-      case 3: case 4: case 5: case 6: case 7: err = fn(IC<32>{}, IC<1>{}, l, b, e - b); break;
-      case 8: err = fn(IC<32>{}, IC<2>{}, l, b, e - b); break;
-      case 9: err = fn(IC<64>{}, IC<2>{}, l, b, e - b); break;
-      case 10: err = fn(IC<128>{}, IC<2>{}, l, b, e - b); break;
-      case 11: err = fn(IC<256>{}, IC<2>{}, l, b, e - b); break;
-      case 12: err = fn(IC<512>{}, IC<2>{}, l, b, e - b); break;
-      case 13: err = fn(IC<512>{}, IC<4>{}, l, b, e - b); break;
+      case 3: case 4: case 5: case 6: case 7: err = fn(IC<32>{}, IC<1>{}, l, b, e - b, cs); break;
+      case 8: err = fn(IC<32>{}, IC<2>{}, l, b, e - b, cs); break;
+      case 9: err = fn(IC<64>{}, IC<2>{}, l, b, e - b, cs); break;
+      case 10: err = fn(IC<128>{}, IC<2>{}, l, b, e - b, cs); break;
+      case 11: err = fn(IC<256>{}, IC<2>{}, l, b, e - b, cs); break;
+      case 12: err = fn(IC<512>{}, IC<2>{}, l, b, e - b, cs); break;
+      case 13: err = fn(IC<512>{}, IC<4>{}, l, b, e - b, cs); break;
       default: return cudaErrorInvalidValue;
     }
     if (err != cudaSuccess) return err;
+    if (fan) {
+      if (cudaEventRecord(lay.join[ci], cs) != cudaSuccess ||
+          cudaStreamWaitEvent(s, lay.join[ci], 0) != cudaSuccess)
+        return cudaGetLastError();
+    }
+    ++ci;
   }
   return cudaSuccess;
 }

@@ -77,6 +77,7 @@ struct sgn_layout {
   sgn::Layout2d l2;
   void* ws = nullptr;               // spectral workspace
   double* scratch = nullptr;        // 5 P doubles (rhs intermediates)
+  float* coef_lo = nullptr;         // 3 P floats (double-float coefficient remainders)
   SolveRec* rec = nullptr;          // [count] per-instance solve reports
   SolveRec* given = nullptr;        // [count] caller-provided coefficients
 };
@@ -108,21 +109,21 @@ __device__ void solve_flops(double n, double lg, int iters, int refinements, int
   }
 }
 
+// One thread per instance; the counters are summed with atomics (one block).
 __global__ void k_accum(const SolveRec* __restrict__ rec, const Inst1d* __restrict__ insts,
                         int count, long long n2d, int log2n2d, int mixed, DevStats* st) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    for (int i = 0; i < count; ++i) {
-      st->solves += 1;
-      st->iterations += rec[i].iters;
-      st->max_iters = max(st->max_iters, rec[i].iters);
-      if (rec[i].status > st->status) st->status = rec[i].status;
-      double f32, f64;
-      const double n = insts ? (double)insts[i].n : (double)n2d;
-      const double lg = insts ? (double)insts[i].log2n : (double)log2n2d;
-      solve_flops(n, lg, rec[i].iters, rec[i].refinements, mixed, f32, f64);
-      st->flops32 += f32;
-      st->flops64 += f64;
-    }
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(&st->solves), 1ull);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&st->iterations),
+              (unsigned long long)rec[i].iters);
+    atomicMax(&st->max_iters, rec[i].iters);
+    atomicMax(&st->status, rec[i].status);
+    double f32, f64;
+    const double n = insts ? (double)insts[i].n : (double)n2d;
+    const double lg = insts ? (double)insts[i].log2n : (double)log2n2d;
+    solve_flops(n, lg, rec[i].iters, rec[i].refinements, mixed, f32, f64);
+    atomicAdd(&st->flops32, f32);
+    atomicAdd(&st->flops64, f64);
   }
 }
 
@@ -235,7 +236,7 @@ extern "C" sgn_status sgn_create(sgn_ctx** out, int device, size_t workspace_byt
   ctx->device = device;
   DeviceGuard g(device);
   if (cudaMalloc(&ctx->tw64, sizeof(double) * 2 * sgn::kTwiddleN) != cudaSuccess ||
-      cudaMalloc(&ctx->tw32, sizeof(float) * 2 * sgn::kTwiddleN) != cudaSuccess) {
+      cudaMalloc(&ctx->tw32, sgn::kTw32Bytes + sgn::kTwDfBytes) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(ctx->tw64);
     delete ctx;
@@ -372,6 +373,7 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
         cudaMalloc(&L.d_ids, sizeof(int) * count) != cudaSuccess ||
         cudaMalloc(&lay->ws, sizeof(double) * 2 * ws) != cudaSuccess ||
         cudaMalloc(&lay->scratch, sizeof(double) * 5 * off) != cudaSuccess ||
+        cudaMalloc(&lay->coef_lo, sizeof(float) * 3 * off) != cudaSuccess ||
         cudaMalloc(&lay->rec, sizeof(SolveRec) * count) != cudaSuccess ||
         cudaMalloc(&lay->given, sizeof(SolveRec) * count) != cudaSuccess) {
       cudaGetLastError();
@@ -383,6 +385,19 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
             cudaSuccess) {
       cudaGetLastError();
       return cleanup(SGN_ERR_CUDA, "layout upload");
+    }
+    int ncls = 0;
+    for (int l = 3; l <= 13; ++l) ncls += L.class_end[l] > L.class_begin[l];
+    if (ncls > 1) {
+      if (cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming) != cudaSuccess)
+        return cleanup(SGN_ERR_CUDA, "layout events");
+      for (int c = 0; c < ncls; ++c) {
+        if (cudaStreamCreateWithFlags(&L.side[c], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&L.join[c], cudaEventDisableTiming) != cudaSuccess) {
+          cudaGetLastError();
+          return cleanup(SGN_ERR_CUDA, "layout streams");
+        }
+      }
     }
   } else {
     cudaError_t e = sgn::layout2d_create(lay->l2, grids[0]);
@@ -403,12 +418,18 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
 extern "C" void sgn_layout_destroy(sgn_layout* lay) {
   if (!lay) return;
   DeviceGuard g(lay->ctx->device);
+  for (int c = 0; c < 16; ++c) {
+    if (lay->l1.side[c]) cudaStreamDestroy(lay->l1.side[c]);
+    if (lay->l1.join[c]) cudaEventDestroy(lay->l1.join[c]);
+  }
+  if (lay->l1.fork) cudaEventDestroy(lay->l1.fork);
   cudaFree(lay->l1.d_inst);
   cudaFree(lay->l1.d_ids);
   delete[] lay->l1.h_inst;
   sgn::layout2d_destroy(lay->l2);
   cudaFree(lay->ws);
   cudaFree(lay->scratch);
+  cudaFree(lay->coef_lo);
   cudaFree(lay->rec);
   cudaFree(lay->given);
   delete lay;
@@ -538,7 +559,7 @@ sgn_status run_pcg(sgn_layout* lay, const double* eta, const double* gradh, cons
   ProfScope prof(ctx, s, 0);
   if (lay->dim == 1) {
     e = sgn::launch_pcg1d(lay->l1, ctx->tw64, ctx->tw32, prec, eta, gradh, b, x, given, kind, rtol,
-                          rtol_inner, maxit, max_refine, lay->rec, lay->ws, s);
+                          rtol_inner, maxit, max_refine, lay->rec, lay->ws, lay->coef_lo, s);
   } else {
     e = sgn::launch_pcg2d(lay->l2, ctx->tw64, ctx->tw32, prec, eta, gradh, b, x, given, kind, rtol,
                           rtol_inner, maxit, max_refine, lay->rec, s);
@@ -593,8 +614,8 @@ extern "C" sgn_status sgn_rhs(sgn_ctx* ctx, const sgn_layout* lay, const double*
   ProfScope prof(ctx, as_stream(stream), 1);
   cudaError_t e =
       lay->dim == 1
-          ? sgn::launch_rhs1d(lay->l1, ctx->tw64, grav, eta, u, h, gradh, f_eta, f_U, lay->scratch,
-                              as_stream(stream))
+          ? sgn::launch_rhs1d(lay->l1, ctx->tw64, ctx->tw32, SGN_PREC_FP64, grav, eta, u, h, gradh,
+                              f_eta, f_U, lay->scratch, as_stream(stream))
           : sgn::launch_rhs2d(lay->l2, ctx->tw64, grav, eta, u, h, gradh, f_eta, f_U,
                               as_stream(stream));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sgn_rhs");
@@ -635,6 +656,7 @@ struct sgn_state {
   DevStats* stats = nullptr;
   int hist = HIST_NONE;
   int levels = 0;                   // valid multistep levels
+  int prec = SGN_PREC_FP64;         // precision of the current step call
   std::vector<double> dt_last;
   double t = 0.0;
   long long step = 0;
@@ -718,9 +740,18 @@ sgn_status lincomb(sgn_state* st, double* out, std::initializer_list<std::pair<c
   return SGN_OK;
 }
 
+// Right-hand side inside the steppers: float64 for FP64 solves, double-float for MIXED.
 sgn_status rhs_at(sgn_state* st, const double* eta, const double* u, double* fe, double* fU,
                   cudaStream_t s) {
-  return sgn_rhs(st->lay->ctx, st->lay, eta, u, st->h, st->gradh, fe, fU, s);
+  sgn_layout* lay = st->lay;
+  if (lay->dim != 1 || st->prec != SGN_PREC_MIXED)
+    return sgn_rhs(lay->ctx, lay, eta, u, st->h, st->gradh, fe, fU, s);
+  ProfScope prof(lay->ctx, s, 1);
+  cudaError_t e = sgn::launch_rhs1d(lay->l1, lay->ctx->tw64, lay->ctx->tw32, SGN_PREC_MIXED,
+                                    lay->grids[0].g, eta, u, st->h, st->gradh, fe, fU,
+                                    lay->scratch, s);
+  if (e != cudaSuccess) return cuda_fail(lay->ctx, e, "rhs launch");
+  return SGN_OK;
 }
 
 sgn_status solve_at(sgn_state* st, const double* eta, const double* U, double* u,
@@ -729,7 +760,7 @@ sgn_status solve_at(sgn_state* st, const double* eta, const double* U, double* u
                          o->prec, o->rtol_inner, o->max_refine, s);
   if (r) return r;
   const bool d1 = st->lay->dim == 1;
-  k_accum<<<1, 32, 0, s>>>(st->lay->rec, d1 ? st->lay->l1.d_inst : nullptr, st->lay->count,
+  k_accum<<<1, 256, 0, s>>>(st->lay->rec, d1 ? st->lay->l1.d_inst : nullptr, st->lay->count,
                            d1 ? 0 : st->lay->l2.P, d1 ? 0 : st->lay->l2.lx + st->lay->l2.ly,
                            o->prec == SGN_PREC_MIXED, st->stats);
   SGN_CUDA(st->lay->ctx, cudaGetLastError());
@@ -777,6 +808,7 @@ sgn_status check_opts(sgn_state* st, const sgn_opts* o) {
   if (!o || !(o->rtol > 0.0) || o->maxit <= 0 ||
       (o->prec != SGN_PREC_FP64 && o->prec != SGN_PREC_MIXED))
     return fail(st->lay->ctx, SGN_ERR_INVALID_ARG, "opts");
+  st->prec = o->prec;
   return SGN_OK;
 }
 

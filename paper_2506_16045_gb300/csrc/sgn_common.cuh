@@ -13,6 +13,66 @@
 
 namespace sgn {
 
+// -------------------------------------------------------------------------------------
+// Double-float number: value = hi + lo with |lo| <= ulp(hi)/2, ~48-bit significand, built
+// from float32 operations only (error-free transformations: Knuth's two-sum and the
+// fused-multiply-add two-product, as in Dekker (1971) and the QD library of Hida, Li and
+// Bailey).  On this part float64 FMA throughput is 1/62 of float32; a double-float add
+// costs 11 float32 operations and a multiply 7, so float64-grade transforms run several
+// times faster in this form.
+// -------------------------------------------------------------------------------------
+struct df {
+  float hi, lo;
+  __host__ __device__ df() {}
+  __device__ __forceinline__ df(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ explicit df(double d) {
+    hi = (float)d;
+    lo = (float)(d - (double)hi);
+  }
+  __device__ __forceinline__ explicit df(int i) : df((double)i) {}
+  __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+// The _rn intrinsics are never contracted into FMAs, which the error-free transformations
+// rely on (each rounding must be the plain rounding of one operation).
+__device__ __forceinline__ df operator+(df a, df b) {
+  float s = __fadd_rn(a.hi, b.hi);
+  float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  float h = __fadd_rn(s, e);
+  return df(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator*(df a, df b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  float h = __fadd_rn(p, e);
+  return df(h, __fsub_rn(e, __fsub_rn(h, p)));
+}
+
+// Conversions used by the generic kernels: num<T>(double), from_int<T>(int), to_f64(T).
+template <typename T>
+__device__ __forceinline__ T num(double d) { return (T)d; }
+template <>
+__device__ __forceinline__ df num<df>(double d) { return df(d); }
+template <typename T>
+__device__ __forceinline__ T from_int(int m) { return (T)m; }
+template <>
+__device__ __forceinline__ df from_int<df>(int m) { return df((float)m, 0.0f); }  // |m| < 2^24
+__device__ __forceinline__ df half(df a) { return df(a.hi * 0.5f, a.lo * 0.5f); }
+__device__ __forceinline__ float half(float a) { return a * 0.5f; }
+__device__ __forceinline__ double half(double a) { return a * 0.5; }
+// reciprocal in the working precision (float: correctly rounded, no float64 involved)
+__device__ __forceinline__ float recip(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ double recip(double a) { return 1.0 / a; }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) { return (double)v; }
+__device__ __forceinline__ double to_f64(df v) { return (double)v; }
+
 template <typename T>
 struct alignas(2 * sizeof(T)) cplx {
   T x, y;

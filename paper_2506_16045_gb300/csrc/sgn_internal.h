@@ -9,6 +9,11 @@ namespace sgn {
 
 constexpr int kTwiddleLog2 = 14;                 // twiddle table resolution: n <= 16384 per axis
 constexpr int kTwiddleN = 1 << kTwiddleLog2;
+// The float32 twiddle allocation also holds the double-float table right after it:
+// [ float32 table, kTw32Bytes ][ double-float table, kTwDfBytes ].
+constexpr size_t kTw64Bytes = (size_t)16 * kTwiddleN;
+constexpr size_t kTw32Bytes = (size_t)8 * kTwiddleN;
+constexpr size_t kTwDfBytes = (size_t)16 * kTwiddleN;
 
 // One 1d periodic instance inside a packed batch.  Real fields of instance i occupy
 // [off, off + n) of every packed array; the spectral workspace of the instance starts at
@@ -42,6 +47,10 @@ struct Layout1d {
   int* d_ids = nullptr;                // instance ids grouped by size class
   int class_begin[16] = {0};           // per log2n: [begin, end) into ids
   int class_end[16] = {0};
+  // side streams and events for running size classes concurrently (null: one stream)
+  cudaStream_t side[16] = {nullptr};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[16] = {nullptr};
 };
 
 // Launchers (all asynchronous on `stream`; return cudaError_t of the launch).
@@ -60,8 +69,10 @@ cudaError_t launch_precond1d(const Layout1d& lay, const void* tw64, const SolveR
 cudaError_t launch_pcg1d(const Layout1d& lay, const void* tw64, const void* tw32, int precision,
                          const double* eta, const double* hx, const double* b, double* x,
                          const SolveRec* given, int kind, double rtol, double rtol_inner,
-                         int maxit, int max_refine, SolveRec* rec, void* ws, cudaStream_t s);
-cudaError_t launch_rhs1d(const Layout1d& lay, const void* tw64, double g, const double* eta,
+                         int maxit, int max_refine, SolveRec* rec, void* ws, float* coef_lo,
+                         cudaStream_t s);
+cudaError_t launch_rhs1d(const Layout1d& lay, const void* tw64, const void* tw32, int precision,
+                         double g, const double* eta,
                          const double* u, const double* h, const double* hx, double* f_eta,
                          double* f_U, double* scratch, cudaStream_t s);
 // out = base + sum_j c_j dt_i f_j over up to 4 terms (per-instance dt from `dt`)
