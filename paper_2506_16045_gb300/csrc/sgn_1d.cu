@@ -40,7 +40,7 @@ __global__ void k_twiddles(cplx<double>* tw64, cplx<float>* tw32, cplx<df>* twdf
 
 // f_x = D f, one field per CTA (complex transform with zero imaginary part)
 template <int NT, int MAXB>
-__global__ void __launch_bounds__(NT) k_deriv1d(const Inst1d* __restrict__ insts,
+__global__ void __launch_bounds__(NT, 1) k_deriv1d(const Inst1d* __restrict__ insts,
                                                 const int* __restrict__ ids,
                                                 const cplx<double>* __restrict__ tw,
                                                 const double* __restrict__ f,
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(NT) k_deriv1d(const Inst1d* __restrict__ insts
 
 // Gu (Def:G) in float64
 template <int NT, int MAXB>
-__global__ void __launch_bounds__(NT) k_apply_G1d(const Inst1d* __restrict__ insts,
+__global__ void __launch_bounds__(NT, 1) k_apply_G1d(const Inst1d* __restrict__ insts,
                                                   const int* __restrict__ ids,
                                                   const cplx<double>* __restrict__ tw,
                                                   const double* __restrict__ eta,
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(NT) k_apply_G1d(const Inst1d* __restrict__ ins
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT) k_coeffs1d(const Inst1d* __restrict__ insts,
+__global__ void __launch_bounds__(NT, 1) k_coeffs1d(const Inst1d* __restrict__ insts,
                                                  const int* __restrict__ ids,
                                                  const double* __restrict__ eta,
                                                  const double* __restrict__ hx, int kind,
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(NT) k_coeffs1d(const Inst1d* __restrict__ inst
 
 // z = A^{-1} r (Def:A): divide mode m by sigma + alpha k_m^2
 template <int NT, int MAXB>
-__global__ void __launch_bounds__(NT) k_precond1d(const Inst1d* __restrict__ insts,
+__global__ void __launch_bounds__(NT, 1) k_precond1d(const Inst1d* __restrict__ insts,
                                                   const int* __restrict__ ids,
                                                   const cplx<double>* __restrict__ tw,
                                                   const SolveRec* __restrict__ rec,
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(NT) k_precond1d(const Inst1d* __restrict__ ins
 // in), Q = u d_x - d^2, S = u s_x (reading R6), and
 // f_eta = -m, f_U = -g eta zeta_x + Phi'_x - h_x Psi, Psi = eta^2 Q/2 + eta m d + eta S + m s.
 template <typename T, int NT, int MAXB>
-__global__ void __launch_bounds__(NT) k_rhs1d(const Inst1d* __restrict__ insts,
+__global__ void __launch_bounds__(NT, 1) k_rhs1d(const Inst1d* __restrict__ insts,
                                               const int* __restrict__ ids,
                                               const cplx<T>* __restrict__ tw, double g,
                                               const double* __restrict__ eta_all,
@@ -242,7 +242,7 @@ __global__ void k_axpy1d(const Inst1d* __restrict__ insts, const double* __restr
 
 // SBDF2: res^ = (sigma + alpha k^2) u^ - (G u)^ + U^  (half spectrum, float64)
 template <int NT, int MAXB>
-__global__ void __launch_bounds__(NT) k_linimp_res1d(const Inst1d* __restrict__ insts,
+__global__ void __launch_bounds__(NT, 1) k_linimp_res1d(const Inst1d* __restrict__ insts,
                                                      const int* __restrict__ ids,
                                                      const cplx<double>* __restrict__ tw,
                                                      const SolveRec* __restrict__ A,
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(NT) k_linimp_res1d(const Inst1d* __restrict__ 
 
 // SBDF2: u = F^{-1}[(c1 res1^ + c0 res0^) / (sigma + alpha k^2)]
 template <int NT, int MAXB>
-__global__ void __launch_bounds__(NT) k_linimp_solve1d(const Inst1d* __restrict__ insts,
+__global__ void __launch_bounds__(NT, 1) k_linimp_solve1d(const Inst1d* __restrict__ insts,
                                                        const int* __restrict__ ids,
                                                        const cplx<double>* __restrict__ tw,
                                                        const SolveRec* __restrict__ A,

@@ -103,6 +103,25 @@ __device__ __forceinline__ Spec<T> make_spec(int n, double L, double sigma, doub
 // for m in [0, n/2] (it may read buf[m]: each thread writes only buf[m] and buf[n-m] of
 // the modes it read).  On return buf holds Y = FFT(w + i q); extract (G v)_m with gv_mode.
 // ---------------------------------------------------------------------------------------
+// Inverse FFT of Z (already in buf), pointwise coefficients, forward FFT.
+template <typename T, int NT, int MAXB, typename Coef>
+__device__ __forceinline__ void matvec_core(cplx<T>* buf, int n, int log2n, const Coef& coef,
+                                            double* __restrict__ vout,
+                                            const cplx<T>* __restrict__ tw) {
+  cta_fft<T, NT, MAXB>(buf, n, log2n, true, tw);
+  const T inv_n = num<T>(1.0 / (double)n);
+  for (int j = threadIdx.x; j < n; j += NT) {
+    cplx<T> z = buf[j];
+    T v = z.x * inv_n, vx = z.y * inv_n;
+    T c1, c2, c3;
+    coef(j, c1, c2, c3);
+    if (vout) vout[j] = to_f64(v);
+    buf[j] = mk(c1 * v + c2 * vx, c2 * v + c3 * vx);
+  }
+  __syncthreads();
+  cta_fft<T, NT, MAXB>(buf, n, log2n, false, tw);
+}
+
 template <typename T, int NT, int MAXB, typename Get, typename Coef>
 __device__ __forceinline__ void spectral_matvec(cplx<T>* buf, const Spec<T>& sp, int log2n,
                                                 Get get, Coef coef, double* __restrict__ vout,
@@ -116,18 +135,7 @@ __device__ __forceinline__ void spectral_matvec(cplx<T>* buf, const Spec<T>& sp,
     if (m > 0 && m < h) buf[n - m] = conj(v) * (one + k);
   }
   __syncthreads();
-  cta_fft<T, NT, MAXB>(buf, n, log2n, true, tw);
-  const T inv_n = num<T>(1.0 / (double)n);
-  for (int j = threadIdx.x; j < n; j += NT) {
-    cplx<T> z = buf[j];
-    T v = z.x * inv_n, vx = z.y * inv_n;
-    T c1, c2, c3;
-    coef(j, c1, c2, c3);
-    if (vout) vout[j] = to_f64(v);
-    buf[j] = mk(c1 * v + c2 * vx, c2 * v + c3 * vx);
-  }
-  __syncthreads();
-  cta_fft<T, NT, MAXB>(buf, n, log2n, false, tw);
+  matvec_core<T, NT, MAXB>(buf, n, log2n, coef, vout, tw);
 }
 
 // (G v)_m = w_m - i k_m q_m = ((1 - k) Y_m + (1 + k) conj(Y_{n-m})) / 2

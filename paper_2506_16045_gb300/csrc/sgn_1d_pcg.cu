@@ -120,8 +120,152 @@ __device__ __forceinline__ double pcg_loop(cplx<TT>* fbuf, double* red, const Sp
   return rz;
 }
 
+// Float32 PCG with r^, p^ and G p held in registers (thread t owns modes t + b NT < n/2;
+// thread 0 also owns the Nyquist mode n/2, whose wavenumber is 0).  R0 holds the
+// right-hand side, Xt accumulates the iterate in global memory.  Same iteration and
+// stopping rule as pcg_loop.  Dot products reduce in double-float across the CTA and
+// thread 0 alone forms alpha, beta and the stopping decision, published through `sc`.
+struct PcgScalars {
+  double rz;      // current r.A^{-1}r
+  float alpha, beta;
+  int state;      // 0 iterate, 1 converged, 2 breakdown, 3 iteration cap
+};
+
+template <int NT, int MAXB>
+__device__ __forceinline__ double pcg_loop_f32(cplx<float>* fbuf, df* slots, PcgScalars* sc,
+                                               const Spec<float>& sp, int log2n,
+                                               const cplx<float>* __restrict__ R0,
+                                               cplx<float>* __restrict__ Xt,
+                                               const CoefSmem32& coef, double tol_abs,
+                                               int it_cap, int& iters, int& status) {
+  constexpr int M = 2 * MAXB;
+  constexpr int W = NT / 32;
+  const int n = sp.n, h = sp.h, t = threadIdx.x;
+  const bool nyq = (t == 0);
+  const float dN = recip(sp.sigma);              // Nyquist: k = 0
+  cplx<float> r[M], p[M], rN = mk(0.0f, 0.0f), pN = mk(0.0f, 0.0f);
+  int it = iters;
+  {
+    float loc = 0.0f;
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      const int m = t + b * NT;
+      if (m < h) {
+        const float k = sp.k(m);
+        const float di = recip(sp.sigma + sp.alpha * k * k);
+        r[b] = R0[m];
+        p[b] = r[b] * di;
+        loc += sp.weight(m) * (r[b].x * p[b].x + r[b].y * p[b].y);
+      }
+    }
+    if (nyq) {
+      rN = R0[h];
+      pN = rN * dN;
+      loc += rN.x * pN.x + rN.y * pN.y;
+    }
+    block_sum_df<NT>(loc, slots, [&](float hi, float lo) {
+      const double rz = (double)hi + (double)lo;
+      sc->rz = rz;
+      sc->state = (sqrt(rz) <= tol_abs) ? 1 : (it >= it_cap ? 3 : 0);
+    });
+  }
+  for (;;) {
+    const int state = sc->state;
+    if (state != 0) {
+      if (state == 3) status = SGN_ERR_NOT_CONVERGED;
+      if (state == 2) status = SGN_ERR_BREAKDOWN;
+      break;
+    }
+    // Z = (1 - k) p for m < n/2, its conjugate mirror, and the Nyquist entry
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      const int m = t + b * NT;
+      if (m < h) {
+        const float k = sp.k(m);
+        fbuf[m] = p[b] * (1.0f - k);
+        if (m > 0) fbuf[n - m] = conj(p[b]) * (1.0f + k);
+      }
+    }
+    if (nyq) fbuf[h] = pN;
+    __syncthreads();
+    matvec_core<float, NT, MAXB>(fbuf, n, log2n, coef, nullptr, nullptr);
+    cplx<float> g[M], gN = mk(0.0f, 0.0f);
+    float pq_loc = 0.0f;
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      const int m = t + b * NT;
+      if (m < h) {
+        g[b] = gv_mode(fbuf, m, n, sp.k(m));
+        pq_loc += sp.weight(m) * (p[b].x * g[b].x + p[b].y * g[b].y);
+      }
+    }
+    if (nyq) {
+      gN = gv_mode(fbuf, h, n, 0.0f);
+      pq_loc += pN.x * gN.x + pN.y * gN.y;
+    }
+    block_sum_df<NT>(pq_loc, slots, [&](float hi, float lo) {
+      const double pq = (double)hi + (double)lo;
+      if (!(pq > 0.0) || !isfinite(pq)) {
+        sc->state = 2;
+      } else {
+        sc->alpha = (float)(sc->rz / pq);
+      }
+    });
+    if (sc->state == 2) {
+      status = SGN_ERR_BREAKDOWN;
+      break;
+    }
+    const float at = sc->alpha;
+    float rz_loc = 0.0f;
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      const int m = t + b * NT;
+      if (m < h) {
+        const float k = sp.k(m);
+        const float di = recip(sp.sigma + sp.alpha * k * k);
+        Xt[m] = Xt[m] + p[b] * at;
+        r[b] = r[b] - g[b] * at;
+        rz_loc += sp.weight(m) * (r[b].x * r[b].x + r[b].y * r[b].y) * di;
+      }
+    }
+    if (nyq) {
+      Xt[h] = Xt[h] + pN * at;
+      rN = rN - gN * at;
+      rz_loc += (rN.x * rN.x + rN.y * rN.y) * dN;
+    }
+    ++it;
+    block_sum_df<NT>(rz_loc, slots + W, [&](float hi, float lo) {
+      const double rz_new = (double)hi + (double)lo;
+      if (!isfinite(rz_new)) {
+        sc->state = 2;
+      } else {
+        sc->beta = (float)(rz_new / sc->rz);
+        sc->rz = rz_new;
+        sc->state = (sqrt(rz_new) <= tol_abs) ? 1 : (it >= it_cap ? 3 : 0);
+      }
+    });
+    if (sc->state == 2) {
+      status = SGN_ERR_BREAKDOWN;
+      break;
+    }
+    const float beta = sc->beta;
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      const int m = t + b * NT;
+      if (m < h) {
+        const float k = sp.k(m);
+        const float di = recip(sp.sigma + sp.alpha * k * k);
+        p[b] = r[b] * di + p[b] * beta;
+      }
+    }
+    if (nyq) pN = rN * dN + pN * beta;
+  }
+  iters = it;
+  return sc->rz;
+}
+
 template <typename TI, int NT, int MAXB, bool MIXED>
-__global__ void __launch_bounds__(NT) k_pcg1d(const Inst1d* __restrict__ insts,
+__global__ void __launch_bounds__(NT, 1) k_pcg1d(const Inst1d* __restrict__ insts,
                                               const int* __restrict__ ids,
                                               const cplx<double>* __restrict__ tw64,
                                               const cplx<float>* __restrict__ tw32,
@@ -139,6 +283,8 @@ __global__ void __launch_bounds__(NT) k_pcg1d(const Inst1d* __restrict__ insts,
   constexpr int MPT = 2 * MAXB + 1;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[NT / 32 + 1];
+  __shared__ df slots[2 * (NT / 32)];
+  __shared__ PcgScalars sc;
   cplx<TH>* bufh = reinterpret_cast<cplx<TH>*>(smem);
   const cplx<TH>* twh;
   if constexpr (MIXED) twh = twdf; else twh = tw64;
@@ -265,9 +411,10 @@ __global__ void __launch_bounds__(NT) k_pcg1d(const Inst1d* __restrict__ insts,
           Dh[m] = mk(0.0f, 0.0f);
         }
       }
+      __syncthreads();
       int st_in = SGN_OK;
-      pcg_loop<float, NT, MAXB>(buf32, red, spi, log2n, Rh, Ph, Dh, Gh, coef32, tw32, rtol_inner,
-                                maxit, iters, st_in);
+      pcg_loop_f32<NT, MAXB>(buf32, slots, &sc, spi, log2n, Rh, Dh, coef32, rtol_inner, maxit,
+                             iters, st_in);
       if (st_in == SGN_ERR_BREAKDOWN) status = SGN_ERR_BREAKDOWN;
       ++refinements;
       const df unscale(sqrt(rz64));

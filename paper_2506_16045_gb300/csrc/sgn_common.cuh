@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "sgn_internal.h"
 
 namespace sgn {
@@ -104,6 +106,14 @@ __device__ __forceinline__ cplx<T> mul_pi(cplx<T> a) { return mk(-a.y, a.x); }  
 template <typename T>
 __device__ __forceinline__ cplx<T> mul_mi(cplx<T> a) { return mk(a.y, -a.x); }   // * (-i)
 
+// e^{-+2 pi i j / m} for integers j and m = 2^log2m, float32, computed in registers
+// (sincospif of the exactly representable argument 2j/m) instead of a table load.
+__device__ __forceinline__ cplx<float> twiddle_f32(int j, int log2m, bool inverse) {
+  float s, c;
+  sincospif(__int_as_float((128 - log2m) << 23) * (float)j, &s, &c);   // (2/m) j
+  return mk(c, inverse ? s : -s);
+}
+
 // Signed integer wavenumber index of mode m for length n, with the n/2 mode mapped to 0.
 __device__ __forceinline__ int wave_index(int m, int n) {
   int h = n >> 1;
@@ -119,6 +129,9 @@ __device__ __forceinline__ int wave_index(int m, int n) {
 // is in place.  MAXB bounds butterflies per thread per radix-4 stage: n/4 <= MAXB*NT.
 // All NT threads must call; returns after a barrier.
 // -------------------------------------------------------------------------------------
+// Twiddles come from `tw` (a table of e^{-2 pi i j / 2^14}); with tw == nullptr (float32
+// only) they are computed in registers, which avoids L2 round trips when shared memory
+// leaves little L1 for the table.
 template <typename T, int NT, int MAXB>
 __device__ __forceinline__ void cta_fft(cplx<T>* buf, int n, int log2n, bool inverse,
                                         const cplx<T>* __restrict__ tw) {
@@ -169,10 +182,27 @@ __device__ __forceinline__ void cta_fft(cplx<T>* buf, int n, int log2n, bool inv
         cplx<T> a2 = buf[i + 2 * q];
         cplx<T> a3 = buf[i + 3 * q];
         if (p > 1) {
-          int e = k << tshift;
-          a1 = cmul_tw(a1, tw[e], inverse);
-          a2 = cmul_tw(a2, tw[2 * e], inverse);
-          a3 = cmul_tw(a3, tw[3 * e], inverse);
+          if constexpr (std::is_same<T, float>::value) {
+            if (tw == nullptr) {
+              // w = e^{-+2 pi i k / (4p)}, w^2 and w^3 by complex products
+              const cplx<float> w1 = twiddle_f32(k, lp + 2, inverse);
+              const cplx<float> w2 = cmul(w1, w1);
+              const cplx<float> w3 = cmul(w1, w2);
+              a1 = cmul(a1, w1);
+              a2 = cmul(a2, w2);
+              a3 = cmul(a3, w3);
+            } else {
+              int e = k << tshift;
+              a1 = cmul_tw(a1, tw[e], inverse);
+              a2 = cmul_tw(a2, tw[2 * e], inverse);
+              a3 = cmul_tw(a3, tw[3 * e], inverse);
+            }
+          } else {
+            int e = k << tshift;
+            a1 = cmul_tw(a1, tw[e], inverse);
+            a2 = cmul_tw(a2, tw[2 * e], inverse);
+            a3 = cmul_tw(a3, tw[3 * e], inverse);
+          }
         }
         cplx<T> s02 = a0 + a2, d02 = a0 - a2;
         cplx<T> s13 = a1 + a3, d13 = a1 - a3;
@@ -223,6 +253,35 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
   }
   __syncthreads();
   return scratch[NT / 32];
+}
+
+// Block sum of float partials with double-float (~48-bit) accumulation: warp shuffles of
+// (hi, lo) pairs, then warp 0 over the per-warp partials.  No float64 instruction runs
+// (on this part each costs ~62 float32 ones).  `slot` (NT/32 df entries) must not be in use
+// by another reduction still being read; callers alternate two slots.  After the call only
+// warp 0 holds the result; `finish(total_hi, total_lo)` runs on thread 0 before the final
+// barrier, so it can publish scalars through shared memory to the whole CTA.
+template <int NT, typename Finish>
+__device__ __forceinline__ void block_sum_df(float v, df* slot, Finish finish) {
+  df a(v, 0.0f);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    df b(__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o));
+    a = a + b;
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) slot[w] = a;
+  __syncthreads();
+  if (w == 0) {
+    df r = (l < NT / 32) ? slot[l] : df(0.0f, 0.0f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      df b(__shfl_xor_sync(0xffffffffu, r.hi, o), __shfl_xor_sync(0xffffffffu, r.lo, o));
+      r = r + b;
+    }
+    if (l == 0) finish(r.hi, r.lo);
+  }
+  __syncthreads();
 }
 
 template <int NT>
