@@ -130,6 +130,8 @@ __device__ __forceinline__ void spectral_matvec(cplx<T>* buf, const Spec<T>& sp,
   const T one = from_int<T>(1);
   for (int m = threadIdx.x; m <= h; m += NT) {
     cplx<T> v = get(m);
+    // the DC and Nyquist coefficients of a real field are real: drop rounding residue
+    if (m == 0 || m == h) v = mk(v.x, from_int<T>(0));
     const T k = sp.k(m);
     buf[m] = v * (one - k);
     if (m > 0 && m < h) buf[n - m] = conj(v) * (one + k);

@@ -182,11 +182,15 @@ __device__ __forceinline__ double pcg_loop_f32(cplx<float>* fbuf, df* slots, Pcg
       const int m = t + b * NT;
       if (m < h) {
         const float k = sp.k(m);
-        fbuf[m] = p[b] * (1.0f - k);
-        if (m > 0) fbuf[n - m] = conj(p[b]) * (1.0f + k);
+        if (m > 0) {
+          fbuf[m] = p[b] * (1.0f - k);
+          fbuf[n - m] = conj(p[b]) * (1.0f + k);
+        } else {
+          fbuf[0] = mk(p[b].x, 0.0f);            // real DC coefficient
+        }
       }
     }
-    if (nyq) fbuf[h] = pN;
+    if (nyq) fbuf[h] = mk(pN.x, 0.0f);            // real Nyquist coefficient
     __syncthreads();
     matvec_core<float, NT, MAXB>(fbuf, n, log2n, coef, nullptr, nullptr);
     cplx<float> g[M], gN = mk(0.0f, 0.0f);

@@ -1,51 +1,1396 @@
-// 2d (doubly periodic) kernels.
+// 2d (doubly periodic) kernels: spectral derivatives, G-matvec, A^{-1}, PCG (float64, or
+// float32 inner solves inside double-float refinement), right-hand side, SBDF2 pieces.
+//
+// Layout.  Real fields are [ny][nx] row-major; a vector field is two such planes.  Spectra
+// of real fields are half spectra [ny][H], H = nx/2 + 1 (kx = 0..nx/2, all ky).  A 2d
+// transform is a row pass (two real rows packed into one complex FFT of length nx, split
+// into two half rows by Hermitian symmetry) and a column pass (tiles of TW half-spectrum
+// columns transposed into shared memory and transformed as a batch of length-ny FFTs).
+//
+// Matvec (Def:G, §2.2, in the weak form of Def:MatrixM): with d = div p,
+//   w = eta (I + grad h grad h^T) p + eta^2/2 grad h d,   q = eta^2/2 grad h . p + eta^3/3 d,
+//   G p = w - grad q.
+// In spectral form: column iFFT of (p1^, p2^, d^ = i kx p1^ + i ky p2^), one row kernel
+// (C2R, pointwise w and q, R2C), column FFT whose epilogue forms (G p)^ = w^ - i k q^.
+// A^{-1} per mode (Def:A): z = (r - alpha k (k.r) / (sigma + alpha |k|^2)) / sigma.
+// The n/2 wavenumbers are 0 in both directions (§6.1).
+#include <cstdio>
+#include <vector>
+
+#include "sgn_1d_dev.cuh"
 #include "sgn_2d.h"
 
 namespace sgn {
 
+// device-resident scalars of one 2d solve
+struct Scal2d {
+  double bb;           // b.A^{-1}b (high precision problem)
+  double rz;           // inner r.z
+  double rz64;         // refinement residual r.A^{-1}r
+  double alpha, beta;
+  double tol;          // inner absolute tolerance on sqrt(r.z)
+  int done;            // inner loop finished
+  int iters;           // inner iterations (this solve)
+  int cap;             // iteration cap
+  int status;
+  unsigned int ticket; // last-block counter
+  double sigma, alpha_A, kappa_ub, eta_min, eta_max;
+  int flat;
+};
+
+namespace {
+
+using d1::kPi;
+using d1::kLambdaPlus;
+using d1::kLambdaMinus;
+using d1::kFlatSlope;
+
+constexpr int kRowNT = 256;
+constexpr int kColNT = 512;
+constexpr int kMaxParts = 2048;
+
+// ---- mode helpers --------------------------------------------------------------------
+struct Modes2d {
+  int nx, ny, H;
+  double kxu, kyu;     // 2 pi / Lx, 2 pi / Ly
+  __device__ __forceinline__ double kx(int c) const { return c == (nx >> 1) ? 0.0 : kxu * c; }
+  __device__ __forceinline__ double ky(int y) const { return kyu * wave_index(y, ny); }
+  __device__ __forceinline__ double weight(int c) const {
+    return (c == 0 || c == (nx >> 1)) ? 1.0 : 2.0;
+  }
+};
+
+__host__ Modes2d modes_of(const Layout2d& L) {
+  Modes2d M;
+  M.nx = L.nx;
+  M.ny = L.ny;
+  M.H = L.nx / 2 + 1;
+  M.kxu = 2.0 * kPi / L.Lx;
+  M.kyu = 2.0 * kPi / L.Ly;
+  return M;
+}
+
+template <typename T>
+__device__ __forceinline__ cplx<T> mul_ik(cplx<T> a, T k) {   // i k a
+  return mk(-(a.y * k), a.x * k);
+}
+
+template <typename T>
+__device__ __forceinline__ cplx<T> ld_c(const void* base, long long i) {
+  return reinterpret_cast<const cplx<T>*>(base)[i];
+}
+template <typename T>
+__device__ __forceinline__ void st_c(void* base, long long i, cplx<T> v) {
+  reinterpret_cast<cplx<T>*>(base)[i] = v;
+}
+
+// the twiddle table of each precision
+template <typename T>
+struct Tw;
+template <>
+struct Tw<double> {
+  static __device__ __forceinline__ const cplx<double>* get(const void* t64, const void* t32) {
+    return static_cast<const cplx<double>*>(t64);
+  }
+};
+template <>
+struct Tw<float> {
+  static __device__ __forceinline__ const cplx<float>* get(const void* t64, const void* t32) {
+    return static_cast<const cplx<float>*>(t32);
+  }
+};
+template <>
+struct Tw<df> {
+  static __device__ __forceinline__ const cplx<df>* get(const void* t64, const void* t32) {
+    return reinterpret_cast<const cplx<df>*>(static_cast<const char*>(t32) + kTw32Bytes);
+  }
+};
+
+// ---- last-block reduction ------------------------------------------------------------
+// Each block writes its partial sum; the last block to arrive sums them in a fixed order
+// (deterministic) and runs `fin(total)` on thread 0.
+template <int NT, typename Fin>
+__device__ __forceinline__ void grid_reduce(double v, double* parts, Scal2d* sc, Fin fin) {
+  __shared__ double red[NT / 32 + 1];
+  __shared__ bool last;
+  double s = block_sum<NT>(v, red);
+  if (threadIdx.x == 0) {
+    parts[blockIdx.x] = s;
+    __threadfence();
+    unsigned int t = atomicAdd(&sc->ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < gridDim.x; i += NT) acc += ((volatile double*)parts)[i];
+    acc = block_sum<NT>(acc, red);
+    if (threadIdx.x == 0) {
+      sc->ticket = 0;
+      fin(acc);
+      __threadfence();
+    }
+  }
+}
+
+// =======================================================================================
+// Column pass: tiles of TW columns of K half planes, transposed into shared memory
+// (column c of plane q at buf + (q TW + c) * (ny + 1)), transformed along y.
+// =======================================================================================
+enum ColMode { COL_FWD = 0, COL_INV = 1, COL_MATVEC_IN = 2, COL_MATVEC_OUT = 3 };
+
+struct ColArgs {
+  void* planes[4];          // K half planes (cplx<T>), in place unless noted
+  int K;
+  // COL_MATVEC_IN: input vector (2 half planes of cplx<TV>) and optional p update
+  const void* vin[2];
+  // COL_MATVEC_OUT: output G v (2 half planes) and the dot partner
+  void* vout[2];
+  const void* vdot[2];
+  const void* bvec[2];      // residual mode: r = b - G x (high precision)
+  int residual;             // 1: out = b - G v instead of G v
+  Scal2d* sc;
+  double* parts;
+  int pupdate;              // COL_MATVEC_IN: p = A^{-1} r + beta p first (r in rin)
+  void* pio[2];             // p planes (read/write) when pupdate
+  const void* rin[2];
+  int check_done;           // return immediately when sc->done
+};
+
+template <typename T, int TW, int MAXB, int MODE>
+__global__ void __launch_bounds__(kColNT, 1) k2_cols(Modes2d M, int log2ny, const void* t64,
+                                                     const void* t32, ColArgs a) {
+  if (a.check_done && ((volatile Scal2d*)a.sc)->done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem);
+  const cplx<T>* tw = Tw<T>::get(t64, t32);
+  const int ny = M.ny, H = M.H, stride = ny + 1;
+  const int c0 = blockIdx.x * TW;
+  const int nplanes = (MODE == COL_MATVEC_IN || MODE == COL_MATVEC_OUT) ? 3 : a.K;
+  const double sigma = a.sc ? a.sc->sigma : 0.0, alphaA = a.sc ? a.sc->alpha_A : 0.0;
+
+  // ---- load
+  for (int e = threadIdx.x; e < TW * ny; e += kColNT) {
+    const int y = e / TW, c = e % TW, col = c0 + c;
+    const long long gi = (long long)y * H + col;
+    const bool ok = col < H;
+    if constexpr (MODE == COL_MATVEC_IN) {
+      cplx<T> p1 = mk(from_int<T>(0), from_int<T>(0)), p2 = p1;
+      if (ok) {
+        if (a.pupdate) {
+          // p = A^{-1} r + beta p (Sherman-Morrison of sigma I + alpha k k^T)
+          const double kx = M.kx(col), ky = M.ky(y);
+          cplx<T> r1 = ld_c<T>(a.rin[0], gi), r2 = ld_c<T>(a.rin[1], gi);
+          cplx<T> q1 = ld_c<T>(a.pio[0], gi), q2 = ld_c<T>(a.pio[1], gi);
+          const T beta = num<T>(a.sc->beta);
+          const T kxT = num<T>(kx), kyT = num<T>(ky);
+          const T f = num<T>(alphaA / (sigma + alphaA * (kx * kx + ky * ky)));
+          const T is = num<T>(1.0 / sigma);
+          cplx<T> kr = r1 * kxT + r2 * kyT;
+          cplx<T> z1 = (r1 - kr * (f * kxT)) * is, z2 = (r2 - kr * (f * kyT)) * is;
+          p1 = z1 + q1 * beta;
+          p2 = z2 + q2 * beta;
+          st_c<T>(a.pio[0], gi, p1);
+          st_c<T>(a.pio[1], gi, p2);
+        } else {
+          p1 = ld_c<T>(a.vin[0], gi);
+          p2 = ld_c<T>(a.vin[1], gi);
+        }
+      }
+      buf[(0 * TW + c) * stride + y] = p1;
+      buf[(1 * TW + c) * stride + y] = p2;
+    } else {
+      for (int q = 0; q < nplanes; ++q)
+        buf[(q * TW + c) * stride + y] = ok ? ld_c<T>(a.planes[q], gi)
+                                            : mk(from_int<T>(0), from_int<T>(0));
+    }
+  }
+  __syncthreads();
+  if constexpr (MODE == COL_MATVEC_IN) {
+    // A real field's half spectrum is Hermitian in ky on the kx = 0 and kx = nx/2 columns.
+    // Rounding in the float32 inner solves leaves a small anti-Hermitian part there, which
+    // the packed row C2R would leak between fields; project it out before the transform,
+    // then form d^ = i kx p1^ + i ky p2^ from the projected vector.
+    for (int c = 0; c < TW; ++c) {
+      const int col = c0 + c;
+      if (col != 0 && col != (M.nx >> 1)) continue;
+      for (int q = 0; q < 2; ++q) {
+        cplx<T>* v = buf + (q * TW + c) * stride;
+        for (int y = threadIdx.x; y <= (ny >> 1); y += kColNT) {
+          const int ym = (ny - y) & (ny - 1);
+          cplx<T> a = v[y], b = conj(v[ym]);
+          cplx<T> s = a + b;
+          cplx<T> hm = mk(half(s.x), half(s.y));
+          v[y] = hm;
+          v[ym] = conj(hm);
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < TW * ny; e += kColNT) {
+      const int y = e / TW, c = e % TW, col = c0 + c;
+      const T kx = num<T>(col < H ? M.kx(col) : 0.0), ky = num<T>(M.ky(y));
+      buf[(2 * TW + c) * stride + y] =
+          mul_ik(buf[(0 * TW + c) * stride + y], kx) + mul_ik(buf[(1 * TW + c) * stride + y], ky);
+    }
+    __syncthreads();
+  }
+  const bool inverse = (MODE == COL_INV || MODE == COL_MATVEC_IN);
+  for (int q = 0; q < nplanes; ++q)
+    cta_fft_batch<T, kColNT, MAXB>(buf + q * TW * stride, ny, log2ny, TW, stride, inverse, tw);
+
+  // ---- store / epilogue
+  if constexpr (MODE == COL_MATVEC_OUT) {
+    double part = 0.0;
+    for (int e = threadIdx.x; e < TW * ny; e += kColNT) {
+      const int y = e / TW, c = e % TW, col = c0 + c;
+      if (col >= H) continue;
+      const long long gi = (long long)y * H + col;
+      const T kx = num<T>(M.kx(col)), ky = num<T>(M.ky(y));
+      cplx<T> w1 = buf[(0 * TW + c) * stride + y], w2 = buf[(1 * TW + c) * stride + y];
+      cplx<T> qh = buf[(2 * TW + c) * stride + y];
+      cplx<T> g1 = w1 - mul_ik(qh, kx), g2 = w2 - mul_ik(qh, ky);
+      if (a.residual) {
+        g1 = ld_c<T>(a.bvec[0], gi) - g1;
+        g2 = ld_c<T>(a.bvec[1], gi) - g2;
+        // r.A^{-1}r for the stopping test
+        const double kxd = M.kx(col), kyd = M.ky(y);
+        const double k2 = kxd * kxd + kyd * kyd;
+        const double f = alphaA / (sigma + alphaA * k2);
+        double r1x = to_f64(g1.x), r1y = to_f64(g1.y), r2x = to_f64(g2.x), r2y = to_f64(g2.y);
+        double krx = kxd * r1x + kyd * r2x, kry = kxd * r1y + kyd * r2y;
+        double z1x = (r1x - f * kxd * krx) / sigma, z1y = (r1y - f * kxd * kry) / sigma;
+        double z2x = (r2x - f * kyd * krx) / sigma, z2y = (r2y - f * kyd * kry) / sigma;
+        part += M.weight(col) * (r1x * z1x + r1y * z1y + r2x * z2x + r2y * z2y);
+      } else if (a.vdot[0]) {
+        cplx<T> p1 = ld_c<T>(a.vdot[0], gi), p2 = ld_c<T>(a.vdot[1], gi);
+        part += M.weight(col) *
+                to_f64(p1.x * g1.x + p1.y * g1.y + p2.x * g2.x + p2.y * g2.y);
+      }
+      st_c<T>(a.vout[0], gi, g1);
+      st_c<T>(a.vout[1], gi, g2);
+    }
+    if (a.residual) {
+      grid_reduce<kColNT>(part, a.parts, a.sc, [&](double s) { a.sc->rz64 = s; });
+    } else if (a.vdot[0]) {
+      grid_reduce<kColNT>(part, a.parts, a.sc, [&](double s) {
+        Scal2d* sc = a.sc;
+        if (!(s > 0.0) || !isfinite(s)) {
+          sc->status = SGN_ERR_BREAKDOWN;
+          sc->done = 1;
+        } else {
+          sc->alpha = sc->rz / s;
+        }
+      });
+    }
+  } else {
+    for (int e = threadIdx.x; e < TW * ny; e += kColNT) {
+      const int y = e / TW, c = e % TW, col = c0 + c;
+      if (col >= H) continue;
+      const long long gi = (long long)y * H + col;
+      for (int q = 0; q < nplanes; ++q) st_c<T>(a.planes[q], gi, buf[(q * TW + c) * stride + y]);
+    }
+  }
+}
+
+// =======================================================================================
+// Row passes.  Two rows per block (y0 = 2b, y1 = 2b + 1).
+// =======================================================================================
+
+// C2R of one packed pair: buf <- A + i B over the full row from two half rows, iFFT.
+template <typename T>
+__device__ __forceinline__ void load_c2r_pair(cplx<T>* z, const cplx<T>* A, const cplx<T>* B,
+                                              int nx, int NT) {
+  const int h = nx >> 1;
+  for (int m = threadIdx.x; m < nx; m += NT) {
+    cplx<T> a, b;
+    if (m <= h) {
+      a = A[m];
+      b = B[m];
+    } else {
+      a = conj(A[nx - m]);
+      b = conj(B[nx - m]);
+    }
+    // a + i b
+    z[m] = mk(a.x - b.y, a.y + b.x);
+  }
+}
+
+// R2C split of a packed FFT row Y = FFT(a + i b): A[m] = (Y_m + conj Y_{n-m})/2,
+// B[m] = (Y_m - conj Y_{n-m})/(2i), m = 0..nx/2.
+template <typename T>
+__device__ __forceinline__ void split_r2c_pair(const cplx<T>* Y, cplx<T>* A, cplx<T>* B, int nx,
+                                               int NT) {
+  const int h = nx >> 1;
+  for (int m = threadIdx.x; m <= h; m += NT) {
+    cplx<T> y = Y[m], yc = conj(Y[(nx - m) & (nx - 1)]);
+    cplx<T> s = y + yc, d = mul_mi(y - yc);
+    A[m] = mk(half(s.x), half(s.y));
+    B[m] = mk(half(d.x), half(d.y));
+  }
+}
+
+// coefficient planes: c11 = eta(1+hx^2), c12 = eta hx hy, c22 = eta(1+hy^2),
+// c13 = eta^2 hx/2, c23 = eta^2 hy/2, c33 = eta^3/3 (Def:MatrixM); hi in float, the
+// double-float remainder in lo.
+template <typename T>
+__device__ __forceinline__ void coef6(const float* hi, const float* lo, long long P, long long j,
+                                      T c[6]);
+template <>
+__device__ __forceinline__ void coef6<float>(const float* hi, const float* lo, long long P,
+                                             long long j, float c[6]) {
+#pragma unroll
+  for (int q = 0; q < 6; ++q) c[q] = hi[q * P + j];
+}
+template <>
+__device__ __forceinline__ void coef6<df>(const float* hi, const float* lo, long long P,
+                                          long long j, df c[6]) {
+#pragma unroll
+  for (int q = 0; q < 6; ++q) c[q] = df(hi[q * P + j], lo[q * P + j]);
+}
+template <>
+__device__ __forceinline__ void coef6<double>(const float* hi, const float* lo, long long P,
+                                              long long j, double c[6]) {
+#pragma unroll
+  for (int q = 0; q < 6; ++q) c[q] = (double)hi[q * P + j] + (double)lo[q * P + j];
+}
+
+// Matvec row kernel: planes t0, t1, t2 hold (after the column iFFT) the row half spectra of
+// p1, p2, d.  C2R -> pointwise w1, w2, q -> R2C back into t0, t1, t2.  Optionally writes
+// the real-space input (p1, p2) to xout (two planes of P doubles).
+template <typename T, int MAXB>
+__global__ void __launch_bounds__(kRowNT, 1) k2_rows_matvec(Modes2d M, int log2nx, long long P,
+                                                            const void* t64, const void* t32,
+                                                            void* t0, void* t1, void* t2,
+                                                            const float* chi, const float* clo,
+                                                            double* xout, Scal2d* sc,
+                                                            int check_done) {
+  if (check_done && ((volatile Scal2d*)sc)->done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nx = M.nx, H = M.H;
+  cplx<T>* z = reinterpret_cast<cplx<T>*>(smem);           // 3 rows of nx
+  const cplx<T>* tw = Tw<T>::get(t64, t32);
+  const int y0 = 2 * blockIdx.x, y1 = y0 + 1;
+  cplx<T>* T0 = reinterpret_cast<cplx<T>*>(t0);
+  cplx<T>* T1 = reinterpret_cast<cplx<T>*>(t1);
+  cplx<T>* T2 = reinterpret_cast<cplx<T>*>(t2);
+  load_c2r_pair<T>(z, T0 + (long long)y0 * H, T1 + (long long)y0 * H, nx, kRowNT);
+  load_c2r_pair<T>(z + nx, T0 + (long long)y1 * H, T1 + (long long)y1 * H, nx, kRowNT);
+  load_c2r_pair<T>(z + 2 * nx, T2 + (long long)y0 * H, T2 + (long long)y1 * H, nx, kRowNT);
+  __syncthreads();
+  cta_fft_batch<T, kRowNT, MAXB>(z, nx, log2nx, 3, nx, true, tw);
+  const T inv = num<T>(1.0 / ((double)nx * (double)M.ny));
+  for (int x = threadIdx.x; x < nx; x += kRowNT) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int y = r ? y1 : y0;
+      const long long j = (long long)y * nx + x;
+      cplx<T> pp = z[r * nx + x];
+      T p1 = pp.x * inv, p2 = pp.y * inv;
+      T d = (r ? z[2 * nx + x].y : z[2 * nx + x].x) * inv;
+      if (xout) {
+        xout[j] = to_f64(p1);
+        xout[P + j] = to_f64(p2);
+      }
+      T c[6];
+      coef6<T>(chi, clo, P, j, c);
+      T w1 = c[0] * p1 + c[1] * p2 + c[3] * d;
+      T w2 = c[1] * p1 + c[2] * p2 + c[4] * d;
+      T q = c[3] * p1 + c[4] * p2 + c[5] * d;
+      z[r * nx + x] = mk(w1, w2);
+      if (r) z[2 * nx + x].y = q; else z[2 * nx + x].x = q;
+    }
+  }
+  __syncthreads();
+  cta_fft_batch<T, kRowNT, MAXB>(z, nx, log2nx, 3, nx, false, tw);
+  // split back into half rows: (w1, w2) of y0, (w1, w2) of y1, (q y0, q y1); the row FFT
+  // results are read only here, so the splits may write the half planes directly.
+  split_r2c_pair<T>(z, T0 + (long long)y0 * H, T1 + (long long)y0 * H, nx, kRowNT);
+  split_r2c_pair<T>(z + nx, T0 + (long long)y1 * H, T1 + (long long)y1 * H, nx, kRowNT);
+  split_r2c_pair<T>(z + 2 * nx, T2 + (long long)y0 * H, T2 + (long long)y1 * H, nx, kRowNT);
+}
+
+// R2C row pass of K/2 packed pairs of real planes (double storage): pair q packs
+// (src[2q], src[2q+1]); half rows go to dst[2q], dst[2q+1].  `scale` multiplies the input.
+template <typename T, int MAXB>
+__global__ void __launch_bounds__(kRowNT, 1) k2_rows_r2c(Modes2d M, int log2nx, long long P,
+                                                         const void* t64, const void* t32,
+                                                         const double* s0, const double* s1,
+                                                         const double* s2, const double* s3,
+                                                         void* d0, void* d1, void* d2, void* d3,
+                                                         int npairs) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nx = M.nx, H = M.H;
+  cplx<T>* z = reinterpret_cast<cplx<T>*>(smem);
+  const cplx<T>* tw = Tw<T>::get(t64, t32);
+  const int y = blockIdx.x;
+  const double* src[4] = {s0, s1, s2, s3};
+  void* dst[4] = {d0, d1, d2, d3};
+  for (int q = 0; q < npairs; ++q)
+    for (int x = threadIdx.x; x < nx; x += kRowNT) {
+      const long long j = (long long)y * nx + x;
+      const double a = src[2 * q] ? src[2 * q][j] : 0.0, b = src[2 * q + 1] ? src[2 * q + 1][j] : 0.0;
+      z[q * nx + x] = mk(num<T>(a), num<T>(b));
+    }
+  __syncthreads();
+  cta_fft_batch<T, kRowNT, MAXB>(z, nx, log2nx, npairs, nx, false, tw);
+  for (int q = 0; q < npairs; ++q)
+    split_r2c_pair<T>(z + q * nx, reinterpret_cast<cplx<T>*>(dst[2 * q]) + (long long)y * H,
+                      reinterpret_cast<cplx<T>*>(dst[2 * q + 1]) + (long long)y * H, nx, kRowNT);
+}
+
+// C2R row pass: pair q of half planes (src[2q], src[2q+1]) -> real planes dst[2q],
+// dst[2q+1] (double storage), scaled by 1/(nx ny).
+template <typename T, int MAXB>
+__global__ void __launch_bounds__(kRowNT, 1) k2_rows_c2r(Modes2d M, int log2nx, long long P,
+                                                         const void* t64, const void* t32,
+                                                         const void* s0, const void* s1,
+                                                         const void* s2, const void* s3,
+                                                         double* d0, double* d1, double* d2,
+                                                         double* d3, int npairs) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nx = M.nx, H = M.H;
+  cplx<T>* z = reinterpret_cast<cplx<T>*>(smem);
+  const cplx<T>* tw = Tw<T>::get(t64, t32);
+  const int y = blockIdx.x;
+  const void* src[4] = {s0, s1, s2, s3};
+  double* dst[4] = {d0, d1, d2, d3};
+  for (int q = 0; q < npairs; ++q)
+    load_c2r_pair<T>(z + q * nx, reinterpret_cast<const cplx<T>*>(src[2 * q]) + (long long)y * H,
+                     reinterpret_cast<const cplx<T>*>(src[2 * q + 1]) + (long long)y * H, nx,
+                     kRowNT);
+  __syncthreads();
+  cta_fft_batch<T, kRowNT, MAXB>(z, nx, log2nx, npairs, nx, true, tw);
+  const T inv = num<T>(1.0 / ((double)nx * (double)M.ny));
+  for (int q = 0; q < npairs; ++q)
+    for (int x = threadIdx.x; x < nx; x += kRowNT) {
+      const long long j = (long long)y * nx + x;
+      cplx<T> v = z[q * nx + x];
+      if (dst[2 * q]) dst[2 * q][j] = to_f64(v.x * inv);
+      if (dst[2 * q + 1]) dst[2 * q + 1][j] = to_f64(v.y * inv);
+    }
+}
+
+// =======================================================================================
+// Per-mode kernels over half spectra
+// =======================================================================================
+
+// Spectral ops for derivatives and A^{-1}:
+//   OP_GRAD: out0 = i kx in0, out1 = i ky in0 (and out2, out3 from in1)
+//   OP_AINV: (out0, out1) = A^{-1} (in0, in1)
+//   OP_DIV : out0 = i kx in0 + i ky in1
+enum SpecOp { OP_GRAD = 0, OP_AINV = 1 };
+
+template <typename T, int OP>
+__global__ void k2_spec(Modes2d M, const void* in0, const void* in1, void* out0, void* out1,
+                        void* out2, void* out3, const Scal2d* sc, const SolveRec* A) {
+  const long long HP = (long long)M.ny * M.H;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HP;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(i / M.H), c = (int)(i % M.H);
+    const double kx = M.kx(c), ky = M.ky(y);
+    if constexpr (OP == OP_GRAD) {
+      cplx<T> a = ld_c<T>(in0, i);
+      st_c<T>(out0, i, mul_ik(a, num<T>(kx)));
+      st_c<T>(out1, i, mul_ik(a, num<T>(ky)));
+      if (in1) {
+        cplx<T> b = ld_c<T>(in1, i);
+        st_c<T>(out2, i, mul_ik(b, num<T>(kx)));
+        st_c<T>(out3, i, mul_ik(b, num<T>(ky)));
+      }
+    } else {
+      const double sigma = A ? A->sigma : sc->sigma, alpha = A ? A->alpha : sc->alpha_A;
+      const double f = alpha / (sigma + alpha * (kx * kx + ky * ky));
+      const T kxT = num<T>(kx), kyT = num<T>(ky), fT = num<T>(f), is = num<T>(1.0 / sigma);
+      cplx<T> r1 = ld_c<T>(in0, i), r2 = ld_c<T>(in1, i);
+      cplx<T> kr = r1 * kxT + r2 * kyT;
+      st_c<T>(out0, i, (r1 - kr * (fT * kxT)) * is);
+      st_c<T>(out1, i, (r2 - kr * (fT * kyT)) * is);
+    }
+  }
+}
+
+// Inner PCG update: x += alpha p; r -= alpha g; rz = r.A^{-1}r; last block forms beta and
+// the stopping decision.
+template <typename T>
+__global__ void __launch_bounds__(256) k2_update(Modes2d M, void* x1, void* x2, void* r1p,
+                                                 void* r2p, const void* p1p, const void* p2p,
+                                                 const void* g1p, const void* g2p, Scal2d* sc,
+                                                 double* parts) {
+  if (((volatile Scal2d*)sc)->done) return;
+  const long long HP = (long long)M.ny * M.H;
+  const double sigma = sc->sigma, alphaA = sc->alpha_A;
+  const T a = num<T>(sc->alpha);
+  double part = 0.0;
+  for (long long i = blockIdx.x * 256ll + threadIdx.x; i < HP; i += (long long)gridDim.x * 256) {
+    const int y = (int)(i / M.H), c = (int)(i % M.H);
+    const double kx = M.kx(c), ky = M.ky(y);
+    cplx<T> p1 = ld_c<T>(p1p, i), p2 = ld_c<T>(p2p, i);
+    st_c<T>(x1, i, ld_c<T>(x1, i) + p1 * a);
+    st_c<T>(x2, i, ld_c<T>(x2, i) + p2 * a);
+    cplx<T> r1 = ld_c<T>(r1p, i) - ld_c<T>(g1p, i) * a;
+    cplx<T> r2 = ld_c<T>(r2p, i) - ld_c<T>(g2p, i) * a;
+    st_c<T>(r1p, i, r1);
+    st_c<T>(r2p, i, r2);
+    const double f = alphaA / (sigma + alphaA * (kx * kx + ky * ky));
+    const T kxT = num<T>(kx), kyT = num<T>(ky), fT = num<T>(f), is = num<T>(1.0 / sigma);
+    cplx<T> kr = r1 * kxT + r2 * kyT;
+    cplx<T> z1 = (r1 - kr * (fT * kxT)) * is, z2 = (r2 - kr * (fT * kyT)) * is;
+    part += M.weight(c) * to_f64(r1.x * z1.x + r1.y * z1.y + r2.x * z2.x + r2.y * z2.y);
+  }
+  grid_reduce<256>(part, parts, sc, [&](double rz_new) {
+    sc->iters += 1;
+    if (!isfinite(rz_new)) {
+      sc->status = SGN_ERR_BREAKDOWN;
+      sc->done = 1;
+      return;
+    }
+    sc->beta = rz_new / sc->rz;
+    sc->rz = rz_new;
+    if (sqrt(rz_new) <= sc->tol) {
+      sc->done = 1;
+    } else if (sc->iters >= sc->cap) {
+      sc->status = SGN_ERR_NOT_CONVERGED;
+      sc->done = 1;
+    }
+  });
+}
+
+// Start of an inner solve: r = scale * src (high -> T), x = 0, p = 0, beta = 0,
+// rz = r.A^{-1}r (last block), done if already below tol.
+template <typename TH, typename T>
+__global__ void __launch_bounds__(256) k2_inner_start(Modes2d M, const void* s1, const void* s2,
+                                                      double scale, void* r1p, void* r2p,
+                                                      void* x1, void* x2, void* p1, void* p2,
+                                                      Scal2d* sc, double* parts) {
+  const long long HP = (long long)M.ny * M.H;
+  const double sigma = sc->sigma, alphaA = sc->alpha_A;
+  double part = 0.0;
+  const cplx<T> zero = mk(from_int<T>(0), from_int<T>(0));
+  for (long long i = blockIdx.x * 256ll + threadIdx.x; i < HP; i += (long long)gridDim.x * 256) {
+    const int y = (int)(i / M.H), c = (int)(i % M.H);
+    const double kx = M.kx(c), ky = M.ky(y);
+    cplx<TH> a = ld_c<TH>(s1, i), b = ld_c<TH>(s2, i);
+    cplx<T> r1 = mk(num<T>(to_f64(a.x) * scale), num<T>(to_f64(a.y) * scale));
+    cplx<T> r2 = mk(num<T>(to_f64(b.x) * scale), num<T>(to_f64(b.y) * scale));
+    st_c<T>(r1p, i, r1);
+    st_c<T>(r2p, i, r2);
+    st_c<T>(x1, i, zero);
+    st_c<T>(x2, i, zero);
+    st_c<T>(p1, i, zero);
+    st_c<T>(p2, i, zero);
+    const double f = alphaA / (sigma + alphaA * (kx * kx + ky * ky));
+    double r1x = to_f64(r1.x), r1y = to_f64(r1.y), r2x = to_f64(r2.x), r2y = to_f64(r2.y);
+    double krx = kx * r1x + ky * r2x, kry = kx * r1y + ky * r2y;
+    part += M.weight(c) * ((r1x * (r1x - f * kx * krx) + r1y * (r1y - f * kx * kry) +
+                            r2x * (r2x - f * ky * krx) + r2y * (r2y - f * ky * kry)) / sigma);
+  }
+  grid_reduce<256>(part, parts, sc, [&](double rz) {
+    sc->rz = rz;
+    sc->beta = 0.0;
+    sc->done = (sqrt(rz) <= sc->tol) ? 1 : 0;
+  });
+}
+
+// x_high += scale * d (T -> high precision)
+template <typename TH, typename T>
+__global__ void k2_accumulate(Modes2d M, void* x1, void* x2, const void* d1, const void* d2,
+                              double scale) {
+  const long long HP = (long long)M.ny * M.H;
+  const TH s = num<TH>(scale);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HP;
+       i += (long long)gridDim.x * blockDim.x) {
+    cplx<T> a = ld_c<T>(d1, i), b = ld_c<T>(d2, i);
+    cplx<TH> u = ld_c<TH>(x1, i), v = ld_c<TH>(x2, i);
+    st_c<TH>(x1, i, mk(u.x + num<TH>(to_f64(a.x)) * s, u.y + num<TH>(to_f64(a.y)) * s));
+    st_c<TH>(x2, i, mk(v.x + num<TH>(to_f64(b.x)) * s, v.y + num<TH>(to_f64(b.y)) * s));
+  }
+}
+
+// b.A^{-1}b for a vector of two half planes (high precision) -> sc->bb
+template <typename TH>
+__global__ void __launch_bounds__(256) k2_bnorm(Modes2d M, const void* b1, const void* b2,
+                                                Scal2d* sc, double* parts) {
+  const long long HP = (long long)M.ny * M.H;
+  const double sigma = sc->sigma, alphaA = sc->alpha_A;
+  double part = 0.0;
+  for (long long i = blockIdx.x * 256ll + threadIdx.x; i < HP; i += (long long)gridDim.x * 256) {
+    const int y = (int)(i / M.H), c = (int)(i % M.H);
+    const double kx = M.kx(c), ky = M.ky(y);
+    cplx<TH> a = ld_c<TH>(b1, i), b = ld_c<TH>(b2, i);
+    const double f = alphaA / (sigma + alphaA * (kx * kx + ky * ky));
+    double r1x = to_f64(a.x), r1y = to_f64(a.y), r2x = to_f64(b.x), r2y = to_f64(b.y);
+    double krx = kx * r1x + ky * r2x, kry = kx * r1y + ky * r2y;
+    part += M.weight(c) * ((r1x * (r1x - f * kx * krx) + r1y * (r1y - f * kx * kry) +
+                            r2x * (r2x - f * ky * krx) + r2y * (r2y - f * ky * kry)) / sigma);
+  }
+  grid_reduce<256>(part, parts, sc, [&](double s) { sc->bb = s; });
+}
+
+// coefficient planes (Def:MatrixM) from eta, grad h
+__global__ void k2_coef_planes(long long P, const double* eta, const double* gh, float* hi,
+                               float* lo) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < P;
+       j += (long long)gridDim.x * blockDim.x) {
+    const double e = eta[j], hx = gh[j], hy = gh[P + j];
+    const double c[6] = {e * (1.0 + hx * hx), e * hx * hy, e * (1.0 + hy * hy), 0.5 * e * e * hx,
+                         0.5 * e * e * hy, e * e * e / 3.0};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const float h = (float)c[q];
+      hi[q * P + j] = h;
+      lo[q * P + j] = (float)(c[q] - (double)h);
+    }
+  }
+}
+
+// a1 in 2d: block reductions of eta_min, eta_max, max |grad h|^2, max eta(1 + l+ |grad h|^2)
+__global__ void __launch_bounds__(256) k2_coeffs(long long P, const double* eta, const double* gh,
+                                                 int kind, double* parts, Scal2d* sc,
+                                                 SolveRec* rec) {
+  __shared__ double red[256 / 32 + 1];
+  double emin = 1e308, emax = -1e308, g2max = 0.0, sopt = -1e308, bad = 0.0;
+  for (long long j = blockIdx.x * 256ll + threadIdx.x; j < P; j += (long long)gridDim.x * 256) {
+    const double e = eta[j], hx = gh[j], hy = gh[P + j], g2 = hx * hx + hy * hy;
+    if (!(e > 0.0) || !(g2 < 1e300)) bad = 1.0;
+    emin = fmin(emin, e);
+    emax = fmax(emax, e);
+    g2max = fmax(g2max, g2);
+    sopt = fmax(sopt, e + kLambdaPlus * e * g2);
+  }
+  emin = block_min<256>(emin, red);
+  emax = block_max<256>(emax, red);
+  g2max = block_max<256>(g2max, red);
+  sopt = block_max<256>(sopt, red);
+  bad = block_max<256>(bad, red);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    double* p = parts + 5 * blockIdx.x;
+    p[0] = emin;
+    p[1] = emax;
+    p[2] = g2max;
+    p[3] = sopt;
+    p[4] = bad;
+    __threadfence();
+    last = atomicAdd(&sc->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    sc->ticket = 0;
+    volatile double* vp = parts;
+    double a = 1e308, b = -1e308, g = 0.0, s = -1e308, bd = 0.0;
+    for (int i = 0; i < (int)gridDim.x; ++i) {
+      a = fmin(a, vp[5 * i]);
+      b = fmax(b, vp[5 * i + 1]);
+      g = fmax(g, vp[5 * i + 2]);
+      s = fmax(s, vp[5 * i + 3]);
+      bd = fmax(bd, vp[5 * i + 4]);
+    }
+    SolveRec R = {};
+    R.eta_min = a;
+    R.eta_max = b;
+    if (bd > 0.0) {
+      R.status = SGN_ERR_NONPOSITIVE_DEPTH;
+    } else {
+      const double ratio3 = (b / a) * (b / a) * (b / a);
+      R.flat = sqrt(g) <= kFlatSlope;
+      if (R.flat) {
+        R.sigma = b;
+        R.alpha = b * b * b / 3.0;
+        R.kappa_ub = ratio3;
+      } else if (kind == SGN_COEF_OPT) {
+        R.sigma = s;
+        R.alpha = kLambdaPlus * b * b * b;
+        R.kappa_ub = fmax(s / a, (kLambdaPlus / kLambdaMinus) * ratio3);
+      } else {
+        R.sigma = b * (1.0 + kLambdaPlus * g);
+        R.alpha = kLambdaPlus * b * b * b;
+        R.kappa_ub = fmax((b / a) * (1.0 + kLambdaPlus * g), (kLambdaPlus / kLambdaMinus) * ratio3);
+      }
+      R.status = SGN_OK;
+    }
+    if (rec) *rec = R;
+    sc->sigma = R.sigma;
+    sc->alpha_A = R.alpha;
+    sc->kappa_ub = R.kappa_ub;
+    sc->eta_min = R.eta_min;
+    sc->eta_max = R.eta_max;
+    sc->flat = R.flat;
+    sc->status = R.status;
+    __threadfence();
+  }
+}
+
+__global__ void k2_set_given(Scal2d* sc, const SolveRec* g) {
+  sc->sigma = g->sigma;
+  sc->alpha_A = g->alpha;
+  sc->kappa_ub = g->kappa_ub;
+  sc->flat = g->flat;
+  sc->status = SGN_OK;
+}
+
+__global__ void k2_report(const Scal2d* sc, SolveRec* rec, int refinements) {
+  SolveRec R = {};
+  R.sigma = sc->sigma;
+  R.alpha = sc->alpha_A;
+  R.kappa_ub = sc->kappa_ub;
+  R.eta_min = sc->eta_min;
+  R.eta_max = sc->eta_max;
+  R.flat = sc->flat;
+  R.iters = sc->iters;
+  R.refinements = refinements;
+  R.ratio = sc->bb > 0.0 ? sqrt(fmax(sc->rz64, 0.0) / sc->bb) : 0.0;
+  R.status = sc->status;
+  *rec = R;
+}
+
+__global__ void k2_lincomb(long long n, double* out, const double* x0, const double* x1,
+                           const double* x2, const double* x3, double a0, double a1, double a2,
+                           double a3, int nx, const double* f0, const double* f1, const double* f2,
+                           const double* f3, double c0, double c1, double c2, double c3, int nf,
+                           const double* dt) {
+  const double d = dt[0];
+  const double* X[4] = {x0, x1, x2, x3};
+  const double A[4] = {a0, a1, a2, a3};
+  const double* F[4] = {f0, f1, f2, f3};
+  const double Cc[4] = {c0, c1, c2, c3};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0, accf = 0.0;
+    for (int t = 0; t < nx; ++t) acc += A[t] * X[t][i];
+    for (int t = 0; t < nf; ++t) accf += Cc[t] * F[t][i];
+    out[i] = acc + d * accf;
+  }
+}
+
+// RHS pointwise stages (T arithmetic, double storage), see launch_rhs2d.
+template <typename T>
+__global__ void k2_rhs_stage(int stage, long long P, double g, const double* eta, const double* u,
+                             const double* hgt, const double* gh, double* w, double* f_eta,
+                             double* f_U) {
+  // w: scratch planes [0..]; see launch_rhs2d for the meaning of each index
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < P;
+       j += (long long)gridDim.x * blockDim.x) {
+    const T e = num<T>(eta[j]), uu = num<T>(u[j]), vv = num<T>(u[P + j]);
+    const T hx = num<T>(gh[j]), hy = num<T>(gh[P + j]);
+    if (stage == 0) {
+      // inputs for the first derivative passes
+      w[0 * P + j] = to_f64(e * uu);                       // eta u
+      w[1 * P + j] = to_f64(e * vv);                       // eta v
+      w[2 * P + j] = eta[j] - hgt[j];                      // zeta
+      w[3 * P + j] = to_f64(hx * uu + hy * vv);            // s
+      w[4 * P + j] = to_f64(e * uu * uu);                  // eta u u
+      w[5 * P + j] = to_f64(e * uu * vv);                  // eta u v
+      w[6 * P + j] = to_f64(e * vv * vv);                  // eta v v
+    } else if (stage == 1) {
+      // derivatives available: 10 u_x, 11 u_y, 12 v_x, 13 v_y, 14 (eta u)_x, 15 (eta u)_y,
+      // 16 (eta v)_x, 17 (eta v)_y; d = u_x + v_y -> plane 7
+      w[7 * P + j] = w[10 * P + j] + w[13 * P + j];
+    } else {
+      // 18 zeta_x, 19 zeta_y, 20 s_x, 21 s_y, 22 d_x, 23 d_y, 24 (euu)_x, 25 (euu)_y,
+      // 26 (euv)_x, 27 (euv)_y, 28 (evv)_x, 29 (evv)_y; Phi -> 8, Psi -> 9
+      const T d = num<T>(w[7 * P + j]);
+      const T m = num<T>(w[14 * P + j]) + num<T>(w[17 * P + j]);
+      const T s = hx * uu + hy * vv;
+      const T Sv = uu * num<T>(w[20 * P + j]) + vv * num<T>(w[21 * P + j]);
+      const T Q = uu * num<T>(w[22 * P + j]) + vv * num<T>(w[23 * P + j]) - d * d;
+      const T e2 = e * e, md = m * d;
+      if (stage == 2) {
+        w[8 * P + j] = to_f64(e2 * e * Q * num<T>(1.0 / 3.0) + e2 * md + half(e2 * Sv) + e * m * s);
+        w[9 * P + j] = to_f64(half(e2 * Q) + e * md + e * Sv + m * s);
+      } else {
+        // stage 3: Phi_x -> 30, Phi_y -> 31
+        const T Psi = num<T>(w[9 * P + j]);
+        const T gT = num<T>(g);
+        f_eta[j] = -to_f64(m);
+        const T fx = num<T>(w[30 * P + j]) - gT * e * num<T>(w[18 * P + j]) -
+                     num<T>(w[24 * P + j]) - num<T>(w[27 * P + j]) - hx * Psi;
+        const T fy = num<T>(w[31 * P + j]) - gT * e * num<T>(w[19 * P + j]) -
+                     num<T>(w[26 * P + j]) - num<T>(w[29 * P + j]) - hy * Psi;
+        f_U[j] = to_f64(fx);
+        f_U[P + j] = to_f64(fy);
+      }
+    }
+  }
+}
+
+// SBDF2 residual in spectral form: res = A u - G u + U with A u = sigma u + alpha k (k.u)
+template <typename T>
+__global__ void k2_linimp_combine(Modes2d M, const SolveRec* A, const void* u1, const void* u2,
+                                  const void* g1, const void* g2, const void* U1, const void* U2,
+                                  void* o1, void* o2) {
+  const long long HP = (long long)M.ny * M.H;
+  const double sigma = A->sigma, alpha = A->alpha;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HP;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(i / M.H), c = (int)(i % M.H);
+    const T kx = num<T>(M.kx(c)), ky = num<T>(M.ky(y));
+    cplx<T> a = ld_c<T>(u1, i), b = ld_c<T>(u2, i);
+    cplx<T> ku = a * kx + b * ky;
+    const T s = num<T>(sigma), al = num<T>(alpha);
+    st_c<T>(o1, i, a * s + ku * (al * kx) - ld_c<T>(g1, i) + ld_c<T>(U1, i));
+    st_c<T>(o2, i, b * s + ku * (al * ky) - ld_c<T>(g2, i) + ld_c<T>(U2, i));
+  }
+}
+
+template <typename T>
+__global__ void k2_axpby(long long HP, void* o1, void* o2, const void* a1, const void* a2,
+                         const void* b1, const void* b2, double ca, double cb) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HP;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T A = num<T>(ca), B = num<T>(cb);
+    st_c<T>(o1, i, ld_c<T>(a1, i) * A + ld_c<T>(b1, i) * B);
+    st_c<T>(o2, i, ld_c<T>(a2, i) * A + ld_c<T>(b2, i) * B);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Host-side helpers
+// ---------------------------------------------------------------------------------------
+
+template <typename K>
+cudaError_t smem_attr(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T>
+constexpr int col_tw() { return sizeof(T) == 8 ? 4 : 2; }     // 32-byte row segments
+
+template <typename T>
+size_t col_smem(const Layout2d& L, int K) {
+  return (size_t)K * col_tw<T>() * (L.ny + 1) * sizeof(cplx<T>);
+}
+
+template <typename T>
+size_t row_smem(const Layout2d& L, int nrows) {
+  return (size_t)nrows * L.nx * sizeof(cplx<T>);
+}
+
+// column pass launcher: MAXB from ny (TW columns x ny/4 butterflies over 512 threads)
+template <typename T, int MODE>
+cudaError_t cols(const Layout2d& L, const void* t64, const void* t32, const ColArgs& a,
+                 cudaStream_t s) {
+  constexpr int TW = col_tw<T>();
+  const Modes2d M = modes_of(L);
+  const int tiles = (M.H + TW - 1) / TW;
+  const int K = (MODE == COL_MATVEC_IN || MODE == COL_MATVEC_OUT) ? 3 : a.K;
+  const size_t sm = col_smem<T>(L, K);
+  // TW * ny / 4 butterflies per radix-4 stage; MAXB = ceil(that / 512)
+  const int need = (TW * L.ny / 4 + kColNT - 1) / kColNT;
+  cudaError_t e;
+  if (need <= 1) {
+    auto k = k2_cols<T, TW, 1, MODE>;
+    if ((e = smem_attr(k, sm))) return e;
+    k<<<tiles, kColNT, sm, s>>>(M, L.ly, t64, t32, a);
+  } else if (need <= 2) {
+    auto k = k2_cols<T, TW, 2, MODE>;
+    if ((e = smem_attr(k, sm))) return e;
+    k<<<tiles, kColNT, sm, s>>>(M, L.ly, t64, t32, a);
+  } else {
+    auto k = k2_cols<T, TW, 4, MODE>;
+    if ((e = smem_attr(k, sm))) return e;
+    k<<<tiles, kColNT, sm, s>>>(M, L.ly, t64, t32, a);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t rows_matvec(const Layout2d& L, const void* t64, const void* t32, void* t0, void* t1,
+                        void* t2, double* xout, Scal2d* sc, int check_done, cudaStream_t s) {
+  const Modes2d M = modes_of(L);
+  const size_t sm = row_smem<T>(L, 3);
+  const int need = (3 * L.nx / 4 + kRowNT - 1) / kRowNT;   // butterflies per thread
+  cudaError_t e;
+#define SGN_ROWS_MV(MB)                                                                     \
+  {                                                                                        \
+    auto k = k2_rows_matvec<T, MB>;                                                        \
+    if ((e = smem_attr(k, sm))) return e;                                                  \
+    k<<<L.ny / 2, kRowNT, sm, s>>>(M, L.lx, L.P, t64, t32, t0, t1, t2, L.coef,              \
+                                   L.coef_lo, xout, sc, check_done);                       \
+  }
+  if (need <= 1) SGN_ROWS_MV(1) else if (need <= 2) SGN_ROWS_MV(2) else if (need <= 3) SGN_ROWS_MV(3)
+  else SGN_ROWS_MV(4)
+#undef SGN_ROWS_MV
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t rows_r2c(const Layout2d& L, const void* t64, const void* t32, const double* s0,
+                     const double* s1, const double* s2, const double* s3, void* d0, void* d1,
+                     void* d2, void* d3, int npairs, cudaStream_t s) {
+  const Modes2d M = modes_of(L);
+  const size_t sm = row_smem<T>(L, npairs);
+  const int need = (npairs * L.nx / 4 + kRowNT - 1) / kRowNT;
+  cudaError_t e;
+#define SGN_ROWS_F(MB)                                                                       \
+  {                                                                                         \
+    auto k = k2_rows_r2c<T, MB>;                                                            \
+    if ((e = smem_attr(k, sm))) return e;                                                   \
+    k<<<L.ny, kRowNT, sm, s>>>(M, L.lx, L.P, t64, t32, s0, s1, s2, s3, d0, d1, d2, d3, npairs); \
+  }
+  if (need <= 1) SGN_ROWS_F(1) else if (need <= 2) SGN_ROWS_F(2) else SGN_ROWS_F(4)
+#undef SGN_ROWS_F
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t rows_c2r(const Layout2d& L, const void* t64, const void* t32, const void* s0,
+                     const void* s1, const void* s2, const void* s3, double* d0, double* d1,
+                     double* d2, double* d3, int npairs, cudaStream_t s) {
+  const Modes2d M = modes_of(L);
+  const size_t sm = row_smem<T>(L, npairs);
+  const int need = (npairs * L.nx / 4 + kRowNT - 1) / kRowNT;
+  cudaError_t e;
+#define SGN_ROWS_I(MB)                                                                       \
+  {                                                                                         \
+    auto k = k2_rows_c2r<T, MB>;                                                            \
+    if ((e = smem_attr(k, sm))) return e;                                                   \
+    k<<<L.ny, kRowNT, sm, s>>>(M, L.lx, L.P, t64, t32, s0, s1, s2, s3, d0, d1, d2, d3, npairs); \
+  }
+  if (need <= 1) SGN_ROWS_I(1) else if (need <= 2) SGN_ROWS_I(2) else SGN_ROWS_I(4)
+#undef SGN_ROWS_I
+  return cudaGetLastError();
+}
+
+// half-plane slot q of the workspace (16 bytes per element)
+inline void* slot(const Layout2d& L, int q) {
+  return static_cast<char*>(L.vec) + (size_t)q * L.HP * 16;
+}
+inline void* tplane(const Layout2d& L, int q) {
+  return static_cast<char*>(L.tp) + (size_t)q * L.HP * 16;
+}
+
+int grid_for(long long n, int nt) {
+  long long b = (n + nt - 1) / nt;
+  if (b > kMaxParts) b = kMaxParts;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// Forward transform of a real vector field (2 planes of P doubles) into 2 half planes.
+template <typename T>
+cudaError_t r2c_vec(const Layout2d& L, const void* t64, const void* t32, const double* v,
+                    void* o1, void* o2, cudaStream_t s) {
+  cudaError_t e = rows_r2c<T>(L, t64, t32, v, v + L.P, nullptr, nullptr, o1, o2, nullptr, nullptr,
+                              1, s);
+  if (e) return e;
+  ColArgs a{};
+  a.planes[0] = o1;
+  a.planes[1] = o2;
+  a.K = 2;
+  return cols<T, COL_FWD>(L, t64, t32, a, s);
+}
+
+// Inverse transform of 2 half planes into a real vector field (the half planes are
+// transformed in place along y first).
+template <typename T>
+cudaError_t c2r_vec(const Layout2d& L, const void* t64, const void* t32, void* i1, void* i2,
+                    double* v, cudaStream_t s) {
+  ColArgs a{};
+  a.planes[0] = i1;
+  a.planes[1] = i2;
+  a.K = 2;
+  cudaError_t e = cols<T, COL_INV>(L, t64, t32, a, s);
+  if (e) return e;
+  return rows_c2r<T>(L, t64, t32, i1, i2, nullptr, nullptr, v, v + L.P, nullptr, nullptr, 1, s);
+}
+
+// One spectral matvec: (g1, g2) = G (v1, v2) (or b - G v when residual) in precision T.
+// Uses the 3 transform planes.  xout (nullable): real-space v on the way.
+template <typename T>
+cudaError_t matvec(const Layout2d& L, const void* t64, const void* t32, const void* v1,
+                   const void* v2, void* g1, void* g2, const void* dot1, const void* dot2,
+                   const void* b1, const void* b2, int residual, double* xout, Scal2d* sc,
+                   int check_done, int pupdate, void* p1, void* p2, const void* r1,
+                   const void* r2, cudaStream_t s) {
+  ColArgs a{};
+  a.planes[0] = tplane(L, 0);
+  a.planes[1] = tplane(L, 1);
+  a.planes[2] = tplane(L, 2);
+  a.K = 3;
+  a.vin[0] = v1;
+  a.vin[1] = v2;
+  a.sc = sc;
+  a.parts = L.parts;
+  a.check_done = check_done;
+  a.pupdate = pupdate;
+  a.pio[0] = p1;
+  a.pio[1] = p2;
+  a.rin[0] = r1;
+  a.rin[1] = r2;
+  // the column kernel writes its results into the transform planes
+  ColArgs ain = a;
+  cudaError_t e = cols<T, COL_MATVEC_IN>(L, t64, t32, ain, s);
+  if (e) return e;
+  if ((e = rows_matvec<T>(L, t64, t32, tplane(L, 0), tplane(L, 1), tplane(L, 2), xout, sc,
+                          check_done, s)))
+    return e;
+  ColArgs aout = a;
+  aout.vout[0] = g1;
+  aout.vout[1] = g2;
+  aout.vdot[0] = dot1;
+  aout.vdot[1] = dot2;
+  aout.bvec[0] = b1;
+  aout.bvec[1] = b2;
+  aout.residual = residual;
+  return cols<T, COL_MATVEC_OUT>(L, t64, t32, aout, s);
+}
+
+}  // namespace
+
+// =======================================================================================
+// Layout
+// =======================================================================================
+
 cudaError_t layout2d_create(Layout2d& L, const sgn_grid& g) {
-  (void)L; (void)g;
-  return cudaErrorNotSupported;
+  L.nx = g.nx;
+  L.ny = g.ny;
+  L.Lx = g.Lx;
+  L.Ly = g.Ly;
+  L.lx = 0;
+  while ((1 << L.lx) < g.nx) ++L.lx;
+  L.ly = 0;
+  while ((1 << L.ly) < g.ny) ++L.ly;
+  L.P = (long long)g.nx * g.ny;
+  L.H = g.nx / 2 + 1;
+  L.HP = (long long)g.ny * L.H;
+  cudaError_t e;
+  if ((e = cudaMalloc(&L.vec, (size_t)16 * L.HP * 14))) return e;
+  if ((e = cudaMalloc(&L.tp, (size_t)16 * L.HP * 4))) return e;
+  if ((e = cudaMalloc(&L.coef, sizeof(float) * 6 * L.P))) return e;
+  if ((e = cudaMalloc(&L.coef_lo, sizeof(float) * 6 * L.P))) return e;
+  if ((e = cudaMalloc(&L.parts, sizeof(double) * 5 * kMaxParts))) return e;
+  if ((e = cudaMalloc(&L.sc, sizeof(Scal2d)))) return e;
+  if ((e = cudaMalloc(&L.rhs_w, sizeof(double) * 32 * L.P))) return e;
+  if ((e = cudaMemset(L.sc, 0, sizeof(Scal2d)))) return e;
+  return cudaSuccess;
 }
-void layout2d_destroy(Layout2d& L) { cudaFree(L.work); L.work = nullptr; }
-size_t layout2d_res_bytes(const Layout2d& L) { return 16 * (size_t)(L.P > 0 ? L.P : 1); }
-cudaError_t launch_grad2d(const Layout2d&, const void*, const double*, double*, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+void layout2d_destroy(Layout2d& L) {
+  cudaFree(L.vec);
+  cudaFree(L.tp);
+  cudaFree(L.coef);
+  cudaFree(L.coef_lo);
+  cudaFree(L.parts);
+  cudaFree(L.sc);
+  cudaFree(L.rhs_w);
+  L.vec = L.tp = nullptr;
+  L.coef = L.coef_lo = nullptr;
+  L.parts = nullptr;
+  L.sc = nullptr;
+  L.rhs_w = nullptr;
 }
-cudaError_t launch_coeffs2d(const Layout2d&, const double*, const double*, int, SolveRec*,
-                            cudaStream_t) {
-  return cudaErrorNotSupported;
+
+size_t layout2d_res_bytes(const Layout2d& L) { return (size_t)16 * 2 * (L.HP > 0 ? L.HP : 1); }
+
+// =======================================================================================
+// Entry points
+// =======================================================================================
+
+cudaError_t launch_grad2d(const Layout2d& L, const void* tw64, const double* f, double* gradf,
+                          cudaStream_t s) {
+  // forward transform of f (paired with zero), i k, inverse of both components
+  cudaError_t e = rows_r2c<double>(L, tw64, nullptr, f, nullptr, nullptr, nullptr,
+                                   tplane(L, 0), tplane(L, 3), nullptr, nullptr, 1, s);
+  if (e) return e;
+  ColArgs a{};
+  a.planes[0] = tplane(L, 0);
+  a.K = 1;
+  if ((e = cols<double, COL_FWD>(L, tw64, nullptr, a, s))) return e;
+  const Modes2d M = modes_of(L);
+  k2_spec<double, OP_GRAD><<<grid_for(L.HP, 256), 256, 0, s>>>(
+      M, tplane(L, 0), nullptr, tplane(L, 1), tplane(L, 2), nullptr, nullptr, nullptr, nullptr);
+  if ((e = cudaGetLastError())) return e;
+  return c2r_vec<double>(L, tw64, nullptr, tplane(L, 1), tplane(L, 2), gradf, s);
 }
-cudaError_t launch_apply_G2d(const Layout2d&, const void*, const double*, const double*,
-                             const double*, double*, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+cudaError_t launch_coeffs2d(const Layout2d& L, const double* eta, const double* gradh, int kind,
+                            SolveRec* rec, cudaStream_t s) {
+  k2_coeffs<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, eta, gradh, kind, L.parts, L.sc, rec);
+  return cudaGetLastError();
 }
-cudaError_t launch_precond2d(const Layout2d&, const void*, const SolveRec*, const double*, double*,
-                             cudaStream_t) {
-  return cudaErrorNotSupported;
+
+cudaError_t launch_apply_G2d(const Layout2d& L, const void* tw64, const double* eta,
+                             const double* gradh, const double* u, double* Gu, cudaStream_t s) {
+  k2_coef_planes<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, eta, gradh, L.coef, L.coef_lo);
+  cudaError_t e = cudaGetLastError();
+  if (e) return e;
+  if ((e = r2c_vec<double>(L, tw64, nullptr, u, slot(L, 0), slot(L, 1), s))) return e;
+  if ((e = matvec<double>(L, tw64, nullptr, slot(L, 0), slot(L, 1), slot(L, 2), slot(L, 3),
+                          nullptr, nullptr, nullptr, nullptr, 0, nullptr, L.sc, 0, 0, nullptr,
+                          nullptr, nullptr, nullptr, s)))
+    return e;
+  return c2r_vec<double>(L, tw64, nullptr, slot(L, 2), slot(L, 3), Gu, s);
 }
-cudaError_t launch_pcg2d(const Layout2d&, const void*, const void*, int, const double*,
-                         const double*, const double*, double*, const SolveRec*, int, double,
-                         double, int, int, SolveRec*, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+cudaError_t launch_precond2d(const Layout2d& L, const void* tw64, const SolveRec* rec,
+                             const double* r, double* z, cudaStream_t s) {
+  cudaError_t e = r2c_vec<double>(L, tw64, nullptr, r, slot(L, 0), slot(L, 1), s);
+  if (e) return e;
+  const Modes2d M = modes_of(L);
+  k2_spec<double, OP_AINV><<<grid_for(L.HP, 256), 256, 0, s>>>(
+      M, slot(L, 0), slot(L, 1), slot(L, 2), slot(L, 3), nullptr, nullptr, nullptr, rec);
+  if ((e = cudaGetLastError())) return e;
+  return c2r_vec<double>(L, tw64, nullptr, slot(L, 2), slot(L, 3), z, s);
 }
-cudaError_t launch_rhs2d(const Layout2d&, const void*, double, const double*, const double*,
-                         const double*, const double*, double*, double*, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+namespace {
+
+// Inner PCG in precision T on the spectral system G d = r (slots: r 4-5, p 6-7, d 8-9,
+// G p 10-11), iterating in chunks with a device-side stop flag.
+template <typename T>
+cudaError_t inner_pcg(const Layout2d& L, const void* t64, const void* t32, int cap_total,
+                      cudaStream_t s) {
+  const Modes2d M = modes_of(L);
+  const int chunk = 4;
+  for (int done_iters = 0;;) {
+    for (int c = 0; c < chunk; ++c) {
+      cudaError_t e = matvec<T>(L, t64, t32, slot(L, 6), slot(L, 7), slot(L, 10), slot(L, 11),
+                                slot(L, 6), slot(L, 7), nullptr, nullptr, 0, nullptr, L.sc, 1, 1,
+                                slot(L, 6), slot(L, 7), slot(L, 4), slot(L, 5), s);
+      if (e) return e;
+      k2_update<T><<<grid_for(L.HP, 256), 256, 0, s>>>(M, slot(L, 8), slot(L, 9), slot(L, 4),
+                                                        slot(L, 5), slot(L, 6), slot(L, 7),
+                                                        slot(L, 10), slot(L, 11), L.sc, L.parts);
+      if ((e = cudaGetLastError())) return e;
+    }
+    done_iters += chunk;
+    int done = 0;
+    cudaError_t e = cudaMemcpyAsync(&done, &L.sc->done, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e) return e;
+    if ((e = cudaStreamSynchronize(s))) return e;
+    if (done || done_iters > cap_total + chunk) break;
+  }
+  return cudaSuccess;
 }
-cudaError_t launch_lincomb2d(const Layout2d&, const double*, double*, const double* const*,
-                             const double*, int, const double* const*, const double*, int, int,
-                             cudaStream_t) {
-  return cudaErrorNotSupported;
+
+template <typename T>
+__global__ void k2_set_inner(Scal2d* sc, double tol, int cap) {
+  sc->tol = tol;
+  sc->cap = cap;
+  sc->done = 0;
 }
-cudaError_t launch_linimp_res2d(const Layout2d&, const void*, const SolveRec*, const double*,
-                                const double*, const double*, const double*, void*,
-                                cudaStream_t) {
-  return cudaErrorNotSupported;
+
+__global__ void k2_set_status(Scal2d* sc, int st) { sc->status = st; }
+
+__global__ void k2_reset(Scal2d* sc) {
+  sc->iters = 0;
+  sc->ticket = 0;
+  sc->rz64 = 0.0;
+  sc->done = 0;
 }
-cudaError_t launch_linimp_solve2d(const Layout2d&, const void*, const SolveRec*, const void*,
-                                  const void*, double, double, double*, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+}  // namespace
+
+cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, int precision,
+                         const double* eta, const double* gradh, const double* b, double* x,
+                         const SolveRec* given, int kind, double rtol, double rtol_inner,
+                         int maxit, int max_refine, SolveRec* rec, cudaStream_t s) {
+  const Modes2d M = modes_of(L);
+  cudaError_t e;
+  k2_reset<<<1, 1, 0, s>>>(L.sc);
+  if (given) {
+    k2_set_given<<<1, 1, 0, s>>>(L.sc, given);
+  } else {
+    k2_coeffs<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, eta, gradh, kind, L.parts, L.sc, nullptr);
+  }
+  k2_coef_planes<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, eta, gradh, L.coef, L.coef_lo);
+  if ((e = cudaGetLastError())) return e;
+  Scal2d h{};
+  if ((e = cudaMemcpyAsync(&h, L.sc, sizeof(Scal2d), cudaMemcpyDeviceToHost, s))) return e;
+  if ((e = cudaStreamSynchronize(s))) return e;
+  if (h.status != SGN_OK) {
+    k2_report<<<1, 1, 0, s>>>(L.sc, rec, 0);
+    return cudaGetLastError();
+  }
+  const bool mixed = precision == SGN_PREC_MIXED;
+  // b^ -> slots 0-1, x0^ -> slots 2-3 (high precision)
+  if (mixed) {
+    if ((e = r2c_vec<df>(L, tw64, tw32, b, slot(L, 0), slot(L, 1), s))) return e;
+    if ((e = r2c_vec<df>(L, tw64, tw32, x, slot(L, 2), slot(L, 3), s))) return e;
+    k2_bnorm<df><<<grid_for(L.HP, 256), 256, 0, s>>>(M, slot(L, 0), slot(L, 1), L.sc, L.parts);
+  } else {
+    if ((e = r2c_vec<double>(L, tw64, tw32, b, slot(L, 0), slot(L, 1), s))) return e;
+    if ((e = r2c_vec<double>(L, tw64, tw32, x, slot(L, 2), slot(L, 3), s))) return e;
+    k2_bnorm<double><<<grid_for(L.HP, 256), 256, 0, s>>>(M, slot(L, 0), slot(L, 1), L.sc,
+                                                         L.parts);
+  }
+  if ((e = cudaGetLastError())) return e;
+  if ((e = cudaMemcpyAsync(&h, L.sc, sizeof(Scal2d), cudaMemcpyDeviceToHost, s))) return e;
+  if ((e = cudaStreamSynchronize(s))) return e;
+  const double bnorm = sqrt(fmax(h.bb, 0.0));
+  if (!(bnorm > 0.0)) {
+    cudaMemsetAsync(x, 0, sizeof(double) * 2 * L.P, s);
+    k2_report<<<1, 1, 0, s>>>(L.sc, rec, 0);
+    return cudaGetLastError();
+  }
+  if (!mixed) {
+    // r = b - G x0 (slots 4-5), then PCG in float64 with x^ accumulating in slots 2-3
+    if ((e = matvec<double>(L, tw64, tw32, slot(L, 2), slot(L, 3), slot(L, 4), slot(L, 5),
+                            nullptr, nullptr, slot(L, 0), slot(L, 1), 1, nullptr, L.sc, 0, 0,
+                            nullptr, nullptr, nullptr, nullptr, s)))
+      return e;
+    // start: copy r into the T slots (scale 1), x -> separate accumulation in slots 8-9
+    k2_set_inner<double><<<1, 1, 0, s>>>(L.sc, rtol * bnorm, maxit);
+    k2_inner_start<double, double><<<grid_for(L.HP, 256), 256, 0, s>>>(
+        M, slot(L, 4), slot(L, 5), 1.0, slot(L, 12), slot(L, 13), slot(L, 8), slot(L, 9),
+        slot(L, 6), slot(L, 7), L.sc, L.parts);
+    if ((e = cudaGetLastError())) return e;
+    // move r into slots 4-5 for the loop
+    cudaMemcpyAsync(slot(L, 4), slot(L, 12), (size_t)16 * L.HP, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(slot(L, 5), slot(L, 13), (size_t)16 * L.HP, cudaMemcpyDeviceToDevice, s);
+    if ((e = inner_pcg<double>(L, tw64, tw32, maxit, s))) return e;
+    k2_accumulate<double, double><<<grid_for(L.HP, 256), 256, 0, s>>>(
+        M, slot(L, 2), slot(L, 3), slot(L, 8), slot(L, 9), 1.0);
+    // final float64 residual for the report and x = F^{-1} x^
+    if ((e = matvec<double>(L, tw64, tw32, slot(L, 2), slot(L, 3), slot(L, 10), slot(L, 11),
+                            nullptr, nullptr, slot(L, 0), slot(L, 1), 1, x, L.sc, 0, 0, nullptr,
+                            nullptr, nullptr, nullptr, s)))
+      return e;
+    k2_report<<<1, 1, 0, s>>>(L.sc, rec, 0);
+    return cudaGetLastError();
+  }
+  // mixed: double-float refinement around float32 inner solves
+  int refinements = 0;
+  for (;;) {
+    // r^ = b^ - G x^ (double-float) into slots 10-11 (as df), writes real-space x
+    if ((e = matvec<df>(L, tw64, tw32, slot(L, 2), slot(L, 3), slot(L, 10), slot(L, 11), nullptr,
+                        nullptr, slot(L, 0), slot(L, 1), 1, x, L.sc, 0, 0, nullptr, nullptr,
+                        nullptr, nullptr, s)))
+      return e;
+    if ((e = cudaMemcpyAsync(&h, L.sc, sizeof(Scal2d), cudaMemcpyDeviceToHost, s))) return e;
+    if ((e = cudaStreamSynchronize(s))) return e;
+    const double ratio = sqrt(fmax(h.rz64, 0.0)) / bnorm;
+    if (ratio <= rtol || h.status != SGN_OK) break;
+    if (refinements >= max_refine || h.iters >= maxit) {
+      k2_set_status<<<1, 1, 0, s>>>(L.sc, SGN_ERR_NOT_CONVERGED);
+      k2_report<<<1, 1, 0, s>>>(L.sc, rec, refinements);
+      return cudaGetLastError();
+    }
+    const double rn = sqrt(h.rz64);
+    k2_set_inner<float><<<1, 1, 0, s>>>(L.sc, rtol_inner, maxit);
+    k2_inner_start<df, float><<<grid_for(L.HP, 256), 256, 0, s>>>(
+        M, slot(L, 10), slot(L, 11), 1.0 / rn, slot(L, 4), slot(L, 5), slot(L, 8), slot(L, 9),
+        slot(L, 6), slot(L, 7), L.sc, L.parts);
+    if ((e = cudaGetLastError())) return e;
+    if ((e = inner_pcg<float>(L, tw64, tw32, maxit, s))) return e;
+    k2_accumulate<df, float><<<grid_for(L.HP, 256), 256, 0, s>>>(M, slot(L, 2), slot(L, 3),
+                                                                  slot(L, 8), slot(L, 9), rn);
+    if ((e = cudaGetLastError())) return e;
+    ++refinements;
+  }
+  k2_report<<<1, 1, 0, s>>>(L.sc, rec, refinements);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs2d(const Layout2d& L, const void* tw64, double g, const double* eta,
+                         const double* u, const double* h, const double* gradh, double* f_eta,
+                         double* f_U, cudaStream_t s) {
+  // float64 right-hand side with six derivative pairs (see k2_rhs_stage for plane indices)
+  double* w = L.rhs_w;
+  const long long P = L.P;
+  auto W = [&](int q) { return w + (long long)q * P; };
+  const int gb = grid_for(P, 256);
+  cudaError_t e;
+  auto grad_pair = [&](const double* a, const double* b, double* ax, double* ay, double* bx,
+                       double* by) -> cudaError_t {
+    cudaError_t r = rows_r2c<double>(L, tw64, nullptr, a, b, nullptr, nullptr, tplane(L, 0),
+                                     tplane(L, 1), nullptr, nullptr, 1, s);
+    if (r) return r;
+    ColArgs c{};
+    c.planes[0] = tplane(L, 0);
+    c.planes[1] = tplane(L, 1);
+    c.K = 2;
+    if ((r = cols<double, COL_FWD>(L, tw64, nullptr, c, s))) return r;
+    const Modes2d M = modes_of(L);
+    k2_spec<double, OP_GRAD><<<grid_for(L.HP, 256), 256, 0, s>>>(
+        M, tplane(L, 0), tplane(L, 1), slot(L, 0), slot(L, 1), slot(L, 2), slot(L, 3), nullptr,
+        nullptr);
+    if ((r = cudaGetLastError())) return r;
+    ColArgs ci{};
+    ci.planes[0] = slot(L, 0);
+    ci.planes[1] = slot(L, 1);
+    ci.planes[2] = slot(L, 2);
+    ci.planes[3] = slot(L, 3);
+    ci.K = 4;
+    if ((r = cols<double, COL_INV>(L, tw64, nullptr, ci, s))) return r;
+    return rows_c2r<double>(L, tw64, nullptr, slot(L, 0), slot(L, 1), slot(L, 2), slot(L, 3), ax,
+                            ay, bx, by, 2, s);
+  };
+  k2_rhs_stage<double><<<gb, 256, 0, s>>>(0, P, g, eta, u, h, gradh, w, f_eta, f_U);
+  if ((e = cudaGetLastError())) return e;
+  if ((e = grad_pair(u, u + P, W(10), W(11), W(12), W(13)))) return e;
+  if ((e = grad_pair(W(0), W(1), W(14), W(15), W(16), W(17)))) return e;
+  if ((e = grad_pair(W(2), W(3), W(18), W(19), W(20), W(21)))) return e;
+  k2_rhs_stage<double><<<gb, 256, 0, s>>>(1, P, g, eta, u, h, gradh, w, f_eta, f_U);
+  if ((e = cudaGetLastError())) return e;
+  if ((e = grad_pair(W(7), W(4), W(22), W(23), W(24), W(25)))) return e;
+  if ((e = grad_pair(W(5), W(6), W(26), W(27), W(28), W(29)))) return e;
+  k2_rhs_stage<double><<<gb, 256, 0, s>>>(2, P, g, eta, u, h, gradh, w, f_eta, f_U);
+  if ((e = cudaGetLastError())) return e;
+  if ((e = grad_pair(W(8), nullptr, W(30), W(31), nullptr, nullptr))) return e;
+  k2_rhs_stage<double><<<gb, 256, 0, s>>>(3, P, g, eta, u, h, gradh, w, f_eta, f_U);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lincomb2d(const Layout2d& L, const double* dt, double* out,
+                             const double* const* x, const double* a, int nx,
+                             const double* const* f, const double* c, int nf, int components,
+                             cudaStream_t s) {
+  const long long n = L.P * components;
+  const double* X[4] = {nullptr, nullptr, nullptr, nullptr};
+  const double* F[4] = {nullptr, nullptr, nullptr, nullptr};
+  double A[4] = {0, 0, 0, 0}, Cc[4] = {0, 0, 0, 0};
+  for (int t = 0; t < nx; ++t) {
+    X[t] = x[t];
+    A[t] = a[t];
+  }
+  for (int t = 0; t < nf; ++t) {
+    F[t] = f[t];
+    Cc[t] = c[t];
+  }
+  k2_lincomb<<<grid_for(n, 256), 256, 0, s>>>(n, out, X[0], X[1], X[2], X[3], A[0], A[1], A[2],
+                                               A[3], nx, F[0], F[1], F[2], F[3], Cc[0], Cc[1],
+                                               Cc[2], Cc[3], nf, dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_linimp_res2d(const Layout2d& L, const void* tw64, const SolveRec* A,
+                                const double* eta, const double* gradh, const double* u,
+                                const double* U, void* res_hat, cudaStream_t s) {
+  // res^ = A u^ - (G u)^ + U^, float64, stored as two half planes in res_hat
+  k2_coef_planes<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, eta, gradh, L.coef, L.coef_lo);
+  cudaError_t e = cudaGetLastError();
+  if (e) return e;
+  if ((e = r2c_vec<double>(L, tw64, nullptr, u, slot(L, 0), slot(L, 1), s))) return e;
+  if ((e = r2c_vec<double>(L, tw64, nullptr, U, slot(L, 4), slot(L, 5), s))) return e;
+  if ((e = matvec<double>(L, tw64, nullptr, slot(L, 0), slot(L, 1), slot(L, 2), slot(L, 3),
+                          nullptr, nullptr, nullptr, nullptr, 0, nullptr, L.sc, 0, 0, nullptr,
+                          nullptr, nullptr, nullptr, s)))
+    return e;
+  char* r = static_cast<char*>(res_hat);
+  const Modes2d M = modes_of(L);
+  k2_linimp_combine<double><<<grid_for(L.HP, 256), 256, 0, s>>>(
+      M, A, slot(L, 0), slot(L, 1), slot(L, 2), slot(L, 3), slot(L, 4), slot(L, 5), r,
+      r + (size_t)16 * L.HP);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_linimp_solve2d(const Layout2d& L, const void* tw64, const SolveRec* A,
+                                  const void* res1_hat, const void* res0_hat, double c1,
+                                  double c0, double* u, cudaStream_t s) {
+  const char* r1 = static_cast<const char*>(res1_hat);
+  const char* r0 = static_cast<const char*>(res0_hat);
+  const size_t off = (size_t)16 * L.HP;
+  k2_axpby<double><<<grid_for(L.HP, 256), 256, 0, s>>>(L.HP, slot(L, 4), slot(L, 5), r1,
+                                                        r1 + off, r0, r0 + off, c1, c0);
+  cudaError_t e = cudaGetLastError();
+  if (e) return e;
+  const Modes2d M = modes_of(L);
+  k2_spec<double, OP_AINV><<<grid_for(L.HP, 256), 256, 0, s>>>(
+      M, slot(L, 4), slot(L, 5), slot(L, 6), slot(L, 7), nullptr, nullptr, nullptr, A);
+  if ((e = cudaGetLastError())) return e;
+  return c2r_vec<double>(L, tw64, nullptr, slot(L, 6), slot(L, 7), u, s);
 }
 
 }  // namespace sgn

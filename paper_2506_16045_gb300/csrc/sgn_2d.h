@@ -6,13 +6,25 @@
 
 namespace sgn {
 
+struct Scal2d;   // device-resident scalars of one 2d solve (sgn_2d.cu)
+
 // One 2d instance: fields [ny][nx] row-major; vector fields are two planes of P = nx ny.
+// Spectra are half spectra [ny][H], H = nx/2 + 1; every half-plane buffer has 16 bytes
+// per element so that it can hold complex float, double-float or double.
 struct Layout2d {
   int nx = 0, ny = 0, lx = 0, ly = 0;
   double Lx = 0.0, Ly = 0.0;
-  long long P = 0;
-  void* work = nullptr;      // device workspace (complex planes and reduction scratch)
-  size_t work_bytes = 0;
+  long long P = 0;          // points
+  int H = 0;                // half width
+  long long HP = 0;         // half-plane elements
+  void* vec = nullptr;      // 14 half planes: b^ (0,1), x^ (2,3), r^ (4,5), p^ (6,7), d^ (8,9),
+                            // G p / residual (10,11), spare (12,13)
+  void* tp = nullptr;       // 4 transform half planes
+  float* coef = nullptr;    // 6 coefficient planes (float parts)
+  float* coef_lo = nullptr; // 6 coefficient planes (double-float remainders)
+  double* parts = nullptr;  // per-block partial sums
+  Scal2d* sc = nullptr;
+  double* rhs_w = nullptr;  // 32 real planes of right-hand-side intermediates
 };
 
 cudaError_t layout2d_create(Layout2d& L, const sgn_grid& g);
@@ -27,6 +39,7 @@ cudaError_t launch_apply_G2d(const Layout2d& L, const void* tw64, const double* 
                              const double* gradh, const double* u, double* Gu, cudaStream_t s);
 cudaError_t launch_precond2d(const Layout2d& L, const void* tw64, const SolveRec* rec,
                              const double* r, double* z, cudaStream_t s);
+// Synchronises the stream between refinement passes and inner-iteration chunks.
 cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, int precision,
                          const double* eta, const double* gradh, const double* b, double* x,
                          const SolveRec* given, int kind, double rtol, double rtol_inner,

@@ -233,6 +233,90 @@ __device__ __forceinline__ void cta_fft(cplx<T>* buf, int n, int log2n, bool inv
 }
 
 // -------------------------------------------------------------------------------------
+// Batched form of cta_fft: nb independent sequences of length n in shared memory, sequence
+// s starting at buf + s * stride.  Butterflies of all sequences are spread over the CTA
+// (nb n/4 <= MAXB NT).  Same Stockham stages and barriers as cta_fft.
+// -------------------------------------------------------------------------------------
+template <typename T, int NT, int MAXB>
+__device__ __forceinline__ void cta_fft_batch(cplx<T>* buf, int n, int log2n, int nb, int stride,
+                                              bool inverse, const cplx<T>* __restrict__ tw) {
+  const int t = threadIdx.x;
+  int p = 1, lp = 0;
+  if (log2n & 1) {
+    const int h = n >> 1, tot = nb * h;
+    cplx<T> y0[2 * MAXB], y1[2 * MAXB];
+    int dst[2 * MAXB];
+#pragma unroll
+    for (int b = 0; b < 2 * MAXB; ++b) {
+      int g = t + b * NT;
+      if (g < tot) {
+        int s = g >> (log2n - 1), i = g & (h - 1);
+        cplx<T>* q = buf + s * stride;
+        cplx<T> a0 = q[i], a1 = q[i + h];
+        y0[b] = a0 + a1;
+        y1[b] = a0 - a1;
+        dst[b] = s * stride + i * 2;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < 2 * MAXB; ++b) {
+      int g = t + b * NT;
+      if (g < tot) {
+        buf[dst[b]] = y0[b];
+        buf[dst[b] + 1] = y1[b];
+      }
+    }
+    __syncthreads();
+    p = 2;
+    lp = 1;
+  }
+  const int qn = n >> 2, tot = nb * qn;
+  while (p < n) {
+    cplx<T> y[MAXB][4];
+    int dst[MAXB];
+    const int tshift = kTwiddleLog2 - lp - 2;
+#pragma unroll
+    for (int b = 0; b < MAXB; ++b) {
+      int g = t + b * NT;
+      if (g < tot) {
+        int s = g >> (log2n - 2), i = g & (qn - 1);
+        const cplx<T>* q = buf + s * stride;
+        int k = i & (p - 1);
+        cplx<T> a0 = q[i], a1 = q[i + qn], a2 = q[i + 2 * qn], a3 = q[i + 3 * qn];
+        if (p > 1) {
+          int e = k << tshift;
+          a1 = cmul_tw(a1, tw[e], inverse);
+          a2 = cmul_tw(a2, tw[2 * e], inverse);
+          a3 = cmul_tw(a3, tw[3 * e], inverse);
+        }
+        cplx<T> s02 = a0 + a2, d02 = a0 - a2, s13 = a1 + a3, d13 = a1 - a3;
+        cplx<T> r13 = inverse ? mul_pi(d13) : mul_mi(d13);
+        y[b][0] = s02 + s13;
+        y[b][1] = d02 + r13;
+        y[b][2] = s02 - s13;
+        y[b][3] = d02 - r13;
+        dst[b] = s * stride + ((i - k) << 2) + k;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < MAXB; ++b) {
+      int g = t + b * NT;
+      if (g < tot) {
+        buf[dst[b]] = y[b][0];
+        buf[dst[b] + p] = y[b][1];
+        buf[dst[b] + 2 * p] = y[b][2];
+        buf[dst[b] + 3 * p] = y[b][3];
+      }
+    }
+    __syncthreads();
+    p <<= 2;
+    lp += 2;
+  }
+}
+
+// -------------------------------------------------------------------------------------
 // Block reduction of a double (deterministic: fixed shuffle tree, then warp 0 over the
 // per-warp partials).  scratch must hold NT/32 doubles.  Result broadcast to all threads.
 // -------------------------------------------------------------------------------------
