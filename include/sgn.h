@@ -206,6 +206,67 @@ sgn_status sgn_state_get_stats(sgn_state* st, sgn_state_stats* out);
 void sgn_state_free(sgn_state* st);
 
 /* ---------------------------------------------------------------------------------- */
+/* Serving: continuous batching of constraint solves and SGN runs on one GPU            */
+/* ---------------------------------------------------------------------------------- */
+
+/* A server admits requests against a device-memory budget, keeps their state on the
+ * device, and advances every admitted request concurrently: 1d RK4 runs move together
+ * through one batched launch per kernel (per-instance dt), pending 1d solves run as one
+ * batched PCG, and 2d or multistep runs advance in per-request chunks.  Requests that
+ * arrive while others run join at the next chunk boundary as memory frees up.  The paper
+ * has no counterpart; each result equals the request run alone (RK4 is a one-step method
+ * and every instance is computed by its own CTAs, so batching does not change a result). */
+typedef struct sgn_server sgn_server;
+
+typedef enum { SGN_REQ_SOLVE = 0, SGN_REQ_RUN = 1 } sgn_req_kind;
+typedef enum {
+  SGN_SCHEME_RK4 = 0,      /* Eq:ERK */
+  SGN_SCHEME_AB2 = 2,      /* Eq:AB, Table 1 */
+  SGN_SCHEME_AB3 = 3,
+  SGN_SCHEME_AB4 = 4,
+  SGN_SCHEME_LINIMP = 5    /* Eq:MM (SBDF2) */
+} sgn_scheme;
+
+typedef struct {
+  sgn_req_kind kind;
+  sgn_grid grid;           /* one instance */
+  sgn_scheme scheme;       /* RUN only */
+  double dt;               /* RUN only */
+  int nsteps;              /* RUN only */
+  sgn_opts opts;           /* solve options (rtol, maxit, precision, coefficients) */
+  const double* eta;       /* [N] depth eta = h + zeta (the PCG coefficient for SOLVE) */
+  const double* u_or_b;    /* RUN: initial velocity u; SOLVE: right-hand side b (vector) */
+  const double* h;         /* [N] bathymetry (grad h = D h is formed on the device) */
+  int host_memory;         /* 1: eta, u_or_b, h are host pointers; 0: device pointers */
+} sgn_request;
+
+typedef struct {
+  sgn_status status;
+  const double* eta;       /* RUN: final eta (device, library-owned until release); SOLVE: NULL */
+  const double* u;         /* RUN: final u; SOLVE: the solution x (vector) */
+  const double* U;         /* RUN: final U = G u; SOLVE: NULL */
+  sgn_pcg_info info;       /* SOLVE: the solve report; RUN: iters = PCG iterations of the run */
+  double t_submit, t_admit, t_done;   /* seconds on sgn_clock() */
+} sgn_result;
+
+/* Starts a server (a worker thread with its own stream) on the context's device.
+ * budget_fraction of the device's total memory bounds the admitted requests' footprint
+ * (0 = 0.8). */
+sgn_status sgn_server_create(sgn_ctx* ctx, double budget_fraction, sgn_server** out);
+/* Copies the request's arrays (host or device) to the device and queues it; returns a
+ * ticket.  SGN_ERR_REJECTED when its footprint exceeds the whole budget; validation errors
+ * as for the corresponding direct calls. */
+sgn_status sgn_batch_submit(sgn_server* srv, const sgn_request* req, uint64_t* ticket);
+/* SGN_ERR_PENDING until the request is done; then fills *out (arrays stay valid until
+ * sgn_result_release) and returns the request's status. */
+sgn_status sgn_batch_poll(sgn_server* srv, uint64_t ticket, sgn_result* out);
+sgn_status sgn_result_release(sgn_server* srv, uint64_t ticket);
+/* Finishes all queued work, then stops the worker and frees everything. */
+void sgn_server_destroy(sgn_server* srv);
+/* The monotonic clock of the t_* fields, in seconds. */
+double sgn_clock(void);
+
+/* ---------------------------------------------------------------------------------- */
 /* Allocation-free solve (no counterpart in the paper)                                 */
 /* ---------------------------------------------------------------------------------- */
 

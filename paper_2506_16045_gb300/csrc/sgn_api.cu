@@ -862,6 +862,21 @@ extern "C" sgn_status sgn_state_init(sgn_state* st, sgn_stream stream) {
   return SGN_OK;
 }
 
+// Internal (serving): treat the bound arrays as a state that is already initialised (its
+// gradh and U were computed earlier, for example per request before packing into a
+// batch); clear counters and multistep history only.
+namespace sgn {
+sgn_status state_attach(sgn_state* st, cudaStream_t s) {
+  if (!st) return SGN_ERR_INVALID_ARG;
+  DeviceGuard g(st->lay->ctx->device);
+  SGN_CUDA(st->lay->ctx, cudaMemsetAsync(st->stats, 0, sizeof(DevStats), s));
+  st->hist = HIST_NONE;
+  st->levels = 0;
+  st->last = s;
+  return SGN_OK;
+}
+}  // namespace sgn
+
 extern "C" sgn_status sgn_step_rk4(sgn_state* st, const double* dt, int nsteps,
                                    const sgn_opts* opts, sgn_stream stream) {
   if (!st || !dt || nsteps < 0) return SGN_ERR_INVALID_ARG;

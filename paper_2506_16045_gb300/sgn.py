@@ -51,6 +51,22 @@ class SgnStateStats(C.Structure):
                 ("flops32", C.c_double), ("flops64", C.c_double)]
 
 
+class SgnRequest(C.Structure):
+    _fields_ = [("kind", C.c_int), ("grid", SgnGrid), ("scheme", C.c_int), ("dt", C.c_double),
+                ("nsteps", C.c_int), ("opts", SgnOpts), ("eta", C.c_void_p),
+                ("u_or_b", C.c_void_p), ("h", C.c_void_p), ("host_memory", C.c_int)]
+
+
+class SgnResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("eta", C.c_void_p), ("u", C.c_void_p), ("U", C.c_void_p),
+                ("info", SgnPcgInfo), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double)]
+
+
+REQ_SOLVE, REQ_RUN = 0, 1
+SCHEME_RK4, SCHEME_AB2, SCHEME_AB3, SCHEME_AB4, SCHEME_LINIMP = 0, 2, 3, 4, 5
+SGN_ERR_PENDING = 8
+
 # (name, restype, argtypes) of every exported entry point declared in include/sgn.h
 _VP = C.c_void_p
 _DP = C.c_void_p       # device pointers travel as integers
@@ -80,6 +96,12 @@ SIGNATURES = [
     ("sgn_state_free", None, [_VP]),
     ("sgn_pcg1d_noalloc", C.c_int, [C.c_int, C.c_double, _DP, _DP, _DP, _DP, C.c_double, C.c_int,
                                     C.c_int, C.POINTER(SgnPcgInfo), _VP]),
+    ("sgn_server_create", C.c_int, [_VP, C.c_double, C.POINTER(_VP)]),
+    ("sgn_batch_submit", C.c_int, [_VP, C.POINTER(SgnRequest), C.POINTER(C.c_uint64)]),
+    ("sgn_batch_poll", C.c_int, [_VP, C.c_uint64, C.POINTER(SgnResult)]),
+    ("sgn_result_release", C.c_int, [_VP, C.c_uint64]),
+    ("sgn_server_destroy", None, [_VP]),
+    ("sgn_clock", C.c_double, []),
     ("sgn_profile_enable", C.c_int, [_VP, C.c_int]),
     ("sgn_profile_read", C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                                    C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
@@ -336,3 +358,70 @@ class State:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching server (sgn_server) on the context's device."""
+
+    def __init__(self, ctx: Context, budget_fraction: float = 0.0):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        h = C.c_void_p()
+        ctx.check(self.lib.sgn_server_create(ctx.h, budget_fraction, C.byref(h)),
+                  "sgn_server_create")
+        self.h = h
+
+    def submit(self, kind, grid: Grid, eta, u_or_b, h, scheme=SCHEME_RK4, dt=0.0, nsteps=0,
+               rtol=1e-10, maxit=4000, prec=PREC_MIXED, coef=COEF_OPT, host=False):
+        """Queue a request; arrays are CUDA float64 tensors (host=False) or contiguous numpy
+        float64 arrays (host=True).  Returns (status, ticket)."""
+        if host:
+            import numpy as np
+            keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (eta, u_or_b, h)]
+            ptrs = [a.ctypes.data for a in keep]
+        else:
+            ptrs = [_ptr(eta), _ptr(u_or_b), _ptr(h)]
+        req = SgnRequest(kind, grid.c(), scheme, dt, nsteps,
+                         SgnOpts(rtol, maxit, prec, coef, 0.0, 0), ptrs[0], ptrs[1], ptrs[2],
+                         1 if host else 0)
+        t = C.c_uint64()
+        s = self.lib.sgn_batch_submit(self.h, C.byref(req), C.byref(t))
+        return s, t.value
+
+    def poll(self, ticket):
+        """None while pending, else a dict with status, device pointers, info and times."""
+        r = SgnResult()
+        s = self.lib.sgn_batch_poll(self.h, ticket, C.byref(r))
+        if s == SGN_ERR_PENDING:
+            return None
+        return dict(status=r.status, eta=r.eta, u=r.u, U=r.U, iters=r.info.iters,
+                    refinements=r.info.refinements, ratio=r.info.rel_resid_Ainv,
+                    t_submit=r.t_submit, t_admit=r.t_admit, t_done=r.t_done)
+
+    def release(self, ticket):
+        return self.lib.sgn_result_release(self.h, ticket)
+
+    def close(self):
+        if self.h:
+            self.lib.sgn_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _CudaArray:
+    """Minimal __cuda_array_interface__ wrapper of a device float64 array (no copy)."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f8",
+                                         "data": (int(ptr), False), "version": 3}
+
+
+def device_array(ptr, n):
+    """A CUDA float64 tensor copy of the n values at device address ptr (e.g. a result)."""
+    import torch
+    return torch.as_tensor(_CudaArray(ptr, n), device="cuda").clone()

@@ -1,0 +1,178 @@
+"""Serving: continuous batching through sgn_batch_submit / poll / release.
+
+Checks that requests arriving while others run are admitted and finish, that every result
+equals the same request run alone through the direct API (bitwise for the batched 1d RK4
+runs and 1d solves, whose instances own their CTAs), that oversize requests are rejected
+against the memory budget, and that the timestamps are ordered.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import sgn_oracle as O
+from paper_2506_16045_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2506_16045_gb300 import sgn
+    ctx = sgn.Context(0)
+    yield sgn, ctx
+    ctx.close()
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(), device="cuda")
+
+
+def wait(srv, tickets, timeout=120.0):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for t in tickets:
+            if t not in out:
+                r = srv.poll(t)
+                if r is not None:
+                    out[t] = r
+        assert time.time() - t0 < timeout, "serving requests did not finish"
+        time.sleep(0.002)
+    return out
+
+
+def alone_run(sgn, ctx, c, scheme, nsteps, rtol, prec):
+    lay = sgn.Layout(ctx, [sgn.Grid(1, c.n, c.L, g=c.g)])
+    eta, u, h = dev(c.eta), dev(c.u), dev(c.h)
+    U, gh = torch.zeros_like(eta), torch.zeros_like(eta)
+    st = sgn.State(lay, eta, U, u, h, gh)
+    st.init()
+    if scheme == sgn.SCHEME_RK4:
+        st.rk4(c.dt, nsteps, rtol=rtol, maxit=4000, prec=prec)
+    elif scheme == sgn.SCHEME_LINIMP:
+        st.linimp(c.dt, nsteps, rtol=rtol, maxit=4000, prec=prec)
+    else:
+        st.abk(scheme, c.dt, nsteps, rtol=rtol, maxit=4000, prec=prec)
+    torch.cuda.synchronize()
+    res = eta.cpu().numpy(), u.cpu().numpy(), U.cpu().numpy()
+    st.close()
+    return res
+
+
+def test_mixed_stream_results_equal_alone(S):
+    sgn, ctx = S
+    srv = sgn.Server(ctx)
+    rtol, prec = 1e-10, sgn.PREC_MIXED
+    ens = I.ensemble_1d(count=5, seed=11, kmin=9, kmax=12)
+    steps = [3, 7, 20, 5, 12]
+    # first wave
+    tickets, spec = [], {}
+    for c, k in zip(ens[:3], steps[:3]):
+        st, t = srv.submit(sgn.REQ_RUN, sgn.Grid(1, c.n, c.L, g=c.g), dev(c.eta), dev(c.u),
+                           dev(c.h), scheme=sgn.SCHEME_RK4, dt=c.dt, nsteps=k, rtol=rtol,
+                           prec=prec)
+        assert st == 0
+        tickets.append(t)
+        spec[t] = ("rk4", c, k)
+    # 1d solves (Eq:Testproblem) and a multistep run, submitted while the first wave runs
+    for n in (256, 1024):
+        _, h, eta, b = I.testproblem_1d(n, 1.0, 1.0)
+        st, t = srv.submit(sgn.REQ_SOLVE, sgn.Grid(1, n, 1.0), dev(eta), dev(b), dev(h),
+                           rtol=1e-12, prec=prec, host=False)
+        assert st == 0
+        tickets.append(t)
+        spec[t] = ("solve", (n, h, eta, b), None)
+    c = ens[3]
+    st, t = srv.submit(sgn.REQ_RUN, sgn.Grid(1, c.n, c.L, g=c.g), c.eta, c.u, c.h,
+                       scheme=sgn.SCHEME_AB4, dt=c.dt, nsteps=steps[3], rtol=rtol, prec=prec,
+                       host=True)
+    assert st == 0
+    tickets.append(t)
+    spec[t] = ("ab4", c, steps[3])
+    c = ens[4]
+    st, t = srv.submit(sgn.REQ_RUN, sgn.Grid(1, c.n, c.L, g=c.g), dev(c.eta), dev(c.u), dev(c.h),
+                       scheme=sgn.SCHEME_RK4, dt=c.dt, nsteps=steps[4], rtol=rtol, prec=prec)
+    tickets.append(t)
+    spec[t] = ("rk4", c, steps[4])
+    res = wait(srv, tickets)
+    for t in tickets:
+        r = res[t]
+        assert r["status"] == 0
+        assert r["t_submit"] <= r["t_admit"] <= r["t_done"]
+        kind, c, k = spec[t]
+        if kind == "solve":
+            n, h, eta, b = c
+            x = sgn.device_array(r["u"], n).cpu().numpy()
+            lay = sgn.Layout(ctx, [sgn.Grid(1, n, 1.0)])
+            gh = torch.zeros(n, dtype=torch.float64, device="cuda")
+            sgn.spectral_grad(lay, dev(h), gh)
+            xa = torch.zeros(n, dtype=torch.float64, device="cuda")
+            sgn.pcg(lay, dev(eta), gh, dev(b), xa, rtol=1e-12, maxit=4000, prec=prec)
+            assert np.array_equal(x, xa.cpu().numpy())
+            ref, _, _, _ = O.solve_G(eta, O.deriv(h, 1.0), b, O.make_grid(1, n, 1.0, 1.0),
+                                     rtol=1e-14, maxit=4000)
+            assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < 1e-9
+        else:
+            scheme = sgn.SCHEME_RK4 if kind == "rk4" else sgn.SCHEME_AB4
+            ea, ua, Ua = alone_run(sgn, ctx, c, scheme, k, rtol, prec)
+            eg = sgn.device_array(r["eta"], c.n).cpu().numpy()
+            ug = sgn.device_array(r["u"], c.n).cpu().numpy()
+            Ug = sgn.device_array(r["U"], c.n).cpu().numpy()
+            assert np.array_equal(eg, ea) and np.array_equal(ug, ua) and np.array_equal(Ug, Ua)
+        assert srv.release(t) == 0
+    srv.close()
+
+
+def test_2d_requests_in_the_mix(S):
+    sgn, ctx = S
+    srv = sgn.Server(ctx)
+    c2 = I.bump2d_case(n=32, L=40.0, a=0.2, x0=10.0, H=0.5, R=3.0, dt=0.05)
+    g2 = sgn.Grid(2, 32, 40.0, g=9.81, ny=32, Ly=40.0)
+    st, t_run = srv.submit(sgn.REQ_RUN, g2, dev(c2["eta"]), dev(c2["u"]), dev(c2["h"]),
+                           scheme=sgn.SCHEME_RK4, dt=0.05, nsteps=4, rtol=1e-11,
+                           prec=sgn.PREC_MIXED)
+    assert st == 0
+    _, _, h, eta, rhs = I.elliptical_bump_2d(32, 1.0, 1.0)
+    st, t_sol = srv.submit(sgn.REQ_SOLVE, sgn.Grid(2, 32, 1.0, ny=32, Ly=1.0), dev(eta),
+                           dev(rhs), dev(h), rtol=1e-12, prec=sgn.PREC_MIXED)
+    assert st == 0
+    res = wait(srv, [t_run, t_sol])
+    assert res[t_run]["status"] == 0 and res[t_sol]["status"] == 0
+    x = sgn.device_array(res[t_sol]["u"], 2 * 32 * 32).cpu().numpy().reshape(2, 32, 32)
+    gh = O.grad(h, (1.0, 1.0))
+    ref, _, _, _ = O.solve_G(eta, gh, rhs, O.make_grid(2, 32, 1.0, 1.0, ny=32, Ly=1.0),
+                             rtol=1e-14, maxit=4000)
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < 1e-9
+    grid = O.make_grid(2, 32, 40.0, 9.81, ny=32, Ly=40.0)
+    ost = O.init_state(c2["eta"], c2["u"], c2["h"], grid)
+    O.run_rk4(ost, 0.05, 4, 1e-13)
+    eg = sgn.device_array(res[t_run]["eta"], 32 * 32).cpu().numpy().reshape(32, 32)
+    assert np.linalg.norm(eg - ost.eta) / np.linalg.norm(ost.eta) < 1e-6
+    for t in (t_run, t_sol):
+        srv.release(t)
+    srv.close()
+
+
+def test_admission_budget_and_rejection(S):
+    sgn, ctx = S
+    free, total = torch.cuda.mem_get_info()
+    # a budget that holds about one 2d 512^2 request: an oversize 1024^2 request is rejected
+    frac = 1.5 * (5 * 8 * 512 * 512 + 760 * 512 * 512) / total
+    srv = sgn.Server(ctx, budget_fraction=frac)
+    z = torch.zeros(2 * 1024 * 1024, dtype=torch.float64, device="cuda")
+    st, _ = srv.submit(sgn.REQ_SOLVE, sgn.Grid(2, 1024, 1.0, ny=1024, Ly=1.0), z, z, z)
+    assert st == 10                                # SGN_ERR_REJECTED
+    # several small requests still run to completion under the same budget
+    tickets = []
+    for n in (512, 1024, 2048):
+        _, h, eta, b = I.testproblem_1d(n, 1.0, 0.5)
+        st, t = srv.submit(sgn.REQ_SOLVE, sgn.Grid(1, n, 1.0), dev(eta), dev(b), dev(h),
+                           rtol=1e-10)
+        assert st == 0
+        tickets.append(t)
+    res = wait(srv, tickets)
+    assert all(r["status"] == 0 for r in res.values())
+    srv.close()
