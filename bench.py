@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--count", type=int, default=256)
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the shelf/2d/serving sections after the headline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -381,9 +383,185 @@ def gpu_arm(args, world, rank, local, pg):
                    "iterations": s1["iterations"] - s0["iterations"],
                    "max_iters": s1["max_iters"], "status": s1["status"]},
     }
+    if rank == 0 and world == 1 and not args.no_extra:
+        E.st.close()
+        extra = {}
+        for name, fn in (("shelf_1d", bench_shelf), ("bump_2d", bench_2d),
+                         ("serving", bench_serving)):
+            try:
+                extra[name] = fn(sgn, ctx, torch)
+            except Exception as exc:                          # reported, never silent
+                extra[name] = {"error": repr(exc)}
+        line["configs"] = extra
+        print(json.dumps(line))
+        return
     if rank == 0:
         print(json.dumps(line))
     E.st.close()
+
+
+def bench_2d(sgn, ctx, torch, steps=3):
+    """2d plane solitary wave over a Gaussian bump (80 x 80 at 512^2), RK4, mixed; error
+    against the float64 path after the same steps."""
+    import numpy as np
+
+    from paper_2506_16045_gb300 import inputs as I
+    c = I.bump2d_case(n=512, L=80.0, a=0.2, x0=20.0, H=0.5, R=3.0, dt=0.02)
+    n = c["n"]
+    lay = sgn.Layout(ctx, [sgn.Grid(2, n, c["L"], g=c["g"], ny=n, Ly=c["L"])])
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a).ravel(), dtype=torch.float64,
+                                    device="cuda")
+    out = {}
+    for prec in (sgn.PREC_MIXED, sgn.PREC_FP64):
+        eta, u, h = dev(c["eta"]), dev(c["u"]), dev(c["h"])
+        U = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+        gh = torch.zeros_like(U)
+        st = sgn.State(lay, eta, U, u, h, gh)
+        st.init()
+        st.rk4(c["dt"], 1, rtol=1e-10, maxit=4000, prec=prec)        # warm-up step
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st.rk4(c["dt"], steps, rtol=1e-10, maxit=4000, prec=prec)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[prec] = (dt, eta.cpu().numpy(), u.cpu().numpy(), st.stats())
+        st.close()
+    tm, em, um, sm = out[sgn.PREC_MIXED]
+    t6, e6, u6, _ = out[sgn.PREC_FP64]
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    return {"workload": "2d bump 80x80 at 512^2, RK4, rtol 1e-10", "steps": steps,
+            "value": n * n * steps / tm, "unit": UNIT, "fp64_value": n * n * steps / t6,
+            "rel_l2_eta_vs_fp64": rel(em, e6), "rel_l2_u_vs_fp64": rel(um, u6),
+            "iterations_per_solve": sm["iterations"] / max(1, sm["solves"])}
+
+
+def bench_shelf(sgn, ctx, torch, steps=40):
+    """1d shelf (N=4096, L=200, a=0.3): AB4 + mixed PCG versus linearly implicit SBDF2."""
+    import numpy as np
+
+    from paper_2506_16045_gb300 import inputs as I
+    c = I.shelf_case()
+    lay = sgn.Layout(ctx, [sgn.Grid(1, c.n, c.L, g=c.g)])
+    res = {}
+    for name in ("ab4_mixed", "ab4_fp64", "sbdf2"):
+        eta, u, h = (torch.as_tensor(a, dtype=torch.float64, device="cuda")
+                     for a in (c.eta, c.u, c.h))
+        U, gh = torch.zeros_like(eta), torch.zeros_like(eta)
+        st = sgn.State(lay, eta, U, u, h, gh)
+        st.init()
+        prec = sgn.PREC_FP64 if name != "ab4_mixed" else sgn.PREC_MIXED
+        run = (lambda k: st.linimp(c.dt, k, rtol=1e-12, prec=prec)) if name == "sbdf2" else \
+              (lambda k: st.abk(4, c.dt, k, rtol=1e-12, prec=prec))
+        run(4)                                      # start-up levels and warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run(steps)
+        torch.cuda.synchronize()
+        res[name] = c.n * steps / (time.perf_counter() - t0)
+        st.close()
+    return {"workload": "1d shelf N=4096 L=200, 40 steps after start-up", "unit": UNIT, **res}
+
+
+def bench_serving(sgn, ctx, torch, nreq=120, rate=200.0, seed=16045, baseline_sample=8):
+    """Poisson stream of SGN runs and constraint solves (half 1d, half 2d), host inputs."""
+    import numpy as np
+
+    from paper_2506_16045_gb300 import inputs as I
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for _ in range(nreq):
+        kind = sgn.REQ_RUN if rng.random() < 0.5 else sgn.REQ_SOLVE
+        dim = 1 if rng.random() < 0.5 else 2
+        H, R = rng.uniform(0.1, 0.6), rng.uniform(1.0, 5.0)
+        a = rng.uniform(0.05, 0.3)
+        if dim == 1:
+            n, L = 2 ** int(rng.integers(10, 14)), 200.0
+            x = I.grid_1d(n, L)
+            xb = rng.uniform(0.3, 0.7) * L
+            h = 1.0 - H * np.exp(-((x - xb) ** 2) / R ** 2)
+            eta, u = I.solitary_wave_1d(x, L, 1.0, a, 0.2 * L, 9.81)
+            eta = h + (eta - 1.0)
+            grid = sgn.Grid(1, n, L)
+            pts = n
+        else:
+            n, L = 2 ** int(rng.integers(7, 10)), 80.0
+            X, Y = I.grid_2d(n, n, L, L)
+            xb, yb = rng.uniform(0.3, 0.7, 2) * L
+            h = I.gaussian_bump_2d(X, Y, L, L, H, R, xb, yb)
+            eta, u = I.solitary_wave_2d(X, Y, L, L, 1.0, a, 0.2 * L, 9.81)
+            eta = h + (eta - 1.0)
+            grid = sgn.Grid(2, n, L, ny=n, Ly=L)
+            pts = n * n
+        dx = L / n
+        dt = 0.25 * dx / np.sqrt(9.81 * (1 + a))
+        nsteps = int(rng.integers(5, 31)) if kind == sgn.REQ_RUN else 0
+        reqs.append((kind, grid, eta, u, h, dt, nsteps, pts))
+    srv = sgn.Server(ctx)
+    gaps = rng.exponential(1.0 / rate, nreq)
+    tickets = []
+    t_start = time.perf_counter()
+    t_next = t_start
+    for (kind, grid, eta, u, h, dt, nsteps, pts), gap in zip(reqs, gaps):
+        t_next += gap
+        while time.perf_counter() < t_next:
+            time.sleep(0.0002)
+        st, t = srv.submit(kind, grid, eta, u, h, scheme=sgn.SCHEME_RK4, dt=dt, nsteps=nsteps,
+                           rtol=1e-10, prec=sgn.PREC_MIXED, host=True)
+        tickets.append((t, kind, pts, nsteps, st))
+    done = {}
+    while len(done) < len(tickets):
+        for t, *_ in tickets:
+            if t not in done:
+                r = srv.poll(t)
+                if r is not None:
+                    done[t] = r
+        time.sleep(0.001)
+    lat = np.array([1e3 * (done[t]["t_done"] - done[t]["t_submit"]) for t, *_ in tickets])
+    solve_lat = np.array([1e3 * (done[t]["t_done"] - done[t]["t_submit"])
+                          for t, k, *_ in tickets if k == sgn.REQ_SOLVE])
+    t0 = min(done[t]["t_submit"] for t, *_ in tickets)
+    t1 = max(done[t]["t_done"] for t, *_ in tickets)
+    work = sum(p * max(k, 1) for t, kind, p, k, _ in tickets)     # a solve counts one step
+    ok = all(done[t]["status"] == 0 for t, *_ in tickets)
+    for t, *_ in tickets:
+        srv.release(t)
+    srv.close()
+    # plain sequential float64 on a sample of the same stream, one request per launch group
+    import math
+    idx = list(range(0, nreq, max(1, nreq // baseline_sample)))[:baseline_sample]
+    wsum, tsum = 0, 0.0
+    for i in idx:
+        kind, grid, eta, u, h, dt, nsteps, pts = reqs[i]
+        lay = sgn.Layout(ctx, [grid])
+        d = 1 if grid.dim == 1 else 2
+        e_, u_, h_ = (torch.as_tensor(np.ascontiguousarray(a).ravel(), dtype=torch.float64,
+                                      device="cuda") for a in (eta, u, h))
+        U_ = torch.zeros(d * pts, dtype=torch.float64, device="cuda")
+        g_ = torch.zeros_like(U_)
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        if kind == sgn.REQ_RUN:
+            st = sgn.State(lay, e_, U_, u_, h_, g_)
+            st.init()
+            st.rk4(dt, nsteps, rtol=1e-10, maxit=4000, prec=sgn.PREC_FP64)
+            torch.cuda.synchronize()
+            st.close()
+        else:
+            sgn.spectral_grad(lay, h_, g_)
+            sgn.pcg(lay, e_, g_, u_, U_, rtol=1e-10, maxit=4000, prec=sgn.PREC_FP64)
+        torch.cuda.synchronize()
+        tsum += time.perf_counter() - ts
+        wsum += pts * max(nsteps, 1)
+    return {"workload": f"Poisson {rate:.0f}/s, {nreq} requests (seed {seed}): 50% RK4 runs "
+                        "(5-30 steps) / 50% solves, 50% 1d n in 2^10..2^13 / 50% 2d 2^7..2^9 "
+                        "per side, Gaussian bumps, mixed precision, rtol 1e-10",
+            "all_ok": ok, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)),
+            "solve_p50_ms": float(np.percentile(solve_lat, 50)) if solve_lat.size else None,
+            "solve_p99_ms": float(np.percentile(solve_lat, 99)) if solve_lat.size else None,
+            "throughput": work / (t1 - t0), "unit": UNIT,
+            "plain_fp64_sequential": wsum / tsum,
+            "plain_sample": f"{len(idx)} requests of the same stream run one at a time"}
 
 
 def main():
