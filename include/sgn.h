@@ -179,7 +179,9 @@ typedef struct {
   double t;                       /* simulated time of instance 0 */
   long long step;                 /* steps taken */
   double flops32;                 /* algorithmic float32 flops of the PCG solves */
-  double flops64;                 /* algorithmic float64 flops of the PCG solves */
+  double flops64;                 /* algorithmic flops of the solves' high-precision part:
+                                     float64 for SGN_PREC_FP64, double-float (pairs of
+                                     float32) for SGN_PREC_MIXED */
 } sgn_state_stats;
 
 /* Binds caller-owned packed arrays: eta [P], U (vector), u (vector), h [P], gradh (vector,

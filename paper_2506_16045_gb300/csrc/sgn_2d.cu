@@ -675,17 +675,25 @@ __global__ void __launch_bounds__(256) k2_coeffs(long long P, const double* eta,
     last = atomicAdd(&sc->ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    sc->ticket = 0;
+  if (!last) return;
+  {
+    // the last block reduces the per-block partials with all its threads
     volatile double* vp = parts;
     double a = 1e308, b = -1e308, g = 0.0, s = -1e308, bd = 0.0;
-    for (int i = 0; i < (int)gridDim.x; ++i) {
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += 256) {
       a = fmin(a, vp[5 * i]);
       b = fmax(b, vp[5 * i + 1]);
       g = fmax(g, vp[5 * i + 2]);
       s = fmax(s, vp[5 * i + 3]);
       bd = fmax(bd, vp[5 * i + 4]);
     }
+    a = block_min<256>(a, red);
+    b = block_max<256>(b, red);
+    g = block_max<256>(g, red);
+    s = block_max<256>(s, red);
+    bd = block_max<256>(bd, red);
+    if (threadIdx.x != 0) return;
+    sc->ticket = 0;
     SolveRec R = {};
     R.eta_min = a;
     R.eta_max = b;
