@@ -167,7 +167,9 @@ typedef struct {
   int maxit;                      /* PCG iteration cap per solve */
   sgn_precision prec;             /* FP64 or MIXED constraint solves */
   sgn_coef_kind coef;             /* preconditioner coefficients for the PCG solves */
-  double rtol_inner;              /* mixed: float32 inner tolerance (0 = 1e-5) */
+  double rtol_inner;              /* mixed: float32 inner tolerance; 0 = adaptive: each inner
+                                     solve targets 0.3 rtol / (current residual ratio),
+                                     clamped to [1e-6, 0.1] */
   int max_refine;                 /* mixed: refinement cap (0 = 12) */
 } sgn_opts;
 

@@ -5,7 +5,8 @@
 //   MIXED = true : iterative refinement in double-float (~48-bit) precision.  Each pass
 //                  computes the residual r = b - G x with double-float FFTs and
 //                  coefficients, stops when sqrt(r.A^{-1}r) <= rtol sqrt(b.A^{-1}b), and
-//                  otherwise solves G d = r / ||r||_{A^{-1}} by float32 PCG to rtol_inner
+//                  otherwise solves G d = r / ||r||_{A^{-1}} by float32 PCG (to rtol_inner,
+//                  or adaptively to 0.3 rtol / current ratio within [1e-6, 0.1])
 //                  and updates x += ||r||_{A^{-1}} d in double-float.  Float32 products are
 //                  summed per thread (at most 2 MAXB + 1 terms) and the per-thread partials
 //                  are summed across the CTA in float64.
@@ -417,9 +418,16 @@ __global__ void __launch_bounds__(NT, 1) k_pcg1d(const Inst1d* __restrict__ inst
       }
       __syncthreads();
       int st_in = SGN_OK;
-      pcg_loop_f32<NT, MAXB>(buf32, slots, &sc, spi, log2n, Rh, Dh, coef32, rtol_inner, maxit,
-                             iters, st_in);
-      if (st_in == SGN_ERR_BREAKDOWN) status = SGN_ERR_BREAKDOWN;
+      // inner target: the reduction still needed (with a 0.3 margin), within what float32
+      // PCG resolves, unless the caller fixed rtol_inner
+      const double tin =
+          rtol_inner > 0.0 ? rtol_inner : fmin(0.1, fmax(1e-6, 0.3 * rtol / R.ratio));
+      const int it_before = iters;
+      pcg_loop_f32<NT, MAXB>(buf32, slots, &sc, spi, log2n, Rh, Dh, coef32, tin, maxit, iters,
+                             st_in);
+      // A float32 breakdown after some progress only means float32 has resolved what it
+      // can: keep the correction and let the next refinement pass decide.
+      if (st_in == SGN_ERR_BREAKDOWN && iters == it_before) status = SGN_ERR_BREAKDOWN;
       ++refinements;
       const df unscale(sqrt(rz64));
       for (int m = threadIdx.x; m <= h; m += NT) {

@@ -1276,12 +1276,23 @@ cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, 
       return cudaGetLastError();
     }
     const double rn = sqrt(h.rz64);
-    k2_set_inner<float><<<1, 1, 0, s>>>(L.sc, rtol_inner, maxit);
+    const double tin =
+        rtol_inner > 0.0 ? rtol_inner : fmin(0.1, fmax(1e-6, 0.3 * rtol / ratio));
+    k2_set_inner<float><<<1, 1, 0, s>>>(L.sc, tin, maxit);
     k2_inner_start<df, float><<<grid_for(L.HP, 256), 256, 0, s>>>(
         M, slot(L, 10), slot(L, 11), 1.0 / rn, slot(L, 4), slot(L, 5), slot(L, 8), slot(L, 9),
         slot(L, 6), slot(L, 7), L.sc, L.parts);
     if ((e = cudaGetLastError())) return e;
+    const int it_before = h.iters;
     if ((e = inner_pcg<float>(L, tw64, tw32, maxit, s))) return e;
+    {
+      // a float32 breakdown after some progress keeps the correction (see the 1d solve)
+      Scal2d hs{};
+      if ((e = cudaMemcpyAsync(&hs, L.sc, sizeof(Scal2d), cudaMemcpyDeviceToHost, s))) return e;
+      if ((e = cudaStreamSynchronize(s))) return e;
+      if (hs.status == SGN_ERR_BREAKDOWN && hs.iters > it_before)
+        k2_set_status<<<1, 1, 0, s>>>(L.sc, SGN_OK);
+    }
     k2_accumulate<df, float><<<grid_for(L.HP, 256), 256, 0, s>>>(M, slot(L, 2), slot(L, 3),
                                                                   slot(L, 8), slot(L, 9), rn);
     if ((e = cudaGetLastError())) return e;

@@ -553,7 +553,7 @@ sgn_status run_pcg(sgn_layout* lay, const double* eta, const double* gradh, cons
                    sgn_coef_kind kind, const double* b, double* x, double rtol, int maxit,
                    sgn_precision prec, double rtol_inner, int max_refine, cudaStream_t s) {
   sgn_ctx* ctx = lay->ctx;
-  if (rtol_inner <= 0.0) rtol_inner = 1e-5;
+  if (rtol_inner <= 0.0) rtol_inner = -1.0;   // adaptive inner tolerance
   if (max_refine <= 0) max_refine = 12;
   cudaError_t e;
   ProfScope prof(ctx, s, 0);

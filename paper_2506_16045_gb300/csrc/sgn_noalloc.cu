@@ -120,7 +120,7 @@ extern "C" sgn_status sgn_pcg1d_noalloc(int n, double L, const double* eta, cons
   lay.class_begin[log2n] = 0;
   lay.class_end[log2n] = 1;
   cudaError_t e = sgn::launch_pcg1d(lay, P.tw64, P.tw32, prec, eta, gradh, b, x, nullptr,
-                                    SGN_COEF_OPT, rtol, 1e-5, maxit, 12, P.rec, P.ws,
+                                    SGN_COEF_OPT, rtol, -1.0, maxit, 12, P.rec, P.ws,
                                     P.coef_lo, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
