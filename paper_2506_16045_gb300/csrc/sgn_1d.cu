@@ -76,7 +76,6 @@ __global__ void __launch_bounds__(NT, 1) k_apply_G1d(const Inst1d* __restrict__ 
   cplx<double>* buf = reinterpret_cast<cplx<double>*>(smem);
   const Inst1d I = insts[ids[blockIdx.x]];
   const int n = I.n, h = n >> 1;
-  const double kunit = 2.0 * kPi / I.L;
   for (int j = threadIdx.x; j < n; j += NT) buf[j] = mk(u[I.off + j], 0.0);
   __syncthreads();
   cta_fft<double, NT, MAXB>(buf, n, I.log2n, false, tw);
@@ -147,79 +146,6 @@ __global__ void __launch_bounds__(NT, 1) k_precond1d(const Inst1d* __restrict__ 
   for (int j = threadIdx.x; j < n; j += NT) z[I.off + j] = buf[j].x;
 }
 
-// a7: right-hand side of Eq:DAE_DSWE with F from Def:bigF, in number type T (float64 for
-// the float64 path, double-float for the mixed path): four derivative pairs
-// (u, eta u) -> (d, m); (zeta, s) -> (zeta_x, s_x); d -> d_x; Phi' -> Phi'_x with
-// Phi' = eta^3 Q/3 + eta^2 m d + eta^2 S/2 + eta m s - eta u^2 (the flux -(eta u^2)_x folded
-// in), Q = u d_x - d^2, S = u s_x (reading R6), and
-// f_eta = -m, f_U = -g eta zeta_x + Phi'_x - h_x Psi, Psi = eta^2 Q/2 + eta m d + eta S + m s.
-template <typename T, int NT, int MAXB>
-__global__ void __launch_bounds__(NT, 1) k_rhs1d(const Inst1d* __restrict__ insts,
-                                              const int* __restrict__ ids,
-                                              const cplx<T>* __restrict__ tw, double g,
-                                              const double* __restrict__ eta_all,
-                                              const double* __restrict__ u_all,
-                                              const double* __restrict__ h_all,
-                                              const double* __restrict__ hx_all,
-                                              double* __restrict__ fe_all,
-                                              double* __restrict__ fU_all,
-                                              double* __restrict__ scratch, long long P) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem);
-  const Inst1d I = insts[ids[blockIdx.x]];
-  const int n = I.n, log2n = I.log2n;
-  const T kn = num<T>(2.0 * kPi / I.L / (double)n);
-  const T third = num<T>(1.0 / 3.0);
-  const T gT = num<T>(g);
-  const double* eta = eta_all + I.off;
-  const double* u = u_all + I.off;
-  const double* hh = h_all + I.off;
-  const double* hx = hx_all + I.off;
-  // scratch planes hold T values (8 bytes each for double and double-float)
-  T* sd = reinterpret_cast<T*>(scratch + I.off);           // d = u_x
-  T* sm = reinterpret_cast<T*>(scratch + P + I.off);       // m = (eta u)_x
-  T* szx = reinterpret_cast<T*>(scratch + 2 * P + I.off);  // zeta_x
-  T* ssx = reinterpret_cast<T*>(scratch + 3 * P + I.off);  // s_x, s = h_x u
-  T* spsi = reinterpret_cast<T*>(scratch + 4 * P + I.off); // Psi
-  deriv_pair<T, NT, MAXB>(buf, n, log2n, kn, [&](int j) {
-    T uj = num<T>(u[j]);
-    return mk(uj, num<T>(eta[j]) * uj);
-  }, tw);
-  for (int j = threadIdx.x; j < n; j += NT) {
-    sd[j] = buf[j].x;
-    sm[j] = buf[j].y;
-  }
-  __syncthreads();
-  deriv_pair<T, NT, MAXB>(buf, n, log2n, kn, [&](int j) {
-    return mk(num<T>(eta[j] - hh[j]), num<T>(hx[j]) * num<T>(u[j]));
-  }, tw);
-  for (int j = threadIdx.x; j < n; j += NT) {
-    szx[j] = buf[j].x;
-    ssx[j] = buf[j].y;
-  }
-  __syncthreads();
-  deriv_pair<T, NT, MAXB>(buf, n, log2n, kn, [&](int j) { return mk(sd[j], from_int<T>(0)); },
-                          tw);
-  for (int j = threadIdx.x; j < n; j += NT) {
-    T e = num<T>(eta[j]), uj = num<T>(u[j]), d = sd[j], m = sm[j];
-    T s = num<T>(hx[j]) * uj;
-    T Q = uj * buf[j].x - d * d;
-    T Sv = uj * ssx[j];
-    T e2 = e * e;
-    T md = m * d;
-    T Phi = e2 * e * Q * third + e2 * md + half(e2 * Sv) + e * m * s - e * uj * uj;
-    spsi[j] = half(e2 * Q) + e * md + e * Sv + m * s;
-    buf[j] = mk(Phi, from_int<T>(0));
-  }
-  __syncthreads();
-  deriv_pair<T, NT, MAXB>(buf, n, log2n, kn, [&](int j) { return buf[j]; }, tw);
-  for (int j = threadIdx.x; j < n; j += NT) {
-    fe_all[I.off + j] = -to_f64(sm[j]);
-    T fU = buf[j].x - gT * num<T>(eta[j]) * szx[j] - num<T>(hx[j]) * spsi[j];
-    fU_all[I.off + j] = to_f64(fU);
-  }
-}
-
 struct AxpyArgs {
   const double* f[4];
   double c[4];
@@ -257,7 +183,6 @@ __global__ void __launch_bounds__(NT, 1) k_linimp_res1d(const Inst1d* __restrict
   const int id = ids[blockIdx.x];
   const Inst1d I = insts[id];
   const int n = I.n, h = n >> 1;
-  const double kunit = 2.0 * kPi / I.L;
   const double sigma = A[id].sigma, alpha = A[id].alpha;
   const long long S = h + 1;
   cplx<double>* Uh = ws + I.ws;
@@ -369,32 +294,6 @@ cudaError_t launch_precond1d(const Layout1d& lay, const void* tw64, const SolveR
     cudaError_t e = set_smem(k, sm);
     if (e) return e;
     k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, tw, rec, r, z);
-    return cudaGetLastError();
-  });
-}
-
-cudaError_t launch_rhs1d(const Layout1d& lay, const void* tw64, const void* tw32, int precision,
-                         double g, const double* eta, const double* u, const double* h,
-                         const double* hx, double* f_eta, double* f_U, double* scratch,
-                         cudaStream_t s) {
-  auto t64 = static_cast<const cplx<double>*>(tw64);
-  auto tdf = reinterpret_cast<const cplx<df>*>(static_cast<const char*>(tw32) + kTw32Bytes);
-  return for_each_class(lay, s, [&](auto NTc, auto MBc, int l, int first, int num, cudaStream_t s) {
-    constexpr int NT = decltype(NTc)::value, MB = decltype(MBc)::value;
-    size_t sm = (size_t)16 << l;
-    if (precision == SGN_PREC_MIXED) {
-      auto k = k_rhs1d<df, NT, MB>;
-      cudaError_t e = set_smem(k, sm);
-      if (e) return e;
-      k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, tdf, g, eta, u, h, hx, f_eta, f_U,
-                            scratch, lay.points);
-    } else {
-      auto k = k_rhs1d<double, NT, MB>;
-      cudaError_t e = set_smem(k, sm);
-      if (e) return e;
-      k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, t64, g, eta, u, h, hx, f_eta, f_U,
-                            scratch, lay.points);
-    }
     return cudaGetLastError();
   });
 }

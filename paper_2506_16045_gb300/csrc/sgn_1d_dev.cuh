@@ -222,8 +222,7 @@ __device__ __forceinline__ void deriv_pair(cplx<T>* buf, int n, int log2n, T kun
 }
 
 // ---------------------------------------------------------------------------------------
-// Size-class dispatch: NT = clamp(n/8, 32, 512) threads, MAXB = n/(4 NT) butterflies
-// per thread per radix-4 stage.
+// Size classes (one per log2 n).
 // ---------------------------------------------------------------------------------------
 template <int V>
 using IC = std::integral_constant<int, V>;
@@ -231,8 +230,9 @@ using IC = std::integral_constant<int, V>;
 // One launch per size class.  When a layout holds several classes they run concurrently on
 // the layout's side streams (event fork from `s`, join back into `s`; largest class first),
 // so a class that occupies few SMs does not leave the rest of the GPU idle.
-template <typename Fn>
-cudaError_t for_each_class(const Layout1d& lay, cudaStream_t s, Fn&& fn) {
+// call(l, first, num, stream) launches class l = log2 n.
+template <typename Call>
+cudaError_t fan_classes(const Layout1d& lay, cudaStream_t s, Call&& call) {
   int ncls = 0;
   for (int l = 3; l <= 13; ++l) ncls += lay.class_end[l] > lay.class_begin[l];
   const bool fan = ncls > 1 && lay.side[0] != nullptr;
@@ -246,17 +246,7 @@ cudaError_t for_each_class(const Layout1d& lay, cudaStream_t s, Fn&& fn) {
       cs = lay.side[ci];
       if (cudaStreamWaitEvent(cs, lay.fork, 0) != cudaSuccess) return cudaGetLastError();
     }
-    cudaError_t err = cudaSuccess;
-    switch (l) {
-      case 3: case 4: case 5: case 6: case 7: err = fn(IC<32>{}, IC<1>{}, l, b, e - b, cs); break;
-      case 8: err = fn(IC<32>{}, IC<2>{}, l, b, e - b, cs); break;
-      case 9: err = fn(IC<64>{}, IC<2>{}, l, b, e - b, cs); break;
-      case 10: err = fn(IC<128>{}, IC<2>{}, l, b, e - b, cs); break;
-      case 11: err = fn(IC<256>{}, IC<2>{}, l, b, e - b, cs); break;
-      case 12: err = fn(IC<512>{}, IC<2>{}, l, b, e - b, cs); break;
-      case 13: err = fn(IC<512>{}, IC<4>{}, l, b, e - b, cs); break;
-      default: return cudaErrorInvalidValue;
-    }
+    const cudaError_t err = call(l, b, e - b, cs);
     if (err != cudaSuccess) return err;
     if (fan) {
       if (cudaEventRecord(lay.join[ci], cs) != cudaSuccess ||
@@ -266,6 +256,45 @@ cudaError_t for_each_class(const Layout1d& lay, cudaStream_t s, Fn&& fn) {
     ++ci;
   }
   return cudaSuccess;
+}
+
+// Size-class dispatch for the cta_fft kernels: NT = clamp(n/8, 32, 512) threads, MAXB =
+// n/(4 NT) butterflies per thread per radix-4 stage.
+template <typename Fn>
+cudaError_t for_each_class(const Layout1d& lay, cudaStream_t s, Fn&& fn) {
+  return fan_classes(lay, s, [&](int l, int b, int num, cudaStream_t cs) -> cudaError_t {
+    switch (l) {
+      case 3: case 4: case 5: case 6: case 7: return fn(IC<32>{}, IC<1>{}, l, b, num, cs);
+      case 8: return fn(IC<32>{}, IC<2>{}, l, b, num, cs);
+      case 9: return fn(IC<64>{}, IC<2>{}, l, b, num, cs);
+      case 10: return fn(IC<128>{}, IC<2>{}, l, b, num, cs);
+      case 11: return fn(IC<256>{}, IC<2>{}, l, b, num, cs);
+      case 12: return fn(IC<512>{}, IC<2>{}, l, b, num, cs);
+      case 13: return fn(IC<512>{}, IC<4>{}, l, b, num, cs);
+      default: return cudaErrorInvalidValue;
+    }
+  });
+}
+
+// Size-class dispatch for the register-FFT kernels, templated on log2 n.
+template <typename Fn>
+cudaError_t for_each_size(const Layout1d& lay, cudaStream_t s, Fn&& fn) {
+  return fan_classes(lay, s, [&](int l, int b, int num, cudaStream_t cs) -> cudaError_t {
+    switch (l) {
+      case 3: return fn(IC<3>{}, b, num, cs);
+      case 4: return fn(IC<4>{}, b, num, cs);
+      case 5: return fn(IC<5>{}, b, num, cs);
+      case 6: return fn(IC<6>{}, b, num, cs);
+      case 7: return fn(IC<7>{}, b, num, cs);
+      case 8: return fn(IC<8>{}, b, num, cs);
+      case 9: return fn(IC<9>{}, b, num, cs);
+      case 10: return fn(IC<10>{}, b, num, cs);
+      case 11: return fn(IC<11>{}, b, num, cs);
+      case 12: return fn(IC<12>{}, b, num, cs);
+      case 13: return fn(IC<13>{}, b, num, cs);
+      default: return cudaErrorInvalidValue;
+    }
+  });
 }
 
 template <typename K>

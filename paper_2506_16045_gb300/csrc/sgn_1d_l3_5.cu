@@ -1,0 +1,12 @@
+// 1d solve and right-hand-side kernels for n = 2^3 .. 2^5 (sgn_1d_pcg.cuh, sgn_1d_rhs.cuh).
+#include "sgn_1d_pcg.cuh"
+#include "sgn_1d_rhs.cuh"
+
+namespace sgn {
+template cudaError_t pcg1d_launch<3>(const PcgArgs&, int, int, cudaStream_t);
+template cudaError_t pcg1d_launch<4>(const PcgArgs&, int, int, cudaStream_t);
+template cudaError_t pcg1d_launch<5>(const PcgArgs&, int, int, cudaStream_t);
+template cudaError_t rhs1d_launch<3>(const RhsArgs&, int, int, cudaStream_t);
+template cudaError_t rhs1d_launch<4>(const RhsArgs&, int, int, cudaStream_t);
+template cudaError_t rhs1d_launch<5>(const RhsArgs&, int, int, cudaStream_t);
+}  // namespace sgn

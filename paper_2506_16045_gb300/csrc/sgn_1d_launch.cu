@@ -1,0 +1,85 @@
+// Launchers of the register-FFT 1d kernels: one launch per size class.  The kernels
+// (sgn_1d_pcg.cuh: a5/a6 solve, sgn_1d_rhs.cuh: a7 right-hand side) are instantiated per
+// size in the sgn_1d_l*.cu translation units, which compile in parallel.
+#include "sgn_1d_pcg.cuh"
+#include "sgn_1d_rhs.cuh"
+
+namespace sgn {
+
+extern template cudaError_t pcg1d_launch<3>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<4>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<5>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<6>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<7>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<8>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<9>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<10>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<11>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<12>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<13>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<3>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<4>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<5>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<6>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<7>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<8>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<9>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<10>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<11>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<12>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<13>(const RhsArgs&, int, int, cudaStream_t);
+
+cudaError_t launch_pcg1d(const Layout1d& lay, const void* tw64, const void* tw32, int precision,
+                         const double* eta, const double* hx, const double* b, double* x,
+                         const SolveRec* given, int kind, double rtol, double rtol_inner,
+                         int maxit, int max_refine, SolveRec* rec, void* ws, float* coef_lo,
+                         cudaStream_t s) {
+  PcgArgs a;
+  a.insts = lay.d_inst;
+  a.ids = lay.d_ids;
+  a.tw64 = static_cast<const cplx<double>*>(tw64);
+  a.twdf = reinterpret_cast<const cplx<df>*>(static_cast<const char*>(tw32) + kTw32Bytes);
+  a.eta = eta;
+  a.hx = hx;
+  a.b = b;
+  a.x = x;
+  a.given = given;
+  a.kind = kind;
+  a.rtol = rtol;
+  a.rtol_inner = rtol_inner;
+  a.maxit = maxit;
+  a.max_refine = max_refine;
+  a.rec = rec;
+  a.ws = static_cast<cplx<double>*>(ws);
+  a.coef_lo = precision == SGN_PREC_MIXED ? coef_lo : nullptr;
+  a.precision = precision;
+  return d1::for_each_size(lay, s, [&](auto Lc, int first, int num, cudaStream_t cs) {
+    return pcg1d_launch<decltype(Lc)::value>(a, first, num, cs);
+  });
+}
+
+cudaError_t launch_rhs1d(const Layout1d& lay, const void* tw64, const void* tw32, int precision,
+                         double g, const double* eta, const double* u, const double* h,
+                         const double* hx, double* f_eta, double* f_U, double* scratch,
+                         cudaStream_t s) {
+  RhsArgs a;
+  a.insts = lay.d_inst;
+  a.ids = lay.d_ids;
+  a.tw64 = static_cast<const cplx<double>*>(tw64);
+  a.twdf = reinterpret_cast<const cplx<df>*>(static_cast<const char*>(tw32) + kTw32Bytes);
+  a.g = g;
+  a.eta = eta;
+  a.u = u;
+  a.h = h;
+  a.hx = hx;
+  a.f_eta = f_eta;
+  a.f_U = f_U;
+  a.scratch = scratch;
+  a.P = lay.points;
+  a.precision = precision;
+  return d1::for_each_size(lay, s, [&](auto Lc, int first, int num, cudaStream_t cs) {
+    return rhs1d_launch<decltype(Lc)::value>(a, first, num, cs);
+  });
+}
+
+}  // namespace sgn

@@ -1,0 +1,634 @@
+// a5/a6: preconditioned conjugate gradients for G_{eta,h} x = b in 1d (§3.2, Eq:PCGLinSyst,
+// preconditioner A of §4), one CTA per instance, in spectral space (see sgn_1d.cu for the
+// formulation) on the register-blocked FFT of sgn_fft1d.cuh.
+//
+//   MIXED = false: float64 PCG from the caller's initial guess; the Krylov vectors are
+//                  half spectra in the workspace, each thread touching only the modes of
+//                  its slots (so no barrier guards them).
+//   MIXED = true : iterative refinement in double-float (~48-bit) precision.  Each pass
+//                  computes the residual r = b - G x with double-float FFTs and
+//                  coefficients, stops when sqrt(r.A^{-1}r) <= rtol sqrt(b.A^{-1}b), and
+//                  otherwise solves G d = r / ||r||_{A^{-1}} by float32 PCG (to rtol_inner,
+//                  or adaptively to 0.3 rtol / current ratio within [1e-6, 0.1]) and updates
+//                  x += ||r||_{A^{-1}} d in double-float.  The float32 PCG keeps r and p in
+//                  registers (the paired spectral layout makes every per-mode step local to
+//                  a thread) and the correction d in shared memory; its dot products reduce
+//                  in double-float and one thread forms alpha, beta and the stopping test.
+//
+// Workspace slots per instance (half spectra of n/2 + 1 modes, 16 bytes per mode each):
+//   0: b^ (high precision), 1: x^ (high), 2: r^ and 3: p^ (float64 path only).
+// The mixed path also keeps the remainders of its double-float coefficients in coef_lo
+// (3 floats per point).
+#pragma once
+#include <type_traits>
+
+#include "sgn_1d_dev.cuh"
+#include "sgn_fft1d.cuh"
+
+namespace sgn {
+
+// Arguments of one solve launch (kernel parameter space: read on use, not held in registers).
+struct PcgArgs {
+  const Inst1d* insts;
+  const int* ids;
+  const cplx<double>* tw64;
+  const cplx<df>* twdf;
+  const double* eta;
+  const double* hx;
+  const double* b;
+  double* x;
+  const SolveRec* given;
+  int kind;
+  double rtol, rtol_inner;
+  int maxit, max_refine;
+  SolveRec* rec;
+  cplx<double>* ws;
+  float* coef_lo;
+  int precision;
+};
+
+template <int L>
+cudaError_t pcg1d_launch(const PcgArgs& a, int first, int num, cudaStream_t s);
+
+namespace pcg1d {
+
+using namespace d1;
+using f1::Geo;
+using f1::Plan;
+using f1::XBuf;
+
+// Shared memory of one solve CTA: [exchange planes | (mixed) float32 coefficients]; the
+// float32 correction d of the inner solve sits after the float32 exchange plane, inside the
+// double-float planes, which are idle while the inner solve runs.
+template <int L>
+struct SmemPcg {
+  using PL = Plan<L>;
+  static constexpr size_t n = (size_t)PL::n;
+  static constexpr size_t off_d = 8 * n;
+  static constexpr size_t d_bytes = (size_t)(PL::RP + 1) * PL::NT * 8;
+  static constexpr size_t off_c =
+      ((16 * n > off_d + d_bytes ? 16 * n : off_d + d_bytes) + 15) / 16 * 16;
+  static constexpr size_t mixed = off_c + 12 * n;
+  static constexpr size_t fp64 = 16 * n;
+};
+
+struct PcgScalars {     // inner float32 PCG
+  float rz, alpha, beta;
+  int state;            // 0 iterate, 1 converged, 2 breakdown, 3 iteration cap
+};
+
+struct PassScalars {    // refinement pass
+  double ratio;         // sqrt(r.A^{-1}r) / sqrt(b.A^{-1}b)
+  df unscale;           // ||r||_{A^{-1}}
+  float scale;          // 1 / ||r||_{A^{-1}}
+  float tin2;           // (inner tolerance)^2
+  int go;               // 1: run another inner solve
+  int status;
+};
+
+// Slot (b, s) of the paired layout for slot number q < RP (compile-time after unrolling).
+template <int L>
+struct Slot {
+  static constexpr int b(int q) { return q / Plan<L>::HS; }
+  static constexpr int s(int q) { return q % Plan<L>::HS; }
+  static constexpr int reg(int q) { return b(q) * Plan<L>::RP + s(q); }
+};
+
+template <int L, bool MIXED>
+__global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
+    k_pcg1d(const __grid_constant__ PcgArgs A, int first) {
+  using PL = Plan<L>;
+  using SL = Slot<L>;
+  using SM = SmemPcg<L>;
+  constexpr int n = PL::n, h = n / 2, E = PL::E, RP = PL::RP, HS = PL::HS, NTA = PL::NTA;
+  constexpr int NT = PL::NT, W = NT / 32;
+  using TH = typename std::conditional<MIXED, df, double>::type;   // high precision
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[W + 1];
+  __shared__ df slots[2 * W];
+  __shared__ PcgScalars sc;
+  __shared__ PassScalars ps;
+
+  const int t = threadIdx.x;
+  const Geo<L> g(t);
+  const bool t0 = (t == 0);
+  const int id = A.ids[first + blockIdx.x];
+  const Inst1d I = A.insts[id];
+  const double* eta = A.eta + I.off;
+  const double* hx = A.hx + I.off;
+  const double* b = A.b + I.off;
+  double* x = A.x + I.off;
+  const long long S = h + 1;
+  cplx<TH>* Bh = reinterpret_cast<cplx<TH>*>(A.ws + I.ws);
+  cplx<TH>* Xh = reinterpret_cast<cplx<TH>*>(A.ws + I.ws + S);
+  const double rtol = A.rtol, rtol_inner = A.rtol_inner;
+  const int maxit = A.maxit, max_refine = A.max_refine;
+
+  // ---- a1: coefficients (or the caller's)
+  SolveRec R = {};
+  if (A.given) {
+    R = A.given[id];
+    R.status = SGN_OK;
+  } else {
+    coeffs_block<NT>(eta, hx, n, A.kind, red, R);
+  }
+  R.iters = 0;
+  R.refinements = 0;
+  R.ratio = 0.0;
+  if (R.status != SGN_OK) {
+    if (t0) A.rec[id] = R;
+    return;
+  }
+  const double kunit = 2.0 * kPi / I.L;
+  const float kf = (float)kunit, sigf = (float)R.sigma, alf = (float)R.alpha;
+  const XBuf<TH> XH(smem, n);
+  // float32 preconditioner symbol 1 / (sigma + alpha k^2) of mode m < n/2 (Nyquist: 1/sigma)
+  auto dinv = [&](int m) {
+    const float k = kf * (float)m;
+    return recip(sigf + alf * k * k);
+  };
+  const float dN = recip(sigf);
+
+  float* c32 = reinterpret_cast<float*>(smem + SM::off_c);
+  const float* clo = A.coef_lo ? A.coef_lo + 3 * I.off : nullptr;
+  if constexpr (MIXED) split_coefficients<NT>(eta, hx, n, c32, A.coef_lo + 3 * I.off);
+
+  // ---- b^ and x0^ from one transform of b + i x0
+  {
+    const typename f1::TwOf<TH>::type twh{
+        MIXED ? reinterpret_cast<const cplx<TH>*>(A.twdf) : reinterpret_cast<const cplx<TH>*>(A.tw64)};
+    cplx<TH> v[E];
+    if (g.act) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int j = t + e * NTA;
+        v[e] = mk(num<TH>(b[j]), num<TH>(x[j]));
+      }
+    }
+    f1::fft_fwd<TH, L>(XH, v, g, twh);
+    float bb = 0.0f;
+    if (g.act) {
+#pragma unroll
+      for (int q = 0; q < RP; ++q) {
+        const int m = g.mode(SL::b(q), SL::s(q));
+        const cplx<TH> y = v[SL::reg(q)];
+        const cplx<TH> ym = conj(f1::mirror_get<L>(v, t0, SL::b(q), SL::s(q)));
+        const cplx<TH> s = y + ym, d = mul_mi(y - ym);
+        const cplx<TH> bh = mk(half(s.x), half(s.y));
+        Bh[m] = bh;
+        Xh[m] = mk(half(d.x), half(d.y));
+        const float bx = (float)to_f64(bh.x), by = (float)to_f64(bh.y);
+        bb += ((t0 && q == 0) ? 1.0f : 2.0f) * (bx * bx + by * by) * dinv(m);
+      }
+      if (t0) {
+        const cplx<TH> y = v[HS];
+        Bh[h] = mk(y.x, from_int<TH>(0));
+        Xh[h] = mk(y.y, from_int<TH>(0));
+        const float bx = (float)to_f64(y.x);
+        bb += bx * bx * dN;
+      }
+    }
+    block_sum_df<NT>(bb, slots, [&](float hi, float lo) {
+      ps.ratio = (double)hi + (double)lo;        // b.A^{-1}b
+    });
+  }
+  const double bb = ps.ratio;
+  const double bnorm = sqrt(bb);
+  __syncthreads();                               // ps is reused below
+  if (!(bnorm > 0.0)) {
+    if (g.act)
+#pragma unroll
+      for (int e = 0; e < E; ++e) x[t + e * NTA] = 0.0;
+    R.status = (bb == 0.0) ? SGN_OK : SGN_ERR_BREAKDOWN;
+    if (t0) A.rec[id] = R;
+    return;
+  }
+
+  int iters = 0;
+  int status = SGN_OK;
+  if constexpr (!MIXED) {
+    // ------------------------------------------------------------------ float64 PCG
+    cplx<double>* Rh = A.ws + I.ws + 2 * S;
+    cplx<double>* Ph = A.ws + I.ws + 3 * S;
+    const CoefGlobal64 coef64{eta, hx};
+    const double tol_abs = rtol * bnorm;
+    const double inv_n = 1.0 / (double)n;
+    const f1::TwTab<double> tw{A.tw64};
+    const double isig = 1.0 / R.sigma;
+    auto dinv64 = [&](int m) {
+      const double k = kunit * (double)m;
+      return 1.0 / (R.sigma + R.alpha * k * k);
+    };
+    // (G v)^ of the slots of the half spectrum Vh into gq / gN
+    auto matvec = [&](const cplx<double>* __restrict__ Vh, cplx<double>(&gq)[RP],
+                      cplx<double>& gN) {
+      cplx<double> v[E];
+      if (g.act) {
+#pragma unroll
+        for (int q = 0; q < RP; ++q) {
+          const double k = kunit * (double)g.mode(SL::b(q), SL::s(q));
+          const cplx<double> p = Vh[g.mode(SL::b(q), SL::s(q))];
+          if (t0 && q == 0) {
+            v[0] = mk(p.x, 0.0);
+          } else {
+            v[SL::reg(q)] = p * (1.0 - k);
+            f1::mirror_set<L>(v, t0, SL::b(q), SL::s(q), conj(p) * (1.0 + k));
+          }
+        }
+        if (t0) v[HS] = mk(Vh[h].x, 0.0);
+      }
+      f1::fft_inv<double, L>(XH, v, g, tw);
+      if (g.act) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const double pv = v[e].x * inv_n, px = v[e].y * inv_n;
+          double c1, c2, c3;
+          coef64(t + e * NTA, c1, c2, c3);
+          v[e] = mk(c1 * pv + c2 * px, c2 * pv + c3 * px);
+        }
+      }
+      f1::fft_fwd<double, L>(XH, v, g, tw);
+      if (g.act) {
+#pragma unroll
+        for (int q = 0; q < RP; ++q) {
+          const double k = kunit * (double)g.mode(SL::b(q), SL::s(q));
+          const cplx<double> y = v[SL::reg(q)];
+          const cplx<double> ym = conj(f1::mirror_get<L>(v, t0, SL::b(q), SL::s(q)));
+          const cplx<double> s = y * (1.0 - k) + ym * (1.0 + k);
+          gq[q] = mk(0.5 * s.x, 0.5 * s.y);
+        }
+        if (t0) gN = mk(v[HS].x, 0.0);
+      }
+    };
+    // r = b - G x0, p = A^{-1} r
+    double rz;
+    {
+      cplx<double> gq[RP], gN = mk(0.0, 0.0);
+      matvec(Xh, gq, gN);
+      double loc = 0.0;
+      if (g.act) {
+#pragma unroll
+        for (int q = 0; q < RP; ++q) {
+          const int m = g.mode(SL::b(q), SL::s(q));
+          const cplx<double> r = Bh[m] - gq[q];
+          const double di = dinv64(m);
+          Rh[m] = r;
+          Ph[m] = r * di;
+          loc += ((t0 && q == 0) ? 1.0 : 2.0) * (r.x * r.x + r.y * r.y) * di;
+        }
+        if (t0) {
+          const cplx<double> r = Bh[h] - gN;
+          Rh[h] = r;
+          Ph[h] = r * isig;
+          loc += (r.x * r.x + r.y * r.y) * isig;
+        }
+      }
+      rz = block_sum<NT>(loc, red);
+    }
+    while (sqrt(rz) > tol_abs) {
+      if (iters >= maxit) {
+        status = SGN_ERR_NOT_CONVERGED;
+        break;
+      }
+      cplx<double> gq[RP], gN = mk(0.0, 0.0);
+      matvec(Ph, gq, gN);
+      double pq_loc = 0.0;
+      if (g.act) {
+#pragma unroll
+        for (int q = 0; q < RP; ++q) {
+          const cplx<double> p = Ph[g.mode(SL::b(q), SL::s(q))];
+          pq_loc += ((t0 && q == 0) ? 1.0 : 2.0) * (p.x * gq[q].x + p.y * gq[q].y);
+        }
+        if (t0) pq_loc += Ph[h].x * gN.x;
+      }
+      const double pq = block_sum<NT>(pq_loc, red);
+      if (!(pq > 0.0) || !isfinite(pq)) {
+        status = SGN_ERR_BREAKDOWN;
+        break;
+      }
+      const double at = rz / pq;
+      double rz_loc = 0.0;
+      if (g.act) {
+#pragma unroll
+        for (int q = 0; q < RP; ++q) {
+          const int m = g.mode(SL::b(q), SL::s(q));
+          Xh[m] = Xh[m] + Ph[m] * at;
+          const cplx<double> r = Rh[m] - gq[q] * at;
+          Rh[m] = r;
+          rz_loc += ((t0 && q == 0) ? 1.0 : 2.0) * (r.x * r.x + r.y * r.y) * dinv64(m);
+        }
+        if (t0) {
+          Xh[h] = Xh[h] + Ph[h] * at;
+          const cplx<double> r = Rh[h] - gN * at;
+          Rh[h] = r;
+          rz_loc += (r.x * r.x + r.y * r.y) * isig;
+        }
+      }
+      const double rz_new = block_sum<NT>(rz_loc, red);
+      ++iters;
+      if (!isfinite(rz_new)) {
+        status = SGN_ERR_BREAKDOWN;
+        break;
+      }
+      const double beta = rz_new / rz;
+      rz = rz_new;
+      if (g.act) {
+#pragma unroll
+        for (int q = 0; q < RP; ++q) {
+          const int m = g.mode(SL::b(q), SL::s(q));
+          Ph[m] = Rh[m] * dinv64(m) + Ph[m] * beta;
+        }
+        if (t0) Ph[h] = Rh[h] * isig + Ph[h] * beta;
+      }
+    }
+    R.ratio = sqrt(rz) / bnorm;
+    // x = F^{-1} x^
+    cplx<double> v[E];
+    if (g.act) {
+#pragma unroll
+      for (int q = 0; q < RP; ++q) {
+        const cplx<double> xv = Xh[g.mode(SL::b(q), SL::s(q))];
+        if (t0 && q == 0) {
+          v[0] = mk(xv.x, 0.0);
+        } else {
+          v[SL::reg(q)] = xv;
+          f1::mirror_set<L>(v, t0, SL::b(q), SL::s(q), conj(xv));
+        }
+      }
+      if (t0) v[HS] = mk(Xh[h].x, 0.0);
+    }
+    f1::fft_inv<double, L>(XH, v, g, tw);
+    if (g.act)
+#pragma unroll
+      for (int e = 0; e < E; ++e) x[t + e * NTA] = v[e].x * inv_n;
+  } else {
+    // ------------------------------------------------------------------ mixed precision
+    const XBuf<float> XF(smem, n);
+    const f1::TwF32 twf;
+    const f1::TwTab<df> twd{A.twdf};
+    cplx<float>* D = reinterpret_cast<cplx<float>*>(smem + SM::off_d);   // [RP + 1][NT]
+    const df inv_n(1.0f / (float)n, 0.0f);                                 // exact
+    const float inv_nf = 1.0f / (float)n;
+    const df one(1.0f, 0.0f), zero(0.0f, 0.0f);
+    const df kh = num<df>(kunit);
+    int refinements = 0;
+    for (;;) {
+      // ---- double-float residual r^ = b^ - (G x)^, writing the real-space x on the way
+      cplx<float> rf[RP], rfN = mk(0.0f, 0.0f);
+      {
+        cplx<df> v[E];
+        if (g.act) {
+#pragma unroll
+          for (int q = 0; q < RP; ++q) {
+            const int m = g.mode(SL::b(q), SL::s(q));
+            const df k = kh * df((float)m, 0.0f);
+            const cplx<df> xv = Xh[m];
+            if (t0 && q == 0) {
+              v[0] = mk(xv.x, zero);
+            } else {
+              v[SL::reg(q)] = xv * (one - k);
+              f1::mirror_set<L>(v, t0, SL::b(q), SL::s(q), conj(xv) * (one + k));
+            }
+          }
+          if (t0) v[HS] = mk(Xh[h].x, zero);
+        }
+        f1::fft_inv<df, L>(XH, v, g, twd);
+        if (g.act) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int j = t + e * NTA;
+            const df pv = v[e].x * inv_n, px = v[e].y * inv_n;
+            x[j] = to_f64(pv);
+            const df c1(c32[j], clo[j]), c2(c32[n + j], clo[n + j]),
+                c3(c32[2 * n + j], clo[2 * n + j]);
+            v[e] = mk(c1 * pv + c2 * px, c2 * pv + c3 * px);
+          }
+        }
+        f1::fft_fwd<df, L>(XH, v, g, twd);
+        float rz_loc = 0.0f;
+        if (g.act) {
+#pragma unroll
+          for (int q = 0; q < RP; ++q) {
+            const int m = g.mode(SL::b(q), SL::s(q));
+            const df k = kh * df((float)m, 0.0f);
+            const cplx<df> y = v[SL::reg(q)];
+            const cplx<df> ym = conj(f1::mirror_get<L>(v, t0, SL::b(q), SL::s(q)));
+            const cplx<df> s = y * (one - k) + ym * (one + k);
+            const cplx<df> rr = Bh[m] - mk(half(s.x), half(s.y));
+            rf[q] = mk(rr.x.hi + rr.x.lo, rr.y.hi + rr.y.lo);
+            rz_loc += ((t0 && q == 0) ? 1.0f : 2.0f) *
+                      (rf[q].x * rf[q].x + rf[q].y * rf[q].y) * dinv(m);
+          }
+          if (t0) {
+            const df rr = Bh[h].x - v[HS].x;
+            rfN = mk(rr.hi + rr.lo, 0.0f);
+            rz_loc += rfN.x * rfN.x * dN;
+          }
+        }
+        // thread 0 decides the pass: converged, out of budget, or the next inner solve
+        block_sum_df<NT>(rz_loc, slots, [&](float hi, float lo) {
+          const double rz64 = (double)hi + (double)lo;
+          const double nr = sqrt(rz64);
+          const double ratio = nr / bnorm;
+          ps.ratio = ratio;
+          ps.go = 0;
+          ps.status = status;
+          if (ratio <= rtol || status != SGN_OK) return;
+          if (refinements >= max_refine || iters >= maxit) {
+            ps.status = SGN_ERR_NOT_CONVERGED;
+            return;
+          }
+          const double tin =
+              rtol_inner > 0.0 ? rtol_inner : fmin(0.1, fmax(1e-6, 0.3 * rtol / ratio));
+          ps.scale = (float)(1.0 / nr);
+          ps.unscale = df(nr);
+          ps.tin2 = (float)(tin * tin);
+          ps.go = 1;
+        });
+      }
+      R.ratio = ps.ratio;
+      status = ps.status;
+      if (!ps.go) break;
+      const float scale = ps.scale, tin2 = ps.tin2;
+      const df unscale = ps.unscale;
+
+      // ---- float32 PCG for G d = r / ||r||, r and p in registers, d in shared memory
+      const int it_before = iters;
+      int st_in = SGN_OK;
+      {
+        cplx<float> r[RP], p[RP], rN = mk(0.0f, 0.0f), pN = mk(0.0f, 0.0f);
+        int it = iters;
+        float loc = 0.0f;
+        if (g.act) {
+#pragma unroll
+          for (int q = 0; q < RP; ++q) {
+            const float di = dinv(g.mode(SL::b(q), SL::s(q)));
+            r[q] = rf[q] * scale;
+            p[q] = r[q] * di;
+            loc += ((t0 && q == 0) ? 1.0f : 2.0f) * (r[q].x * p[q].x + r[q].y * p[q].y);
+            D[q * NT + t] = mk(0.0f, 0.0f);
+          }
+          if (t0) {
+            rN = rfN * scale;
+            pN = rN * dN;
+            loc += rN.x * pN.x;
+            D[RP * NT] = mk(0.0f, 0.0f);
+          }
+        }
+        // (the previous barrier-separated readers of sc are done: ps was read after one)
+        block_sum_df<NT>(loc, slots + W, [&](float hi, float lo) {
+          const float rz = hi + lo;
+          sc.rz = rz;
+          sc.state = (rz <= tin2) ? 1 : (it >= maxit ? 3 : 0);
+        });
+        for (;;) {
+          const int state = sc.state;
+          if (state != 0) {
+            if (state == 3) st_in = SGN_ERR_NOT_CONVERGED;
+            if (state == 2) st_in = SGN_ERR_BREAKDOWN;
+            break;
+          }
+          cplx<float> v[E];
+          if (g.act) {
+#pragma unroll
+            for (int q = 0; q < RP; ++q) {
+              const float k = kf * (float)g.mode(SL::b(q), SL::s(q));
+              if (t0 && q == 0) {
+                v[0] = mk(p[0].x, 0.0f);
+              } else {
+                v[SL::reg(q)] = p[q] * (1.0f - k);
+                f1::mirror_set<L>(v, t0, SL::b(q), SL::s(q), conj(p[q]) * (1.0f + k));
+              }
+            }
+            if (t0) v[HS] = mk(pN.x, 0.0f);
+          }
+          f1::fft_inv<float, L>(XF, v, g, twf);
+          if (g.act) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              const int j = t + e * NTA;
+              const float pv = v[e].x * inv_nf, px = v[e].y * inv_nf;
+              const float c1 = c32[j], c2 = c32[n + j], c3 = c32[2 * n + j];
+              v[e] = mk(c1 * pv + c2 * px, c2 * pv + c3 * px);
+            }
+          }
+          f1::fft_fwd<float, L>(XF, v, g, twf);
+          cplx<float> gq[RP], gN = mk(0.0f, 0.0f);
+          float pq_loc = 0.0f;
+          if (g.act) {
+#pragma unroll
+            for (int q = 0; q < RP; ++q) {
+              const float k = kf * (float)g.mode(SL::b(q), SL::s(q));
+              const cplx<float> y = v[SL::reg(q)];
+              const cplx<float> ym = conj(f1::mirror_get<L>(v, t0, SL::b(q), SL::s(q)));
+              const cplx<float> s = y * (1.0f - k) + ym * (1.0f + k);
+              gq[q] = mk(0.5f * s.x, 0.5f * s.y);
+              pq_loc += ((t0 && q == 0) ? 1.0f : 2.0f) * (p[q].x * gq[q].x + p[q].y * gq[q].y);
+            }
+            if (t0) {
+              gN = mk(v[HS].x, 0.0f);
+              pq_loc += pN.x * gN.x;
+            }
+          }
+          block_sum_df<NT>(pq_loc, slots, [&](float hi, float lo) {
+            const float pq = hi + lo;
+            if (!(pq > 0.0f) || !isfinite(pq)) sc.state = 2;
+            else sc.alpha = sc.rz / pq;
+          });
+          if (sc.state == 2) {
+            st_in = SGN_ERR_BREAKDOWN;
+            break;
+          }
+          const float at = sc.alpha;
+          float rz_loc = 0.0f;
+          if (g.act) {
+#pragma unroll
+            for (int q = 0; q < RP; ++q) {
+              const float di = dinv(g.mode(SL::b(q), SL::s(q)));
+              D[q * NT + t] = D[q * NT + t] + p[q] * at;
+              r[q] = r[q] - gq[q] * at;
+              rz_loc += ((t0 && q == 0) ? 1.0f : 2.0f) *
+                        (r[q].x * r[q].x + r[q].y * r[q].y) * di;
+            }
+            if (t0) {
+              D[RP * NT] = D[RP * NT] + pN * at;
+              rN = rN - gN * at;
+              rz_loc += rN.x * rN.x * dN;
+            }
+          }
+          ++it;
+          block_sum_df<NT>(rz_loc, slots + W, [&](float hi, float lo) {
+            const float rz_new = hi + lo;
+            if (!isfinite(rz_new)) {
+              sc.state = 2;
+            } else {
+              sc.beta = rz_new / sc.rz;
+              sc.rz = rz_new;
+              sc.state = (rz_new <= tin2) ? 1 : (it >= maxit ? 3 : 0);
+            }
+          });
+          if (sc.state == 2) {
+            st_in = SGN_ERR_BREAKDOWN;
+            break;
+          }
+          const float beta = sc.beta;
+          if (g.act) {
+#pragma unroll
+            for (int q = 0; q < RP; ++q) {
+              const float di = dinv(g.mode(SL::b(q), SL::s(q)));
+              p[q] = r[q] * di + p[q] * beta;
+            }
+            if (t0) pN = rN * dN + pN * beta;
+          }
+        }
+        iters = it;
+      }
+      // A float32 breakdown after some progress only means float32 has resolved what it
+      // can: keep the correction and let the next refinement pass decide.
+      if (st_in == SGN_ERR_BREAKDOWN && iters == it_before) status = SGN_ERR_BREAKDOWN;
+      ++refinements;
+      // x^ += ||r|| d in double-float (each thread updates the modes of its own slots)
+      if (g.act) {
+#pragma unroll
+        for (int q = 0; q < RP; ++q) {
+          const int m = g.mode(SL::b(q), SL::s(q));
+          const cplx<float> d = D[q * NT + t];
+          const cplx<df> xv = Xh[m];
+          Xh[m] = mk(xv.x + df(d.x, 0.0f) * unscale, xv.y + df(d.y, 0.0f) * unscale);
+        }
+        if (t0) {
+          const cplx<float> d = D[RP * NT];
+          const cplx<df> xv = Xh[h];
+          Xh[h] = mk(xv.x + df(d.x, 0.0f) * unscale, xv.y);
+        }
+      }
+    }
+    R.refinements = refinements;
+  }
+  R.iters = iters;
+  R.status = status;
+  if (t0) A.rec[id] = R;
+}
+
+}  // namespace pcg1d
+
+template <int L>
+cudaError_t pcg1d_launch(const PcgArgs& a, int first, int num, cudaStream_t s) {
+  using PL = f1::Plan<L>;
+  if (a.precision == SGN_PREC_MIXED) {
+    auto k = pcg1d::k_pcg1d<L, true>;
+    const size_t sm = pcg1d::SmemPcg<L>::mixed;
+    cudaError_t e = d1::set_smem(k, sm);
+    if (e) return e;
+    k<<<num, PL::NT, sm, s>>>(a, first);
+  } else {
+    auto k = pcg1d::k_pcg1d<L, false>;
+    const size_t sm = pcg1d::SmemPcg<L>::fp64;
+    cudaError_t e = d1::set_smem(k, sm);
+    if (e) return e;
+    k<<<num, PL::NT, sm, s>>>(a, first);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace sgn

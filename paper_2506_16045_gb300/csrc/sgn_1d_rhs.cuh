@@ -1,0 +1,166 @@
+// a7: right-hand side of Eq:DAE_DSWE with F from Def:bigF, one CTA per 1d instance on the
+// register-blocked FFT of sgn_fft1d.cuh, in number type T (float64 for the float64 path,
+// double-float for the mixed path).  Four derivative pairs:
+//   (u, eta u) -> (d, m);  (zeta, s) -> (zeta_x, s_x) with s = h_x u;  d -> d_x;
+//   Phi' -> Phi'_x with Phi' = eta^3 Q/3 + eta^2 m d + eta^2 S/2 + eta m s - eta u^2 (the
+//   flux -(eta u^2)_x folded in), Q = u d_x - d^2, S = u s_x (reading R6);
+// and f_eta = -m, f_U = -g eta zeta_x + Phi'_x - h_x Psi, Psi = eta^2 Q/2 + eta m d + eta S
+// + m s.  Every pointwise step works on the thread's natural elements j = t + e NTA, so the
+// intermediate planes in `scratch` are written and read by the same thread.
+#pragma once
+#include <type_traits>
+
+#include "sgn_1d_dev.cuh"
+#include "sgn_fft1d.cuh"
+
+namespace sgn {
+
+struct RhsArgs {
+  const Inst1d* insts;
+  const int* ids;
+  const cplx<double>* tw64;
+  const cplx<df>* twdf;
+  double g;
+  const double* eta;
+  const double* u;
+  const double* h;
+  const double* hx;
+  double* f_eta;
+  double* f_U;
+  double* scratch;        // 5 planes of P values (8 bytes each)
+  long long P;
+  int precision;
+};
+
+template <int L>
+cudaError_t rhs1d_launch(const RhsArgs& a, int first, int num, cudaStream_t s);
+
+namespace rhs1d {
+
+using namespace d1;
+using f1::Geo;
+using f1::Plan;
+using f1::XBuf;
+
+// v <- D v for the two real fields packed in v (natural registers in and out): forward
+// transform, i k_m / n on every mode of the paired layout (Nyquist 0), inverse transform.
+template <typename T, int L>
+__device__ __forceinline__ void deriv_pair(const XBuf<T>& X, cplx<T> (&v)[Plan<L>::E],
+                                           const Geo<L>& g, T kn, const f1::TwTab<T>& tw) {
+  using PL = Plan<L>;
+  f1::fft_fwd<T, L>(X, v, g, tw);
+  if (g.act) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int s = 0; s < PL::RP; ++s) {
+        const T k = kn * from_int<T>(wave_index(g.mode(b, s), PL::n));
+        v[b * PL::RP + s] = mul_pi(v[b * PL::RP + s]) * k;
+      }
+  }
+  f1::fft_inv<T, L>(X, v, g, tw);
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
+    k_rhs1d(const __grid_constant__ RhsArgs A, int first) {
+  using PL = Plan<L>;
+  constexpr int n = PL::n, E = PL::E, NTA = PL::NTA;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int t = threadIdx.x;
+  const Geo<L> g(t);
+  const Inst1d I = A.insts[A.ids[first + blockIdx.x]];
+  const T kn = num<T>(2.0 * kPi / I.L / (double)n);
+  const T third = num<T>(1.0 / 3.0);
+  const T gT = num<T>(A.g);
+  const XBuf<T> X(smem, n);
+  const f1::TwTab<T> tw{std::is_same<T, df>::value
+                            ? reinterpret_cast<const cplx<T>*>(A.twdf)
+                            : reinterpret_cast<const cplx<T>*>(A.tw64)};
+  const double* eta = A.eta + I.off;
+  const double* u = A.u + I.off;
+  const double* hh = A.h + I.off;
+  const double* hx = A.hx + I.off;
+  T* sd = reinterpret_cast<T*>(A.scratch + I.off);              // d = u_x
+  T* sm = reinterpret_cast<T*>(A.scratch + A.P + I.off);        // m = (eta u)_x
+  T* szx = reinterpret_cast<T*>(A.scratch + 2 * A.P + I.off);   // zeta_x
+  T* ssx = reinterpret_cast<T*>(A.scratch + 3 * A.P + I.off);   // s_x
+  T* spsi = reinterpret_cast<T*>(A.scratch + 4 * A.P + I.off);  // Psi
+  cplx<T> v[E];
+  if (g.act) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int j = t + e * NTA;
+      const T uj = num<T>(u[j]);
+      v[e] = mk(uj, num<T>(eta[j]) * uj);
+    }
+  }
+  deriv_pair<T, L>(X, v, g, kn, tw);
+  if (g.act) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int j = t + e * NTA;
+      sd[j] = v[e].x;
+      sm[j] = v[e].y;
+      v[e] = mk(num<T>(eta[j] - hh[j]), num<T>(hx[j]) * num<T>(u[j]));
+    }
+  }
+  deriv_pair<T, L>(X, v, g, kn, tw);
+  if (g.act) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int j = t + e * NTA;
+      szx[j] = v[e].x;
+      ssx[j] = v[e].y;
+      v[e] = mk(sd[j], from_int<T>(0));
+    }
+  }
+  deriv_pair<T, L>(X, v, g, kn, tw);
+  if (g.act) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int j = t + e * NTA;
+      const T ej = num<T>(eta[j]), uj = num<T>(u[j]), d = sd[j], m = sm[j];
+      const T s = num<T>(hx[j]) * uj;
+      const T Q = uj * v[e].x - d * d;
+      const T Sv = uj * ssx[j];
+      const T e2 = ej * ej;
+      const T md = m * d;
+      const T Phi = e2 * ej * Q * third + e2 * md + half(e2 * Sv) + ej * m * s - ej * uj * uj;
+      spsi[j] = half(e2 * Q) + ej * md + ej * Sv + m * s;
+      v[e] = mk(Phi, from_int<T>(0));
+    }
+  }
+  deriv_pair<T, L>(X, v, g, kn, tw);
+  if (g.act) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int j = t + e * NTA;
+      A.f_eta[I.off + j] = -to_f64(sm[j]);
+      const T fU = v[e].x - gT * num<T>(eta[j]) * szx[j] - num<T>(hx[j]) * spsi[j];
+      A.f_U[I.off + j] = to_f64(fU);
+    }
+  }
+}
+
+}  // namespace rhs1d
+
+template <int L>
+cudaError_t rhs1d_launch(const RhsArgs& a, int first, int num, cudaStream_t s) {
+  using PL = f1::Plan<L>;
+  const size_t sm = (size_t)16 << L;
+  if (a.precision == SGN_PREC_MIXED) {
+    auto k = rhs1d::k_rhs1d<df, L>;
+    cudaError_t e = d1::set_smem(k, sm);
+    if (e) return e;
+    k<<<num, PL::NT, sm, s>>>(a, first);
+  } else {
+    auto k = rhs1d::k_rhs1d<double, L>;
+    cudaError_t e = d1::set_smem(k, sm);
+    if (e) return e;
+    k<<<num, PL::NT, sm, s>>>(a, first);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace sgn

@@ -1,0 +1,7 @@
+// 1d right-hand-side kernels for n = 2^12 (sgn_1d_rhs.cuh), a translation unit of its own so
+// the large instantiations compile in parallel.
+#include "sgn_1d_rhs.cuh"
+
+namespace sgn {
+template cudaError_t rhs1d_launch<12>(const RhsArgs&, int, int, cudaStream_t);
+}  // namespace sgn
