@@ -32,7 +32,7 @@ extern template cudaError_t rhs1d_launch<13>(const RhsArgs&, int, int, cudaStrea
 cudaError_t launch_pcg1d(const Layout1d& lay, const void* tw64, const void* tw32, int precision,
                          const double* eta, const double* hx, const double* b, double* x,
                          const SolveRec* given, int kind, double rtol, double rtol_inner,
-                         int maxit, int max_refine, SolveRec* rec, void* ws, float* coef_lo,
+                         int maxit, int max_refine, SolveRec* rec, void* ws, float* coef_df,
                          cudaStream_t s) {
   PcgArgs a;
   a.insts = lay.d_inst;
@@ -51,7 +51,7 @@ cudaError_t launch_pcg1d(const Layout1d& lay, const void* tw64, const void* tw32
   a.max_refine = max_refine;
   a.rec = rec;
   a.ws = static_cast<cplx<double>*>(ws);
-  a.coef_lo = precision == SGN_PREC_MIXED ? coef_lo : nullptr;
+  a.coef_df = precision == SGN_PREC_MIXED ? coef_df : nullptr;
   a.precision = precision;
   return d1::for_each_size(lay, s, [&](auto Lc, int first, int num, cudaStream_t cs) {
     return pcg1d_launch<decltype(Lc)::value>(a, first, num, cs);

@@ -17,8 +17,8 @@
 //
 // Workspace slots per instance (half spectra of n/2 + 1 modes, 16 bytes per mode each):
 //   0: b^ (high precision), 1: x^ (high), 2: r^ and 3: p^ (float64 path only).
-// The mixed path also keeps the remainders of its double-float coefficients in coef_lo
-// (3 floats per point).
+// The mixed path keeps its double-float coefficients c1, c2, c3 in coef_df (high parts,
+// then low parts: 6 floats per point) and float32 copies of eta and h_x in shared memory.
 #pragma once
 #include <type_traits>
 
@@ -43,7 +43,7 @@ struct PcgArgs {
   int maxit, max_refine;
   SolveRec* rec;
   cplx<double>* ws;
-  float* coef_lo;
+  float* coef_df;
   int precision;
 };
 
@@ -57,20 +57,50 @@ using f1::Geo;
 using f1::Plan;
 using f1::XBuf;
 
-// Shared memory of one solve CTA: [exchange planes | (mixed) float32 coefficients]; the
-// float32 correction d of the inner solve sits after the float32 exchange plane, inside the
-// double-float planes, which are idle while the inner solve runs.
+// Shared memory of one solve CTA (bytes):
+//   [0, 16 n)       exchange planes of the double-float / float64 transforms; the float32
+//                   inner solve uses [0, 8 n) for its exchanges and, after it, keeps its
+//                   thread-private slot arrays d (correction), r (residual) and the
+//                   preconditioner symbol 1/(sigma + alpha k^2), [RP + 1][NT] each;
+//   [off_e, +8 n)   (mixed) float32 eta and h_x, from which the inner solve forms its
+//                   coefficients.
+// The slot arrays outlive no double-float transform except the symbol table, which lies
+// beyond the double-float planes.
 template <int L>
 struct SmemPcg {
   using PL = Plan<L>;
   static constexpr size_t n = (size_t)PL::n;
+  static constexpr size_t slot_c = (size_t)(PL::RP + 1) * PL::NT * 8;   // complex float
   static constexpr size_t off_d = 8 * n;
-  static constexpr size_t d_bytes = (size_t)(PL::RP + 1) * PL::NT * 8;
-  static constexpr size_t off_c =
-      ((16 * n > off_d + d_bytes ? 16 * n : off_d + d_bytes) + 15) / 16 * 16;
-  static constexpr size_t mixed = off_c + 12 * n;
+  static constexpr size_t off_r = off_d + slot_c;
+  static constexpr size_t off_di = off_r + slot_c;
+  static constexpr size_t end_di = off_di + slot_c / 2;
+  static constexpr size_t off_e = ((16 * n > end_di ? 16 * n : end_di) + 15) / 16 * 16;
+  static constexpr size_t mixed = off_e + 8 * n;
   static constexpr size_t fp64 = 16 * n;
+  static_assert(off_di >= 16 * n || PL::RP < 2, "symbol table must clear the planes");
 };
+
+// Double-float coefficients of Def:MatrixM in 1d (c1 = eta (1 + h_x^2), c2 = eta^2 h_x / 2,
+// c3 = eta^3 / 3) to global memory, and float32 eta, h_x to shared memory.
+template <int NT>
+__device__ __forceinline__ void prep_coefficients(const double* __restrict__ eta,
+                                                  const double* __restrict__ hx, int n,
+                                                  float* __restrict__ eh,
+                                                  float* __restrict__ cdf) {
+  for (int j = threadIdx.x; j < n; j += NT) {
+    const double e = eta[j], g = hx[j];
+    const double c[3] = {e * (1.0 + g * g), 0.5 * e * e * g, e * e * e * (1.0 / 3.0)};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float hi = (float)c[q];
+      cdf[q * n + j] = hi;
+      cdf[(3 + q) * n + j] = (float)(c[q] - (double)hi);
+    }
+    eh[j] = (float)e;
+    eh[n + j] = (float)g;
+  }
+}
 
 struct PcgScalars {     // inner float32 PCG
   float rz, alpha, beta;
@@ -149,30 +179,31 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
   };
   const float dN = recip(sigf);
 
-  float* c32 = reinterpret_cast<float*>(smem + SM::off_c);
-  const float* clo = A.coef_lo ? A.coef_lo + 3 * I.off : nullptr;
-  if constexpr (MIXED) split_coefficients<NT>(eta, hx, n, c32, A.coef_lo + 3 * I.off);
+  const float* eh = reinterpret_cast<const float*>(smem + SM::off_e);
+  const float* cdf = A.coef_df + 6 * I.off;
+  if constexpr (MIXED)
+    prep_coefficients<NT>(eta, hx, n, reinterpret_cast<float*>(smem + SM::off_e),
+                          A.coef_df + 6 * I.off);
 
   // ---- b^ and x0^ from one transform of b + i x0
   {
-    const typename f1::TwOf<TH>::type twh{
-        MIXED ? reinterpret_cast<const cplx<TH>*>(A.twdf) : reinterpret_cast<const cplx<TH>*>(A.tw64)};
-    cplx<TH> v[E];
+    const cplx<TH>* tw = MIXED ? reinterpret_cast<const cplx<TH>*>(A.twdf)
+                               : reinterpret_cast<const cplx<TH>*>(A.tw64);
     if (g.act) {
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int j = t + e * NTA;
-        v[e] = mk(num<TH>(b[j]), num<TH>(x[j]));
+        XH.st(g.bnat ^ f1::swz_c(e * NTA), mk(num<TH>(b[j]), num<TH>(x[j])));
       }
     }
-    f1::fft_fwd<TH, L>(XH, v, g, twh);
+    f1::fft_smem<TH, L>(XH, tw);
     float bb = 0.0f;
     if (g.act) {
 #pragma unroll
       for (int q = 0; q < RP; ++q) {
         const int m = g.mode(SL::b(q), SL::s(q));
-        const cplx<TH> y = v[SL::reg(q)];
-        const cplx<TH> ym = conj(f1::mirror_get<L>(v, t0, SL::b(q), SL::s(q)));
+        const cplx<TH> y = XH.ld(f1::swz(m));
+        const cplx<TH> ym = conj(XH.ld(f1::swz((n - m) & (n - 1))));
         const cplx<TH> s = y + ym, d = mul_mi(y - ym);
         const cplx<TH> bh = mk(half(s.x), half(s.y));
         Bh[m] = bh;
@@ -181,7 +212,7 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
         bb += ((t0 && q == 0) ? 1.0f : 2.0f) * (bx * bx + by * by) * dinv(m);
       }
       if (t0) {
-        const cplx<TH> y = v[HS];
+        const cplx<TH> y = XH.ld(f1::swz(h));
         Bh[h] = mk(y.x, from_int<TH>(0));
         Xh[h] = mk(y.y, from_int<TH>(0));
         const float bx = (float)to_f64(y.x);
@@ -213,7 +244,6 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
     const CoefGlobal64 coef64{eta, hx};
     const double tol_abs = rtol * bnorm;
     const double inv_n = 1.0 / (double)n;
-    const f1::TwTab<double> tw{A.tw64};
     const double isig = 1.0 / R.sigma;
     auto dinv64 = [&](int m) {
       const double k = kunit * (double)m;
@@ -222,42 +252,48 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
     // (G v)^ of the slots of the half spectrum Vh into gq / gN
     auto matvec = [&](const cplx<double>* __restrict__ Vh, cplx<double>(&gq)[RP],
                       cplx<double>& gN) {
-      cplx<double> v[E];
+      __syncthreads();                           // earlier readers of the buffer are done
       if (g.act) {
+        // conj(Z), Z_m = (1 - k) v_m and Z_{n-m} = conj(Z_m)-mirror (1 + k) conj(v_m)
 #pragma unroll
         for (int q = 0; q < RP; ++q) {
-          const double k = kunit * (double)g.mode(SL::b(q), SL::s(q));
-          const cplx<double> p = Vh[g.mode(SL::b(q), SL::s(q))];
+          const int m = g.mode(SL::b(q), SL::s(q));
+          const double k = kunit * (double)m;
+          const cplx<double> p = Vh[m];
           if (t0 && q == 0) {
-            v[0] = mk(p.x, 0.0);
+            XH.st(0, mk(p.x, 0.0));
           } else {
-            v[SL::reg(q)] = p * (1.0 - k);
-            f1::mirror_set<L>(v, t0, SL::b(q), SL::s(q), conj(p) * (1.0 + k));
+            XH.st(f1::swz(m), conj(p) * (1.0 - k));
+            XH.st(f1::swz(n - m), p * (1.0 + k));
           }
         }
-        if (t0) v[HS] = mk(Vh[h].x, 0.0);
+        if (t0) XH.st(f1::swz(h), mk(Vh[h].x, 0.0));
       }
-      f1::fft_inv<double, L>(XH, v, g, tw);
+      __syncthreads();
+      f1::fft_smem<double, L>(XH, A.tw64);
       if (g.act) {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          const double pv = v[e].x * inv_n, px = v[e].y * inv_n;
+          const int a = g.bnat ^ f1::swz_c(e * NTA);
+          const cplx<double> z = XH.ld(a);       // conj of n (v + i v_x)
+          const double pv = z.x * inv_n, px = -z.y * inv_n;
           double c1, c2, c3;
           coef64(t + e * NTA, c1, c2, c3);
-          v[e] = mk(c1 * pv + c2 * px, c2 * pv + c3 * px);
+          XH.st(a, mk(c1 * pv + c2 * px, c2 * pv + c3 * px));
         }
       }
-      f1::fft_fwd<double, L>(XH, v, g, tw);
+      f1::fft_smem<double, L>(XH, A.tw64);
       if (g.act) {
 #pragma unroll
         for (int q = 0; q < RP; ++q) {
-          const double k = kunit * (double)g.mode(SL::b(q), SL::s(q));
-          const cplx<double> y = v[SL::reg(q)];
-          const cplx<double> ym = conj(f1::mirror_get<L>(v, t0, SL::b(q), SL::s(q)));
+          const int m = g.mode(SL::b(q), SL::s(q));
+          const double k = kunit * (double)m;
+          const cplx<double> y = XH.ld(f1::swz(m));
+          const cplx<double> ym = conj(XH.ld(f1::swz((n - m) & (n - 1))));
           const cplx<double> s = y * (1.0 - k) + ym * (1.0 + k);
           gq[q] = mk(0.5 * s.x, 0.5 * s.y);
         }
-        if (t0) gN = mk(v[HS].x, 0.0);
+        if (t0) gN = mk(XH.ld(f1::swz(h)).x, 0.0);
       }
     };
     // r = b - G x0, p = A^{-1} r
@@ -342,31 +378,39 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
       }
     }
     R.ratio = sqrt(rz) / bnorm;
-    // x = F^{-1} x^
-    cplx<double> v[E];
+    // x = F^{-1} x^ = conj(F(conj x^)) / n
+    __syncthreads();
     if (g.act) {
 #pragma unroll
       for (int q = 0; q < RP; ++q) {
-        const cplx<double> xv = Xh[g.mode(SL::b(q), SL::s(q))];
+        const int m = g.mode(SL::b(q), SL::s(q));
+        const cplx<double> xv = Xh[m];
         if (t0 && q == 0) {
-          v[0] = mk(xv.x, 0.0);
+          XH.st(0, mk(xv.x, 0.0));
         } else {
-          v[SL::reg(q)] = xv;
-          f1::mirror_set<L>(v, t0, SL::b(q), SL::s(q), conj(xv));
+          XH.st(f1::swz(m), conj(xv));
+          XH.st(f1::swz(n - m), xv);
         }
       }
-      if (t0) v[HS] = mk(Xh[h].x, 0.0);
+      if (t0) XH.st(f1::swz(h), mk(Xh[h].x, 0.0));
     }
-    f1::fft_inv<double, L>(XH, v, g, tw);
+    __syncthreads();
+    f1::fft_smem<double, L>(XH, A.tw64);
     if (g.act)
 #pragma unroll
-      for (int e = 0; e < E; ++e) x[t + e * NTA] = v[e].x * inv_n;
+      for (int e = 0; e < E; ++e) x[t + e * NTA] = XH.ld(g.bnat ^ f1::swz_c(e * NTA)).x * inv_n;
   } else {
     // ------------------------------------------------------------------ mixed precision
     const XBuf<float> XF(smem, n);
     const f1::TwF32 twf;
-    const f1::TwTab<df> twd{A.twdf};
     cplx<float>* D = reinterpret_cast<cplx<float>*>(smem + SM::off_d);   // [RP + 1][NT]
+    cplx<float>* Rr = reinterpret_cast<cplx<float>*>(smem + SM::off_r);  // [RP + 1][NT]
+    float* DI = reinterpret_cast<float*>(smem + SM::off_di);             // [RP + 1][NT]
+    if (g.act) {
+#pragma unroll
+      for (int q = 0; q < RP; ++q) DI[q * NT + t] = dinv(g.mode(SL::b(q), SL::s(q)));
+      if (t0) DI[RP * NT] = dN;
+    }
     const df inv_n(1.0f / (float)n, 0.0f);                                 // exact
     const float inv_nf = 1.0f / (float)n;
     const df one(1.0f, 0.0f), zero(0.0f, 0.0f);
@@ -376,43 +420,48 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
       // ---- double-float residual r^ = b^ - (G x)^, writing the real-space x on the way
       cplx<float> rf[RP], rfN = mk(0.0f, 0.0f);
       {
-        cplx<df> v[E];
+        __syncthreads();                         // the previous correction d has been read
         if (g.act) {
+          // conj(Z) with Z_m = (1 - k) x_m, Z_{n-m} = (1 + k) conj(x_m)
 #pragma unroll
           for (int q = 0; q < RP; ++q) {
             const int m = g.mode(SL::b(q), SL::s(q));
             const df k = kh * df((float)m, 0.0f);
             const cplx<df> xv = Xh[m];
             if (t0 && q == 0) {
-              v[0] = mk(xv.x, zero);
+              XH.st(0, mk(xv.x, zero));
             } else {
-              v[SL::reg(q)] = xv * (one - k);
-              f1::mirror_set<L>(v, t0, SL::b(q), SL::s(q), conj(xv) * (one + k));
+              XH.st(f1::swz(m), conj(xv) * (one - k));
+              XH.st(f1::swz(n - m), xv * (one + k));
             }
           }
-          if (t0) v[HS] = mk(Xh[h].x, zero);
+          if (t0) XH.st(f1::swz(h), mk(Xh[h].x, zero));
         }
-        f1::fft_inv<df, L>(XH, v, g, twd);
+        __syncthreads();
+        f1::fft_smem<df, L>(XH, A.twdf);
         if (g.act) {
-#pragma unroll
+          // rolled: unrolled, the compiler hoists the 6 coefficient loads of every element
+#pragma unroll 1
           for (int e = 0; e < E; ++e) {
             const int j = t + e * NTA;
-            const df pv = v[e].x * inv_n, px = v[e].y * inv_n;
+            const int a = f1::swz(j);
+            const cplx<df> z = XH.ld(a);         // conj of n (x + i x_x)
+            const df pv = z.x * inv_n, px = -(z.y * inv_n);
             x[j] = to_f64(pv);
-            const df c1(c32[j], clo[j]), c2(c32[n + j], clo[n + j]),
-                c3(c32[2 * n + j], clo[2 * n + j]);
-            v[e] = mk(c1 * pv + c2 * px, c2 * pv + c3 * px);
+            const df c1(cdf[j], cdf[3 * n + j]), c2(cdf[n + j], cdf[4 * n + j]),
+                c3(cdf[2 * n + j], cdf[5 * n + j]);
+            XH.st(a, mk(c1 * pv + c2 * px, c2 * pv + c3 * px));
           }
         }
-        f1::fft_fwd<df, L>(XH, v, g, twd);
+        f1::fft_smem<df, L>(XH, A.twdf);
         float rz_loc = 0.0f;
         if (g.act) {
 #pragma unroll
           for (int q = 0; q < RP; ++q) {
             const int m = g.mode(SL::b(q), SL::s(q));
             const df k = kh * df((float)m, 0.0f);
-            const cplx<df> y = v[SL::reg(q)];
-            const cplx<df> ym = conj(f1::mirror_get<L>(v, t0, SL::b(q), SL::s(q)));
+            const cplx<df> y = XH.ld(f1::swz(m));
+            const cplx<df> ym = conj(XH.ld(f1::swz((n - m) & (n - 1))));
             const cplx<df> s = y * (one - k) + ym * (one + k);
             const cplx<df> rr = Bh[m] - mk(half(s.x), half(s.y));
             rf[q] = mk(rr.x.hi + rr.x.lo, rr.y.hi + rr.y.lo);
@@ -420,7 +469,7 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
                       (rf[q].x * rf[q].x + rf[q].y * rf[q].y) * dinv(m);
           }
           if (t0) {
-            const df rr = Bh[h].x - v[HS].x;
+            const df rr = Bh[h].x - XH.ld(f1::swz(h)).x;
             rfN = mk(rr.hi + rr.lo, 0.0f);
             rz_loc += rfN.x * rfN.x * dN;
           }
@@ -452,30 +501,31 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
       const float scale = ps.scale, tin2 = ps.tin2;
       const df unscale = ps.unscale;
 
-      // ---- float32 PCG for G d = r / ||r||, r and p in registers, d in shared memory
+      // ---- float32 PCG for G d = r / ||r||: p in registers, r, d and the preconditioner
+      // symbol in thread-private shared slots (slot q of thread t at q NT + t)
       const int it_before = iters;
       int st_in = SGN_OK;
       {
-        cplx<float> r[RP], p[RP], rN = mk(0.0f, 0.0f), pN = mk(0.0f, 0.0f);
+        cplx<float> p[RP], pN = mk(0.0f, 0.0f);
         int it = iters;
         float loc = 0.0f;
         if (g.act) {
 #pragma unroll
           for (int q = 0; q < RP; ++q) {
-            const float di = dinv(g.mode(SL::b(q), SL::s(q)));
-            r[q] = rf[q] * scale;
-            p[q] = r[q] * di;
-            loc += ((t0 && q == 0) ? 1.0f : 2.0f) * (r[q].x * p[q].x + r[q].y * p[q].y);
+            const cplx<float> r = rf[q] * scale;
+            p[q] = r * DI[q * NT + t];
+            loc += ((t0 && q == 0) ? 1.0f : 2.0f) * (r.x * p[q].x + r.y * p[q].y);
+            Rr[q * NT + t] = r;
             D[q * NT + t] = mk(0.0f, 0.0f);
           }
           if (t0) {
-            rN = rfN * scale;
-            pN = rN * dN;
-            loc += rN.x * pN.x;
+            const cplx<float> r = rfN * scale;
+            pN = r * dN;
+            loc += r.x * pN.x;
+            Rr[RP * NT] = r;
             D[RP * NT] = mk(0.0f, 0.0f);
           }
         }
-        // (the previous barrier-separated readers of sc are done: ps was read after one)
         block_sum_df<NT>(loc, slots + W, [&](float hi, float lo) {
           const float rz = hi + lo;
           sc.rz = rz;
@@ -508,7 +558,10 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
             for (int e = 0; e < E; ++e) {
               const int j = t + e * NTA;
               const float pv = v[e].x * inv_nf, px = v[e].y * inv_nf;
-              const float c1 = c32[j], c2 = c32[n + j], c3 = c32[2 * n + j];
+              const float et = eh[j], gx = eh[n + j];
+              const float e2 = et * et;
+              const float c1 = fmaf(et * gx, gx, et), c2 = 0.5f * e2 * gx,
+                          c3 = e2 * et * (1.0f / 3.0f);
               v[e] = mk(c1 * pv + c2 * px, c2 * pv + c3 * px);
             }
           }
@@ -544,16 +597,17 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
           if (g.act) {
 #pragma unroll
             for (int q = 0; q < RP; ++q) {
-              const float di = dinv(g.mode(SL::b(q), SL::s(q)));
-              D[q * NT + t] = D[q * NT + t] + p[q] * at;
-              r[q] = r[q] - gq[q] * at;
-              rz_loc += ((t0 && q == 0) ? 1.0f : 2.0f) *
-                        (r[q].x * r[q].x + r[q].y * r[q].y) * di;
+              const int o = q * NT + t;
+              D[o] = D[o] + p[q] * at;
+              const cplx<float> r = Rr[o] - gq[q] * at;
+              Rr[o] = r;
+              rz_loc += ((t0 && q == 0) ? 1.0f : 2.0f) * (r.x * r.x + r.y * r.y) * DI[o];
             }
             if (t0) {
               D[RP * NT] = D[RP * NT] + pN * at;
-              rN = rN - gN * at;
-              rz_loc += rN.x * rN.x * dN;
+              const cplx<float> r = Rr[RP * NT] - gN * at;
+              Rr[RP * NT] = r;
+              rz_loc += r.x * r.x * dN;
             }
           }
           ++it;
@@ -575,10 +629,10 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
           if (g.act) {
 #pragma unroll
             for (int q = 0; q < RP; ++q) {
-              const float di = dinv(g.mode(SL::b(q), SL::s(q)));
-              p[q] = r[q] * di + p[q] * beta;
+              const int o = q * NT + t;
+              p[q] = Rr[o] * DI[o] + p[q] * beta;
             }
-            if (t0) pN = rN * dN + pN * beta;
+            if (t0) pN = Rr[RP * NT] * dN + pN * beta;
           }
         }
         iters = it;

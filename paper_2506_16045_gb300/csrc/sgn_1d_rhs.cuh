@@ -38,27 +38,36 @@ cudaError_t rhs1d_launch(const RhsArgs& a, int first, int num, cudaStream_t s);
 namespace rhs1d {
 
 using namespace d1;
-using f1::Geo;
 using f1::Plan;
 using f1::XBuf;
 
-// v <- D v for the two real fields packed in v (natural registers in and out): forward
-// transform, i k_m / n on every mode of the paired layout (Nyquist 0), inverse transform.
+// v <- D v for the two real fields packed in v (the thread's natural elements in and out):
+// forward transform, i k_m / n on every mode (Nyquist 0), inverse transform as
+// conj(F(conj .)).  Each thread touches only its own natural positions of X outside the
+// transforms, so no barrier is needed around them.
 template <typename T, int L>
-__device__ __forceinline__ void deriv_pair(const XBuf<T>& X, cplx<T> (&v)[Plan<L>::E],
-                                           const Geo<L>& g, T kn, const f1::TwTab<T>& tw) {
+__device__ __forceinline__ void deriv_pair(const XBuf<T>& X, cplx<T> (&v)[Plan<L>::E], int t,
+                                           int bnat, bool act, T kn,
+                                           const cplx<T>* __restrict__ tw) {
   using PL = Plan<L>;
-  f1::fft_fwd<T, L>(X, v, g, tw);
-  if (g.act) {
+  if (act) {
 #pragma unroll
-    for (int b = 0; b < 2; ++b)
-#pragma unroll
-      for (int s = 0; s < PL::RP; ++s) {
-        const T k = kn * from_int<T>(wave_index(g.mode(b, s), PL::n));
-        v[b * PL::RP + s] = mul_pi(v[b * PL::RP + s]) * k;
-      }
+    for (int e = 0; e < PL::E; ++e) X.st(bnat ^ f1::swz_c(e * PL::NTA), v[e]);
   }
-  f1::fft_inv<T, L>(X, v, g, tw);
+  f1::fft_smem<T, L>(X, tw);
+  if (act) {
+#pragma unroll
+    for (int e = 0; e < PL::E; ++e) {
+      const int a = bnat ^ f1::swz_c(e * PL::NTA);
+      const T k = kn * from_int<T>(wave_index(t + e * PL::NTA, PL::n));
+      X.st(a, conj(mul_pi(X.ld(a)) * k));
+    }
+  }
+  f1::fft_smem<T, L>(X, tw);
+  if (act) {
+#pragma unroll
+    for (int e = 0; e < PL::E; ++e) v[e] = conj(X.ld(bnat ^ f1::swz_c(e * PL::NTA)));
+  }
 }
 
 template <typename T, int L>
@@ -68,15 +77,15 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
   constexpr int n = PL::n, E = PL::E, NTA = PL::NTA;
   extern __shared__ __align__(16) unsigned char smem[];
   const int t = threadIdx.x;
-  const Geo<L> g(t);
   const Inst1d I = A.insts[A.ids[first + blockIdx.x]];
   const T kn = num<T>(2.0 * kPi / I.L / (double)n);
   const T third = num<T>(1.0 / 3.0);
   const T gT = num<T>(A.g);
   const XBuf<T> X(smem, n);
-  const f1::TwTab<T> tw{std::is_same<T, df>::value
-                            ? reinterpret_cast<const cplx<T>*>(A.twdf)
-                            : reinterpret_cast<const cplx<T>*>(A.tw64)};
+  const cplx<T>* tw = std::is_same<T, df>::value ? reinterpret_cast<const cplx<T>*>(A.twdf)
+                                                 : reinterpret_cast<const cplx<T>*>(A.tw64);
+  const int bnat = f1::swz(t);
+  const bool act = !PL::kIdle || t < NTA;
   const double* eta = A.eta + I.off;
   const double* u = A.u + I.off;
   const double* hh = A.h + I.off;
@@ -87,7 +96,7 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
   T* ssx = reinterpret_cast<T*>(A.scratch + 3 * A.P + I.off);   // s_x
   T* spsi = reinterpret_cast<T*>(A.scratch + 4 * A.P + I.off);  // Psi
   cplx<T> v[E];
-  if (g.act) {
+  if (act) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int j = t + e * NTA;
@@ -95,8 +104,8 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
       v[e] = mk(uj, num<T>(eta[j]) * uj);
     }
   }
-  deriv_pair<T, L>(X, v, g, kn, tw);
-  if (g.act) {
+  deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);
+  if (act) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int j = t + e * NTA;
@@ -105,8 +114,8 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
       v[e] = mk(num<T>(eta[j] - hh[j]), num<T>(hx[j]) * num<T>(u[j]));
     }
   }
-  deriv_pair<T, L>(X, v, g, kn, tw);
-  if (g.act) {
+  deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);
+  if (act) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int j = t + e * NTA;
@@ -115,8 +124,8 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
       v[e] = mk(sd[j], from_int<T>(0));
     }
   }
-  deriv_pair<T, L>(X, v, g, kn, tw);
-  if (g.act) {
+  deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);
+  if (act) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int j = t + e * NTA;
@@ -131,8 +140,8 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
       v[e] = mk(Phi, from_int<T>(0));
     }
   }
-  deriv_pair<T, L>(X, v, g, kn, tw);
-  if (g.act) {
+  deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);
+  if (act) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int j = t + e * NTA;

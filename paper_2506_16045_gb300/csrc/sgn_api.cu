@@ -77,7 +77,7 @@ struct sgn_layout {
   sgn::Layout2d l2;
   void* ws = nullptr;               // spectral workspace
   double* scratch = nullptr;        // 5 P doubles (rhs intermediates)
-  float* coef_lo = nullptr;         // 3 P floats (double-float coefficient remainders)
+  float* coef_df = nullptr;         // 6 P floats (double-float coefficients, high and low parts)
   SolveRec* rec = nullptr;          // [count] per-instance solve reports
   SolveRec* given = nullptr;        // [count] caller-provided coefficients
 };
@@ -373,7 +373,7 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
         cudaMalloc(&L.d_ids, sizeof(int) * count) != cudaSuccess ||
         cudaMalloc(&lay->ws, sizeof(double) * 2 * ws) != cudaSuccess ||
         cudaMalloc(&lay->scratch, sizeof(double) * 5 * off) != cudaSuccess ||
-        cudaMalloc(&lay->coef_lo, sizeof(float) * 3 * off) != cudaSuccess ||
+        cudaMalloc(&lay->coef_df, sizeof(float) * 6 * off) != cudaSuccess ||
         cudaMalloc(&lay->rec, sizeof(SolveRec) * count) != cudaSuccess ||
         cudaMalloc(&lay->given, sizeof(SolveRec) * count) != cudaSuccess) {
       cudaGetLastError();
@@ -429,7 +429,7 @@ extern "C" void sgn_layout_destroy(sgn_layout* lay) {
   sgn::layout2d_destroy(lay->l2);
   cudaFree(lay->ws);
   cudaFree(lay->scratch);
-  cudaFree(lay->coef_lo);
+  cudaFree(lay->coef_df);
   cudaFree(lay->rec);
   cudaFree(lay->given);
   delete lay;
@@ -559,7 +559,7 @@ sgn_status run_pcg(sgn_layout* lay, const double* eta, const double* gradh, cons
   ProfScope prof(ctx, s, 0);
   if (lay->dim == 1) {
     e = sgn::launch_pcg1d(lay->l1, ctx->tw64, ctx->tw32, prec, eta, gradh, b, x, given, kind, rtol,
-                          rtol_inner, maxit, max_refine, lay->rec, lay->ws, lay->coef_lo, s);
+                          rtol_inner, maxit, max_refine, lay->rec, lay->ws, lay->coef_df, s);
   } else {
     e = sgn::launch_pcg2d(lay->l2, ctx->tw64, ctx->tw32, prec, eta, gradh, b, x, given, kind, rtol,
                           rtol_inner, maxit, max_refine, lay->rec, s);

@@ -515,5 +515,82 @@ __device__ __forceinline__ void mirror_set(V (&v)[Plan<L>::E], bool t0, int b, i
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Compact in-shared-memory transform for the double-float and float64 paths.
+//
+// The register-resident transforms above are fully unrolled, which for double-float and
+// float64 arithmetic makes hundreds of kilobytes of code per call site and stalls on
+// instruction fetch.  fft_smem runs the same Stockham stages with the data in the exchange
+// buffer between stages, natural order in and out: a stage reads the thread's natural
+// elements, waits at a barrier, computes its butterflies and writes their outputs in
+// Stockham order, and waits again.  Stages of equal radix share one code body through a
+// runtime stage loop, only the forward transform exists (callers form the inverse as
+// conj(F(conj x))), and the function is not inlined, so every caller runs the same code.
+// ---------------------------------------------------------------------------------------
+template <int L>
+struct SmemPlan {
+  static constexpr int LE = Plan<L>::LE;
+  static constexpr int NS = (L + LE - 1) / LE;
+  static constexpr int bits(int q) { return L / NS + (q < L % NS ? 1 : 0); }
+  static constexpr bool uses(int lr) {
+    for (int q = 0; q < NS; ++q)
+      if (bits(q) == lr) return true;
+    return false;
+  }
+};
+
+template <typename T, int L, int LR>
+__device__ __forceinline__ void smem_stage(const XBuf<T>& X, int t, int bnat, int lp,
+                                           const cplx<T>* __restrict__ tw) {
+  using PL = Plan<L>;
+  constexpr int E = PL::E, NTA = PL::NTA, R = 1 << LR, BB = E / R;
+  const bool act = !PL::kIdle || t < NTA;
+  cplx<T> v[E];
+  if (act) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = X.ld(bnat ^ swz_c(e * NTA));
+  }
+  __syncthreads();
+  if (act) {
+    const int pm = (1 << lp) - 1, sh = kTwiddleLog2 - lp - LR;
+#pragma unroll
+    for (int j = 0; j < BB; ++j) {
+      const int i = t + j * NTA, k = i & pm;
+      const int base = k | ((i >> lp) << (lp + LR));
+      cplx<T> a[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) a[r] = v[j + r * BB];
+      if (k != 0) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) a[r] = cmul(a[r], tw[(r * k) << sh]);
+      }
+      dft<T, R, false>(a);
+#pragma unroll
+      for (int s = 0; s < R; ++s) X.st(swz(base | (s << lp)), a[s]);
+    }
+  }
+  __syncthreads();
+}
+
+// Forward transform of the n = 2^L elements in X (natural order in and out).  All threads
+// of the CTA call; entered and left at a barrier-consistent point (the caller's writes of
+// the input must be complete, or be the caller's own natural elements).
+template <typename T, int L>
+__device__ __noinline__ void fft_smem(const XBuf<T> X, const cplx<T>* __restrict__ tw) {
+  using SP = SmemPlan<L>;
+  const int t = threadIdx.x;
+  const int bnat = swz(t);
+  int lp = 0;
+#pragma unroll 1
+  for (int q = 0; q < SP::NS; ++q) {
+    const int lr = SP::bits(q);
+    if constexpr (SP::uses(4)) if (lr == 4) smem_stage<T, L, 4>(X, t, bnat, lp, tw);
+    if constexpr (SP::uses(3)) if (lr == 3) smem_stage<T, L, 3>(X, t, bnat, lp, tw);
+    if constexpr (SP::uses(2)) if (lr == 2) smem_stage<T, L, 2>(X, t, bnat, lp, tw);
+    if constexpr (SP::uses(1)) if (lr == 1) smem_stage<T, L, 1>(X, t, bnat, lp, tw);
+    lp += lr;
+  }
+}
+
 }  // namespace f1
 }  // namespace sgn

@@ -69,7 +69,7 @@ cudaError_t launch_precond1d(const Layout1d& lay, const void* tw64, const SolveR
 cudaError_t launch_pcg1d(const Layout1d& lay, const void* tw64, const void* tw32, int precision,
                          const double* eta, const double* hx, const double* b, double* x,
                          const SolveRec* given, int kind, double rtol, double rtol_inner,
-                         int maxit, int max_refine, SolveRec* rec, void* ws, float* coef_lo,
+                         int maxit, int max_refine, SolveRec* rec, void* ws, float* coef_df,
                          cudaStream_t s);
 cudaError_t launch_rhs1d(const Layout1d& lay, const void* tw64, const void* tw32, int precision,
                          double g, const double* eta,

@@ -24,7 +24,7 @@ constexpr long long kWsCplx = (long long)sgn::kWsVectors * (SGN_NOALLOC_MAX_N / 
 static __device__ __align__(256) double g_ws[2 * kWsCplx];
 static __device__ __align__(256) double g_tw64[2 * sgn::kTwiddleN];
 static __device__ __align__(256) float g_tw32[(sgn::kTw32Bytes + sgn::kTwDfBytes) / sizeof(float)];
-static __device__ __align__(256) float g_coef_lo[3 * SGN_NOALLOC_MAX_N];
+static __device__ __align__(256) float g_coef_df[6 * SGN_NOALLOC_MAX_N];
 static __device__ __align__(256) sgn::Inst1d g_inst[1];
 static __device__ __align__(256) int g_ids[1];
 static __device__ __align__(256) sgn::SolveRec g_rec[1];
@@ -39,7 +39,7 @@ struct DevicePtrs {
   sgn::Inst1d* inst = nullptr;
   int* ids = nullptr;
   sgn::SolveRec* rec = nullptr;
-  float* coef_lo = nullptr;
+  float* coef_df = nullptr;
 };
 
 constexpr int kMaxDevices = 64;
@@ -57,7 +57,7 @@ sgn_status setup_device(int dev, cudaStream_t s) {
       cudaGetSymbolAddress(reinterpret_cast<void**>(&P.inst), g_inst) != cudaSuccess ||
       cudaGetSymbolAddress(reinterpret_cast<void**>(&P.ids), g_ids) != cudaSuccess ||
       cudaGetSymbolAddress(reinterpret_cast<void**>(&P.rec), g_rec) != cudaSuccess ||
-      cudaGetSymbolAddress(reinterpret_cast<void**>(&P.coef_lo), g_coef_lo) != cudaSuccess) {
+      cudaGetSymbolAddress(reinterpret_cast<void**>(&P.coef_df), g_coef_df) != cudaSuccess) {
     cudaGetLastError();
     return SGN_ERR_CUDA;
   }
@@ -121,7 +121,7 @@ extern "C" sgn_status sgn_pcg1d_noalloc(int n, double L, const double* eta, cons
   lay.class_end[log2n] = 1;
   cudaError_t e = sgn::launch_pcg1d(lay, P.tw64, P.tw32, prec, eta, gradh, b, x, nullptr,
                                     SGN_COEF_OPT, rtol, -1.0, maxit, 12, P.rec, P.ws,
-                                    P.coef_lo, s);
+                                    P.coef_df, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return SGN_ERR_CUDA;
