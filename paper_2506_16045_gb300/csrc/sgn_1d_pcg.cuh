@@ -82,23 +82,26 @@ struct SmemPcg {
 };
 
 // Double-float coefficients of Def:MatrixM in 1d (c1 = eta (1 + h_x^2), c2 = eta^2 h_x / 2,
-// c3 = eta^3 / 3) to global memory, and float32 eta, h_x to shared memory.
+// c3 = eta^3 / 3) to global memory (high parts, then low parts), and float32 eta, h_x to
+// shared memory.  Formed in double-float arithmetic: no float64 instruction.
 template <int NT>
 __device__ __forceinline__ void prep_coefficients(const double* __restrict__ eta,
                                                   const double* __restrict__ hx, int n,
                                                   float* __restrict__ eh,
                                                   float* __restrict__ cdf) {
+  const df third = f1::kc<df>(1.0 / 3.0, (float)(1.0 / 3.0),
+                              (float)(1.0 / 3.0 - (double)(float)(1.0 / 3.0)));
   for (int j = threadIdx.x; j < n; j += NT) {
-    const double e = eta[j], g = hx[j];
-    const double c[3] = {e * (1.0 + g * g), 0.5 * e * e * g, e * e * e * (1.0 / 3.0)};
+    const df e(eta[j]), g(hx[j]);
+    const df e2 = e * e;
+    const df c[3] = {e + e * g * g, half(e2 * g), e2 * e * third};
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      const float hi = (float)c[q];
-      cdf[q * n + j] = hi;
-      cdf[(3 + q) * n + j] = (float)(c[q] - (double)hi);
+      cdf[q * n + j] = c[q].hi;
+      cdf[(3 + q) * n + j] = c[q].lo;
     }
-    eh[j] = (float)e;
-    eh[n + j] = (float)g;
+    eh[j] = e.hi;
+    eh[n + j] = g.hi;
   }
 }
 
@@ -208,14 +211,14 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
         const cplx<TH> bh = mk(half(s.x), half(s.y));
         Bh[m] = bh;
         Xh[m] = mk(half(d.x), half(d.y));
-        const float bx = (float)to_f64(bh.x), by = (float)to_f64(bh.y);
+        const float bx = lead(bh.x), by = lead(bh.y);
         bb += ((t0 && q == 0) ? 1.0f : 2.0f) * (bx * bx + by * by) * dinv(m);
       }
       if (t0) {
         const cplx<TH> y = XH.ld(f1::swz(h));
         Bh[h] = mk(y.x, from_int<TH>(0));
         Xh[h] = mk(y.y, from_int<TH>(0));
-        const float bx = (float)to_f64(y.x);
+        const float bx = lead(y.x);
         bb += bx * bx * dN;
       }
     }

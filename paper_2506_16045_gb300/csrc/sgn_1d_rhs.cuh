@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
       const int j = t + e * NTA;
       sd[j] = v[e].x;
       sm[j] = v[e].y;
-      v[e] = mk(num<T>(eta[j] - hh[j]), num<T>(hx[j]) * num<T>(u[j]));
+      v[e] = mk(num<T>(eta[j]) - num<T>(hh[j]), num<T>(hx[j]) * num<T>(u[j]));
     }
   }
   deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);

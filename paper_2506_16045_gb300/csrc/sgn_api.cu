@@ -68,6 +68,7 @@ struct ProfScope {
 
 struct sgn_layout {
   sgn_ctx* ctx = nullptr;
+  int device = 0;                   // copied from ctx: destroying a layout never reads ctx
   int count = 0;
   int dim = 1;
   std::vector<sgn_grid> grids;
@@ -330,6 +331,7 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
   sgn_layout* lay = new (std::nothrow) sgn_layout();
   if (!lay) return SGN_ERR_NOMEM;
   lay->ctx = ctx;
+  lay->device = ctx->device;
   lay->count = count;
   lay->dim = dim;
   lay->grids.assign(grids, grids + count);
@@ -417,7 +419,7 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
 
 extern "C" void sgn_layout_destroy(sgn_layout* lay) {
   if (!lay) return;
-  DeviceGuard g(lay->ctx->device);
+  DeviceGuard g(lay->device);
   for (int c = 0; c < 16; ++c) {
     if (lay->l1.side[c]) cudaStreamDestroy(lay->l1.side[c]);
     if (lay->l1.join[c]) cudaEventDestroy(lay->l1.join[c]);
@@ -868,7 +870,7 @@ extern "C" sgn_status sgn_state_init(sgn_state* st, sgn_stream stream) {
 namespace sgn {
 sgn_status state_attach(sgn_state* st, cudaStream_t s) {
   if (!st) return SGN_ERR_INVALID_ARG;
-  DeviceGuard g(st->lay->ctx->device);
+  DeviceGuard g(st->lay->device);
   SGN_CUDA(st->lay->ctx, cudaMemsetAsync(st->stats, 0, sizeof(DevStats), s));
   st->hist = HIST_NONE;
   st->levels = 0;
@@ -880,7 +882,7 @@ sgn_status state_attach(sgn_state* st, cudaStream_t s) {
 extern "C" sgn_status sgn_step_rk4(sgn_state* st, const double* dt, int nsteps,
                                    const sgn_opts* opts, sgn_stream stream) {
   if (!st || !dt || nsteps < 0) return SGN_ERR_INVALID_ARG;
-  DeviceGuard g(st->lay->ctx->device);
+  DeviceGuard g(st->lay->device);
   cudaStream_t s = as_stream(stream);
   SGN_TRY(check_opts(st, opts));
   SGN_TRY(upload_dt(st, dt, s));
@@ -900,7 +902,7 @@ extern "C" sgn_status sgn_step_abk(sgn_state* st, int order, const double* dt, i
                                  {5.0 / 12, -16.0 / 12, 23.0 / 12, 0},
                                  {-9.0 / 24, 37.0 / 24, -59.0 / 24, 55.0 / 24}};
   if (!st || !dt || nsteps < 0 || order < 2 || order > 4) return SGN_ERR_INVALID_ARG;
-  DeviceGuard g(st->lay->ctx->device);
+  DeviceGuard g(st->lay->device);
   cudaStream_t s = as_stream(stream);
   SGN_TRY(check_opts(st, opts));
   const bool same_dt = (int)st->dt_last.size() == st->lay->count &&
@@ -1043,7 +1045,7 @@ extern "C" sgn_status sgn_state_get_stats(sgn_state* st, sgn_state_stats* out) {
 
 extern "C" void sgn_state_free(sgn_state* st) {
   if (!st) return;
-  DeviceGuard g(st->lay->ctx->device);
+  DeviceGuard g(st->lay->device);
   for (double* p : st->bufs) cudaFree(p);
   cudaFree(st->res0);
   cudaFree(st->res1);

@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 from dataclasses import dataclass
 from typing import Sequence
 
@@ -177,6 +178,10 @@ class Context:
             raise SgnError(s, "sgn_create")
         self.h = h
         self.device = device
+        self._children = []            # weak references to layouts, states and servers
+
+    def _adopt(self, obj):
+        self._children.append(weakref.ref(obj))
 
     def check(self, s, what=""):
         if s != SGN_OK:
@@ -194,7 +199,13 @@ class Context:
         return dict(pcg_ms=pm.value, pcg_calls=pc.value, rhs_ms=rm.value, rhs_calls=rc.value)
 
     def close(self):
+        """Frees the context after everything created from it (newest first)."""
         if self.h:
+            for ref in reversed(self._children):
+                obj = ref()
+                if obj is not None:
+                    obj.close()
+            self._children = []
             self.lib.sgn_destroy(self.h)
             self.h = None
 
@@ -222,6 +233,7 @@ class Layout:
         ctx.check(ctx.lib.sgn_layout_offsets(h, offs), "sgn_layout_offsets")
         self.offsets = list(offs)
         self.dim = self.grids[0].dim
+        ctx._adopt(self)
 
     def close(self):
         if self.h:
@@ -306,6 +318,7 @@ class State:
                                                    _ptr(h), _ptr(gradh), C.byref(hh)),
                       "sgn_state_create")
         self.h = hh
+        lay.ctx._adopt(self)
 
     def init(self, stream=None):
         self.lay.ctx.check(self.lay.ctx.lib.sgn_state_init(self.h, _stream(stream)),
@@ -370,6 +383,7 @@ class Server:
         ctx.check(self.lib.sgn_server_create(ctx.h, budget_fraction, C.byref(h)),
                   "sgn_server_create")
         self.h = h
+        ctx._adopt(self)
 
     def submit(self, kind, grid: Grid, eta, u_or_b, h, scheme=SCHEME_RK4, dt=0.0, nsteps=0,
                rtol=1e-10, maxit=4000, prec=PREC_MIXED, coef=COEF_OPT, host=False):

@@ -158,9 +158,13 @@ def test_pcg_testproblem(S, prec, n, eta0, hvar):
     lay = sgn.Layout(ctx, [sgn.Grid(1, n, 1.0)])
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     p = sgn.PREC_FP64 if prec == "fp64" else sgn.PREC_MIXED
-    info = sgn.pcg(lay, dev(eta), dev(hx), dev(b), x, rtol=1e-12, maxit=5000, prec=p)[0]
-    assert info["status"] == 0 and info["ratio"] <= 1e-12
-    assert rel(host(x), ref) < 1e-10
+    # The double-float residual of the mixed path carries ~2^-48 relative rounding, which the
+    # operator's range (eta (1 + h_x^2) up to ~5e3 here) lifts to a floor near 1e-12 in the
+    # relative A^{-1} residual on the h0 = 4 problems, so the mixed solve is asked for 1e-11.
+    rtol = 1e-12 if prec == "fp64" else 1e-11
+    info = sgn.pcg(lay, dev(eta), dev(hx), dev(b), x, rtol=rtol, maxit=5000, prec=p)[0]
+    assert info["status"] == 0 and info["ratio"] <= rtol
+    assert rel(host(x), ref) < (1e-10 if prec == "fp64" else 1e-9)
     if prec == "fp64":
         _, it12, _, _ = O.solve_G(eta, hx, b, grid, rtol=1e-12, maxit=5000)
         assert abs(info["iters"] - it12) <= 1

@@ -32,9 +32,11 @@ def test_noalloc_matches_sgn_pcg_on_two_calls_in_a_row():
         hx = O.deriv(h, 1.0)
         lay = sgn.Layout(ctx, [sgn.Grid(1, n, 1.0)])
         x_ref = torch.zeros(n, dtype=torch.float64, device="cuda")
-        info_ref = sgn.pcg(lay, d(eta), d(hx), d(b), x_ref, rtol=1e-12, maxit=5000, prec=prec)[0]
+        # mixed precision: 1e-11 (its double-float residual floor is near 1e-12 on h0 = 4)
+        rtol = 1e-12 if prec == sgn.PREC_FP64 else 1e-11
+        info_ref = sgn.pcg(lay, d(eta), d(hx), d(b), x_ref, rtol=rtol, maxit=5000, prec=prec)[0]
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
-        st, info = sgn.pcg1d_noalloc(n, 1.0, d(eta), d(hx), d(b), x, rtol=1e-12, maxit=5000,
+        st, info = sgn.pcg1d_noalloc(n, 1.0, d(eta), d(hx), d(b), x, rtol=rtol, maxit=5000,
                                      prec=prec)
         torch.cuda.synchronize()
         assert st == sgn.SGN_OK and info["status"] == sgn.SGN_OK
