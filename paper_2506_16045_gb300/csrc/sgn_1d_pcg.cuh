@@ -59,13 +59,11 @@ using f1::XBuf;
 
 // Shared memory of one solve CTA (bytes):
 //   [0, 16 n)       exchange planes of the double-float / float64 transforms; the float32
-//                   inner solve uses [0, 8 n) for its exchanges and, after it, keeps its
-//                   thread-private slot arrays d (correction), r (residual) and the
-//                   preconditioner symbol 1/(sigma + alpha k^2), [RP + 1][NT] each;
+//                   inner solve uses [0, 8 n) for its exchanges and, after them, keeps its
+//                   thread-private slot arrays d (correction) and r (residual), [RP + 1][NT]
+//                   each, which live only while the inner solve runs;
 //   [off_e, +8 n)   (mixed) float32 eta and h_x, from which the inner solve forms its
 //                   coefficients.
-// The slot arrays outlive no double-float transform except the symbol table, which lies
-// beyond the double-float planes.
 template <int L>
 struct SmemPcg {
   using PL = Plan<L>;
@@ -73,12 +71,11 @@ struct SmemPcg {
   static constexpr size_t slot_c = (size_t)(PL::RP + 1) * PL::NT * 8;   // complex float
   static constexpr size_t off_d = 8 * n;
   static constexpr size_t off_r = off_d + slot_c;
-  static constexpr size_t off_di = off_r + slot_c;
-  static constexpr size_t end_di = off_di + slot_c / 2;
-  static constexpr size_t off_e = ((16 * n > end_di ? 16 * n : end_di) + 15) / 16 * 16;
+  static constexpr size_t end_r = off_r + slot_c;
+  static constexpr size_t off_e = ((16 * n > end_r ? 16 * n : end_r) + 15) / 16 * 16;
   static constexpr size_t mixed = off_e + 8 * n;
   static constexpr size_t fp64 = 16 * n;
-  static_assert(off_di >= 16 * n || PL::RP < 2, "symbol table must clear the planes");
+  static_assert(mixed + 1024 <= 232448, "solve CTA exceeds the shared memory of one SM");
 };
 
 // Double-float coefficients of Def:MatrixM in 1d (c1 = eta (1 + h_x^2), c2 = eta^2 h_x / 2,
@@ -408,12 +405,6 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
     const f1::TwF32 twf;
     cplx<float>* D = reinterpret_cast<cplx<float>*>(smem + SM::off_d);   // [RP + 1][NT]
     cplx<float>* Rr = reinterpret_cast<cplx<float>*>(smem + SM::off_r);  // [RP + 1][NT]
-    float* DI = reinterpret_cast<float*>(smem + SM::off_di);             // [RP + 1][NT]
-    if (g.act) {
-#pragma unroll
-      for (int q = 0; q < RP; ++q) DI[q * NT + t] = dinv(g.mode(SL::b(q), SL::s(q)));
-      if (t0) DI[RP * NT] = dN;
-    }
     const df inv_n(1.0f / (float)n, 0.0f);                                 // exact
     const float inv_nf = 1.0f / (float)n;
     const df one(1.0f, 0.0f), zero(0.0f, 0.0f);
@@ -516,7 +507,7 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
 #pragma unroll
           for (int q = 0; q < RP; ++q) {
             const cplx<float> r = rf[q] * scale;
-            p[q] = r * DI[q * NT + t];
+            p[q] = r * dinv(g.mode(SL::b(q), SL::s(q)));
             loc += ((t0 && q == 0) ? 1.0f : 2.0f) * (r.x * p[q].x + r.y * p[q].y);
             Rr[q * NT + t] = r;
             D[q * NT + t] = mk(0.0f, 0.0f);
@@ -604,7 +595,7 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
               D[o] = D[o] + p[q] * at;
               const cplx<float> r = Rr[o] - gq[q] * at;
               Rr[o] = r;
-              rz_loc += ((t0 && q == 0) ? 1.0f : 2.0f) * (r.x * r.x + r.y * r.y) * DI[o];
+              rz_loc += ((t0 && q == 0) ? 1.0f : 2.0f) * (r.x * r.x + r.y * r.y) * dinv(g.mode(SL::b(q), SL::s(q)));
             }
             if (t0) {
               D[RP * NT] = D[RP * NT] + pN * at;
@@ -633,7 +624,7 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
 #pragma unroll
             for (int q = 0; q < RP; ++q) {
               const int o = q * NT + t;
-              p[q] = Rr[o] * DI[o] + p[q] * beta;
+              p[q] = Rr[o] * dinv(g.mode(SL::b(q), SL::s(q))) + p[q] * beta;
             }
             if (t0) pN = Rr[RP * NT] * dN + pN * beta;
           }

@@ -160,10 +160,9 @@ sgn_status fail(sgn_ctx* ctx, sgn_status s, const std::string& msg) {
 }
 
 sgn_status cuda_fail(sgn_ctx* ctx, cudaError_t e, const char* where) {
-  if (e == cudaErrorMemoryAllocation) {
-    cudaGetLastError();
+  cudaGetLastError();   // a failed call also sets the runtime's last error: do not pass it on
+  if (e == cudaErrorMemoryAllocation)
     return fail(ctx, SGN_ERR_NOMEM, std::string(where) + ": out of device memory");
-  }
   return fail(ctx, SGN_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 

@@ -1,8 +1,9 @@
 // Register-blocked Stockham FFT for one 1d instance per CTA, with a paired spectral layout.
 //
-// A length-n transform (n = 2^L) runs on NTA = n/E threads that each hold E = 16 (n >= 512),
-// 8 (n = 256) or 4 (n <= 128) elements in registers.  Thread t's "natural" elements are
-// x[t + e NTA], e < E.  The transform is a sequence of Stockham stages: a stage of radix R
+// A length-n transform (n = 2^L) runs on NTA = n/E threads that each hold E = 8 (n >= 256)
+// or 4 (n <= 128) elements in registers (8 rather than 16: twice the resident warps, and a
+// double-float or float64 stage fits the 64 registers per thread of a 1024-thread CTA).
+// Thread t's "natural" elements are x[t + e NTA], e < E.  The transform is a sequence of Stockham stages: a stage of radix R
 // at sub-transform length P takes butterfly i's inputs x[i + r n/R], twiddles them by
 // w^{r k} (w = e^{-+2 pi i/(P R)}, k = i mod P), applies the R-point DFT, and writes output
 // s to ((i - k) R + k) + s P.  Every stage but the paired one gives each thread E/R
@@ -50,7 +51,7 @@ __device__ __forceinline__ void static_for(F&& f) {
 template <int L>
 struct Plan {
   static constexpr int n = 1 << L;
-  static constexpr int LE = L >= 9 ? 4 : (L == 8 ? 3 : 2);   // log2 elements per thread
+  static constexpr int LE = L >= 8 ? 3 : 2;                 // log2 elements per thread
   static constexpr int E = 1 << LE;
   static constexpr int LP = LE - 1;                          // log2 radix of the paired stage
   static constexpr int RP = 1 << LP;
@@ -75,7 +76,8 @@ struct Plan {
     for (int i = q + 1; i < NS; ++i) s += bits(i);
     return s;
   }
-  // CTAs per SM the kernels are compiled for: keeps 128 registers per thread available
+  // CTAs per SM the kernels are compiled for: one CTA of NT >= 512 threads (65536 / NT
+  // registers per thread), else enough CTAs for 512 threads (128 registers per thread)
   static constexpr int kMinBlocks = NT >= 512 ? 1 : 512 / NT;
 };
 
