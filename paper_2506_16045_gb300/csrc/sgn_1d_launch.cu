@@ -29,11 +29,12 @@ extern template cudaError_t rhs1d_launch<11>(const RhsArgs&, int, int, cudaStrea
 extern template cudaError_t rhs1d_launch<12>(const RhsArgs&, int, int, cudaStream_t);
 extern template cudaError_t rhs1d_launch<13>(const RhsArgs&, int, int, cudaStream_t);
 
-cudaError_t launch_pcg1d(const Layout1d& lay, const void* tw64, const void* tw32, int precision,
-                         const double* eta, const double* hx, const double* b, double* x,
-                         const SolveRec* given, int kind, double rtol, double rtol_inner,
-                         int maxit, int max_refine, SolveRec* rec, void* ws, float* coef_df,
-                         cudaStream_t s) {
+namespace {
+
+PcgArgs pcg_args(const Layout1d& lay, const void* tw64, const void* tw32, int precision,
+                 const double* eta, const double* hx, const double* b, double* x,
+                 const SolveRec* given, int kind, double rtol, double rtol_inner, int maxit,
+                 int max_refine, SolveRec* rec, void* ws, float* coef_df) {
   PcgArgs a;
   a.insts = lay.d_inst;
   a.ids = lay.d_ids;
@@ -53,15 +54,13 @@ cudaError_t launch_pcg1d(const Layout1d& lay, const void* tw64, const void* tw32
   a.ws = static_cast<cplx<double>*>(ws);
   a.coef_df = precision == SGN_PREC_MIXED ? coef_df : nullptr;
   a.precision = precision;
-  return d1::for_each_size(lay, s, [&](auto Lc, int first, int num, cudaStream_t cs) {
-    return pcg1d_launch<decltype(Lc)::value>(a, first, num, cs);
-  });
+  a.ux = nullptr;
+  return a;
 }
 
-cudaError_t launch_rhs1d(const Layout1d& lay, const void* tw64, const void* tw32, int precision,
-                         double g, const double* eta, const double* u, const double* h,
-                         const double* hx, double* f_eta, double* f_U, double* scratch,
-                         cudaStream_t s) {
+RhsArgs rhs_args(const Layout1d& lay, const void* tw64, const void* tw32, int precision,
+                 double g, const double* eta, const double* u, const double* h,
+                 const double* hx, double* f_eta, double* f_U, double* scratch) {
   RhsArgs a;
   a.insts = lay.d_inst;
   a.ids = lay.d_ids;
@@ -77,6 +76,53 @@ cudaError_t launch_rhs1d(const Layout1d& lay, const void* tw64, const void* tw32
   a.scratch = scratch;
   a.P = lay.points;
   a.precision = precision;
+  a.ux_given = 0;
+  return a;
+}
+
+}  // namespace
+
+cudaError_t launch_pcg1d(const Layout1d& lay, const void* tw64, const void* tw32, int precision,
+                         const double* eta, const double* hx, const double* b, double* x,
+                         const SolveRec* given, int kind, double rtol, double rtol_inner,
+                         int maxit, int max_refine, SolveRec* rec, void* ws, float* coef_df,
+                         cudaStream_t s) {
+  const PcgArgs a = pcg_args(lay, tw64, tw32, precision, eta, hx, b, x, given, kind, rtol,
+                             rtol_inner, maxit, max_refine, rec, ws, coef_df);
+  return d1::for_each_size(lay, s, [&](auto Lc, int first, int num, cudaStream_t cs) {
+    return pcg1d_launch<decltype(Lc)::value>(a, first, num, cs);
+  });
+}
+
+cudaError_t launch_pcg1d_ux(const Layout1d& lay, const void* tw64, const void* tw32,
+                            int precision, const double* eta, const double* hx, const double* b,
+                            double* x, int kind, double rtol, double rtol_inner, int maxit,
+                            int max_refine, SolveRec* rec, void* ws, float* coef_df,
+                            double* scratch, cudaStream_t s) {
+  PcgArgs a = pcg_args(lay, tw64, tw32, precision, eta, hx, b, x, nullptr, kind, rtol,
+                       rtol_inner, maxit, max_refine, rec, ws, coef_df);
+  a.ux = scratch;
+  return d1::for_each_size(lay, s, [&](auto Lc, int first, int num, cudaStream_t cs) {
+    return pcg1d_launch<decltype(Lc)::value>(a, first, num, cs);
+  });
+}
+
+cudaError_t launch_rhs1d(const Layout1d& lay, const void* tw64, const void* tw32, int precision,
+                         double g, const double* eta, const double* u, const double* h,
+                         const double* hx, double* f_eta, double* f_U, double* scratch,
+                         cudaStream_t s) {
+  const RhsArgs a = rhs_args(lay, tw64, tw32, precision, g, eta, u, h, hx, f_eta, f_U, scratch);
+  return d1::for_each_size(lay, s, [&](auto Lc, int first, int num, cudaStream_t cs) {
+    return rhs1d_launch<decltype(Lc)::value>(a, first, num, cs);
+  });
+}
+
+cudaError_t launch_rhs1d_ux(const Layout1d& lay, const void* tw64, const void* tw32,
+                            int precision, double g, const double* eta, const double* u,
+                            const double* h, const double* hx, double* f_eta, double* f_U,
+                            double* scratch, cudaStream_t s) {
+  RhsArgs a = rhs_args(lay, tw64, tw32, precision, g, eta, u, h, hx, f_eta, f_U, scratch);
+  a.ux_given = 1;
   return d1::for_each_size(lay, s, [&](auto Lc, int first, int num, cudaStream_t cs) {
     return rhs1d_launch<decltype(Lc)::value>(a, first, num, cs);
   });

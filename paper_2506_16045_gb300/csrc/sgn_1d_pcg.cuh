@@ -45,6 +45,7 @@ struct PcgArgs {
   cplx<double>* ws;
   float* coef_df;
   int precision;
+  void* ux;             // nullable: also store x_x here (see pcg_body)
 };
 
 template <int L>
@@ -124,9 +125,13 @@ struct Slot {
   static constexpr int reg(int q) { return b(q) * Plan<L>::RP + s(q); }
 };
 
+// The solve of one instance by one CTA.  With ux non-null it also stores x_x
+// (double-float for the mixed path, float64 otherwise) at ux[off + j]: the mixed path takes
+// it from the inverse transform of its last refinement pass, which yields x + i x_x; the
+// float64 path from its final transform.  A right-hand side that follows the solve in a
+// time step then needs one derivative pair less.
 template <int L, bool MIXED>
-__global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
-    k_pcg1d(const __grid_constant__ PcgArgs A, int first) {
+__device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) {
   using PL = Plan<L>;
   using SL = Slot<L>;
   using SM = SmemPcg<L>;
@@ -378,27 +383,34 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
       }
     }
     R.ratio = sqrt(rz) / bnorm;
-    // x = F^{-1} x^ = conj(F(conj x^)) / n
+    // x = F^{-1} x^ = conj(F(conj x^)) / n; with ux, the transform of Z = (1 - k) x^ (mirror
+    // (1 + k) conj x^) instead, which gives x + i x_x
     __syncthreads();
     if (g.act) {
 #pragma unroll
       for (int q = 0; q < RP; ++q) {
         const int m = g.mode(SL::b(q), SL::s(q));
+        const double k = ux ? kunit * (double)m : 0.0;
         const cplx<double> xv = Xh[m];
         if (t0 && q == 0) {
           XH.st(0, mk(xv.x, 0.0));
         } else {
-          XH.st(f1::swz(m), conj(xv));
-          XH.st(f1::swz(n - m), xv);
+          XH.st(f1::swz(m), conj(xv) * (1.0 - k));
+          XH.st(f1::swz(n - m), xv * (1.0 + k));
         }
       }
       if (t0) XH.st(f1::swz(h), mk(Xh[h].x, 0.0));
     }
     __syncthreads();
     f1::fft_smem<double, L>(XH, A.tw64);
-    if (g.act)
+    if (g.act) {
 #pragma unroll
-      for (int e = 0; e < E; ++e) x[t + e * NTA] = XH.ld(g.bnat ^ f1::swz_c(e * NTA)).x * inv_n;
+      for (int e = 0; e < E; ++e) {
+        const cplx<double> z = XH.ld(g.bnat ^ f1::swz_c(e * NTA));
+        x[t + e * NTA] = z.x * inv_n;
+        if (ux) static_cast<double*>(ux)[I.off + t + e * NTA] = -z.y * inv_n;
+      }
+    }
   } else {
     // ------------------------------------------------------------------ mixed precision
     const XBuf<float> XF(smem, n);
@@ -442,6 +454,7 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
             const cplx<df> z = XH.ld(a);         // conj of n (x + i x_x)
             const df pv = z.x * inv_n, px = -(z.y * inv_n);
             x[j] = to_f64(pv);
+            if (ux) static_cast<df*>(ux)[I.off + j] = px;
             const df c1(cdf[j], cdf[3 * n + j]), c2(cdf[n + j], cdf[4 * n + j]),
                 c3(cdf[2 * n + j], cdf[5 * n + j]);
             XH.st(a, mk(c1 * pv + c2 * px, c2 * pv + c3 * px));
@@ -656,6 +669,12 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
   R.iters = iters;
   R.status = status;
   if (t0) A.rec[id] = R;
+}
+
+template <int L, bool MIXED>
+__global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
+    k_pcg1d(const __grid_constant__ PcgArgs A, int first) {
+  pcg_body<L, MIXED>(A, first, A.ux);
 }
 
 }  // namespace pcg1d

@@ -30,6 +30,7 @@ struct RhsArgs {
   double* scratch;        // 5 planes of P values (8 bytes each)
   long long P;
   int precision;
+  int ux_given;           // 1: the first scratch plane already holds u_x (see rhs_body)
 };
 
 template <int L>
@@ -70,9 +71,12 @@ __device__ __forceinline__ void deriv_pair(const XBuf<T>& X, cplx<T> (&v)[Plan<L
   }
 }
 
-template <typename T, int L>
-__global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
-    k_rhs1d(const __grid_constant__ RhsArgs A, int first) {
+// The right-hand side of one instance by one CTA.  UXG: d = u_x is already in the first
+// scratch plane (written by the solve that produced u, in the same precision), so the
+// derivative pairs are (eta u, zeta) -> (m, zeta_x), (s, d) -> (s_x, d_x) and Phi': six
+// transforms instead of eight.
+template <typename T, int L, bool UXG>
+__device__ __forceinline__ void rhs_body(const RhsArgs& A, int first) {
   using PL = Plan<L>;
   constexpr int n = PL::n, E = PL::E, NTA = PL::NTA;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -96,43 +100,67 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
   T* ssx = reinterpret_cast<T*>(A.scratch + 3 * A.P + I.off);   // s_x
   T* spsi = reinterpret_cast<T*>(A.scratch + 4 * A.P + I.off);  // Psi
   cplx<T> v[E];
-  if (act) {
+  if constexpr (UXG) {
+    if (act) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int j = t + e * NTA;
-      const T uj = num<T>(u[j]);
-      v[e] = mk(uj, num<T>(eta[j]) * uj);
+      for (int e = 0; e < E; ++e) {
+        const int j = t + e * NTA;
+        const T ej = num<T>(eta[j]);
+        v[e] = mk(ej * num<T>(u[j]), ej - num<T>(hh[j]));
+      }
     }
-  }
-  deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);
-  if (act) {
+    deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);
+    if (act) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int j = t + e * NTA;
-      sd[j] = v[e].x;
-      sm[j] = v[e].y;
-      v[e] = mk(num<T>(eta[j]) - num<T>(hh[j]), num<T>(hx[j]) * num<T>(u[j]));
+      for (int e = 0; e < E; ++e) {
+        const int j = t + e * NTA;
+        sm[j] = v[e].x;
+        szx[j] = v[e].y;
+        v[e] = mk(num<T>(hx[j]) * num<T>(u[j]), sd[j]);
+      }
     }
-  }
-  deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);
-  if (act) {
+    deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);   // v = (s_x, d_x)
+  } else {
+    if (act) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int j = t + e * NTA;
-      szx[j] = v[e].x;
-      ssx[j] = v[e].y;
-      v[e] = mk(sd[j], from_int<T>(0));
+      for (int e = 0; e < E; ++e) {
+        const int j = t + e * NTA;
+        const T uj = num<T>(u[j]);
+        v[e] = mk(uj, num<T>(eta[j]) * uj);
+      }
     }
+    deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);
+    if (act) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int j = t + e * NTA;
+        sd[j] = v[e].x;
+        sm[j] = v[e].y;
+        v[e] = mk(num<T>(eta[j]) - num<T>(hh[j]), num<T>(hx[j]) * num<T>(u[j]));
+      }
+    }
+    deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);
+    if (act) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int j = t + e * NTA;
+        szx[j] = v[e].x;
+        ssx[j] = v[e].y;
+        v[e] = mk(sd[j], from_int<T>(0));
+      }
+    }
+    deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);   // v.x = d_x
   }
-  deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);
   if (act) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int j = t + e * NTA;
       const T ej = num<T>(eta[j]), uj = num<T>(u[j]), d = sd[j], m = sm[j];
+      const T dx = UXG ? v[e].y : v[e].x;
+      const T sx = UXG ? v[e].x : ssx[j];
       const T s = num<T>(hx[j]) * uj;
-      const T Q = uj * v[e].x - d * d;
-      const T Sv = uj * ssx[j];
+      const T Q = uj * dx - d * d;
+      const T Sv = uj * sx;
       const T e2 = ej * ej;
       const T md = m * d;
       const T Phi = e2 * ej * Q * third + e2 * md + half(e2 * Sv) + ej * m * s - ej * uj * uj;
@@ -152,24 +180,27 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
   }
 }
 
+template <typename T, int L, bool UXG>
+__global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
+    k_rhs1d(const __grid_constant__ RhsArgs A, int first) {
+  rhs_body<T, L, UXG>(A, first);
+}
+
 }  // namespace rhs1d
 
 template <int L>
 cudaError_t rhs1d_launch(const RhsArgs& a, int first, int num, cudaStream_t s) {
   using PL = f1::Plan<L>;
   const size_t sm = (size_t)16 << L;
-  if (a.precision == SGN_PREC_MIXED) {
-    auto k = rhs1d::k_rhs1d<df, L>;
+  auto go = [&](auto k) -> cudaError_t {
     cudaError_t e = d1::set_smem(k, sm);
     if (e) return e;
     k<<<num, PL::NT, sm, s>>>(a, first);
-  } else {
-    auto k = rhs1d::k_rhs1d<double, L>;
-    cudaError_t e = d1::set_smem(k, sm);
-    if (e) return e;
-    k<<<num, PL::NT, sm, s>>>(a, first);
-  }
-  return cudaGetLastError();
+    return cudaGetLastError();
+  };
+  if (a.precision == SGN_PREC_MIXED)
+    return a.ux_given ? go(rhs1d::k_rhs1d<df, L, true>) : go(rhs1d::k_rhs1d<df, L, false>);
+  return a.ux_given ? go(rhs1d::k_rhs1d<double, L, true>) : go(rhs1d::k_rhs1d<double, L, false>);
 }
 
 }  // namespace sgn

@@ -779,6 +779,36 @@ sgn_status copy_field(sgn_state* st, double* dst, const double* src, long long n
     if (s_ != SGN_OK) return s_; \
   } while (0)
 
+// Solve G u = U at eta, then the right-hand side at (eta, u).  For 1d layouts the
+// right-hand side reuses the u_x that the solve leaves in the scratch planes.
+sgn_status stage_at(sgn_state* st, const double* eta, const double* U, double* u, double* fe,
+                    double* fU, const sgn_opts* o, cudaStream_t s) {
+  sgn_layout* lay = st->lay;
+  if (lay->dim != 1) {
+    SGN_TRY(solve_at(st, eta, U, u, o, s));
+    return rhs_at(st, eta, u, fe, fU, s);
+  }
+  sgn_ctx* ctx = lay->ctx;
+  const double rtol_inner = o->rtol_inner > 0.0 ? o->rtol_inner : -1.0;
+  const int max_refine = o->max_refine > 0 ? o->max_refine : 12;
+  {
+    ProfScope prof(ctx, s, 0);
+    const cudaError_t e = sgn::launch_pcg1d_ux(
+        lay->l1, ctx->tw64, ctx->tw32, o->prec, eta, st->gradh, U, u, o->coef, o->rtol,
+        rtol_inner, o->maxit, max_refine, lay->rec, lay->ws, lay->coef_df, lay->scratch, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pcg launch");
+  }
+  k_accum<<<1, 256, 0, s>>>(lay->rec, lay->l1.d_inst, lay->count, 0, 0,
+                           o->prec == SGN_PREC_MIXED, st->stats);
+  SGN_CUDA(ctx, cudaGetLastError());
+  ProfScope prof(ctx, s, 1);
+  const cudaError_t e = sgn::launch_rhs1d_ux(lay->l1, ctx->tw64, ctx->tw32, o->prec,
+                                             lay->grids[0].g, eta, u, st->h, st->gradh, fe, fU,
+                                             lay->scratch, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "rhs launch");
+  return SGN_OK;
+}
+
 // One RK4 step (Eq:ERK): stages with a_{i,i-1} = 1/2, 1/2, 1 and weights 1/6, 1/3, 1/3, 1/6.
 sgn_status rk4_once(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
   const int d = st->d;
@@ -789,8 +819,7 @@ sgn_status rk4_once(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
   for (int i = 1; i < 4; ++i) {
     SGN_TRY(lincomb(st, st->eta_s, {{st->eta, 1.0}}, {{st->fe[i - 1], a[i]}}, 1, s));
     SGN_TRY(lincomb(st, st->U_s, {{st->U, 1.0}}, {{st->fU[i - 1], a[i]}}, d, s));
-    SGN_TRY(solve_at(st, st->eta_s, st->U_s, st->u_s, o, s));
-    SGN_TRY(rhs_at(st, st->eta_s, st->u_s, st->fe[i], st->fU[i], s));
+    SGN_TRY(stage_at(st, st->eta_s, st->U_s, st->u_s, st->fe[i], st->fU[i], o, s));
   }
   const double b0 = 1.0 / 6.0, b1 = 1.0 / 3.0;
   SGN_TRY(lincomb(st, st->eta, {{st->eta, 1.0}},
@@ -910,13 +939,16 @@ extern "C" sgn_status sgn_step_abk(sgn_state* st, int order, const double* dt, i
   SGN_TRY(upload_dt(st, dt, s));
   st->last = s;
   const int d = st->d;
-  auto push = [&]() -> sgn_status {
+  auto make_room = [&]() {
     // rotate so that he[levels-1] is the newest
     if (st->levels == 4) {
       std::rotate(st->he, st->he + 1, st->he + 4);
       std::rotate(st->hU, st->hU + 1, st->hU + 4);
       st->levels = 3;
     }
+  };
+  auto push = [&]() -> sgn_status {
+    make_room();
     SGN_TRY(rhs_at(st, st->eta, st->u, st->he[st->levels], st->hU[st->levels], s));
     st->levels += 1;
     return SGN_OK;
@@ -946,9 +978,15 @@ extern "C" sgn_status sgn_step_abk(sgn_state* st, int order, const double* dt, i
                         {{hU[0], B[4][0]}, {hU[1], B[4][1]}, {hU[2], B[4][2]}, {hU[3], B[4][3]}},
                         d, s));
       }
-      SGN_TRY(solve_at(st, st->eta, st->U, st->u, opts, s));
+      // the solve for u_{n+1} and the newest history level f(w_{n+1}) (the combinations
+      // above were launched with the current history pointers, so rotating is safe)
+      make_room();
+      SGN_TRY(stage_at(st, st->eta, st->U, st->u, st->he[st->levels], st->hU[st->levels], opts,
+                       s));
+      st->levels += 1;
       st->t += st->dt_last[0];
       st->step += 1;
+      continue;
     }
     SGN_TRY(push());
   }

@@ -3,8 +3,9 @@
 // A length-n transform (n = 2^L) runs on NTA = n/E threads that each hold E = 8 (n >= 256)
 // or 4 (n <= 128) elements in registers (8 rather than 16: twice the resident warps, and a
 // double-float or float64 stage fits the 64 registers per thread of a 1024-thread CTA).
-// Thread t's "natural" elements are x[t + e NTA], e < E.  The transform is a sequence of Stockham stages: a stage of radix R
-// at sub-transform length P takes butterfly i's inputs x[i + r n/R], twiddles them by
+// Thread t's "natural" elements are x[t + e NTA], e < E.  The transform is a sequence of
+// Stockham stages: a stage of radix R at sub-transform length P takes butterfly i's inputs
+// x[i + r n/R], twiddles them by
 // w^{r k} (w = e^{-+2 pi i/(P R)}, k = i mod P), applies the R-point DFT, and writes output
 // s to ((i - k) R + k) + s P.  Every stage but the paired one gives each thread E/R
 // butterflies whose inputs are its natural elements, so a stage is: compute in registers,

@@ -75,6 +75,19 @@ cudaError_t launch_rhs1d(const Layout1d& lay, const void* tw64, const void* tw32
                          double g, const double* eta,
                          const double* u, const double* h, const double* hx, double* f_eta,
                          double* f_U, double* scratch, cudaStream_t s);
+// Solve and right-hand side of a time-stepping stage, passing u_x between them: the solve
+// (as launch_pcg1d with computed coefficients of `kind`) also stores x_x in the first plane
+// of `scratch` (double-float for MIXED, float64 otherwise), and the right-hand side (as
+// launch_rhs1d at u = x) takes it from there: six transforms instead of eight.
+cudaError_t launch_pcg1d_ux(const Layout1d& lay, const void* tw64, const void* tw32,
+                            int precision, const double* eta, const double* hx, const double* b,
+                            double* x, int kind, double rtol, double rtol_inner, int maxit,
+                            int max_refine, SolveRec* rec, void* ws, float* coef_df,
+                            double* scratch, cudaStream_t s);
+cudaError_t launch_rhs1d_ux(const Layout1d& lay, const void* tw64, const void* tw32,
+                            int precision, double g, const double* eta, const double* u,
+                            const double* h, const double* hx, double* f_eta, double* f_U,
+                            double* scratch, cudaStream_t s);
 // out = base + sum_j c_j dt_i f_j over up to 4 terms (per-instance dt from `dt`)
 cudaError_t launch_axpy1d(const Layout1d& lay, const double* dt, double* out, const double* base,
                           int nterms, const double* const* f, const double* c, double scale,
