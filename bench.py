@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the shelf/2d/serving sections after the headline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--only-config", choices=["shelf_1d", "bump_2d", "serving"],
+                    help="run only this extra configuration and print its result as one JSON "
+                         "line (for profiling one workload; not the headline)")
     return ap.parse_args()
 
 
@@ -578,6 +581,15 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             reference_arm(args)
+        return
+    if args.only_config:
+        import torch
+
+        from paper_2506_16045_gb300 import sgn
+        ctx = sgn.Context(0)
+        fn = {"shelf_1d": bench_shelf, "bump_2d": bench_2d, "serving": bench_serving}
+        print(json.dumps({args.only_config: fn[args.only_config](sgn, ctx, torch)}))
+        ctx.close()
         return
     gpu_arm(args, world, rank, local, pg)
 

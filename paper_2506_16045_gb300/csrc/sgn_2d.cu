@@ -36,6 +36,10 @@ struct Scal2d {
   unsigned int ticket; // last-block counter
   double sigma, alpha_A, kappa_ub, eta_min, eta_max;
   int flat;
+  // float32 copies for the inner solve's kernels, written where the doubles are: on this
+  // part a float64 instruction costs 62 float32 ones, so per-mode work stays in float32
+  float sigf, alphaAf, isigf;   // sigma, alpha of A and 1 / sigma
+  float alphaf, betaf;          // CG alpha, beta
 };
 
 namespace {
@@ -106,14 +110,108 @@ struct Tw<df> {
   }
 };
 
+// ---- per-mode arithmetic in the working precision ---------------------------------------
+// float32 for the float32 kernels of the inner solve, float64 otherwise.
+template <typename T>
+struct WorkP {
+  using type = double;
+};
+template <>
+struct WorkP<float> {
+  using type = float;
+};
+
+template <typename TP>
+struct ModesT {
+  TP kxu, kyu;
+  int nx, ny;
+  __device__ __forceinline__ explicit ModesT(const Modes2d& M)
+      : kxu((TP)M.kxu), kyu((TP)M.kyu), nx(M.nx), ny(M.ny) {}
+  __device__ __forceinline__ TP kx(int c) const { return c == (nx >> 1) ? TP(0) : kxu * (TP)c; }
+  __device__ __forceinline__ TP ky(int y) const { return kyu * (TP)wave_index(y, ny); }
+  __device__ __forceinline__ TP weight(int c) const {
+    return (c == 0 || c == (nx >> 1)) ? TP(1) : TP(2);
+  }
+};
+
+// z = A^{-1} r per mode (Sherman-Morrison of sigma I + alpha k k^T)
+template <typename TP>
+struct AinvT {
+  TP sigma, alpha, isig;
+  __device__ __forceinline__ void apply(TP kx, TP ky, cplx<TP> r1, cplx<TP> r2, cplx<TP>& z1,
+                                        cplx<TP>& z2) const {
+    const TP f = alpha * recip(sigma + alpha * (kx * kx + ky * ky));
+    const cplx<TP> kr = r1 * kx + r2 * ky;
+    z1 = (r1 - kr * (f * kx)) * isig;
+    z2 = (r2 - kr * (f * ky)) * isig;
+  }
+};
+__device__ __forceinline__ AinvT<float> ainv_of(const Scal2d* sc, float) {
+  return AinvT<float>{sc->sigf, sc->alphaAf, sc->isigf};
+}
+__device__ __forceinline__ AinvT<double> ainv_of(const Scal2d* sc, double) {
+  return AinvT<double>{sc->sigma, sc->alpha_A, 1.0 / sc->sigma};
+}
+__device__ __forceinline__ float cg_alpha(const Scal2d* sc, float) { return sc->alphaf; }
+__device__ __forceinline__ double cg_alpha(const Scal2d* sc, double) { return sc->alpha; }
+__device__ __forceinline__ float cg_beta(const Scal2d* sc, float) { return sc->betaf; }
+__device__ __forceinline__ double cg_beta(const Scal2d* sc, double) { return sc->beta; }
+
+// 2^-e in T (exact), for the 1 / (nx ny) of the inverse transforms
+template <typename T>
+__device__ __forceinline__ T pow2_inv(int e) {
+  const float f = __int_as_float((127 - e) << 23);
+  if constexpr (std::is_same<T, df>::value) return df(f, 0.0f);
+  else return (T)f;
+}
+
+// wavenumber of column c (x) or row y in the number type T of a kernel's data
+template <typename T, typename TP>
+__device__ __forceinline__ T mode_k(const ModesT<TP>& MT, int i, bool xdir) {
+  const TP k = xdir ? MT.kx(i) : MT.ky(i);
+  if constexpr (std::is_same<T, df>::value) return df((double)k);
+  else return (T)k;
+}
+
+// high-precision value -> working precision, and back, without float64 where T is float
+template <typename T>
+__device__ __forceinline__ T to_work(double v) { return (T)v; }
+template <typename T>
+__device__ __forceinline__ T to_work(df v) { return (T)to_f64(v); }
+template <>
+__device__ __forceinline__ float to_work<float>(df v) { return v.hi + v.lo; }
+template <typename TH>
+__device__ __forceinline__ TH widen(float v) { return (TH)v; }
+template <>
+__device__ __forceinline__ df widen<df>(float v) { return df(v, 0.0f); }
+template <typename TH>
+__device__ __forceinline__ TH widen(double v) { return num<TH>(v); }
+
 // ---- last-block reduction ------------------------------------------------------------
 // Each block writes its partial sum; the last block to arrive sums them in a fixed order
-// (deterministic) and runs `fin(total)` on thread 0.
+// (deterministic) and runs `fin(total)` on thread 0.  float32 partials reduce across the
+// block in double-float; only the block sums are float64.
+template <int NT, typename Fin>
+__device__ __forceinline__ void grid_finish(double s, double* parts, Scal2d* sc, Fin fin);
+
 template <int NT, typename Fin>
 __device__ __forceinline__ void grid_reduce(double v, double* parts, Scal2d* sc, Fin fin) {
+  __shared__ double redb[NT / 32 + 1];
+  grid_finish<NT>(block_sum<NT>(v, redb), parts, sc, fin);
+}
+
+template <int NT, typename Fin>
+__device__ __forceinline__ void grid_reduce(float v, double* parts, Scal2d* sc, Fin fin) {
+  __shared__ df slot[NT / 32];
+  __shared__ double bs;
+  block_sum_df<NT>(v, slot, [&](float hi, float lo) { bs = (double)hi + (double)lo; });
+  grid_finish<NT>(bs, parts, sc, fin);
+}
+
+template <int NT, typename Fin>
+__device__ __forceinline__ void grid_finish(double s, double* parts, Scal2d* sc, Fin fin) {
   __shared__ double red[NT / 32 + 1];
   __shared__ bool last;
-  double s = block_sum<NT>(v, red);
   if (threadIdx.x == 0) {
     parts[blockIdx.x] = s;
     __threadfence();
@@ -167,7 +265,8 @@ __global__ void __launch_bounds__(kColNT, 1) k2_cols(Modes2d M, int log2ny, cons
   const int ny = M.ny, H = M.H, stride = ny + 1;
   const int c0 = blockIdx.x * TW;
   const int nplanes = (MODE == COL_MATVEC_IN || MODE == COL_MATVEC_OUT) ? 3 : a.K;
-  const double sigma = a.sc ? a.sc->sigma : 0.0, alphaA = a.sc ? a.sc->alpha_A : 0.0;
+  using TP = typename WorkP<T>::type;         // per-mode precision (float32 for float32)
+  const ModesT<TP> MT(M);
 
   // ---- load
   for (int e = threadIdx.x; e < TW * ny; e += kColNT) {
@@ -178,18 +277,16 @@ __global__ void __launch_bounds__(kColNT, 1) k2_cols(Modes2d M, int log2ny, cons
       cplx<T> p1 = mk(from_int<T>(0), from_int<T>(0)), p2 = p1;
       if (ok) {
         if (a.pupdate) {
-          // p = A^{-1} r + beta p (Sherman-Morrison of sigma I + alpha k k^T)
-          const double kx = M.kx(col), ky = M.ky(y);
-          cplx<T> r1 = ld_c<T>(a.rin[0], gi), r2 = ld_c<T>(a.rin[1], gi);
-          cplx<T> q1 = ld_c<T>(a.pio[0], gi), q2 = ld_c<T>(a.pio[1], gi);
-          const T beta = num<T>(a.sc->beta);
-          const T kxT = num<T>(kx), kyT = num<T>(ky);
-          const T f = num<T>(alphaA / (sigma + alphaA * (kx * kx + ky * ky)));
-          const T is = num<T>(1.0 / sigma);
-          cplx<T> kr = r1 * kxT + r2 * kyT;
-          cplx<T> z1 = (r1 - kr * (f * kxT)) * is, z2 = (r2 - kr * (f * kyT)) * is;
-          p1 = z1 + q1 * beta;
-          p2 = z2 + q2 * beta;
+          // p = A^{-1} r + beta p (the inner solve: T is float32 or float64)
+          if constexpr (std::is_same<T, TP>::value) {
+            cplx<T> r1 = ld_c<T>(a.rin[0], gi), r2 = ld_c<T>(a.rin[1], gi);
+            cplx<T> q1 = ld_c<T>(a.pio[0], gi), q2 = ld_c<T>(a.pio[1], gi);
+            const T beta = cg_beta(a.sc, T(0));
+            cplx<T> z1, z2;
+            ainv_of(a.sc, T(0)).apply(MT.kx(col), MT.ky(y), r1, r2, z1, z2);
+            p1 = z1 + q1 * beta;
+            p2 = z2 + q2 * beta;
+          }
           st_c<T>(a.pio[0], gi, p1);
           st_c<T>(a.pio[1], gi, p2);
         } else {
@@ -229,7 +326,8 @@ __global__ void __launch_bounds__(kColNT, 1) k2_cols(Modes2d M, int log2ny, cons
     __syncthreads();
     for (int e = threadIdx.x; e < TW * ny; e += kColNT) {
       const int y = e / TW, c = e % TW, col = c0 + c;
-      const T kx = num<T>(col < H ? M.kx(col) : 0.0), ky = num<T>(M.ky(y));
+      const T kx = mode_k<T>(MT, col < H ? col : (M.nx >> 1), true),
+              ky = mode_k<T>(MT, y, false);
       buf[(2 * TW + c) * stride + y] =
           mul_ik(buf[(0 * TW + c) * stride + y], kx) + mul_ik(buf[(1 * TW + c) * stride + y], ky);
     }
@@ -241,12 +339,14 @@ __global__ void __launch_bounds__(kColNT, 1) k2_cols(Modes2d M, int log2ny, cons
 
   // ---- store / epilogue
   if constexpr (MODE == COL_MATVEC_OUT) {
-    double part = 0.0;
+    const double sigma = a.sc ? a.sc->sigma : 0.0, alphaA = a.sc ? a.sc->alpha_A : 0.0;
+    double part = 0.0;      // residual mode (double-float or float64 data)
+    TP partw = 0;           // dot-product mode, in the working precision
     for (int e = threadIdx.x; e < TW * ny; e += kColNT) {
       const int y = e / TW, c = e % TW, col = c0 + c;
       if (col >= H) continue;
       const long long gi = (long long)y * H + col;
-      const T kx = num<T>(M.kx(col)), ky = num<T>(M.ky(y));
+      const T kx = mode_k<T>(MT, col, true), ky = mode_k<T>(MT, y, false);
       cplx<T> w1 = buf[(0 * TW + c) * stride + y], w2 = buf[(1 * TW + c) * stride + y];
       cplx<T> qh = buf[(2 * TW + c) * stride + y];
       cplx<T> g1 = w1 - mul_ik(qh, kx), g2 = w2 - mul_ik(qh, ky);
@@ -263,9 +363,10 @@ __global__ void __launch_bounds__(kColNT, 1) k2_cols(Modes2d M, int log2ny, cons
         double z2x = (r2x - f * kyd * krx) / sigma, z2y = (r2y - f * kyd * kry) / sigma;
         part += M.weight(col) * (r1x * z1x + r1y * z1y + r2x * z2x + r2y * z2y);
       } else if (a.vdot[0]) {
-        cplx<T> p1 = ld_c<T>(a.vdot[0], gi), p2 = ld_c<T>(a.vdot[1], gi);
-        part += M.weight(col) *
-                to_f64(p1.x * g1.x + p1.y * g1.y + p2.x * g2.x + p2.y * g2.y);
+        if constexpr (std::is_same<T, TP>::value) {
+          cplx<T> p1 = ld_c<T>(a.vdot[0], gi), p2 = ld_c<T>(a.vdot[1], gi);
+          partw += MT.weight(col) * (p1.x * g1.x + p1.y * g1.y + p2.x * g2.x + p2.y * g2.y);
+        }
       }
       st_c<T>(a.vout[0], gi, g1);
       st_c<T>(a.vout[1], gi, g2);
@@ -273,13 +374,14 @@ __global__ void __launch_bounds__(kColNT, 1) k2_cols(Modes2d M, int log2ny, cons
     if (a.residual) {
       grid_reduce<kColNT>(part, a.parts, a.sc, [&](double s) { a.sc->rz64 = s; });
     } else if (a.vdot[0]) {
-      grid_reduce<kColNT>(part, a.parts, a.sc, [&](double s) {
+      grid_reduce<kColNT>(partw, a.parts, a.sc, [&](double s) {
         Scal2d* sc = a.sc;
         if (!(s > 0.0) || !isfinite(s)) {
           sc->status = SGN_ERR_BREAKDOWN;
           sc->done = 1;
         } else {
           sc->alpha = sc->rz / s;
+          sc->alphaf = (float)sc->alpha;
         }
       });
     }
@@ -379,7 +481,7 @@ __global__ void __launch_bounds__(kRowNT, 1) k2_rows_matvec(Modes2d M, int log2n
   load_c2r_pair<T>(z + 2 * nx, T2 + (long long)y0 * H, T2 + (long long)y1 * H, nx, kRowNT);
   __syncthreads();
   cta_fft_batch<T, kRowNT, MAXB>(z, nx, log2nx, 3, nx, true, tw);
-  const T inv = num<T>(1.0 / ((double)nx * (double)M.ny));
+  const T inv = pow2_inv<T>(log2nx + (__ffs(M.ny) - 1));    // 1 / (nx ny), exact
   for (int x = threadIdx.x; x < nx; x += kRowNT) {
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -461,7 +563,7 @@ __global__ void __launch_bounds__(kRowNT, 1) k2_rows_c2r(Modes2d M, int log2nx, 
                      kRowNT);
   __syncthreads();
   cta_fft_batch<T, kRowNT, MAXB>(z, nx, log2nx, npairs, nx, true, tw);
-  const T inv = num<T>(1.0 / ((double)nx * (double)M.ny));
+  const T inv = pow2_inv<T>(log2nx + (__ffs(M.ny) - 1));    // 1 / (nx ny), exact
   for (int q = 0; q < npairs; ++q)
     for (int x = threadIdx.x; x < nx; x += kRowNT) {
       const long long j = (long long)y * nx + x;
@@ -519,12 +621,12 @@ __global__ void __launch_bounds__(256) k2_update(Modes2d M, void* x1, void* x2, 
                                                  double* parts) {
   if (((volatile Scal2d*)sc)->done) return;
   const long long HP = (long long)M.ny * M.H;
-  const double sigma = sc->sigma, alphaA = sc->alpha_A;
-  const T a = num<T>(sc->alpha);
-  double part = 0.0;
+  const ModesT<T> MT(M);
+  const AinvT<T> Ai = ainv_of(sc, T(0));
+  const T a = cg_alpha(sc, T(0));
+  T part = 0;
   for (long long i = blockIdx.x * 256ll + threadIdx.x; i < HP; i += (long long)gridDim.x * 256) {
     const int y = (int)(i / M.H), c = (int)(i % M.H);
-    const double kx = M.kx(c), ky = M.ky(y);
     cplx<T> p1 = ld_c<T>(p1p, i), p2 = ld_c<T>(p2p, i);
     st_c<T>(x1, i, ld_c<T>(x1, i) + p1 * a);
     st_c<T>(x2, i, ld_c<T>(x2, i) + p2 * a);
@@ -532,11 +634,9 @@ __global__ void __launch_bounds__(256) k2_update(Modes2d M, void* x1, void* x2, 
     cplx<T> r2 = ld_c<T>(r2p, i) - ld_c<T>(g2p, i) * a;
     st_c<T>(r1p, i, r1);
     st_c<T>(r2p, i, r2);
-    const double f = alphaA / (sigma + alphaA * (kx * kx + ky * ky));
-    const T kxT = num<T>(kx), kyT = num<T>(ky), fT = num<T>(f), is = num<T>(1.0 / sigma);
-    cplx<T> kr = r1 * kxT + r2 * kyT;
-    cplx<T> z1 = (r1 - kr * (fT * kxT)) * is, z2 = (r2 - kr * (fT * kyT)) * is;
-    part += M.weight(c) * to_f64(r1.x * z1.x + r1.y * z1.y + r2.x * z2.x + r2.y * z2.y);
+    cplx<T> z1, z2;
+    Ai.apply(MT.kx(c), MT.ky(y), r1, r2, z1, z2);
+    part += MT.weight(c) * (r1.x * z1.x + r1.y * z1.y + r2.x * z2.x + r2.y * z2.y);
   }
   grid_reduce<256>(part, parts, sc, [&](double rz_new) {
     sc->iters += 1;
@@ -546,6 +646,7 @@ __global__ void __launch_bounds__(256) k2_update(Modes2d M, void* x1, void* x2, 
       return;
     }
     sc->beta = rz_new / sc->rz;
+    sc->betaf = (float)sc->beta;
     sc->rz = rz_new;
     if (sqrt(rz_new) <= sc->tol) {
       sc->done = 1;
@@ -564,30 +665,30 @@ __global__ void __launch_bounds__(256) k2_inner_start(Modes2d M, const void* s1,
                                                       void* x1, void* x2, void* p1, void* p2,
                                                       Scal2d* sc, double* parts) {
   const long long HP = (long long)M.ny * M.H;
-  const double sigma = sc->sigma, alphaA = sc->alpha_A;
-  double part = 0.0;
-  const cplx<T> zero = mk(from_int<T>(0), from_int<T>(0));
+  const ModesT<T> MT(M);
+  const AinvT<T> Ai = ainv_of(sc, T(0));
+  const T sc_t = (T)scale;
+  T part = 0;
+  const cplx<T> zero = mk(T(0), T(0));
   for (long long i = blockIdx.x * 256ll + threadIdx.x; i < HP; i += (long long)gridDim.x * 256) {
     const int y = (int)(i / M.H), c = (int)(i % M.H);
-    const double kx = M.kx(c), ky = M.ky(y);
     cplx<TH> a = ld_c<TH>(s1, i), b = ld_c<TH>(s2, i);
-    cplx<T> r1 = mk(num<T>(to_f64(a.x) * scale), num<T>(to_f64(a.y) * scale));
-    cplx<T> r2 = mk(num<T>(to_f64(b.x) * scale), num<T>(to_f64(b.y) * scale));
+    cplx<T> r1 = mk(to_work<T>(a.x) * sc_t, to_work<T>(a.y) * sc_t);
+    cplx<T> r2 = mk(to_work<T>(b.x) * sc_t, to_work<T>(b.y) * sc_t);
     st_c<T>(r1p, i, r1);
     st_c<T>(r2p, i, r2);
     st_c<T>(x1, i, zero);
     st_c<T>(x2, i, zero);
     st_c<T>(p1, i, zero);
     st_c<T>(p2, i, zero);
-    const double f = alphaA / (sigma + alphaA * (kx * kx + ky * ky));
-    double r1x = to_f64(r1.x), r1y = to_f64(r1.y), r2x = to_f64(r2.x), r2y = to_f64(r2.y);
-    double krx = kx * r1x + ky * r2x, kry = kx * r1y + ky * r2y;
-    part += M.weight(c) * ((r1x * (r1x - f * kx * krx) + r1y * (r1y - f * kx * kry) +
-                            r2x * (r2x - f * ky * krx) + r2y * (r2y - f * ky * kry)) / sigma);
+    cplx<T> z1, z2;
+    Ai.apply(MT.kx(c), MT.ky(y), r1, r2, z1, z2);
+    part += MT.weight(c) * (r1.x * z1.x + r1.y * z1.y + r2.x * z2.x + r2.y * z2.y);
   }
   grid_reduce<256>(part, parts, sc, [&](double rz) {
     sc->rz = rz;
     sc->beta = 0.0;
+    sc->betaf = 0.0f;
     sc->done = (sqrt(rz) <= sc->tol) ? 1 : 0;
   });
 }
@@ -602,8 +703,8 @@ __global__ void k2_accumulate(Modes2d M, void* x1, void* x2, const void* d1, con
        i += (long long)gridDim.x * blockDim.x) {
     cplx<T> a = ld_c<T>(d1, i), b = ld_c<T>(d2, i);
     cplx<TH> u = ld_c<TH>(x1, i), v = ld_c<TH>(x2, i);
-    st_c<TH>(x1, i, mk(u.x + num<TH>(to_f64(a.x)) * s, u.y + num<TH>(to_f64(a.y)) * s));
-    st_c<TH>(x2, i, mk(v.x + num<TH>(to_f64(b.x)) * s, v.y + num<TH>(to_f64(b.y)) * s));
+    st_c<TH>(x1, i, mk(u.x + widen<TH>(a.x) * s, u.y + widen<TH>(a.y) * s));
+    st_c<TH>(x2, i, mk(v.x + widen<TH>(b.x) * s, v.y + widen<TH>(b.y) * s));
   }
 }
 
@@ -720,6 +821,9 @@ __global__ void __launch_bounds__(256) k2_coeffs(long long P, const double* eta,
     if (rec) *rec = R;
     sc->sigma = R.sigma;
     sc->alpha_A = R.alpha;
+    sc->sigf = (float)R.sigma;
+    sc->alphaAf = (float)R.alpha;
+    sc->isigf = (float)(1.0 / R.sigma);
     sc->kappa_ub = R.kappa_ub;
     sc->eta_min = R.eta_min;
     sc->eta_max = R.eta_max;
@@ -732,6 +836,9 @@ __global__ void __launch_bounds__(256) k2_coeffs(long long P, const double* eta,
 __global__ void k2_set_given(Scal2d* sc, const SolveRec* g) {
   sc->sigma = g->sigma;
   sc->alpha_A = g->alpha;
+  sc->sigf = (float)g->sigma;
+  sc->alphaAf = (float)g->alpha;
+  sc->isigf = (float)(1.0 / g->sigma);
   sc->kappa_ub = g->kappa_ub;
   sc->flat = g->flat;
   sc->status = SGN_OK;
