@@ -970,7 +970,7 @@ cudaError_t smem_attr(K kernel, size_t bytes) {
 }
 
 template <typename T>
-constexpr int col_tw() { return sizeof(T) == 8 ? 4 : 2; }     // 32-byte row segments
+constexpr int col_tw() { return 2; }   // 2 columns per CTA: 129 CTAs at 512^2 (152 SMs)
 
 template <typename T>
 size_t col_smem(const Layout2d& L, int K) {
@@ -1409,10 +1409,15 @@ cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_rhs2d(const Layout2d& L, const void* tw64, double g, const double* eta,
-                         const double* u, const double* h, const double* gradh, double* f_eta,
-                         double* f_U, cudaStream_t s) {
-  // float64 right-hand side with six derivative pairs (see k2_rhs_stage for plane indices)
+namespace {
+
+// Right-hand side with six derivative pairs (see k2_rhs_stage for plane indices).  The
+// transforms run in T (float64, or double-float for the mixed path); the pointwise stages
+// and the intermediate planes are float64.
+template <typename T>
+cudaError_t rhs2d(const Layout2d& L, const void* tw64, const void* tw32, double g,
+                  const double* eta, const double* u, const double* h, const double* gradh,
+                  double* f_eta, double* f_U, cudaStream_t s) {
   double* w = L.rhs_w;
   const long long P = L.P;
   auto W = [&](int q) { return w + (long long)q * P; };
@@ -1420,16 +1425,16 @@ cudaError_t launch_rhs2d(const Layout2d& L, const void* tw64, double g, const do
   cudaError_t e;
   auto grad_pair = [&](const double* a, const double* b, double* ax, double* ay, double* bx,
                        double* by) -> cudaError_t {
-    cudaError_t r = rows_r2c<double>(L, tw64, nullptr, a, b, nullptr, nullptr, tplane(L, 0),
+    cudaError_t r = rows_r2c<T>(L, tw64, tw32, a, b, nullptr, nullptr, tplane(L, 0),
                                      tplane(L, 1), nullptr, nullptr, 1, s);
     if (r) return r;
     ColArgs c{};
     c.planes[0] = tplane(L, 0);
     c.planes[1] = tplane(L, 1);
     c.K = 2;
-    if ((r = cols<double, COL_FWD>(L, tw64, nullptr, c, s))) return r;
+    if ((r = cols<T, COL_FWD>(L, tw64, tw32, c, s))) return r;
     const Modes2d M = modes_of(L);
-    k2_spec<double, OP_GRAD><<<grid_for(L.HP, 256), 256, 0, s>>>(
+    k2_spec<T, OP_GRAD><<<grid_for(L.HP, 256), 256, 0, s>>>(
         M, tplane(L, 0), tplane(L, 1), slot(L, 0), slot(L, 1), slot(L, 2), slot(L, 3), nullptr,
         nullptr);
     if ((r = cudaGetLastError())) return r;
@@ -1439,8 +1444,8 @@ cudaError_t launch_rhs2d(const Layout2d& L, const void* tw64, double g, const do
     ci.planes[2] = slot(L, 2);
     ci.planes[3] = slot(L, 3);
     ci.K = 4;
-    if ((r = cols<double, COL_INV>(L, tw64, nullptr, ci, s))) return r;
-    return rows_c2r<double>(L, tw64, nullptr, slot(L, 0), slot(L, 1), slot(L, 2), slot(L, 3), ax,
+    if ((r = cols<T, COL_INV>(L, tw64, tw32, ci, s))) return r;
+    return rows_c2r<T>(L, tw64, tw32, slot(L, 0), slot(L, 1), slot(L, 2), slot(L, 3), ax,
                             ay, bx, by, 2, s);
   };
   k2_rhs_stage<double><<<gb, 256, 0, s>>>(0, P, g, eta, u, h, gradh, w, f_eta, f_U);
@@ -1457,6 +1462,16 @@ cudaError_t launch_rhs2d(const Layout2d& L, const void* tw64, double g, const do
   if ((e = grad_pair(W(8), nullptr, W(30), W(31), nullptr, nullptr))) return e;
   k2_rhs_stage<double><<<gb, 256, 0, s>>>(3, P, g, eta, u, h, gradh, w, f_eta, f_U);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_rhs2d(const Layout2d& L, const void* tw64, const void* tw32, int precision,
+                         double g, const double* eta, const double* u, const double* h,
+                         const double* gradh, double* f_eta, double* f_U, cudaStream_t s) {
+  return precision == SGN_PREC_MIXED
+             ? rhs2d<df>(L, tw64, tw32, g, eta, u, h, gradh, f_eta, f_U, s)
+             : rhs2d<double>(L, tw64, tw32, g, eta, u, h, gradh, f_eta, f_U, s);
 }
 
 cudaError_t launch_lincomb2d(const Layout2d& L, const double* dt, double* out,

@@ -44,9 +44,10 @@ cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, 
                          const double* eta, const double* gradh, const double* b, double* x,
                          const SolveRec* given, int kind, double rtol, double rtol_inner,
                          int maxit, int max_refine, SolveRec* rec, cudaStream_t s);
-cudaError_t launch_rhs2d(const Layout2d& L, const void* tw64, double g, const double* eta,
-                         const double* u, const double* h, const double* gradh, double* f_eta,
-                         double* f_U, cudaStream_t s);
+// precision SGN_PREC_MIXED: transforms in double-float (pointwise work stays float64)
+cudaError_t launch_rhs2d(const Layout2d& L, const void* tw64, const void* tw32, int precision,
+                         double g, const double* eta, const double* u, const double* h,
+                         const double* gradh, double* f_eta, double* f_U, cudaStream_t s);
 cudaError_t launch_lincomb2d(const Layout2d& L, const double* dt, double* out,
                              const double* const* x, const double* a, int nx,
                              const double* const* f, const double* c, int nf, int components,

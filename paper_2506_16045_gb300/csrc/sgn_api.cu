@@ -617,8 +617,8 @@ extern "C" sgn_status sgn_rhs(sgn_ctx* ctx, const sgn_layout* lay, const double*
       lay->dim == 1
           ? sgn::launch_rhs1d(lay->l1, ctx->tw64, ctx->tw32, SGN_PREC_FP64, grav, eta, u, h, gradh,
                               f_eta, f_U, lay->scratch, as_stream(stream))
-          : sgn::launch_rhs2d(lay->l2, ctx->tw64, grav, eta, u, h, gradh, f_eta, f_U,
-                              as_stream(stream));
+          : sgn::launch_rhs2d(lay->l2, ctx->tw64, ctx->tw32, SGN_PREC_FP64, grav, eta, u, h,
+                              gradh, f_eta, f_U, as_stream(stream));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sgn_rhs");
   return SGN_OK;
 }
@@ -745,8 +745,15 @@ sgn_status lincomb(sgn_state* st, double* out, std::initializer_list<std::pair<c
 sgn_status rhs_at(sgn_state* st, const double* eta, const double* u, double* fe, double* fU,
                   cudaStream_t s) {
   sgn_layout* lay = st->lay;
-  if (lay->dim != 1 || st->prec != SGN_PREC_MIXED)
-    return sgn_rhs(lay->ctx, lay, eta, u, st->h, st->gradh, fe, fU, s);
+  if (st->prec != SGN_PREC_MIXED) return sgn_rhs(lay->ctx, lay, eta, u, st->h, st->gradh, fe, fU, s);
+  if (lay->dim == 2) {
+    ProfScope prof(lay->ctx, s, 1);
+    const cudaError_t e = sgn::launch_rhs2d(lay->l2, lay->ctx->tw64, lay->ctx->tw32,
+                                            SGN_PREC_MIXED, lay->grids[0].g, eta, u, st->h,
+                                            st->gradh, fe, fU, s);
+    if (e != cudaSuccess) return cuda_fail(lay->ctx, e, "rhs launch");
+    return SGN_OK;
+  }
   ProfScope prof(lay->ctx, s, 1);
   cudaError_t e = sgn::launch_rhs1d(lay->l1, lay->ctx->tw64, lay->ctx->tw32, SGN_PREC_MIXED,
                                     lay->grids[0].g, eta, u, st->h, st->gradh, fe, fU,
