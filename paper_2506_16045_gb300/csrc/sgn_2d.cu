@@ -589,7 +589,7 @@ __global__ void k2_spec(Modes2d M, const void* in0, const void* in1, void* out0,
   const long long HP = (long long)M.ny * M.H;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HP;
        i += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(i / M.H), c = (int)(i % M.H);
+    const int y = (int)i / M.H, c = (int)i - y * M.H;   // half planes < 2^31 elements
     const double kx = M.kx(c), ky = M.ky(y);
     if constexpr (OP == OP_GRAD) {
       cplx<T> a = ld_c<T>(in0, i);
@@ -626,7 +626,7 @@ __global__ void __launch_bounds__(256) k2_update(Modes2d M, void* x1, void* x2, 
   const T a = cg_alpha(sc, T(0));
   T part = 0;
   for (long long i = blockIdx.x * 256ll + threadIdx.x; i < HP; i += (long long)gridDim.x * 256) {
-    const int y = (int)(i / M.H), c = (int)(i % M.H);
+    const int y = (int)i / M.H, c = (int)i - y * M.H;   // half planes < 2^31 elements
     cplx<T> p1 = ld_c<T>(p1p, i), p2 = ld_c<T>(p2p, i);
     st_c<T>(x1, i, ld_c<T>(x1, i) + p1 * a);
     st_c<T>(x2, i, ld_c<T>(x2, i) + p2 * a);
@@ -671,7 +671,7 @@ __global__ void __launch_bounds__(256) k2_inner_start(Modes2d M, const void* s1,
   T part = 0;
   const cplx<T> zero = mk(T(0), T(0));
   for (long long i = blockIdx.x * 256ll + threadIdx.x; i < HP; i += (long long)gridDim.x * 256) {
-    const int y = (int)(i / M.H), c = (int)(i % M.H);
+    const int y = (int)i / M.H, c = (int)i - y * M.H;   // half planes < 2^31 elements
     cplx<TH> a = ld_c<TH>(s1, i), b = ld_c<TH>(s2, i);
     cplx<T> r1 = mk(to_work<T>(a.x) * sc_t, to_work<T>(a.y) * sc_t);
     cplx<T> r2 = mk(to_work<T>(b.x) * sc_t, to_work<T>(b.y) * sc_t);
@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(256) k2_bnorm(Modes2d M, const void* b1, const
   const double sigma = sc->sigma, alphaA = sc->alpha_A;
   double part = 0.0;
   for (long long i = blockIdx.x * 256ll + threadIdx.x; i < HP; i += (long long)gridDim.x * 256) {
-    const int y = (int)(i / M.H), c = (int)(i % M.H);
+    const int y = (int)i / M.H, c = (int)i - y * M.H;   // half planes < 2^31 elements
     const double kx = M.kx(c), ky = M.ky(y);
     cplx<TH> a = ld_c<TH>(b1, i), b = ld_c<TH>(b2, i);
     const double f = alphaA / (sigma + alphaA * (kx * kx + ky * ky));
@@ -938,7 +938,7 @@ __global__ void k2_linimp_combine(Modes2d M, const SolveRec* A, const void* u1, 
   const double sigma = A->sigma, alpha = A->alpha;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HP;
        i += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(i / M.H), c = (int)(i % M.H);
+    const int y = (int)i / M.H, c = (int)i - y * M.H;   // half planes < 2^31 elements
     const T kx = num<T>(M.kx(c)), ky = num<T>(M.ky(y));
     cplx<T> a = ld_c<T>(u1, i), b = ld_c<T>(u2, i);
     cplx<T> ku = a * kx + b * ky;
