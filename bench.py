@@ -392,6 +392,7 @@ def gpu_arm(args, world, rank, local, pg):
                                                                      int(0.99 * len(srt)))]},
         "solver": {"solves": s1["solves"] - s0["solves"],
                    "iterations": s1["iterations"] - s0["iterations"],
+                   "refinements": s1["refinements"] - s0["refinements"],
                    "max_iters": s1["max_iters"], "status": s1["status"]},
     }
     if rank == 0 and world == 1 and not args.no_extra:

@@ -184,6 +184,8 @@ typedef struct {
   double flops64;                 /* algorithmic flops of the solves' high-precision part:
                                      float64 for SGN_PREC_FP64, double-float (pairs of
                                      float32) for SGN_PREC_MIXED */
+  long long refinements;          /* SGN_PREC_MIXED: float32 inner solves (refinement passes
+                                     less one per solve) since init; 0 for FP64 */
 } sgn_state_stats;
 
 /* Binds caller-owned packed arrays: eta [P], U (vector), u (vector), h [P], gradh (vector,
@@ -193,7 +195,9 @@ sgn_status sgn_state_create(sgn_ctx* ctx, const sgn_layout* lay, double* eta, do
 /* gradh = D h, U = G_{eta,h} u (Eq:DSWEcf4), clears history and counters. */
 sgn_status sgn_state_init(sgn_state* st, sgn_stream stream);
 /* Classical RK4 with one constraint solve per stage 2..4 and one for u_{n+1} (Eq:ERK,
- * §5.1); U stages start from U_n.  dt: HOST array [count] (per-instance step). */
+ * §5.1); U stages start from U_n.  dt: HOST array [count] (per-instance step).  The stage-4
+ * solve starts from 2 u^(3) - u_n (u extrapolated to its stage time), which changes only
+ * the initial guess. */
 sgn_status sgn_step_rk4(sgn_state* st, const double* dt, int nsteps, const sgn_opts* opts,
                         sgn_stream stream);
 /* Adams-Bashforth of order 2..4 (Eq:AB, Table 1, §5.2), one solve per step; the first

@@ -92,6 +92,7 @@ struct DevStats {
   int status;
   double flops32;        // algorithmic float32 flops of the PCG solves
   double flops64;        // algorithmic float64 flops of the PCG solves
+  long long refinements; // float32 inner solves (mixed)
 };
 
 // Algorithmic flop model of one solve on n points (complex FFT of length n: 5 n log2 n):
@@ -117,6 +118,8 @@ __global__ void k_accum(const SolveRec* __restrict__ rec, const Inst1d* __restri
     atomicAdd(reinterpret_cast<unsigned long long*>(&st->solves), 1ull);
     atomicAdd(reinterpret_cast<unsigned long long*>(&st->iterations),
               (unsigned long long)rec[i].iters);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&st->refinements),
+              (unsigned long long)rec[i].refinements);
     atomicMax(&st->max_iters, rec[i].iters);
     atomicMax(&st->status, rec[i].status);
     double f32, f64;
@@ -392,8 +395,18 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
     if (ncls > 1) {
       if (cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming) != cudaSuccess)
         return cleanup(SGN_ERR_CUDA, "layout events");
+      // Side stream c carries the c-th largest class.  A solve CTA of the largest classes
+      // needs a whole SM (its registers or shared memory), so their blocks must not queue
+      // behind small classes spread over the SMs: larger classes get higher priorities,
+      // and the block scheduler dispatches their pending blocks first.
+      int lo = 0, hi = 0;   // cudaDeviceGetStreamPriorityRange: hi is the greatest priority
+      if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) {
+        cudaGetLastError();
+        lo = hi = 0;
+      }
       for (int c = 0; c < ncls; ++c) {
-        if (cudaStreamCreateWithFlags(&L.side[c], cudaStreamNonBlocking) != cudaSuccess ||
+        const int prio = hi + c < lo ? hi + c : lo;   // numerically lower = higher priority
+        if (cudaStreamCreateWithPriority(&L.side[c], cudaStreamNonBlocking, prio) != cudaSuccess ||
             cudaEventCreateWithFlags(&L.join[c], cudaEventDisableTiming) != cudaSuccess) {
           cudaGetLastError();
           return cleanup(SGN_ERR_CUDA, "layout streams");
@@ -826,6 +839,9 @@ sgn_status rk4_once(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
   for (int i = 1; i < 4; ++i) {
     SGN_TRY(lincomb(st, st->eta_s, {{st->eta, 1.0}}, {{st->fe[i - 1], a[i]}}, 1, s));
     SGN_TRY(lincomb(st, st->U_s, {{st->U, 1.0}}, {{st->fU[i - 1], a[i]}}, d, s));
+    // stage 4 (c = 1) starts from u extrapolated from c = 0 and c = 1/2: 2 u^(3) - u_n
+    // (only the initial guess of the solve changes)
+    if (i == 3) SGN_TRY(lincomb(st, st->u_s, {{st->u_s, 2.0}, {st->u, -1.0}}, {}, d, s));
     SGN_TRY(stage_at(st, st->eta_s, st->U_s, st->u_s, st->fe[i], st->fU[i], o, s));
   }
   const double b0 = 1.0 / 6.0, b1 = 1.0 / 3.0;
@@ -1084,6 +1100,7 @@ extern "C" sgn_status sgn_state_get_stats(sgn_state* st, sgn_state_stats* out) {
   out->step = st->step;
   out->flops32 = h.flops32;
   out->flops64 = h.flops64;
+  out->refinements = h.refinements;
   return SGN_OK;
 }
 

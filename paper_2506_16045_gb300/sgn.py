@@ -49,7 +49,8 @@ class SgnOpts(C.Structure):
 class SgnStateStats(C.Structure):
     _fields_ = [("solves", C.c_longlong), ("iterations", C.c_longlong), ("max_iters", C.c_int),
                 ("status", C.c_int), ("t", C.c_double), ("step", C.c_longlong),
-                ("flops32", C.c_double), ("flops64", C.c_double)]
+                ("flops32", C.c_double), ("flops64", C.c_double),
+                ("refinements", C.c_longlong)]
 
 
 class SgnRequest(C.Structure):
@@ -359,7 +360,7 @@ class State:
                            "sgn_state_get_stats")
         return dict(solves=st.solves, iterations=st.iterations, max_iters=st.max_iters,
                     status=st.status, t=st.t, step=st.step, flops32=st.flops32,
-                    flops64=st.flops64)
+                    flops64=st.flops64, refinements=st.refinements)
 
     def close(self):
         if self.h:
