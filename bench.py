@@ -238,11 +238,12 @@ def gpu_arm(args, world, rank, local, pg):
 
     # ---- mixed precision, batched (the headline)
     E.reset()
+    ctx.profile(True)         # on for the warm-up too, so the timed steps replay one graph
     for _ in range(args.warmup):
         E.step(sgn.PREC_MIXED)
     torch.cuda.synchronize()
+    ctx.profile_read()        # discard the warm-up's launch-group timings
     s0 = E.st.stats()
-    ctx.profile(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     barrier()

@@ -24,6 +24,13 @@ struct ProfRec {
   int kind;              // 0 = PCG launch group, 1 = right-hand side launch group
 };
 
+// A profiled launch group inside a captured graph: its two event-record nodes, which get
+// fresh events before every replay (so replays accumulate without synchronising).
+struct CapRec {
+  cudaGraphNode_t a, b;
+  int kind;
+};
+
 struct sgn_ctx {
   int device = 0;
   void* tw64 = nullptr;
@@ -32,6 +39,7 @@ struct sgn_ctx {
   int prof = 0;
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> pool;
+  std::vector<CapRec>* capture = nullptr;   // non-null while a profiled step is captured
 };
 
 namespace {
@@ -41,12 +49,29 @@ struct ProfScope {
   cudaStream_t s;
   ProfRec r{};
   bool on;
+  cudaGraphNode_t na = nullptr;
   ProfScope(sgn_ctx* c, cudaStream_t st, int kind) : ctx(c), s(st), on(c && c->prof) {
     if (!on) return;
     r.kind = kind;
     r.a = take();
     r.b = take();
-    cudaEventRecord(r.a, s);
+    if (ctx->capture) {
+      na = record_node(r.a);
+    } else {
+      cudaEventRecord(r.a, s);
+    }
+  }
+  // during capture: an external event-record node (it records a timestamp on replay); the
+  // stream's dependency set right after the record is that node
+  cudaGraphNode_t record_node(cudaEvent_t e) {
+    cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &nd) != cudaSuccess ||
+        nd != 1)
+      return nullptr;
+    return deps[0];
   }
   cudaEvent_t take() {
     cudaEvent_t e;
@@ -60,6 +85,13 @@ struct ProfScope {
   }
   ~ProfScope() {
     if (!on) return;
+    if (ctx->capture) {
+      const cudaGraphNode_t nb = record_node(r.b);
+      if (na && nb) ctx->capture->push_back(CapRec{na, nb, r.kind});
+      ctx->pool.push_back(r.a);   // the replays use their own events
+      ctx->pool.push_back(r.b);
+      return;
+    }
     cudaEventRecord(r.b, s);
     ctx->recs.push_back(r);
   }
@@ -675,6 +707,15 @@ struct sgn_state {
   double t = 0.0;
   long long step = 0;
   cudaStream_t last = nullptr;
+  // CUDA graph of one 1d RK4 step, replayed while the step options repeat
+  cudaStream_t gs = nullptr;        // capture / replay stream (joined to the caller's by events)
+  cudaEvent_t ge0 = nullptr, ge1 = nullptr;
+  cudaGraph_t graph = nullptr;      // the captured graph (its nodes address gexec's nodes)
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<CapRec> gprof;        // profiled launch groups of gexec
+  sgn_opts gkey{};                  // options of the last 1d RK4 step
+  int gkey_prof = -1;               // profiling state it was taken with (-1: none yet)
+  bool gdisabled = false;           // capture failed once: direct launches from then on
 };
 
 namespace {
@@ -930,6 +971,117 @@ sgn_status state_attach(sgn_state* st, cudaStream_t s) {
 }
 }  // namespace sgn
 
+namespace {
+
+void graph_drop(sgn_state* st) {
+  if (st->gexec) cudaGraphExecDestroy(st->gexec);
+  if (st->graph) cudaGraphDestroy(st->graph);
+  st->gexec = nullptr;
+  st->graph = nullptr;
+  st->gprof.clear();
+}
+
+bool same_opts(const sgn_opts& a, const sgn_opts& b) {
+  return a.rtol == b.rtol && a.maxit == b.maxit && a.prec == b.prec && a.coef == b.coef &&
+         a.rtol_inner == b.rtol_inner && a.max_refine == b.max_refine;
+}
+
+// Captures one RK4 step of a 1d state into st->gexec (launch work only: every array and the
+// per-instance dt are device buffers of the state, so one graph serves every later step).
+sgn_status graph_capture(sgn_state* st, const sgn_opts* o) {
+  sgn_ctx* ctx = st->lay->ctx;
+  if (!st->gs && (cudaStreamCreateWithFlags(&st->gs, cudaStreamNonBlocking) != cudaSuccess ||
+                  cudaEventCreateWithFlags(&st->ge0, cudaEventDisableTiming) != cudaSuccess ||
+                  cudaEventCreateWithFlags(&st->ge1, cudaEventDisableTiming) != cudaSuccess)) {
+    cudaGetLastError();
+    return SGN_ERR_CUDA;
+  }
+  std::vector<CapRec> prof;
+  const double t0 = st->t;
+  const long long k0 = st->step;
+  if (cudaStreamBeginCapture(st->gs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return SGN_ERR_CUDA;
+  }
+  ctx->capture = ctx->prof ? &prof : nullptr;
+  const sgn_status r = rk4_once(st, o, st->gs);
+  ctx->capture = nullptr;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(st->gs, &graph);
+  st->t = t0;                       // the capture ran nothing
+  st->step = k0;
+  cudaGraphExec_t exec = nullptr;
+  const bool ok = r == SGN_OK && ec == cudaSuccess && graph &&
+                  cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority) ==
+                      cudaSuccess &&
+                  (!ctx->prof || prof.size() > 0);
+  if (!ok) {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return SGN_ERR_CUDA;
+  }
+  st->graph = graph;
+  st->gexec = exec;
+  st->gprof = std::move(prof);
+  return SGN_OK;
+}
+
+// One replay on st->gs, ordered after the caller's prior work on s and before its later work.
+sgn_status graph_replay(sgn_state* st, cudaStream_t s) {
+  sgn_ctx* ctx = st->lay->ctx;
+  if (ctx->prof) {
+    for (const CapRec& c : st->gprof) {
+      ProfRec r{};
+      r.kind = c.kind;
+      auto take = [&]() {
+        cudaEvent_t e;
+        if (!ctx->pool.empty()) {
+          e = ctx->pool.back();
+          ctx->pool.pop_back();
+        } else {
+          cudaEventCreate(&e);
+        }
+        return e;
+      };
+      r.a = take();
+      r.b = take();
+      SGN_CUDA(ctx, cudaGraphExecEventRecordNodeSetEvent(st->gexec, c.a, r.a));
+      SGN_CUDA(ctx, cudaGraphExecEventRecordNodeSetEvent(st->gexec, c.b, r.b));
+      ctx->recs.push_back(r);
+    }
+  }
+  SGN_CUDA(ctx, cudaEventRecord(st->ge0, s));
+  SGN_CUDA(ctx, cudaStreamWaitEvent(st->gs, st->ge0, 0));
+  SGN_CUDA(ctx, cudaGraphLaunch(st->gexec, st->gs));
+  SGN_CUDA(ctx, cudaEventRecord(st->ge1, st->gs));
+  SGN_CUDA(ctx, cudaStreamWaitEvent(s, st->ge1, 0));
+  st->t += st->dt_last[0];
+  st->step += 1;
+  return SGN_OK;
+}
+
+// A 1d RK4 step: the first with given options runs directly; later ones replay a graph of it
+// (one launch instead of ~200 launches and event operations per step).
+sgn_status rk4_step(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
+  sgn_ctx* ctx = st->lay->ctx;
+  if (st->lay->dim != 1 || st->gdisabled) return rk4_once(st, o, s);
+  const bool same = st->gkey_prof == ctx->prof && same_opts(st->gkey, *o);
+  if (!same) {
+    graph_drop(st);
+    st->gkey = *o;
+    st->gkey_prof = ctx->prof;
+    return rk4_once(st, o, s);
+  }
+  if (!st->gexec && graph_capture(st, o) != SGN_OK) {
+    st->gdisabled = true;           // e.g. the caller is itself capturing: launch directly
+    return rk4_once(st, o, s);
+  }
+  return graph_replay(st, s);
+}
+
+}  // namespace
+
 extern "C" sgn_status sgn_step_rk4(sgn_state* st, const double* dt, int nsteps,
                                    const sgn_opts* opts, sgn_stream stream) {
   if (!st || !dt || nsteps < 0) return SGN_ERR_INVALID_ARG;
@@ -938,7 +1090,7 @@ extern "C" sgn_status sgn_step_rk4(sgn_state* st, const double* dt, int nsteps,
   SGN_TRY(check_opts(st, opts));
   SGN_TRY(upload_dt(st, dt, s));
   st->last = s;
-  for (int k = 0; k < nsteps; ++k) SGN_TRY(rk4_once(st, opts, s));
+  for (int k = 0; k < nsteps; ++k) SGN_TRY(rk4_step(st, opts, s));
   st->hist = HIST_NONE;
   st->levels = 0;
   return SGN_OK;
@@ -1107,6 +1259,10 @@ extern "C" sgn_status sgn_state_get_stats(sgn_state* st, sgn_state_stats* out) {
 extern "C" void sgn_state_free(sgn_state* st) {
   if (!st) return;
   DeviceGuard g(st->lay->device);
+  graph_drop(st);
+  if (st->gs) cudaStreamDestroy(st->gs);
+  if (st->ge0) cudaEventDestroy(st->ge0);
+  if (st->ge1) cudaEventDestroy(st->ge1);
   for (double* p : st->bufs) cudaFree(p);
   cudaFree(st->res0);
   cudaFree(st->res1);

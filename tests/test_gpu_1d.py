@@ -317,3 +317,35 @@ def test_ensemble_batch_equals_alone(S):
     for i, c in enumerate(ens):
         (eta_1, _, u_1), _ = _run_gpu(sgn, ctx, [c], "rk4", 3, "mixed", 1e-10)
         assert np.array_equal(eta_b[i], eta_1[0]) and np.array_equal(u_b[i], u_1[0])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_rk4_graph_replay_equals_direct_launches(S, prec):
+    """From the second 1d RK4 step with unchanged options the library replays a captured CUDA
+    graph of the step.  Alternating max_refine (12, 13: a cap never reached here) changes the
+    options every call, which keeps every step on direct launches; both runs must agree
+    bitwise, and so must the solver counters."""
+    sgn, ctx = S
+    ens = I.ensemble_1d(count=5, seed=11, kmin=8, kmax=11)
+    p = sgn.PREC_FP64 if prec == "fp64" else sgn.PREC_MIXED
+    outs = []
+    for alternate in (False, True):
+        lay = sgn.Layout(ctx, [sgn.Grid(1, c.n, c.L, g=c.g) for c in ens])
+        eta = dev(pack([c.eta for c in ens]))
+        u = dev(pack([c.u for c in ens]))
+        h = dev(pack([c.h for c in ens]))
+        U = torch.zeros_like(eta)
+        gh = torch.zeros_like(eta)
+        st = sgn.State(lay, eta, U, u, h, gh)
+        st.init()
+        dts = [c.dt for c in ens]
+        for k in range(5):
+            mr = (12 + k % 2) if alternate else 12
+            st.rk4(dts, 1, rtol=1e-10, prec=p, max_refine=mr)
+        stats = st.stats()
+        outs.append((host(eta), host(u), stats["iterations"], stats["solves"], stats["t"]))
+        st.close()
+        lay.close()
+    (ea, ua, ia, sa, ta), (eb, ub, ib, sb, tb) = outs
+    assert np.array_equal(ea, eb) and np.array_equal(ua, ub)
+    assert (ia, sa) == (ib, sb) and ta == tb
