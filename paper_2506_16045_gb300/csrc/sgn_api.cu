@@ -173,18 +173,36 @@ struct LinComb {
   int nf;
 };
 
-__global__ void k_lincomb(const Inst1d* __restrict__ insts, const double* __restrict__ dt,
-                          double* __restrict__ out, LinComb lc, long long plane,
-                          int components) {
-  const Inst1d I = insts[blockIdx.x];
-  const double d = dt[blockIdx.x];
-  for (int comp = 0; comp < components; ++comp) {
-    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+// Up to two combinations in one launch (blockIdx.z selects), each over all instances
+// (blockIdx.y) in chunks of kLinChunk points (blockIdx.x), so large instances do not
+// serialise the launch.
+struct LinJob {
+  double* out;
+  LinComb lc;
+  int components;
+};
+struct LinJobs {
+  LinJob j[2];
+};
+constexpr int kLinChunk = 1024;
+
+__global__ void __launch_bounds__(256) k_lincomb(const Inst1d* __restrict__ insts,
+                                                 const double* __restrict__ dt,
+                                                 const __grid_constant__ LinJobs J,
+                                                 long long plane) {
+  const LinJob& jb = J.j[blockIdx.z];
+  const Inst1d I = insts[blockIdx.y];
+  const int j0 = blockIdx.x * kLinChunk;
+  if (j0 >= I.n) return;
+  const int j1 = min(I.n, j0 + kLinChunk);
+  const double d = dt[blockIdx.y];
+  for (int comp = 0; comp < jb.components; ++comp) {
+    for (int j = j0 + threadIdx.x; j < j1; j += 256) {
       const long long q = comp * plane + I.off + j;
       double acc = 0.0, accf = 0.0;
-      for (int t = 0; t < lc.nx; ++t) acc += lc.a[t] * lc.x[t][q];
-      for (int t = 0; t < lc.nf; ++t) accf += lc.c[t] * lc.f[t][q];
-      out[q] = acc + d * accf;
+      for (int t = 0; t < jb.lc.nx; ++t) acc += jb.lc.a[t] * jb.lc.x[t][q];
+      for (int t = 0; t < jb.lc.nf; ++t) accf += jb.lc.c[t] * jb.lc.f[t][q];
+      jb.out[q] = acc + d * accf;
     }
   }
 }
@@ -769,10 +787,9 @@ sgn_status upload_dt(sgn_state* st, const double* dt, cudaStream_t s) {
   return SGN_OK;
 }
 
-// out = sum a_t x_t + dt sum c_t f_t for scalar (components=1) or vector fields
-sgn_status lincomb(sgn_state* st, double* out, std::initializer_list<std::pair<const double*, double>> xs,
-                   std::initializer_list<std::pair<const double*, double>> fs, int components,
-                   cudaStream_t s) {
+using Terms = std::initializer_list<std::pair<const double*, double>>;
+
+LinComb make_lincomb(Terms xs, Terms fs) {
   LinComb lc{};
   for (auto& p : xs) {
     lc.x[lc.nx] = p.first;
@@ -784,12 +801,31 @@ sgn_status lincomb(sgn_state* st, double* out, std::initializer_list<std::pair<c
     lc.c[lc.nf] = p.second;
     ++lc.nf;
   }
+  return lc;
+}
+
+// out = sum a_t x_t + dt sum c_t f_t for scalar (components=1) or vector fields; with out2
+// set, a second combination in the same launch (1d) or right after it (2d)
+sgn_status lincomb(sgn_state* st, double* out, Terms xs, Terms fs, int components,
+                   cudaStream_t s, double* out2 = nullptr, Terms xs2 = {}, Terms fs2 = {},
+                   int components2 = 0) {
+  const LinComb lc = make_lincomb(xs, fs), lc2 = make_lincomb(xs2, fs2);
   if (st->lay->dim == 1) {
-    k_lincomb<<<st->lay->count, 256, 0, s>>>(st->lay->l1.d_inst, st->dt_dev, out, lc, st->P,
-                                             components);
+    const sgn::Layout1d& L = st->lay->l1;
+    int maxn = 8;
+    for (int l = 3; l <= 13; ++l)
+      if (L.class_end[l] > L.class_begin[l]) maxn = 1 << l;
+    LinJobs J{};
+    J.j[0] = LinJob{out, lc, components};
+    J.j[1] = LinJob{out2, lc2, components2};
+    const dim3 grid((maxn + kLinChunk - 1) / kLinChunk, L.count, out2 ? 2 : 1);
+    k_lincomb<<<grid, 256, 0, s>>>(L.d_inst, st->dt_dev, J, st->P);
   } else {
     sgn::launch_lincomb2d(st->lay->l2, st->dt_dev, out, lc.x, lc.a, lc.nx, lc.f, lc.c, lc.nf,
                           components, s);
+    if (out2)
+      sgn::launch_lincomb2d(st->lay->l2, st->dt_dev, out2, lc2.x, lc2.a, lc2.nx, lc2.f, lc2.c,
+                            lc2.nf, components2, s);
   }
   SGN_CUDA(st->lay->ctx, cudaGetLastError());
   return SGN_OK;
@@ -878,8 +914,8 @@ sgn_status rk4_once(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
   SGN_TRY(rhs_at(st, st->eta, st->u, st->fe[0], st->fU[0], s));
   SGN_TRY(copy_field(st, st->u_s, st->u, V, s));
   for (int i = 1; i < 4; ++i) {
-    SGN_TRY(lincomb(st, st->eta_s, {{st->eta, 1.0}}, {{st->fe[i - 1], a[i]}}, 1, s));
-    SGN_TRY(lincomb(st, st->U_s, {{st->U, 1.0}}, {{st->fU[i - 1], a[i]}}, d, s));
+    SGN_TRY(lincomb(st, st->eta_s, {{st->eta, 1.0}}, {{st->fe[i - 1], a[i]}}, 1, s, st->U_s,
+                    {{st->U, 1.0}}, {{st->fU[i - 1], a[i]}}, d));
     // stage 4 (c = 1) starts from u extrapolated from c = 0 and c = 1/2: 2 u^(3) - u_n
     // (only the initial guess of the solve changes)
     if (i == 3) SGN_TRY(lincomb(st, st->u_s, {{st->u_s, 2.0}, {st->u, -1.0}}, {}, d, s));
@@ -887,9 +923,9 @@ sgn_status rk4_once(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
   }
   const double b0 = 1.0 / 6.0, b1 = 1.0 / 3.0;
   SGN_TRY(lincomb(st, st->eta, {{st->eta, 1.0}},
-                  {{st->fe[0], b0}, {st->fe[1], b1}, {st->fe[2], b1}, {st->fe[3], b0}}, 1, s));
-  SGN_TRY(lincomb(st, st->U, {{st->U, 1.0}},
-                  {{st->fU[0], b0}, {st->fU[1], b1}, {st->fU[2], b1}, {st->fU[3], b0}}, d, s));
+                  {{st->fe[0], b0}, {st->fe[1], b1}, {st->fe[2], b1}, {st->fe[3], b0}}, 1, s,
+                  st->U, {{st->U, 1.0}},
+                  {{st->fU[0], b0}, {st->fU[1], b1}, {st->fU[2], b1}, {st->fU[3], b0}}, d));
   SGN_TRY(copy_field(st, st->u, st->u_s, V, s));
   SGN_TRY(solve_at(st, st->eta, st->U, st->u, o, s));
   (void)P;
@@ -1138,20 +1174,19 @@ extern "C" sgn_status sgn_step_abk(sgn_state* st, int order, const double* dt, i
       const double* const* he = st->he + L0;
       const double* const* hU = st->hU + L0;
       if (order == 2) {
-        SGN_TRY(lincomb(st, st->eta, {{st->eta, 1.0}}, {{he[0], B[2][0]}, {he[1], B[2][1]}}, 1, s));
-        SGN_TRY(lincomb(st, st->U, {{st->U, 1.0}}, {{hU[0], B[2][0]}, {hU[1], B[2][1]}}, d, s));
+        SGN_TRY(lincomb(st, st->eta, {{st->eta, 1.0}}, {{he[0], B[2][0]}, {he[1], B[2][1]}}, 1, s,
+                        st->U, {{st->U, 1.0}}, {{hU[0], B[2][0]}, {hU[1], B[2][1]}}, d));
       } else if (order == 3) {
         SGN_TRY(lincomb(st, st->eta, {{st->eta, 1.0}},
-                        {{he[0], B[3][0]}, {he[1], B[3][1]}, {he[2], B[3][2]}}, 1, s));
-        SGN_TRY(lincomb(st, st->U, {{st->U, 1.0}},
-                        {{hU[0], B[3][0]}, {hU[1], B[3][1]}, {hU[2], B[3][2]}}, d, s));
+                        {{he[0], B[3][0]}, {he[1], B[3][1]}, {he[2], B[3][2]}}, 1, s, st->U,
+                        {{st->U, 1.0}}, {{hU[0], B[3][0]}, {hU[1], B[3][1]}, {hU[2], B[3][2]}},
+                        d));
       } else {
         SGN_TRY(lincomb(st, st->eta, {{st->eta, 1.0}},
                         {{he[0], B[4][0]}, {he[1], B[4][1]}, {he[2], B[4][2]}, {he[3], B[4][3]}},
-                        1, s));
-        SGN_TRY(lincomb(st, st->U, {{st->U, 1.0}},
+                        1, s, st->U, {{st->U, 1.0}},
                         {{hU[0], B[4][0]}, {hU[1], B[4][1]}, {hU[2], B[4][2]}, {hU[3], B[4][3]}},
-                        d, s));
+                        d));
       }
       // the solve for u_{n+1} and the newest history level f(w_{n+1}) (the combinations
       // above were launched with the current history pointers, so rotating is safe)
@@ -1212,9 +1247,9 @@ extern "C" sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nstep
     SGN_TRY(rhs_at(st, st->eta, st->u, st->he[1], st->hU[1], s));
     SGN_TRY(res_of(st->eta, st->u, st->U, st->res1));
     SGN_TRY(lincomb(st, st->eta_s, {{st->eta, 4.0 / 3.0}, {st->eta_p, -1.0 / 3.0}},
-                    {{st->he[1], 4.0 / 3.0}, {st->he[0], -2.0 / 3.0}}, 1, s));
-    SGN_TRY(lincomb(st, st->U_s, {{st->U, 4.0 / 3.0}, {st->U_p, -1.0 / 3.0}},
-                    {{st->hU[1], 4.0 / 3.0}, {st->hU[0], -2.0 / 3.0}}, d, s));
+                    {{st->he[1], 4.0 / 3.0}, {st->he[0], -2.0 / 3.0}}, 1, s, st->U_s,
+                    {{st->U, 4.0 / 3.0}, {st->U_p, -1.0 / 3.0}},
+                    {{st->hU[1], 4.0 / 3.0}, {st->hU[0], -2.0 / 3.0}}, d));
     cudaError_t e =
         st->lay->dim == 1
             ? sgn::launch_linimp_solve1d(st->lay->l1, ctx->tw64, st->A_fixed, st->res1, st->res0,
