@@ -24,7 +24,8 @@
  *    is row-major [ny][nx] (x fastest).
  *  - Grid (§6.1): x_j = j Lx/nx; spectral derivatives D = F^{-1}(iK)F with
  *    k_j = 2 pi j/L, j = -n/2+1..n/2-1, and the n/2 wavenumber set to 0.
- *    nx, ny must be powers of two; 1d needs 8 <= nx <= 8192.
+ *    nx, ny must be powers of two; 1d needs 8 <= nx <= 16384 (nx = 16384 runs each solve
+ *    and right-hand side on a thread-block cluster of two CTAs), 2d 8 <= nx, ny <= 1024.
  */
 #ifndef SGN_H
 #define SGN_H

@@ -1,5 +1,9 @@
-// 1d periodic SGN kernels: one CTA owns one instance (n <= 8192) and keeps the whole
-// transform in shared memory, so a PCG solve never leaves the SM between iterations.
+// 1d periodic SGN kernels: one CTA owns one instance and keeps the whole transform in
+// shared memory (n <= 8192), so a PCG solve never leaves the SM between iterations.  The
+// float64 helper kernels of this file (derivative, G apply, A solve, SBDF2 pieces) take the
+// transform buffer of n = 16384 from a global scratch (`big`, L2-resident) instead; the
+// solve and right-hand side run n = 16384 on two-CTA clusters (sgn_1d_pcg.cuh,
+// sgn_1d_rhs.cuh).
 //
 // Spectral-space PCG.  All Krylov vectors live as half spectra (modes 0..n/2 of real
 // fields).  One iteration needs two complex FFTs of length n:
@@ -42,11 +46,13 @@ __global__ void k_twiddles(cplx<double>* tw64, cplx<float>* tw32, cplx<df>* twdf
 template <int NT, int MAXB>
 __global__ void __launch_bounds__(NT, 1) k_deriv1d(const Inst1d* __restrict__ insts,
                                                 const int* __restrict__ ids,
+                                                cplx<double>* big,
                                                 const cplx<double>* __restrict__ tw,
                                                 const double* __restrict__ f,
                                                 double* __restrict__ fx) {
   extern __shared__ __align__(16) unsigned char smem[];
-  cplx<double>* buf = reinterpret_cast<cplx<double>*>(smem);
+  cplx<double>* buf = big ? big + ((size_t)blockIdx.x << kMaxLog1d)
+                          : reinterpret_cast<cplx<double>*>(smem);
   const Inst1d I = insts[ids[blockIdx.x]];
   const int n = I.n;
   const double kunit = 2.0 * kPi / I.L;
@@ -67,13 +73,15 @@ __global__ void __launch_bounds__(NT, 1) k_deriv1d(const Inst1d* __restrict__ in
 template <int NT, int MAXB>
 __global__ void __launch_bounds__(NT, 1) k_apply_G1d(const Inst1d* __restrict__ insts,
                                                   const int* __restrict__ ids,
+                                                  cplx<double>* big,
                                                   const cplx<double>* __restrict__ tw,
                                                   const double* __restrict__ eta,
                                                   const double* __restrict__ hx,
                                                   const double* __restrict__ u,
                                                   double* __restrict__ Gu) {
   extern __shared__ __align__(16) unsigned char smem[];
-  cplx<double>* buf = reinterpret_cast<cplx<double>*>(smem);
+  cplx<double>* buf = big ? big + ((size_t)blockIdx.x << kMaxLog1d)
+                          : reinterpret_cast<cplx<double>*>(smem);
   const Inst1d I = insts[ids[blockIdx.x]];
   const int n = I.n, h = n >> 1;
   for (int j = threadIdx.x; j < n; j += NT) buf[j] = mk(u[I.off + j], 0.0);
@@ -123,12 +131,14 @@ __global__ void __launch_bounds__(NT, 1) k_coeffs1d(const Inst1d* __restrict__ i
 template <int NT, int MAXB>
 __global__ void __launch_bounds__(NT, 1) k_precond1d(const Inst1d* __restrict__ insts,
                                                   const int* __restrict__ ids,
+                                                  cplx<double>* big,
                                                   const cplx<double>* __restrict__ tw,
                                                   const SolveRec* __restrict__ rec,
                                                   const double* __restrict__ r,
                                                   double* __restrict__ z) {
   extern __shared__ __align__(16) unsigned char smem[];
-  cplx<double>* buf = reinterpret_cast<cplx<double>*>(smem);
+  cplx<double>* buf = big ? big + ((size_t)blockIdx.x << kMaxLog1d)
+                          : reinterpret_cast<cplx<double>*>(smem);
   const int id = ids[blockIdx.x];
   const Inst1d I = insts[id];
   const int n = I.n;
@@ -170,6 +180,7 @@ __global__ void k_axpy1d(const Inst1d* __restrict__ insts, const double* __restr
 template <int NT, int MAXB>
 __global__ void __launch_bounds__(NT, 1) k_linimp_res1d(const Inst1d* __restrict__ insts,
                                                      const int* __restrict__ ids,
+                                                     cplx<double>* big,
                                                      const cplx<double>* __restrict__ tw,
                                                      const SolveRec* __restrict__ A,
                                                      const double* __restrict__ eta_all,
@@ -179,7 +190,8 @@ __global__ void __launch_bounds__(NT, 1) k_linimp_res1d(const Inst1d* __restrict
                                                      cplx<double>* __restrict__ res,
                                                      cplx<double>* __restrict__ ws) {
   extern __shared__ __align__(16) unsigned char smem[];
-  cplx<double>* buf = reinterpret_cast<cplx<double>*>(smem);
+  cplx<double>* buf = big ? big + ((size_t)blockIdx.x << kMaxLog1d)
+                          : reinterpret_cast<cplx<double>*>(smem);
   const int id = ids[blockIdx.x];
   const Inst1d I = insts[id];
   const int n = I.n, h = n >> 1;
@@ -211,6 +223,7 @@ __global__ void __launch_bounds__(NT, 1) k_linimp_res1d(const Inst1d* __restrict
 template <int NT, int MAXB>
 __global__ void __launch_bounds__(NT, 1) k_linimp_solve1d(const Inst1d* __restrict__ insts,
                                                        const int* __restrict__ ids,
+                                                       cplx<double>* big,
                                                        const cplx<double>* __restrict__ tw,
                                                        const SolveRec* __restrict__ A,
                                                        const cplx<double>* __restrict__ res1,
@@ -218,7 +231,8 @@ __global__ void __launch_bounds__(NT, 1) k_linimp_solve1d(const Inst1d* __restri
                                                        double c1, double c0,
                                                        double* __restrict__ u_all) {
   extern __shared__ __align__(16) unsigned char smem[];
-  cplx<double>* buf = reinterpret_cast<cplx<double>*>(smem);
+  cplx<double>* buf = big ? big + ((size_t)blockIdx.x << kMaxLog1d)
+                          : reinterpret_cast<cplx<double>*>(smem);
   const int id = ids[blockIdx.x];
   const Inst1d I = insts[id];
   const int n = I.n, h = n >> 1;
@@ -255,11 +269,13 @@ cudaError_t launch_deriv1d(const Layout1d& lay, const void* tw64, const double* 
   auto tw = static_cast<const cplx<double>*>(tw64);
   return for_each_class(lay, s, [&](auto NTc, auto MBc, int l, int first, int num, cudaStream_t s) {
     constexpr int NT = decltype(NTc)::value, MB = decltype(MBc)::value;
-    size_t sm = (size_t)16 << l;
+    const bool gl = l > kSmemLog1d;                // transform buffer in global scratch
+    const size_t sm = gl ? 0 : (size_t)16 << l;
+    cplx<double>* big = gl ? static_cast<cplx<double>*>(lay.big) : nullptr;
     auto k = k_deriv1d<NT, MB>;
     cudaError_t e = set_smem(k, sm);
     if (e) return e;
-    k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, tw, f, fx);
+    k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, big, tw, f, fx);
     return cudaGetLastError();
   });
 }
@@ -269,11 +285,13 @@ cudaError_t launch_apply_G1d(const Layout1d& lay, const void* tw64, const double
   auto tw = static_cast<const cplx<double>*>(tw64);
   return for_each_class(lay, s, [&](auto NTc, auto MBc, int l, int first, int num, cudaStream_t s) {
     constexpr int NT = decltype(NTc)::value, MB = decltype(MBc)::value;
-    size_t sm = (size_t)16 << l;
+    const bool gl = l > kSmemLog1d;                // transform buffer in global scratch
+    const size_t sm = gl ? 0 : (size_t)16 << l;
+    cplx<double>* big = gl ? static_cast<cplx<double>*>(lay.big) : nullptr;
     auto k = k_apply_G1d<NT, MB>;
     cudaError_t e = set_smem(k, sm);
     if (e) return e;
-    k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, tw, eta, hx, u, Gu);
+    k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, big, tw, eta, hx, u, Gu);
     return cudaGetLastError();
   });
 }
@@ -289,11 +307,13 @@ cudaError_t launch_precond1d(const Layout1d& lay, const void* tw64, const SolveR
   auto tw = static_cast<const cplx<double>*>(tw64);
   return for_each_class(lay, s, [&](auto NTc, auto MBc, int l, int first, int num, cudaStream_t s) {
     constexpr int NT = decltype(NTc)::value, MB = decltype(MBc)::value;
-    size_t sm = (size_t)16 << l;
+    const bool gl = l > kSmemLog1d;                // transform buffer in global scratch
+    const size_t sm = gl ? 0 : (size_t)16 << l;
+    cplx<double>* big = gl ? static_cast<cplx<double>*>(lay.big) : nullptr;
     auto k = k_precond1d<NT, MB>;
     cudaError_t e = set_smem(k, sm);
     if (e) return e;
-    k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, tw, rec, r, z);
+    k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, big, tw, rec, r, z);
     return cudaGetLastError();
   });
 }
@@ -317,11 +337,13 @@ cudaError_t launch_linimp_res1d(const Layout1d& lay, const void* tw64, const Sol
   auto tw = static_cast<const cplx<double>*>(tw64);
   return for_each_class(lay, s, [&](auto NTc, auto MBc, int l, int first, int num, cudaStream_t s) {
     constexpr int NT = decltype(NTc)::value, MB = decltype(MBc)::value;
-    size_t sm = (size_t)16 << l;
+    const bool gl = l > kSmemLog1d;                // transform buffer in global scratch
+    const size_t sm = gl ? 0 : (size_t)16 << l;
+    cplx<double>* big = gl ? static_cast<cplx<double>*>(lay.big) : nullptr;
     auto k = k_linimp_res1d<NT, MB>;
     cudaError_t e = set_smem(k, sm);
     if (e) return e;
-    k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, tw, A, eta, hx, u, U,
+    k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, big, tw, A, eta, hx, u, U,
                           static_cast<cplx<double>*>(res_hat), static_cast<cplx<double>*>(ws));
     return cudaGetLastError();
   });
@@ -333,11 +355,13 @@ cudaError_t launch_linimp_solve1d(const Layout1d& lay, const void* tw64, const S
   auto tw = static_cast<const cplx<double>*>(tw64);
   return for_each_class(lay, s, [&](auto NTc, auto MBc, int l, int first, int num, cudaStream_t s) {
     constexpr int NT = decltype(NTc)::value, MB = decltype(MBc)::value;
-    size_t sm = (size_t)16 << l;
+    const bool gl = l > kSmemLog1d;                // transform buffer in global scratch
+    const size_t sm = gl ? 0 : (size_t)16 << l;
+    cplx<double>* big = gl ? static_cast<cplx<double>*>(lay.big) : nullptr;
     auto k = k_linimp_solve1d<NT, MB>;
     cudaError_t e = set_smem(k, sm);
     if (e) return e;
-    k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, tw, A,
+    k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, big, tw, A,
                           static_cast<const cplx<double>*>(res1_hat),
                           static_cast<const cplx<double>*>(res0_hat), c1, c0, u);
     return cudaGetLastError();

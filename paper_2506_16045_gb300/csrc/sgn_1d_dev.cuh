@@ -21,9 +21,11 @@ __device__ __forceinline__ double mode_k(int m, int n, double kunit) {
 
 // ---------------------------------------------------------------------------------------
 // a1: preconditioner coefficients by block reductions (Eq:FlatbathCoeff, Eq:Optcoeff,
-// Eq:Optcoeffb, replacement remark of §4).
+// Eq:Optcoeffb, replacement remark of §4).  With CL = 2 the CTA holds one half of the
+// instance (n points each) and the two halves' extrema meet through distributed shared
+// memory; max and min are exact, so both CTAs form the same coefficients.
 // ---------------------------------------------------------------------------------------
-template <int NT>
+template <int NT, int CL = 1>
 __device__ __forceinline__ void coeffs_block(const double* __restrict__ eta, const double* __restrict__ hx, int n,
                              int kind, double* red, SolveRec& R) {
   double emin = 1.0e308, emax = -1.0e308, g2max = 0.0, sopt = -1.0e308, bad = 0.0;
@@ -41,6 +43,23 @@ __device__ __forceinline__ void coeffs_block(const double* __restrict__ eta, con
   g2max = block_max<NT>(g2max, red);
   sopt = block_max<NT>(sopt, red);
   bad = block_max<NT>(bad, red);
+  if constexpr (CL > 1) {
+    __shared__ double xc[5];
+    if (threadIdx.x == 0) {
+      xc[0] = emin;
+      xc[1] = emax;
+      xc[2] = g2max;
+      xc[3] = sopt;
+      xc[4] = bad;
+    }
+    cluster_sync();
+    const double* pc = peer(xc);
+    emin = fmin(emin, pc[0]);
+    emax = fmax(emax, pc[1]);
+    g2max = fmax(g2max, pc[2]);
+    sopt = fmax(sopt, pc[3]);
+    bad = fmax(bad, pc[4]);
+  }
   R.eta_min = emin;
   R.eta_max = emax;
   if (bad > 0.0) {
@@ -234,11 +253,11 @@ using IC = std::integral_constant<int, V>;
 template <typename Call>
 cudaError_t fan_classes(const Layout1d& lay, cudaStream_t s, Call&& call) {
   int ncls = 0;
-  for (int l = 3; l <= 13; ++l) ncls += lay.class_end[l] > lay.class_begin[l];
+  for (int l = 3; l <= kMaxLog1d; ++l) ncls += lay.class_end[l] > lay.class_begin[l];
   const bool fan = ncls > 1 && lay.side[0] != nullptr;
   if (fan && cudaEventRecord(lay.fork, s) != cudaSuccess) return cudaGetLastError();
   int ci = 0;
-  for (int l = 13; l >= 3; --l) {
+  for (int l = kMaxLog1d; l >= 3; --l) {
     const int b = lay.class_begin[l], e = lay.class_end[l];
     if (e <= b) continue;
     cudaStream_t cs = s;
@@ -259,7 +278,8 @@ cudaError_t fan_classes(const Layout1d& lay, cudaStream_t s, Call&& call) {
 }
 
 // Size-class dispatch for the cta_fft kernels: NT = clamp(n/8, 32, 512) threads, MAXB =
-// n/(4 NT) butterflies per thread per radix-4 stage.
+// n/(4 NT) butterflies per thread per radix-4 stage (n = 16384: 1024 threads, and the
+// transform buffer in the layout's global scratch instead of shared memory).
 template <typename Fn>
 cudaError_t for_each_class(const Layout1d& lay, cudaStream_t s, Fn&& fn) {
   return fan_classes(lay, s, [&](int l, int b, int num, cudaStream_t cs) -> cudaError_t {
@@ -271,6 +291,7 @@ cudaError_t for_each_class(const Layout1d& lay, cudaStream_t s, Fn&& fn) {
       case 11: return fn(IC<256>{}, IC<2>{}, l, b, num, cs);
       case 12: return fn(IC<512>{}, IC<2>{}, l, b, num, cs);
       case 13: return fn(IC<512>{}, IC<4>{}, l, b, num, cs);
+      case 14: return fn(IC<1024>{}, IC<4>{}, l, b, num, cs);
       default: return cudaErrorInvalidValue;
     }
   });
@@ -292,9 +313,34 @@ cudaError_t for_each_size(const Layout1d& lay, cudaStream_t s, Fn&& fn) {
       case 11: return fn(IC<11>{}, b, num, cs);
       case 12: return fn(IC<12>{}, b, num, cs);
       case 13: return fn(IC<13>{}, b, num, cs);
+      case 14: return fn(IC<14>{}, b, num, cs);
       default: return cudaErrorInvalidValue;
     }
   });
+}
+
+// num instances of CL CTAs each (CL = 2: thread-block clusters of two consecutive CTAs)
+template <int CL, typename... P>
+cudaError_t launch_clustered(void (*kernel)(P...), int num, int threads, size_t smem,
+                             cudaStream_t s, const P&... args) {
+  if constexpr (CL == 1) {
+    kernel<<<num, threads, smem, s>>>(args...);
+    return cudaGetLastError();
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(num * CL), 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+  }
 }
 
 template <typename K>

@@ -17,6 +17,7 @@ extern template cudaError_t pcg1d_launch<10>(const PcgArgs&, int, int, cudaStrea
 extern template cudaError_t pcg1d_launch<11>(const PcgArgs&, int, int, cudaStream_t);
 extern template cudaError_t pcg1d_launch<12>(const PcgArgs&, int, int, cudaStream_t);
 extern template cudaError_t pcg1d_launch<13>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<14>(const PcgArgs&, int, int, cudaStream_t);
 extern template cudaError_t rhs1d_launch<3>(const RhsArgs&, int, int, cudaStream_t);
 extern template cudaError_t rhs1d_launch<4>(const RhsArgs&, int, int, cudaStream_t);
 extern template cudaError_t rhs1d_launch<5>(const RhsArgs&, int, int, cudaStream_t);
@@ -28,6 +29,7 @@ extern template cudaError_t rhs1d_launch<10>(const RhsArgs&, int, int, cudaStrea
 extern template cudaError_t rhs1d_launch<11>(const RhsArgs&, int, int, cudaStream_t);
 extern template cudaError_t rhs1d_launch<12>(const RhsArgs&, int, int, cudaStream_t);
 extern template cudaError_t rhs1d_launch<13>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<14>(const RhsArgs&, int, int, cudaStream_t);
 
 namespace {
 

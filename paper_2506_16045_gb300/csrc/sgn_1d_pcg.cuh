@@ -15,6 +15,11 @@
 //                  a thread) and the correction d in shared memory; its dot products reduce
 //                  in double-float and one thread forms alpha, beta and the stopping test.
 //
+// n = 16384 runs on a thread-block cluster of two CTAs (CL = 2, sgn_fft1d.cuh's two-CTA
+// transforms): each CTA holds half of the points and, in spectral space, the modes of one
+// parity; dot products add the two CTAs' block sums in rank order through distributed
+// shared memory, so both CTAs take every decision from the same numbers.
+//
 // Workspace slots per instance (half spectra of n/2 + 1 modes, 16 bytes per mode each):
 //   0: b^ (high precision), 1: x^ (high), 2: r^ and 3: p^ (float64 path only).
 // The mixed path keeps its double-float coefficients c1, c2, c3 in coef_df (high parts,
@@ -48,7 +53,8 @@ struct PcgArgs {
   void* ux;             // nullable: also store x_x here (see pcg_body)
 };
 
-template <int L>
+// LG = log2 n (LG = 14: two-CTA clusters of the n = 8192 kernel)
+template <int LG>
 cudaError_t pcg1d_launch(const PcgArgs& a, int first, int num, cudaStream_t s);
 
 namespace pcg1d {
@@ -117,6 +123,43 @@ struct PassScalars {    // refinement pass
   int status;
 };
 
+// Sums over the CTAs of a cluster of CL (1 or 2).  The block's total is published in the
+// CTA's slot xs[par]; after a cluster barrier both CTAs add rank 0's and rank 1's totals in
+// that order.  Callers flip par after every call, so a slot is rewritten only after the
+// partner has passed the next barrier (and so has read it).
+template <int NT, int CL, typename Finish>
+__device__ __forceinline__ void sum_df(float v, df* slot, df* xs, int& par, Finish finish) {
+  if constexpr (CL == 1) {
+    block_sum_df<NT>(v, slot, finish);
+  } else {
+    df* mine = xs + par;
+    block_sum_df<NT>(v, slot, [&](float hi, float lo) { *mine = df(hi, lo); });
+    cluster_sync();
+    if (threadIdx.x == 0) {
+      const df o = *peer(mine);
+      const df s = cluster_rank() == 0 ? *mine + o : o + *mine;
+      finish(s.hi, s.lo);
+    }
+    __syncthreads();
+    par ^= 1;
+  }
+}
+
+template <int NT, int CL>
+__device__ __forceinline__ double sum64(double v, double* red, double* xs, int& par) {
+  const double s = block_sum<NT>(v, red);
+  if constexpr (CL == 1) {
+    return s;
+  } else {
+    double* mine = xs + par;
+    if (threadIdx.x == 0) *mine = s;
+    cluster_sync();
+    const double o = *peer(mine);
+    par ^= 1;
+    return cluster_rank() == 0 ? s + o : o + s;
+  }
+}
+
 // Slot (b, s) of the paired layout for slot number q < RP (compile-time after unrolling).
 template <int L>
 struct Slot {
@@ -125,17 +168,19 @@ struct Slot {
   static constexpr int reg(int q) { return b(q) * Plan<L>::RP + s(q); }
 };
 
-// The solve of one instance by one CTA.  With ux non-null it also stores x_x
-// (double-float for the mixed path, float64 otherwise) at ux[off + j]: the mixed path takes
-// it from the inverse transform of its last refinement pass, which yields x + i x_x; the
-// float64 path from its final transform.  A right-hand side that follows the solve in a
-// time step then needs one derivative pair less.
-template <int L, bool MIXED>
+// The solve of one instance by one CTA (CL = 1) or one cluster of two (CL = 2: n = 2^(L+1),
+// the CTA of rank r holding points [r nl, r nl + nl) and modes 2 k + r).  With ux non-null
+// it also stores x_x (double-float for the mixed path, float64 otherwise) at ux[off + j]:
+// the mixed path takes it from the inverse transform of its last refinement pass, which
+// yields x + i x_x; the float64 path from its final transform.  A right-hand side that
+// follows the solve in a time step then needs one derivative pair less.
+template <int L, bool MIXED, int CL>
 __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) {
   using PL = Plan<L>;
   using SL = Slot<L>;
   using SM = SmemPcg<L>;
-  constexpr int n = PL::n, h = n / 2, E = PL::E, RP = PL::RP, HS = PL::HS, NTA = PL::NTA;
+  constexpr int nl = PL::n, E = PL::E, RP = PL::RP, HS = PL::HS, NTA = PL::NTA;
+  constexpr int n = CL * nl, h = n / 2;
   constexpr int NT = PL::NT, W = NT / 32;
   using TH = typename std::conditional<MIXED, df, double>::type;   // high precision
   extern __shared__ __align__(16) unsigned char smem[];
@@ -143,17 +188,28 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
   __shared__ df slots[2 * W];
   __shared__ PcgScalars sc;
   __shared__ PassScalars ps;
+  __shared__ df xs_df[2];
+  __shared__ double xs64[2];
+  int par = 0;
 
   const int t = threadIdx.x;
-  const Geo<L> g(t);
+  const unsigned rk = CL > 1 ? cluster_rank() : 0u;
+  const Geo<L> g(t, rk != 0);
   const bool t0 = (t == 0);
-  const int id = A.ids[first + blockIdx.x];
+  const bool ts = t0 && rk == 0;       // owner of the real modes 0 and n/2
+  const int id = A.ids[first + (CL > 1 ? (int)(blockIdx.x / CL) : (int)blockIdx.x)];
   const Inst1d I = A.insts[id];
-  const double* eta = A.eta + I.off;
-  const double* hx = A.hx + I.off;
-  const double* b = A.b + I.off;
-  double* x = A.x + I.off;
+  const long long own = I.off + (long long)rk * nl;    // first point of this CTA
+  const double* eta = A.eta + own;
+  const double* hx = A.hx + own;
+  const double* b = A.b + own;
+  double* x = A.x + own;
   const long long S = h + 1;
+  // global mode of local spectral index k, and the local index of its mirror n - m
+  auto gm = [&](int k) { return CL * k + (int)rk; };
+  auto mir = [&](int k) { return rk ? nl - 1 - k : (nl - k) & (nl - 1); };
+  auto sum_f = [&](float v, df* sl, auto finish) { sum_df<NT, CL>(v, sl, xs_df, par, finish); };
+  auto sum_d = [&](double v) { return sum64<NT, CL>(v, red, xs64, par); };
   cplx<TH>* Bh = reinterpret_cast<cplx<TH>*>(A.ws + I.ws);
   cplx<TH>* Xh = reinterpret_cast<cplx<TH>*>(A.ws + I.ws + S);
   const double rtol = A.rtol, rtol_inner = A.rtol_inner;
@@ -165,18 +221,19 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
     R = A.given[id];
     R.status = SGN_OK;
   } else {
-    coeffs_block<NT>(eta, hx, n, A.kind, red, R);
+    coeffs_block<NT, CL>(eta, hx, nl, A.kind, red, R);
   }
   R.iters = 0;
   R.refinements = 0;
   R.ratio = 0.0;
   if (R.status != SGN_OK) {
-    if (t0) A.rec[id] = R;
+    if (ts) A.rec[id] = R;
     return;
   }
   const double kunit = 2.0 * kPi / I.L;
   const float kf = (float)kunit, sigf = (float)R.sigma, alf = (float)R.alpha;
-  const XBuf<TH> XH(smem, n);
+  const XBuf<TH> XH(smem, nl);
+  const XBuf<TH> XHp = CL > 1 ? XBuf<TH>(peer(smem), nl) : XH;   // the partner's
   // float32 preconditioner symbol 1 / (sigma + alpha k^2) of mode m < n/2 (Nyquist: 1/sigma)
   auto dinv = [&](int m) {
     const float k = kf * (float)m;
@@ -185,15 +242,22 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
   const float dN = recip(sigf);
 
   const float* eh = reinterpret_cast<const float*>(smem + SM::off_e);
-  const float* cdf = A.coef_df + 6 * I.off;
+  const float* cdf = A.coef_df + 6 * own;     // this CTA's points, planes of nl
   if constexpr (MIXED)
-    prep_coefficients<NT>(eta, hx, n, reinterpret_cast<float*>(smem + SM::off_e),
-                          A.coef_df + 6 * I.off);
+    prep_coefficients<NT>(eta, hx, nl, reinterpret_cast<float*>(smem + SM::off_e),
+                          A.coef_df + 6 * own);
+  const cplx<TH>* twh = MIXED ? reinterpret_cast<const cplx<TH>*>(A.twdf)
+                              : reinterpret_cast<const cplx<TH>*>(A.tw64);
+  // the cross-CTA stages of CL = 2 around the compact transforms
+  auto split_h = [&]() {
+    if constexpr (CL > 1) f1::cross_smem<TH, L, f1::kSplitFwd>(XH, XHp, t, g.bnat, g.act, rk, twh);
+  };
+  auto join_h = [&]() {
+    if constexpr (CL > 1) f1::cross_smem<TH, L, f1::kJoinConj>(XH, XHp, t, g.bnat, g.act, rk, twh);
+  };
 
   // ---- b^ and x0^ from one transform of b + i x0
   {
-    const cplx<TH>* tw = MIXED ? reinterpret_cast<const cplx<TH>*>(A.twdf)
-                               : reinterpret_cast<const cplx<TH>*>(A.tw64);
     if (g.act) {
 #pragma unroll
       for (int e = 0; e < E; ++e) {
@@ -201,30 +265,31 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
         XH.st(g.bnat ^ f1::swz_c(e * NTA), mk(num<TH>(b[j]), num<TH>(x[j])));
       }
     }
-    f1::fft_smem<TH, L>(XH, tw);
+    split_h();
+    f1::fft_smem<TH, L>(XH, twh);
     float bb = 0.0f;
     if (g.act) {
 #pragma unroll
       for (int q = 0; q < RP; ++q) {
-        const int m = g.mode(SL::b(q), SL::s(q));
-        const cplx<TH> y = XH.ld(f1::swz(m));
-        const cplx<TH> ym = conj(XH.ld(f1::swz((n - m) & (n - 1))));
+        const int k = g.mode(SL::b(q), SL::s(q)), m = gm(k);
+        const cplx<TH> y = XH.ld(f1::swz(k));
+        const cplx<TH> ym = conj(XH.ld(f1::swz(mir(k))));
         const cplx<TH> s = y + ym, d = mul_mi(y - ym);
         const cplx<TH> bh = mk(half(s.x), half(s.y));
         Bh[m] = bh;
         Xh[m] = mk(half(d.x), half(d.y));
         const float bx = lead(bh.x), by = lead(bh.y);
-        bb += ((t0 && q == 0) ? 1.0f : 2.0f) * (bx * bx + by * by) * dinv(m);
+        bb += ((ts && q == 0) ? 1.0f : 2.0f) * (bx * bx + by * by) * dinv(m);
       }
-      if (t0) {
-        const cplx<TH> y = XH.ld(f1::swz(h));
+      if (ts) {
+        const cplx<TH> y = XH.ld(f1::swz(nl / 2));
         Bh[h] = mk(y.x, from_int<TH>(0));
         Xh[h] = mk(y.y, from_int<TH>(0));
         const float bx = lead(y.x);
         bb += bx * bx * dN;
       }
     }
-    block_sum_df<NT>(bb, slots, [&](float hi, float lo) {
+    sum_f(bb, slots, [&](float hi, float lo) {
       ps.ratio = (double)hi + (double)lo;        // b.A^{-1}b
     });
   }
@@ -236,7 +301,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
 #pragma unroll
       for (int e = 0; e < E; ++e) x[t + e * NTA] = 0.0;
     R.status = (bb == 0.0) ? SGN_OK : SGN_ERR_BREAKDOWN;
-    if (t0) A.rec[id] = R;
+    if (ts) A.rec[id] = R;
     return;
   }
 
@@ -254,28 +319,33 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
       const double k = kunit * (double)m;
       return 1.0 / (R.sigma + R.alpha * k * k);
     };
-    // (G v)^ of the slots of the half spectrum Vh into gq / gN
-    auto matvec = [&](const cplx<double>* __restrict__ Vh, cplx<double>(&gq)[RP],
-                      cplx<double>& gN) {
+    // conj(Z) of the half spectrum Vh into XH, Z_m = (1 - k) v_m and Z_{n-m} = (1 + k)
+    // conj(v_m) (k = 0: the plain inverse), then the transform: XH holds conj(n (v + i v_x))
+    auto to_real = [&](const cplx<double>* __restrict__ Vh, bool with_k) {
       __syncthreads();                           // earlier readers of the buffer are done
       if (g.act) {
-        // conj(Z), Z_m = (1 - k) v_m and Z_{n-m} = conj(Z_m)-mirror (1 + k) conj(v_m)
 #pragma unroll
         for (int q = 0; q < RP; ++q) {
-          const int m = g.mode(SL::b(q), SL::s(q));
-          const double k = kunit * (double)m;
+          const int k = g.mode(SL::b(q), SL::s(q)), m = gm(k);
+          const double kk = with_k ? kunit * (double)m : 0.0;
           const cplx<double> p = Vh[m];
-          if (t0 && q == 0) {
+          if (ts && q == 0) {
             XH.st(0, mk(p.x, 0.0));
           } else {
-            XH.st(f1::swz(m), conj(p) * (1.0 - k));
-            XH.st(f1::swz(n - m), p * (1.0 + k));
+            XH.st(f1::swz(k), conj(p) * (1.0 - kk));
+            XH.st(f1::swz(mir(k)), p * (1.0 + kk));
           }
         }
-        if (t0) XH.st(f1::swz(h), mk(Vh[h].x, 0.0));
+        if (ts) XH.st(f1::swz(nl / 2), mk(Vh[h].x, 0.0));
       }
       __syncthreads();
       f1::fft_smem<double, L>(XH, A.tw64);
+      join_h();
+    };
+    // (G v)^ of the slots of the half spectrum Vh into gq / gN
+    auto matvec = [&](const cplx<double>* __restrict__ Vh, cplx<double>(&gq)[RP],
+                      cplx<double>& gN) {
+      to_real(Vh, true);
       if (g.act) {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -287,18 +357,19 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
           XH.st(a, mk(c1 * pv + c2 * px, c2 * pv + c3 * px));
         }
       }
+      split_h();
       f1::fft_smem<double, L>(XH, A.tw64);
       if (g.act) {
 #pragma unroll
         for (int q = 0; q < RP; ++q) {
-          const int m = g.mode(SL::b(q), SL::s(q));
-          const double k = kunit * (double)m;
-          const cplx<double> y = XH.ld(f1::swz(m));
-          const cplx<double> ym = conj(XH.ld(f1::swz((n - m) & (n - 1))));
-          const cplx<double> s = y * (1.0 - k) + ym * (1.0 + k);
+          const int k = g.mode(SL::b(q), SL::s(q));
+          const double kk = kunit * (double)gm(k);
+          const cplx<double> y = XH.ld(f1::swz(k));
+          const cplx<double> ym = conj(XH.ld(f1::swz(mir(k))));
+          const cplx<double> s = y * (1.0 - kk) + ym * (1.0 + kk);
           gq[q] = mk(0.5 * s.x, 0.5 * s.y);
         }
-        if (t0) gN = mk(XH.ld(f1::swz(h)).x, 0.0);
+        if (ts) gN = mk(XH.ld(f1::swz(nl / 2)).x, 0.0);
       }
     };
     // r = b - G x0, p = A^{-1} r
@@ -310,21 +381,21 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
       if (g.act) {
 #pragma unroll
         for (int q = 0; q < RP; ++q) {
-          const int m = g.mode(SL::b(q), SL::s(q));
+          const int m = gm(g.mode(SL::b(q), SL::s(q)));
           const cplx<double> r = Bh[m] - gq[q];
           const double di = dinv64(m);
           Rh[m] = r;
           Ph[m] = r * di;
-          loc += ((t0 && q == 0) ? 1.0 : 2.0) * (r.x * r.x + r.y * r.y) * di;
+          loc += ((ts && q == 0) ? 1.0 : 2.0) * (r.x * r.x + r.y * r.y) * di;
         }
-        if (t0) {
+        if (ts) {
           const cplx<double> r = Bh[h] - gN;
           Rh[h] = r;
           Ph[h] = r * isig;
           loc += (r.x * r.x + r.y * r.y) * isig;
         }
       }
-      rz = block_sum<NT>(loc, red);
+      rz = sum_d(loc);
     }
     while (sqrt(rz) > tol_abs) {
       if (iters >= maxit) {
@@ -337,12 +408,12 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
       if (g.act) {
 #pragma unroll
         for (int q = 0; q < RP; ++q) {
-          const cplx<double> p = Ph[g.mode(SL::b(q), SL::s(q))];
-          pq_loc += ((t0 && q == 0) ? 1.0 : 2.0) * (p.x * gq[q].x + p.y * gq[q].y);
+          const cplx<double> p = Ph[gm(g.mode(SL::b(q), SL::s(q)))];
+          pq_loc += ((ts && q == 0) ? 1.0 : 2.0) * (p.x * gq[q].x + p.y * gq[q].y);
         }
-        if (t0) pq_loc += Ph[h].x * gN.x;
+        if (ts) pq_loc += Ph[h].x * gN.x;
       }
-      const double pq = block_sum<NT>(pq_loc, red);
+      const double pq = sum_d(pq_loc);
       if (!(pq > 0.0) || !isfinite(pq)) {
         status = SGN_ERR_BREAKDOWN;
         break;
@@ -352,20 +423,20 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
       if (g.act) {
 #pragma unroll
         for (int q = 0; q < RP; ++q) {
-          const int m = g.mode(SL::b(q), SL::s(q));
+          const int m = gm(g.mode(SL::b(q), SL::s(q)));
           Xh[m] = Xh[m] + Ph[m] * at;
           const cplx<double> r = Rh[m] - gq[q] * at;
           Rh[m] = r;
-          rz_loc += ((t0 && q == 0) ? 1.0 : 2.0) * (r.x * r.x + r.y * r.y) * dinv64(m);
+          rz_loc += ((ts && q == 0) ? 1.0 : 2.0) * (r.x * r.x + r.y * r.y) * dinv64(m);
         }
-        if (t0) {
+        if (ts) {
           Xh[h] = Xh[h] + Ph[h] * at;
           const cplx<double> r = Rh[h] - gN * at;
           Rh[h] = r;
           rz_loc += (r.x * r.x + r.y * r.y) * isig;
         }
       }
-      const double rz_new = block_sum<NT>(rz_loc, red);
+      const double rz_new = sum_d(rz_loc);
       ++iters;
       if (!isfinite(rz_new)) {
         status = SGN_ERR_BREAKDOWN;
@@ -376,44 +447,28 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
       if (g.act) {
 #pragma unroll
         for (int q = 0; q < RP; ++q) {
-          const int m = g.mode(SL::b(q), SL::s(q));
+          const int m = gm(g.mode(SL::b(q), SL::s(q)));
           Ph[m] = Rh[m] * dinv64(m) + Ph[m] * beta;
         }
-        if (t0) Ph[h] = Rh[h] * isig + Ph[h] * beta;
+        if (ts) Ph[h] = Rh[h] * isig + Ph[h] * beta;
       }
     }
     R.ratio = sqrt(rz) / bnorm;
     // x = F^{-1} x^ = conj(F(conj x^)) / n; with ux, the transform of Z = (1 - k) x^ (mirror
     // (1 + k) conj x^) instead, which gives x + i x_x
-    __syncthreads();
-    if (g.act) {
-#pragma unroll
-      for (int q = 0; q < RP; ++q) {
-        const int m = g.mode(SL::b(q), SL::s(q));
-        const double k = ux ? kunit * (double)m : 0.0;
-        const cplx<double> xv = Xh[m];
-        if (t0 && q == 0) {
-          XH.st(0, mk(xv.x, 0.0));
-        } else {
-          XH.st(f1::swz(m), conj(xv) * (1.0 - k));
-          XH.st(f1::swz(n - m), xv * (1.0 + k));
-        }
-      }
-      if (t0) XH.st(f1::swz(h), mk(Xh[h].x, 0.0));
-    }
-    __syncthreads();
-    f1::fft_smem<double, L>(XH, A.tw64);
+    to_real(Xh, ux != nullptr);
     if (g.act) {
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const cplx<double> z = XH.ld(g.bnat ^ f1::swz_c(e * NTA));
         x[t + e * NTA] = z.x * inv_n;
-        if (ux) static_cast<double*>(ux)[I.off + t + e * NTA] = -z.y * inv_n;
+        if (ux) static_cast<double*>(ux)[own + t + e * NTA] = -z.y * inv_n;
       }
     }
   } else {
     // ------------------------------------------------------------------ mixed precision
-    const XBuf<float> XF(smem, n);
+    const XBuf<float> XF(smem, nl);
+    const XBuf<float> XFp = CL > 1 ? XBuf<float>(peer(smem), nl) : XF;
     const f1::TwF32 twf;
     cplx<float>* D = reinterpret_cast<cplx<float>*>(smem + SM::off_d);   // [RP + 1][NT]
     cplx<float>* Rr = reinterpret_cast<cplx<float>*>(smem + SM::off_r);  // [RP + 1][NT]
@@ -431,20 +486,21 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
           // conj(Z) with Z_m = (1 - k) x_m, Z_{n-m} = (1 + k) conj(x_m)
 #pragma unroll
           for (int q = 0; q < RP; ++q) {
-            const int m = g.mode(SL::b(q), SL::s(q));
+            const int kl = g.mode(SL::b(q), SL::s(q)), m = gm(kl);
             const df k = kh * df((float)m, 0.0f);
             const cplx<df> xv = Xh[m];
-            if (t0 && q == 0) {
+            if (ts && q == 0) {
               XH.st(0, mk(xv.x, zero));
             } else {
-              XH.st(f1::swz(m), conj(xv) * (one - k));
-              XH.st(f1::swz(n - m), xv * (one + k));
+              XH.st(f1::swz(kl), conj(xv) * (one - k));
+              XH.st(f1::swz(mir(kl)), xv * (one + k));
             }
           }
-          if (t0) XH.st(f1::swz(h), mk(Xh[h].x, zero));
+          if (ts) XH.st(f1::swz(nl / 2), mk(Xh[h].x, zero));
         }
         __syncthreads();
         f1::fft_smem<df, L>(XH, A.twdf);
+        join_h();
         if (g.act) {
           // rolled: unrolled, the compiler hoists the 6 coefficient loads of every element
 #pragma unroll 1
@@ -454,35 +510,36 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
             const cplx<df> z = XH.ld(a);         // conj of n (x + i x_x)
             const df pv = z.x * inv_n, px = -(z.y * inv_n);
             x[j] = to_f64(pv);
-            if (ux) static_cast<df*>(ux)[I.off + j] = px;
-            const df c1(cdf[j], cdf[3 * n + j]), c2(cdf[n + j], cdf[4 * n + j]),
-                c3(cdf[2 * n + j], cdf[5 * n + j]);
+            if (ux) static_cast<df*>(ux)[own + j] = px;
+            const df c1(cdf[j], cdf[3 * nl + j]), c2(cdf[nl + j], cdf[4 * nl + j]),
+                c3(cdf[2 * nl + j], cdf[5 * nl + j]);
             XH.st(a, mk(c1 * pv + c2 * px, c2 * pv + c3 * px));
           }
         }
+        split_h();
         f1::fft_smem<df, L>(XH, A.twdf);
         float rz_loc = 0.0f;
         if (g.act) {
 #pragma unroll
           for (int q = 0; q < RP; ++q) {
-            const int m = g.mode(SL::b(q), SL::s(q));
+            const int kl = g.mode(SL::b(q), SL::s(q)), m = gm(kl);
             const df k = kh * df((float)m, 0.0f);
-            const cplx<df> y = XH.ld(f1::swz(m));
-            const cplx<df> ym = conj(XH.ld(f1::swz((n - m) & (n - 1))));
+            const cplx<df> y = XH.ld(f1::swz(kl));
+            const cplx<df> ym = conj(XH.ld(f1::swz(mir(kl))));
             const cplx<df> s = y * (one - k) + ym * (one + k);
             const cplx<df> rr = Bh[m] - mk(half(s.x), half(s.y));
             rf[q] = mk(rr.x.hi + rr.x.lo, rr.y.hi + rr.y.lo);
-            rz_loc += ((t0 && q == 0) ? 1.0f : 2.0f) *
+            rz_loc += ((ts && q == 0) ? 1.0f : 2.0f) *
                       (rf[q].x * rf[q].x + rf[q].y * rf[q].y) * dinv(m);
           }
-          if (t0) {
-            const df rr = Bh[h].x - XH.ld(f1::swz(h)).x;
+          if (ts) {
+            const df rr = Bh[h].x - XH.ld(f1::swz(nl / 2)).x;
             rfN = mk(rr.hi + rr.lo, 0.0f);
             rz_loc += rfN.x * rfN.x * dN;
           }
         }
         // thread 0 decides the pass: converged, out of budget, or the next inner solve
-        block_sum_df<NT>(rz_loc, slots, [&](float hi, float lo) {
+        sum_f(rz_loc, slots, [&](float hi, float lo) {
           const double rz64 = (double)hi + (double)lo;
           const double nr = sqrt(rz64);
           const double ratio = nr / bnorm;
@@ -520,12 +577,12 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
 #pragma unroll
           for (int q = 0; q < RP; ++q) {
             const cplx<float> r = rf[q] * scale;
-            p[q] = r * dinv(g.mode(SL::b(q), SL::s(q)));
-            loc += ((t0 && q == 0) ? 1.0f : 2.0f) * (r.x * p[q].x + r.y * p[q].y);
+            p[q] = r * dinv(gm(g.mode(SL::b(q), SL::s(q))));
+            loc += ((ts && q == 0) ? 1.0f : 2.0f) * (r.x * p[q].x + r.y * p[q].y);
             Rr[q * NT + t] = r;
             D[q * NT + t] = mk(0.0f, 0.0f);
           }
-          if (t0) {
+          if (ts) {
             const cplx<float> r = rfN * scale;
             pN = r * dN;
             loc += r.x * pN.x;
@@ -533,7 +590,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
             D[RP * NT] = mk(0.0f, 0.0f);
           }
         }
-        block_sum_df<NT>(loc, slots + W, [&](float hi, float lo) {
+        sum_f(loc, slots + W, [&](float hi, float lo) {
           const float rz = hi + lo;
           sc.rz = rz;
           sc.state = (rz <= tin2) ? 1 : (it >= maxit ? 3 : 0);
@@ -549,48 +606,52 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
           if (g.act) {
 #pragma unroll
             for (int q = 0; q < RP; ++q) {
-              const float k = kf * (float)g.mode(SL::b(q), SL::s(q));
-              if (t0 && q == 0) {
+              const float k = kf * (float)gm(g.mode(SL::b(q), SL::s(q)));
+              if (ts && q == 0) {
                 v[0] = mk(p[0].x, 0.0f);
               } else {
                 v[SL::reg(q)] = p[q] * (1.0f - k);
-                f1::mirror_set<L>(v, t0, SL::b(q), SL::s(q), conj(p[q]) * (1.0f + k));
+                f1::mirror_set<L>(v, ts, SL::b(q), SL::s(q), conj(p[q]) * (1.0f + k));
               }
             }
-            if (t0) v[HS] = mk(pN.x, 0.0f);
+            if (ts) v[HS] = mk(pN.x, 0.0f);
           }
           f1::fft_inv<float, L>(XF, v, g, twf);
+          if constexpr (CL > 1)
+            f1::cross<float, L, f1::kJoinInv>(XF, XFp, v, t, g.bnat, g.act, rk, nullptr);
           if (g.act) {
 #pragma unroll
             for (int e = 0; e < E; ++e) {
               const int j = t + e * NTA;
               const float pv = v[e].x * inv_nf, px = v[e].y * inv_nf;
-              const float et = eh[j], gx = eh[n + j];
+              const float et = eh[j], gx = eh[nl + j];
               const float e2 = et * et;
               const float c1 = fmaf(et * gx, gx, et), c2 = 0.5f * e2 * gx,
                           c3 = e2 * et * (1.0f / 3.0f);
               v[e] = mk(c1 * pv + c2 * px, c2 * pv + c3 * px);
             }
           }
+          if constexpr (CL > 1)
+            f1::cross<float, L, f1::kSplitFwd>(XF, XFp, v, t, g.bnat, g.act, rk, nullptr);
           f1::fft_fwd<float, L>(XF, v, g, twf);
           cplx<float> gq[RP], gN = mk(0.0f, 0.0f);
           float pq_loc = 0.0f;
           if (g.act) {
 #pragma unroll
             for (int q = 0; q < RP; ++q) {
-              const float k = kf * (float)g.mode(SL::b(q), SL::s(q));
+              const float k = kf * (float)gm(g.mode(SL::b(q), SL::s(q)));
               const cplx<float> y = v[SL::reg(q)];
-              const cplx<float> ym = conj(f1::mirror_get<L>(v, t0, SL::b(q), SL::s(q)));
+              const cplx<float> ym = conj(f1::mirror_get<L>(v, ts, SL::b(q), SL::s(q)));
               const cplx<float> s = y * (1.0f - k) + ym * (1.0f + k);
               gq[q] = mk(0.5f * s.x, 0.5f * s.y);
-              pq_loc += ((t0 && q == 0) ? 1.0f : 2.0f) * (p[q].x * gq[q].x + p[q].y * gq[q].y);
+              pq_loc += ((ts && q == 0) ? 1.0f : 2.0f) * (p[q].x * gq[q].x + p[q].y * gq[q].y);
             }
-            if (t0) {
+            if (ts) {
               gN = mk(v[HS].x, 0.0f);
               pq_loc += pN.x * gN.x;
             }
           }
-          block_sum_df<NT>(pq_loc, slots, [&](float hi, float lo) {
+          sum_f(pq_loc, slots, [&](float hi, float lo) {
             const float pq = hi + lo;
             if (!(pq > 0.0f) || !isfinite(pq)) sc.state = 2;
             else sc.alpha = sc.rz / pq;
@@ -608,9 +669,9 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
               D[o] = D[o] + p[q] * at;
               const cplx<float> r = Rr[o] - gq[q] * at;
               Rr[o] = r;
-              rz_loc += ((t0 && q == 0) ? 1.0f : 2.0f) * (r.x * r.x + r.y * r.y) * dinv(g.mode(SL::b(q), SL::s(q)));
+              rz_loc += ((ts && q == 0) ? 1.0f : 2.0f) * (r.x * r.x + r.y * r.y) * dinv(gm(g.mode(SL::b(q), SL::s(q))));
             }
-            if (t0) {
+            if (ts) {
               D[RP * NT] = D[RP * NT] + pN * at;
               const cplx<float> r = Rr[RP * NT] - gN * at;
               Rr[RP * NT] = r;
@@ -618,7 +679,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
             }
           }
           ++it;
-          block_sum_df<NT>(rz_loc, slots + W, [&](float hi, float lo) {
+          sum_f(rz_loc, slots + W, [&](float hi, float lo) {
             const float rz_new = hi + lo;
             if (!isfinite(rz_new)) {
               sc.state = 2;
@@ -637,9 +698,9 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
 #pragma unroll
             for (int q = 0; q < RP; ++q) {
               const int o = q * NT + t;
-              p[q] = Rr[o] * dinv(g.mode(SL::b(q), SL::s(q))) + p[q] * beta;
+              p[q] = Rr[o] * dinv(gm(g.mode(SL::b(q), SL::s(q)))) + p[q] * beta;
             }
-            if (t0) pN = Rr[RP * NT] * dN + pN * beta;
+            if (ts) pN = Rr[RP * NT] * dN + pN * beta;
           }
         }
         iters = it;
@@ -652,12 +713,12 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
       if (g.act) {
 #pragma unroll
         for (int q = 0; q < RP; ++q) {
-          const int m = g.mode(SL::b(q), SL::s(q));
+          const int m = gm(g.mode(SL::b(q), SL::s(q)));
           const cplx<float> d = D[q * NT + t];
           const cplx<df> xv = Xh[m];
           Xh[m] = mk(xv.x + df(d.x, 0.0f) * unscale, xv.y + df(d.y, 0.0f) * unscale);
         }
-        if (t0) {
+        if (ts) {
           const cplx<float> d = D[RP * NT];
           const cplx<df> xv = Xh[h];
           Xh[h] = mk(xv.x + df(d.x, 0.0f) * unscale, xv.y);
@@ -668,34 +729,30 @@ __device__ __forceinline__ void pcg_body(const PcgArgs& A, int first, void* ux) 
   }
   R.iters = iters;
   R.status = status;
-  if (t0) A.rec[id] = R;
+  if (ts) A.rec[id] = R;
 }
 
-template <int L, bool MIXED>
+template <int L, bool MIXED, int CL>
 __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
     k_pcg1d(const __grid_constant__ PcgArgs A, int first) {
-  pcg_body<L, MIXED>(A, first, A.ux);
+  pcg_body<L, MIXED, CL>(A, first, A.ux);
+  // a CTA's shared memory must outlive the partner's last read of it
+  if constexpr (CL > 1) cluster_sync();
 }
 
 }  // namespace pcg1d
 
-template <int L>
+template <int LG>
 cudaError_t pcg1d_launch(const PcgArgs& a, int first, int num, cudaStream_t s) {
+  constexpr int CL = LG > kSmemLog1d ? 2 : 1;
+  constexpr int L = LG - (CL - 1);          // points per CTA: 2^L
   using PL = f1::Plan<L>;
-  if (a.precision == SGN_PREC_MIXED) {
-    auto k = pcg1d::k_pcg1d<L, true>;
-    const size_t sm = pcg1d::SmemPcg<L>::mixed;
-    cudaError_t e = d1::set_smem(k, sm);
-    if (e) return e;
-    k<<<num, PL::NT, sm, s>>>(a, first);
-  } else {
-    auto k = pcg1d::k_pcg1d<L, false>;
-    const size_t sm = pcg1d::SmemPcg<L>::fp64;
-    cudaError_t e = d1::set_smem(k, sm);
-    if (e) return e;
-    k<<<num, PL::NT, sm, s>>>(a, first);
-  }
-  return cudaGetLastError();
+  const bool mixed = a.precision == SGN_PREC_MIXED;
+  auto k = mixed ? pcg1d::k_pcg1d<L, true, CL> : pcg1d::k_pcg1d<L, false, CL>;
+  const size_t sm = mixed ? pcg1d::SmemPcg<L>::mixed : pcg1d::SmemPcg<L>::fp64;
+  cudaError_t e = d1::set_smem(k, sm);
+  if (e) return e;
+  return d1::launch_clustered<CL>(k, num, PL::NT, sm, s, a, first);
 }
 
 }  // namespace sgn

@@ -6,7 +6,9 @@
 //   flux -(eta u^2)_x folded in), Q = u d_x - d^2, S = u s_x (reading R6);
 // and f_eta = -m, f_U = -g eta zeta_x + Phi'_x - h_x Psi, Psi = eta^2 Q/2 + eta m d + eta S
 // + m s.  Every pointwise step works on the thread's natural elements j = t + e NTA, so the
-// intermediate planes in `scratch` are written and read by the same thread.
+// intermediate planes in `scratch` are written and read by the same thread.  n = 16384 runs
+// on a cluster of two CTAs, each holding half of the points (sgn_fft1d.cuh's two-CTA
+// transforms).
 #pragma once
 #include <type_traits>
 
@@ -33,7 +35,8 @@ struct RhsArgs {
   int ux_given;           // 1: the first scratch plane already holds u_x (see rhs_body)
 };
 
-template <int L>
+// LG = log2 n (LG = 14: two-CTA clusters of the n = 8192 kernel)
+template <int LG>
 cudaError_t rhs1d_launch(const RhsArgs& a, int first, int num, cudaStream_t s);
 
 namespace rhs1d {
@@ -45,12 +48,17 @@ using f1::XBuf;
 // v <- D v for the two real fields packed in v (the thread's natural elements in and out):
 // forward transform, i k_m / n on every mode (Nyquist 0), inverse transform as
 // conj(F(conj .)).  Each thread touches only its own natural positions of X outside the
-// transforms, so no barrier is needed around them.
-template <typename T, int L>
-__device__ __forceinline__ void deriv_pair(const XBuf<T>& X, cplx<T> (&v)[Plan<L>::E], int t,
-                                           int bnat, bool act, T kn,
+// transforms, so no barrier is needed around them.  CL = 2: X holds rank r's points and,
+// after the split, its modes m = 2 k + r; XP is the partner's buffer.
+template <typename T, int L, int CL>
+__device__ __forceinline__ void deriv_pair(const XBuf<T>& X, const XBuf<T>& XP,
+                                           cplx<T> (&v)[Plan<L>::E], int t, int bnat,
+                                           bool act, unsigned rk, T kn,
                                            const cplx<T>* __restrict__ tw) {
   using PL = Plan<L>;
+  if constexpr (CL > 1) {
+    f1::cross<T, L, f1::kSplitFwd>(X, XP, v, t, bnat, act, rk, tw);
+  }
   if (act) {
 #pragma unroll
     for (int e = 0; e < PL::E; ++e) X.st(bnat ^ f1::swz_c(e * PL::NTA), v[e]);
@@ -60,14 +68,22 @@ __device__ __forceinline__ void deriv_pair(const XBuf<T>& X, cplx<T> (&v)[Plan<L
 #pragma unroll
     for (int e = 0; e < PL::E; ++e) {
       const int a = bnat ^ f1::swz_c(e * PL::NTA);
-      const T k = kn * from_int<T>(wave_index(t + e * PL::NTA, PL::n));
+      const int m = CL * (t + e * PL::NTA) + (int)rk;
+      const T k = kn * from_int<T>(wave_index(m, CL * PL::n));
       X.st(a, conj(mul_pi(X.ld(a)) * k));
     }
   }
   f1::fft_smem<T, L>(X, tw);
   if (act) {
 #pragma unroll
-    for (int e = 0; e < PL::E; ++e) v[e] = conj(X.ld(bnat ^ f1::swz_c(e * PL::NTA)));
+    for (int e = 0; e < PL::E; ++e) v[e] = X.ld(bnat ^ f1::swz_c(e * PL::NTA));
+  }
+  if constexpr (CL > 1) {
+    f1::cross<T, L, f1::kJoinConj>(X, XP, v, t, bnat, act, rk, tw);
+  }
+  if (act) {
+#pragma unroll
+    for (int e = 0; e < PL::E; ++e) v[e] = conj(v[e]);
   }
 }
 
@@ -75,30 +91,33 @@ __device__ __forceinline__ void deriv_pair(const XBuf<T>& X, cplx<T> (&v)[Plan<L
 // scratch plane (written by the solve that produced u, in the same precision), so the
 // derivative pairs are (eta u, zeta) -> (m, zeta_x), (s, d) -> (s_x, d_x) and Phi': six
 // transforms instead of eight.
-template <typename T, int L, bool UXG>
+template <typename T, int L, bool UXG, int CL>
 __device__ __forceinline__ void rhs_body(const RhsArgs& A, int first) {
   using PL = Plan<L>;
-  constexpr int n = PL::n, E = PL::E, NTA = PL::NTA;
+  constexpr int nl = PL::n, n = CL * nl, E = PL::E, NTA = PL::NTA;
   extern __shared__ __align__(16) unsigned char smem[];
   const int t = threadIdx.x;
-  const Inst1d I = A.insts[A.ids[first + blockIdx.x]];
+  const unsigned rk = CL > 1 ? cluster_rank() : 0u;
+  const Inst1d I = A.insts[A.ids[first + (CL > 1 ? (int)(blockIdx.x / CL) : (int)blockIdx.x)]];
+  const long long own = I.off + (long long)rk * nl;    // first point of this CTA
   const T kn = num<T>(2.0 * kPi / I.L / (double)n);
   const T third = num<T>(1.0 / 3.0);
   const T gT = num<T>(A.g);
-  const XBuf<T> X(smem, n);
+  const XBuf<T> X(smem, nl);
+  const XBuf<T> XP = CL > 1 ? XBuf<T>(peer(smem), nl) : X;
   const cplx<T>* tw = std::is_same<T, df>::value ? reinterpret_cast<const cplx<T>*>(A.twdf)
                                                  : reinterpret_cast<const cplx<T>*>(A.tw64);
   const int bnat = f1::swz(t);
   const bool act = !PL::kIdle || t < NTA;
-  const double* eta = A.eta + I.off;
-  const double* u = A.u + I.off;
-  const double* hh = A.h + I.off;
-  const double* hx = A.hx + I.off;
-  T* sd = reinterpret_cast<T*>(A.scratch + I.off);              // d = u_x
-  T* sm = reinterpret_cast<T*>(A.scratch + A.P + I.off);        // m = (eta u)_x
-  T* szx = reinterpret_cast<T*>(A.scratch + 2 * A.P + I.off);   // zeta_x
-  T* ssx = reinterpret_cast<T*>(A.scratch + 3 * A.P + I.off);   // s_x
-  T* spsi = reinterpret_cast<T*>(A.scratch + 4 * A.P + I.off);  // Psi
+  const double* eta = A.eta + own;
+  const double* u = A.u + own;
+  const double* hh = A.h + own;
+  const double* hx = A.hx + own;
+  T* sd = reinterpret_cast<T*>(A.scratch + own);              // d = u_x
+  T* sm = reinterpret_cast<T*>(A.scratch + A.P + own);        // m = (eta u)_x
+  T* szx = reinterpret_cast<T*>(A.scratch + 2 * A.P + own);   // zeta_x
+  T* ssx = reinterpret_cast<T*>(A.scratch + 3 * A.P + own);   // s_x
+  T* spsi = reinterpret_cast<T*>(A.scratch + 4 * A.P + own);  // Psi
   cplx<T> v[E];
   if constexpr (UXG) {
     if (act) {
@@ -109,7 +128,7 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& A, int first) {
         v[e] = mk(ej * num<T>(u[j]), ej - num<T>(hh[j]));
       }
     }
-    deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);
+    deriv_pair<T, L, CL>(X, XP, v, t, bnat, act, rk, kn, tw);
     if (act) {
 #pragma unroll
       for (int e = 0; e < E; ++e) {
@@ -119,7 +138,7 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& A, int first) {
         v[e] = mk(num<T>(hx[j]) * num<T>(u[j]), sd[j]);
       }
     }
-    deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);   // v = (s_x, d_x)
+    deriv_pair<T, L, CL>(X, XP, v, t, bnat, act, rk, kn, tw);   // v = (s_x, d_x)
   } else {
     if (act) {
 #pragma unroll
@@ -129,7 +148,7 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& A, int first) {
         v[e] = mk(uj, num<T>(eta[j]) * uj);
       }
     }
-    deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);
+    deriv_pair<T, L, CL>(X, XP, v, t, bnat, act, rk, kn, tw);
     if (act) {
 #pragma unroll
       for (int e = 0; e < E; ++e) {
@@ -139,7 +158,7 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& A, int first) {
         v[e] = mk(num<T>(eta[j]) - num<T>(hh[j]), num<T>(hx[j]) * num<T>(u[j]));
       }
     }
-    deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);
+    deriv_pair<T, L, CL>(X, XP, v, t, bnat, act, rk, kn, tw);
     if (act) {
 #pragma unroll
       for (int e = 0; e < E; ++e) {
@@ -149,7 +168,7 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& A, int first) {
         v[e] = mk(sd[j], from_int<T>(0));
       }
     }
-    deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);   // v.x = d_x
+    deriv_pair<T, L, CL>(X, XP, v, t, bnat, act, rk, kn, tw);   // v.x = d_x
   }
   if (act) {
 #pragma unroll
@@ -168,39 +187,43 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& A, int first) {
       v[e] = mk(Phi, from_int<T>(0));
     }
   }
-  deriv_pair<T, L>(X, v, t, bnat, act, kn, tw);
+  deriv_pair<T, L, CL>(X, XP, v, t, bnat, act, rk, kn, tw);
   if (act) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int j = t + e * NTA;
-      A.f_eta[I.off + j] = -to_f64(sm[j]);
+      A.f_eta[own + j] = -to_f64(sm[j]);
       const T fU = v[e].x - gT * num<T>(eta[j]) * szx[j] - num<T>(hx[j]) * spsi[j];
-      A.f_U[I.off + j] = to_f64(fU);
+      A.f_U[own + j] = to_f64(fU);
     }
   }
 }
 
-template <typename T, int L, bool UXG>
+template <typename T, int L, bool UXG, int CL>
 __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
     k_rhs1d(const __grid_constant__ RhsArgs A, int first) {
-  rhs_body<T, L, UXG>(A, first);
+  rhs_body<T, L, UXG, CL>(A, first);
+  // a CTA's shared memory must outlive the partner's last read of it
+  if constexpr (CL > 1) cluster_sync();
 }
 
 }  // namespace rhs1d
 
-template <int L>
+template <int LG>
 cudaError_t rhs1d_launch(const RhsArgs& a, int first, int num, cudaStream_t s) {
+  constexpr int CL = LG > kSmemLog1d ? 2 : 1;
+  constexpr int L = LG - (CL - 1);          // points per CTA: 2^L
   using PL = f1::Plan<L>;
   const size_t sm = (size_t)16 << L;
   auto go = [&](auto k) -> cudaError_t {
     cudaError_t e = d1::set_smem(k, sm);
     if (e) return e;
-    k<<<num, PL::NT, sm, s>>>(a, first);
-    return cudaGetLastError();
+    return d1::launch_clustered<CL>(k, num, PL::NT, sm, s, a, first);
   };
   if (a.precision == SGN_PREC_MIXED)
-    return a.ux_given ? go(rhs1d::k_rhs1d<df, L, true>) : go(rhs1d::k_rhs1d<df, L, false>);
-  return a.ux_given ? go(rhs1d::k_rhs1d<double, L, true>) : go(rhs1d::k_rhs1d<double, L, false>);
+    return a.ux_given ? go(rhs1d::k_rhs1d<df, L, true, CL>) : go(rhs1d::k_rhs1d<df, L, false, CL>);
+  return a.ux_given ? go(rhs1d::k_rhs1d<double, L, true, CL>)
+                    : go(rhs1d::k_rhs1d<double, L, false, CL>);
 }
 
 }  // namespace sgn

@@ -372,8 +372,8 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
       return fail(ctx, SGN_ERR_INVALID_ARG, "grid fields");
     if (dim == 1 && g.ny != 1) return fail(ctx, SGN_ERR_INVALID_ARG, "1d grid needs ny = 1");
     const int lx = ilog2_exact(g.nx);
-    if (dim == 1 && (lx < 3 || lx > 13))
-      return fail(ctx, SGN_ERR_UNSUPPORTED_SIZE, "1d nx must be a power of two in [8, 8192]");
+    if (dim == 1 && (lx < 3 || lx > sgn::kMaxLog1d))
+      return fail(ctx, SGN_ERR_UNSUPPORTED_SIZE, "1d nx must be a power of two in [8, 16384]");
     if (dim == 2) {
       const int ly = ilog2_exact(g.ny);
       if (lx < 3 || ly < 3 || lx > 10 || ly > 10)
@@ -407,7 +407,7 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
     L.h_inst = new Inst1d[count];
     long long ws = 0;
     std::vector<int> ids;
-    for (int l = 3; l <= 13; ++l) {
+    for (int l = 3; l <= sgn::kMaxLog1d; ++l) {
       L.class_begin[l] = (int)ids.size();
       for (int i = 0; i < count; ++i)
         if (ilog2_exact(grids[i].nx) == l) ids.push_back(i);
@@ -423,6 +423,12 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
       ws += (long long)sgn::kWsVectors * (I.n / 2 + 1);
     }
     L.ws_cplx = ws;
+    const int nbig = L.class_end[sgn::kMaxLog1d] - L.class_begin[sgn::kMaxLog1d];
+    if (nbig > 0 &&
+        cudaMalloc(&L.big, sizeof(double) * 2 * ((size_t)nbig << sgn::kMaxLog1d)) != cudaSuccess) {
+      cudaGetLastError();
+      return cleanup(SGN_ERR_NOMEM, "layout allocation");
+    }
     if (cudaMalloc(&L.d_inst, sizeof(Inst1d) * count) != cudaSuccess ||
         cudaMalloc(&L.d_ids, sizeof(int) * count) != cudaSuccess ||
         cudaMalloc(&lay->ws, sizeof(double) * 2 * ws) != cudaSuccess ||
@@ -441,7 +447,7 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
       return cleanup(SGN_ERR_CUDA, "layout upload");
     }
     int ncls = 0;
-    for (int l = 3; l <= 13; ++l) ncls += L.class_end[l] > L.class_begin[l];
+    for (int l = 3; l <= sgn::kMaxLog1d; ++l) ncls += L.class_end[l] > L.class_begin[l];
     if (ncls > 1) {
       if (cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming) != cudaSuccess)
         return cleanup(SGN_ERR_CUDA, "layout events");
@@ -488,6 +494,7 @@ extern "C" void sgn_layout_destroy(sgn_layout* lay) {
   }
   if (lay->l1.fork) cudaEventDestroy(lay->l1.fork);
   cudaFree(lay->l1.d_inst);
+  cudaFree(lay->l1.big);
   cudaFree(lay->l1.d_ids);
   delete[] lay->l1.h_inst;
   sgn::layout2d_destroy(lay->l2);
@@ -813,7 +820,7 @@ sgn_status lincomb(sgn_state* st, double* out, Terms xs, Terms fs, int component
   if (st->lay->dim == 1) {
     const sgn::Layout1d& L = st->lay->l1;
     int maxn = 8;
-    for (int l = 3; l <= 13; ++l)
+    for (int l = 3; l <= sgn::kMaxLog1d; ++l)
       if (L.class_end[l] > L.class_begin[l]) maxn = 1 << l;
     LinJobs J{};
     J.j[0] = LinJob{out, lc, components};

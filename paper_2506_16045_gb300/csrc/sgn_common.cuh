@@ -432,4 +432,20 @@ __device__ __forceinline__ double block_min(double v, double* scratch) {
   return -block_max<NT>(-v, scratch);
 }
 
+// -------------------------------------------------------------------------------------
+// Thread-block clusters: a barrier over every thread of the cluster (release/acquire, so
+// shared-memory writes before it are visible to the partner CTA after it), the CTA's rank,
+// and the partner CTA's copy of a shared-memory object in a cluster of two.
+// -------------------------------------------------------------------------------------
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+               ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank() { return __clusterRelativeBlockRank(); }
+template <typename P>
+__device__ __forceinline__ P* peer(P* p) {
+  return static_cast<P*>(__cluster_map_shared_rank(static_cast<const void*>(p),
+                                                   __clusterRelativeBlockRank() ^ 1u));
+}
+
 }  // namespace sgn

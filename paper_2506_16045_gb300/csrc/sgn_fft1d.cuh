@@ -385,7 +385,9 @@ __device__ __forceinline__ void read_natural(const XBuf<T>& X, cplx<T> (&v)[Plan
   for (int e = 0; e < PL::E; ++e) v[e] = X.ld(bnat ^ swz_c(e * PL::NTA));
 }
 
-// Per-thread geometry of the layouts.
+// Per-thread geometry of the layouts.  `odd` selects the pairing of the odd-mode half of a
+// two-CTA transform (see the cluster section below): butterflies t and 2 NTA - 1 - t, whose
+// outputs k and N - 1 - k (N = 2^L) are the local indices of the global mirror pair there.
 template <int L>
 struct Geo {
   using PL = Plan<L>;
@@ -395,9 +397,9 @@ struct Geo {
   int bnat;            // swz(t)
   int bp0, bp1;        // swz(i_0), swz(i_1): paired reads
   int bw0, bw1;        // swz(i_0 RP), swz(i_1 RP): paired writes
-  __device__ __forceinline__ explicit Geo(int tt) : t(tt) {
+  __device__ __forceinline__ explicit Geo(int tt, bool odd = false) : t(tt) {
     act = !PL::kIdle || t < PL::NTA;
-    i1 = (t == 0) ? PL::NTA : 2 * PL::NTA - t;
+    i1 = odd ? 2 * PL::NTA - 1 - t : ((t == 0) ? PL::NTA : 2 * PL::NTA - t);
     bnat = swz(t);
     bp0 = bnat;
     bp1 = swz(i1);
@@ -493,7 +495,9 @@ __device__ __forceinline__ void fft_inv(const XBuf<T>& X, cplx<T> (&v)[Plan<L>::
 // ---------------------------------------------------------------------------------------
 // Half-spectrum slots of the paired layout.  Slot (b, s), s < HS, is mode i_b + s 2 NTA
 // (all below n/2); thread 0 also owns the Nyquist mode n/2 in register HS.  The mirror
-// n - m of a slot sits in register mirror(b, s).
+// n - m of a slot sits in register mirror(b, s).  `t0` selects thread 0's pairing; the
+// odd half of a two-CTA transform passes false on every thread (its pairing has no
+// self-paired butterfly).
 // ---------------------------------------------------------------------------------------
 template <int L, typename V>
 __device__ __forceinline__ V mirror_get(const V (&v)[Plan<L>::E], bool t0, int b, int s) {
@@ -592,6 +596,86 @@ __device__ __noinline__ void fft_smem(const XBuf<T> X, const cplx<T>* __restrict
     if constexpr (SP::uses(2)) if (lr == 2) smem_stage<T, L, 2>(X, t, bnat, lp, tw);
     if constexpr (SP::uses(1)) if (lr == 1) smem_stage<T, L, 1>(X, t, bnat, lp, tw);
     lp += lr;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Two-CTA transforms: an instance of n = 2 N points (N = 2^L) on a thread-block cluster of
+// two CTAs.  Rank r holds the real-space points [r N, r N + N) and the spectral modes
+// m = 2 k + r (k < N) at local index k: one radix-2 stage across the pair plus a local
+// length-N transform on each CTA.
+//   forward (decimation in frequency): y_r[j] = (x[j] + (-1)^r x[j + N]) w^{r j}, then
+//     Y_r = F_N(y_r), so Y_r[k] = X[2 k + r] (w = e^{-2 pi i / n});
+//   after a forward transform that computes an inverse as conj(F(conj X)):
+//     u_r = F_N(conj X_r), conj(x)[j] = u_0[j] + w^j u_1[j], conj(x)[j + N] = u_0 - w^j u_1;
+//   after a true inverse transform: z_r = F_N^{-1}(X_r), x[j] = z_0 + w^{-j} z_1,
+//     x[j + N] = z_0 - w^{-j} z_1.
+// The global mirror n - m of mode m = 2 k + r has local index N - k (mod N) on rank 0 (the
+// ordinary paired layout) and N - 1 - k on rank 1 (Geo's odd pairing).  The exchange runs
+// through distributed shared memory: each CTA publishes its natural elements in its own
+// exchange buffer, the pair meets at a cluster barrier, each reads the partner's elements
+// at the same positions, and a second barrier ends the reads before either buffer is
+// written again.
+// ---------------------------------------------------------------------------------------
+// e^{-+2 pi i j / 2^LG} in number type T (float32 from sincospif, else from the table)
+template <typename T, int LG>
+__device__ __forceinline__ cplx<T> xtw(int j, bool inv, const cplx<T>* __restrict__ tw) {
+  if constexpr (std::is_same<T, float>::value) {
+    return twiddle_f32(j, LG, inv);
+  } else {
+    const cplx<T> w = tw[j << (kTwiddleLog2 - LG)];
+    return inv ? conj(w) : w;
+  }
+}
+
+enum CrossKind { kSplitFwd = 0, kJoinConj = 1, kJoinInv = 2 };
+
+// The cross-CTA stage on the thread's natural elements v[e] (local j = t + e NTA), through
+// the exchange buffers X (own) and XP (partner).  All threads of both CTAs call it.
+template <typename T, int L, int KIND>
+__device__ __forceinline__ void cross(const XBuf<T>& X, const XBuf<T>& XP,
+                                      cplx<T> (&v)[Plan<L>::E], int t, int bnat, bool act,
+                                      unsigned r, const cplx<T>* __restrict__ tw) {
+  using PL = Plan<L>;
+  if (act) {
+#pragma unroll
+    for (int e = 0; e < PL::E; ++e) {
+      cplx<T> a = v[e];
+      if (KIND != kSplitFwd && r)
+        a = cmul(a, xtw<T, L + 1>(t + e * PL::NTA, KIND == kJoinInv, tw));
+      v[e] = a;
+      X.st(bnat ^ swz_c(e * PL::NTA), a);
+    }
+  }
+  cluster_sync();
+  if (act) {
+#pragma unroll
+    for (int e = 0; e < PL::E; ++e) {
+      const cplx<T> b = XP.ld(bnat ^ swz_c(e * PL::NTA));
+      if (!r) {
+        v[e] = v[e] + b;
+      } else if (KIND == kSplitFwd) {
+        v[e] = cmul(b - v[e], xtw<T, L + 1>(t + e * PL::NTA, false, tw));
+      } else {
+        v[e] = b - v[e];
+      }
+    }
+  }
+  cluster_sync();
+}
+
+// The same on the natural elements held in X (the state around fft_smem).
+template <typename T, int L, int KIND>
+__device__ __forceinline__ void cross_smem(const XBuf<T>& X, const XBuf<T>& XP, int t,
+                                           int bnat, bool act, unsigned r,
+                                           const cplx<T>* __restrict__ tw) {
+  using PL = Plan<L>;
+  cplx<T> v[PL::E];
+  if (act) read_natural<T, L>(X, v, bnat);
+  cross<T, L, KIND>(X, XP, v, t, bnat, act, r, tw);
+  if (act) {
+#pragma unroll
+    for (int e = 0; e < PL::E; ++e) X.st(bnat ^ swz_c(e * PL::NTA), v[e]);
   }
 }
 

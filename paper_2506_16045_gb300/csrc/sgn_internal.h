@@ -37,6 +37,8 @@ struct SolveRec {
 };
 
 constexpr int kWsVectors = 6;          // half-spectrum vectors per instance in the workspace
+constexpr int kMaxLog1d = 14;          // 1d n <= 16384 (n = 16384: two-CTA clusters)
+constexpr int kSmemLog1d = 13;         // largest 1d n whose float64 transform fits in one CTA
 
 struct Layout1d {
   int count = 0;
@@ -47,6 +49,9 @@ struct Layout1d {
   int* d_ids = nullptr;                // instance ids grouped by size class
   int class_begin[16] = {0};           // per log2n: [begin, end) into ids
   int class_end[16] = {0};
+  // float64 transform buffers (n complex doubles per instance) of the cta_fft kernels for
+  // the instances above kSmemLog1d, indexed by position in their size class
+  void* big = nullptr;
   // side streams and events for running size classes concurrently (null: one stream)
   cudaStream_t side[16] = {nullptr};
   cudaEvent_t fork = nullptr;

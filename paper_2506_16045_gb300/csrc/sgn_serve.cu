@@ -98,7 +98,8 @@ namespace {
 size_t footprint_of(int d, long long N) {
   const size_t io = (size_t)(2 + 3 * d) * 8 * N;          // eta, h, u/b, U, gradh
   const size_t work = d == 1 ? (size_t)260 * N : (size_t)760 * N;
-  return io + work + (1 << 16);
+  const size_t big = (d == 1 && N > 8192) ? (size_t)16 * N : 0;   // global transform buffer
+  return io + work + big + (1 << 16);
 }
 
 void free_req_work(Req* r) {
@@ -432,7 +433,7 @@ extern "C" sgn_status sgn_batch_submit(sgn_server* S, const sgn_request* q, uint
   const sgn_grid& g = q->grid;
   const int d = g.dim;
   if (d == 1) {
-    if (g.ny != 1 || !pow2_in(g.nx, 8, 8192)) return SGN_ERR_UNSUPPORTED_SIZE;
+    if (g.ny != 1 || !pow2_in(g.nx, 8, 16384)) return SGN_ERR_UNSUPPORTED_SIZE;
   } else if (d == 2) {
     if (!pow2_in(g.nx, 8, 1024) || !pow2_in(g.ny, 8, 1024)) return SGN_ERR_UNSUPPORTED_SIZE;
   } else {
