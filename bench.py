@@ -488,7 +488,7 @@ def bench_serving(sgn, ctx, torch, nreq=120, rate=200.0, seed=16045, baseline_sa
         H, R = rng.uniform(0.1, 0.6), rng.uniform(1.0, 5.0)
         a = rng.uniform(0.05, 0.3)
         if dim == 1:
-            n, L = 2 ** int(rng.integers(10, 14)), 200.0
+            n, L = 2 ** int(rng.integers(10, 15)), 200.0
             x = I.grid_1d(n, L)
             xb = rng.uniform(0.3, 0.7) * L
             h = 1.0 - H * np.exp(-((x - xb) ** 2) / R ** 2)
@@ -497,7 +497,7 @@ def bench_serving(sgn, ctx, torch, nreq=120, rate=200.0, seed=16045, baseline_sa
             grid = sgn.Grid(1, n, L)
             pts = n
         else:
-            n, L = 2 ** int(rng.integers(7, 10)), 80.0
+            n, L = 2 ** int(rng.integers(7, 11)), 80.0
             X, Y = I.grid_2d(n, n, L, L)
             xb, yb = rng.uniform(0.3, 0.7, 2) * L
             h = I.gaussian_bump_2d(X, Y, L, L, H, R, xb, yb)
@@ -566,7 +566,7 @@ def bench_serving(sgn, ctx, torch, nreq=120, rate=200.0, seed=16045, baseline_sa
         tsum += time.perf_counter() - ts
         wsum += pts * max(nsteps, 1)
     return {"workload": f"Poisson {rate:.0f}/s, {nreq} requests (seed {seed}): 50% RK4 runs "
-                        "(5-30 steps) / 50% solves, 50% 1d n in 2^10..2^13 / 50% 2d 2^7..2^9 "
+                        "(5-30 steps) / 50% solves, 50% 1d n in 2^10..2^14 / 50% 2d 2^7..2^10 "
                         "per side, Gaussian bumps, mixed precision, rtol 1e-10",
             "all_ok": ok, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)),

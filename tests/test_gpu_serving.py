@@ -77,8 +77,9 @@ def test_mixed_stream_results_equal_alone(S):
         assert st == 0
         tickets.append(t)
         spec[t] = ("rk4", c, k)
-    # 1d solves (Eq:Testproblem) and a multistep run, submitted while the first wave runs
-    for n in (256, 1024):
+    # 1d solves (Eq:Testproblem; n = 16384 on two-CTA clusters) and a multistep run,
+    # submitted while the first wave runs
+    for n in (256, 1024, 16384):
         _, h, eta, b = I.testproblem_1d(n, 1.0, 1.0)
         st, t = srv.submit(sgn.REQ_SOLVE, sgn.Grid(1, n, 1.0), dev(eta), dev(b), dev(h),
                            rtol=1e-12, prec=prec, host=False)
@@ -97,6 +98,13 @@ def test_mixed_stream_results_equal_alone(S):
                        scheme=sgn.SCHEME_RK4, dt=c.dt, nsteps=steps[4], rtol=rtol, prec=prec)
     tickets.append(t)
     spec[t] = ("rk4", c, steps[4])
+    c = I.ensemble_1d(count=3, seed=11, kmin=13, kmax=14)[2]
+    assert c.n == 16384
+    st, t = srv.submit(sgn.REQ_RUN, sgn.Grid(1, c.n, c.L, g=c.g), dev(c.eta), dev(c.u), dev(c.h),
+                       scheme=sgn.SCHEME_RK4, dt=c.dt, nsteps=4, rtol=rtol, prec=prec)
+    assert st == 0
+    tickets.append(t)
+    spec[t] = ("rk4", c, 4)
     res = wait(srv, tickets)
     for t in tickets:
         r = res[t]
