@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the shelf/2d/serving sections after the headline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--only-config", choices=["shelf_1d", "bump_2d", "serving"],
+    ap.add_argument("--only-config", choices=["shelf_1d", "bump_2d", "serving", "robustness"],
                     help="run only this extra configuration and print its result as one JSON "
                          "line (for profiling one workload; not the headline)")
     return ap.parse_args()
@@ -400,7 +400,7 @@ def gpu_arm(args, world, rank, local, pg):
         E.st.close()
         extra = {}
         for name, fn in (("shelf_1d", bench_shelf), ("bump_2d", bench_2d),
-                         ("serving", bench_serving)):
+                         ("serving", bench_serving), ("robustness", bench_robustness)):
             try:
                 extra[name] = fn(sgn, ctx, torch)
             except Exception as exc:                          # reported, never silent
@@ -473,6 +473,91 @@ def bench_shelf(sgn, ctx, torch, steps=40):
         res[name] = c.n * steps / (time.perf_counter() - t0)
         st.close()
     return {"workload": "1d shelf N=4096 L=200, 40 steps after start-up", "unit": UNIT, **res}
+
+
+def bench_robustness(sgn, ctx, torch, reps=5):
+    """The PCG robustness suite of §6.2-§6.3 on the GPU: solve clock time against n for
+    Eq:Testproblem (eta0 = h0 = 1, rtol 1e-12; the paper's clock-time-versus-n figure),
+    iterations over the eta0 / h0 sweeps, optimal against replacement coefficients on the
+    square-wave depth, and the 2d elliptical bump at three aspect ratios."""
+    import numpy as np
+
+    from paper_2506_16045_gb300 import inputs as I
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a).ravel(), dtype=torch.float64,
+                                    device="cuda")
+
+    def grad_dev(lay, h, comps):
+        gh = torch.zeros(comps * h.size, dtype=torch.float64, device="cuda")
+        sgn.spectral_grad(lay, dev(h), gh)
+        return gh
+
+    def timed(lay, eta, gh, b, npts, rtol, prec, P=None):
+        x = torch.zeros(npts, dtype=torch.float64, device="cuda")
+        info = sgn.pcg(lay, eta, gh, b, x, rtol=rtol, maxit=20000, prec=prec, P=P)[0]
+        ts = []
+        for _ in range(reps):
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sgn.pcg(lay, eta, gh, b, x, rtol=rtol, maxit=20000, prec=prec, P=P)
+            ts.append(time.perf_counter() - t0)
+        return float(np.median(ts)) * 1e3, info
+
+    clock = []
+    for k in range(5, 15):
+        n = 2 ** k
+        _, h, eta, b = I.testproblem_1d(n, 1.0, 1.0)
+        lay = sgn.Layout(ctx, [sgn.Grid(1, n, 1.0)])
+        gh = grad_dev(lay, h, 1)
+        row = {"n": n}
+        for name, prec in (("fp64", sgn.PREC_FP64), ("mixed", sgn.PREC_MIXED)):
+            ms, info = timed(lay, dev(eta), gh, dev(b), n, 1e-12 if name == "fp64" else 1e-11,
+                             prec)
+            row[f"ms_{name}"] = round(ms, 4)
+            row[f"iters_{name}"] = info["iters"]
+            row[f"ns_per_nlog2n_{name}"] = round(1e6 * ms / (n * k), 3)
+        lay.close()
+        clock.append(row)
+    sweep = []
+    n = 4096
+    lay = sgn.Layout(ctx, [sgn.Grid(1, n, 1.0)])
+    for eta0, hvar in ((0.5, 1.0), (1.0, 1.0), (4.0, 1.0), (16.0, 1.0), (1.0, 0.5), (1.0, 2.0),
+                       (1.0, 4.0)):
+        _, h, eta, b = I.testproblem_1d(n, eta0, hvar)
+        gh = grad_dev(lay, h, 1)
+        P = sgn.precond_coeffs(lay, dev(eta), gh)
+        ms, info = timed(lay, dev(eta), gh, dev(b), n, 1e-12, sgn.PREC_FP64)
+        sweep.append({"eta0": eta0, "h0": hvar, "kappa_ub": round(P[0]["kappa_ub"], 1),
+                      "iters": info["iters"], "ms": round(ms, 3)})
+    square = {}
+    lay512 = sgn.Layout(ctx, [sgn.Grid(1, 512, 1.0)])
+    for eta0 in (0.25, 5.0):
+        _, h, eta, b = I.squarewave_1d(512, eta0)
+        gh = grad_dev(lay512, h, 1)
+        for name, kind in (("opt", sgn.COEF_OPT), ("replacement", sgn.COEF_REPLACEMENT)):
+            P = sgn.precond_coeffs(lay512, dev(eta), gh, kind=kind)
+            x = torch.zeros(512, dtype=torch.float64, device="cuda")
+            info = sgn.pcg(lay512, dev(eta), gh, dev(b), x, rtol=1e-10, maxit=5000, P=P)[0]
+            square[f"eta0={eta0} {name}"] = {"sigma": round(P[0]["sigma"], 5),
+                                             "iters": info["iters"]}
+    bump = []
+    n = 256
+    lay2 = sgn.Layout(ctx, [sgn.Grid(2, n, 1.0, ny=n, Ly=1.0)])
+    for a, bb in ((1.0, 1.0), (1.0, 20.0), (1.0, 40.0)):
+        _, _, h, eta, rhs = I.elliptical_bump_2d(n, a, bb)
+        gh = grad_dev(lay2, h, 2)
+        P = sgn.precond_coeffs(lay2, dev(eta), gh)
+        ms, info = timed(lay2, dev(eta), gh, dev(rhs), 2 * n * n, 1e-10, sgn.PREC_FP64)
+        msm, infom = timed(lay2, dev(eta), gh, dev(rhs), 2 * n * n, 1e-10, sgn.PREC_MIXED)
+        bump.append({"a": a, "b": bb, "n": f"{n}^2", "kappa_ub": round(P[0]["kappa_ub"], 1),
+                     "iters_fp64": info["iters"], "ms_fp64": round(ms, 3),
+                     "iters_mixed": infom["iters"], "ms_mixed": round(msm, 3)})
+    return {"workload": "Eq:Testproblem (eta0 = h0 = 1) solve clock time for n = 2^5..2^14 "
+                        "(fp64 rtol 1e-12, mixed rtol 1e-11; one instance per call, median of "
+                        f"{reps}); eta0 / h0 sweep at n = 4096; square-wave depth, optimal vs "
+                        "replacement coefficients at n = 512; 2d elliptical bump at 256^2",
+            "clock_vs_n": clock, "sweep_n4096": sweep, "square_wave_n512": square,
+            "elliptical_bump_2d": bump}
 
 
 def bench_serving(sgn, ctx, torch, nreq=120, rate=200.0, seed=16045, baseline_sample=8):
@@ -589,7 +674,8 @@ def main():
 
         from paper_2506_16045_gb300 import sgn
         ctx = sgn.Context(0)
-        fn = {"shelf_1d": bench_shelf, "bump_2d": bench_2d, "serving": bench_serving}
+        fn = {"shelf_1d": bench_shelf, "bump_2d": bench_2d, "serving": bench_serving,
+              "robustness": bench_robustness}
         print(json.dumps({args.only_config: fn[args.only_config](sgn, ctx, torch)}))
         ctx.close()
         return

@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
 
 template <int LG>
 cudaError_t rhs1d_launch(const RhsArgs& a, int first, int num, cudaStream_t s) {
-  constexpr int CL = LG > kSmemLog1d ? 2 : 1;
+  constexpr int CL = LG >= kClusterLog1d ? 2 : 1;
   constexpr int L = LG - (CL - 1);          // points per CTA: 2^L
   using PL = f1::Plan<L>;
   const size_t sm = (size_t)16 << L;

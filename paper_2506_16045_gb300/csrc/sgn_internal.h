@@ -39,6 +39,7 @@ struct SolveRec {
 constexpr int kWsVectors = 6;          // half-spectrum vectors per instance in the workspace
 constexpr int kMaxLog1d = 14;          // 1d n <= 16384 (n = 16384: two-CTA clusters)
 constexpr int kSmemLog1d = 13;         // largest 1d n whose float64 transform fits in one CTA
+constexpr int kClusterLog1d = 14;      // smallest 1d log2 n solved on two-CTA clusters
 
 struct Layout1d {
   int count = 0;

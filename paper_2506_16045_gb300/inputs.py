@@ -106,6 +106,19 @@ def testproblem_1d(n: int, eta0: float, hvar: float, sigma: float = 1.0 / 20.0):
     return x, h, eta, b
 
 
+def squarewave_1d(n: int, eta0: float, hvar: float = 1.0, sigma: float = 1.0 / 20.0):
+    """The discontinuous depth of the coefficient comparison in §6.2: h as in
+    Eq:Testproblem1_var, eta = 0.1 where |h'(x)|^2 <= 0.2 and 0.1 eta0 elsewhere (h' the
+    analytic derivative of the Gaussian), b = cos(4 pi x).  Returns (x, h, eta, b)."""
+    x = grid_1d(n, 1.0)
+    g = np.exp(-((x - 0.5) ** 2) / sigma ** 2)
+    h = 1.0 + hvar * g
+    dh = -2.0 * hvar * (x - 0.5) / sigma ** 2 * g
+    eta = np.where(dh ** 2 <= 0.2, 0.1, 0.1 * eta0)
+    b = np.cos(4.0 * np.pi * x)
+    return x, h, eta, b
+
+
 def elliptical_bump_2d(n: int, a: float, b: float):
     """Eq:ellipticalbump on the unit torus, bump centred at the origin (minimum image)."""
     X, Y = grid_2d(n, n, 1.0, 1.0)

@@ -234,6 +234,51 @@ def test_pcg_error_monotone_and_within_cg_bound(eta0, hvar):
         assert O.g_error(x, ustar, Gd, b) <= bound * 1.01
 
 
+@pytest.mark.parametrize("eta0,hvar", [(1.0, 1.0), (4.0, 1.0), (1.0, 4.0)])
+def test_pcg_iterations_bounded_under_mesh_refinement(eta0, hvar):
+    """§6.2: the iterations grow with eta0 and h0 but stay bounded as n grows (the discrete
+    bound kappa(A^{-1}G) <= kappa_ub holds at every n): from n = 1024 to 16384 the count to
+    rtol 1e-12 changes by at most 2, and kappa_ub converges to its continuum value."""
+    its, kap = [], []
+    for n in (1024, 4096, 16384):
+        _, h, eta, b = I.testproblem_1d(n, eta0, hvar)
+        hx = O.deriv(h, 1.0)
+        _, it, ratio, c = O.solve_G(eta, hx, b, O.make_grid(1, n, 1.0, 1.0), rtol=1e-12,
+                                    maxit=5000)
+        assert ratio <= 1e-12
+        its.append(it), kap.append(c["kappa_ub"])
+    assert max(its) - min(its) <= 2, its
+    assert abs(kap[2] - kap[1]) <= 1e-3 * kap[2]
+    rho = (math.sqrt(kap[2]) - 1) / (math.sqrt(kap[2]) + 1)
+    assert its[2] <= math.log(1e-12 / 2) / math.log(rho)       # inside the CG bound's count
+
+
+def test_replacement_coefficients_lose_only_where_eta_is_small_at_steep_bottom():
+    """§6.2's comparison of sigma*, alpha* with the replacement coefficients on the square-wave
+    depth: when eta is small where |h_x| is large (eta0 < 1 here) sigma** exceeds sigma* and
+    PCG needs more iterations to epsilon < 1e-8 (def:discrete_Gerr); when the condition fails
+    (eta0 = 5) the two coefficient sets give the same iteration count."""
+    n = 256
+    grid = O.make_grid(1, n, 1.0, 1.0)
+    counts = {}
+    for eta0 in (0.25, 5.0):
+        _, h, eta, b = I.squarewave_1d(n, eta0)
+        hx = O.deriv(h, 1.0)
+        Gd = O.dense_G_1d(eta, hx, 1.0)
+        ustar = np.linalg.solve(Gd, b)
+        for kind in ("opt", "replacement"):
+            c = O.precond_coeffs(eta, hx, kind)
+            _, _, _, hist = O.pcg(lambda v: O.apply_G(eta, hx, v, grid),
+                                  lambda v: O.apply_Ainv(v, c["sigma"], c["alpha"], grid),
+                                  b, None, 1e-15, 400, history=True)
+            eps = [O.g_error(u, ustar, Gd, b) for u in hist]
+            counts[(eta0, kind)] = (next(j for j, e in enumerate(eps) if e < 1e-8), c["sigma"])
+    (io, so), (ir, sr) = counts[(0.25, "opt")], counts[(0.25, "replacement")]
+    assert sr > 1.5 * so and ir >= io + 10, counts
+    (io, so), (ir, sr) = counts[(5.0, "opt")], counts[(5.0, "replacement")]
+    assert abs(ir - io) <= 1, counts
+
+
 def test_pcg_zero_rhs_and_exact_warm_start():
     n = 32
     _, h, eta, b = I.testproblem_1d(n, 1.0, 1.0)
