@@ -389,9 +389,11 @@ def rhs(eta, u, h, gradh, grid):
 # ======================================================================================
 
 class State:
-    """(eta, U, u) at time t plus the fixed bathymetry (h, grad h)."""
+    """(eta, U, u) at time t plus the fixed bathymetry (h, grad h), and an optional external
+    forcing: a callable t -> (S_eta, S_U) added to the right-hand side at every stage time
+    (the source term of Test 1 of §6.4)."""
 
-    def __init__(self, eta, U, u, h, gradh, grid, t=0.0):
+    def __init__(self, eta, U, u, h, gradh, grid, t=0.0, forcing=None):
         self.eta = np.array(eta, dtype=np.float64)
         self.U = np.array(U, dtype=np.float64)
         self.u = np.array(u, dtype=np.float64)
@@ -399,11 +401,12 @@ class State:
         self.gradh = gradh
         self.grid = grid
         self.t = t
+        self.forcing = forcing
         self.solves = 0
         self.iterations = 0
 
     def copy(self):
-        s = State(self.eta, self.U, self.u, self.h, self.gradh, self.grid, self.t)
+        s = State(self.eta, self.U, self.u, self.h, self.gradh, self.grid, self.t, self.forcing)
         s.solves, s.iterations = self.solves, self.iterations
         return s
 
@@ -418,6 +421,15 @@ def init_state(eta, u, h, grid):
     gradh = grad(h, L)
     U = apply_G(eta, gradh, u, grid)
     return State(eta, U, u, h, gradh, grid)
+
+
+def _rhs_t(st: State, eta, u, t):
+    """f(eta, u) plus the external forcing at time t (if any)."""
+    a, b = rhs(eta, u, st.h, st.gradh, st.grid)
+    if st.forcing is not None:
+        sa, sb = st.forcing(t)
+        a, b = a + sa, b + sb
+    return a, b
 
 
 def _solve(st: State, eta, U, x0, rtol, maxit):
@@ -438,7 +450,7 @@ def rk4_step(st: State, dt, rtol=1e-12, maxit=2000):
             eta_i = eta_n + dt * sum(RK4_A[i][j] * fe[j] for j in range(i))
             U_i = U_n + dt * sum(RK4_A[i][j] * fU[j] for j in range(i))
             u_i = _solve(st, eta_i, U_i, u_i, rtol, maxit)
-        a, b = rhs(eta_i, u_i, st.h, st.gradh, st.grid)
+        a, b = _rhs_t(st, eta_i, u_i, st.t + dt * sum(RK4_A[i]))
         fe.append(a)
         fU.append(b)
     st.eta = eta_n + dt * sum(RK4_B[j] * fe[j] for j in range(4))
@@ -459,11 +471,11 @@ def run_ab(st: State, order, dt, nsteps, rtol=1e-12):
     then G_{eta_{n+s}} u_{n+s} = U_{n+s}.  The first s-1 steps are RK4 (reading R9)."""
     s = order
     b = AB_B[s]
-    hist = [rhs(st.eta, st.u, st.h, st.gradh, st.grid)]
+    hist = [_rhs_t(st, st.eta, st.u, st.t)]
     done = 0
     while done < min(s - 1, nsteps):
         rk4_step(st, dt, rtol)
-        hist.append(rhs(st.eta, st.u, st.h, st.gradh, st.grid))
+        hist.append(_rhs_t(st, st.eta, st.u, st.t))
         done += 1
     while done < nsteps:
         fe = sum(b[j] * hist[j][0] for j in range(s))
@@ -473,7 +485,7 @@ def run_ab(st: State, order, dt, nsteps, rtol=1e-12):
         st.u = _solve(st, st.eta, st.U, st.u, rtol, 2000)
         st.t += dt
         done += 1
-        hist = hist[1:] + [rhs(st.eta, st.u, st.h, st.gradh, st.grid)]
+        hist = hist[1:] + [_rhs_t(st, st.eta, st.u, st.t)]
     return st
 
 
@@ -489,12 +501,12 @@ def run_sbdf2(st: State, dt, nsteps, rtol=1e-12, coef_scale=1.0):
     if nsteps <= 0:
         return st
     prev = (st.eta.copy(), st.U.copy(), st.u.copy())
-    f_prev = rhs(st.eta, st.u, st.h, st.gradh, grid)
+    f_prev = _rhs_t(st, st.eta, st.u, st.t)
     rk4_step(st, dt, rtol)
     done = 1
     while done < nsteps:
         eta0, U0, u0 = prev
-        f_cur = rhs(st.eta, st.u, st.h, st.gradh, grid)
+        f_cur = _rhs_t(st, st.eta, st.u, st.t)
         eta2 = (4.0 * st.eta - eta0 + 2.0 * dt * (2.0 * f_cur[0] - f_prev[0])) / 3.0
         U2 = (4.0 * st.U - U0 + 2.0 * dt * (2.0 * f_cur[1] - f_prev[1])) / 3.0
         res1 = apply_A(st.u, sigma, alpha, grid) - apply_G(st.eta, st.gradh, st.u, grid) + st.U
@@ -506,6 +518,38 @@ def run_sbdf2(st: State, dt, nsteps, rtol=1e-12, coef_scale=1.0):
         st.t += dt
         done += 1
     return st
+
+
+# ======================================================================================
+# Manufactured solution (Test 1 of §6.4)
+# ======================================================================================
+
+def manufactured_1d(x, t, omega=10.0):
+    """Test 1 of §6.4 on L = 1: h = 2 + sin 2 pi x, eta* = 2 + sin 2 pi x sin(omega t),
+    u* = cos 2 pi x cos(omega t).  Returns (h, eta*, u*, d eta*/dt, d u*/dt)."""
+    s, c = np.sin(2 * np.pi * x), np.cos(2 * np.pi * x)
+    h = 2.0 + s
+    eta = 2.0 + s * math.sin(omega * t)
+    u = c * math.cos(omega * t)
+    return h, eta, u, omega * s * math.cos(omega * t), -omega * c * math.sin(omega * t)
+
+
+def dGdt_1d(eta, eta_t, hx, u, u_t, L):
+    """d/dt (G_{eta(t),h} u(t)) with h fixed: Def:G (1d) differentiated by the product rule,
+    G_eta u_t + eta_t u - (eta^2 eta_t u_x)_x - (eta eta_t h_x u)_x + eta eta_t h_x u_x
+    + eta_t h_x^2 u."""
+    d = deriv(u, L)
+    return (apply_G_1d(eta, hx, u_t, L) + eta_t * u - deriv(eta ** 2 * eta_t * d, L)
+            - deriv(eta * eta_t * hx * u, L) + eta * eta_t * hx * d + eta_t * hx ** 2 * u)
+
+
+def manufactured_forcing_1d(x, t, L, g, omega=10.0):
+    """The source (S_eta, S_U) that makes (eta*, u*) solve the DAE form (Eq:DAE_DSWE) with
+    U* = G_{eta*,h} u*: S_eta = d eta*/dt - f_eta(eta*, u*), S_U = dU*/dt - f_U(eta*, u*)."""
+    h, eta, u, eta_t, u_t = manufactured_1d(x, t, omega)
+    hx = deriv(h, L)
+    fe, fU = rhs_1d(eta, u, h, hx, L, g)
+    return eta_t - fe, dGdt_1d(eta, eta_t, hx, u, u_t, L) - fU
 
 
 # ======================================================================================

@@ -188,6 +188,38 @@ def ensemble_1d(count=256, seed=2506, kmin=9, kmax=13, L=200.0, g=9.81,
     return out
 
 
+def manufactured_fields_1d(x, t, omega=10.0):
+    """Test 1 of §6.4 on L = 1: h = 2 + sin 2 pi x, eta* = 2 + sin 2 pi x sin(omega t),
+    u* = cos 2 pi x cos(omega t).  Returns (h, eta*, u*)."""
+    s, c = np.sin(2 * np.pi * x), np.cos(2 * np.pi * x)
+    return 2.0 + s, 2.0 + s * math.sin(omega * t), c * math.cos(omega * t)
+
+
+def manufactured_case(n=256, omega=10.0) -> Instance1d:
+    """The manufactured-solution run of §6.4 Test 1 at t = 0 (L = 1, g = 1, the paper's
+    non-dimensional gravity); dt is chosen by the caller."""
+    x = grid_1d(n, 1.0)
+    h, eta, u = manufactured_fields_1d(x, 0.0, omega)
+    return Instance1d(n, 1.0, 1.0, 0.0, h, eta, u, dict(omega=omega))
+
+
+def series_forcing_1d(spec: dict, x):
+    """Evaluates a forcing stored as a double Fourier series (entries [j, k, X, T, c] meaning
+    c X(2 pi j x / L) T(k omega t), for "eta" and "U") on the grid x, grouped by time
+    function: returns (phi_eta [K][n], phi_U [K][n], omega [K], theta [K]) with
+    S(x, t) = sum_k cos(omega_k t + theta_k) phi_k(x)  (sin a = cos(a - pi/2))."""
+    L, w = spec["L"], spec["omega"]
+    f = {"cos": np.cos, "sin": np.sin}
+    keys = sorted({(k, T) for part in ("eta", "U") for _, k, _, T, _ in spec[part]})
+    phi = {part: np.zeros((len(keys), x.size)) for part in ("eta", "U")}
+    for part in ("eta", "U"):
+        for j, k, X, T, c in spec[part]:
+            phi[part][keys.index((k, T))] += c * f[X](2 * np.pi * j * x / L)
+    omega = np.array([k * w for k, _ in keys])
+    theta = np.array([0.0 if T == "cos" else -np.pi / 2 for _, T in keys])
+    return phi["eta"], phi["U"], omega, theta
+
+
 def bump2d_case(n=512, L=80.0, a=0.2, x0=20.0, H=0.5, R=3.0, g=9.81, dt=0.02):
     """2d plane solitary wave (theta=0) approaching a Gaussian bump at the domain centre."""
     X, Y = grid_2d(n, n, L, L)

@@ -401,6 +401,62 @@ def test_planted_forcing_mistake_breaks_energy_pin(monkeypatch):
     assert abs(O.energy(st) - E0) / E0 > 1e-5
 
 
+def _manufactured_error(scheme, order, dt, n=64, t_final=0.5):
+    x = np.arange(n) / n
+    h, eta, u, _, _ = O.manufactured_1d(x, 0.0)
+    st = O.init_state(eta, u, h, O.make_grid(1, n, 1.0, 1.0))
+    st.forcing = lambda t: O.manufactured_forcing_1d(x, t, 1.0, 1.0)
+    steps = int(round(t_final / dt))
+    if scheme == "rk4":
+        O.run_rk4(st, dt, steps, 1e-13)
+    elif scheme == "ab":
+        O.run_ab(st, order, dt, steps, 1e-13)
+    else:
+        O.run_sbdf2(st, dt, steps, 1e-13)
+    _, e1, u1, _, _ = O.manufactured_1d(x, st.t)
+    return max(np.abs(st.eta - e1).max(), np.abs(st.u - u1).max())
+
+
+@pytest.mark.parametrize("scheme,order,dts,min_order", [
+    ("rk4", 0, (1 / 50, 1 / 100), 3.8), ("ab", 2, (1 / 200, 1 / 400), 1.9),
+    ("ab", 3, (1 / 200, 1 / 400), 2.7), ("ab", 4, (1 / 200, 1 / 400), 3.8),
+    ("sbdf2", 0, (1 / 800, 1 / 1600), 1.9)])
+def test_forced_schemes_converge_to_manufactured_solution(scheme, order, dts, min_order):
+    """Test 1 of §6.4: with the oracle's forcing (S_eta = eta*_t - f_eta, S_U = d/dt(G u*) -
+    f_U) every scheme converges to the closed-form (eta*, u*) at its order.  A slip in the
+    forcing, in d/dt G, or in a scheme's stage times leaves an O(1) error or drops the
+    order."""
+    e = [_manufactured_error(scheme, order, dt) for dt in dts]
+    assert e[1] < 5e-3
+    assert math.log2(e[0] / e[1]) >= min_order, e
+
+
+def test_manufactured_forcing_fixture_is_the_oracles():
+    """tests/golden/manufactured_forcing.json (written by make_manufactured_forcing.py from
+    the oracle) is the oracle's forcing: the stored series regenerates exactly and, evaluated
+    through the input module's grouping by time function, equals the oracle's forcing at
+    times between the fitting samples."""
+    import importlib.util
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    spec_ = importlib.util.spec_from_file_location(
+        "make_mf", os.path.join(here, "make_manufactured_forcing.py"))
+    mk = importlib.util.module_from_spec(spec_)
+    spec_.loader.exec_module(mk)
+    stored = json.load(open(os.path.join(here, "manufactured_forcing.json")))
+    for part, idx in (("eta", 0), ("U", 1)):
+        fresh = mk.series(lambda x, t: O.manufactured_forcing_1d(x, t, 1.0, 1.0, 10.0)[idx])
+        assert [e[:4] for e in fresh] == [e[:4] for e in stored[part]]
+        scale = max(abs(e[4]) for e in fresh)
+        assert max(abs(a[4] - b[4]) for a, b in zip(fresh, stored[part])) <= 1e-13 * scale
+    x = I.grid_1d(32, 1.0)
+    pe, pu, om, th = I.series_forcing_1d(stored, x)
+    for t in (0.03, 0.5, 0.91):
+        se, sU = O.manufactured_forcing_1d(x, t, 1.0, 1.0, 10.0)
+        w = np.cos(om * t + th)
+        assert np.abs(w @ pe - se).max() <= 1e-12 * np.abs(se).max()
+        assert np.abs(w @ pu - sU).max() <= 1e-12 * np.abs(sU).max()
+
+
 def test_2d_plane_wave_matches_1d_evolution():
     """A y-independent 2d solitary wave evolves like the 1d one (§6.5 sanity check)."""
     n, ny, L = 64, 4, 40.0
