@@ -176,7 +176,7 @@ __global__ void k_axpy1d(const Inst1d* __restrict__ insts, const double* __restr
   }
 }
 
-// SBDF2: res^ = (sigma + alpha k^2) u^ - (G u)^ + U^  (half spectrum, float64)
+// SBDF2: res^ = (sigma + alpha k^2) u^ - (G u - U)^  (half spectrum, float64)
 template <int NT, int MAXB>
 __global__ void __launch_bounds__(NT, 1) k_linimp_res1d(const Inst1d* __restrict__ insts,
                                                      const int* __restrict__ ids,
@@ -197,25 +197,25 @@ __global__ void __launch_bounds__(NT, 1) k_linimp_res1d(const Inst1d* __restrict
   const int n = I.n, h = n >> 1;
   const double sigma = A[id].sigma, alpha = A[id].alpha;
   const long long S = h + 1;
-  cplx<double>* Uh = ws + I.ws;
   cplx<double>* uh = ws + I.ws + S;
   cplx<double>* out = res + I.ws / kWsVectors;
-  for (int j = threadIdx.x; j < n; j += NT) buf[j] = mk(u_all[I.off + j], U_all[I.off + j]);
+  // u^ from a transform of u alone; U enters inside the matvec (w - U, so the matvec yields
+  // (G u - U)^).  Packed as u + i U, u^ would carry U's rounding (~eps ||U||), and U = G u
+  // can outweigh u by eta^3 k^2 / 3, which the right-hand side's third derivatives pass on.
+  for (int j = threadIdx.x; j < n; j += NT) buf[j] = mk(u_all[I.off + j], 0.0);
   __syncthreads();
   cta_fft<double, NT, MAXB>(buf, n, I.log2n, false, tw);
-  for (int m = threadIdx.x; m <= h; m += NT) {
-    cplx<double> z = buf[m], zc = conj(buf[(n - m) & (n - 1)]);
-    uh[m] = (z + zc) * 0.5;
-    Uh[m] = mul_mi(z - zc) * 0.5;
-  }
+  for (int m = threadIdx.x; m <= h; m += NT)
+    uh[m] = (m == 0 || m == h) ? mk(buf[m].x, 0.0) : buf[m];   // real modes of a real field
   __syncthreads();
   const Spec<double> sp = make_spec<double>(n, I.L, sigma, alpha);
   spectral_matvec<double, NT, MAXB>(buf, sp, I.log2n, [&](int m) { return uh[m]; },
-                                    CoefGlobal64{eta_all + I.off, hx_all + I.off}, nullptr, tw);
+                                    CoefGlobal64{eta_all + I.off, hx_all + I.off}, nullptr, tw,
+                                    U_all + I.off);
   for (int m = threadIdx.x; m <= h; m += NT) {
     double k = sp.k(m);
-    cplx<double> gu = gv_mode(buf, m, n, k);
-    out[m] = uh[m] * (sigma + alpha * k * k) - gu + Uh[m];
+    cplx<double> gu = gv_mode(buf, m, n, k);       // (G u - U)^_m
+    out[m] = uh[m] * (sigma + alpha * k * k) - gu;
   }
 }
 

@@ -123,10 +123,12 @@ __device__ __forceinline__ Spec<T> make_spec(int n, double L, double sigma, doub
 // the modes it read).  On return buf holds Y = FFT(w + i q); extract (G v)_m with gv_mode.
 // ---------------------------------------------------------------------------------------
 // Inverse FFT of Z (already in buf), pointwise coefficients, forward FFT.
+// With wsub set, w - wsub is transformed instead of w, so the result is (G v - wsub)^.
 template <typename T, int NT, int MAXB, typename Coef>
 __device__ __forceinline__ void matvec_core(cplx<T>* buf, int n, int log2n, const Coef& coef,
                                             double* __restrict__ vout,
-                                            const cplx<T>* __restrict__ tw) {
+                                            const cplx<T>* __restrict__ tw,
+                                            const double* __restrict__ wsub = nullptr) {
   cta_fft<T, NT, MAXB>(buf, n, log2n, true, tw);
   const T inv_n = num<T>(1.0 / (double)n);
   for (int j = threadIdx.x; j < n; j += NT) {
@@ -135,7 +137,9 @@ __device__ __forceinline__ void matvec_core(cplx<T>* buf, int n, int log2n, cons
     T c1, c2, c3;
     coef(j, c1, c2, c3);
     if (vout) vout[j] = to_f64(v);
-    buf[j] = mk(c1 * v + c2 * vx, c2 * v + c3 * vx);
+    T w = c1 * v + c2 * vx;
+    if (wsub) w = w - num<T>(wsub[j]);
+    buf[j] = mk(w, c2 * v + c3 * vx);
   }
   __syncthreads();
   cta_fft<T, NT, MAXB>(buf, n, log2n, false, tw);
@@ -144,7 +148,8 @@ __device__ __forceinline__ void matvec_core(cplx<T>* buf, int n, int log2n, cons
 template <typename T, int NT, int MAXB, typename Get, typename Coef>
 __device__ __forceinline__ void spectral_matvec(cplx<T>* buf, const Spec<T>& sp, int log2n,
                                                 Get get, Coef coef, double* __restrict__ vout,
-                                                const cplx<T>* __restrict__ tw) {
+                                                const cplx<T>* __restrict__ tw,
+                                                const double* __restrict__ wsub = nullptr) {
   const int n = sp.n, h = sp.h;
   const T one = from_int<T>(1);
   for (int m = threadIdx.x; m <= h; m += NT) {
@@ -156,7 +161,7 @@ __device__ __forceinline__ void spectral_matvec(cplx<T>* buf, const Spec<T>& sp,
     if (m > 0 && m < h) buf[n - m] = conj(v) * (one + k);
   }
   __syncthreads();
-  matvec_core<T, NT, MAXB>(buf, n, log2n, coef, vout, tw);
+  matvec_core<T, NT, MAXB>(buf, n, log2n, coef, vout, tw, wsub);
 }
 
 // (G v)_m = w_m - i k_m q_m = ((1 - k) Y_m + (1 + k) conj(Y_{n-m})) / 2
