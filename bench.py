@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the shelf/2d/serving sections after the headline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--only-config", choices=["shelf_1d", "bump_2d", "serving", "robustness"],
+    ap.add_argument("--only-config", choices=["shelf_1d", "bump_2d", "serving", "robustness",
+                                              "manufactured"],
                     help="run only this extra configuration and print its result as one JSON "
                          "line (for profiling one workload; not the headline)")
     return ap.parse_args()
@@ -400,7 +401,8 @@ def gpu_arm(args, world, rank, local, pg):
         E.st.close()
         extra = {}
         for name, fn in (("shelf_1d", bench_shelf), ("bump_2d", bench_2d),
-                         ("serving", bench_serving), ("robustness", bench_robustness)):
+                         ("serving", bench_serving), ("robustness", bench_robustness),
+                         ("manufactured", bench_manufactured)):
             try:
                 extra[name] = fn(sgn, ctx, torch)
             except Exception as exc:                          # reported, never silent
@@ -560,6 +562,63 @@ def bench_robustness(sgn, ctx, torch, reps=5):
             "elliptical_bump_2d": bump}
 
 
+def bench_manufactured(sgn, ctx, torch, n=256, t_final=1.0):
+    """Test 1 of §6.4: the forced SGN equations with the manufactured solution (h = 2 +
+    sin 2 pi x, eta* = 2 + sin 2 pi x sin 10t, u* = cos 2 pi x cos 10t, L = 1, g = 1) at
+    n = 256 to t = 1, every scheme at two step sizes (RK4 C = 0.2, 0.1; SBDF2 C = 0.05,
+    0.025, dt = C dx; Adams-Bashforth C = 0.1, 0.05, inside its smaller stability region):
+    L-infinity error against the closed form and clock time per run."""
+    import numpy as np
+
+    from paper_2506_16045_gb300 import inputs as I
+    spec = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests",
+                                       "golden", "manufactured_forcing.json")))
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a).ravel(), dtype=torch.float64,
+                                    device="cuda")
+    x = I.grid_1d(n, 1.0)
+    pe, pu, om, th = I.series_forcing_1d(spec, x)
+    pe, pu = dev(pe), dev(pu)
+    lay = sgn.Layout(ctx, [sgn.Grid(1, n, 1.0, g=1.0)])
+    runs = []
+    for name, order, Cs in (("rk4", 0, (0.2, 0.1)), ("ab2", 2, (0.1, 0.05)),
+                            ("ab3", 3, (0.1, 0.05)), ("ab4", 4, (0.1, 0.05)),
+                            ("sbdf2", 0, (0.05, 0.025))):
+        for C in Cs:
+            dt = C / n
+            steps = int(round(t_final / dt))
+            c = I.manufactured_case(n)
+            eta, u, h = dev(c.eta), dev(c.u), dev(c.h)
+            U, gh = torch.zeros_like(eta), torch.zeros_like(eta)
+            st = sgn.State(lay, eta, U, u, h, gh)
+            st.init()
+            st.set_forcing(pe, pu, om, th)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            kw = dict(rtol=1e-12, maxit=4000, prec=sgn.PREC_MIXED)
+            if name == "rk4":
+                st.rk4(dt, steps, **kw)
+            elif name == "sbdf2":
+                st.linimp(dt, steps, **kw)
+            else:
+                st.abk(order, dt, steps, **kw)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            _, e1, u1 = I.manufactured_fields_1d(x, steps * dt)
+            runs.append({"scheme": name, "dt": dt, "steps": steps, "seconds": round(sec, 4),
+                         "err_eta": float(np.abs(eta.cpu().numpy() - e1).max()),
+                         "err_u": float(np.abs(u.cpu().numpy() - u1).max()),
+                         "status": st.stats()["status"]})
+            st.close()
+    orders = {}
+    for name in ("rk4", "ab2", "ab3", "ab4", "sbdf2"):
+        a, b = [r for r in runs if r["scheme"] == name]
+        orders[name] = round(math.log2(max(a["err_eta"], a["err_u"]) /
+                                       max(b["err_eta"], b["err_u"])), 2)
+    return {"workload": f"forced SGN, manufactured solution of §6.4 Test 1, n = {n}, t = 0 to "
+                        f"{t_final}, mixed precision (rtol 1e-12), one instance",
+            "runs": runs, "observed_order": orders}
+
+
 def bench_serving(sgn, ctx, torch, nreq=120, rate=200.0, seed=16045, baseline_sample=8):
     """Poisson stream of SGN runs and constraint solves (half 1d, half 2d), host inputs."""
     import numpy as np
@@ -675,7 +734,7 @@ def main():
         from paper_2506_16045_gb300 import sgn
         ctx = sgn.Context(0)
         fn = {"shelf_1d": bench_shelf, "bump_2d": bench_2d, "serving": bench_serving,
-              "robustness": bench_robustness}
+              "robustness": bench_robustness, "manufactured": bench_manufactured}
         print(json.dumps({args.only_config: fn[args.only_config](sgn, ctx, torch)}))
         ctx.close()
         return

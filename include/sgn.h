@@ -210,6 +210,19 @@ sgn_status sgn_step_abk(sgn_state* st, int order, const double* dt, int nsteps,
  * is an RK4 step. */
 sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nsteps, const sgn_opts* opts,
                            sgn_stream stream);
+/* External forcing of the time steppers, as Test 1 of §6.4 (manufactured solutions) adds
+ * to the SGN equations: a finite Fourier series in time,
+ *   f_eta += sum_k cos(omega_k t + theta_k) phi_eta_k,  f_U += sum_k cos(omega_k t + theta_k) phi_U_k,
+ * added to every right-hand side evaluation of sgn_step_rk4 / _abk / _linimp at its stage
+ * time t (per instance; t = 0 at sgn_state_init, advanced by each instance's dt).
+ * phi_eta: DEVICE array [nterms][P] packed like eta; phi_U: DEVICE array [nterms][d P]
+ * packed like U.  Both stay owned by the caller and are read at every step, so they must
+ * outlive the state's use of them.  omega, theta: HOST arrays [nterms], copied.
+ * 0 <= nterms <= SGN_MAX_FORCING; nterms = 0 removes the forcing.  SGN_ERR_INVALID_ARG on a
+ * bad count, a null array with nterms > 0, or a non-finite omega / theta. */
+#define SGN_MAX_FORCING 16
+sgn_status sgn_state_set_forcing(sgn_state* st, int nterms, const double* phi_eta,
+                                 const double* phi_U, const double* omega, const double* theta);
 /* Synchronises the stream used by the last step call and reports counters. */
 sgn_status sgn_state_get_stats(sgn_state* st, sgn_state_stats* out);
 void sgn_state_free(sgn_state* st);

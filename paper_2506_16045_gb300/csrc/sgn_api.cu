@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <initializer_list>
 #include <utility>
 #include <cstdio>
@@ -205,6 +206,56 @@ __global__ void __launch_bounds__(256) k_lincomb(const Inst1d* __restrict__ inst
       jb.out[q] = acc + d * accf;
     }
   }
+}
+
+// External forcing of the steppers (Test 1 of §6.4, manufactured solutions): a finite
+// Fourier series in time, f_eta += sum_k cos(omega_k tau + theta_k) phi_eta_k and likewise
+// for f_U, at the stage time tau = t_i + c dt_i of every instance.
+struct ForceTerms {
+  const double* pe[SGN_MAX_FORCING];    // phi_eta_k, packed like eta (P doubles)
+  const double* pu[SGN_MAX_FORCING];    // phi_U_k, packed like U (d P doubles)
+  double omega[SGN_MAX_FORCING];
+  double theta[SGN_MAX_FORCING];
+  int K;
+};
+
+// insts == nullptr: one instance of n2d points (a 2d layout)
+__global__ void __launch_bounds__(256) k_force(const Inst1d* __restrict__ insts,
+                                               const double* __restrict__ tnow,
+                                               const double* __restrict__ dt, double c,
+                                               const __grid_constant__ ForceTerms F,
+                                               double* __restrict__ fe, double* __restrict__ fU,
+                                               long long plane, int d, long long n2d) {
+  __shared__ double w[SGN_MAX_FORCING];
+  const int i = blockIdx.y;
+  const long long off = insts ? insts[i].off : 0;
+  const long long n = insts ? insts[i].n : n2d;
+  const long long j0 = (long long)blockIdx.x * kLinChunk;
+  if (j0 >= n) return;                                  // uniform over the block
+  if (threadIdx.x < F.K) {
+    const double tau = tnow[i] + c * dt[i];
+    w[threadIdx.x] = cos(F.omega[threadIdx.x] * tau + F.theta[threadIdx.x]);
+  }
+  __syncthreads();
+  const long long j1 = j0 + kLinChunk < n ? j0 + kLinChunk : n;
+  for (long long j = j0 + threadIdx.x; j < j1; j += 256) {
+    const long long q = off + j;
+    double ae = 0.0;
+    for (int k = 0; k < F.K; ++k) ae += w[k] * F.pe[k][q];
+    fe[q] += ae;
+    for (int comp = 0; comp < d; ++comp) {
+      const long long qc = comp * plane + q;
+      double au = 0.0;
+      for (int k = 0; k < F.K; ++k) au += w[k] * F.pu[k][qc];
+      fU[qc] += au;
+    }
+  }
+}
+
+// t_i += dt_i: per-instance simulated time on the device (read by k_force; advanced inside
+// captured steps, so a replayed graph keeps it current)
+__global__ void k_advance_time(double* __restrict__ t, const double* __restrict__ dt, int count) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) t[i] += dt[i];
 }
 
 sgn_status fail(sgn_ctx* ctx, sgn_status s, const std::string& msg) {
@@ -723,6 +774,8 @@ struct sgn_state {
   void* res0 = nullptr;             // SBDF2 residual spectra (previous / current)
   void* res1 = nullptr;
   double* dt_dev = nullptr;
+  double* t_dev = nullptr;          // per-instance simulated time (external forcing)
+  ForceTerms force{};               // external forcing (K = 0: none)
   SolveRec* A_fixed = nullptr;      // SBDF2 preconditioner, fixed at init
   DevStats* stats = nullptr;
   int hist = HIST_NONE;
@@ -764,7 +817,7 @@ sgn_status alloc_state(sgn_state* st) {
   }
   if (!(st->eta_s = get(P)) || !(st->U_s = get(V)) || !(st->u_s = get(V)) ||
       !(st->eta_p = get(P)) || !(st->U_p = get(V)) || !(st->u_p = get(V)) ||
-      !(st->dt_dev = get(st->lay->count)))
+      !(st->dt_dev = get(st->lay->count)) || !(st->t_dev = get(st->lay->count)))
     return SGN_ERR_NOMEM;
   const size_t res_bytes = st->lay->dim == 1 ? sizeof(double) * 2 * (size_t)(st->lay->l1.ws_cplx /
                                                                             sgn::kWsVectors)
@@ -838,9 +891,48 @@ sgn_status lincomb(sgn_state* st, double* out, Terms xs, Terms fs, int component
   return SGN_OK;
 }
 
-// Right-hand side inside the steppers: float64 for FP64 solves, double-float for MIXED.
+// fe, fU += the external forcing at the stage time t_i + c dt_i (nothing when unset)
+sgn_status force_at(sgn_state* st, double* fe, double* fU, double c, cudaStream_t s) {
+  if (st->force.K == 0) return SGN_OK;
+  const bool d1 = st->lay->dim == 1;
+  int maxn = 8;
+  long long n2d = 0;
+  if (d1) {
+    const sgn::Layout1d& L = st->lay->l1;
+    for (int l = 3; l <= sgn::kMaxLog1d; ++l)
+      if (L.class_end[l] > L.class_begin[l]) maxn = 1 << l;
+  } else {
+    n2d = st->P;
+  }
+  const long long span = d1 ? maxn : n2d;
+  const dim3 grid((unsigned)((span + kLinChunk - 1) / kLinChunk), st->lay->count, 1);
+  k_force<<<grid, 256, 0, s>>>(d1 ? st->lay->l1.d_inst : nullptr, st->t_dev, st->dt_dev, c,
+                               st->force, fe, fU, st->P, st->d, n2d);
+  SGN_CUDA(st->lay->ctx, cudaGetLastError());
+  return SGN_OK;
+}
+
+sgn_status advance_time(sgn_state* st, cudaStream_t s) {
+  if (st->force.K == 0) return SGN_OK;
+  k_advance_time<<<1, 256, 0, s>>>(st->t_dev, st->dt_dev, st->lay->count);
+  SGN_CUDA(st->lay->ctx, cudaGetLastError());
+  return SGN_OK;
+}
+
+sgn_status rhs_plain(sgn_state* st, const double* eta, const double* u, double* fe, double* fU,
+                     cudaStream_t s);
+
+// Right-hand side inside the steppers (float64 for FP64 solves, double-float for MIXED),
+// plus the external forcing at the stage time t + c dt.
 sgn_status rhs_at(sgn_state* st, const double* eta, const double* u, double* fe, double* fU,
-                  cudaStream_t s) {
+                  cudaStream_t s, double c = 0.0) {
+  const sgn_status r = rhs_plain(st, eta, u, fe, fU, s);
+  if (r != SGN_OK) return r;
+  return force_at(st, fe, fU, c, s);
+}
+
+sgn_status rhs_plain(sgn_state* st, const double* eta, const double* u, double* fe, double* fU,
+                     cudaStream_t s) {
   sgn_layout* lay = st->lay;
   if (st->prec != SGN_PREC_MIXED) return sgn_rhs(lay->ctx, lay, eta, u, st->h, st->gradh, fe, fU, s);
   if (lay->dim == 2) {
@@ -886,11 +978,11 @@ sgn_status copy_field(sgn_state* st, double* dst, const double* src, long long n
 // Solve G u = U at eta, then the right-hand side at (eta, u).  For 1d layouts the
 // right-hand side reuses the u_x that the solve leaves in the scratch planes.
 sgn_status stage_at(sgn_state* st, const double* eta, const double* U, double* u, double* fe,
-                    double* fU, const sgn_opts* o, cudaStream_t s) {
+                    double* fU, const sgn_opts* o, cudaStream_t s, double c) {
   sgn_layout* lay = st->lay;
   if (lay->dim != 1) {
     SGN_TRY(solve_at(st, eta, U, u, o, s));
-    return rhs_at(st, eta, u, fe, fU, s);
+    return rhs_at(st, eta, u, fe, fU, s, c);
   }
   sgn_ctx* ctx = lay->ctx;
   const double rtol_inner = o->rtol_inner > 0.0 ? o->rtol_inner : -1.0;
@@ -910,7 +1002,7 @@ sgn_status stage_at(sgn_state* st, const double* eta, const double* U, double* u
                                              lay->grids[0].g, eta, u, st->h, st->gradh, fe, fU,
                                              lay->scratch, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "rhs launch");
-  return SGN_OK;
+  return force_at(st, fe, fU, c, s);
 }
 
 // One RK4 step (Eq:ERK): stages with a_{i,i-1} = 1/2, 1/2, 1 and weights 1/6, 1/3, 1/3, 1/6.
@@ -926,7 +1018,7 @@ sgn_status rk4_once(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
     // stage 4 (c = 1) starts from u extrapolated from c = 0 and c = 1/2: 2 u^(3) - u_n
     // (only the initial guess of the solve changes)
     if (i == 3) SGN_TRY(lincomb(st, st->u_s, {{st->u_s, 2.0}, {st->u, -1.0}}, {}, d, s));
-    SGN_TRY(stage_at(st, st->eta_s, st->U_s, st->u_s, st->fe[i], st->fU[i], o, s));
+    SGN_TRY(stage_at(st, st->eta_s, st->U_s, st->u_s, st->fe[i], st->fU[i], o, s, a[i]));
   }
   const double b0 = 1.0 / 6.0, b1 = 1.0 / 3.0;
   SGN_TRY(lincomb(st, st->eta, {{st->eta, 1.0}},
@@ -935,6 +1027,7 @@ sgn_status rk4_once(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
                   {{st->fU[0], b0}, {st->fU[1], b1}, {st->fU[2], b1}, {st->fU[3], b0}}, d));
   SGN_TRY(copy_field(st, st->u, st->u_s, V, s));
   SGN_TRY(solve_at(st, st->eta, st->U, st->u, o, s));
+  SGN_TRY(advance_time(st, s));
   (void)P;
   st->t += st->dt_last[0];
   st->step += 1;
@@ -991,6 +1084,7 @@ extern "C" sgn_status sgn_state_init(sgn_state* st, sgn_stream stream) {
                                              st->A_fixed, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "state init coefficients");
   SGN_CUDA(ctx, cudaMemsetAsync(st->stats, 0, sizeof(DevStats), s));
+  SGN_CUDA(ctx, cudaMemsetAsync(st->t_dev, 0, sizeof(double) * st->lay->count, s));
   st->hist = HIST_NONE;
   st->levels = 0;
   st->t = 0.0;
@@ -1198,8 +1292,9 @@ extern "C" sgn_status sgn_step_abk(sgn_state* st, int order, const double* dt, i
       // the solve for u_{n+1} and the newest history level f(w_{n+1}) (the combinations
       // above were launched with the current history pointers, so rotating is safe)
       make_room();
+      SGN_TRY(advance_time(st, s));          // the new level's right-hand side is at t_{n+1}
       SGN_TRY(stage_at(st, st->eta, st->U, st->u, st->he[st->levels], st->hU[st->levels], opts,
-                       s));
+                       s, 0.0));
       st->levels += 1;
       st->t += st->dt_last[0];
       st->step += 1;
@@ -1273,9 +1368,32 @@ extern "C" sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nstep
     std::swap(st->he[0], st->he[1]);
     std::swap(st->hU[0], st->hU[1]);
     std::swap(st->res0, st->res1);
+    SGN_TRY(advance_time(st, s));
     st->t += st->dt_last[0];
     st->step += 1;
   }
+  return SGN_OK;
+}
+
+extern "C" sgn_status sgn_state_set_forcing(sgn_state* st, int nterms, const double* phi_eta,
+                                            const double* phi_U, const double* omega,
+                                            const double* theta) {
+  if (!st || nterms < 0 || nterms > SGN_MAX_FORCING ||
+      (nterms > 0 && (!phi_eta || !phi_U || !omega || !theta)))
+    return SGN_ERR_INVALID_ARG;
+  for (int k = 0; k < nterms; ++k)
+    if (!std::isfinite(omega[k]) || !std::isfinite(theta[k])) return SGN_ERR_INVALID_ARG;
+  DeviceGuard g(st->lay->device);
+  ForceTerms F{};
+  F.K = nterms;
+  for (int k = 0; k < nterms; ++k) {
+    F.pe[k] = phi_eta + (long long)k * st->P;
+    F.pu[k] = phi_U + (long long)k * st->d * st->P;
+    F.omega[k] = omega[k];
+    F.theta[k] = theta[k];
+  }
+  st->force = F;
+  graph_drop(st);                   // a captured step holds the previous terms
   return SGN_OK;
 }
 

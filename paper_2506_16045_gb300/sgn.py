@@ -94,6 +94,8 @@ SIGNATURES = [
     ("sgn_step_abk", C.c_int, [_VP, C.c_int, C.POINTER(C.c_double), C.c_int, C.POINTER(SgnOpts),
                                _VP]),
     ("sgn_step_linimp", C.c_int, [_VP, C.POINTER(C.c_double), C.c_int, C.POINTER(SgnOpts), _VP]),
+    ("sgn_state_set_forcing", C.c_int, [_VP, C.c_int, _DP, _DP, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double)]),
     ("sgn_state_get_stats", C.c_int, [_VP, C.POINTER(SgnStateStats)]),
     ("sgn_state_free", None, [_VP]),
     ("sgn_pcg1d_noalloc", C.c_int, [C.c_int, C.c_double, _DP, _DP, _DP, _DP, C.c_double, C.c_int,
@@ -353,6 +355,18 @@ class State:
         self.lay.ctx.check(self.lay.ctx.lib.sgn_step_linimp(self.h, self._dt(dt), nsteps,
                                                             C.byref(o), _stream(stream)),
                            "sgn_step_linimp")
+
+    def set_forcing(self, phi_eta, phi_U, omega, theta):
+        """External forcing sum_k cos(omega_k t + theta_k) (phi_eta_k, phi_U_k) (device
+        tensors [K][P] and [K][d P]); K = 0 (empty omega) removes it.  The tensors are kept
+        referenced here, since the library reads them at every step."""
+        K = len(omega)
+        om = (C.c_double * max(K, 1))(*[float(v) for v in omega])
+        th = (C.c_double * max(K, 1))(*[float(v) for v in theta])
+        self._forcing = (phi_eta, phi_U) if K else None
+        self.lay.ctx.check(self.lay.ctx.lib.sgn_state_set_forcing(
+            self.h, K, _ptr(phi_eta) if K else None, _ptr(phi_U) if K else None, om, th),
+            "sgn_state_set_forcing")
 
     def stats(self):
         st = SgnStateStats()
