@@ -40,6 +40,11 @@ struct Scal2d {
   // part a float64 instruction costs 62 float32 ones, so per-mode work stays in float32
   float sigf, alphaAf, isigf;   // sigma, alpha of A and 1 / sigma
   float alphaf, betaf;          // CG alpha, beta
+  // device-driven solve (the cached solve graph): options, and the refinement loop's state
+  double rtol, rtol_in;         // outer tolerance; inner tolerance (<= 0: adaptive)
+  double rn;                    // ||r||_{A^{-1}} of the last refinement residual
+  int maxit, max_refine, kind;
+  int refinements, it_before;
 };
 
 namespace {
@@ -614,12 +619,19 @@ __global__ void k2_spec(Modes2d M, const void* in0, const void* in1, void* out0,
 
 // Inner PCG update: x += alpha p; r -= alpha g; rz = r.A^{-1}r; last block forms beta and
 // the stopping decision.
+// In a solve graph (use_h) it also sets the inner loop's condition: 0 once done, which
+// covers a breakdown found by the matvec (done already set: every block returns at once,
+// and block 0 ends the loop), so the loop cannot outlive the iteration cap.
 template <typename T>
 __global__ void __launch_bounds__(256) k2_update(Modes2d M, void* x1, void* x2, void* r1p,
                                                  void* r2p, const void* p1p, const void* p2p,
                                                  const void* g1p, const void* g2p, Scal2d* sc,
-                                                 double* parts) {
-  if (((volatile Scal2d*)sc)->done) return;
+                                                 double* parts, cudaGraphConditionalHandle hin,
+                                                 int use_h) {
+  if (((volatile Scal2d*)sc)->done) {
+    if (use_h && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hin, 0u);
+    return;
+  }
   const long long HP = (long long)M.ny * M.H;
   const ModesT<T> MT(M);
   const AinvT<T> Ai = ainv_of(sc, T(0));
@@ -643,31 +655,35 @@ __global__ void __launch_bounds__(256) k2_update(Modes2d M, void* x1, void* x2, 
     if (!isfinite(rz_new)) {
       sc->status = SGN_ERR_BREAKDOWN;
       sc->done = 1;
-      return;
+    } else {
+      sc->beta = rz_new / sc->rz;
+      sc->betaf = (float)sc->beta;
+      sc->rz = rz_new;
+      if (sqrt(rz_new) <= sc->tol) {
+        sc->done = 1;
+      } else if (sc->iters >= sc->cap) {
+        sc->status = SGN_ERR_NOT_CONVERGED;
+        sc->done = 1;
+      }
     }
-    sc->beta = rz_new / sc->rz;
-    sc->betaf = (float)sc->beta;
-    sc->rz = rz_new;
-    if (sqrt(rz_new) <= sc->tol) {
-      sc->done = 1;
-    } else if (sc->iters >= sc->cap) {
-      sc->status = SGN_ERR_NOT_CONVERGED;
-      sc->done = 1;
-    }
+    if (use_h) cudaGraphSetConditional(hin, sc->done ? 0u : 1u);
   });
 }
 
 // Start of an inner solve: r = scale * src (high -> T), x = 0, p = 0, beta = 0,
 // rz = r.A^{-1}r (last block), done if already below tol.
+// scale_sc: scale = 1 / sc->rn (the solve graph); use_h: set the inner loop's condition.
+// A solve whose status is already an error starts done.
 template <typename TH, typename T>
 __global__ void __launch_bounds__(256) k2_inner_start(Modes2d M, const void* s1, const void* s2,
                                                       double scale, void* r1p, void* r2p,
                                                       void* x1, void* x2, void* p1, void* p2,
-                                                      Scal2d* sc, double* parts) {
+                                                      Scal2d* sc, double* parts, int scale_sc,
+                                                      cudaGraphConditionalHandle hin, int use_h) {
   const long long HP = (long long)M.ny * M.H;
   const ModesT<T> MT(M);
   const AinvT<T> Ai = ainv_of(sc, T(0));
-  const T sc_t = (T)scale;
+  const T sc_t = (T)(scale_sc ? 1.0 / sc->rn : scale);
   T part = 0;
   const cplx<T> zero = mk(T(0), T(0));
   for (long long i = blockIdx.x * 256ll + threadIdx.x; i < HP; i += (long long)gridDim.x * 256) {
@@ -689,16 +705,17 @@ __global__ void __launch_bounds__(256) k2_inner_start(Modes2d M, const void* s1,
     sc->rz = rz;
     sc->beta = 0.0;
     sc->betaf = 0.0f;
-    sc->done = (sqrt(rz) <= sc->tol) ? 1 : 0;
+    sc->done = (sc->status != SGN_OK || sqrt(rz) <= sc->tol) ? 1 : 0;
+    if (use_h) cudaGraphSetConditional(hin, sc->done ? 0u : 1u);
   });
 }
 
 // x_high += scale * d (T -> high precision)
 template <typename TH, typename T>
 __global__ void k2_accumulate(Modes2d M, void* x1, void* x2, const void* d1, const void* d2,
-                              double scale) {
+                              double scale, const Scal2d* sc) {   // sc: scale = sc->rn
   const long long HP = (long long)M.ny * M.H;
-  const TH s = num<TH>(scale);
+  const TH s = num<TH>(sc ? sc->rn : scale);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HP;
        i += (long long)gridDim.x * blockDim.x) {
     cplx<T> a = ld_c<T>(d1, i), b = ld_c<T>(d2, i);
@@ -795,6 +812,7 @@ __global__ void __launch_bounds__(256) k2_coeffs(long long P, const double* eta,
     bd = block_max<256>(bd, red);
     if (threadIdx.x != 0) return;
     sc->ticket = 0;
+    if (kind < 0) kind = sc->kind;          // the solve graph passes the kind through sc
     SolveRec R = {};
     R.eta_min = a;
     R.eta_max = b;
@@ -844,7 +862,8 @@ __global__ void k2_set_given(Scal2d* sc, const SolveRec* g) {
   sc->status = SGN_OK;
 }
 
-__global__ void k2_report(const Scal2d* sc, SolveRec* rec, int refinements) {
+__global__ void k2_report(const Scal2d* sc, SolveRec* rec, int refinements) {   // < 0: sc's
+  if (refinements < 0) refinements = sc->refinements;
   SolveRec R = {};
   R.sigma = sc->sigma;
   R.alpha = sc->alpha_A;
@@ -1177,11 +1196,22 @@ cudaError_t layout2d_create(Layout2d& L, const sgn_grid& g) {
   if ((e = cudaMalloc(&L.parts, sizeof(double) * 5 * kMaxParts))) return e;
   if ((e = cudaMalloc(&L.sc, sizeof(Scal2d)))) return e;
   if ((e = cudaMalloc(&L.rhs_w, sizeof(double) * 32 * L.P))) return e;
+  if ((e = cudaMalloc(&L.stage, sizeof(double) * 7 * L.P))) return e;
+  if ((e = cudaMalloc(&L.stage_rec, sizeof(SolveRec) * 2))) return e;
   if ((e = cudaMemset(L.sc, 0, sizeof(Scal2d)))) return e;
   return cudaSuccess;
 }
 
 void layout2d_destroy(Layout2d& L) {
+  for (auto& row : L.solve_exec)
+    for (auto& ex : row) {
+      if (ex) cudaGraphExecDestroy(ex);
+      ex = nullptr;
+    }
+  cudaFree(L.stage);
+  cudaFree(L.stage_rec);
+  L.stage = nullptr;
+  L.stage_rec = nullptr;
   cudaFree(L.vec);
   cudaFree(L.tp);
   cudaFree(L.coef);
@@ -1266,7 +1296,8 @@ cudaError_t inner_pcg(const Layout2d& L, const void* t64, const void* t32, int c
       if (e) return e;
       k2_update<T><<<grid_for(L.HP, 256), 256, 0, s>>>(M, slot(L, 8), slot(L, 9), slot(L, 4),
                                                         slot(L, 5), slot(L, 6), slot(L, 7),
-                                                        slot(L, 10), slot(L, 11), L.sc, L.parts);
+                                                        slot(L, 10), slot(L, 11), L.sc, L.parts,
+                                                        cudaGraphConditionalHandle{}, 0);
       if ((e = cudaGetLastError())) return e;
     }
     done_iters += chunk;
@@ -1293,6 +1324,251 @@ __global__ void k2_reset(Scal2d* sc) {
   sc->ticket = 0;
   sc->rz64 = 0.0;
   sc->done = 0;
+  sc->refinements = 0;
+  sc->it_before = 0;
+}
+
+// ---- device-driven solve: the host loop's decisions as one-thread kernels ---------------
+// Options of a graph solve, written before the cached graph runs.
+__global__ void k2_set_opts(Scal2d* sc, double rtol, double rtol_in, int maxit, int max_refine,
+                            int kind) {
+  sc->rtol = rtol;
+  sc->rtol_in = rtol_in;
+  sc->maxit = maxit;
+  sc->max_refine = max_refine;
+  sc->kind = kind;
+}
+
+// Mixed path, after a double-float residual: stop (converged, an error status, a zero
+// right-hand side, or out of budget: not converged), or set up the next float32 inner solve
+// for G d = r / ||r|| (tolerance as the host loop: 0.3 rtol / ratio within [1e-6, 0.1]).
+// Sets the refinement loop's condition; the loop ends within max_refine passes.
+__global__ void k2_decide(Scal2d* sc, cudaGraphConditionalHandle hout) {
+  unsigned int go = 0u;
+  const double bb = sc->bb;
+  if (bb > 0.0 && sc->status == SGN_OK) {
+    const double ratio = sqrt(fmax(sc->rz64, 0.0)) / sqrt(bb);
+    if (ratio > sc->rtol) {
+      if (sc->refinements >= sc->max_refine || sc->iters >= sc->maxit) {
+        sc->status = SGN_ERR_NOT_CONVERGED;
+      } else {
+        const double tin =
+            sc->rtol_in > 0.0 ? sc->rtol_in : fmin(0.1, fmax(1e-6, 0.3 * sc->rtol / ratio));
+        sc->rn = sqrt(sc->rz64);
+        sc->tol = tin;
+        sc->cap = sc->maxit;
+        sc->done = 0;
+        sc->it_before = sc->iters;
+        go = 1u;
+      }
+    }
+  }
+  cudaGraphSetConditional(hout, go);
+}
+
+// Mixed path, after an inner solve: a float32 breakdown after some progress keeps the
+// correction (the next residual decides); count the pass.
+__global__ void k2_after_inner(Scal2d* sc) {
+  if (sc->status == SGN_ERR_BREAKDOWN && sc->iters > sc->it_before) sc->status = SGN_OK;
+  sc->refinements += 1;
+}
+
+// float64 path: one PCG from x0 to sqrt(r.A^{-1}r) <= rtol sqrt(b.A^{-1}b)
+__global__ void k2_setup_fp64(Scal2d* sc) {
+  sc->tol = sc->rtol * sqrt(fmax(sc->bb, 0.0));
+  sc->cap = sc->maxit;
+  sc->done = 0;
+}
+
+// A zero (or non-finite) right-hand side gives x = 0, as in the host-driven solve.
+__global__ void k2_finalize(const Scal2d* sc, double* x, long long n) {
+  if (sc->bb > 0.0) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = 0.0;
+}
+
+}  // namespace
+
+namespace {
+
+// Appends a while node after the work captured so far on `cs` (which keeps capturing after
+// it) and returns the node's body graph.
+cudaError_t add_while(cudaStream_t cs, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(cs, &st, nullptr, &g, &deps, &edges, &nd);
+  if (e) return e;
+  if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, g, deps, edges, nd, &p))) return e;
+  *body = p.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1,
+                                             cudaStreamSetCaptureDependencies);
+}
+
+// The solve of launch_pcg2d's host-driven path, with every host decision moved into the
+// graph: the refinement loop (mixed) and the inner PCG loop become while nodes whose
+// conditions k2_decide, k2_inner_start and k2_update set.  Inputs come from L.stage,
+// options from sc (k2_set_opts), the report goes to L.stage_rec[1].
+cudaError_t build_solve_graph(const Layout2d& L, const void* tw64, const void* tw32, bool mixed,
+                              bool given, cudaGraphExec_t* out) {
+  const Modes2d M = modes_of(L);
+  const long long P = L.P;
+  const double* eta = L.stage;
+  const double* gh = L.stage + P;
+  const double* b = L.stage + 3 * P;
+  double* x = L.stage + 5 * P;
+  cudaStream_t cs[3] = {nullptr, nullptr, nullptr};
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaSuccess;
+  int capturing = 0;          // streams with a capture begun (ended on every path)
+  for (auto& c : cs)
+    if (!e) e = cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking);
+  if (!e) e = cudaGraphCreate(&g, 0);
+  auto begin = [&](int i, cudaGraph_t into) {
+    cudaError_t r = cudaStreamBeginCaptureToGraph(cs[i], into, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeRelaxed);
+    if (!r) capturing |= 1 << i;
+    return r;
+  };
+  auto end = [&](int i) {
+    cudaGraph_t dummy;
+    capturing &= ~(1 << i);
+    cudaError_t r = cudaStreamEndCapture(cs[i], &dummy);
+    return r ? r : cudaGetLastError();
+  };
+  const int blocks = grid_for(L.HP, 256);
+  auto inner_loop = [&](auto Tc, cudaStream_t st, cudaGraphConditionalHandle hin) {
+    using T = decltype(Tc);
+    cudaError_t r = matvec<T>(L, tw64, tw32, slot(L, 6), slot(L, 7), slot(L, 10), slot(L, 11),
+                              slot(L, 6), slot(L, 7), nullptr, nullptr, 0, nullptr, L.sc, 1, 1,
+                              slot(L, 6), slot(L, 7), slot(L, 4), slot(L, 5), st);
+    if (r) return r;
+    k2_update<T><<<blocks, 256, 0, st>>>(M, slot(L, 8), slot(L, 9), slot(L, 4), slot(L, 5),
+                                         slot(L, 6), slot(L, 7), slot(L, 10), slot(L, 11), L.sc,
+                                         L.parts, hin, 1);
+    return cudaGetLastError();
+  };
+  if (!e) e = begin(0, g);
+  if (!e) {
+    k2_reset<<<1, 1, 0, cs[0]>>>(L.sc);
+    if (given) {
+      k2_set_given<<<1, 1, 0, cs[0]>>>(L.sc, L.stage_rec);
+    } else {
+      k2_coeffs<<<grid_for(P, 256), 256, 0, cs[0]>>>(P, eta, gh, -1, L.parts, L.sc, nullptr);
+    }
+    k2_coef_planes<<<grid_for(P, 256), 256, 0, cs[0]>>>(P, eta, gh, L.coef, L.coef_lo);
+    e = cudaGetLastError();
+  }
+  if (mixed) {
+    cudaGraphConditionalHandle hout, hin;
+    cudaGraph_t body = nullptr, ibody = nullptr;
+    if (!e) e = r2c_vec<df>(L, tw64, tw32, b, slot(L, 0), slot(L, 1), cs[0]);
+    if (!e) e = r2c_vec<df>(L, tw64, tw32, x, slot(L, 2), slot(L, 3), cs[0]);
+    if (!e) {
+      k2_bnorm<df><<<blocks, 256, 0, cs[0]>>>(M, slot(L, 0), slot(L, 1), L.sc, L.parts);
+      e = cudaGetLastError();
+    }
+    // r^ = b^ - G x^ (double-float) into slots 10-11, real-space x on the way
+    auto residual = [&](cudaStream_t st) {
+      return matvec<df>(L, tw64, tw32, slot(L, 2), slot(L, 3), slot(L, 10), slot(L, 11), nullptr,
+                        nullptr, slot(L, 0), slot(L, 1), 1, x, L.sc, 0, 0, nullptr, nullptr,
+                        nullptr, nullptr, st);
+    };
+    if (!e) e = residual(cs[0]);
+    if (!e) e = cudaGraphConditionalHandleCreate(&hout, g, 0, 0);
+    if (!e) {
+      k2_decide<<<1, 1, 0, cs[0]>>>(L.sc, hout);
+      e = cudaGetLastError();
+    }
+    if (!e) e = add_while(cs[0], hout, &body);
+    // refinement pass: inner solve of G d = r / ||r||, x^ += ||r|| d, next residual, decide
+    if (!e) e = begin(1, body);
+    if (!e) e = cudaGraphConditionalHandleCreate(&hin, body, 0, 0);
+    if (!e) {
+      k2_inner_start<df, float><<<blocks, 256, 0, cs[1]>>>(
+          M, slot(L, 10), slot(L, 11), 1.0, slot(L, 4), slot(L, 5), slot(L, 8), slot(L, 9),
+          slot(L, 6), slot(L, 7), L.sc, L.parts, 1, hin, 1);
+      e = cudaGetLastError();
+    }
+    if (!e) e = add_while(cs[1], hin, &ibody);
+    if (!e) e = begin(2, ibody);
+    if (!e) e = inner_loop(float(0), cs[2], hin);
+    if (!e) e = end(2);
+    if (!e) {
+      k2_after_inner<<<1, 1, 0, cs[1]>>>(L.sc);
+      k2_accumulate<df, float><<<blocks, 256, 0, cs[1]>>>(M, slot(L, 2), slot(L, 3), slot(L, 8),
+                                                         slot(L, 9), 1.0, L.sc);
+      e = cudaGetLastError();
+    }
+    if (!e) e = residual(cs[1]);
+    if (!e) {
+      k2_decide<<<1, 1, 0, cs[1]>>>(L.sc, hout);
+      e = cudaGetLastError();
+    }
+    if (!e) e = end(1);
+  } else {
+    cudaGraphConditionalHandle hin;
+    cudaGraph_t ibody = nullptr;
+    if (!e) e = r2c_vec<double>(L, tw64, tw32, b, slot(L, 0), slot(L, 1), cs[0]);
+    if (!e) e = r2c_vec<double>(L, tw64, tw32, x, slot(L, 2), slot(L, 3), cs[0]);
+    if (!e) {
+      k2_bnorm<double><<<blocks, 256, 0, cs[0]>>>(M, slot(L, 0), slot(L, 1), L.sc, L.parts);
+      e = cudaGetLastError();
+    }
+    // r = b - G x0 (slots 4-5), then PCG in float64 with the correction in slots 8-9
+    if (!e) e = matvec<double>(L, tw64, tw32, slot(L, 2), slot(L, 3), slot(L, 4), slot(L, 5),
+                               nullptr, nullptr, slot(L, 0), slot(L, 1), 1, nullptr, L.sc, 0, 0,
+                               nullptr, nullptr, nullptr, nullptr, cs[0]);
+    if (!e) e = cudaGraphConditionalHandleCreate(&hin, g, 0, 0);
+    if (!e) {
+      k2_setup_fp64<<<1, 1, 0, cs[0]>>>(L.sc);
+      k2_inner_start<double, double><<<blocks, 256, 0, cs[0]>>>(
+          M, slot(L, 4), slot(L, 5), 1.0, slot(L, 12), slot(L, 13), slot(L, 8), slot(L, 9),
+          slot(L, 6), slot(L, 7), L.sc, L.parts, 0, hin, 1);
+      e = cudaGetLastError();
+    }
+    if (!e) e = cudaMemcpyAsync(slot(L, 4), slot(L, 12), (size_t)16 * L.HP,
+                                cudaMemcpyDeviceToDevice, cs[0]);
+    if (!e) e = cudaMemcpyAsync(slot(L, 5), slot(L, 13), (size_t)16 * L.HP,
+                                cudaMemcpyDeviceToDevice, cs[0]);
+    if (!e) e = add_while(cs[0], hin, &ibody);
+    if (!e) e = begin(1, ibody);
+    if (!e) e = inner_loop(double(0), cs[1], hin);
+    if (!e) e = end(1);
+    if (!e) {
+      k2_accumulate<double, double><<<blocks, 256, 0, cs[0]>>>(M, slot(L, 2), slot(L, 3),
+                                                               slot(L, 8), slot(L, 9), 1.0,
+                                                               nullptr);
+      e = cudaGetLastError();
+    }
+    // final float64 residual for the report and x = F^{-1} x^
+    if (!e) e = matvec<double>(L, tw64, tw32, slot(L, 2), slot(L, 3), slot(L, 10), slot(L, 11),
+                               nullptr, nullptr, slot(L, 0), slot(L, 1), 1, x, L.sc, 0, 0,
+                               nullptr, nullptr, nullptr, nullptr, cs[0]);
+  }
+  if (!e) {
+    k2_finalize<<<grid_for(2 * P, 256), 256, 0, cs[0]>>>(L.sc, x, 2 * P);
+    k2_report<<<1, 1, 0, cs[0]>>>(L.sc, L.stage_rec + 1, -1);
+    e = cudaGetLastError();
+  }
+  if (!e) e = end(0);
+  for (int i = 2; i >= 0; --i)
+    if (capturing & (1 << i)) end(i);          // a failed build: close its captures
+  if (!e) e = cudaGraphInstantiate(out, g, 0);
+  if (g) cudaGraphDestroy(g);
+  for (auto& c : cs)
+    if (c) cudaStreamDestroy(c);
+  return e;
 }
 
 }  // namespace
@@ -1303,6 +1579,38 @@ cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, 
                          int maxit, int max_refine, SolveRec* rec, cudaStream_t s) {
   const Modes2d M = modes_of(L);
   cudaError_t e;
+  // ---- device-driven: one graph launch between staging copies
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  if (!L.solve_graph_off && cudaStreamIsCapturing(s, &cst) == cudaSuccess &&
+      cst == cudaStreamCaptureStatusNone) {
+    const int mi = precision == SGN_PREC_MIXED ? 1 : 0, gi = given ? 1 : 0;
+    cudaGraphExec_t& ex = L.solve_exec[mi][gi];
+    if (!ex && build_solve_graph(L, tw64, tw32, mi == 1, gi == 1, &ex) != cudaSuccess) {
+      cudaGetLastError();
+      ex = nullptr;
+      L.solve_graph_off = true;
+    }
+    if (ex) {
+      const long long P = L.P;
+      const size_t d = sizeof(double);
+      if ((e = cudaMemcpyAsync(L.stage, eta, d * P, cudaMemcpyDeviceToDevice, s)) ||
+          (e = cudaMemcpyAsync(L.stage + P, gradh, d * 2 * P, cudaMemcpyDeviceToDevice, s)) ||
+          (e = cudaMemcpyAsync(L.stage + 3 * P, b, d * 2 * P, cudaMemcpyDeviceToDevice, s)) ||
+          (e = cudaMemcpyAsync(L.stage + 5 * P, x, d * 2 * P, cudaMemcpyDeviceToDevice, s)))
+        return e;
+      if (given && (e = cudaMemcpyAsync(L.stage_rec, given, sizeof(SolveRec),
+                                        cudaMemcpyDeviceToDevice, s)))
+        return e;
+      k2_set_opts<<<1, 1, 0, s>>>(L.sc, rtol, rtol_inner, maxit, max_refine, kind);
+      if ((e = cudaGetLastError()) || (e = cudaGraphLaunch(ex, s))) return e;
+      if ((e = cudaMemcpyAsync(x, L.stage + 5 * P, d * 2 * P, cudaMemcpyDeviceToDevice, s)) ||
+          (e = cudaMemcpyAsync(rec, L.stage_rec + 1, sizeof(SolveRec), cudaMemcpyDeviceToDevice,
+                               s)))
+        return e;
+      return cudaSuccess;
+    }
+  }
+  // ---- host-driven
   k2_reset<<<1, 1, 0, s>>>(L.sc);
   if (given) {
     k2_set_given<<<1, 1, 0, s>>>(L.sc, given);
@@ -1349,14 +1657,14 @@ cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, 
     k2_set_inner<double><<<1, 1, 0, s>>>(L.sc, rtol * bnorm, maxit);
     k2_inner_start<double, double><<<grid_for(L.HP, 256), 256, 0, s>>>(
         M, slot(L, 4), slot(L, 5), 1.0, slot(L, 12), slot(L, 13), slot(L, 8), slot(L, 9),
-        slot(L, 6), slot(L, 7), L.sc, L.parts);
+        slot(L, 6), slot(L, 7), L.sc, L.parts, 0, cudaGraphConditionalHandle{}, 0);
     if ((e = cudaGetLastError())) return e;
     // move r into slots 4-5 for the loop
     cudaMemcpyAsync(slot(L, 4), slot(L, 12), (size_t)16 * L.HP, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(slot(L, 5), slot(L, 13), (size_t)16 * L.HP, cudaMemcpyDeviceToDevice, s);
     if ((e = inner_pcg<double>(L, tw64, tw32, maxit, s))) return e;
     k2_accumulate<double, double><<<grid_for(L.HP, 256), 256, 0, s>>>(
-        M, slot(L, 2), slot(L, 3), slot(L, 8), slot(L, 9), 1.0);
+        M, slot(L, 2), slot(L, 3), slot(L, 8), slot(L, 9), 1.0, nullptr);
     // final float64 residual for the report and x = F^{-1} x^
     if ((e = matvec<double>(L, tw64, tw32, slot(L, 2), slot(L, 3), slot(L, 10), slot(L, 11),
                             nullptr, nullptr, slot(L, 0), slot(L, 1), 1, x, L.sc, 0, 0, nullptr,
@@ -1388,7 +1696,7 @@ cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, 
     k2_set_inner<float><<<1, 1, 0, s>>>(L.sc, tin, maxit);
     k2_inner_start<df, float><<<grid_for(L.HP, 256), 256, 0, s>>>(
         M, slot(L, 10), slot(L, 11), 1.0 / rn, slot(L, 4), slot(L, 5), slot(L, 8), slot(L, 9),
-        slot(L, 6), slot(L, 7), L.sc, L.parts);
+        slot(L, 6), slot(L, 7), L.sc, L.parts, 0, cudaGraphConditionalHandle{}, 0);
     if ((e = cudaGetLastError())) return e;
     const int it_before = h.iters;
     if ((e = inner_pcg<float>(L, tw64, tw32, maxit, s))) return e;
@@ -1401,7 +1709,8 @@ cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, 
         k2_set_status<<<1, 1, 0, s>>>(L.sc, SGN_OK);
     }
     k2_accumulate<df, float><<<grid_for(L.HP, 256), 256, 0, s>>>(M, slot(L, 2), slot(L, 3),
-                                                                  slot(L, 8), slot(L, 9), rn);
+                                                                  slot(L, 8), slot(L, 9), rn,
+                                                                  nullptr);
     if ((e = cudaGetLastError())) return e;
     ++refinements;
   }

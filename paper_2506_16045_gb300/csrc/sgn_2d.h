@@ -25,6 +25,13 @@ struct Layout2d {
   double* parts = nullptr;  // per-block partial sums
   Scal2d* sc = nullptr;
   double* rhs_w = nullptr;  // 32 real planes of right-hand-side intermediates
+  // Device-driven solves: one instantiated graph per [mixed][given coefficients], built on
+  // first use, and the buffers its kernels address: staged eta [P], grad h [2P], b [2P],
+  // x [2P], and two solve records (given coefficients in, report out).
+  mutable cudaGraphExec_t solve_exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  mutable bool solve_graph_off = false;   // building one failed: host-driven solves
+  double* stage = nullptr;
+  SolveRec* stage_rec = nullptr;
 };
 
 cudaError_t layout2d_create(Layout2d& L, const sgn_grid& g);
@@ -39,7 +46,9 @@ cudaError_t launch_apply_G2d(const Layout2d& L, const void* tw64, const double* 
                              const double* gradh, const double* u, double* Gu, cudaStream_t s);
 cudaError_t launch_precond2d(const Layout2d& L, const void* tw64, const SolveRec* rec,
                              const double* r, double* z, cudaStream_t s);
-// Synchronises the stream between refinement passes and inner-iteration chunks.
+// Runs as one cached graph whose refinement and inner loops are conditional (while) nodes
+// driven by device-side decisions: no host round trip.  A stream under capture, or a graph
+// the driver refuses, takes the host-driven path, which reads the stop flags back.
 cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, int precision,
                          const double* eta, const double* gradh, const double* b, double* x,
                          const SolveRec* given, int kind, double rtol, double rtol_inner,

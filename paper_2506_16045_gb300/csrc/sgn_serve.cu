@@ -97,7 +97,7 @@ namespace {
 
 size_t footprint_of(int d, long long N) {
   const size_t io = (size_t)(2 + 3 * d) * 8 * N;          // eta, h, u/b, U, gradh
-  const size_t work = d == 1 ? (size_t)260 * N : (size_t)760 * N;
+  const size_t work = d == 1 ? (size_t)260 * N : (size_t)816 * N;
   const size_t big = (d == 1 && N > 8192) ? (size_t)16 * N : 0;   // global transform buffer
   return io + work + big + (1 << 16);
 }

@@ -168,7 +168,7 @@ def test_admission_budget_and_rejection(S):
     sgn, ctx = S
     free, total = torch.cuda.mem_get_info()
     # a budget that holds about one 2d 512^2 request: an oversize 1024^2 request is rejected
-    frac = 1.5 * (5 * 8 * 512 * 512 + 760 * 512 * 512) / total
+    frac = 1.5 * (5 * 8 * 512 * 512 + 816 * 512 * 512) / total
     srv = sgn.Server(ctx, budget_fraction=frac)
     z = torch.zeros(2 * 1024 * 1024, dtype=torch.float64, device="cuda")
     st, _ = srv.submit(sgn.REQ_SOLVE, sgn.Grid(2, 1024, 1.0, ny=1024, Ly=1.0), z, z, z)
