@@ -1373,9 +1373,12 @@ __global__ void k2_after_inner(Scal2d* sc) {
   sc->refinements += 1;
 }
 
-// float64 path: one PCG from x0 to sqrt(r.A^{-1}r) <= rtol sqrt(b.A^{-1}b)
+// float64 path: one PCG from x0 to sqrt(r.A^{-1}r) <= rtol sqrt(b.A^{-1}b).  A zero (or
+// non-finite) right-hand side skips the loop (every residual meets the tolerance), and
+// k2_finalize returns x = 0.
 __global__ void k2_setup_fp64(Scal2d* sc) {
-  sc->tol = sc->rtol * sqrt(fmax(sc->bb, 0.0));
+  const double bb = sc->bb;
+  sc->tol = bb > 0.0 ? sc->rtol * sqrt(bb) : 1.0e308;
   sc->cap = sc->maxit;
   sc->done = 0;
 }

@@ -116,6 +116,44 @@ def test_pcg_2d_elliptical_bump(S, prec, n, a, b):
         assert abs(info["iters"] - it12) <= max(1, 0.02 * it12)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_pcg_2d_edge_cases(S, prec):
+    """The solve's decisions, taken on the device in the solve graph: a zero right-hand side
+    (x = 0, no iteration), an exact warm start (no iteration), a budget too small (not
+    converged, reported), a non-positive depth (reported), and given coefficients equal to
+    the computed ones (bitwise the same solve)."""
+    sgn, ctx = S
+    n = 32
+    p = sgn.PREC_FP64 if prec == "fp64" else sgn.PREC_MIXED
+    _, _, h, eta, rhs = I.elliptical_bump_2d(n, 1.0, 1.0)
+    gh = O.grad(h, (1.0, 1.0))
+    lay = sgn.Layout(ctx, [sgn.Grid(2, n, 1.0, ny=n, Ly=1.0)])
+    x = dev(np.ones(2 * n * n))
+    info = sgn.pcg(lay, dev(eta), dev(gh), dev(np.zeros(2 * n * n)), x, prec=p)[0]
+    assert info["status"] == 0 and info["iters"] == 0 and np.all(host(x, (2 * n * n,)) == 0.0)
+    ref = np.linalg.solve(O.dense_G_2d(eta, gh, 1.0, 1.0), rhs.ravel())
+    x = dev(ref)
+    info = sgn.pcg(lay, dev(eta), dev(gh), dev(rhs), x, rtol=1e-8, prec=p)[0]
+    assert info["status"] == 0 and info["iters"] == 0
+    assert rel(host(x, ref.shape), ref) < 1e-12
+    x = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+    info = sgn.pcg(lay, dev(eta), dev(gh), dev(rhs), x, rtol=1e-14, maxit=2, prec=p,
+                   check=False)[0]
+    assert info["status"] == 5 and info["iters"] <= 2 + 1        # SGN_ERR_NOT_CONVERGED
+    bad = eta.copy()
+    bad[3, 5] = -0.5
+    x = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+    info = sgn.pcg(lay, dev(bad), dev(gh), dev(rhs), x, prec=p, check=False)[0]
+    assert info["status"] == 7                                    # SGN_ERR_NONPOSITIVE_DEPTH
+    P = sgn.precond_coeffs(lay, dev(eta), dev(gh))
+    x1 = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+    x2 = torch.zeros_like(x1)
+    i1 = sgn.pcg(lay, dev(eta), dev(gh), dev(rhs), x1, rtol=1e-11, prec=p)[0]
+    i2 = sgn.pcg(lay, dev(eta), dev(gh), dev(rhs), x2, rtol=1e-11, prec=p, P=P)[0]
+    assert i1["iters"] == i2["iters"] and torch.equal(x1, x2)
+    assert rel(host(x1, ref.shape), ref) < 1e-9
+
+
 def test_rhs_2d(S):
     sgn, ctx = S
     nx, ny, Lx, Ly = 64, 32, 20.0, 10.0
