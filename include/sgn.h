@@ -108,6 +108,18 @@ sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid* grids, sgn
 void sgn_layout_destroy(sgn_layout* lay);
 /* Total packed points P (per component). */
 long long sgn_layout_points(const sgn_layout* lay);
+/* Kernel forms of a 1d layout's size classes.  The solve and the right-hand side of the
+ * instances of n = 2^log2n run on one CTA per instance (ctas = 1, n <= 8192) or on a
+ * thread-block cluster of two CTAs per instance that splits the instance's points and
+ * modes between them (ctas = 2, n = 4096, 8192 and 16384; the only form of n = 16384).
+ * The two forms agree up to rounding (their dot products add in another order).  A batch
+ * that fills the GPU runs fastest on one CTA per instance; a few large instances run with
+ * less latency on clusters.  Default: 1 below n = 16384.  set_form: SGN_ERR_INVALID_ARG on
+ * a 2d layout or bad arguments, SGN_ERR_UNSUPPORTED_SIZE for a form the size lacks.
+ * States step with the new forms from their next step. */
+sgn_status sgn_layout_set_form(sgn_layout* lay, int log2n, int ctas);
+sgn_status sgn_layout_get_form(const sgn_layout* lay, int log2n, int* ctas);
+
 /* offsets[0..count]: start of each instance in a packed scalar array (host array). */
 sgn_status sgn_layout_offsets(const sgn_layout* lay, long long* offsets);
 
@@ -223,6 +235,15 @@ sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nsteps, const sg
 #define SGN_MAX_FORCING 16
 sgn_status sgn_state_set_forcing(sgn_state* st, int nterms, const double* phi_eta,
                                  const double* phi_U, const double* omega, const double* theta);
+/* Autotuner of the layout's kernel forms (sgn_layout_set_form) on this state's own
+ * problem: for every combination of forms of the n = 4096 and 8192 classes, one untimed
+ * and two timed RK4 steps with these dt (HOST [count]) and options, each combination from
+ * the same state, and the fastest combination stays set on the layout.  The state (eta, U,
+ * u, time, counters) is restored afterwards, so tuning leaves no trace on the solution.
+ * Allocates and frees 3 P doubles; synchronises `stream`; best_ms (nullable, host) receives
+ * the winning time per step.  A 2d state, or one without such classes, is left as it is. */
+sgn_status sgn_state_autotune(sgn_state* st, const double* dt, const sgn_opts* opts,
+                              sgn_stream stream, double* best_ms);
 /* Synchronises the stream used by the last step call and reports counters. */
 sgn_status sgn_state_get_stats(sgn_state* st, sgn_state_stats* out);
 void sgn_state_free(sgn_state* st);

@@ -4,6 +4,6 @@
 #include "sgn_1d_rhs.cuh"
 
 namespace sgn {
-template cudaError_t pcg1d_launch<10>(const PcgArgs&, int, int, cudaStream_t);
-template cudaError_t rhs1d_launch<10>(const RhsArgs&, int, int, cudaStream_t);
+template cudaError_t pcg1d_launch<10, 1>(const PcgArgs&, int, int, cudaStream_t);
+template cudaError_t rhs1d_launch<10, 1>(const RhsArgs&, int, int, cudaStream_t);
 }  // namespace sgn

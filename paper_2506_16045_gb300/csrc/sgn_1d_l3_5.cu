@@ -3,10 +3,10 @@
 #include "sgn_1d_rhs.cuh"
 
 namespace sgn {
-template cudaError_t pcg1d_launch<3>(const PcgArgs&, int, int, cudaStream_t);
-template cudaError_t pcg1d_launch<4>(const PcgArgs&, int, int, cudaStream_t);
-template cudaError_t pcg1d_launch<5>(const PcgArgs&, int, int, cudaStream_t);
-template cudaError_t rhs1d_launch<3>(const RhsArgs&, int, int, cudaStream_t);
-template cudaError_t rhs1d_launch<4>(const RhsArgs&, int, int, cudaStream_t);
-template cudaError_t rhs1d_launch<5>(const RhsArgs&, int, int, cudaStream_t);
+template cudaError_t pcg1d_launch<3, 1>(const PcgArgs&, int, int, cudaStream_t);
+template cudaError_t pcg1d_launch<4, 1>(const PcgArgs&, int, int, cudaStream_t);
+template cudaError_t pcg1d_launch<5, 1>(const PcgArgs&, int, int, cudaStream_t);
+template cudaError_t rhs1d_launch<3, 1>(const RhsArgs&, int, int, cudaStream_t);
+template cudaError_t rhs1d_launch<4, 1>(const RhsArgs&, int, int, cudaStream_t);
+template cudaError_t rhs1d_launch<5, 1>(const RhsArgs&, int, int, cudaStream_t);
 }  // namespace sgn

@@ -3,10 +3,10 @@
 #include "sgn_1d_rhs.cuh"
 
 namespace sgn {
-template cudaError_t pcg1d_launch<6>(const PcgArgs&, int, int, cudaStream_t);
-template cudaError_t pcg1d_launch<7>(const PcgArgs&, int, int, cudaStream_t);
-template cudaError_t pcg1d_launch<8>(const PcgArgs&, int, int, cudaStream_t);
-template cudaError_t rhs1d_launch<6>(const RhsArgs&, int, int, cudaStream_t);
-template cudaError_t rhs1d_launch<7>(const RhsArgs&, int, int, cudaStream_t);
-template cudaError_t rhs1d_launch<8>(const RhsArgs&, int, int, cudaStream_t);
+template cudaError_t pcg1d_launch<6, 1>(const PcgArgs&, int, int, cudaStream_t);
+template cudaError_t pcg1d_launch<7, 1>(const PcgArgs&, int, int, cudaStream_t);
+template cudaError_t pcg1d_launch<8, 1>(const PcgArgs&, int, int, cudaStream_t);
+template cudaError_t rhs1d_launch<6, 1>(const RhsArgs&, int, int, cudaStream_t);
+template cudaError_t rhs1d_launch<7, 1>(const RhsArgs&, int, int, cudaStream_t);
+template cudaError_t rhs1d_launch<8, 1>(const RhsArgs&, int, int, cudaStream_t);
 }  // namespace sgn

@@ -6,32 +6,64 @@
 
 namespace sgn {
 
-extern template cudaError_t pcg1d_launch<3>(const PcgArgs&, int, int, cudaStream_t);
-extern template cudaError_t pcg1d_launch<4>(const PcgArgs&, int, int, cudaStream_t);
-extern template cudaError_t pcg1d_launch<5>(const PcgArgs&, int, int, cudaStream_t);
-extern template cudaError_t pcg1d_launch<6>(const PcgArgs&, int, int, cudaStream_t);
-extern template cudaError_t pcg1d_launch<7>(const PcgArgs&, int, int, cudaStream_t);
-extern template cudaError_t pcg1d_launch<8>(const PcgArgs&, int, int, cudaStream_t);
-extern template cudaError_t pcg1d_launch<9>(const PcgArgs&, int, int, cudaStream_t);
-extern template cudaError_t pcg1d_launch<10>(const PcgArgs&, int, int, cudaStream_t);
-extern template cudaError_t pcg1d_launch<11>(const PcgArgs&, int, int, cudaStream_t);
-extern template cudaError_t pcg1d_launch<12>(const PcgArgs&, int, int, cudaStream_t);
-extern template cudaError_t pcg1d_launch<13>(const PcgArgs&, int, int, cudaStream_t);
-extern template cudaError_t pcg1d_launch<14>(const PcgArgs&, int, int, cudaStream_t);
-extern template cudaError_t rhs1d_launch<3>(const RhsArgs&, int, int, cudaStream_t);
-extern template cudaError_t rhs1d_launch<4>(const RhsArgs&, int, int, cudaStream_t);
-extern template cudaError_t rhs1d_launch<5>(const RhsArgs&, int, int, cudaStream_t);
-extern template cudaError_t rhs1d_launch<6>(const RhsArgs&, int, int, cudaStream_t);
-extern template cudaError_t rhs1d_launch<7>(const RhsArgs&, int, int, cudaStream_t);
-extern template cudaError_t rhs1d_launch<8>(const RhsArgs&, int, int, cudaStream_t);
-extern template cudaError_t rhs1d_launch<9>(const RhsArgs&, int, int, cudaStream_t);
-extern template cudaError_t rhs1d_launch<10>(const RhsArgs&, int, int, cudaStream_t);
-extern template cudaError_t rhs1d_launch<11>(const RhsArgs&, int, int, cudaStream_t);
-extern template cudaError_t rhs1d_launch<12>(const RhsArgs&, int, int, cudaStream_t);
-extern template cudaError_t rhs1d_launch<13>(const RhsArgs&, int, int, cudaStream_t);
-extern template cudaError_t rhs1d_launch<14>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<3, 1>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<4, 1>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<5, 1>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<6, 1>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<7, 1>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<8, 1>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<9, 1>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<10, 1>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<11, 1>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<12, 1>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<13, 1>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<12, 2>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<13, 2>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t pcg1d_launch<14, 2>(const PcgArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<3, 1>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<4, 1>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<5, 1>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<6, 1>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<7, 1>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<8, 1>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<9, 1>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<10, 1>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<11, 1>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<12, 1>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<13, 1>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<12, 2>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<13, 2>(const RhsArgs&, int, int, cudaStream_t);
+extern template cudaError_t rhs1d_launch<14, 2>(const RhsArgs&, int, int, cudaStream_t);
 
 namespace {
+
+// The form of size class LG in this layout: one CTA per instance, or a two-CTA cluster
+// (n = 4096 and 8192 by choice, n = 16384 always).
+struct PcgKernels {
+  template <int LG, int CL>
+  static cudaError_t go(const PcgArgs& a, int first, int num, cudaStream_t s) {
+    return pcg1d_launch<LG, CL>(a, first, num, s);
+  }
+};
+struct RhsKernels {
+  template <int LG, int CL>
+  static cudaError_t go(const RhsArgs& a, int first, int num, cudaStream_t s) {
+    return rhs1d_launch<LG, CL>(a, first, num, s);
+  }
+};
+
+template <int LG, typename K, typename Args>
+cudaError_t launch_form(const Layout1d& lay, const Args& a, int first, int num, cudaStream_t s,
+                        K) {
+  if constexpr (LG > kSmemLog1d) {
+    return K::template go<LG, 2>(a, first, num, s);
+  } else if constexpr (LG >= kClusterLog1d) {
+    return lay.ctas(LG) == 2 ? K::template go<LG, 2>(a, first, num, s)
+                             : K::template go<LG, 1>(a, first, num, s);
+  } else {
+    return K::template go<LG, 1>(a, first, num, s);
+  }
+}
 
 PcgArgs pcg_args(const Layout1d& lay, const void* tw64, const void* tw32, int precision,
                  const double* eta, const double* hx, const double* b, double* x,
@@ -92,7 +124,7 @@ cudaError_t launch_pcg1d(const Layout1d& lay, const void* tw64, const void* tw32
   const PcgArgs a = pcg_args(lay, tw64, tw32, precision, eta, hx, b, x, given, kind, rtol,
                              rtol_inner, maxit, max_refine, rec, ws, coef_df);
   return d1::for_each_size(lay, s, [&](auto Lc, int first, int num, cudaStream_t cs) {
-    return pcg1d_launch<decltype(Lc)::value>(a, first, num, cs);
+    return launch_form<decltype(Lc)::value>(lay, a, first, num, cs, PcgKernels{});
   });
 }
 
@@ -105,7 +137,7 @@ cudaError_t launch_pcg1d_ux(const Layout1d& lay, const void* tw64, const void* t
                        rtol_inner, maxit, max_refine, rec, ws, coef_df);
   a.ux = scratch;
   return d1::for_each_size(lay, s, [&](auto Lc, int first, int num, cudaStream_t cs) {
-    return pcg1d_launch<decltype(Lc)::value>(a, first, num, cs);
+    return launch_form<decltype(Lc)::value>(lay, a, first, num, cs, PcgKernels{});
   });
 }
 
@@ -115,7 +147,7 @@ cudaError_t launch_rhs1d(const Layout1d& lay, const void* tw64, const void* tw32
                          cudaStream_t s) {
   const RhsArgs a = rhs_args(lay, tw64, tw32, precision, g, eta, u, h, hx, f_eta, f_U, scratch);
   return d1::for_each_size(lay, s, [&](auto Lc, int first, int num, cudaStream_t cs) {
-    return rhs1d_launch<decltype(Lc)::value>(a, first, num, cs);
+    return launch_form<decltype(Lc)::value>(lay, a, first, num, cs, RhsKernels{});
   });
 }
 
@@ -126,7 +158,7 @@ cudaError_t launch_rhs1d_ux(const Layout1d& lay, const void* tw64, const void* t
   RhsArgs a = rhs_args(lay, tw64, tw32, precision, g, eta, u, h, hx, f_eta, f_U, scratch);
   a.ux_given = 1;
   return d1::for_each_size(lay, s, [&](auto Lc, int first, int num, cudaStream_t cs) {
-    return rhs1d_launch<decltype(Lc)::value>(a, first, num, cs);
+    return launch_form<decltype(Lc)::value>(lay, a, first, num, cs, RhsKernels{});
   });
 }
 

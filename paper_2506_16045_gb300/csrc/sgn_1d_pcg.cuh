@@ -53,8 +53,9 @@ struct PcgArgs {
   void* ux;             // nullable: also store x_x here (see pcg_body)
 };
 
-// LG = log2 n (LG = 14: two-CTA clusters of the n = 8192 kernel)
-template <int LG>
+// LG = log2 n; CL = CTAs per instance (2: thread-block clusters of two CTAs of the
+// 2^(LG-1)-point kernel; the only form for LG = 14)
+template <int LG, int CL>
 cudaError_t pcg1d_launch(const PcgArgs& a, int first, int num, cudaStream_t s);
 
 namespace pcg1d {
@@ -742,9 +743,10 @@ __global__ void __launch_bounds__(Plan<L>::NT, Plan<L>::kMinBlocks)
 
 }  // namespace pcg1d
 
-template <int LG>
+template <int LG, int CL>
 cudaError_t pcg1d_launch(const PcgArgs& a, int first, int num, cudaStream_t s) {
-  constexpr int CL = LG >= kClusterLog1d ? 2 : 1;
+  static_assert(CL == 1 || CL == 2, "one CTA or a cluster of two per instance");
+  static_assert(LG <= kSmemLog1d || CL == 2, "n = 16384 needs two CTAs");
   constexpr int L = LG - (CL - 1);          // points per CTA: 2^L
   using PL = f1::Plan<L>;
   const bool mixed = a.precision == SGN_PREC_MIXED;

@@ -3,5 +3,5 @@
 #include "sgn_1d_pcg.cuh"
 
 namespace sgn {
-template cudaError_t pcg1d_launch<11>(const PcgArgs&, int, int, cudaStream_t);
+template cudaError_t pcg1d_launch<11, 1>(const PcgArgs&, int, int, cudaStream_t);
 }  // namespace sgn

@@ -3,5 +3,5 @@
 #include "sgn_1d_pcg.cuh"
 
 namespace sgn {
-template cudaError_t pcg1d_launch<12>(const PcgArgs&, int, int, cudaStream_t);
+template cudaError_t pcg1d_launch<12, 1>(const PcgArgs&, int, int, cudaStream_t);
 }  // namespace sgn

@@ -3,5 +3,5 @@
 #include "sgn_1d_rhs.cuh"
 
 namespace sgn {
-template cudaError_t rhs1d_launch<12>(const RhsArgs&, int, int, cudaStream_t);
+template cudaError_t rhs1d_launch<12, 1>(const RhsArgs&, int, int, cudaStream_t);
 }  // namespace sgn

@@ -559,6 +559,31 @@ extern "C" void sgn_layout_destroy(sgn_layout* lay) {
 
 extern "C" long long sgn_layout_points(const sgn_layout* lay) { return lay ? lay->points : -1; }
 
+extern "C" sgn_status sgn_layout_set_form(sgn_layout* lay, int log2n, int ctas) {
+  if (check_layout(lay) || lay->dim != 1 || log2n < 3 || log2n > sgn::kMaxLog1d ||
+      (ctas != 1 && ctas != 2))
+    return fail(lay ? lay->ctx : nullptr, SGN_ERR_INVALID_ARG, "set_form args");
+  if ((ctas == 2 && log2n < sgn::kClusterLog1d) || (ctas == 1 && log2n > sgn::kSmemLog1d))
+    return fail(lay->ctx, SGN_ERR_UNSUPPORTED_SIZE, "no such form for this size");
+  if (lay->l1.ctas(log2n) != ctas) {
+    lay->l1.form[log2n] = ctas;
+    lay->l1.gen += 1;
+  }
+  return SGN_OK;
+}
+
+extern "C" sgn_status sgn_layout_get_form(const sgn_layout* lay, int log2n, int* ctas) {
+  if (check_layout(lay) || lay->dim != 1 || !ctas || log2n < 3 || log2n > sgn::kMaxLog1d)
+    return SGN_ERR_INVALID_ARG;
+  *ctas = lay->l1.ctas(log2n);
+  return SGN_OK;
+}
+
+namespace {
+
+}  // namespace
+
+
 extern "C" sgn_status sgn_layout_offsets(const sgn_layout* lay, long long* offsets) {
   if (!lay || !offsets) return SGN_ERR_INVALID_ARG;
   std::copy(lay->offsets.begin(), lay->offsets.end(), offsets);
@@ -793,6 +818,7 @@ struct sgn_state {
   std::vector<CapRec> gprof;        // profiled launch groups of gexec
   sgn_opts gkey{};                  // options of the last 1d RK4 step
   int gkey_prof = -1;               // profiling state it was taken with (-1: none yet)
+  int gkey_gen = -1;                // the layout's kernel forms it was taken with
   bool gdisabled = false;           // capture failed once: direct launches from then on
 };
 
@@ -1203,11 +1229,13 @@ sgn_status graph_replay(sgn_state* st, cudaStream_t s) {
 sgn_status rk4_step(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
   sgn_ctx* ctx = st->lay->ctx;
   if (st->lay->dim != 1 || st->gdisabled) return rk4_once(st, o, s);
-  const bool same = st->gkey_prof == ctx->prof && same_opts(st->gkey, *o);
+  const bool same = st->gkey_prof == ctx->prof && st->gkey_gen == st->lay->l1.gen &&
+                    same_opts(st->gkey, *o);
   if (!same) {
     graph_drop(st);
     st->gkey = *o;
     st->gkey_prof = ctx->prof;
+    st->gkey_gen = st->lay->l1.gen;
     return rk4_once(st, o, s);
   }
   if (!st->gexec && graph_capture(st, o) != SGN_OK) {
@@ -1394,6 +1422,90 @@ extern "C" sgn_status sgn_state_set_forcing(sgn_state* st, int nterms, const dou
   }
   st->force = F;
   graph_drop(st);                   // a captured step holds the previous terms
+  return SGN_OK;
+}
+
+
+extern "C" sgn_status sgn_state_autotune(sgn_state* st, const double* dt, const sgn_opts* opts,
+                                         sgn_stream stream, double* best_ms) {
+  if (!st || !dt || !opts) return SGN_ERR_INVALID_ARG;
+  if (best_ms) *best_ms = 0.0;
+  sgn_layout* lay = st->lay;
+  if (lay->dim != 1) return SGN_OK;                  // 2d layouts have one form
+  sgn_ctx* ctx = lay->ctx;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  sgn::Layout1d& L = lay->l1;
+  std::vector<int> cls;                              // classes with a choice of form
+  for (int l = sgn::kClusterLog1d; l <= sgn::kSmemLog1d; ++l)
+    if (L.class_end[l] > L.class_begin[l]) cls.push_back(l);
+  if (cls.empty()) return SGN_OK;
+  SGN_TRY(check_opts(st, opts));
+  SGN_TRY(upload_dt(st, dt, s));
+  // the state to come back to before every timing and at the end
+  const long long P = st->P;
+  double* save = nullptr;
+  if (cudaMalloc(&save, sizeof(double) * (3 * (size_t)P + L.count) + sizeof(DevStats)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, SGN_ERR_NOMEM, "autotune buffers");
+  }
+  DevStats* save_stats = reinterpret_cast<DevStats*>(save + 3 * P + L.count);
+  const double t0 = st->t;
+  const long long k0 = st->step;
+  auto copy3 = [&](bool to_save) -> sgn_status {
+    double* f[3] = {st->eta, st->U, st->u};
+    for (int i = 0; i < 3; ++i) {
+      double* src = to_save ? f[i] : save + i * P;
+      double* dst = to_save ? save + i * P : f[i];
+      SGN_CUDA(ctx, cudaMemcpyAsync(dst, src, sizeof(double) * P, cudaMemcpyDeviceToDevice, s));
+    }
+    SGN_CUDA(ctx, cudaMemcpyAsync(to_save ? save + 3 * P : st->t_dev,
+                                  to_save ? st->t_dev : save + 3 * P,
+                                  sizeof(double) * L.count, cudaMemcpyDeviceToDevice, s));
+    SGN_CUDA(ctx, cudaMemcpyAsync(to_save ? (void*)save_stats : (void*)st->stats,
+                                  to_save ? (const void*)st->stats : (const void*)save_stats,
+                                  sizeof(DevStats), cudaMemcpyDeviceToDevice, s));
+    st->t = t0;
+    st->step = k0;
+    return SGN_OK;
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  sgn_status r = copy3(true);
+  if (!r && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+    cudaGetLastError();
+    r = fail(ctx, SGN_ERR_CUDA, "autotune events");
+  }
+  // every combination of forms over the classes, from the same state: one untimed RK4 step
+  // (loads the kernels), then two timed (direct launches: no graph capture in the timing)
+  const int combos = 1 << (int)cls.size();
+  int best = 0;
+  float best_t = 0.0f;
+  for (int c = 0; c < combos && !r; ++c) {
+    for (size_t i = 0; i < cls.size(); ++i) L.form[cls[i]] = (c >> i) & 1 ? 2 : 1;
+    r = rk4_once(st, opts, s);
+    if (!r) r = copy3(false);
+    if (!r && cudaEventRecord(e0, s) != cudaSuccess) r = cuda_fail(ctx, cudaGetLastError(), "autotune");
+    for (int k = 0; k < 2 && !r; ++k) r = rk4_once(st, opts, s);
+    float ms = 0.0f;
+    if (!r && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+               cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      r = cuda_fail(ctx, cudaGetLastError(), "autotune timing");
+    if (!r) r = copy3(false);
+    if (!r && (c == 0 || ms < best_t)) {
+      best = c;
+      best_t = ms;
+    }
+  }
+  for (size_t i = 0; i < cls.size(); ++i) L.form[cls[i]] = (best >> i) & 1 ? 2 : 1;
+  L.gen += 1;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaFree(save);
+  st->last = s;
+  if (r) return r;
+  if (best_ms) *best_ms = best_t / 2.0;
   return SGN_OK;
 }
 

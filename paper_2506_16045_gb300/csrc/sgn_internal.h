@@ -39,7 +39,7 @@ struct SolveRec {
 constexpr int kWsVectors = 6;          // half-spectrum vectors per instance in the workspace
 constexpr int kMaxLog1d = 14;          // 1d n <= 16384 (n = 16384: two-CTA clusters)
 constexpr int kSmemLog1d = 13;         // largest 1d n whose float64 transform fits in one CTA
-constexpr int kClusterLog1d = 14;      // smallest 1d log2 n solved on two-CTA clusters
+constexpr int kClusterLog1d = 12;      // smallest 1d log2 n with a two-CTA cluster form
 
 struct Layout1d {
   int count = 0;
@@ -53,6 +53,12 @@ struct Layout1d {
   // float64 transform buffers (n complex doubles per instance) of the cta_fft kernels for
   // the instances above kSmemLog1d, indexed by position in their size class
   void* big = nullptr;
+  // CTAs per instance of each size class's solve and right-hand side (0: the default, one
+  // CTA up to kSmemLog1d and two above); set_form / autotune change it for the classes from
+  // kClusterLog1d, and `gen` counts the changes (captured step graphs hold the old forms)
+  int form[16] = {0};
+  int gen = 0;
+  int ctas(int l) const { return form[l] ? form[l] : (l > kSmemLog1d ? 2 : 1); }
   // side streams and events for running size classes concurrently (null: one stream)
   cudaStream_t side[16] = {nullptr};
   cudaEvent_t fork = nullptr;

@@ -81,6 +81,8 @@ SIGNATURES = [
     ("sgn_layout_destroy", None, [_VP]),
     ("sgn_layout_points", C.c_longlong, [_VP]),
     ("sgn_layout_offsets", C.c_int, [_VP, C.POINTER(C.c_longlong)]),
+    ("sgn_layout_set_form", C.c_int, [_VP, C.c_int, C.c_int]),
+    ("sgn_layout_get_form", C.c_int, [_VP, C.c_int, C.POINTER(C.c_int)]),
     ("sgn_spectral_grad", C.c_int, [_VP, _VP, _DP, _DP, _VP]),
     ("sgn_precond_coeffs", C.c_int, [_VP, _VP, _DP, _DP, C.c_int, C.POINTER(SgnPrecond), _VP]),
     ("sgn_apply_operator", C.c_int, [_VP, _VP, _DP, _DP, _DP, _DP, _VP]),
@@ -96,6 +98,8 @@ SIGNATURES = [
     ("sgn_step_linimp", C.c_int, [_VP, C.POINTER(C.c_double), C.c_int, C.POINTER(SgnOpts), _VP]),
     ("sgn_state_set_forcing", C.c_int, [_VP, C.c_int, _DP, _DP, C.POINTER(C.c_double),
                                         C.POINTER(C.c_double)]),
+    ("sgn_state_autotune", C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(SgnOpts), _VP,
+                                     C.POINTER(C.c_double)]),
     ("sgn_state_get_stats", C.c_int, [_VP, C.POINTER(SgnStateStats)]),
     ("sgn_state_free", None, [_VP]),
     ("sgn_pcg1d_noalloc", C.c_int, [C.c_int, C.c_double, _DP, _DP, _DP, _DP, C.c_double, C.c_int,
@@ -238,6 +242,17 @@ class Layout:
         self.dim = self.grids[0].dim
         ctx._adopt(self)
 
+    def set_form(self, log2n, ctas):
+        """One CTA (1) or a two-CTA cluster (2) per instance for the class n = 2^log2n."""
+        self.ctx.check(self.ctx.lib.sgn_layout_set_form(self.h, log2n, ctas),
+                       "sgn_layout_set_form")
+
+    def form(self, log2n):
+        c = C.c_int()
+        self.ctx.check(self.ctx.lib.sgn_layout_get_form(self.h, log2n, C.byref(c)),
+                       "sgn_layout_get_form")
+        return c.value
+
     def close(self):
         if self.h:
             self.ctx.lib.sgn_layout_destroy(self.h)
@@ -355,6 +370,17 @@ class State:
         self.lay.ctx.check(self.lay.ctx.lib.sgn_step_linimp(self.h, self._dt(dt), nsteps,
                                                             C.byref(o), _stream(stream)),
                            "sgn_step_linimp")
+
+    def autotune(self, dt, rtol=1e-12, maxit=2000, prec=PREC_FP64, coef=COEF_OPT,
+                 rtol_inner=0.0, max_refine=0, stream=None):
+        """Times the layout's kernel forms on RK4 steps of this state's problem and keeps the
+        fastest (the state is restored); returns the winning time per step (ms)."""
+        o = self._opts(rtol, maxit, prec, coef, rtol_inner, max_refine)
+        ms = C.c_double()
+        self.lay.ctx.check(self.lay.ctx.lib.sgn_state_autotune(self.h, self._dt(dt), C.byref(o),
+                                                               _stream(stream), C.byref(ms)),
+                           "sgn_state_autotune")
+        return ms.value
 
     def set_forcing(self, phi_eta, phi_U, omega, theta):
         """External forcing sum_k cos(omega_k t + theta_k) (phi_eta_k, phi_U_k) (device
