@@ -52,6 +52,8 @@ def parse():
                                               "manufactured"],
                     help="run only this extra configuration and print its result as one JSON "
                          "line (for profiling one workload; not the headline)")
+    ap.add_argument("--n2d", type=int, default=512, choices=[128, 256, 512, 1024],
+                    help="grid side of the bump_2d configuration")
     return ap.parse_args()
 
 
@@ -492,13 +494,14 @@ def gpu_arm(args, world, rank, local, pg):
     E.st.close()
 
 
-def bench_2d(sgn, ctx, torch, steps=3):
-    """2d plane solitary wave over a Gaussian bump (80 x 80 at 512^2), RK4, mixed; error
-    against the float64 path after the same steps."""
+def bench_2d(sgn, ctx, torch, steps=3, n=512):
+    """2d plane solitary wave over a Gaussian bump (80 x 80 at n^2, 512^2 by default; dt 0.02
+    at 512^2, scaled with the grid spacing), RK4, mixed; error against the float64 path
+    after the same steps."""
     import numpy as np
 
     from paper_2506_16045_gb300 import inputs as I
-    c = I.bump2d_case(n=512, L=80.0, a=0.2, x0=20.0, H=0.5, R=3.0, dt=0.02)
+    c = I.bump2d_case(n=n, L=80.0, a=0.2, x0=20.0, H=0.5, R=3.0, dt=0.02 * 512 / n)
     n = c["n"]
     lay = sgn.Layout(ctx, [sgn.Grid(2, n, c["L"], g=c["g"], ny=n, Ly=c["L"])])
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a).ravel(), dtype=torch.float64,
@@ -521,7 +524,7 @@ def bench_2d(sgn, ctx, torch, steps=3):
     tm, em, um, sm = out[sgn.PREC_MIXED]
     t6, e6, u6, _ = out[sgn.PREC_FP64]
     rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
-    return {"workload": "2d bump 80x80 at 512^2, RK4, rtol 1e-10", "steps": steps,
+    return {"workload": f"2d bump 80x80 at {n}^2, RK4, rtol 1e-10", "steps": steps,
             "value": n * n * steps / tm, "unit": UNIT, "fp64_value": n * n * steps / t6,
             "rel_l2_eta_vs_fp64": rel(em, e6), "rel_l2_u_vs_fp64": rel(um, u6),
             "iterations_per_solve": sm["iterations"] / max(1, sm["solves"])}
@@ -810,8 +813,9 @@ def main():
 
         from paper_2506_16045_gb300 import sgn
         ctx = sgn.Context(0)
-        fn = {"shelf_1d": bench_shelf, "bump_2d": bench_2d, "serving": bench_serving,
-              "robustness": bench_robustness, "manufactured": bench_manufactured}
+        fn = {"shelf_1d": bench_shelf, "bump_2d": lambda *a: bench_2d(*a, n=args.n2d),
+              "serving": bench_serving, "robustness": bench_robustness,
+              "manufactured": bench_manufactured}
         print(json.dumps({args.only_config: fn[args.only_config](sgn, ctx, torch)}))
         ctx.close()
         return
