@@ -988,12 +988,18 @@ cudaError_t smem_attr(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Columns per CTA for this layout: 2, or 4 for float32 planes when 2-column tiles would not
+// fit one wave on 152 SMs (nx = 1024: 257 tiles).  Four float32 columns also fill each
+// 32-byte sector of a row (two leave half of it unread); wider elements fill it with two.
 template <typename T>
-constexpr int col_tw() { return 2; }   // 2 columns per CTA: 129 CTAs at 512^2 (152 SMs)
+int col_tw_of(const Layout2d& L) {
+  const int H = L.nx / 2 + 1;
+  return (std::is_same<T, float>::value && (H + 1) / 2 > 152) ? 4 : 2;
+}
 
 template <typename T>
 size_t col_smem(const Layout2d& L, int K) {
-  return (size_t)K * col_tw<T>() * (L.ny + 1) * sizeof(cplx<T>);
+  return (size_t)K * col_tw_of<T>(L) * (L.ny + 1) * sizeof(cplx<T>);
 }
 
 template <typename T>
@@ -1002,14 +1008,13 @@ size_t row_smem(const Layout2d& L, int nrows) {
 }
 
 // column pass launcher: MAXB from ny (TW columns x ny/4 butterflies over 512 threads)
-template <typename T, int MODE>
-cudaError_t cols(const Layout2d& L, const void* t64, const void* t32, const ColArgs& a,
-                 cudaStream_t s) {
-  constexpr int TW = col_tw<T>();
+template <typename T, int TW, int MODE>
+cudaError_t cols_tw(const Layout2d& L, const void* t64, const void* t32, const ColArgs& a,
+                    cudaStream_t s) {
   const Modes2d M = modes_of(L);
   const int tiles = (M.H + TW - 1) / TW;
   const int K = (MODE == COL_MATVEC_IN || MODE == COL_MATVEC_OUT) ? 3 : a.K;
-  const size_t sm = col_smem<T>(L, K);
+  const size_t sm = (size_t)K * TW * (L.ny + 1) * sizeof(cplx<T>);
   // TW * ny / 4 butterflies per radix-4 stage; MAXB = ceil(that / 512)
   const int need = (TW * L.ny / 4 + kColNT - 1) / kColNT;
   cudaError_t e;
@@ -1027,6 +1032,15 @@ cudaError_t cols(const Layout2d& L, const void* t64, const void* t32, const ColA
     k<<<tiles, kColNT, sm, s>>>(M, L.ly, t64, t32, a);
   }
   return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+cudaError_t cols(const Layout2d& L, const void* t64, const void* t32, const ColArgs& a,
+                 cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (col_tw_of<T>(L) == 4) return cols_tw<T, 4, MODE>(L, t64, t32, a, s);
+  }
+  return cols_tw<T, 2, MODE>(L, t64, t32, a, s);
 }
 
 template <typename T>
