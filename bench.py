@@ -530,31 +530,55 @@ def bench_2d(sgn, ctx, torch, steps=3, n=512):
             "iterations_per_solve": sm["iterations"] / max(1, sm["solves"])}
 
 
-def bench_shelf(sgn, ctx, torch, steps=40):
-    """1d shelf (N=4096, L=200, a=0.3): AB4 + mixed PCG versus linearly implicit SBDF2."""
+def bench_shelf(sgn, ctx, torch, steps=2000):
+    """1d shelf (N = 4096, L = 200, a = 0.3, ramp of width 5 at x = 60), whole 2000-step runs:
+    AB4 with PCG (float64 at rtol 1e-12; mixed at rtol 1e-10) against the linearly implicit
+    SBDF2 step (float64 and mixed), each at its own stable step (AB4 dt 0.004, SBDF2
+    dt 0.002).  Each run is timed with CUDA events from its initial state, start-up steps
+    included, after a short untimed run of the same kind."""
     import numpy as np
 
     from paper_2506_16045_gb300 import inputs as I
     c = I.shelf_case()
     lay = sgn.Layout(ctx, [sgn.Grid(1, c.n, c.L, g=c.g)])
-    res = {}
-    for name in ("ab4_mixed", "ab4_fp64", "sbdf2"):
-        eta, u, h = (torch.as_tensor(a, dtype=torch.float64, device="cuda")
-                     for a in (c.eta, c.u, c.h))
-        U, gh = torch.zeros_like(eta), torch.zeros_like(eta)
-        st = sgn.State(lay, eta, U, u, h, gh)
-        st.init()
-        prec = sgn.PREC_FP64 if name != "ab4_mixed" else sgn.PREC_MIXED
-        run = (lambda k: st.linimp(c.dt, k, rtol=1e-12, prec=prec)) if name == "sbdf2" else \
-              (lambda k: st.abk(4, c.dt, k, rtol=1e-12, prec=prec))
-        run(4)                                      # start-up levels and warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        run(steps)
-        torch.cuda.synchronize()
-        res[name] = c.n * steps / (time.perf_counter() - t0)
-        st.close()
-    return {"workload": "1d shelf N=4096 L=200, 40 steps after start-up", "unit": UNIT, **res}
+    variants = (("ab4_fp64", "ab4", sgn.PREC_FP64, 1e-12),
+                ("ab4_mixed", "ab4", sgn.PREC_MIXED, 1e-10),
+                ("sbdf2_fp64", "sbdf2", sgn.PREC_FP64, 1e-12),
+                ("sbdf2_mixed", "sbdf2", sgn.PREC_MIXED, 1e-10))
+    res, final = {}, {}
+    for name, scheme, prec, rtol in variants:
+        dt = I.SHELF_DT[scheme]
+        for k in (8, steps):
+            eta, u, h = (torch.as_tensor(a, dtype=torch.float64, device="cuda")
+                         for a in (c.eta, c.u, c.h))
+            U, gh = torch.zeros_like(eta), torch.zeros_like(eta)
+            st = sgn.State(lay, eta, U, u, h, gh)
+            st.init()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            if scheme == "sbdf2":
+                st.linimp(dt, k, rtol=rtol, maxit=4000, prec=prec)
+            else:
+                st.abk(4, dt, k, rtol=rtol, maxit=4000, prec=prec)
+            e1.record()
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) * 1e-3
+            stats = st.stats()
+            st.close()
+        final[name] = (eta.cpu().numpy() - c.h, u.cpu().numpy())
+        res[name] = {"value": c.n * steps / sec, "seconds": round(sec, 4), "dt": dt,
+                     "t_final": steps * dt, "simulated_time_per_s": steps * dt / sec,
+                     "status": stats["status"],
+                     "iterations_per_solve": stats["iterations"] / max(1, stats["solves"])}
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    for s_ in ("ab4", "sbdf2"):
+        (zm, um), (z6, u6) = final[s_ + "_mixed"], final[s_ + "_fp64"]
+        res[s_ + "_mixed"]["rel_l2_zeta_vs_fp64"] = rel(zm, z6)
+        res[s_ + "_mixed"]["rel_l2_u_vs_fp64"] = rel(um, u6)
+    return {"workload": f"1d shelf N=4096 L=200, {steps} steps per run (AB4 dt 0.004 to "
+                        f"t = {steps * 0.004:g}; SBDF2 dt 0.002 to t = {steps * 0.002:g})",
+            "unit": UNIT, **res}
 
 
 def bench_robustness(sgn, ctx, torch, reps=5):

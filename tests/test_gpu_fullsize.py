@@ -1,0 +1,300 @@
+"""Parity at the full sizes of the benchmarked workloads, in the launch configurations the
+benchmark times.
+
+- Flat-bottom solitary wave (L = 100, n = 256, a = 0.2, dt = 0.01, float64 RK4, rtol 1e-12),
+  all 500 steps: against the oracle, the closed-form travelling wave, and the conservation
+  of mass and energy (Remark rmk:dswe_as_constraint).
+- Shelf (n = 4096, L = 200, a = 0.3, ramp of width 5 at x = 60), 2000 steps of AB4 and of
+  the linearly implicit SBDF2 step (§5.3), float64 and mixed, each at its own stable step.
+- 2d bump (80 x 80 at 512^2, mixed, rtol 1e-10): one RK4 step against the oracle, and the
+  float64 step at a tight tolerance.
+- The 256-instance ensemble with the autotuned kernel forms and the replayed step graph:
+  size-stratified instances against the oracle after the same steps.
+- Serving at the largest request sizes (1d n = 16384, 2d 1024^2) in one mix: each solve is
+  checked through the oracle's operator against a known solution, the run against the
+  oracle's steps.
+
+Tolerances: float64 1e-11 relative L2 where the oracle's own sensitivity allows it, mixed
+1e-6 relative L2 (both stated per test with the measured sensitivity they rest on).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import sgn_oracle as O
+from paper_2506_16045_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2506_16045_gb300 import sgn
+    ctx = sgn.Context(0)
+    yield sgn, ctx
+    ctx.close()
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x).ravel(), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def run_1d(sgn, ctx, c, scheme, steps, prec, rtol, dt=None):
+    """One instance through sgn_step_rk4 / _abk / _linimp; returns host (eta, U, u), stats."""
+    lay = sgn.Layout(ctx, [sgn.Grid(1, c.n, c.L, g=c.g)])
+    eta, u, h = dev(c.eta), dev(c.u), dev(c.h)
+    U, gh = torch.zeros_like(eta), torch.zeros_like(eta)
+    st = sgn.State(lay, eta, U, u, h, gh)
+    st.init()
+    dt = c.dt if dt is None else dt
+    if scheme == "rk4":
+        st.rk4(dt, steps, rtol=rtol, maxit=4000, prec=prec)
+    elif scheme == "ab4":
+        st.abk(4, dt, steps, rtol=rtol, maxit=4000, prec=prec)
+    else:
+        st.linimp(dt, steps, rtol=rtol, maxit=4000, prec=prec)
+    out = host(eta), host(U), host(u)
+    stats = st.stats()
+    st.close()
+    return out, stats
+
+
+# --------------------------------------------------------------------------------------
+# Flat-bottom solitary wave, 500 steps
+# --------------------------------------------------------------------------------------
+
+def test_solitary_wave_500_steps(S):
+    """The oracle's own sensitivity over these 500 steps: rtol 1e-12 against 1e-13 moves zeta
+    by 5e-13 and u by 6e-13 (relative L2), so 1e-11 holds the GPU to the paper-level
+    float64 bar.  The scheme's error against the closed form is 5e-9 (eta) and 1.2e-8 (u) in
+    the oracle; mass is conserved to rounding and RK4's energy drift is 2.5e-10."""
+    sgn, ctx = S
+    c = I.solitary_case()
+    (eta, U, u), stats = run_1d(sgn, ctx, c, "rk4", 500, sgn.PREC_FP64, 1e-12)
+    grid = O.make_grid(1, c.n, c.L, c.g)
+    ref = O.init_state(c.eta, c.u, c.h, grid)
+    E0, m0 = O.energy(ref), O.mass(ref.eta, ref.h, c.L / c.n)
+    O.run_rk4(ref, c.dt, 500, 1e-13)
+    assert stats["status"] == 0 and stats["solves"] == 2000
+    assert rel(eta - c.h, ref.eta - c.h) < 1e-11 and rel(u, ref.u) < 1e-11
+    assert rel(U, ref.U) < 1e-11
+    x = I.grid_1d(c.n, c.L)
+    ee, ue = I.solitary_wave_1d(x, c.L, 1.0, 0.2, 25.0, c.g, t=500 * c.dt)
+    assert np.abs(eta - ee).max() < 1e-8 and np.abs(u - ue).max() < 2e-8
+    got = O.init_state(eta, u, c.h, grid)
+    assert abs(O.mass(eta, c.h, c.L / c.n) - m0) < 1e-12 * abs(m0)
+    assert abs(O.energy(got) / E0 - 1.0) < 1e-9
+    assert abs(O.energy(got) - O.energy(ref)) < 1e-11 * E0
+
+
+# --------------------------------------------------------------------------------------
+# Shelf, 2000 steps of AB4 and SBDF2
+# --------------------------------------------------------------------------------------
+
+_SHELF = {}
+
+
+def shelf_oracle(scheme):
+    if scheme not in _SHELF:
+        c = I.shelf_case()
+        st = O.init_state(c.eta, c.u, c.h, O.make_grid(1, c.n, c.L, c.g))
+        if scheme == "ab4":
+            O.run_ab(st, 4, I.SHELF_DT["ab4"], 2000, 1e-13)
+        else:
+            O.run_sbdf2(st, I.SHELF_DT["sbdf2"], 2000, 1e-13)
+        _SHELF[scheme] = st
+    return _SHELF[scheme]
+
+
+@pytest.mark.parametrize("scheme", ["ab4", "sbdf2"])
+def test_shelf_2000_steps(S, scheme):
+    """float64 at rtol 1e-13 and mixed at rtol 1e-10 (the benchmarked setting) against the
+    oracle at rtol 1e-13 after 2000 steps.  The oracle's own sensitivity to last-bit changes
+    of its initial data over these steps: AB4 zeta 5e-13, u 2e-14, U 1.6e-11; SBDF2 zeta
+    3e-13, u 8e-14, U 7.8e-12.  U, advanced explicitly and only smoothed by the solve for u,
+    carries that rounding at high wavenumbers, so its float64 bar is 2e-10 (over ten times
+    the oracle's sensitivity) while zeta and u keep 1e-11."""
+    sgn, ctx = S
+    c = I.shelf_case()
+    dt = I.SHELF_DT[scheme]
+    ref = shelf_oracle(scheme)
+    z_ref = ref.eta - c.h
+    (e6, U6, u6), s6 = run_1d(sgn, ctx, c, scheme, 2000, sgn.PREC_FP64, 1e-13, dt)
+    assert s6["status"] == 0 and abs(s6["t"] - 2000 * dt) < 1e-9
+    assert rel(e6 - c.h, z_ref) < 1e-11 and rel(u6, ref.u) < 1e-11
+    assert rel(U6, ref.U) < 2e-10
+    (em, Um, um), sm = run_1d(sgn, ctx, c, scheme, 2000, sgn.PREC_MIXED, 1e-10, dt)
+    assert sm["status"] == 0
+    assert rel(em - c.h, z_ref) < 1e-6 and rel(um, ref.u) < 1e-6 and rel(Um, ref.U) < 1e-6
+    assert np.isfinite(em).all() and np.abs(em - c.h).max() < 0.5
+
+
+# --------------------------------------------------------------------------------------
+# 2d bump at 512^2
+# --------------------------------------------------------------------------------------
+
+_BUMP = {}
+
+
+def bump_oracle():
+    if "st" not in _BUMP:
+        b = I.bump2d_case()
+        grid = O.make_grid(2, b["n"], b["L"], b["g"], ny=b["n"], Ly=b["L"])
+        st = O.init_state(b["eta"], b["u"], b["h"], grid)
+        O.rk4_step(st, b["dt"], 1e-13)
+        _BUMP["st"] = st
+    return _BUMP["st"]
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_bump_2d_512_rk4_step(S, prec):
+    """Mixed at rtol 1e-10 (the benchmarked setting) within 1e-6; float64 at rtol 1e-12
+    within 1e-11 on zeta and 1e-10 on u (the solve fixes u to rtol sqrt(kappa_ub))."""
+    sgn, ctx = S
+    b = I.bump2d_case()
+    n = b["n"]
+    lay = sgn.Layout(ctx, [sgn.Grid(2, n, b["L"], g=b["g"], ny=n, Ly=b["L"])])
+    eta, u, h = dev(b["eta"]), dev(b["u"]), dev(b["h"])
+    U, gh = torch.zeros_like(u), torch.zeros_like(u)
+    st = sgn.State(lay, eta, U, u, h, gh)
+    st.init()
+    p, rtol = (sgn.PREC_MIXED, 1e-10) if prec == "mixed" else (sgn.PREC_FP64, 1e-12)
+    st.rk4(b["dt"], 1, rtol=rtol, maxit=4000, prec=p)
+    stats = st.stats()
+    e, uu = host(eta).reshape(n, n), host(u).reshape(2, n, n)
+    st.close()
+    ref = bump_oracle()
+    assert stats["status"] == 0 and stats["solves"] == 4
+    if prec == "mixed":
+        assert rel(e - b["h"], ref.eta - b["h"]) < 1e-6 and rel(uu, ref.u) < 1e-6
+    else:
+        assert rel(e - b["h"], ref.eta - b["h"]) < 1e-11 and rel(uu, ref.u) < 1e-10
+
+
+# --------------------------------------------------------------------------------------
+# The 256-instance ensemble
+# --------------------------------------------------------------------------------------
+
+def test_ensemble_256_bench_configuration(S):
+    """The benchmark's launch configuration: the whole ensemble in one layout, kernel forms
+    chosen by sgn_state_autotune, launch-group profiling on, six mixed RK4 steps at rtol
+    1e-10 (the second onwards replay the captured step graph).  Eight instances, the first
+    of each size class and three more, against the oracle's float64 steps."""
+    sgn, ctx = S
+    ens = I.ensemble_1d()
+    assert len(ens) == 256
+    lay = sgn.Layout(ctx, [sgn.Grid(1, c.n, c.L, g=c.g) for c in ens])
+    cat = lambda k: np.concatenate([getattr(c, k) for c in ens])
+    eta, u, h = dev(cat("eta")), dev(cat("u")), dev(cat("h"))
+    U, gh = torch.zeros_like(eta), torch.zeros_like(eta)
+    st = sgn.State(lay, eta, U, u, h, gh)
+    st.init()
+    dts = [c.dt for c in ens]
+    st.autotune(dts, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
+    ctx.profile(True)
+    try:
+        for _ in range(6):
+            st.rk4(dts, 1, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
+        torch.cuda.synchronize()
+    finally:
+        ctx.profile(False)
+        ctx.profile_read()
+    stats = st.stats()
+    assert stats["status"] == 0 and stats["step"] == 6
+    he, hu = host(eta), host(u)
+    offs = lay.offsets
+    pick = []
+    for n in sorted({c.n for c in ens}):
+        pick.append(next(i for i, c in enumerate(ens) if c.n == n))
+    rng = np.random.default_rng(5)
+    pick += [int(i) for i in rng.choice([i for i in range(256) if i not in pick], 3,
+                                        replace=False)]
+    for i in pick:
+        c = ens[i]
+        ref = O.init_state(c.eta, c.u, c.h, O.make_grid(1, c.n, c.L, c.g))
+        O.run_rk4(ref, c.dt, 6, 1e-13)
+        e_i, u_i = he[offs[i]:offs[i + 1]], hu[offs[i]:offs[i + 1]]
+        assert rel(e_i - c.h, ref.eta - c.h) < 1e-6 and rel(u_i, ref.u) < 1e-6, (i, c.n)
+    st.close()
+
+
+# --------------------------------------------------------------------------------------
+# Serving at the largest request sizes
+# --------------------------------------------------------------------------------------
+
+def test_serving_largest_requests(S):
+    """A 2d 1024^2 solve (80 x 80, Gaussian bump of height 0.6 and radius 1, the sharpest
+    of the stream's range), a 1d n = 16384 solve and a 1d n = 16384 RK4 run, submitted
+    together from host memory as the benchmark's stream does, mixed at rtol 1e-10.  Each
+    solve's right-hand side is the oracle's G applied to a known smooth velocity, so the
+    solution is known: the error must be within 10 rtol sqrt(kappa_ub), and the oracle's
+    residual of the returned solution within 10 rtol.  The run must match the oracle's
+    steps within 1e-6."""
+    import time
+    sgn, ctx = S
+    srv = sgn.Server(ctx)
+    n2, L2 = 1024, 80.0
+    X, Y = I.grid_2d(n2, n2, L2, L2)
+    h2 = I.gaussian_bump_2d(X, Y, L2, L2, 0.6, 1.0, 0.5 * L2, 0.5 * L2)
+    e2, _ = I.solitary_wave_2d(X, Y, L2, L2, 1.0, 0.3, 0.2 * L2, 9.81)
+    e2 = h2 + (e2 - 1.0)
+    us2 = np.stack([np.cos(2 * np.pi * X / L2) * np.sin(4 * np.pi * Y / L2),
+                    0.5 * np.sin(2 * np.pi * X / L2)])
+    gh2 = O.grad(h2, (L2, L2))
+    b2 = O.apply_G_2d(e2, gh2, us2, L2, L2)
+    n1, L1 = 16384, 200.0
+    x = I.grid_1d(n1, L1)
+    h1 = 1.0 - 0.6 * np.exp(-((x - 0.5 * L1) ** 2))
+    e1, uw = I.solitary_wave_1d(x, L1, 1.0, 0.3, 0.2 * L1, 9.81)
+    e1 = h1 + (e1 - 1.0)
+    us1 = np.cos(2 * np.pi * x / L1) + 0.25 * np.sin(6 * np.pi * x / L1)
+    b1 = O.apply_G_1d(e1, O.deriv(h1, L1), us1, L1)
+    dt1 = 0.25 * (L1 / n1) / math.sqrt(9.81 * 1.3)
+    flat = lambda a: np.ascontiguousarray(a, dtype=np.float64).ravel()
+    kw = dict(rtol=1e-10, prec=sgn.PREC_MIXED, host=True)
+    s_a, t2 = srv.submit(sgn.REQ_SOLVE, sgn.Grid(2, n2, L2, ny=n2, Ly=L2), flat(e2), flat(b2),
+                         flat(h2), **kw)
+    s_b, t1 = srv.submit(sgn.REQ_SOLVE, sgn.Grid(1, n1, L1), flat(e1), flat(b1), flat(h1), **kw)
+    s_c, tr = srv.submit(sgn.REQ_RUN, sgn.Grid(1, n1, L1), flat(e1), flat(uw), flat(h1),
+                         scheme=sgn.SCHEME_RK4, dt=dt1, nsteps=5, **kw)
+    assert s_a == 0 and s_b == 0 and s_c == 0
+    out, t0 = {}, time.time()
+    while len(out) < 3:
+        for t in (t2, t1, tr):
+            if t not in out:
+                r = srv.poll(t)
+                if r is not None:
+                    out[t] = r
+        assert time.time() - t0 < 300.0, "serving requests did not finish"
+        time.sleep(0.005)
+    assert all(r["status"] == 0 for r in out.values())
+    x2 = sgn.device_array(out[t2]["u"], 2 * n2 * n2).cpu().numpy().reshape(2, n2, n2)
+    k2 = O.precond_coeffs(e2, gh2)["kappa_ub"]
+    assert rel(x2, us2) < 10 * 1e-10 * math.sqrt(k2)
+    assert rel(O.apply_G_2d(e2, gh2, x2, L2, L2), b2) < 1e-9
+    x1 = sgn.device_array(out[t1]["u"], n1).cpu().numpy()
+    k1 = O.precond_coeffs(e1, O.deriv(h1, L1))["kappa_ub"]
+    assert rel(x1, us1) < 10 * 1e-10 * math.sqrt(k1)
+    assert rel(O.apply_G_1d(e1, O.deriv(h1, L1), x1, L1), b1) < 1e-9
+    ref = O.init_state(e1, uw, h1, O.make_grid(1, n1, L1, 9.81))
+    O.run_rk4(ref, dt1, 5, 1e-13)
+    er = sgn.device_array(out[tr]["eta"], n1).cpu().numpy()
+    ur = sgn.device_array(out[tr]["u"], n1).cpu().numpy()
+    assert rel(er - h1, ref.eta - h1) < 1e-6 and rel(ur, ref.u) < 1e-6
+    for t in (t2, t1, tr):
+        assert srv.release(t) == 0
+    srv.close()
