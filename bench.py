@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SGN grid-point-steps/s batched vs plain at ≤1e-6 rel err; p50/p99 solve ms"
 UNIT = "grid-point-steps/s"
+FULL_STEPS = 200            # the ensemble configuration's run length
 FP32_PEAK = 152 * 128 * 2 * 2.07e9          # FMA lanes x 2 flops x max SM clock
 DF_COST = 9.6     # float32 ops per double-float flop in an FFT butterfly
 RTOL = 1e-10
@@ -348,6 +349,16 @@ def gpu_arm(args, world, rank, local, pg):
     zeta64 = eta64 - E.h.cpu().numpy()
     err_zeta = rel(eta_mixed - E.h.cpu().numpy(), zeta64)
 
+    # ---- the configuration's whole 200-step run: mixed against batched float64 at the end
+    E.reset()
+    E.step(sgn.PREC_MIXED, FULL_STEPS)
+    zm, um = E.eta.cpu().numpy() - E.h.cpu().numpy(), E.u.cpu().numpy()
+    E.reset()
+    E.step(sgn.PREC_FP64, FULL_STEPS)
+    z6, u6 = E.eta.cpu().numpy() - E.h.cpu().numpy(), E.u.cpu().numpy()
+    err_full = {"steps": FULL_STEPS, "rel_l2_zeta_vs_fp64": rel(zm, z6),
+                "rel_l2_u_vs_fp64": rel(um, u6)}
+
     # ---- plain float64, one instance per launch, on a size-stratified sample
     plain = None
     if not args.no_plain:
@@ -466,7 +477,8 @@ def gpu_arm(args, world, rank, local, pg):
         "cpu_baseline": cpu,
         "accuracy": {"rel_l2_eta_vs_fp64": err_eta, "rel_l2_u_vs_fp64": err_u,
                      "rel_l2_zeta_vs_fp64": err_zeta, "steps_compared": nref,
-                     "rel_l2_vs_oracle_sample_1step": oracle_err},
+                     "rel_l2_vs_oracle_sample_1step": oracle_err,
+                     "whole_run": err_full},
         "batched_fp64": {"value": total_points / (fp64_ms * 1e-3), "unit": UNIT},
         "plain_fp64": plain,
         "step_latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1,
@@ -494,46 +506,60 @@ def gpu_arm(args, world, rank, local, pg):
     E.st.close()
 
 
-def bench_2d(sgn, ctx, torch, steps=3, n=512):
+def bench_2d(sgn, ctx, torch, steps=300, n=512):
     """2d plane solitary wave over a Gaussian bump (80 x 80 at n^2, 512^2 by default; dt 0.02
-    at 512^2, scaled with the grid spacing), RK4, mixed; error against the float64 path
-    after the same steps."""
+    at 512^2, scaled with the grid spacing), RK4 over the whole run (300 steps to t = 6 at
+    512^2, where the wave has reached the bump), mixed and float64 at rtol 1e-10; the mixed
+    run's error against the float64 run at the end, and the mass drift of each."""
     import numpy as np
 
     from paper_2506_16045_gb300 import inputs as I
     c = I.bump2d_case(n=n, L=80.0, a=0.2, x0=20.0, H=0.5, R=3.0, dt=0.02 * 512 / n)
     n = c["n"]
+    steps = steps * n // 512
     lay = sgn.Layout(ctx, [sgn.Grid(2, n, c["L"], g=c["g"], ny=n, Ly=c["L"])])
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a).ravel(), dtype=torch.float64,
                                     device="cuda")
+    zeta0 = c["eta"] - c["h"]
     out = {}
     for prec in (sgn.PREC_MIXED, sgn.PREC_FP64):
-        eta, u, h = dev(c["eta"]), dev(c["u"]), dev(c["h"])
-        U = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
-        gh = torch.zeros_like(U)
-        st = sgn.State(lay, eta, U, u, h, gh)
-        st.init()
-        st.rk4(c["dt"], 1, rtol=1e-10, maxit=4000, prec=prec)        # warm-up step
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st.rk4(c["dt"], steps, rtol=1e-10, maxit=4000, prec=prec)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        out[prec] = (dt, eta.cpu().numpy(), u.cpu().numpy(), st.stats())
-        st.close()
+        for k in (2, steps):                       # a short untimed run, then the whole run
+            eta, u, h = dev(c["eta"]), dev(c["u"]), dev(c["h"])
+            U = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+            gh = torch.zeros_like(U)
+            st = sgn.State(lay, eta, U, u, h, gh)
+            st.init()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            st.rk4(c["dt"], k, rtol=1e-10, maxit=4000, prec=prec)
+            e1.record()
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) * 1e-3
+            stats = st.stats()
+            st.close()
+        out[prec] = (sec, eta.cpu().numpy().reshape(n, n), u.cpu().numpy(), stats)
     tm, em, um, sm = out[sgn.PREC_MIXED]
     t6, e6, u6, _ = out[sgn.PREC_FP64]
     rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
-    return {"workload": f"2d bump 80x80 at {n}^2, RK4, rtol 1e-10", "steps": steps,
+    mass = lambda e: float(np.sum(e - c["h"]))
+    m0 = float(np.sum(zeta0))
+    return {"workload": f"2d bump 80x80 at {n}^2, RK4 dt {c['dt']:g}, {steps} steps to "
+                        f"t = {steps * c['dt']:g}, rtol 1e-10", "steps": steps,
             "value": n * n * steps / tm, "unit": UNIT, "fp64_value": n * n * steps / t6,
-            "rel_l2_eta_vs_fp64": rel(em, e6), "rel_l2_u_vs_fp64": rel(um, u6),
-            "iterations_per_solve": sm["iterations"] / max(1, sm["solves"])}
+            "seconds_mixed": round(tm, 3), "seconds_fp64": round(t6, 3),
+            "rel_l2_zeta_vs_fp64": rel(em - c["h"], e6 - c["h"]),
+            "rel_l2_u_vs_fp64": rel(um, u6),
+            "mass_drift_rel": {"mixed": abs(mass(em) - m0) / abs(m0),
+                               "fp64": abs(mass(e6) - m0) / abs(m0)},
+            "max_zeta": float(np.abs(em - c["h"]).max()),
+            "iterations_per_solve": sm["iterations"] / max(1, sm["solves"]), "status": sm["status"]}
 
 
 def bench_shelf(sgn, ctx, torch, steps=2000):
     """1d shelf (N = 4096, L = 200, a = 0.3, ramp of width 5 at x = 60), whole 2000-step runs:
-    AB4 with PCG (float64 at rtol 1e-12; mixed at rtol 1e-10) against the linearly implicit
-    SBDF2 step (float64 and mixed), each at its own stable step (AB4 dt 0.004, SBDF2
+    AB4 with PCG (float64, and mixed refined to the same rtol 1e-12) against the linearly
+    implicit SBDF2 step (float64 and mixed), each at its own stable step (AB4 dt 0.004, SBDF2
     dt 0.002).  Each run is timed with CUDA events from its initial state, start-up steps
     included, after a short untimed run of the same kind."""
     import numpy as np
@@ -542,9 +568,9 @@ def bench_shelf(sgn, ctx, torch, steps=2000):
     c = I.shelf_case()
     lay = sgn.Layout(ctx, [sgn.Grid(1, c.n, c.L, g=c.g)])
     variants = (("ab4_fp64", "ab4", sgn.PREC_FP64, 1e-12),
-                ("ab4_mixed", "ab4", sgn.PREC_MIXED, 1e-10),
+                ("ab4_mixed", "ab4", sgn.PREC_MIXED, 1e-12),
                 ("sbdf2_fp64", "sbdf2", sgn.PREC_FP64, 1e-12),
-                ("sbdf2_mixed", "sbdf2", sgn.PREC_MIXED, 1e-10))
+                ("sbdf2_mixed", "sbdf2", sgn.PREC_MIXED, 1e-12))
     res, final = {}, {}
     for name, scheme, prec, rtol in variants:
         dt = I.SHELF_DT[scheme]

@@ -7,9 +7,10 @@ benchmark times.
 - Shelf (n = 4096, L = 200, a = 0.3, ramp of width 5 at x = 60), 2000 steps of AB4 and of
   the linearly implicit SBDF2 step (§5.3), float64 and mixed, each at its own stable step.
 - 2d bump (80 x 80 at 512^2, mixed, rtol 1e-10): one RK4 step against the oracle, and the
-  float64 step at a tight tolerance.
+  float64 step at a tight tolerance; the whole 300-step run against float64 and mass.
 - The 256-instance ensemble with the autotuned kernel forms and the replayed step graph:
-  size-stratified instances against the oracle after the same steps.
+  size-stratified instances against the oracle after the same steps, then the whole
+  200-step run against the batched float64 path.
 - Serving at the largest request sizes (1d n = 16384, 2d 1024^2) in one mix: each solve is
   checked through the oracle's operator against a known solution, the run against the
   oracle's steps.
@@ -122,12 +123,12 @@ def shelf_oracle(scheme):
 
 @pytest.mark.parametrize("scheme", ["ab4", "sbdf2"])
 def test_shelf_2000_steps(S, scheme):
-    """float64 at rtol 1e-13 and mixed at rtol 1e-10 (the benchmarked setting) against the
-    oracle at rtol 1e-13 after 2000 steps.  The oracle's own sensitivity to last-bit changes
-    of its initial data over these steps: AB4 zeta 5e-13, u 2e-14, U 1.6e-11; SBDF2 zeta
-    3e-13, u 8e-14, U 7.8e-12.  U, advanced explicitly and only smoothed by the solve for u,
-    carries that rounding at high wavenumbers, so its float64 bar is 2e-10 (over ten times
-    the oracle's sensitivity) while zeta and u keep 1e-11."""
+    """float64 at rtol 1e-13 and mixed refined to rtol 1e-12 (the benchmarked setting)
+    against the oracle at rtol 1e-13 after 2000 steps.  The oracle's own sensitivity to
+    last-bit changes of its initial data over these steps: AB4 zeta 5e-13, u 2e-14,
+    U 1.6e-11; SBDF2 zeta 3e-13, u 8e-14, U 7.8e-12.  U, advanced explicitly and only
+    smoothed by the solve for u, carries that rounding at high wavenumbers, so its float64
+    bar is 2e-10 (over ten times the oracle's sensitivity) while zeta and u keep 1e-11."""
     sgn, ctx = S
     c = I.shelf_case()
     dt = I.SHELF_DT[scheme]
@@ -137,7 +138,7 @@ def test_shelf_2000_steps(S, scheme):
     assert s6["status"] == 0 and abs(s6["t"] - 2000 * dt) < 1e-9
     assert rel(e6 - c.h, z_ref) < 1e-11 and rel(u6, ref.u) < 1e-11
     assert rel(U6, ref.U) < 2e-10
-    (em, Um, um), sm = run_1d(sgn, ctx, c, scheme, 2000, sgn.PREC_MIXED, 1e-10, dt)
+    (em, Um, um), sm = run_1d(sgn, ctx, c, scheme, 2000, sgn.PREC_MIXED, 1e-12, dt)
     assert sm["status"] == 0
     assert rel(em - c.h, z_ref) < 1e-6 and rel(um, ref.u) < 1e-6 and rel(Um, ref.U) < 1e-6
     assert np.isfinite(em).all() and np.abs(em - c.h).max() < 0.5
@@ -185,6 +186,35 @@ def test_bump_2d_512_rk4_step(S, prec):
         assert rel(e - b["h"], ref.eta - b["h"]) < 1e-11 and rel(uu, ref.u) < 1e-10
 
 
+def test_bump_2d_512_whole_run(S):
+    """The whole 300-step run (t = 6, the wave over the bump) of the benchmarked
+    configuration, too long for the oracle: properties that hold at any length.  The mixed
+    run (rtol 1e-10) stays within 1e-6 of the float64 run (rtol 1e-12), whose single step is
+    tied to the oracle above; both conserve mass to rounding (the spectral divergence has
+    zero mean); the wave stays bounded."""
+    sgn, ctx = S
+    b = I.bump2d_case()
+    n = b["n"]
+    lay = sgn.Layout(ctx, [sgn.Grid(2, n, b["L"], g=b["g"], ny=n, Ly=b["L"])])
+    out = {}
+    for prec, rtol in ((sgn.PREC_MIXED, 1e-10), (sgn.PREC_FP64, 1e-12)):
+        eta, u, h = dev(b["eta"]), dev(b["u"]), dev(b["h"])
+        U, gh = torch.zeros_like(u), torch.zeros_like(u)
+        st = sgn.State(lay, eta, U, u, h, gh)
+        st.init()
+        st.rk4(b["dt"], 300, rtol=rtol, maxit=4000, prec=prec)
+        stats = st.stats()
+        out[prec] = host(eta).reshape(n, n), host(u)
+        st.close()
+        assert stats["status"] == 0 and stats["solves"] == 1200
+    (em, um), (e6, u6) = out[sgn.PREC_MIXED], out[sgn.PREC_FP64]
+    z0 = b["eta"] - b["h"]
+    assert rel(em - b["h"], e6 - b["h"]) < 1e-6 and rel(um, u6) < 1e-6
+    for e in (em, e6):
+        assert abs(np.sum(e - b["h"]) - np.sum(z0)) < 1e-11 * np.sum(np.abs(z0))
+        assert np.abs(e - b["h"]).max() < 0.5
+
+
 # --------------------------------------------------------------------------------------
 # The 256-instance ensemble
 # --------------------------------------------------------------------------------------
@@ -229,6 +259,20 @@ def test_ensemble_256_bench_configuration(S):
         O.run_rk4(ref, c.dt, 6, 1e-13)
         e_i, u_i = he[offs[i]:offs[i + 1]], hu[offs[i]:offs[i + 1]]
         assert rel(e_i - c.h, ref.eta - c.h) < 1e-6 and rel(u_i, ref.u) < 1e-6, (i, c.n)
+    # on to the configuration's 200 steps, against the batched float64 path (tied to the
+    # oracle instance by instance above and in the 1d tests) over the same steps
+    st.rk4(dts, 194, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
+    em, um = host(eta), host(u)
+    st.close()
+    eta.copy_(dev(cat("eta")))
+    u.copy_(dev(cat("u")))
+    st = sgn.State(lay, eta, U, u, h, gh)
+    st.init()
+    st.rk4(dts, 200, rtol=1e-12, maxit=4000, prec=sgn.PREC_FP64)
+    assert st.stats()["status"] == 0
+    e6, u6 = host(eta), host(u)
+    hh = cat("h")
+    assert rel(em - hh, e6 - hh) < 1e-6 and rel(um, u6) < 1e-6
     st.close()
 
 
