@@ -17,7 +17,8 @@ Serre-Green-Naghdi Equations") in float64 numpy:
     Fourier mode (a 1x1 or 2x2 solve per mode);
   * the coefficients sigma*, alpha*, kappa_ub (Eq:FlatbathCoeff, Eq:Optcoeff,
     Eq:Optcoeffb) and the replacement coefficients (Remark "replacementcoeff", §4);
-  * textbook preconditioned conjugate gradients (§3.2, Eq:PCGLinSyst);
+  * textbook preconditioned conjugate gradients (§3.2, Eq:PCGLinSyst), and textbook
+    restarted GMRES with right preconditioning by A as the Krylov option besides PCG;
   * the right-hand side of the DAE form (Eq:DAE_DSWE, §5) with the forcing F (Def:bigF);
   * RK4 (Eq:ERK, §5.1), Adams-Bashforth 2-4 (Eq:AB, Table 1, §5.2) and the linearly
     implicit SBDF2 step (Eq:MM, §5.3).
@@ -305,6 +306,88 @@ def pcg(applyG, applyPinv, b, x0=None, rtol=1e-12, maxit=1000, history=False):
             iters.append(x.copy())
     ratio = math.sqrt(max(rz, 0.0)) / bnorm
     return (x, it, ratio, iters) if history else (x, it, ratio)
+
+
+# ======================================================================================
+# Restarted GMRES with right preconditioning (the Krylov option besides PCG)
+# ======================================================================================
+
+def gmres(applyG, applyPinv, b, x0=None, rtol=1e-10, restart=30, maxit=1000, history=False):
+    """Restarted GMRES(m) for G x = b with right preconditioning: the Arnoldi process on
+    G P^{-1} (modified Gram-Schmidt), Givens rotations for the small least-squares problem,
+    and x = x0 + P^{-1} V y at the end of each cycle.  This is the textbook method; the paper
+    solves with PCG (§3.2) and prescribes no GMRES variant.
+    Stops when ||b - G x||_2 <= rtol ||b||_2: inside a cycle through the rotated right-hand
+    side (which equals the residual norm of the current minimiser), and on the true residual
+    at every restart.  `maxit` bounds the Arnoldi steps over all cycles.
+    Returns (x, steps, final true ratio, cycles[, x after every step])."""
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    bnorm = float(np.linalg.norm(b))
+    hist = [] if history else None
+    if bnorm == 0.0:
+        x[...] = 0.0
+        return (x, 0, 0.0, 0, hist) if history else (x, 0, 0.0, 0)
+    m = restart
+    steps = cycles = 0
+    r = b - applyG(x)
+    beta = float(np.linalg.norm(r))
+    while beta > rtol * bnorm and steps < maxit:
+        cycles += 1
+        V = [r / beta]
+        H = np.zeros((m + 1, m))
+        cs, sn = np.zeros(m), np.zeros(m)
+        gvec = np.zeros(m + 1)
+        gvec[0] = beta
+        j = 0
+        while j < m and steps < maxit:
+            w = applyG(applyPinv(V[j]))
+            for i in range(j + 1):                       # modified Gram-Schmidt
+                H[i, j] = float(np.vdot(w, V[i]))
+                w = w - H[i, j] * V[i]
+            hnext = float(np.linalg.norm(w))
+            H[j + 1, j] = hnext
+            for i in range(j):                           # earlier rotations on the new column
+                a, c = H[i, j], H[i + 1, j]
+                H[i, j] = cs[i] * a + sn[i] * c
+                H[i + 1, j] = -sn[i] * a + cs[i] * c
+            den = math.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j], H[j + 1, j] = den, 0.0
+            gvec[j + 1] = -sn[j] * gvec[j]
+            gvec[j] = cs[j] * gvec[j]
+            j += 1
+            steps += 1
+            if history:
+                y = _back_substitute(H[:j, :j], gvec[:j])
+                hist.append(x + applyPinv(sum(y[i] * V[i] for i in range(j))))
+            if abs(gvec[j]) <= rtol * bnorm or hnext == 0.0:
+                break
+            V.append(w / hnext)
+        y = _back_substitute(H[:j, :j], gvec[:j])
+        x = x + applyPinv(sum(y[i] * V[i] for i in range(j)))
+        r = b - applyG(x)
+        beta = float(np.linalg.norm(r))
+    ratio = beta / bnorm
+    return (x, steps, ratio, cycles, hist) if history else (x, steps, ratio, cycles)
+
+
+def _back_substitute(R, g):
+    """Solves the upper-triangular R y = g."""
+    k = g.size
+    y = np.zeros(k)
+    for i in range(k - 1, -1, -1):
+        y[i] = (g[i] - float(R[i, i + 1:] @ y[i + 1:])) / R[i, i]
+    return y
+
+
+def gmres_G(eta, gradh, b, grid, x0=None, rtol=1e-10, restart=30, maxit=2000, kind="opt"):
+    """Solve G_{eta,h} x = b by GMRES(restart) right-preconditioned with the A of §4.
+    Returns (x, steps, ratio, cycles, coefficients)."""
+    c = precond_coeffs(eta, gradh, kind)
+    x, it, ratio, cyc = gmres(lambda v: apply_G(eta, gradh, v, grid),
+                              lambda v: apply_Ainv(v, c["sigma"], c["alpha"], grid),
+                              b, x0, rtol, restart, maxit)
+    return x, it, ratio, cyc, c
 
 
 def solve_G(eta, gradh, b, grid, x0=None, rtol=1e-12, maxit=2000, kind="opt"):

@@ -490,3 +490,94 @@ def test_sbdf2_zero_stability_region():
     s = 0.7 * lam_top / lam_max                     # pushes the top eigenvalue past 4/3
     assert O.sbdf2_zero_stability_growth(
         Gd, O.dense_A_1d(s * c["sigma"], s * c["alpha"], n, 1.0), nsteps=400) > 1e3
+
+
+# ---------------------------------------------------------------------------- GMRES option
+
+def _dense_case(dim):
+    if dim == 1:
+        n = 16
+        _, h, eta, b = I.testproblem_1d(n, 1.0, 1.0)
+        gh = O.deriv(h, 1.0)
+        grid = O.make_grid(1, n, 1.0, 1.0)
+        c = O.precond_coeffs(eta, gh)
+        Gd = O.dense_G_1d(eta, gh, 1.0)
+        Ad = O.dense_A_1d(c["sigma"], c["alpha"], n, 1.0)
+        return eta, gh, b, grid, c, Gd, Ad, b.shape
+    n = 8
+    _, _, h, eta, rhs = I.elliptical_bump_2d(n, 1.0, 1.0)
+    gh = O.grad(h, (1.0, 1.0))
+    grid = O.make_grid(2, n, 1.0, 1.0, ny=n, Ly=1.0)
+    c = O.precond_coeffs(eta, gh)
+    Gd = O.dense_G_2d(eta, gh, 1.0, 1.0)
+    Ad = O.dense_A_2d(c["sigma"], c["alpha"], n, n, 1.0, 1.0)
+    return eta, gh, rhs, grid, c, Gd, Ad, rhs.shape
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_gmres_iterates_minimise_the_residual_over_the_krylov_space(dim):
+    """The k-th GMRES iterate from x0 = 0 minimises ||b - G x|| over x in
+    A^{-1} span{b, M b, ..., M^{k-1} b} with M = G A^{-1}: brute force with the dense
+    matrices of Def:MatrixM (no matrix-free operator, no Arnoldi) and a least-squares solve."""
+    eta, gh, b, grid, c, Gd, Ad, shape = _dense_case(dim)
+    x, steps, _, _, hist = O.gmres(lambda v: O.apply_G(eta, gh, v, grid),
+                                   lambda v: O.apply_Ainv(v, c["sigma"], c["alpha"], grid),
+                                   b, rtol=1e-14, restart=40, maxit=6, history=True)
+    assert steps == 6 and len(hist) == 6
+    Ainv = np.linalg.inv(Ad)
+    M = Gd @ Ainv
+    bf = b.ravel()
+    K = [bf]
+    for k in range(1, 7):
+        Q, _ = np.linalg.qr(np.stack(K, axis=1))
+        Z = Ainv @ Q
+        coef, *_ = np.linalg.lstsq(Gd @ Z, bf, rcond=None)
+        xb = Z @ coef
+        assert np.linalg.norm(hist[k - 1].ravel() - xb) <= 1e-9 * np.linalg.norm(xb), k
+        K.append(M @ K[-1])
+    res = [np.linalg.norm(bf - Gd @ h_.ravel()) for h_ in hist]
+    assert all(r1 <= r0 * (1 + 1e-12) for r0, r1 in zip(res, res[1:]))
+
+
+def test_gmres_reaches_the_lu_solution_within_n_steps():
+    """Without restarts GMRES is exact after at most N steps (the Krylov space fills R^N):
+    the solution equals a dense LU solve of the Def:MatrixM matrix."""
+    eta, gh, b, grid, c, Gd, Ad, _ = _dense_case(1)
+    x, steps, ratio, cycles = O.gmres(lambda v: O.apply_G(eta, gh, v, grid),
+                                      lambda v: O.apply_Ainv(v, c["sigma"], c["alpha"], grid),
+                                      b, rtol=1e-13, restart=16, maxit=16)
+    xs = np.linalg.solve(Gd, b)
+    assert steps <= 16 and cycles == 1 and ratio <= 1e-13
+    assert np.linalg.norm(x - xs) <= 1e-11 * np.linalg.norm(xs)
+
+
+def test_gmres_one_step_when_A_equals_G():
+    """Flat bottom and constant depth: G = A exactly (§4), so G A^{-1} = I and GMRES stops
+    after one step, with x = A^{-1} b."""
+    n, L = 64, 5.0
+    eta = np.full(n, 1.3)
+    gh = np.zeros(n)
+    b = np.cos(2 * np.pi * I.grid_1d(n, L) / L) + 0.3
+    grid = O.make_grid(1, n, L, 1.0)
+    x, steps, ratio, cycles, c = O.gmres_G(eta, gh, b, grid, rtol=1e-13)
+    assert steps == 1 and ratio <= 1e-13
+    np.testing.assert_allclose(O.apply_G(eta, gh, x, grid), b, atol=1e-13)
+
+
+def test_gmres_agrees_with_pcg_and_restarts_cost_steps():
+    """On Eq:Testproblem (n = 256) GMRES(30) and PCG reach the same solution of the SPD
+    system; GMRES(5) does too, in more steps; every run's true residual is below rtol."""
+    n = 256
+    _, h, eta, b = I.testproblem_1d(n, 1.0, 1.0)
+    hx = O.deriv(h, 1.0)
+    grid = O.make_grid(1, n, 1.0, 1.0)
+    xp, _, _, c = O.solve_G(eta, hx, b, grid, rtol=1e-14, maxit=5000)
+    x30, s30, r30, _, _ = O.gmres_G(eta, hx, b, grid, rtol=1e-11, restart=30)
+    x5, s5, r5, cyc5, _ = O.gmres_G(eta, hx, b, grid, rtol=1e-11, restart=5, maxit=5000)
+    for x, r in ((x30, r30), (x5, r5)):
+        assert r <= 1e-11
+        assert np.linalg.norm(b - O.apply_G(eta, hx, x, grid)) <= 1e-11 * np.linalg.norm(b)
+        assert np.linalg.norm(x - xp) <= 1e-11 * math.sqrt(c["kappa_ub"]) * 50 * np.linalg.norm(xp)
+    assert s5 > s30 and cyc5 >= s5 // 5
+    z, s0, r0, c0, _ = O.gmres_G(eta, hx, np.zeros(n), grid)
+    assert s0 == 0 and r0 == 0.0 and c0 == 0 and not z.any()
