@@ -164,6 +164,30 @@ sgn_status sgn_pcg(sgn_ctx* ctx, const sgn_layout* lay, const double* eta, const
                    const sgn_precond* P, const double* b, double* x, double rtol, int maxit,
                    sgn_precision prec, sgn_pcg_info* info, sgn_stream stream);
 
+/* Restarted GMRES(restart) for G_{eta,h} x = b, right-preconditioned by the A of §4: the
+ * Krylov option besides sgn_pcg.  G is symmetric positive definite, where PCG (§3.2) is the
+ * paper's method and the cheaper one; GMRES is the solver for a non-symmetric variant of
+ * the operator and a cross-check of PCG.  Textbook method in the A^{-1} inner product
+ * <u, v> = u . A^{-1} v: Arnoldi on G A^{-1} (classical Gram-Schmidt with one
+ * reorthogonalisation), Givens rotations, x += A^{-1} V y per cycle.  Each iterate minimises
+ * sqrt(r.A^{-1}r), the residual measure of sgn_pcg's stopping rule; the Euclidean residual
+ * of a fine grid has a rounding floor near eps ||G|| that this measure damps.  float64
+ * throughout.  Each instance stops when sqrt(r.A^{-1}r) <= rtol sqrt(b.A^{-1}b): inside a
+ * cycle through the rotated right-hand side, and on the true residual at every restart.
+ * maxit bounds the Arnoldi steps over all cycles; b = 0 gives x = 0 in 0 steps.
+ *   P: per-instance coefficients, or NULL to compute them (Eq:Optcoeff) as sgn_pcg does.
+ *   x: in: initial guess, out: solution.  restart: 1..SGN_GMRES_MAX_RESTART.
+ *   info: HOST array [count] or NULL; iters = Arnoldi steps, refinements = cycles,
+ *   rel_resid_Ainv = the final true sqrt(r.A^{-1}r) / sqrt(b.A^{-1}b), status.
+ * The call allocates 2 (restart + 2) vectors of the layout's packed size on the stream,
+ * synchronises the stream after every Arnoldi step (the host drives the cycles) and before
+ * returning, and returns the worst instance status (SGN_ERR_NOT_CONVERGED at maxit,
+ * SGN_ERR_BREAKDOWN on NaN/Inf, SGN_ERR_NONPOSITIVE_DEPTH from the coefficients). */
+#define SGN_GMRES_MAX_RESTART 64
+sgn_status sgn_gmres(sgn_ctx* ctx, const sgn_layout* lay, const double* eta, const double* gradh,
+                     const sgn_precond* P, const double* b, double* x, double rtol, int restart,
+                     int maxit, sgn_pcg_info* info, sgn_stream stream);
+
 /* Right-hand side of the DAE form (Eq:DAE_DSWE, §5): f_eta = -div(eta u),
  * f_U = -g eta grad(zeta) - div(eta u (x) u) + F(eta, u, h) with F from Def:bigF and
  * (u.grad)^2 h read as u.grad(u.grad h).  zeta = eta - h.  float64. */

@@ -18,7 +18,8 @@ Serre-Green-Naghdi Equations") in float64 numpy:
   * the coefficients sigma*, alpha*, kappa_ub (Eq:FlatbathCoeff, Eq:Optcoeff,
     Eq:Optcoeffb) and the replacement coefficients (Remark "replacementcoeff", §4);
   * textbook preconditioned conjugate gradients (§3.2, Eq:PCGLinSyst), and textbook
-    restarted GMRES with right preconditioning by A as the Krylov option besides PCG;
+    restarted GMRES, right-preconditioned by A in the A^{-1} inner product, as the Krylov
+    option besides PCG;
   * the right-hand side of the DAE form (Eq:DAE_DSWE, §5) with the forcing F (Def:bigF);
   * RK4 (Eq:ERK, §5.1), Adams-Bashforth 2-4 (Eq:AB, Table 1, §5.2) and the linearly
     implicit SBDF2 step (Eq:MM, §5.3).
@@ -313,16 +314,21 @@ def pcg(applyG, applyPinv, b, x0=None, rtol=1e-12, maxit=1000, history=False):
 # ======================================================================================
 
 def gmres(applyG, applyPinv, b, x0=None, rtol=1e-10, restart=30, maxit=1000, history=False):
-    """Restarted GMRES(m) for G x = b with right preconditioning: the Arnoldi process on
-    G P^{-1} (modified Gram-Schmidt), Givens rotations for the small least-squares problem,
-    and x = x0 + P^{-1} V y at the end of each cycle.  This is the textbook method; the paper
-    solves with PCG (§3.2) and prescribes no GMRES variant.
-    Stops when ||b - G x||_2 <= rtol ||b||_2: inside a cycle through the rotated right-hand
-    side (which equals the residual norm of the current minimiser), and on the true residual
-    at every restart.  `maxit` bounds the Arnoldi steps over all cycles.
+    """Restarted GMRES(m) for G x = b with right preconditioning, in the inner product
+    <u, v> = u . P^{-1} v: the Arnoldi process on G P^{-1} (modified Gram-Schmidt in that
+    inner product), Givens rotations for the small least-squares problem, and
+    x = x0 + P^{-1} V y at the end of each cycle.  Each iterate minimises
+    sqrt(r . P^{-1} r) over its Krylov space, the residual measure of the PCG stopping rule
+    (reading R7); in the Euclidean norm a fine grid's residual has a rounding floor of about
+    eps ||G|| (G grows like eta^3 k^2 / 3), which this norm damps.  This is the textbook
+    method in a weighted inner product; the paper solves with PCG (§3.2) and prescribes no
+    GMRES variant.
+    Stops when sqrt(r.P^{-1}r) <= rtol sqrt(b.P^{-1}b): inside a cycle through the rotated
+    right-hand side (which equals the residual measure of the current minimiser), and on
+    the true residual at every restart.  `maxit` bounds the Arnoldi steps over all cycles.
     Returns (x, steps, final true ratio, cycles[, x after every step])."""
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
-    bnorm = float(np.linalg.norm(b))
+    bnorm = math.sqrt(max(float(np.vdot(b, applyPinv(b))), 0.0))
     hist = [] if history else None
     if bnorm == 0.0:
         x[...] = 0.0
@@ -330,21 +336,24 @@ def gmres(applyG, applyPinv, b, x0=None, rtol=1e-10, restart=30, maxit=1000, his
     m = restart
     steps = cycles = 0
     r = b - applyG(x)
-    beta = float(np.linalg.norm(r))
+    rz = applyPinv(r)
+    beta = math.sqrt(max(float(np.vdot(r, rz)), 0.0))
     while beta > rtol * bnorm and steps < maxit:
         cycles += 1
-        V = [r / beta]
+        V, Z = [r / beta], [rz / beta]                  # Z_i = P^{-1} V_i
         H = np.zeros((m + 1, m))
         cs, sn = np.zeros(m), np.zeros(m)
         gvec = np.zeros(m + 1)
         gvec[0] = beta
         j = 0
         while j < m and steps < maxit:
-            w = applyG(applyPinv(V[j]))
+            w = applyG(Z[j])
+            t = applyPinv(w)                             # kept equal to P^{-1} w
             for i in range(j + 1):                       # modified Gram-Schmidt
-                H[i, j] = float(np.vdot(w, V[i]))
+                H[i, j] = float(np.vdot(w, Z[i]))        # <w, V_i> = w . P^{-1} V_i
                 w = w - H[i, j] * V[i]
-            hnext = float(np.linalg.norm(w))
+                t = t - H[i, j] * Z[i]
+            hnext = math.sqrt(max(float(np.vdot(w, t)), 0.0))
             H[j + 1, j] = hnext
             for i in range(j):                           # earlier rotations on the new column
                 a, c = H[i, j], H[i + 1, j]
@@ -359,14 +368,16 @@ def gmres(applyG, applyPinv, b, x0=None, rtol=1e-10, restart=30, maxit=1000, his
             steps += 1
             if history:
                 y = _back_substitute(H[:j, :j], gvec[:j])
-                hist.append(x + applyPinv(sum(y[i] * V[i] for i in range(j))))
+                hist.append(x + sum(y[i] * Z[i] for i in range(j)))
             if abs(gvec[j]) <= rtol * bnorm or hnext == 0.0:
                 break
             V.append(w / hnext)
+            Z.append(t / hnext)
         y = _back_substitute(H[:j, :j], gvec[:j])
-        x = x + applyPinv(sum(y[i] * V[i] for i in range(j)))
+        x = x + sum(y[i] * Z[i] for i in range(j))
         r = b - applyG(x)
-        beta = float(np.linalg.norm(r))
+        rz = applyPinv(r)
+        beta = math.sqrt(max(float(np.vdot(r, rz)), 0.0))
     ratio = beta / bnorm
     return (x, steps, ratio, cycles, hist) if history else (x, steps, ratio, cycles)
 

@@ -751,6 +751,62 @@ extern "C" sgn_status sgn_pcg(sgn_ctx* ctx, const sgn_layout* lay_c, const doubl
   return SGN_OK;
 }
 
+extern "C" sgn_status sgn_gmres(sgn_ctx* ctx, const sgn_layout* lay_c, const double* eta,
+                                const double* gradh, const sgn_precond* P, const double* b,
+                                double* x, double rtol, int restart, int maxit,
+                                sgn_pcg_info* info, sgn_stream stream) {
+  sgn_layout* lay = const_cast<sgn_layout*>(lay_c);
+  if (!ctx || check_layout(lay) || !eta || !gradh || !b || !x || !(rtol > 0.0) || maxit < 0 ||
+      restart < 1 || restart > SGN_GMRES_MAX_RESTART)
+    return fail(ctx, SGN_ERR_INVALID_ARG, "gmres args");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  sgn::GmresArgs a;
+  if (P) {
+    sgn_status st = upload_given(lay, P, s);
+    if (st) return st;
+    a.coef = lay->given;
+  } else {
+    cudaError_t e = lay->dim == 1
+                        ? sgn::launch_coeffs1d(lay->l1, eta, gradh, SGN_COEF_OPT, lay->rec, s)
+                        : sgn::launch_coeffs2d(lay->l2, eta, gradh, SGN_COEF_OPT, lay->rec, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gmres coefficients");
+    a.coef = lay->rec;
+  }
+  a.dim = lay->dim;
+  a.count = lay->count;
+  a.l1 = &lay->l1;
+  a.l2 = &lay->l2;
+  a.offsets = lay->offsets.data();
+  a.vec_len = (long long)lay->dim * lay->points;
+  a.tw64 = ctx->tw64;
+  a.eta = eta;
+  a.gradh = gradh;
+  a.b = b;
+  a.x = x;
+  a.rec = lay->rec;
+  a.rtol = rtol;
+  a.restart = restart;
+  a.maxit = maxit;
+  cudaError_t e = sgn::run_gmres(a, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "gmres");
+  std::vector<SolveRec> h;
+  sgn_status st = fetch_recs(lay, h, s);
+  if (st) return st;
+  sgn_status worst = SGN_OK;
+  for (int i = 0; i < lay->count; ++i) {
+    if (info) {
+      info[i].iters = h[i].iters;
+      info[i].refinements = h[i].refinements;
+      info[i].rel_resid_Ainv = h[i].ratio;
+      info[i].status = h[i].status;
+    }
+    if (h[i].status > worst) worst = (sgn_status)h[i].status;
+  }
+  if (worst != SGN_OK) return fail(ctx, worst, "gmres: some instance did not finish cleanly");
+  return SGN_OK;
+}
+
 extern "C" sgn_status sgn_rhs(sgn_ctx* ctx, const sgn_layout* lay, const double* eta,
                               const double* u, const double* h, const double* gradh,
                               double* f_eta, double* f_U, sgn_stream stream) {

@@ -113,4 +113,30 @@ cudaError_t launch_linimp_solve1d(const Layout1d& lay, const void* tw64, const S
                                   const void* res1_hat, const void* res0_hat, double c1,
                                   double c0, double* u, cudaStream_t s);
 
+struct Layout2d;
+
+// Restarted GMRES(restart) for G x = b, right-preconditioned by A, over every instance of a
+// 1d layout (l1, offsets [count + 1]) or the one instance of a 2d layout (l2); vec_len is
+// the packed vector length (d P).  coef: per-instance sigma, alpha (and a non-OK status
+// that finishes the instance at once); rec: reports (iters = Arnoldi steps, refinements =
+// cycles, ratio = final sqrt(r.A^{-1}r) / sqrt(b.A^{-1}b), status).  Host-driven; allocates its
+// workspace on the stream and synchronises it before returning.
+struct GmresArgs {
+  int dim = 1, count = 0;
+  const Layout1d* l1 = nullptr;
+  const Layout2d* l2 = nullptr;
+  const long long* offsets = nullptr;
+  long long vec_len = 0;
+  const void* tw64 = nullptr;
+  const double* eta = nullptr;
+  const double* gradh = nullptr;
+  const double* b = nullptr;
+  double* x = nullptr;
+  const SolveRec* coef = nullptr;
+  SolveRec* rec = nullptr;
+  double rtol = 1e-10;
+  int restart = 30, maxit = 1000;
+};
+cudaError_t run_gmres(const GmresArgs& a, cudaStream_t s);
+
 }  // namespace sgn

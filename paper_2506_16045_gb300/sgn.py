@@ -89,6 +89,8 @@ SIGNATURES = [
     ("sgn_precond_solve", C.c_int, [_VP, _VP, C.POINTER(SgnPrecond), _DP, _DP, _VP]),
     ("sgn_pcg", C.c_int, [_VP, _VP, _DP, _DP, C.POINTER(SgnPrecond), _DP, _DP, C.c_double,
                           C.c_int, C.c_int, C.POINTER(SgnPcgInfo), _VP]),
+    ("sgn_gmres", C.c_int, [_VP, _VP, _DP, _DP, C.POINTER(SgnPrecond), _DP, _DP, C.c_double,
+                            C.c_int, C.c_int, C.POINTER(SgnPcgInfo), _VP]),
     ("sgn_rhs", C.c_int, [_VP, _VP, _DP, _DP, _DP, _DP, _DP, _DP, _VP]),
     ("sgn_state_create", C.c_int, [_VP, _VP, _DP, _DP, _DP, _DP, _DP, C.POINTER(_VP)]),
     ("sgn_state_init", C.c_int, [_VP, _VP]),
@@ -307,6 +309,23 @@ def pcg(lay: Layout, eta, gradh, b, x, rtol=1e-12, maxit=1000, prec=PREC_FP64, P
         return None
     return [dict(iters=i.iters, refinements=i.refinements, ratio=i.rel_resid_Ainv,
                  status=i.status) for i in inf]
+
+
+def gmres(lay: Layout, eta, gradh, b, x, rtol=1e-10, restart=30, maxit=1000, P=None,
+          info=True, stream=None, check=True):
+    """sgn_gmres: restarted GMRES right-preconditioned by A, in the A^{-1} inner product (x
+    holds the initial guess).  Returns per-instance info dicts: iters = Arnoldi steps,
+    cycles, ratio = the final sqrt(r.A^{-1}r) / sqrt(b.A^{-1}b), status."""
+    inf = (SgnPcgInfo * lay.count)() if info else None
+    parr = _precond_array(lay, P) if P is not None else None
+    s = lay.ctx.lib.sgn_gmres(lay.ctx.h, lay.h, _ptr(eta), _ptr(gradh), parr, _ptr(b), _ptr(x),
+                              rtol, restart, maxit, inf, _stream(stream))
+    if check:
+        lay.ctx.check(s, "sgn_gmres")
+    if not info:
+        return None
+    return [dict(iters=i.iters, cycles=i.refinements, ratio=i.rel_resid_Ainv, status=i.status)
+            for i in inf]
 
 
 def pcg1d_noalloc(n, L, eta, gradh, b, x, rtol=1e-12, maxit=1000, prec=PREC_FP64, stream=None):

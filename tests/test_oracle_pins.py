@@ -516,26 +516,28 @@ def _dense_case(dim):
 
 @pytest.mark.parametrize("dim", [1, 2])
 def test_gmres_iterates_minimise_the_residual_over_the_krylov_space(dim):
-    """The k-th GMRES iterate from x0 = 0 minimises ||b - G x|| over x in
+    """The k-th GMRES iterate from x0 = 0 minimises sqrt(r.A^{-1}r), r = b - G x, over x in
     A^{-1} span{b, M b, ..., M^{k-1} b} with M = G A^{-1}: brute force with the dense
-    matrices of Def:MatrixM (no matrix-free operator, no Arnoldi) and a least-squares solve."""
+    matrices of Def:MatrixM (no matrix-free operator, no Arnoldi), a Cholesky factor
+    A = C C^T, and a least-squares solve of min ||C^{-1}(b - G Z c)||."""
     eta, gh, b, grid, c, Gd, Ad, shape = _dense_case(dim)
     x, steps, _, _, hist = O.gmres(lambda v: O.apply_G(eta, gh, v, grid),
                                    lambda v: O.apply_Ainv(v, c["sigma"], c["alpha"], grid),
                                    b, rtol=1e-14, restart=40, maxit=6, history=True)
     assert steps == 6 and len(hist) == 6
     Ainv = np.linalg.inv(Ad)
+    Ci = np.linalg.inv(np.linalg.cholesky(Ad))
     M = Gd @ Ainv
     bf = b.ravel()
     K = [bf]
     for k in range(1, 7):
         Q, _ = np.linalg.qr(np.stack(K, axis=1))
         Z = Ainv @ Q
-        coef, *_ = np.linalg.lstsq(Gd @ Z, bf, rcond=None)
+        coef, *_ = np.linalg.lstsq(Ci @ Gd @ Z, Ci @ bf, rcond=None)
         xb = Z @ coef
         assert np.linalg.norm(hist[k - 1].ravel() - xb) <= 1e-9 * np.linalg.norm(xb), k
         K.append(M @ K[-1])
-    res = [np.linalg.norm(bf - Gd @ h_.ravel()) for h_ in hist]
+    res = [np.linalg.norm(Ci @ (bf - Gd @ h_.ravel())) for h_ in hist]
     assert all(r1 <= r0 * (1 + 1e-12) for r0, r1 in zip(res, res[1:]))
 
 
@@ -574,9 +576,11 @@ def test_gmres_agrees_with_pcg_and_restarts_cost_steps():
     xp, _, _, c = O.solve_G(eta, hx, b, grid, rtol=1e-14, maxit=5000)
     x30, s30, r30, _, _ = O.gmres_G(eta, hx, b, grid, rtol=1e-11, restart=30)
     x5, s5, r5, cyc5, _ = O.gmres_G(eta, hx, b, grid, rtol=1e-11, restart=5, maxit=5000)
+    Ainv = lambda v: O.apply_Ainv(v, c["sigma"], c["alpha"], grid)
     for x, r in ((x30, r30), (x5, r5)):
         assert r <= 1e-11
-        assert np.linalg.norm(b - O.apply_G(eta, hx, x, grid)) <= 1e-11 * np.linalg.norm(b)
+        res = b - O.apply_G(eta, hx, x, grid)
+        assert math.sqrt(res @ Ainv(res)) <= 1e-11 * math.sqrt(b @ Ainv(b))
         assert np.linalg.norm(x - xp) <= 1e-11 * math.sqrt(c["kappa_ub"]) * 50 * np.linalg.norm(xp)
     assert s5 > s30 and cyc5 >= s5 // 5
     z, s0, r0, c0, _ = O.gmres_G(eta, hx, np.zeros(n), grid)
