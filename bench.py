@@ -684,12 +684,46 @@ def bench_robustness(sgn, ctx, torch, reps=5):
         bump.append({"a": a, "b": bb, "n": f"{n}^2", "kappa_ub": round(P[0]["kappa_ub"], 1),
                      "iters_fp64": info["iters"], "ms_fp64": round(ms, 3),
                      "iters_mixed": infom["iters"], "ms_mixed": round(msm, 3)})
+    # the GMRES option against PCG on the same problems (float64, rtol 1e-10 in the A^{-1}
+    # measure for both)
+    def timed_gmres(lay, eta, gh, b, npts, restart=30):
+        x = torch.zeros(npts, dtype=torch.float64, device="cuda")
+        info = sgn.gmres(lay, eta, gh, b, x, rtol=1e-10, restart=restart, maxit=20000)[0]
+        ts = []
+        for _ in range(reps):
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sgn.gmres(lay, eta, gh, b, x, rtol=1e-10, restart=restart, maxit=20000)
+            ts.append(time.perf_counter() - t0)
+        return float(np.median(ts)) * 1e3, info
+
+    gmres = []
+    for k in (10, 13, 14):
+        n = 2 ** k
+        _, h, eta, b = I.testproblem_1d(n, 1.0, 1.0)
+        lay = sgn.Layout(ctx, [sgn.Grid(1, n, 1.0)])
+        gh = grad_dev(lay, h, 1)
+        msg, ig = timed_gmres(lay, dev(eta), gh, dev(b), n)
+        msp, ip = timed(lay, dev(eta), gh, dev(b), n, 1e-10, sgn.PREC_FP64)
+        gmres.append({"case": f"Eq:Testproblem n={n}", "gmres30_ms": round(msg, 3),
+                      "gmres30_steps": ig["iters"], "gmres30_cycles": ig["cycles"],
+                      "pcg_fp64_ms": round(msp, 3), "pcg_iters": ip["iters"]})
+        lay.close()
+    for a, bb in ((1.0, 1.0), (1.0, 20.0)):
+        _, _, h, eta, rhs = I.elliptical_bump_2d(256, a, bb)
+        gh = grad_dev(lay2, h, 2)
+        msg, ig = timed_gmres(lay2, dev(eta), gh, dev(rhs), 2 * 256 * 256)
+        msp, ip = timed(lay2, dev(eta), gh, dev(rhs), 2 * 256 * 256, 1e-10, sgn.PREC_FP64)
+        gmres.append({"case": f"elliptical bump ({a:g},{bb:g}) 256^2", "gmres30_ms": round(msg, 3),
+                      "gmres30_steps": ig["iters"], "gmres30_cycles": ig["cycles"],
+                      "pcg_fp64_ms": round(msp, 3), "pcg_iters": ip["iters"]})
     return {"workload": "Eq:Testproblem (eta0 = h0 = 1) solve clock time for n = 2^5..2^14 "
                         "(fp64 rtol 1e-12, mixed rtol 1e-11; one instance per call, median of "
                         f"{reps}); eta0 / h0 sweep at n = 4096; square-wave depth, optimal vs "
                         "replacement coefficients at n = 512; 2d elliptical bump at 256^2",
             "clock_vs_n": clock, "sweep_n4096": sweep, "square_wave_n512": square,
-            "elliptical_bump_2d": bump}
+            "elliptical_bump_2d": bump, "gmres_vs_pcg": gmres}
 
 
 def bench_manufactured(sgn, ctx, torch, n=256, t_final=1.0):
