@@ -176,79 +176,93 @@ __global__ void k_axpy1d(const Inst1d* __restrict__ insts, const double* __restr
   }
 }
 
-// SBDF2: res^ = (sigma + alpha k^2) u^ - (G u - U)^  (half spectrum, float64)
-template <int NT, int MAXB>
-__global__ void __launch_bounds__(NT, 1) k_linimp_res1d(const Inst1d* __restrict__ insts,
-                                                     const int* __restrict__ ids,
-                                                     cplx<double>* big,
-                                                     const cplx<double>* __restrict__ tw,
-                                                     const SolveRec* __restrict__ A,
-                                                     const double* __restrict__ eta_all,
-                                                     const double* __restrict__ hx_all,
-                                                     const double* __restrict__ u_all,
-                                                     const double* __restrict__ U_all,
-                                                     cplx<double>* __restrict__ res,
-                                                     cplx<double>* __restrict__ ws) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  cplx<double>* buf = big ? big + ((size_t)blockIdx.x << kMaxLog1d)
-                          : reinterpret_cast<cplx<double>*>(smem);
-  const int id = ids[blockIdx.x];
-  const Inst1d I = insts[id];
-  const int n = I.n, h = n >> 1;
-  const double sigma = A[id].sigma, alpha = A[id].alpha;
-  const long long S = h + 1;
-  cplx<double>* uh = ws + I.ws + S;
-  cplx<double>* out = res + I.ws / kWsVectors;
-  // u^ from a transform of u alone; U enters inside the matvec (w - U, so the matvec yields
-  // (G u - U)^).  Packed as u + i U, u^ would carry U's rounding (~eps ||U||), and U = G u
-  // can outweigh u by eta^3 k^2 / 3, which the right-hand side's third derivatives pass on.
-  for (int j = threadIdx.x; j < n; j += NT) buf[j] = mk(u_all[I.off + j], 0.0);
-  __syncthreads();
-  cta_fft<double, NT, MAXB>(buf, n, I.log2n, false, tw);
-  for (int m = threadIdx.x; m <= h; m += NT)
-    uh[m] = (m == 0 || m == h) ? mk(buf[m].x, 0.0) : buf[m];   // real modes of a real field
-  __syncthreads();
-  const Spec<double> sp = make_spec<double>(n, I.L, sigma, alpha);
-  spectral_matvec<double, NT, MAXB>(buf, sp, I.log2n, [&](int m) { return uh[m]; },
-                                    CoefGlobal64{eta_all + I.off, hx_all + I.off}, nullptr, tw,
-                                    U_all + I.off);
-  for (int m = threadIdx.x; m <= h; m += NT) {
-    double k = sp.k(m);
-    cplx<double> gu = gv_mode(buf, m, n, k);       // (G u - U)^_m
-    out[m] = uh[m] * (sigma + alpha * k * k) - gu;
+// double-float coefficients of Def:MatrixM computed from float64 eta and h_x on the fly
+struct CoefGlobalDF {
+  const double* eta;
+  const double* hx;
+  __device__ __forceinline__ void operator()(int j, df& c1, df& c2, df& c3) const {
+    double e = eta[j], g = hx[j];
+    c1 = df(e * (1.0 + g * g));
+    c2 = df(0.5 * e * e * g);
+    c3 = df(e * e * e * (1.0 / 3.0));
   }
-}
+};
 
-// SBDF2: u = F^{-1}[(c1 res1^ + c0 res0^) / (sigma + alpha k^2)]
-template <int NT, int MAXB>
-__global__ void __launch_bounds__(NT, 1) k_linimp_solve1d(const Inst1d* __restrict__ insts,
-                                                       const int* __restrict__ ids,
-                                                       cplx<double>* big,
-                                                       const cplx<double>* __restrict__ tw,
-                                                       const SolveRec* __restrict__ A,
-                                                       const cplx<double>* __restrict__ res1,
-                                                       const cplx<double>* __restrict__ res0,
-                                                       double c1, double c0,
-                                                       double* __restrict__ u_all) {
+template <typename T>
+struct CoefFor;
+template <>
+struct CoefFor<double> {
+  using type = CoefGlobal64;
+};
+template <>
+struct CoefFor<df> {
+  using type = CoefGlobalDF;
+};
+
+// One SBDF2 velocity update in one launch, transforms in T (float64, or double-float for
+// the mixed path):
+//   res1^ = (sigma + alpha k^2) u^ - (G u - U)^           stored as a half spectrum (float64)
+//   u    <- F^{-1}[(c1 res1^ + c0 res0^) / (sigma + alpha k^2)]   (SOLVE only)
+// u is read at the start and, with SOLVE, overwritten at the end by the same CTA, so the
+// caller's buffer takes the new level in place.  Without SOLVE (the start-up level) only
+// res1^ is produced.  The per-mode combinations run in float64.
+template <typename T, int NT, int MAXB, bool SOLVE>
+__global__ void __launch_bounds__(NT, 1) k_linimp_step1d(const Inst1d* __restrict__ insts,
+                                                      const int* __restrict__ ids,
+                                                      cplx<double>* big,
+                                                      const cplx<T>* __restrict__ tw,
+                                                      const SolveRec* __restrict__ A,
+                                                      const double* __restrict__ eta_all,
+                                                      const double* __restrict__ hx_all,
+                                                      double* __restrict__ u_all,
+                                                      const double* __restrict__ U_all,
+                                                      const cplx<double>* __restrict__ res0,
+                                                      cplx<double>* __restrict__ res1,
+                                                      double c1, double c0,
+                                                      cplx<double>* __restrict__ ws) {
   extern __shared__ __align__(16) unsigned char smem[];
-  cplx<double>* buf = big ? big + ((size_t)blockIdx.x << kMaxLog1d)
-                          : reinterpret_cast<cplx<double>*>(smem);
+  cplx<T>* buf = big ? reinterpret_cast<cplx<T>*>(big + ((size_t)blockIdx.x << kMaxLog1d))
+                     : reinterpret_cast<cplx<T>*>(smem);
   const int id = ids[blockIdx.x];
   const Inst1d I = insts[id];
   const int n = I.n, h = n >> 1;
-  const double kunit = 2.0 * kPi / I.L;
   const double sigma = A[id].sigma, alpha = A[id].alpha;
+  const double kunit = 2.0 * kPi / I.L;
   const long long hs = I.ws / kWsVectors;
+  cplx<double>* uh = ws + I.ws + (h + 1);
+  for (int j = threadIdx.x; j < n; j += NT) buf[j] = mk(num<T>(u_all[I.off + j]), num<T>(0.0));
+  __syncthreads();
+  cta_fft<T, NT, MAXB>(buf, n, I.log2n, false, tw);
   for (int m = threadIdx.x; m <= h; m += NT) {
-    double k = (m == h) ? 0.0 : kunit * (double)m;
-    cplx<double> v = (res1[hs + m] * c1 + res0[hs + m] * c0) * (1.0 / (sigma + alpha * k * k));
-    buf[m] = v;
-    if (m > 0 && m < h) buf[n - m] = conj(v);
+    const cplx<T> v = buf[m];
+    uh[m] = mk(to_f64(v.x), (m == 0 || m == h) ? 0.0 : to_f64(v.y));   // real DC / Nyquist
   }
   __syncthreads();
-  cta_fft<double, NT, MAXB>(buf, n, I.log2n, true, tw);
+  const Spec<T> sp = make_spec<T>(n, I.L, sigma, alpha);
+  spectral_matvec<T, NT, MAXB>(
+      buf, sp, I.log2n, [&](int m) { return mk(num<T>(uh[m].x), num<T>(uh[m].y)); },
+      typename CoefFor<T>::type{eta_all + I.off, hx_all + I.off}, nullptr, tw, U_all + I.off);
+  // mode m owns buf[m] and buf[n - m]: it reads both (gv_mode) before writing both
+  for (int m = threadIdx.x; m <= h; m += NT) {
+    const double k = (m == h) ? 0.0 : kunit * (double)m;
+    const cplx<T> g = gv_mode(buf, m, n, sp.k(m));             // (G u - U)^_m
+    const double sym = sigma + alpha * k * k;
+    cplx<double> r = mk(uh[m].x * sym - to_f64(g.x), uh[m].y * sym - to_f64(g.y));
+    if (m == 0 || m == h) r.y = 0.0;
+    res1[hs + m] = r;
+    if (SOLVE) {
+      const cplx<double> p = res0[hs + m];
+      cplx<double> v = mk((c1 * r.x + c0 * p.x) / sym, (c1 * r.y + c0 * p.y) / sym);
+      if (m == 0 || m == h) v.y = 0.0;
+      buf[m] = mk(num<T>(v.x), num<T>(v.y));
+      if (m > 0 && m < h) buf[n - m] = mk(num<T>(v.x), num<T>(-v.y));
+    }
+  }
+  if (!SOLVE) return;
+  __syncthreads();
+  cta_fft<T, NT, MAXB>(buf, n, I.log2n, true, tw);
   const double inv_n = 1.0 / n;
-  for (int j = threadIdx.x; j < n; j += NT) u_all[I.off + j] = buf[j].x * inv_n;
+  for (int j = threadIdx.x; j < n; j += NT) u_all[I.off + j] = to_f64(buf[j].x) * inv_n;
 }
 
 }  // namespace
@@ -331,40 +345,35 @@ cudaError_t launch_axpy1d(const Layout1d& lay, const double* dt, double* out, co
   return cudaGetLastError();
 }
 
-cudaError_t launch_linimp_res1d(const Layout1d& lay, const void* tw64, const SolveRec* A,
-                                   const double* eta, const double* hx, const double* u,
-                                   const double* U, void* res_hat, void* ws, cudaStream_t s) {
-  auto tw = static_cast<const cplx<double>*>(tw64);
+cudaError_t launch_linimp_step1d(const Layout1d& lay, const void* tw64, const void* tw32,
+                                 int precision, const SolveRec* A, const double* eta,
+                                 const double* hx, double* u, const double* U,
+                                 const void* res0_hat, void* res1_hat, double c1, double c0,
+                                 bool solve, void* ws, cudaStream_t s) {
+  const bool dfp = precision == SGN_PREC_MIXED;
+  const void* twT = dfp ? static_cast<const void*>(static_cast<const char*>(tw32) + kTw32Bytes)
+                        : tw64;
   return for_each_class(lay, s, [&](auto NTc, auto MBc, int l, int first, int num, cudaStream_t s) {
     constexpr int NT = decltype(NTc)::value, MB = decltype(MBc)::value;
     const bool gl = l > kSmemLog1d;                // transform buffer in global scratch
-    const size_t sm = gl ? 0 : (size_t)16 << l;
+    const size_t sm = gl ? 0 : (size_t)16 << l;    // cplx<double> and cplx<df>: 16 bytes
     cplx<double>* big = gl ? static_cast<cplx<double>*>(lay.big) : nullptr;
-    auto k = k_linimp_res1d<NT, MB>;
-    cudaError_t e = set_smem(k, sm);
-    if (e) return e;
-    k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, big, tw, A, eta, hx, u, U,
-                          static_cast<cplx<double>*>(res_hat), static_cast<cplx<double>*>(ws));
-    return cudaGetLastError();
-  });
-}
-
-cudaError_t launch_linimp_solve1d(const Layout1d& lay, const void* tw64, const SolveRec* A,
-                                  const void* res1_hat, const void* res0_hat, double c1,
-                                  double c0, double* u, cudaStream_t s) {
-  auto tw = static_cast<const cplx<double>*>(tw64);
-  return for_each_class(lay, s, [&](auto NTc, auto MBc, int l, int first, int num, cudaStream_t s) {
-    constexpr int NT = decltype(NTc)::value, MB = decltype(MBc)::value;
-    const bool gl = l > kSmemLog1d;                // transform buffer in global scratch
-    const size_t sm = gl ? 0 : (size_t)16 << l;
-    cplx<double>* big = gl ? static_cast<cplx<double>*>(lay.big) : nullptr;
-    auto k = k_linimp_solve1d<NT, MB>;
-    cudaError_t e = set_smem(k, sm);
-    if (e) return e;
-    k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, big, tw, A,
-                          static_cast<const cplx<double>*>(res1_hat),
-                          static_cast<const cplx<double>*>(res0_hat), c1, c0, u);
-    return cudaGetLastError();
+    auto run = [&](auto kern, auto twp) -> cudaError_t {
+      cudaError_t e = set_smem(kern, sm);
+      if (e) return e;
+      kern<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, big, twp, A, eta, hx, u, U,
+                               static_cast<const cplx<double>*>(res0_hat),
+                               static_cast<cplx<double>*>(res1_hat), c1, c0,
+                               static_cast<cplx<double>*>(ws));
+      return cudaGetLastError();
+    };
+    auto twd = static_cast<const cplx<double>*>(twT);
+    auto twf = static_cast<const cplx<df>*>(twT);
+    if (dfp)
+      return solve ? run(k_linimp_step1d<df, NT, MB, true>, twf)
+                   : run(k_linimp_step1d<df, NT, MB, false>, twf);
+    return solve ? run(k_linimp_step1d<double, NT, MB, true>, twd)
+                 : run(k_linimp_step1d<double, NT, MB, false>, twd);
   });
 }
 

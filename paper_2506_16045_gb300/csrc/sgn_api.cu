@@ -1406,13 +1406,16 @@ extern "C" sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nstep
   st->last = s;
   const int d = st->d;
   const long long P = st->P, V = d * P;
+  const bool one_d = st->lay->dim == 1;
+  // 1d: the residual and the A-solve run as one launch (transforms in double-float on the
+  // mixed path) that writes the new u in place; 2d: residual and solve launches.
   auto res_of = [&](const double* eta, const double* u, const double* U, void* out) -> sgn_status {
     cudaError_t e =
-        st->lay->dim == 1
-            ? sgn::launch_linimp_res1d(st->lay->l1, ctx->tw64, st->A_fixed, eta, st->gradh, u, U,
-                                       out, st->lay->ws, s)
-            : sgn::launch_linimp_res2d(st->lay->l2, ctx->tw64, st->A_fixed, eta, st->gradh, u, U,
-                                       out, s);
+        one_d ? sgn::launch_linimp_step1d(st->lay->l1, ctx->tw64, ctx->tw32, st->prec,
+                                          st->A_fixed, eta, st->gradh, const_cast<double*>(u),
+                                          U, nullptr, out, 0.0, 0.0, false, st->lay->ws, s)
+              : sgn::launch_linimp_res2d(st->lay->l2, ctx->tw64, st->A_fixed, eta, st->gradh, u,
+                                         U, out, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "linimp residual");
     return SGN_OK;
   };
@@ -1421,7 +1424,6 @@ extern "C" sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nstep
       // start-up: keep level n, take one RK4 step to level n+1
       SGN_TRY(copy_field(st, st->eta_p, st->eta, P, s));
       SGN_TRY(copy_field(st, st->U_p, st->U, V, s));
-      SGN_TRY(copy_field(st, st->u_p, st->u, V, s));
       SGN_TRY(rhs_at(st, st->eta, st->u, st->he[0], st->hU[0], s));
       SGN_TRY(res_of(st->eta, st->u, st->U, st->res0));
       SGN_TRY(rk4_once(st, opts, s));
@@ -1429,26 +1431,32 @@ extern "C" sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nstep
       st->hist = HIST_SBDF2;
       continue;
     }
-    // f_{n+1} into he[1], res_{n+1} into res1
+    // f_{n+1} into he[1] (before u is overwritten), then res_{n+1} into res1 and, in 1d, the
+    // new u in place
     SGN_TRY(rhs_at(st, st->eta, st->u, st->he[1], st->hU[1], s));
-    SGN_TRY(res_of(st->eta, st->u, st->U, st->res1));
+    if (one_d) {
+      cudaError_t e = sgn::launch_linimp_step1d(st->lay->l1, ctx->tw64, ctx->tw32, st->prec,
+                                                st->A_fixed, st->eta, st->gradh, st->u, st->U,
+                                                st->res0, st->res1, 2.0, -1.0, true,
+                                                st->lay->ws, s);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "linimp step");
+    } else {
+      SGN_TRY(res_of(st->eta, st->u, st->U, st->res1));
+    }
     SGN_TRY(lincomb(st, st->eta_s, {{st->eta, 4.0 / 3.0}, {st->eta_p, -1.0 / 3.0}},
                     {{st->he[1], 4.0 / 3.0}, {st->he[0], -2.0 / 3.0}}, 1, s, st->U_s,
                     {{st->U, 4.0 / 3.0}, {st->U_p, -1.0 / 3.0}},
                     {{st->hU[1], 4.0 / 3.0}, {st->hU[0], -2.0 / 3.0}}, d));
-    cudaError_t e =
-        st->lay->dim == 1
-            ? sgn::launch_linimp_solve1d(st->lay->l1, ctx->tw64, st->A_fixed, st->res1, st->res0,
-                                         2.0, -1.0, st->u_s, s)
-            : sgn::launch_linimp_solve2d(st->lay->l2, ctx->tw64, st->A_fixed, st->res1, st->res0,
-                                         2.0, -1.0, st->u_s, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "linimp solve");
+    if (!one_d) {
+      cudaError_t e = sgn::launch_linimp_solve2d(st->lay->l2, ctx->tw64, st->A_fixed, st->res1,
+                                                 st->res0, 2.0, -1.0, st->u_s, s);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "linimp solve");
+      SGN_TRY(copy_field(st, st->u, st->u_s, V, s));
+    }
     SGN_TRY(copy_field(st, st->eta_p, st->eta, P, s));
     SGN_TRY(copy_field(st, st->U_p, st->U, V, s));
-    SGN_TRY(copy_field(st, st->u_p, st->u, V, s));
     SGN_TRY(copy_field(st, st->eta, st->eta_s, P, s));
     SGN_TRY(copy_field(st, st->U, st->U_s, V, s));
-    SGN_TRY(copy_field(st, st->u, st->u_s, V, s));
     std::swap(st->he[0], st->he[1]);
     std::swap(st->hU[0], st->hU[1]);
     std::swap(st->res0, st->res1);

@@ -104,14 +104,14 @@ cudaError_t launch_rhs1d_ux(const Layout1d& lay, const void* tw64, const void* t
 cudaError_t launch_axpy1d(const Layout1d& lay, const double* dt, double* out, const double* base,
                           int nterms, const double* const* f, const double* c, double scale,
                           cudaStream_t s);
-// SBDF2 pieces: res_hat = (sigma + alpha k^2) u_hat - (G u)_hat + U_hat, stored as half spectra
-cudaError_t launch_linimp_res1d(const Layout1d& lay, const void* tw64, const SolveRec* A,
-                                const double* eta, const double* hx, const double* u,
-                                const double* U, void* res_hat, void* ws, cudaStream_t s);
-// u = A^{-1} iFFT(c1 res1_hat + c0 res0_hat)
-cudaError_t launch_linimp_solve1d(const Layout1d& lay, const void* tw64, const SolveRec* A,
-                                  const void* res1_hat, const void* res0_hat, double c1,
-                                  double c0, double* u, cudaStream_t s);
+// SBDF2 velocity update in one launch (transforms in float64, or double-float for
+// SGN_PREC_MIXED): res1_hat = (sigma + alpha k^2) u_hat - (G u - U)_hat, and with `solve`
+// u <- A^{-1} iFFT(c1 res1_hat + c0 res0_hat) in place.
+cudaError_t launch_linimp_step1d(const Layout1d& lay, const void* tw64, const void* tw32,
+                                 int precision, const SolveRec* A, const double* eta,
+                                 const double* hx, double* u, const double* U,
+                                 const void* res0_hat, void* res1_hat, double c1, double c0,
+                                 bool solve, void* ws, cudaStream_t s);
 
 struct Layout2d;
 
