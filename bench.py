@@ -264,11 +264,13 @@ class Ensemble:
         self.st.init()
 
     def autotune(self):
-        """Kernel forms (one CTA or a two-CTA cluster per instance) of the n = 4096 and 8192
-        classes, timed on RK4 steps of this ensemble; the state is restored."""
+        """Kernel forms (one CTA or a two-CTA cluster per instance, for the solve and the
+        right-hand side separately) of the n = 4096 and 8192 classes, timed on RK4 steps of
+        this ensemble; the state is restored."""
         self.tune_ms = self.st.autotune(self.dts, rtol=RTOL, maxit=4000,
                                         prec=self.sgn.PREC_MIXED)
-        self.forms = {str(1 << l2): self.lay.form(l2) for l2 in (12, 13)}
+        self.forms = {str(1 << l2): dict(zip(("solve", "rhs"), self.lay.forms(l2)))
+                      for l2 in (12, 13)}
 
     def step(self, prec, n=1):
         self.st.rk4(self.dts, n, rtol=RTOL, maxit=4000, prec=prec)

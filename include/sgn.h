@@ -119,6 +119,13 @@ long long sgn_layout_points(const sgn_layout* lay);
  * States step with the new forms from their next step. */
 sgn_status sgn_layout_set_form(sgn_layout* lay, int log2n, int ctas);
 sgn_status sgn_layout_get_form(const sgn_layout* lay, int log2n, int* ctas);
+/* The same with separate forms for the solve and the right-hand side of the class (the
+ * solve hands u_x to the right-hand side in natural point order under either form, so any
+ * pair is valid).  sgn_layout_set_form(l, c) is set_forms(l, c, c); get_form reports the
+ * solve's form. */
+sgn_status sgn_layout_set_forms(sgn_layout* lay, int log2n, int solve_ctas, int rhs_ctas);
+sgn_status sgn_layout_get_forms(const sgn_layout* lay, int log2n, int* solve_ctas,
+                                int* rhs_ctas);
 
 /* offsets[0..count]: start of each instance in a packed scalar array (host array). */
 sgn_status sgn_layout_offsets(const sgn_layout* lay, long long* offsets);
@@ -259,8 +266,9 @@ sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nsteps, const sg
 #define SGN_MAX_FORCING 16
 sgn_status sgn_state_set_forcing(sgn_state* st, int nterms, const double* phi_eta,
                                  const double* phi_U, const double* omega, const double* theta);
-/* Autotuner of the layout's kernel forms (sgn_layout_set_form) on this state's own
- * problem: for every combination of forms of the n = 4096 and 8192 classes, one untimed
+/* Autotuner of the layout's kernel forms (sgn_layout_set_forms) on this state's own
+ * problem: for every combination of forms of the n = 4096 and 8192 classes (solve and
+ * right-hand side chosen separately: up to 16 combinations), one untimed
  * and two timed RK4 steps with these dt (HOST [count]) and options, each combination from
  * the same state, and the fastest combination stays set on the layout.  The state (eta, U,
  * u, time, counters) is restored afterwards, so tuning leaves no trace on the solution.

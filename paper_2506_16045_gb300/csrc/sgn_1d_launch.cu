@@ -38,18 +38,22 @@ extern template cudaError_t rhs1d_launch<14, 2>(const RhsArgs&, int, int, cudaSt
 namespace {
 
 // The form of size class LG in this layout: one CTA per instance, or a two-CTA cluster
-// (n = 4096 and 8192 by choice, n = 16384 always).
+// (n = 4096 and 8192 by choice, for the solve and the right-hand side separately;
+// n = 16384 always).  The solve's u_x hand-off is stored in natural point order by either
+// form, so the two kernels may take different forms.
 struct PcgKernels {
   template <int LG, int CL>
   static cudaError_t go(const PcgArgs& a, int first, int num, cudaStream_t s) {
     return pcg1d_launch<LG, CL>(a, first, num, s);
   }
+  static int ctas(const Layout1d& lay, int l) { return lay.ctas(l); }
 };
 struct RhsKernels {
   template <int LG, int CL>
   static cudaError_t go(const RhsArgs& a, int first, int num, cudaStream_t s) {
     return rhs1d_launch<LG, CL>(a, first, num, s);
   }
+  static int ctas(const Layout1d& lay, int l) { return lay.rhs_ctas(l); }
 };
 
 template <int LG, typename K, typename Args>
@@ -58,7 +62,7 @@ cudaError_t launch_form(const Layout1d& lay, const Args& a, int first, int num, 
   if constexpr (LG > kSmemLog1d) {
     return K::template go<LG, 2>(a, first, num, s);
   } else if constexpr (LG >= kClusterLog1d) {
-    return lay.ctas(LG) == 2 ? K::template go<LG, 2>(a, first, num, s)
+    return K::ctas(lay, LG) == 2 ? K::template go<LG, 2>(a, first, num, s)
                              : K::template go<LG, 1>(a, first, num, s);
   } else {
     return K::template go<LG, 1>(a, first, num, s);

@@ -559,24 +559,41 @@ extern "C" void sgn_layout_destroy(sgn_layout* lay) {
 
 extern "C" long long sgn_layout_points(const sgn_layout* lay) { return lay ? lay->points : -1; }
 
-extern "C" sgn_status sgn_layout_set_form(sgn_layout* lay, int log2n, int ctas) {
+extern "C" sgn_status sgn_layout_set_forms(sgn_layout* lay, int log2n, int solve_ctas,
+                                           int rhs_ctas) {
+  auto bad = [](int c) { return c != 1 && c != 2; };
   if (check_layout(lay) || lay->dim != 1 || log2n < 3 || log2n > sgn::kMaxLog1d ||
-      (ctas != 1 && ctas != 2))
+      bad(solve_ctas) || bad(rhs_ctas))
     return fail(lay ? lay->ctx : nullptr, SGN_ERR_INVALID_ARG, "set_form args");
-  if ((ctas == 2 && log2n < sgn::kClusterLog1d) || (ctas == 1 && log2n > sgn::kSmemLog1d))
-    return fail(lay->ctx, SGN_ERR_UNSUPPORTED_SIZE, "no such form for this size");
-  if (lay->l1.ctas(log2n) != ctas) {
-    lay->l1.form[log2n] = ctas;
-    lay->l1.gen += 1;
+  for (int c : {solve_ctas, rhs_ctas})
+    if ((c == 2 && log2n < sgn::kClusterLog1d) || (c == 1 && log2n > sgn::kSmemLog1d))
+      return fail(lay->ctx, SGN_ERR_UNSUPPORTED_SIZE, "no such form for this size");
+  sgn::Layout1d& L = lay->l1;
+  if (L.ctas(log2n) != solve_ctas || L.rhs_ctas(log2n) != rhs_ctas) {
+    L.form[log2n] = solve_ctas;
+    L.rform[log2n] = rhs_ctas;
+    L.gen += 1;
   }
   return SGN_OK;
 }
 
-extern "C" sgn_status sgn_layout_get_form(const sgn_layout* lay, int log2n, int* ctas) {
-  if (check_layout(lay) || lay->dim != 1 || !ctas || log2n < 3 || log2n > sgn::kMaxLog1d)
+extern "C" sgn_status sgn_layout_set_form(sgn_layout* lay, int log2n, int ctas) {
+  return sgn_layout_set_forms(lay, log2n, ctas, ctas);
+}
+
+extern "C" sgn_status sgn_layout_get_forms(const sgn_layout* lay, int log2n, int* solve_ctas,
+                                           int* rhs_ctas) {
+  if (check_layout(lay) || lay->dim != 1 || !solve_ctas || !rhs_ctas || log2n < 3 ||
+      log2n > sgn::kMaxLog1d)
     return SGN_ERR_INVALID_ARG;
-  *ctas = lay->l1.ctas(log2n);
+  *solve_ctas = lay->l1.ctas(log2n);
+  *rhs_ctas = lay->l1.rhs_ctas(log2n);
   return SGN_OK;
+}
+
+extern "C" sgn_status sgn_layout_get_form(const sgn_layout* lay, int log2n, int* ctas) {
+  int r = 0;
+  return sgn_layout_get_forms(lay, log2n, ctas, &r);
 }
 
 namespace {
@@ -1540,13 +1557,20 @@ extern "C" sgn_status sgn_state_autotune(sgn_state* st, const double* dt, const 
     cudaGetLastError();
     r = fail(ctx, SGN_ERR_CUDA, "autotune events");
   }
-  // every combination of forms over the classes, from the same state: one untimed RK4 step
-  // (loads the kernels), then two timed (direct launches: no graph capture in the timing)
-  const int combos = 1 << (int)cls.size();
+  // every combination of forms over the classes (solve and right-hand side separately),
+  // from the same state: one untimed RK4 step (loads the kernels), then two timed (direct
+  // launches: no graph capture in the timing)
+  auto apply = [&](int c) {
+    for (size_t i = 0; i < cls.size(); ++i) {
+      L.form[cls[i]] = (c >> (2 * i)) & 1 ? 2 : 1;
+      L.rform[cls[i]] = (c >> (2 * i + 1)) & 1 ? 2 : 1;
+    }
+  };
+  const int combos = 1 << (2 * (int)cls.size());
   int best = 0;
   float best_t = 0.0f;
   for (int c = 0; c < combos && !r; ++c) {
-    for (size_t i = 0; i < cls.size(); ++i) L.form[cls[i]] = (c >> i) & 1 ? 2 : 1;
+    apply(c);
     r = rk4_once(st, opts, s);
     if (!r) r = copy3(false);
     if (!r && cudaEventRecord(e0, s) != cudaSuccess) r = cuda_fail(ctx, cudaGetLastError(), "autotune");
@@ -1561,7 +1585,7 @@ extern "C" sgn_status sgn_state_autotune(sgn_state* st, const double* dt, const 
       best_t = ms;
     }
   }
-  for (size_t i = 0; i < cls.size(); ++i) L.form[cls[i]] = (best >> i) & 1 ? 2 : 1;
+  apply(best);
   L.gen += 1;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);

@@ -53,12 +53,15 @@ struct Layout1d {
   // float64 transform buffers (n complex doubles per instance) of the cta_fft kernels for
   // the instances above kSmemLog1d, indexed by position in their size class
   void* big = nullptr;
-  // CTAs per instance of each size class's solve and right-hand side (0: the default, one
-  // CTA up to kSmemLog1d and two above); set_form / autotune change it for the classes from
-  // kClusterLog1d, and `gen` counts the changes (captured step graphs hold the old forms)
+  // CTAs per instance of each size class's solve (form) and right-hand side (rform; 0: the
+  // default, one CTA up to kSmemLog1d and two above, and the right-hand side as the solve);
+  // set_form(s) / autotune change them for the classes from kClusterLog1d, and `gen` counts
+  // the changes (captured step graphs hold the old forms)
   int form[16] = {0};
+  int rform[16] = {0};                 // the right-hand side's own form (0: as the solve's)
   int gen = 0;
   int ctas(int l) const { return form[l] ? form[l] : (l > kSmemLog1d ? 2 : 1); }
+  int rhs_ctas(int l) const { return rform[l] ? rform[l] : ctas(l); }
   // side streams and events for running size classes concurrently (null: one stream)
   cudaStream_t side[16] = {nullptr};
   cudaEvent_t fork = nullptr;

@@ -83,6 +83,8 @@ SIGNATURES = [
     ("sgn_layout_offsets", C.c_int, [_VP, C.POINTER(C.c_longlong)]),
     ("sgn_layout_set_form", C.c_int, [_VP, C.c_int, C.c_int]),
     ("sgn_layout_get_form", C.c_int, [_VP, C.c_int, C.POINTER(C.c_int)]),
+    ("sgn_layout_set_forms", C.c_int, [_VP, C.c_int, C.c_int, C.c_int]),
+    ("sgn_layout_get_forms", C.c_int, [_VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("sgn_spectral_grad", C.c_int, [_VP, _VP, _DP, _DP, _VP]),
     ("sgn_precond_coeffs", C.c_int, [_VP, _VP, _DP, _DP, C.c_int, C.POINTER(SgnPrecond), _VP]),
     ("sgn_apply_operator", C.c_int, [_VP, _VP, _DP, _DP, _DP, _DP, _VP]),
@@ -254,6 +256,18 @@ class Layout:
         self.ctx.check(self.ctx.lib.sgn_layout_get_form(self.h, log2n, C.byref(c)),
                        "sgn_layout_get_form")
         return c.value
+
+    def set_forms(self, log2n, solve_ctas, rhs_ctas):
+        """Separate forms for the class's solve and right-hand side."""
+        self.ctx.check(self.ctx.lib.sgn_layout_set_forms(self.h, log2n, solve_ctas, rhs_ctas),
+                       "sgn_layout_set_forms")
+
+    def forms(self, log2n):
+        """(solve CTAs, right-hand-side CTAs) per instance of the class n = 2^log2n."""
+        a, b = C.c_int(), C.c_int()
+        self.ctx.check(self.ctx.lib.sgn_layout_get_forms(self.h, log2n, C.byref(a), C.byref(b)),
+                       "sgn_layout_get_forms")
+        return a.value, b.value
 
     def close(self):
         if self.h:

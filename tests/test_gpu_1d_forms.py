@@ -94,6 +94,37 @@ def test_cluster_form_matches_oracle(S, log2n):
         assert rel(unpack(host(fU), lay.offsets)[i], rU) < max(1e-13, 20 * rel(pU, rU))
 
 
+@pytest.mark.parametrize("solve_ctas,rhs_ctas", [(1, 2), (2, 1)])
+def test_mixed_forms_rk4_match_oracle(S, solve_ctas, rhs_ctas):
+    """Solve and right-hand side on different forms (the solve's u_x hand-off crosses from
+    one form to the other): RK4 on n = 4096 and 8192 instances against the oracle."""
+    sgn, ctx = S
+    insts = [I.shelf_case(n=n, L=200.0, a=0.3, x0=40.0, r=0.5, xs=45.0,
+                          dt=0.25 * (200.0 / n) / np.sqrt(9.81 * 1.3)) for n in (4096, 8192)]
+    lay = sgn.Layout(ctx, [sgn.Grid(1, c.n, c.L, g=c.g) for c in insts])
+    for l2 in (12, 13):
+        lay.set_forms(l2, solve_ctas, rhs_ctas)
+        assert lay.forms(l2) == (solve_ctas, rhs_ctas) and lay.form(l2) == solve_ctas
+    eta = dev(pack([c.eta for c in insts]))
+    u = dev(pack([c.u for c in insts]))
+    h = dev(pack([c.h for c in insts]))
+    U, gh = torch.zeros_like(eta), torch.zeros_like(eta)
+    st = sgn.State(lay, eta, U, u, h, gh)
+    st.init()
+    for prec, tol in ((sgn.PREC_FP64, 1e-9), (sgn.PREC_MIXED, 1e-6)):
+        eta.copy_(dev(pack([c.eta for c in insts])))
+        u.copy_(dev(pack([c.u for c in insts])))
+        st.init()
+        st.rk4([c.dt for c in insts], 3, rtol=1e-11 if prec == sgn.PREC_MIXED else 1e-13,
+               maxit=4000, prec=prec)
+        he, hu = unpack(host(eta), lay.offsets), unpack(host(u), lay.offsets)
+        for i, c in enumerate(insts):
+            ref = O.init_state(c.eta, c.u, c.h, O.make_grid(1, c.n, c.L, c.g))
+            O.run_rk4(ref, c.dt, 3, 1e-13)
+            assert rel(he[i] - c.h, ref.eta - c.h) < tol and rel(hu[i], ref.u) < tol, (prec, c.n)
+    st.close()
+
+
 def _rk4(sgn, ctx, insts, forms, plan, prec):
     """RK4 on a fresh state; plan = [(forms to set, steps), ...] applied in order."""
     lay = sgn.Layout(ctx, [sgn.Grid(1, c.n, c.L, g=c.g) for c in insts])
@@ -139,8 +170,8 @@ def test_autotune_on_a_state_keeps_valid_forms_and_restores_the_state(S):
 
     def make(forms=None):
         lay = sgn.Layout(ctx, [sgn.Grid(1, c.n, c.L, g=c.g) for c in ens])
-        for l2, f in (forms or {}).items():
-            lay.set_form(l2, f)
+        for l2, (fs, fr) in (forms or {}).items():
+            lay.set_forms(l2, fs, fr)
         eta = dev(pack([c.eta for c in ens]))
         u = dev(pack([c.u for c in ens]))
         h = dev(pack([c.h for c in ens]))
@@ -157,8 +188,8 @@ def test_autotune_on_a_state_keeps_valid_forms_and_restores_the_state(S):
     assert all(np.array_equal(a, b) for a, b in zip(before, after))
     stats = st.stats()
     assert stats["solves"] == 0 and stats["step"] == 0 and stats["t"] == 0.0
-    forms = {l2: lay.form(l2) for l2 in (12, 13)}
-    assert set(forms.values()) <= {1, 2}
+    forms = {l2: lay.forms(l2) for l2 in (12, 13)}
+    assert all(set(f) <= {1, 2} for f in forms.values())
     st.rk4(dts, 2, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
     lay2, st2, (eta2, U2, u2) = make(forms)
     st2.rk4(dts, 2, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
@@ -179,6 +210,12 @@ def test_set_form_arguments(S):
     with pytest.raises(sgn.SgnError) as e:
         lay.set_form(13, 3)
     assert e.value.status == 1
+    with pytest.raises(sgn.SgnError) as e:
+        lay.set_forms(14, 2, 1)                             # 16384's right-hand side too
+    assert e.value.status == 2
+    with pytest.raises(sgn.SgnError) as e:
+        lay.set_forms(11, 1, 2)
+    assert e.value.status == 2
     assert lay.form(14) == 2 and lay.form(11) == 1
     lay2 = sgn.Layout(ctx, [sgn.Grid(2, 32, 1.0, ny=32, Ly=1.0)])
     with pytest.raises(sgn.SgnError):
