@@ -37,6 +37,8 @@ design notes of the repository):
   R8  time-stepping solves warm-start from the most recent velocity.
   R9  AB_s and SBDF2 take RK4 steps of the same dt for their start-up levels.
   R10 the SBDF2 preconditioner A is fixed from the initial data (§6.5).
+  R19 optional dealiasing (1d): Orszag's 2/3 rule applied to every new time level (zeta and
+      U before u is solved from them; u too in SBDF2, where it is not solved from U).
 
 Field layout: 1d fields are arrays [n]; 2d scalar fields are [ny, nx] (row-major, x
 fastest), 2d vector fields are [2, ny, nx] (x component first).
@@ -496,13 +498,36 @@ class State:
         self.grid = grid
         self.t = t
         self.forcing = forcing
+        self.dealias = False       # 1d: 2/3-rule projection of every new level (reading R19)
         self.solves = 0
         self.iterations = 0
 
     def copy(self):
         s = State(self.eta, self.U, self.u, self.h, self.gradh, self.grid, self.t, self.forcing)
-        s.solves, s.iterations = self.solves, self.iterations
+        s.solves, s.iterations, s.dealias = self.solves, self.iterations, self.dealias
         return s
+
+
+def dealias_1d(f):
+    """Orszag's 2/3 rule on a periodic 1d field: its Fourier modes with |j| > n/3 set to zero.
+    The paper reports (§6.4, Test 2) that dealiasing, there by zero padding, helps against
+    the long-time instability of large solitary waves; truncation is the form used here
+    (reading R19)."""
+    n = f.size
+    j = np.fft.fftfreq(n, d=1.0 / n)
+    fh = np.fft.fft(f)
+    fh[np.abs(j) > n / 3.0] = 0.0
+    return np.real(np.fft.ifft(fh))
+
+
+def _new_level(st: State, eta, U):
+    """A new time level (eta, U) as the steppers keep it: with dealiasing on, zeta = eta - h and
+    U are projected before anything (the solve for u, a right-hand side) is computed from it."""
+    if not st.dealias:
+        return eta, U
+    if st.grid["dim"] != 1:
+        raise ValueError("dealiasing is defined for 1d states")
+    return st.h + dealias_1d(eta - st.h), dealias_1d(U)
 
 
 def make_grid(dim, nx, Lx, g, ny=1, Ly=1.0):
@@ -547,8 +572,8 @@ def rk4_step(st: State, dt, rtol=1e-12, maxit=2000):
         a, b = _rhs_t(st, eta_i, u_i, st.t + dt * sum(RK4_A[i]))
         fe.append(a)
         fU.append(b)
-    st.eta = eta_n + dt * sum(RK4_B[j] * fe[j] for j in range(4))
-    st.U = U_n + dt * sum(RK4_B[j] * fU[j] for j in range(4))
+    st.eta, st.U = _new_level(st, eta_n + dt * sum(RK4_B[j] * fe[j] for j in range(4)),
+                              U_n + dt * sum(RK4_B[j] * fU[j] for j in range(4)))
     st.u = _solve(st, st.eta, st.U, u_i, rtol, maxit)
     st.t += dt
     return st
@@ -574,8 +599,7 @@ def run_ab(st: State, order, dt, nsteps, rtol=1e-12):
     while done < nsteps:
         fe = sum(b[j] * hist[j][0] for j in range(s))
         fU = sum(b[j] * hist[j][1] for j in range(s))
-        st.eta = st.eta + dt * fe
-        st.U = st.U + dt * fU
+        st.eta, st.U = _new_level(st, st.eta + dt * fe, st.U + dt * fU)
         st.u = _solve(st, st.eta, st.U, st.u, rtol, 2000)
         st.t += dt
         done += 1
@@ -606,6 +630,9 @@ def run_sbdf2(st: State, dt, nsteps, rtol=1e-12, coef_scale=1.0):
         res1 = apply_A(st.u, sigma, alpha, grid) - apply_G(st.eta, st.gradh, st.u, grid) + st.U
         res0 = apply_A(u0, sigma, alpha, grid) - apply_G(eta0, st.gradh, u0, grid) + U0
         u2 = apply_Ainv(2.0 * res1 - res0, sigma, alpha, grid)
+        eta2, U2 = _new_level(st, eta2, U2)
+        if st.dealias:
+            u2 = dealias_1d(u2)        # u is not solved from U here: it is projected too
         prev = (st.eta, st.U, st.u)
         f_prev = f_cur
         st.eta, st.U, st.u = eta2, U2, u2

@@ -585,3 +585,58 @@ def test_gmres_agrees_with_pcg_and_restarts_cost_steps():
     assert s5 > s30 and cyc5 >= s5 // 5
     z, s0, r0, c0, _ = O.gmres_G(eta, hx, np.zeros(n), grid)
     assert s0 == 0 and r0 == 0.0 and c0 == 0 and not z.any()
+
+
+# ---------------------------------------------------------------------------- dealiasing
+
+@pytest.mark.parametrize("n", [16, 64, 256])
+def test_dealias_is_the_two_thirds_projection(n):
+    """A projection (P P = P) that keeps every trig mode with |j| <= n/3 exactly and removes
+    every mode above it, Nyquist included."""
+    x = I.grid_1d(n, 1.0)
+    for j in range(0, n // 2 + 1):
+        for f in (np.cos(2 * np.pi * j * x), np.sin(2 * np.pi * j * x)):
+            if not f.any():
+                continue
+            keep = j <= n / 3.0
+            np.testing.assert_allclose(O.dealias_1d(f), f if keep else 0 * f, atol=1e-13)
+    rng = np.random.default_rng(n)
+    f = rng.standard_normal(n)
+    np.testing.assert_allclose(O.dealias_1d(O.dealias_1d(f)), O.dealias_1d(f), atol=1e-14)
+
+
+@pytest.mark.parametrize("n", [24, 64, 512])
+def test_dealias_removes_quadratic_aliasing(n):
+    """For f, g limited to |j| <= K with 3K < n, P(f g) formed on the n-point grid equals the
+    exact product (formed on a 2n-point grid, where nothing aliases) truncated to
+    |j| <= n/3: the aliased modes of a quadratic product land at |j| >= n - 2K > n/3 and
+    the projection removes them.  (n = 24 has 3K < n only up to K = 7.)"""
+    rng = np.random.default_rng(7)
+    K = (n - 1) // 3
+
+    def band():
+        c = np.zeros(n, dtype=complex)
+        c[1:K + 1] = rng.standard_normal(K) + 1j * rng.standard_normal(K)
+        c[0] = rng.standard_normal()
+        c[n - K:] = np.conj(c[1:K + 1][::-1])
+        return c
+
+    cf, cg = band(), band()
+    f, g = np.real(np.fft.ifft(cf)) * n, np.real(np.fft.ifft(cg)) * n
+
+    def on_2n(c):                                  # the same trig polynomial sampled on 2n points
+        C = np.zeros(2 * n, dtype=complex)
+        C[:K + 1] = c[:K + 1]
+        C[2 * n - K:] = c[n - K:]
+        return np.real(np.fft.ifft(C)) * 2 * n
+
+    prod2 = on_2n(cf) * on_2n(cg)
+    P2 = np.fft.fft(prod2) / (2 * n)
+    Kc = int(n // 3)                               # the projection's cut-off
+    exact = np.zeros(n, dtype=complex)
+    exact[:Kc + 1] = P2[:Kc + 1]
+    exact[n - Kc:] = P2[2 * n - Kc:]
+    want = np.real(np.fft.ifft(exact)) * n
+    got = O.dealias_1d(f * g)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    assert np.abs(f * g - want).max() > 1e-3 * np.abs(want).max()   # aliasing was there
