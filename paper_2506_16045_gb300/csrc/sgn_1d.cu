@@ -176,6 +176,45 @@ __global__ void k_axpy1d(const Inst1d* __restrict__ insts, const double* __restr
   }
 }
 
+// Orszag's 2/3 rule on a new time level: the modes |j| > n/3 of zeta = eta - h, of U and
+// (if u is non-null) of u are set to zero, one field after the other in the CTA's buffer.
+// Transforms in T: float64, or double-float on the mixed path.
+template <typename T, int NT, int MAXB>
+__global__ void __launch_bounds__(NT, 1) k_dealias1d(const Inst1d* __restrict__ insts,
+                                                  const int* __restrict__ ids,
+                                                  cplx<double>* big,
+                                                  const cplx<T>* __restrict__ tw,
+                                                  const double* __restrict__ h_all,
+                                                  double* __restrict__ eta_all,
+                                                  double* __restrict__ U_all,
+                                                  double* __restrict__ u_all) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cplx<T>* buf = big ? reinterpret_cast<cplx<T>*>(big + ((size_t)blockIdx.x << kMaxLog1d))
+                     : reinterpret_cast<cplx<T>*>(smem);
+  const Inst1d I = insts[ids[blockIdx.x]];
+  const int n = I.n;
+  const double inv_n = 1.0 / n, third = n / 3.0;
+  double* fields[3] = {eta_all, U_all, u_all};
+  for (int q = 0; q < 3; ++q) {
+    double* f = fields[q];
+    if (!f) continue;
+    const double* h = q == 0 ? h_all + I.off : nullptr;
+    for (int j = threadIdx.x; j < n; j += NT)
+      buf[j] = mk(num<T>(f[I.off + j] - (h ? h[j] : 0.0)), num<T>(0.0));
+    __syncthreads();
+    cta_fft<T, NT, MAXB>(buf, n, I.log2n, false, tw);
+    for (int j = threadIdx.x; j < n; j += NT) {
+      const int a = j <= n / 2 ? j : n - j;            // |wavenumber index|
+      if (a > third) buf[j] = mk(num<T>(0.0), num<T>(0.0));
+    }
+    __syncthreads();
+    cta_fft<T, NT, MAXB>(buf, n, I.log2n, true, tw);
+    for (int j = threadIdx.x; j < n; j += NT)
+      f[I.off + j] = to_f64(buf[j].x) * inv_n + (h ? h[j] : 0.0);
+    __syncthreads();                                    // buf is reused by the next field
+  }
+}
+
 // double-float coefficients of Def:MatrixM computed from float64 eta and h_x on the fly
 struct CoefGlobalDF {
   const double* eta;
@@ -343,6 +382,28 @@ cudaError_t launch_axpy1d(const Layout1d& lay, const double* dt, double* out, co
   }
   k_axpy1d<<<lay.count, 256, 0, s>>>(lay.d_inst, dt, out, base, a, scale);
   return cudaGetLastError();
+}
+
+cudaError_t launch_dealias1d(const Layout1d& lay, const void* tw64, const void* tw32,
+                             int precision, const double* h, double* eta, double* U, double* u,
+                             cudaStream_t s) {
+  const bool dfp = precision == SGN_PREC_MIXED;
+  const void* twT = dfp ? static_cast<const void*>(static_cast<const char*>(tw32) + kTw32Bytes)
+                        : tw64;
+  return for_each_class(lay, s, [&](auto NTc, auto MBc, int l, int first, int num, cudaStream_t s) {
+    constexpr int NT = decltype(NTc)::value, MB = decltype(MBc)::value;
+    const bool gl = l > kSmemLog1d;                // transform buffer in global scratch
+    const size_t sm = gl ? 0 : (size_t)16 << l;    // cplx<double> and cplx<df>: 16 bytes
+    cplx<double>* big = gl ? static_cast<cplx<double>*>(lay.big) : nullptr;
+    auto run = [&](auto kern, auto twp) -> cudaError_t {
+      cudaError_t e = set_smem(kern, sm);
+      if (e) return e;
+      kern<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, big, twp, h, eta, U, u);
+      return cudaGetLastError();
+    };
+    if (dfp) return run(k_dealias1d<df, NT, MB>, static_cast<const cplx<df>*>(twT));
+    return run(k_dealias1d<double, NT, MB>, static_cast<const cplx<double>*>(twT));
+  });
 }
 
 cudaError_t launch_linimp_step1d(const Layout1d& lay, const void* tw64, const void* tw32,

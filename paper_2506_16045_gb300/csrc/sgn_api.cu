@@ -877,6 +877,7 @@ struct sgn_state {
   SolveRec* A_fixed = nullptr;      // SBDF2 preconditioner, fixed at init
   DevStats* stats = nullptr;
   int hist = HIST_NONE;
+  int dealias = 0;                  // 1d: 2/3-rule projection of every new level
   int levels = 0;                   // valid multistep levels
   int prec = SGN_PREC_FP64;         // precision of the current step call
   std::vector<double> dt_last;
@@ -1030,6 +1031,18 @@ sgn_status rhs_at(sgn_state* st, const double* eta, const double* u, double* fe,
   return force_at(st, fe, fU, c, s);
 }
 
+// With dealiasing on (1d), a new time level is projected by the 2/3 rule before anything is
+// computed from it: eta - h and U, and u where it is not solved from U (SBDF2); transforms
+// in the precision of the step (double-float on the mixed path).
+sgn_status dealias_at(sgn_state* st, double* eta, double* U, double* u, cudaStream_t s) {
+  if (!st->dealias) return SGN_OK;
+  sgn_ctx* ctx = st->lay->ctx;
+  const cudaError_t e = sgn::launch_dealias1d(st->lay->l1, ctx->tw64, ctx->tw32, st->prec,
+                                              st->h, eta, U, u, s);
+  if (e != cudaSuccess) return cuda_fail(st->lay->ctx, e, "dealias launch");
+  return SGN_OK;
+}
+
 sgn_status rhs_plain(sgn_state* st, const double* eta, const double* u, double* fe, double* fU,
                      cudaStream_t s) {
   sgn_layout* lay = st->lay;
@@ -1124,6 +1137,7 @@ sgn_status rk4_once(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
                   {{st->fe[0], b0}, {st->fe[1], b1}, {st->fe[2], b1}, {st->fe[3], b0}}, 1, s,
                   st->U, {{st->U, 1.0}},
                   {{st->fU[0], b0}, {st->fU[1], b1}, {st->fU[2], b1}, {st->fU[3], b0}}, d));
+  SGN_TRY(dealias_at(st, st->eta, st->U, nullptr, s));
   SGN_TRY(copy_field(st, st->u, st->u_s, V, s));
   SGN_TRY(solve_at(st, st->eta, st->U, st->u, o, s));
   SGN_TRY(advance_time(st, s));
@@ -1390,6 +1404,7 @@ extern "C" sgn_status sgn_step_abk(sgn_state* st, int order, const double* dt, i
                         {{hU[0], B[4][0]}, {hU[1], B[4][1]}, {hU[2], B[4][2]}, {hU[3], B[4][3]}},
                         d));
       }
+      SGN_TRY(dealias_at(st, st->eta, st->U, nullptr, s));
       // the solve for u_{n+1} and the newest history level f(w_{n+1}) (the combinations
       // above were launched with the current history pointers, so rotating is safe)
       make_room();
@@ -1474,6 +1489,7 @@ extern "C" sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nstep
     SGN_TRY(copy_field(st, st->U_p, st->U, V, s));
     SGN_TRY(copy_field(st, st->eta, st->eta_s, P, s));
     SGN_TRY(copy_field(st, st->U, st->U_s, V, s));
+    SGN_TRY(dealias_at(st, st->eta, st->U, st->u, s));
     std::swap(st->he[0], st->he[1]);
     std::swap(st->hU[0], st->hU[1]);
     std::swap(st->res0, st->res1);
@@ -1506,6 +1522,15 @@ extern "C" sgn_status sgn_state_set_forcing(sgn_state* st, int nterms, const dou
   return SGN_OK;
 }
 
+
+extern "C" sgn_status sgn_state_set_dealias(sgn_state* st, int on) {
+  if (!st) return SGN_ERR_INVALID_ARG;
+  if (st->lay->dim != 1 && on)
+    return fail(st->lay->ctx, SGN_ERR_INVALID_ARG, "dealiasing is defined for 1d states");
+  st->dealias = on ? 1 : 0;
+  graph_drop(st);                   // a captured step holds the previous setting
+  return SGN_OK;
+}
 
 extern "C" sgn_status sgn_state_autotune(sgn_state* st, const double* dt, const sgn_opts* opts,
                                          sgn_stream stream, double* best_ms) {

@@ -107,6 +107,11 @@ cudaError_t launch_rhs1d_ux(const Layout1d& lay, const void* tw64, const void* t
 cudaError_t launch_axpy1d(const Layout1d& lay, const double* dt, double* out, const double* base,
                           int nterms, const double* const* f, const double* c, double scale,
                           cudaStream_t s);
+// Orszag's 2/3 rule on a new level: modes |j| > n/3 of eta - h, U and (non-null) u set to 0
+// (transforms in float64, or double-float for SGN_PREC_MIXED)
+cudaError_t launch_dealias1d(const Layout1d& lay, const void* tw64, const void* tw32,
+                             int precision, const double* h, double* eta, double* U, double* u,
+                             cudaStream_t s);
 // SBDF2 velocity update in one launch (transforms in float64, or double-float for
 // SGN_PREC_MIXED): res1_hat = (sigma + alpha k^2) u_hat - (G u - U)_hat, and with `solve`
 // u <- A^{-1} iFFT(c1 res1_hat + c0 res0_hat) in place.

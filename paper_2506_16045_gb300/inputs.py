@@ -173,7 +173,8 @@ def shelf_case(n=4096, L=200.0, a=0.3, x0=40.0, r=0.5, xs=60.0, w=5.0, g=9.81,
 # SBDF2 step takes its remainder G - A explicitly and, like the paper's SBDF2 runs of §6.4
 # (C = 0.05 against 0.2 for RK4), needs a smaller step: at dt = 0.004 its high wavenumbers
 # grow until the run overflows between t = 3.2 and 4.8, while at dt = 0.002 it stays within
-# 3e-4 of AB4 to t = 4 (both measured with the CPU oracle).
+# 3e-4 of AB4 to t = 4 (both measured with the CPU oracle).  Further out, at dt = 0.002, the
+# modes above n/3 grow (aliasing) and the run overflows before t = 8 unless it is dealiased.
 SHELF_DT = {"ab4": 0.004, "sbdf2": 0.002}
 
 

@@ -100,6 +100,7 @@ SIGNATURES = [
     ("sgn_step_abk", C.c_int, [_VP, C.c_int, C.POINTER(C.c_double), C.c_int, C.POINTER(SgnOpts),
                                _VP]),
     ("sgn_step_linimp", C.c_int, [_VP, C.POINTER(C.c_double), C.c_int, C.POINTER(SgnOpts), _VP]),
+    ("sgn_state_set_dealias", C.c_int, [_VP, C.c_int]),
     ("sgn_state_set_forcing", C.c_int, [_VP, C.c_int, _DP, _DP, C.POINTER(C.c_double),
                                         C.POINTER(C.c_double)]),
     ("sgn_state_autotune", C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(SgnOpts), _VP,
@@ -414,6 +415,11 @@ class State:
                                                                _stream(stream), C.byref(ms)),
                            "sgn_state_autotune")
         return ms.value
+
+    def set_dealias(self, on=True):
+        """2/3-rule dealiasing of every new time level of a 1d state (sgn_state_set_dealias)."""
+        self.lay.ctx.check(self.lay.ctx.lib.sgn_state_set_dealias(self.h, 1 if on else 0),
+                           "sgn_state_set_dealias")
 
     def set_forcing(self, phi_eta, phi_U, omega, theta):
         """External forcing sum_k cos(omega_k t + theta_k) (phi_eta_k, phi_U_k) (device
