@@ -266,14 +266,14 @@ sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nsteps, const sg
 #define SGN_MAX_FORCING 16
 sgn_status sgn_state_set_forcing(sgn_state* st, int nterms, const double* phi_eta,
                                  const double* phi_U, const double* omega, const double* theta);
-/* Dealiasing of a 1d state (on = 1; 0 turns it off; default off, as in the paper's runs).
+/* Dealiasing of a state (on = 1; 0 turns it off; default off, as in the paper's runs).
  * The paper reports that large solitary waves destabilise over long times without
  * dealiasing and that dealiasing (there by zero padding) helps (§6.4, Test 2).  Here it is
- * Orszag's 2/3 rule: every new time level has the Fourier modes |j| > n/3 of zeta = eta - h
- * and of U set to zero before u is solved from it (RK4, AB2-4), and of u as well in the
- * SBDF2 step, whose u is not solved from U; intermediate RK4 stages are not projected.
- * Transforms in float64, or double-float on the mixed path.  SGN_ERR_INVALID_ARG for a 2d
- * state.  Applies from the next step call. */
+ * Orszag's 2/3 rule: every new time level has the Fourier modes |j| > n/3 (2d: |jx| > nx/3
+ * or |jy| > ny/3) of zeta = eta - h and of U set to zero before u is solved from it (RK4,
+ * AB2-4), and of u as well in the SBDF2 step, whose u is not solved from U; intermediate
+ * RK4 stages are not projected.  Transforms: 1d in float64, or double-float on the mixed
+ * path; 2d in float64.  Applies from the next step call. */
 sgn_status sgn_state_set_dealias(sgn_state* st, int on);
 /* Autotuner of the layout's kernel forms (sgn_layout_set_forms) on this state's own
  * problem: for every combination of forms of the n = 4096 and 8192 classes (solve and

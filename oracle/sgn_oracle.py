@@ -37,8 +37,9 @@ design notes of the repository):
   R8  time-stepping solves warm-start from the most recent velocity.
   R9  AB_s and SBDF2 take RK4 steps of the same dt for their start-up levels.
   R10 the SBDF2 preconditioner A is fixed from the initial data (§6.5).
-  R19 optional dealiasing (1d): Orszag's 2/3 rule applied to every new time level (zeta and
-      U before u is solved from them; u too in SBDF2, where it is not solved from U).
+  R19 optional dealiasing: Orszag's 2/3 rule applied to every new time level (zeta and U
+      before u is solved from them; u too in SBDF2, where it is not solved from U); in 2d the
+      tensor product of the 1d projections.
 
 Field layout: 1d fields are arrays [n]; 2d scalar fields are [ny, nx] (row-major, x
 fastest), 2d vector fields are [2, ny, nx] (x component first).
@@ -498,7 +499,7 @@ class State:
         self.grid = grid
         self.t = t
         self.forcing = forcing
-        self.dealias = False       # 1d: 2/3-rule projection of every new level (reading R19)
+        self.dealias = False       # 2/3-rule projection of every new level (reading R19)
         self.solves = 0
         self.iterations = 0
 
@@ -520,14 +521,31 @@ def dealias_1d(f):
     return np.real(np.fft.ifft(fh))
 
 
+def dealias_2d(f):
+    """The 2/3 rule on a periodic [ny, nx] field: modes with |jx| > nx/3 or |jy| > ny/3 set to
+    zero (the tensor product of the 1d projections)."""
+    ny, nx = f.shape
+    jx = np.abs(np.fft.fftfreq(nx, d=1.0 / nx))
+    jy = np.abs(np.fft.fftfreq(ny, d=1.0 / ny))
+    keep = (jy[:, None] <= ny / 3.0) & (jx[None, :] <= nx / 3.0)
+    return np.real(np.fft.ifft2(np.fft.fft2(f) * keep))
+
+
+def dealias(f, grid):
+    """The 2/3 rule on a scalar (1d [n], 2d [ny, nx]) or 2d vector ([2, ny, nx]) field."""
+    if grid["dim"] == 1:
+        return dealias_1d(f)
+    if f.ndim == 3:
+        return np.stack([dealias_2d(f[0]), dealias_2d(f[1])])
+    return dealias_2d(f)
+
+
 def _new_level(st: State, eta, U):
     """A new time level (eta, U) as the steppers keep it: with dealiasing on, zeta = eta - h and
     U are projected before anything (the solve for u, a right-hand side) is computed from it."""
     if not st.dealias:
         return eta, U
-    if st.grid["dim"] != 1:
-        raise ValueError("dealiasing is defined for 1d states")
-    return st.h + dealias_1d(eta - st.h), dealias_1d(U)
+    return st.h + dealias(eta - st.h, st.grid), dealias(U, st.grid)
 
 
 def make_grid(dim, nx, Lx, g, ny=1, Ly=1.0):
@@ -632,7 +650,7 @@ def run_sbdf2(st: State, dt, nsteps, rtol=1e-12, coef_scale=1.0):
         u2 = apply_Ainv(2.0 * res1 - res0, sigma, alpha, grid)
         eta2, U2 = _new_level(st, eta2, U2)
         if st.dealias:
-            u2 = dealias_1d(u2)        # u is not solved from U here: it is projected too
+            u2 = dealias(u2, grid)     # u is not solved from U here: it is projected too
         prev = (st.eta, st.U, st.u)
         f_prev = f_cur
         st.eta, st.U, st.u = eta2, U2, u2

@@ -1263,6 +1263,66 @@ cudaError_t launch_grad2d(const Layout2d& L, const void* tw64, const double* f, 
   return c2r_vec<double>(L, tw64, nullptr, tplane(L, 1), tplane(L, 2), gradf, s);
 }
 
+namespace {
+
+// Orszag's 2/3 rule on half planes: modes with |jx| > nx/3 or |jy| > ny/3 set to zero
+// (true indices: the Nyquist rows and column are removed too).
+__global__ void k2_dealias(Modes2d M, void* p0, void* p1) {
+  const long long HP = (long long)M.ny * M.H;
+  const double tx = M.nx / 3.0, ty = M.ny / 3.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HP;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)i / M.H, c = (int)i - y * M.H;
+    const int ay = y <= (M.ny >> 1) ? y : M.ny - y;
+    if (c > tx || ay > ty) {
+      st_c<double>(p0, i, mk(0.0, 0.0));
+      if (p1) st_c<double>(p1, i, mk(0.0, 0.0));
+    }
+  }
+}
+
+__global__ void k2_sub(long long P, const double* a, const double* b, double* out, double sign) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = a[i] + sign * b[i];
+}
+
+}  // namespace
+
+cudaError_t launch_dealias2d(const Layout2d& L, const void* tw64, const double* h, double* eta,
+                             double* U, double* u, cudaStream_t s) {
+  const Modes2d M = modes_of(L);
+  double* zs = L.rhs_w;                        // zeta = eta - h (a free real plane here)
+  k2_sub<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, eta, h, zs, -1.0);
+  cudaError_t e = cudaGetLastError();
+  if (e) return e;
+  // zeta (paired with zero) through the transform planes
+  if ((e = rows_r2c<double>(L, tw64, nullptr, zs, nullptr, nullptr, nullptr, tplane(L, 0),
+                            tplane(L, 3), nullptr, nullptr, 1, s)))
+    return e;
+  ColArgs a{};
+  a.planes[0] = tplane(L, 0);
+  a.K = 1;
+  if ((e = cols<double, COL_FWD>(L, tw64, nullptr, a, s))) return e;
+  k2_dealias<<<grid_for(L.HP, 256), 256, 0, s>>>(M, tplane(L, 0), nullptr);
+  if ((e = cudaGetLastError())) return e;
+  if ((e = cols<double, COL_INV>(L, tw64, nullptr, a, s))) return e;
+  if ((e = rows_c2r<double>(L, tw64, nullptr, tplane(L, 0), tplane(L, 3), nullptr, nullptr, zs,
+                            nullptr, nullptr, nullptr, 1, s)))
+    return e;
+  k2_sub<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, h, zs, eta, 1.0);
+  if ((e = cudaGetLastError())) return e;
+  // the vector fields, two components at a time through the workspace slots
+  for (double* v : {U, u}) {
+    if (!v) continue;
+    if ((e = r2c_vec<double>(L, tw64, nullptr, v, slot(L, 0), slot(L, 1), s))) return e;
+    k2_dealias<<<grid_for(L.HP, 256), 256, 0, s>>>(M, slot(L, 0), slot(L, 1));
+    if ((e = cudaGetLastError())) return e;
+    if ((e = c2r_vec<double>(L, tw64, nullptr, slot(L, 0), slot(L, 1), v, s))) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_coeffs2d(const Layout2d& L, const double* eta, const double* gradh, int kind,
                             SolveRec* rec, cudaStream_t s) {
   k2_coeffs<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, eta, gradh, kind, L.parts, L.sc, rec);

@@ -44,6 +44,10 @@ cudaError_t launch_coeffs2d(const Layout2d& L, const double* eta, const double* 
                             SolveRec* rec, cudaStream_t s);
 cudaError_t launch_apply_G2d(const Layout2d& L, const void* tw64, const double* eta,
                              const double* gradh, const double* u, double* Gu, cudaStream_t s);
+// Orszag's 2/3 rule (modes |jx| > nx/3 or |jy| > ny/3 set to zero) on eta - h, U and, if
+// non-null, u (float64; uses the workspace planes)
+cudaError_t launch_dealias2d(const Layout2d& L, const void* tw64, const double* h, double* eta,
+                             double* U, double* u, cudaStream_t s);
 cudaError_t launch_precond2d(const Layout2d& L, const void* tw64, const SolveRec* rec,
                              const double* r, double* z, cudaStream_t s);
 // Runs as one cached graph whose refinement and inner loops are conditional (while) nodes

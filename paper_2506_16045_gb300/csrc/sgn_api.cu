@@ -877,7 +877,7 @@ struct sgn_state {
   SolveRec* A_fixed = nullptr;      // SBDF2 preconditioner, fixed at init
   DevStats* stats = nullptr;
   int hist = HIST_NONE;
-  int dealias = 0;                  // 1d: 2/3-rule projection of every new level
+  int dealias = 0;                  // 2/3-rule projection of every new level
   int levels = 0;                   // valid multistep levels
   int prec = SGN_PREC_FP64;         // precision of the current step call
   std::vector<double> dt_last;
@@ -1031,14 +1031,16 @@ sgn_status rhs_at(sgn_state* st, const double* eta, const double* u, double* fe,
   return force_at(st, fe, fU, c, s);
 }
 
-// With dealiasing on (1d), a new time level is projected by the 2/3 rule before anything is
-// computed from it: eta - h and U, and u where it is not solved from U (SBDF2); transforms
-// in the precision of the step (double-float on the mixed path).
+// With dealiasing on, a new time level is projected by the 2/3 rule before anything is
+// computed from it: eta - h and U, and u where it is not solved from U (SBDF2); 1d transforms
+// in the precision of the step (double-float on the mixed path), 2d in float64.
 sgn_status dealias_at(sgn_state* st, double* eta, double* U, double* u, cudaStream_t s) {
   if (!st->dealias) return SGN_OK;
   sgn_ctx* ctx = st->lay->ctx;
-  const cudaError_t e = sgn::launch_dealias1d(st->lay->l1, ctx->tw64, ctx->tw32, st->prec,
-                                              st->h, eta, U, u, s);
+  const cudaError_t e =
+      st->lay->dim == 1 ? sgn::launch_dealias1d(st->lay->l1, ctx->tw64, ctx->tw32, st->prec,
+                                                st->h, eta, U, u, s)
+                        : sgn::launch_dealias2d(st->lay->l2, ctx->tw64, st->h, eta, U, u, s);
   if (e != cudaSuccess) return cuda_fail(st->lay->ctx, e, "dealias launch");
   return SGN_OK;
 }
@@ -1525,8 +1527,6 @@ extern "C" sgn_status sgn_state_set_forcing(sgn_state* st, int nterms, const dou
 
 extern "C" sgn_status sgn_state_set_dealias(sgn_state* st, int on) {
   if (!st) return SGN_ERR_INVALID_ARG;
-  if (st->lay->dim != 1 && on)
-    return fail(st->lay->ctx, SGN_ERR_INVALID_ARG, "dealiasing is defined for 1d states");
   st->dealias = on ? 1 : 0;
   graph_drop(st);                   // a captured step holds the previous setting
   return SGN_OK;

@@ -417,7 +417,7 @@ class State:
         return ms.value
 
     def set_dealias(self, on=True):
-        """2/3-rule dealiasing of every new time level of a 1d state (sgn_state_set_dealias)."""
+        """2/3-rule dealiasing of every new time level (sgn_state_set_dealias)."""
         self.lay.ctx.check(self.lay.ctx.lib.sgn_state_set_dealias(self.h, 1 if on else 0),
                            "sgn_state_set_dealias")
 

@@ -1,4 +1,4 @@
-"""2/3-rule dealiasing of 1d states (sgn_state_set_dealias) against the oracle's.
+"""2/3-rule dealiasing of 1d and 2d states (sgn_state_set_dealias) against the oracle's.
 
 Every new time level has its modes |j| > n/3 of zeta = eta - h and U removed before u is
 solved from it (and of u too in SBDF2).  The steppers with dealiasing match the oracle's
@@ -147,14 +147,50 @@ def test_dealiased_sbdf2_shelf_reaches_t8(S):
     assert rel(z, ref.eta - c.h) < 1e-6 and rel(u[0], ref.u) < 1e-6
 
 
-def test_dealias_rejects_2d(S):
+def top_energy_2d(f):
+    """Largest 2d Fourier coefficient outside |jx| <= nx/3, |jy| <= ny/3, relative to the
+    largest overall; a vector field [2, ny, nx] counts its components together (they share
+    one complex transform, hence one absolute rounding level)."""
+    f = f if f.ndim == 3 else f[None]
+    ny, nx = f.shape[1:]
+    c = np.abs(np.fft.fft2(f, axes=(1, 2)))
+    jx = np.abs(np.fft.fftfreq(nx, d=1.0 / nx))
+    jy = np.abs(np.fft.fftfreq(ny, d=1.0 / ny))
+    out = (jy[:, None] > ny / 3.0) | (jx[None, :] > nx / 3.0)
+    return float(c[:, out].max() / c.max())
+
+
+@pytest.mark.parametrize("scheme", ["rk4", "ab2", "sbdf2"])
+def test_dealiased_2d_steppers_match_oracle(S, scheme):
+    """2d: the tensor-product projection on the bump (32^2, 6 steps, float64)."""
     sgn, ctx = S
-    lay = sgn.Layout(ctx, [sgn.Grid(2, 16, 1.0, ny=16, Ly=1.0)])
-    z = torch.ones(2 * 256, dtype=torch.float64, device="cuda")
-    st = sgn.State(lay, z[:256], torch.zeros_like(z), torch.zeros_like(z), z[:256],
-                   torch.zeros_like(z))
-    with pytest.raises(sgn.SgnError) as e:
-        st.set_dealias(True)
-    assert e.value.status == 1
-    st.set_dealias(False)
+    c = I.bump2d_case(n=32, L=40.0, a=0.2, x0=10.0, H=0.5, R=3.0, dt=0.05)
+    n = c["n"]
+    lay = sgn.Layout(ctx, [sgn.Grid(2, n, c["L"], g=c["g"], ny=n, Ly=c["L"])])
+    eta, u, h = dev(c["eta"]), dev(c["u"]), dev(c["h"])
+    U, gh = torch.zeros_like(u), torch.zeros_like(u)
+    st = sgn.State(lay, eta, U, u, h, gh)
+    st.init()
+    st.set_dealias(True)
+    if scheme == "rk4":
+        st.rk4(c["dt"], 6, rtol=1e-13, maxit=4000, prec=sgn.PREC_FP64)
+    elif scheme == "ab2":
+        st.abk(2, c["dt"], 6, rtol=1e-13, maxit=4000, prec=sgn.PREC_FP64)
+    else:
+        st.linimp(c["dt"], 6, rtol=1e-13, maxit=4000, prec=sgn.PREC_FP64)
+    assert st.stats()["status"] == 0
+    e, UU, uu = host(eta).reshape(n, n), host(U).reshape(2, n, n), host(u).reshape(2, n, n)
     st.close()
+    ref = O.init_state(c["eta"], c["u"], c["h"], O.make_grid(2, n, c["L"], c["g"], ny=n,
+                                                                Ly=c["L"]))
+    ref.dealias = True
+    if scheme == "rk4":
+        O.run_rk4(ref, c["dt"], 6, 1e-13)
+    elif scheme == "ab2":
+        O.run_ab(ref, 2, c["dt"], 6, 1e-13)
+    else:
+        O.run_sbdf2(ref, c["dt"], 6, 1e-13)
+    assert rel(e - c["h"], ref.eta - c["h"]) < 1e-10
+    assert rel(uu, ref.u) < 1e-10 and rel(UU, ref.U) < 1e-10
+    assert top_energy_2d(e - c["h"]) < 1e-13
+    assert top_energy_2d(UU) < 1e-13

@@ -640,3 +640,19 @@ def test_dealias_removes_quadratic_aliasing(n):
     got = O.dealias_1d(f * g)
     assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
     assert np.abs(f * g - want).max() > 1e-3 * np.abs(want).max()   # aliasing was there
+
+
+def test_dealias_2d_is_the_tensor_product_projection():
+    """2d: a mode e^{i(jx x + jy y)} survives iff |jx| <= nx/3 and |jy| <= ny/3; the
+    projection of a product field factorises into the 1d projections."""
+    nx, ny = 32, 16
+    X, Y = I.grid_2d(nx, ny, 1.0, 1.0)
+    for jx in (0, 5, 10, 11, 16):
+        for jy in (0, 3, 5, 6, 8):
+            f = np.cos(2 * np.pi * (jx * X + jy * Y))
+            keep = jx <= nx / 3.0 and jy <= ny / 3.0
+            np.testing.assert_allclose(O.dealias_2d(f), f if keep else 0 * f, atol=1e-13)
+    rng = np.random.default_rng(3)
+    a, b = rng.standard_normal(nx), rng.standard_normal(ny)
+    np.testing.assert_allclose(O.dealias_2d(b[:, None] * a[None, :]),
+                               O.dealias_1d(b)[:, None] * O.dealias_1d(a)[None, :], atol=1e-13)
