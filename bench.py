@@ -794,12 +794,16 @@ def bench_manufactured(sgn, ctx, torch, n=256, t_final=1.0):
 
 
 def bench_serving(sgn, ctx, torch, nreq=120, rate=200.0, seed=16045, baseline_sample=8):
-    """Poisson stream of SGN runs and constraint solves (half 1d, half 2d), host inputs."""
+    """Poisson stream of SGN runs (RK4, 20-200 steps) and constraint solves (half 1d, half
+    2d), host inputs.  A solve's right-hand side is b = G u_s for the solitary-wave velocity
+    u_s (formed with sgn_apply_operator before the stream starts), so its answer is known."""
     import numpy as np
 
     from paper_2506_16045_gb300 import inputs as I
     rng = np.random.default_rng(seed)
-    reqs = []
+    reqs, known = [], {}
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a).ravel(), dtype=torch.float64,
+                                    device="cuda")
     for _ in range(nreq):
         kind = sgn.REQ_RUN if rng.random() < 0.5 else sgn.REQ_SOLVE
         dim = 1 if rng.random() < 0.5 else 2
@@ -825,20 +829,29 @@ def bench_serving(sgn, ctx, torch, nreq=120, rate=200.0, seed=16045, baseline_sa
             pts = n * n
         dx = L / n
         dt = 0.25 * dx / np.sqrt(9.81 * (1 + a))
-        nsteps = int(rng.integers(5, 31)) if kind == sgn.REQ_RUN else 0
+        nsteps = int(rng.integers(20, 201)) if kind == sgn.REQ_RUN else 0
+        if kind == sgn.REQ_SOLVE:
+            lay = sgn.Layout(ctx, [grid])
+            gh = torch.zeros(dim * pts, dtype=torch.float64, device="cuda")
+            sgn.spectral_grad(lay, dev(h), gh)
+            b = torch.zeros_like(gh)
+            sgn.apply_operator(lay, dev(eta), gh, dev(u), b)
+            known[len(reqs)] = np.ascontiguousarray(u, dtype=np.float64).ravel()
+            u = b.cpu().numpy()
+            lay.close()
         reqs.append((kind, grid, eta, u, h, dt, nsteps, pts))
     srv = sgn.Server(ctx)
     gaps = rng.exponential(1.0 / rate, nreq)
     tickets = []
     t_start = time.perf_counter()
     t_next = t_start
-    for (kind, grid, eta, u, h, dt, nsteps, pts), gap in zip(reqs, gaps):
+    for i, ((kind, grid, eta, u, h, dt, nsteps, pts), gap) in enumerate(zip(reqs, gaps)):
         t_next += gap
         while time.perf_counter() < t_next:
             time.sleep(0.0002)
         st, t = srv.submit(kind, grid, eta, u, h, scheme=sgn.SCHEME_RK4, dt=dt, nsteps=nsteps,
                            rtol=1e-10, prec=sgn.PREC_MIXED, host=True)
-        tickets.append((t, kind, pts, nsteps, st))
+        tickets.append((t, kind, pts, nsteps, st, i))
     done = {}
     while len(done) < len(tickets):
         for t, *_ in tickets:
@@ -852,8 +865,15 @@ def bench_serving(sgn, ctx, torch, nreq=120, rate=200.0, seed=16045, baseline_sa
                           for t, k, *_ in tickets if k == sgn.REQ_SOLVE])
     t0 = min(done[t]["t_submit"] for t, *_ in tickets)
     t1 = max(done[t]["t_done"] for t, *_ in tickets)
-    work = sum(p * max(k, 1) for t, kind, p, k, _ in tickets)     # a solve counts one step
+    work = sum(p * max(k, 1) for t, kind, p, k, *_ in tickets)    # a solve counts one step
     ok = all(done[t]["status"] == 0 for t, *_ in tickets)
+    solve_err = 0.0
+    for t, kind, p, k, _, i in tickets:
+        if kind == sgn.REQ_SOLVE:
+            d = 1 if reqs[i][1].dim == 1 else 2
+            x = sgn.device_array(done[t]["u"], d * p).cpu().numpy()
+            solve_err = max(solve_err, float(np.linalg.norm(x - known[i]) /
+                                             np.linalg.norm(known[i])))
     for t, *_ in tickets:
         srv.release(t)
     srv.close()
@@ -884,9 +904,10 @@ def bench_serving(sgn, ctx, torch, nreq=120, rate=200.0, seed=16045, baseline_sa
         tsum += time.perf_counter() - ts
         wsum += pts * max(nsteps, 1)
     return {"workload": f"Poisson {rate:.0f}/s, {nreq} requests (seed {seed}): 50% RK4 runs "
-                        "(5-30 steps) / 50% solves, 50% 1d n in 2^10..2^14 / 50% 2d 2^7..2^10 "
-                        "per side, Gaussian bumps, mixed precision, rtol 1e-10",
-            "all_ok": ok, "p50_ms": float(np.percentile(lat, 50)),
+                        "(20-200 steps) / 50% solves of G x = G u_s, 50% 1d n in 2^10..2^14 / "
+                        "50% 2d 2^7..2^10 per side, Gaussian bumps, mixed precision, rtol 1e-10",
+            "all_ok": ok, "solve_max_rel_err_vs_known": solve_err,
+            "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)),
             "solve_p50_ms": float(np.percentile(solve_lat, 50)) if solve_lat.size else None,
             "solve_p99_ms": float(np.percentile(solve_lat, 99)) if solve_lat.size else None,
