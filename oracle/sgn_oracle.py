@@ -40,6 +40,8 @@ design notes of the repository):
   R19 optional dealiasing: Orszag's 2/3 rule applied to every new time level (zeta and U
       before u is solved from them; u too in SBDF2, where it is not solved from U); in 2d the
       tensor product of the 1d projections.
+  R20 the non-constraint form (Eq:dswe, the remark of §5) is advanced on (eta, u) with the
+      RK4 tableau; u_t solves G u_t = M, M the u_t-free terms of Eq:MomEq.
 
 Field layout: 1d fields are arrays [n]; 2d scalar fields are [ny, nx] (row-major, x
 fastest), 2d vector fields are [2, ny, nx] (x component first).
@@ -452,6 +454,22 @@ def rhs_1d(eta, u, h, hx, L, g):
     return f_eta, f_U
 
 
+def rhs_nc_1d(eta, u, h, hx, L, g):
+    """The non-constraint form (Eq:dswe) in 1d, with the u_t terms grouped as in Eq:MomEq:
+    eta_t = -(eta u)_x and G_{eta,h} u_t = M with
+      M = -eta u u_x - g eta zeta_x + (eta^3 Q/3 + eta^2 S/2)_x - h_x (eta^2 Q/2 + eta S),
+    Q = u u_xx - u_x^2 (the u.grad(div u) - (div u)^2 of Eq:MomEq), S = u (h_x u)_x (reading
+    R6 for (u.grad)^2 h).  Returns (f_eta, M)."""
+    zeta = eta - h
+    d = deriv(u, L)
+    Q = u * deriv(d, L) - d * d
+    S = u * deriv(hx * u, L)
+    M = (-eta * u * d - g * eta * deriv(zeta, L)
+         + deriv(eta ** 3 * Q / 3.0 + eta ** 2 * S / 2.0, L)
+         - hx * (eta ** 2 * Q / 2.0 + eta * S))
+    return -deriv(eta * u, L), M
+
+
 def rhs_2d(eta, u, h, gradh, Lx, Ly, g):
     """2d form of rhs_1d: div(eta u tensor u) has components ((eta u u)_x + (eta u v)_y,
     (eta u v)_x + (eta v v)_y) (§2.2); F = grad(Phi) - grad h Psi with d = div u,
@@ -594,6 +612,40 @@ def rk4_step(st: State, dt, rtol=1e-12, maxit=2000):
                               U_n + dt * sum(RK4_B[j] * fU[j] for j in range(4)))
     st.u = _solve(st, st.eta, st.U, u_i, rtol, maxit)
     st.t += dt
+    return st
+
+
+def rk4_nc_step(st: State, dt, rtol=1e-12, maxit=2000):
+    """One RK4 step (Eq:ERK tableau) of the non-constraint form on (eta, u) (the remark of §5
+    that the same time discretisations apply to Eq:dswe): each stage takes
+    k = (f_eta, u_t) with G_{eta_i,h} u_t = M(eta_i, u_i) solved by PCG (warm start from the
+    previous stage's u_t).  U = G u is refreshed at the end so the state stays consistent.
+    1d, without forcing or dealiasing."""
+    grid = st.grid
+    if grid["dim"] != 1 or st.forcing is not None or st.dealias:
+        raise ValueError("the non-constraint stepper is 1d, without forcing or dealiasing")
+    L, g = grid["Lx"], grid["g"]
+    eta_n, u_n = st.eta, st.u
+    fe, ut = [], []
+    ut_prev = getattr(st, "ut", np.zeros_like(u_n))
+    for i in range(4):
+        eta_i = eta_n + dt * sum(RK4_A[i][j] * fe[j] for j in range(i))
+        u_i = u_n + dt * sum(RK4_A[i][j] * ut[j] for j in range(i))
+        f_eta, M = rhs_nc_1d(eta_i, u_i, st.h, st.gradh, L, g)
+        ut_prev = _solve(st, eta_i, M, ut_prev, rtol, maxit)
+        fe.append(f_eta)
+        ut.append(ut_prev)
+    st.eta = eta_n + dt * sum(RK4_B[j] * fe[j] for j in range(4))
+    st.u = u_n + dt * sum(RK4_B[j] * ut[j] for j in range(4))
+    st.U = apply_G_1d(st.eta, st.gradh, st.u, L)
+    st.ut = ut_prev
+    st.t += dt
+    return st
+
+
+def run_rk4_nc(st: State, dt, nsteps, rtol=1e-12):
+    for _ in range(nsteps):
+        rk4_nc_step(st, dt, rtol)
     return st
 
 

@@ -656,3 +656,60 @@ def test_dealias_2d_is_the_tensor_product_projection():
     a, b = rng.standard_normal(nx), rng.standard_normal(ny)
     np.testing.assert_allclose(O.dealias_2d(b[:, None] * a[None, :]),
                                O.dealias_1d(b)[:, None] * O.dealias_1d(a)[None, :], atol=1e-13)
+
+
+# ---------------------------------------------------------------------------- non-constraint form
+
+def test_dGdt_matches_a_finite_difference_in_eta():
+    """d/dt (G_eta u) with u fixed is the eta-derivative of Def:G in the direction eta_t:
+    against a central difference of the matrix-free operator (no shared formula)."""
+    n, L = 128, 10.0
+    x = I.grid_1d(n, L)
+    h = 1.0 + 0.3 * np.sin(2 * np.pi * x / L)
+    hx = O.deriv(h, L)
+    eta = h + 0.2 * np.cos(2 * np.pi * x / L) ** 2
+    u = np.sin(4 * np.pi * x / L) + 0.3
+    e = np.cos(6 * np.pi * x / L)
+    eps = 1e-5
+    fd = (O.apply_G_1d(eta + eps * e, hx, u, L) - O.apply_G_1d(eta - eps * e, hx, u, L)) / (2 * eps)
+    an = O.dGdt_1d(eta, e, hx, u, np.zeros(n), L)
+    assert np.abs(fd - an).max() <= 1e-8 * np.abs(an).max()
+
+
+@pytest.mark.parametrize("n", [64, 256])
+def test_momentum_form_equals_the_constraint_form(n):
+    """Eq:MomEq (u_t-free terms M) and the DAE form must agree: G u_t = M and
+    d/dt(G u) = f_U give M = f_U - (d/dt G) u with eta_t = f_eta.  Two transcriptions (Eq:MomEq
+    against Def:bigF with the product rule) agree to the spectral accuracy of the grid."""
+    L = 20.0
+    x = I.grid_1d(n, L)
+    th = 2 * np.pi * x / L                         # smooth periodic fields (entire functions)
+    h = 1.0 - 0.3 * np.exp(np.cos(th) - 1.0)
+    hx = O.deriv(h, L)
+    eta = h + 0.15 * np.exp(np.cos(th + 1.0) - 1.0)
+    u = 0.3 * np.sin(th) * np.exp(0.5 * np.cos(2 * th))
+    fe, fU = O.rhs_1d(eta, u, h, hx, L, 9.81)
+    fe2, M = O.rhs_nc_1d(eta, u, h, hx, L, 9.81)
+    np.testing.assert_allclose(fe2, fe, atol=1e-14)
+    other = fU - O.dGdt_1d(eta, fe, hx, u, np.zeros(n), L)
+    err = np.abs(M - other).max() / np.abs(M).max()
+    assert err <= 1e-12, err
+
+
+def test_nonconstraint_rk4_solitary_wave_and_constraint_form():
+    """Flat bottom: the non-constraint RK4 follows the exact translate (§6) as the
+    constraint-form RK4 does, and the two discretisations differ at fourth order in dt."""
+    c = I.solitary_case(n=256, L=100.0, a=0.2, x0=25.0, g=9.81)
+    grid = O.make_grid(1, c.n, c.L, c.g)
+    x = I.grid_1d(c.n, c.L)
+    diffs = []
+    for dt, k in ((0.04, 10), (0.02, 20)):
+        a = O.init_state(c.eta, c.u, c.h, grid)
+        b = O.init_state(c.eta, c.u, c.h, grid)
+        O.run_rk4_nc(a, dt, k, 1e-13)
+        O.run_rk4(b, dt, k, 1e-13)
+        ee, _ = I.solitary_wave_1d(x, c.L, 1.0, 0.2, 25.0, c.g, t=0.4)
+        assert np.abs(a.eta - ee).max() < 1e-6
+        assert np.abs(O.apply_G_1d(a.eta, a.gradh, a.u, c.L) - a.U).max() < 1e-12
+        diffs.append(np.abs(a.eta - b.eta).max())
+    assert math.log2(diffs[0] / diffs[1]) > 3.5, diffs
