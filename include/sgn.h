@@ -248,6 +248,18 @@ sgn_status sgn_step_rk4(sgn_state* st, const double* dt, int nsteps, const sgn_o
  * order-1 steps after init are RK4 steps of the same dt. */
 sgn_status sgn_step_abk(sgn_state* st, int order, const double* dt, int nsteps,
                         const sgn_opts* opts, sgn_stream stream);
+/* RK4 on the non-constraint form of the SGN equations (Eq:dswe; the remark of §5 that the
+ * same time discretisations apply to it), 1d.  The state advances (eta, u) with the RK4
+ * tableau of sgn_step_rk4; each stage takes eta_t = -(eta u)_x and u_t from
+ * G_{eta,h} u_t = M, where M collects the u_t-free terms of Eq:MomEq
+ * (M = -eta u u_x - g eta zeta_x + (eta^3 Q/3 + eta^2 S/2)_x - h_x (eta^2 Q/2 + eta S),
+ * Q = u u_xx - u_x^2, S = u (h_x u)_x), solved by the PCG of sgn_pcg with the options
+ * (warm start from the previous u_t).  U = G u is refreshed after every step, so other
+ * steppers can continue from the state.  Right-hand side transforms in float64, or
+ * double-float on the mixed path.  SGN_ERR_INVALID_ARG for a 2d state, or one with a
+ * forcing or dealiasing set. */
+sgn_status sgn_step_rk4_nc(sgn_state* st, const double* dt, int nsteps, const sgn_opts* opts,
+                           sgn_stream stream);
 /* Linearly implicit SBDF2 (Eq:MM with Table 1's SBDF2 row, §5.3): one A-solve per step,
  * no Krylov iteration; A fixed from the state at init (§6.5).  The first step after init
  * is an RK4 step. */
@@ -277,12 +289,14 @@ sgn_status sgn_state_set_forcing(sgn_state* st, int nterms, const double* phi_et
 sgn_status sgn_state_set_dealias(sgn_state* st, int on);
 /* Autotuner of the layout's kernel forms (sgn_layout_set_forms) on this state's own
  * problem: for every combination of forms of the n = 4096 and 8192 classes (solve and
- * right-hand side chosen separately: up to 16 combinations), one untimed
- * and two timed RK4 steps with these dt (HOST [count]) and options, each combination from
- * the same state, and the fastest combination stays set on the layout.  The state (eta, U,
- * u, time, counters) is restored afterwards, so tuning leaves no trace on the solution.
- * Allocates and frees 3 P doubles; synchronises `stream`; best_ms (nullable, host) receives
- * the winning time per step.  A 2d state, or one without such classes, is left as it is. */
+ * right-hand side chosen separately: up to 16 combinations), one untimed and three timed
+ * RK4 steps with these dt (HOST [count]) and options, each from the same state, in two
+ * passes keeping each combination's faster one.  The default (one CTA per instance) stays
+ * unless another combination is at least 3% faster; the choice stays set on the layout.
+ * The state (eta, U, u, time, counters) is restored afterwards, so tuning leaves no trace
+ * on the solution.  Allocates and frees 3 P doubles; synchronises `stream`; best_ms
+ * (nullable, host) receives the chosen time per step.  A 2d state, or one without such
+ * classes, is left as it is. */
 sgn_status sgn_state_autotune(sgn_state* st, const double* dt, const sgn_opts* opts,
                               sgn_stream stream, double* best_ms);
 /* Synchronises the stream used by the last step call and reports counters. */

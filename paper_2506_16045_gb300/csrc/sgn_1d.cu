@@ -215,6 +215,67 @@ __global__ void __launch_bounds__(NT, 1) k_dealias1d(const Inst1d* __restrict__ 
   }
 }
 
+// Right-hand side of the non-constraint form (Eq:dswe with the u_t terms grouped as in
+// Eq:MomEq), per instance: f_eta = -(eta u)_x and
+//   M = -eta u u_x - g eta zeta_x + (eta^3 Q/3 + eta^2 S/2)_x - h_x (eta^2 Q/2 + eta S),
+//   Q = u u_xx - u_x^2, S = u (h_x u)_x,
+// from three derivative pairs (u, h_x u), (u_x, zeta), (eta^3 Q/3 + eta^2 S/2, eta u) with
+// transforms in T; the pointwise terms are formed in float64.  w0, w1: two packed real
+// scratch fields.
+template <typename T, int NT, int MAXB>
+__global__ void __launch_bounds__(NT, 1) k_rhs_nc1d(const Inst1d* __restrict__ insts,
+                                                 const int* __restrict__ ids, cplx<double>* big,
+                                                 const cplx<T>* __restrict__ tw, double g,
+                                                 const double* __restrict__ eta_all,
+                                                 const double* __restrict__ u_all,
+                                                 const double* __restrict__ h_all,
+                                                 const double* __restrict__ hx_all,
+                                                 double* __restrict__ fe_all,
+                                                 double* __restrict__ M_all,
+                                                 double* __restrict__ w0_all,
+                                                 double* __restrict__ w1_all) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cplx<T>* buf = big ? reinterpret_cast<cplx<T>*>(big + ((size_t)blockIdx.x << kMaxLog1d))
+                     : reinterpret_cast<cplx<T>*>(smem);
+  const Inst1d I = insts[ids[blockIdx.x]];
+  const int n = I.n;
+  const double* eta = eta_all + I.off;
+  const double* u = u_all + I.off;
+  const double* h = h_all + I.off;
+  const double* hx = hx_all + I.off;
+  double* fe = fe_all + I.off;
+  double* M = M_all + I.off;
+  double* w0 = w0_all + I.off;
+  double* w1 = w1_all + I.off;
+  const T ku = num<T>(2.0 * kPi / I.L / (double)n);
+  // (u, h_x u) -> (d = u_x, s_x)
+  deriv_pair<T, NT, MAXB>(buf, n, I.log2n, ku,
+                          [&](int j) { return mk(num<T>(u[j]), num<T>(hx[j] * u[j])); }, tw);
+  for (int j = threadIdx.x; j < n; j += NT) {
+    w0[j] = to_f64(buf[j].x);
+    w1[j] = to_f64(buf[j].y);
+  }
+  __syncthreads();
+  // (d, zeta) -> (d_x, zeta_x); the local terms of M, and Phi into w1
+  deriv_pair<T, NT, MAXB>(buf, n, I.log2n, ku,
+                          [&](int j) { return mk(num<T>(w0[j]), num<T>(eta[j] - h[j])); }, tw);
+  for (int j = threadIdx.x; j < n; j += NT) {
+    const double e = eta[j], uj = u[j], d = w0[j], dx = to_f64(buf[j].x);
+    const double zx = to_f64(buf[j].y);
+    const double Q = uj * dx - d * d, S = uj * w1[j];
+    M[j] = -e * uj * d - g * e * zx - hx[j] * (e * e * Q * 0.5 + e * S);
+    w1[j] = e * e * e * Q * (1.0 / 3.0) + e * e * S * 0.5;
+  }
+  __syncthreads();
+  // (Phi, eta u) -> (Phi_x, (eta u)_x)
+  deriv_pair<T, NT, MAXB>(buf, n, I.log2n, ku,
+                          [&](int j) { return mk(num<T>(w1[j]), num<T>(eta[j] * u[j])); }, tw);
+  for (int j = threadIdx.x; j < n; j += NT) {
+    M[j] += to_f64(buf[j].x);
+    fe[j] = -to_f64(buf[j].y);
+  }
+}
+
 // double-float coefficients of Def:MatrixM computed from float64 eta and h_x on the fly
 struct CoefGlobalDF {
   const double* eta;
@@ -403,6 +464,31 @@ cudaError_t launch_dealias1d(const Layout1d& lay, const void* tw64, const void* 
     };
     if (dfp) return run(k_dealias1d<df, NT, MB>, static_cast<const cplx<df>*>(twT));
     return run(k_dealias1d<double, NT, MB>, static_cast<const cplx<double>*>(twT));
+  });
+}
+
+cudaError_t launch_rhs_nc1d(const Layout1d& lay, const void* tw64, const void* tw32,
+                            int precision, double g, const double* eta, const double* u,
+                            const double* h, const double* hx, double* f_eta, double* M,
+                            double* scratch, cudaStream_t s) {
+  const bool dfp = precision == SGN_PREC_MIXED;
+  const void* twT = dfp ? static_cast<const void*>(static_cast<const char*>(tw32) + kTw32Bytes)
+                        : tw64;
+  double* w1 = scratch + lay.points;
+  return for_each_class(lay, s, [&](auto NTc, auto MBc, int l, int first, int num, cudaStream_t s) {
+    constexpr int NT = decltype(NTc)::value, MB = decltype(MBc)::value;
+    const bool gl = l > kSmemLog1d;                // transform buffer in global scratch
+    const size_t sm = gl ? 0 : (size_t)16 << l;    // cplx<double> and cplx<df>: 16 bytes
+    cplx<double>* big = gl ? static_cast<cplx<double>*>(lay.big) : nullptr;
+    auto run = [&](auto kern, auto twp) -> cudaError_t {
+      cudaError_t e = set_smem(kern, sm);
+      if (e) return e;
+      kern<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, big, twp, g, eta, u, h, hx, f_eta,
+                               M, scratch, w1);
+      return cudaGetLastError();
+    };
+    if (dfp) return run(k_rhs_nc1d<df, NT, MB>, static_cast<const cplx<df>*>(twT));
+    return run(k_rhs_nc1d<double, NT, MB>, static_cast<const cplx<double>*>(twT));
   });
 }
 

@@ -868,7 +868,7 @@ struct sgn_state {
   double* u_s = nullptr;
   double* eta_p = nullptr;          // SBDF2 previous level
   double* U_p = nullptr;
-  double* u_p = nullptr;
+  double* ut = nullptr;             // non-constraint form: the last u_t (next warm start)
   void* res0 = nullptr;             // SBDF2 residual spectra (previous / current)
   void* res1 = nullptr;
   double* dt_dev = nullptr;
@@ -916,7 +916,7 @@ sgn_status alloc_state(sgn_state* st) {
       return SGN_ERR_NOMEM;
   }
   if (!(st->eta_s = get(P)) || !(st->U_s = get(V)) || !(st->u_s = get(V)) ||
-      !(st->eta_p = get(P)) || !(st->U_p = get(V)) || !(st->u_p = get(V)) ||
+      !(st->eta_p = get(P)) || !(st->U_p = get(V)) || !(st->ut = get(V)) ||
       !(st->dt_dev = get(st->lay->count)) || !(st->t_dev = get(st->lay->count)))
     return SGN_ERR_NOMEM;
   const size_t res_bytes = st->lay->dim == 1 ? sizeof(double) * 2 * (size_t)(st->lay->l1.ws_cplx /
@@ -1200,6 +1200,7 @@ extern "C" sgn_status sgn_state_init(sgn_state* st, sgn_stream stream) {
   if (e != cudaSuccess) return cuda_fail(ctx, e, "state init coefficients");
   SGN_CUDA(ctx, cudaMemsetAsync(st->stats, 0, sizeof(DevStats), s));
   SGN_CUDA(ctx, cudaMemsetAsync(st->t_dev, 0, sizeof(double) * st->lay->count, s));
+  SGN_CUDA(ctx, cudaMemsetAsync(st->ut, 0, sizeof(double) * st->d * st->P, s));
   st->hist = HIST_NONE;
   st->levels = 0;
   st->t = 0.0;
@@ -1502,6 +1503,82 @@ extern "C" sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nstep
   return SGN_OK;
 }
 
+namespace {
+
+// One RK4 step of the non-constraint form on (eta, u): stage i takes (f_eta, u_t) with
+// G_{eta_i,h} u_t = M(eta_i, u_i) (warm start from the previous u_t); u_t stages live in he[]
+// (the multistep history is reset), M in fU[].  U = G u afterwards.
+sgn_status rk4_nc_once(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
+  sgn_layout* lay = st->lay;
+  sgn_ctx* ctx = lay->ctx;
+  const int d = st->d;
+  const long long P = st->P;
+  static const double a[4] = {0.0, 0.5, 0.5, 1.0};
+  const double rtol_inner = o->rtol_inner > 0.0 ? o->rtol_inner : -1.0;
+  const int max_refine = o->max_refine > 0 ? o->max_refine : 12;
+  for (int i = 0; i < 4; ++i) {
+    const double* eta_i = st->eta;
+    const double* u_i = st->u;
+    if (i > 0) {
+      SGN_TRY(lincomb(st, st->eta_s, {{st->eta, 1.0}}, {{st->fe[i - 1], a[i]}}, 1, s, st->u_s,
+                      {{st->u, 1.0}}, {{st->he[i - 1], a[i]}}, d));
+      eta_i = st->eta_s;
+      u_i = st->u_s;
+    }
+    {
+      ProfScope prof(ctx, s, 1);
+      const cudaError_t e = sgn::launch_rhs_nc1d(lay->l1, ctx->tw64, ctx->tw32, o->prec,
+                                                 lay->grids[0].g, eta_i, u_i, st->h, st->gradh,
+                                                 st->fe[i], st->fU[i], lay->scratch, s);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "non-constraint rhs launch");
+    }
+    SGN_TRY(copy_field(st, st->he[i], i == 0 ? st->ut : st->he[i - 1], P, s));
+    {
+      ProfScope prof(ctx, s, 0);
+      const cudaError_t e = sgn::launch_pcg1d(
+          lay->l1, ctx->tw64, ctx->tw32, o->prec, eta_i, st->gradh, st->fU[i], st->he[i],
+          nullptr, o->coef, o->rtol, rtol_inner, o->maxit, max_refine, lay->rec, lay->ws,
+          lay->coef_df, s);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "pcg launch");
+    }
+    k_accum<<<1, 256, 0, s>>>(lay->rec, lay->l1.d_inst, lay->count, 0, 0,
+                             o->prec == SGN_PREC_MIXED, st->stats);
+    SGN_CUDA(ctx, cudaGetLastError());
+  }
+  const double b0 = 1.0 / 6.0, b1 = 1.0 / 3.0;
+  SGN_TRY(lincomb(st, st->eta, {{st->eta, 1.0}},
+                  {{st->fe[0], b0}, {st->fe[1], b1}, {st->fe[2], b1}, {st->fe[3], b0}}, 1, s,
+                  st->u, {{st->u, 1.0}},
+                  {{st->he[0], b0}, {st->he[1], b1}, {st->he[2], b1}, {st->he[3], b0}}, d));
+  const cudaError_t e =
+      sgn::launch_apply_G1d(lay->l1, ctx->tw64, st->eta, st->gradh, st->u, st->U, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "apply G");
+  SGN_TRY(copy_field(st, st->ut, st->he[3], P, s));
+  SGN_TRY(advance_time(st, s));
+  st->t += st->dt_last[0];
+  st->step += 1;
+  return SGN_OK;
+}
+
+}  // namespace
+
+extern "C" sgn_status sgn_step_rk4_nc(sgn_state* st, const double* dt, int nsteps,
+                                      const sgn_opts* opts, sgn_stream stream) {
+  if (!st || !dt || nsteps < 0) return SGN_ERR_INVALID_ARG;
+  if (st->lay->dim != 1 || st->force.K > 0 || st->dealias)
+    return fail(st->lay->ctx, SGN_ERR_INVALID_ARG,
+                "the non-constraint stepper takes 1d states without forcing or dealiasing");
+  DeviceGuard g(st->lay->device);
+  cudaStream_t s = as_stream(stream);
+  SGN_TRY(check_opts(st, opts));
+  SGN_TRY(upload_dt(st, dt, s));
+  st->last = s;
+  st->hist = HIST_NONE;                  // he[] holds u_t stages here
+  st->levels = 0;
+  for (int k = 0; k < nsteps; ++k) SGN_TRY(rk4_nc_once(st, opts, s));
+  return SGN_OK;
+}
+
 extern "C" sgn_status sgn_state_set_forcing(sgn_state* st, int nterms, const double* phi_eta,
                                             const double* phi_U, const double* omega,
                                             const double* theta) {
@@ -1591,25 +1668,36 @@ extern "C" sgn_status sgn_state_autotune(sgn_state* st, const double* dt, const 
       L.rform[cls[i]] = (c >> (2 * i + 1)) & 1 ? 2 : 1;
     }
   };
+  // Each combination is timed as steps run in production: its own captured step graph
+  // (two untimed steps: direct launches, then capture), then three timed replays, in two
+  // passes over all combinations, keeping each one's faster pass.  (Timed on direct
+  // launches, two-CTA forms for n = 8192 looked 3% faster and replayed 5% slower.)  A
+  // combination other than the default (one CTA everywhere) is taken only when it is at
+  // least 3% faster: a winner within the timing noise of a few steps would be a coin toss.
   const int combos = 1 << (2 * (int)cls.size());
-  int best = 0;
-  float best_t = 0.0f;
-  for (int c = 0; c < combos && !r; ++c) {
-    apply(c);
-    r = rk4_once(st, opts, s);
-    if (!r) r = copy3(false);
-    if (!r && cudaEventRecord(e0, s) != cudaSuccess) r = cuda_fail(ctx, cudaGetLastError(), "autotune");
-    for (int k = 0; k < 2 && !r; ++k) r = rk4_once(st, opts, s);
-    float ms = 0.0f;
-    if (!r && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-               cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-      r = cuda_fail(ctx, cudaGetLastError(), "autotune timing");
-    if (!r) r = copy3(false);
-    if (!r && (c == 0 || ms < best_t)) {
-      best = c;
-      best_t = ms;
+  constexpr int kTimed = 3;
+  std::vector<float> t_of(combos, 0.0f);
+  for (int pass = 0; pass < 2 && !r; ++pass) {
+    for (int c = 0; c < combos && !r; ++c) {
+      apply(c);
+      L.gen += 1;                                  // a new graph key: capture this form
+      for (int k = 0; k < 2 && !r; ++k) r = rk4_step(st, opts, s);
+      if (!r) r = copy3(false);
+      if (!r && cudaEventRecord(e0, s) != cudaSuccess)
+        r = cuda_fail(ctx, cudaGetLastError(), "autotune");
+      for (int k = 0; k < kTimed && !r; ++k) r = rk4_step(st, opts, s);
+      float ms = 0.0f;
+      if (!r && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                 cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        r = cuda_fail(ctx, cudaGetLastError(), "autotune timing");
+      if (!r) r = copy3(false);
+      if (!r && (pass == 0 || ms < t_of[c])) t_of[c] = ms;
     }
   }
+  int best = 0;
+  for (int c = 1; c < combos; ++c)
+    if (t_of[c] < 0.97f * t_of[0] && t_of[c] < t_of[best]) best = c;
+  const float best_t = t_of[best];
   apply(best);
   L.gen += 1;
   if (e0) cudaEventDestroy(e0);
@@ -1618,7 +1706,7 @@ extern "C" sgn_status sgn_state_autotune(sgn_state* st, const double* dt, const 
   cudaFree(save);
   st->last = s;
   if (r) return r;
-  if (best_ms) *best_ms = best_t / 2.0;
+  if (best_ms) *best_ms = best_t / kTimed;
   return SGN_OK;
 }
 

@@ -112,6 +112,13 @@ cudaError_t launch_axpy1d(const Layout1d& lay, const double* dt, double* out, co
 cudaError_t launch_dealias1d(const Layout1d& lay, const void* tw64, const void* tw32,
                              int precision, const double* h, double* eta, double* U, double* u,
                              cudaStream_t s);
+// Non-constraint form (Eq:dswe / Eq:MomEq): f_eta = -(eta u)_x and M, the u_t-free terms
+// with G u_t = M (transforms in float64, or double-float for SGN_PREC_MIXED); scratch:
+// 2 P doubles
+cudaError_t launch_rhs_nc1d(const Layout1d& lay, const void* tw64, const void* tw32,
+                            int precision, double g, const double* eta, const double* u,
+                            const double* h, const double* hx, double* f_eta, double* M,
+                            double* scratch, cudaStream_t s);
 // SBDF2 velocity update in one launch (transforms in float64, or double-float for
 // SGN_PREC_MIXED): res1_hat = (sigma + alpha k^2) u_hat - (G u - U)_hat, and with `solve`
 // u <- A^{-1} iFFT(c1 res1_hat + c0 res0_hat) in place.

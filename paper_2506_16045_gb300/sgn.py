@@ -97,6 +97,8 @@ SIGNATURES = [
     ("sgn_state_create", C.c_int, [_VP, _VP, _DP, _DP, _DP, _DP, _DP, C.POINTER(_VP)]),
     ("sgn_state_init", C.c_int, [_VP, _VP]),
     ("sgn_step_rk4", C.c_int, [_VP, C.POINTER(C.c_double), C.c_int, C.POINTER(SgnOpts), _VP]),
+    ("sgn_step_rk4_nc", C.c_int, [_VP, C.POINTER(C.c_double), C.c_int, C.POINTER(SgnOpts),
+                                  _VP]),
     ("sgn_step_abk", C.c_int, [_VP, C.c_int, C.POINTER(C.c_double), C.c_int, C.POINTER(SgnOpts),
                                _VP]),
     ("sgn_step_linimp", C.c_int, [_VP, C.POINTER(C.c_double), C.c_int, C.POINTER(SgnOpts), _VP]),
@@ -390,6 +392,14 @@ class State:
         o = self._opts(rtol, maxit, prec, coef, rtol_inner, max_refine)
         self.lay.ctx.check(self.lay.ctx.lib.sgn_step_rk4(self.h, self._dt(dt), nsteps, C.byref(o),
                                                          _stream(stream)), "sgn_step_rk4")
+
+    def rk4_nc(self, dt, nsteps, rtol=1e-12, maxit=2000, prec=PREC_FP64, coef=COEF_OPT,
+               rtol_inner=0.0, max_refine=0, stream=None):
+        """sgn_step_rk4_nc: RK4 on the non-constraint form (eta, u), 1d."""
+        o = self._opts(rtol, maxit, prec, coef, rtol_inner, max_refine)
+        self.lay.ctx.check(self.lay.ctx.lib.sgn_step_rk4_nc(self.h, self._dt(dt), nsteps,
+                                                            C.byref(o), _stream(stream)),
+                           "sgn_step_rk4_nc")
 
     def abk(self, order, dt, nsteps, rtol=1e-12, maxit=2000, prec=PREC_FP64, coef=COEF_OPT,
             rtol_inner=0.0, max_refine=0, stream=None):
