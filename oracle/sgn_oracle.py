@@ -493,6 +493,42 @@ def rhs_2d(eta, u, h, gradh, Lx, Ly, g):
     return f_eta, f_U
 
 
+def rhs_nc_2d(eta, u, h, gradh, Lx, Ly, g):
+    """2d form of rhs_nc_1d (Eq:MomEq): G u_t = M with
+      M = -eta (u.grad) u - g eta grad zeta + grad(eta^3 Q/3 + eta^2 S/2)
+          - grad h (eta^2 Q/2 + eta S),
+    d = div u, Q = u.grad d - d^2, s = grad h . u, S = u.grad s.  Returns (f_eta, M)."""
+    uu, vv = u
+    hx, hy = gradh
+    zeta = eta - h
+    d = dx2(uu, Lx) + dy2(vv, Ly)
+    s = hx * uu + hy * vv
+    S = uu * dx2(s, Lx) + vv * dy2(s, Ly)
+    Q = uu * dx2(d, Lx) + vv * dy2(d, Ly) - d * d
+    Phi = eta ** 3 * Q / 3.0 + eta ** 2 * S / 2.0
+    Psi = eta ** 2 * Q / 2.0 + eta * S
+    M = np.empty_like(u)
+    M[0] = (-eta * (uu * dx2(uu, Lx) + vv * dy2(uu, Ly)) - g * eta * dx2(zeta, Lx)
+            + dx2(Phi, Lx) - hx * Psi)
+    M[1] = (-eta * (uu * dx2(vv, Lx) + vv * dy2(vv, Ly)) - g * eta * dy2(zeta, Ly)
+            + dy2(Phi, Ly) - hy * Psi)
+    return -(dx2(eta * uu, Lx) + dy2(eta * vv, Ly)), M
+
+
+def dGdt_2d(eta, eta_t, gradh, u, Lx, Ly):
+    """d/dt (G_{eta(t),h} u) with u and h fixed (2d Def:G by the product rule):
+    eta_t u - grad(eta^2 eta_t d) - grad(eta eta_t s) + eta eta_t grad h d + eta_t grad h s."""
+    hx, hy = gradh
+    d = dx2(u[0], Lx) + dy2(u[1], Ly)
+    s = hx * u[0] + hy * u[1]
+    t1 = eta ** 2 * eta_t * d
+    t2 = eta * eta_t * s
+    out = np.empty_like(u)
+    out[0] = eta_t * u[0] - dx2(t1, Lx) - dx2(t2, Lx) + eta * eta_t * hx * d + eta_t * hx * s
+    out[1] = eta_t * u[1] - dy2(t1, Ly) - dy2(t2, Ly) + eta * eta_t * hy * d + eta_t * hy * s
+    return out
+
+
 def rhs(eta, u, h, gradh, grid):
     if grid["dim"] == 1:
         return rhs_1d(eta, u, h, gradh, grid["Lx"], grid["g"])
@@ -620,24 +656,28 @@ def rk4_nc_step(st: State, dt, rtol=1e-12, maxit=2000):
     that the same time discretisations apply to Eq:dswe): each stage takes
     k = (f_eta, u_t) with G_{eta_i,h} u_t = M(eta_i, u_i) solved by PCG (warm start from the
     previous stage's u_t).  U = G u is refreshed at the end so the state stays consistent.
-    1d, without forcing or dealiasing."""
+    1d and 2d, without forcing or dealiasing."""
     grid = st.grid
-    if grid["dim"] != 1 or st.forcing is not None or st.dealias:
-        raise ValueError("the non-constraint stepper is 1d, without forcing or dealiasing")
-    L, g = grid["Lx"], grid["g"]
+    if st.forcing is not None or st.dealias:
+        raise ValueError("the non-constraint stepper takes no forcing or dealiasing")
+    g = grid["g"]
+    if grid["dim"] == 1:
+        rhs_nc = lambda e, v: rhs_nc_1d(e, v, st.h, st.gradh, grid["Lx"], g)
+    else:
+        rhs_nc = lambda e, v: rhs_nc_2d(e, v, st.h, st.gradh, grid["Lx"], grid["Ly"], g)
     eta_n, u_n = st.eta, st.u
     fe, ut = [], []
     ut_prev = getattr(st, "ut", np.zeros_like(u_n))
     for i in range(4):
         eta_i = eta_n + dt * sum(RK4_A[i][j] * fe[j] for j in range(i))
         u_i = u_n + dt * sum(RK4_A[i][j] * ut[j] for j in range(i))
-        f_eta, M = rhs_nc_1d(eta_i, u_i, st.h, st.gradh, L, g)
+        f_eta, M = rhs_nc(eta_i, u_i)
         ut_prev = _solve(st, eta_i, M, ut_prev, rtol, maxit)
         fe.append(f_eta)
         ut.append(ut_prev)
     st.eta = eta_n + dt * sum(RK4_B[j] * fe[j] for j in range(4))
     st.u = u_n + dt * sum(RK4_B[j] * ut[j] for j in range(4))
-    st.U = apply_G_1d(st.eta, st.gradh, st.u, L)
+    st.U = apply_G(st.eta, st.gradh, st.u, grid)
     st.ut = ut_prev
     st.t += dt
     return st

@@ -713,3 +713,27 @@ def test_nonconstraint_rk4_solitary_wave_and_constraint_form():
         assert np.abs(O.apply_G_1d(a.eta, a.gradh, a.u, c.L) - a.U).max() < 1e-12
         diffs.append(np.abs(a.eta - b.eta).max())
     assert math.log2(diffs[0] / diffs[1]) > 3.5, diffs
+
+
+def test_momentum_form_equals_the_constraint_form_2d():
+    """The 2d Eq:MomEq terms against the 2d DAE form with the product rule (dG/dt in 2d,
+    itself checked against a central difference of the operator in eta)."""
+    nx, ny, Lx, Ly = 48, 32, 20.0, 12.0
+    X, Y = I.grid_2d(nx, ny, Lx, Ly)
+    ax, ay = 2 * np.pi * X / Lx, 2 * np.pi * Y / Ly
+    h = 1.0 - 0.3 * np.exp(np.cos(ax) + np.cos(ay) - 2.0)
+    gh = O.grad(h, (Lx, Ly))
+    eta = h + 0.15 * np.exp(np.cos(ax + 1.0) * np.cos(ay) - 1.0)
+    u = np.stack([0.3 * np.sin(ax) * np.exp(0.5 * np.cos(ay)),
+                  0.2 * np.cos(ay + 0.5) * np.exp(0.3 * np.sin(ax))])
+    e = np.cos(ax) * np.sin(2 * ay)
+    eps = 1e-5
+    fd = (O.apply_G_2d(eta + eps * e, gh, u, Lx, Ly) -
+          O.apply_G_2d(eta - eps * e, gh, u, Lx, Ly)) / (2 * eps)
+    an = O.dGdt_2d(eta, e, gh, u, Lx, Ly)
+    assert np.abs(fd - an).max() <= 1e-8 * np.abs(an).max()
+    fe, fU = O.rhs_2d(eta, u, h, gh, Lx, Ly, 9.81)
+    fe2, M = O.rhs_nc_2d(eta, u, h, gh, Lx, Ly, 9.81)
+    np.testing.assert_allclose(fe2, fe, atol=1e-14)
+    other = fU - O.dGdt_2d(eta, fe, gh, u, Lx, Ly)
+    assert np.abs(M - other).max() <= 1e-12 * np.abs(M).max()
