@@ -249,15 +249,15 @@ sgn_status sgn_step_rk4(sgn_state* st, const double* dt, int nsteps, const sgn_o
 sgn_status sgn_step_abk(sgn_state* st, int order, const double* dt, int nsteps,
                         const sgn_opts* opts, sgn_stream stream);
 /* RK4 on the non-constraint form of the SGN equations (Eq:dswe; the remark of §5 that the
- * same time discretisations apply to it), 1d.  The state advances (eta, u) with the RK4
- * tableau of sgn_step_rk4; each stage takes eta_t = -(eta u)_x and u_t from
+ * same time discretisations apply to it), 1d and 2d.  The state advances (eta, u) with the
+ * RK4 tableau of sgn_step_rk4; each stage takes eta_t = -div(eta u) and u_t from
  * G_{eta,h} u_t = M, where M collects the u_t-free terms of Eq:MomEq
- * (M = -eta u u_x - g eta zeta_x + (eta^3 Q/3 + eta^2 S/2)_x - h_x (eta^2 Q/2 + eta S),
- * Q = u u_xx - u_x^2, S = u (h_x u)_x), solved by the PCG of sgn_pcg with the options
- * (warm start from the previous u_t).  U = G u is refreshed after every step, so other
- * steppers can continue from the state.  Right-hand side transforms in float64, or
- * double-float on the mixed path.  SGN_ERR_INVALID_ARG for a 2d state, or one with a
- * forcing or dealiasing set. */
+ * (M = -eta (u.grad)u - g eta grad zeta + grad(eta^3 Q/3 + eta^2 S/2)
+ *  - grad h (eta^2 Q/2 + eta S), Q = u.grad(div u) - (div u)^2, S = u.grad(grad h.u)),
+ * solved by the PCG of sgn_pcg with the options (warm start from the previous u_t).
+ * U = G u is refreshed after every step, so other steppers can continue from the state.
+ * Right-hand side transforms: 1d in float64, or double-float on the mixed path; 2d in
+ * float64.  SGN_ERR_INVALID_ARG for a state with a forcing or dealiasing set. */
 sgn_status sgn_step_rk4_nc(sgn_state* st, const double* dt, int nsteps, const sgn_opts* opts,
                            sgn_stream stream);
 /* Linearly implicit SBDF2 (Eq:MM with Table 1's SBDF2 row, §5.3): one A-solve per step,

@@ -1323,6 +1323,86 @@ cudaError_t launch_dealias2d(const Layout2d& L, const void* tw64, const double* 
   return cudaSuccess;
 }
 
+namespace {
+
+// Pointwise pieces of the 2d non-constraint right-hand side (planes of P doubles).
+__global__ void k2_nc_a(long long P, const double* __restrict__ eta, const double* __restrict__ h,
+                        const double* __restrict__ u, const double* __restrict__ v,
+                        const double* __restrict__ hx, const double* __restrict__ hy,
+                        const double* __restrict__ ux, const double* __restrict__ vy,
+                        double* __restrict__ d, double* __restrict__ sp, double* __restrict__ z,
+                        double* __restrict__ eu, double* __restrict__ ev) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
+       i += (long long)gridDim.x * blockDim.x) {
+    d[i] = ux[i] + vy[i];
+    sp[i] = hx[i] * u[i] + hy[i] * v[i];
+    z[i] = eta[i] - h[i];
+    eu[i] = eta[i] * u[i];
+    ev[i] = eta[i] * v[i];
+  }
+}
+
+struct NcB {
+  const double *eta, *u, *v, *hx, *hy, *ux, *uy, *vx, *vy, *d, *dx, *dy, *sx, *sy, *zx, *zy;
+  double *Mx, *My, *Phi;
+};
+
+__global__ void k2_nc_b(long long P, double g, NcB a) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double e = a.eta[i], u = a.u[i], v = a.v[i], d = a.d[i];
+    const double Q = u * a.dx[i] + v * a.dy[i] - d * d, S = u * a.sx[i] + v * a.sy[i];
+    const double Psi = e * e * Q * 0.5 + e * S;
+    a.Mx[i] = -e * (u * a.ux[i] + v * a.uy[i]) - g * e * a.zx[i] - a.hx[i] * Psi;
+    a.My[i] = -e * (u * a.vx[i] + v * a.vy[i]) - g * e * a.zy[i] - a.hy[i] * Psi;
+    a.Phi[i] = e * e * e * Q * (1.0 / 3.0) + e * e * S * 0.5;
+  }
+}
+
+__global__ void k2_nc_c(long long P, const double* __restrict__ phx, const double* __restrict__ phy,
+                        const double* __restrict__ eux, const double* __restrict__ evy,
+                        double* __restrict__ Mx, double* __restrict__ My,
+                        double* __restrict__ fe) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
+       i += (long long)gridDim.x * blockDim.x) {
+    Mx[i] += phx[i];
+    My[i] += phy[i];
+    fe[i] = -(eux[i] + evy[i]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_rhs_nc2d(const Layout2d& L, const void* tw64, double g, const double* eta,
+                            const double* u, const double* h, const double* gradh, double* f_eta,
+                            double* M, cudaStream_t s) {
+  const long long P = L.P;
+  double* w = L.rhs_w;                          // free real planes here
+  auto pl = [&](int k) { return w + (long long)k * P; };
+  const double* v = u + P;
+  const double* hx = gradh;
+  const double* hy = gradh + P;
+  const int nb = grid_for(P, 256);
+  cudaError_t e;
+  if ((e = launch_grad2d(L, tw64, u, pl(0), s))) return e;      // u_x, u_y
+  if ((e = launch_grad2d(L, tw64, v, pl(2), s))) return e;      // v_x, v_y
+  k2_nc_a<<<nb, 256, 0, s>>>(P, eta, h, u, v, hx, hy, pl(0), pl(3), pl(4), pl(5), pl(6), pl(7),
+                             pl(8));
+  if ((e = cudaGetLastError())) return e;
+  if ((e = launch_grad2d(L, tw64, pl(4), pl(9), s))) return e;  // d_x, d_y
+  if ((e = launch_grad2d(L, tw64, pl(5), pl(11), s))) return e; // s_x, s_y
+  if ((e = launch_grad2d(L, tw64, pl(6), pl(13), s))) return e; // zeta_x, zeta_y
+  NcB a{eta, u, v, hx, hy, pl(0), pl(1), pl(2), pl(3), pl(4), pl(9), pl(10), pl(11), pl(12),
+        pl(13), pl(14), M, M + P, pl(15)};
+  k2_nc_b<<<nb, 256, 0, s>>>(P, g, a);
+  if ((e = cudaGetLastError())) return e;
+  if ((e = launch_grad2d(L, tw64, pl(15), pl(16), s))) return e;  // Phi_x, Phi_y
+  if ((e = launch_grad2d(L, tw64, pl(7), pl(18), s))) return e;   // (eta u)_x
+  if ((e = launch_grad2d(L, tw64, pl(8), pl(20), s))) return e;   // (eta v)_y in pl(21)
+  k2_nc_c<<<nb, 256, 0, s>>>(P, pl(16), pl(17), pl(18), pl(21), M, M + P, f_eta);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_coeffs2d(const Layout2d& L, const double* eta, const double* gradh, int kind,
                             SolveRec* rec, cudaStream_t s) {
   k2_coeffs<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, eta, gradh, kind, L.parts, L.sc, rec);

@@ -48,6 +48,11 @@ cudaError_t launch_apply_G2d(const Layout2d& L, const void* tw64, const double* 
 // non-null, u (float64; uses the workspace planes)
 cudaError_t launch_dealias2d(const Layout2d& L, const void* tw64, const double* h, double* eta,
                              double* U, double* u, cudaStream_t s);
+// Non-constraint form in 2d (Eq:MomEq): f_eta = -div(eta u) and M (2 planes), float64;
+// uses the right-hand-side planes of the layout
+cudaError_t launch_rhs_nc2d(const Layout2d& L, const void* tw64, double g, const double* eta,
+                            const double* u, const double* h, const double* gradh, double* f_eta,
+                            double* M, cudaStream_t s);
 cudaError_t launch_precond2d(const Layout2d& L, const void* tw64, const SolveRec* rec,
                              const double* r, double* z, cudaStream_t s);
 // Runs as one cached graph whose refinement and inner loops are conditional (while) nodes

@@ -1506,54 +1506,47 @@ extern "C" sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nstep
 namespace {
 
 // One RK4 step of the non-constraint form on (eta, u): stage i takes (f_eta, u_t) with
-// G_{eta_i,h} u_t = M(eta_i, u_i) (warm start from the previous u_t); u_t stages live in he[]
+// G_{eta_i,h} u_t = M(eta_i, u_i) (warm start from the previous u_t); u_t stages live in hU[]
 // (the multistep history is reset), M in fU[].  U = G u afterwards.
 sgn_status rk4_nc_once(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
   sgn_layout* lay = st->lay;
   sgn_ctx* ctx = lay->ctx;
   const int d = st->d;
-  const long long P = st->P;
+  const long long V = (long long)d * st->P;
+  const bool one_d = lay->dim == 1;
   static const double a[4] = {0.0, 0.5, 0.5, 1.0};
-  const double rtol_inner = o->rtol_inner > 0.0 ? o->rtol_inner : -1.0;
-  const int max_refine = o->max_refine > 0 ? o->max_refine : 12;
   for (int i = 0; i < 4; ++i) {
     const double* eta_i = st->eta;
     const double* u_i = st->u;
     if (i > 0) {
       SGN_TRY(lincomb(st, st->eta_s, {{st->eta, 1.0}}, {{st->fe[i - 1], a[i]}}, 1, s, st->u_s,
-                      {{st->u, 1.0}}, {{st->he[i - 1], a[i]}}, d));
+                      {{st->u, 1.0}}, {{st->hU[i - 1], a[i]}}, d));
       eta_i = st->eta_s;
       u_i = st->u_s;
     }
     {
       ProfScope prof(ctx, s, 1);
-      const cudaError_t e = sgn::launch_rhs_nc1d(lay->l1, ctx->tw64, ctx->tw32, o->prec,
-                                                 lay->grids[0].g, eta_i, u_i, st->h, st->gradh,
-                                                 st->fe[i], st->fU[i], lay->scratch, s);
+      const cudaError_t e =
+          one_d ? sgn::launch_rhs_nc1d(lay->l1, ctx->tw64, ctx->tw32, o->prec, lay->grids[0].g,
+                                       eta_i, u_i, st->h, st->gradh, st->fe[i], st->fU[i],
+                                       lay->scratch, s)
+                : sgn::launch_rhs_nc2d(lay->l2, ctx->tw64, lay->grids[0].g, eta_i, u_i, st->h,
+                                       st->gradh, st->fe[i], st->fU[i], s);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "non-constraint rhs launch");
     }
-    SGN_TRY(copy_field(st, st->he[i], i == 0 ? st->ut : st->he[i - 1], P, s));
-    {
-      ProfScope prof(ctx, s, 0);
-      const cudaError_t e = sgn::launch_pcg1d(
-          lay->l1, ctx->tw64, ctx->tw32, o->prec, eta_i, st->gradh, st->fU[i], st->he[i],
-          nullptr, o->coef, o->rtol, rtol_inner, o->maxit, max_refine, lay->rec, lay->ws,
-          lay->coef_df, s);
-      if (e != cudaSuccess) return cuda_fail(ctx, e, "pcg launch");
-    }
-    k_accum<<<1, 256, 0, s>>>(lay->rec, lay->l1.d_inst, lay->count, 0, 0,
-                             o->prec == SGN_PREC_MIXED, st->stats);
-    SGN_CUDA(ctx, cudaGetLastError());
+    SGN_TRY(copy_field(st, st->hU[i], i == 0 ? st->ut : st->hU[i - 1], V, s));
+    SGN_TRY(solve_at(st, eta_i, st->fU[i], st->hU[i], o, s));
   }
   const double b0 = 1.0 / 6.0, b1 = 1.0 / 3.0;
   SGN_TRY(lincomb(st, st->eta, {{st->eta, 1.0}},
                   {{st->fe[0], b0}, {st->fe[1], b1}, {st->fe[2], b1}, {st->fe[3], b0}}, 1, s,
                   st->u, {{st->u, 1.0}},
-                  {{st->he[0], b0}, {st->he[1], b1}, {st->he[2], b1}, {st->he[3], b0}}, d));
+                  {{st->hU[0], b0}, {st->hU[1], b1}, {st->hU[2], b1}, {st->hU[3], b0}}, d));
   const cudaError_t e =
-      sgn::launch_apply_G1d(lay->l1, ctx->tw64, st->eta, st->gradh, st->u, st->U, s);
+      one_d ? sgn::launch_apply_G1d(lay->l1, ctx->tw64, st->eta, st->gradh, st->u, st->U, s)
+            : sgn::launch_apply_G2d(lay->l2, ctx->tw64, st->eta, st->gradh, st->u, st->U, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "apply G");
-  SGN_TRY(copy_field(st, st->ut, st->he[3], P, s));
+  SGN_TRY(copy_field(st, st->ut, st->hU[3], V, s));
   SGN_TRY(advance_time(st, s));
   st->t += st->dt_last[0];
   st->step += 1;
@@ -1565,15 +1558,15 @@ sgn_status rk4_nc_once(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
 extern "C" sgn_status sgn_step_rk4_nc(sgn_state* st, const double* dt, int nsteps,
                                       const sgn_opts* opts, sgn_stream stream) {
   if (!st || !dt || nsteps < 0) return SGN_ERR_INVALID_ARG;
-  if (st->lay->dim != 1 || st->force.K > 0 || st->dealias)
+  if (st->force.K > 0 || st->dealias)
     return fail(st->lay->ctx, SGN_ERR_INVALID_ARG,
-                "the non-constraint stepper takes 1d states without forcing or dealiasing");
+                "the non-constraint stepper takes states without forcing or dealiasing");
   DeviceGuard g(st->lay->device);
   cudaStream_t s = as_stream(stream);
   SGN_TRY(check_opts(st, opts));
   SGN_TRY(upload_dt(st, dt, s));
   st->last = s;
-  st->hist = HIST_NONE;                  // he[] holds u_t stages here
+  st->hist = HIST_NONE;                  // hU[] holds u_t stages here
   st->levels = 0;
   for (int k = 0; k < nsteps; ++k) SGN_TRY(rk4_nc_once(st, opts, s));
   return SGN_OK;

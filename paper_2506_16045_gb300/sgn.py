@@ -395,7 +395,7 @@ class State:
 
     def rk4_nc(self, dt, nsteps, rtol=1e-12, maxit=2000, prec=PREC_FP64, coef=COEF_OPT,
                rtol_inner=0.0, max_refine=0, stream=None):
-        """sgn_step_rk4_nc: RK4 on the non-constraint form (eta, u), 1d."""
+        """sgn_step_rk4_nc: RK4 on the non-constraint form (eta, u), 1d and 2d."""
         o = self._opts(rtol, maxit, prec, coef, rtol_inner, max_refine)
         self.lay.ctx.check(self.lay.ctx.lib.sgn_step_rk4_nc(self.h, self._dt(dt), nsteps,
                                                             C.byref(o), _stream(stream)),
