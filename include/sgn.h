@@ -187,8 +187,8 @@ sgn_status sgn_pcg(sgn_ctx* ctx, const sgn_layout* lay, const double* eta, const
  *   info: HOST array [count] or NULL; iters = Arnoldi steps, refinements = cycles,
  *   rel_resid_Ainv = the final true sqrt(r.A^{-1}r) / sqrt(b.A^{-1}b), status.
  * The call allocates 2 (restart + 2) vectors of the layout's packed size on the stream,
- * synchronises the stream after every Arnoldi step (the host drives the cycles) and before
- * returning, and returns the worst instance status (SGN_ERR_NOT_CONVERGED at maxit,
+ * synchronises the stream every four Arnoldi steps and at the end of each cycle (the host
+ * drives the cycles) and before returning, and returns the worst instance status (SGN_ERR_NOT_CONVERGED at maxit,
  * SGN_ERR_BREAKDOWN on NaN/Inf, SGN_ERR_NONPOSITIVE_DEPTH from the coefficients). */
 #define SGN_GMRES_MAX_RESTART 64
 sgn_status sgn_gmres(sgn_ctx* ctx, const sgn_layout* lay, const double* eta, const double* gradh,

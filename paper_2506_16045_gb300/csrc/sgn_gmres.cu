@@ -22,7 +22,7 @@
 // Vectors are cut into chunks of kChunk elements that never straddle two instances; every
 // dot product is a sum of per-chunk partials taken in chunk order, so an instance's result
 // does not depend on what else is in the batch.  The host drives the cycles and reads one
-// counter of still-running instances after every step (a stream synchronisation).
+// counter of still-running instances every kCheck steps (a stream synchronisation).
 // Arithmetic is float64 throughout.
 #include <algorithm>
 #include <cmath>
@@ -38,6 +38,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kChunk = 4096;                    // vector elements per chunk
 constexpr int kPer = kChunk / kThreads;         // elements per thread
+constexpr int kCheck = 4;                       // Arnoldi steps between host checks
 
 struct Chunk {
   int inst;
@@ -475,8 +476,12 @@ cudaError_t run_gmres(const GmresArgs& a, cudaStream_t s) {
         k_gm_givens<<<ib, 128, 0, s>>>(count, d_fi, d_nc, gm, partial, ld, H, cs, sn, g, m, j,
                                        a.rtol, a.maxit, run);
         GM_TRY(cudaGetLastError());
-        GM_TRY(read_running(nrun));
-        if (nrun == 0) break;
+        // the host looks at the running count every kCheck steps (and at the cycle's end):
+        // instances that stopped skip the steps launched in between
+        if ((j + 1) % kCheck == 0 || j + 1 == m) {
+          GM_TRY(read_running(nrun));
+          if (nrun == 0) break;
+        }
         k_gm_scale<<<nc, kThreads, 0, s>>>(d_ch, gm, w, t, V + (long long)(j + 1) * vlen,
                                            Z + (long long)(j + 1) * vlen);
         GM_TRY(cudaGetLastError());
