@@ -194,3 +194,22 @@ def test_dealiased_2d_steppers_match_oracle(S, scheme):
     assert rel(uu, ref.u) < 1e-10 and rel(UU, ref.U) < 1e-10
     assert top_energy_2d(e - c["h"]) < 1e-13
     assert top_energy_2d(UU) < 1e-13
+
+
+@pytest.mark.parametrize("dealias", [False, True])
+def test_mixed_sbdf2_ragged_with_the_cluster_size(S, dealias):
+    """The double-float SBDF2 kernel and the double-float projection on every transform
+    path (shared memory up to n = 8192, the global buffer at n = 16384) against the oracle's
+    float64 steps."""
+    sgn, ctx = S
+    dt = 0.25 * (200.0 / 16384) / np.sqrt(9.81 * 1.3)
+    insts = [I.shelf_case(n=n, L=200.0, a=0.3, x0=40.0, r=0.5, xs=45.0, dt=dt)
+             for n in (1024, 8192, 16384)]
+    (eta, U, u), stats = run_gpu(sgn, ctx, insts, "sbdf2", [(dealias, 6)], sgn.PREC_MIXED,
+                                 1e-12)
+    assert stats["status"] == 0
+    for i, c in enumerate(insts):
+        ref = run_oracle(c, "sbdf2", [(dealias, 6)])
+        assert rel(eta[i] - c.h, ref.eta - c.h) < 1e-6 and rel(u[i], ref.u) < 1e-6, c.n
+        if dealias:
+            assert top_energy(eta[i] - c.h) < 1e-13 and top_energy(u[i]) < 1e-12, c.n
