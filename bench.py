@@ -55,6 +55,8 @@ def parse():
                          "line (for profiling one workload; not the headline)")
     ap.add_argument("--n2d", type=int, default=512, choices=[128, 256, 512, 1024],
                     help="grid side of the bump_2d configuration")
+    ap.add_argument("--shelf-steps", type=int, default=2000,
+                    help="steps per run of the shelf_1d configuration (2000: the whole run)")
     return ap.parse_args()
 
 
@@ -928,7 +930,8 @@ def main():
 
         from paper_2506_16045_gb300 import sgn
         ctx = sgn.Context(0)
-        fn = {"shelf_1d": bench_shelf, "bump_2d": lambda *a: bench_2d(*a, n=args.n2d),
+        fn = {"shelf_1d": lambda *a: bench_shelf(*a, steps=args.shelf_steps),
+              "bump_2d": lambda *a: bench_2d(*a, n=args.n2d),
               "serving": bench_serving, "robustness": bench_robustness,
               "manufactured": bench_manufactured}
         print(json.dumps({args.only_config: fn[args.only_config](sgn, ctx, torch)}))
