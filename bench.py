@@ -34,7 +34,9 @@ METRIC = "SGN grid-point-steps/s batched vs plain at ≤1e-6 rel err; p50/p99 so
 UNIT = "grid-point-steps/s"
 FULL_STEPS = 200            # the ensemble configuration's run length
 FP32_PEAK = 152 * 128 * 2 * 2.07e9          # FMA lanes x 2 flops x max SM clock
-DF_COST = 9.6     # float32 ops per double-float flop in an FFT butterfly
+# float32 operations per double-float flop in a complex FFT butterfly: a double-float add is
+# 11 float32 operations and a multiply 7, so a butterfly costs about 9.6 times its float32 form
+DF_COST = 9.6
 RTOL = 1e-10
 
 
@@ -448,7 +450,7 @@ def gpu_arm(args, world, rank, local, pg):
 
     # ---- roofline of the dominant kernel (the PCG launch groups, timed in the region)
     # mixed path: the high-precision part runs in double-float, DF_COST float32 operations per
-    # nominal flop (see DESIGN.md); achieved is in float32-operation TFLOP/s
+    # nominal flop; achieved is in float32-operation TFLOP/s
     f32 = s1["flops32"] - s0["flops32"]
     fhi = s1["flops64"] - s0["flops64"]
     pcg_s = prof["pcg_ms"] * 1e-3
