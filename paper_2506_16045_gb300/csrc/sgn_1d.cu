@@ -277,14 +277,17 @@ __global__ void __launch_bounds__(NT, 1) k_rhs_nc1d(const Inst1d* __restrict__ i
 }
 
 // double-float coefficients of Def:MatrixM computed from float64 eta and h_x on the fly
+// (the products in double-float arithmetic, on the float32 units: only eta and h_x are
+// split from float64)
 struct CoefGlobalDF {
   const double* eta;
   const double* hx;
   __device__ __forceinline__ void operator()(int j, df& c1, df& c2, df& c3) const {
-    double e = eta[j], g = hx[j];
-    c1 = df(e * (1.0 + g * g));
-    c2 = df(0.5 * e * e * g);
-    c3 = df(e * e * e * (1.0 / 3.0));
+    const df e(eta[j]), g(hx[j]);
+    const df e2 = e * e;
+    c1 = e + e * (g * g);
+    c2 = half(e2 * g);
+    c3 = e2 * e * df(0.3333333432674408f, -9.934107758624577e-09f);   // 1/3, double-float
   }
 };
 
@@ -329,25 +332,27 @@ __global__ void __launch_bounds__(NT, 1) k_linimp_step1d(const Inst1d* __restric
   const double sigma = A[id].sigma, alpha = A[id].alpha;
   const double kunit = 2.0 * kPi / I.L;
   const long long hs = I.ws / kWsVectors;
-  cplx<double>* uh = ws + I.ws + (h + 1);
+  // u^ kept in the transforms' precision (cplx<df> and cplx<double> are both 16 bytes)
+  cplx<T>* uh = reinterpret_cast<cplx<T>*>(ws + I.ws + (h + 1));
   for (int j = threadIdx.x; j < n; j += NT) buf[j] = mk(num<T>(u_all[I.off + j]), num<T>(0.0));
   __syncthreads();
   cta_fft<T, NT, MAXB>(buf, n, I.log2n, false, tw);
   for (int m = threadIdx.x; m <= h; m += NT) {
     const cplx<T> v = buf[m];
-    uh[m] = mk(to_f64(v.x), (m == 0 || m == h) ? 0.0 : to_f64(v.y));   // real DC / Nyquist
+    uh[m] = mk(v.x, (m == 0 || m == h) ? num<T>(0.0) : v.y);   // real DC / Nyquist
   }
   __syncthreads();
   const Spec<T> sp = make_spec<T>(n, I.L, sigma, alpha);
   spectral_matvec<T, NT, MAXB>(
-      buf, sp, I.log2n, [&](int m) { return mk(num<T>(uh[m].x), num<T>(uh[m].y)); },
+      buf, sp, I.log2n, [&](int m) { return uh[m]; },
       typename CoefFor<T>::type{eta_all + I.off, hx_all + I.off}, nullptr, tw, U_all + I.off);
   // mode m owns buf[m] and buf[n - m]: it reads both (gv_mode) before writing both
   for (int m = threadIdx.x; m <= h; m += NT) {
     const double k = (m == h) ? 0.0 : kunit * (double)m;
     const cplx<T> g = gv_mode(buf, m, n, sp.k(m));             // (G u - U)^_m
     const double sym = sigma + alpha * k * k;
-    cplx<double> r = mk(uh[m].x * sym - to_f64(g.x), uh[m].y * sym - to_f64(g.y));
+    const T symT = num<T>(sym);
+    cplx<double> r = mk(to_f64(uh[m].x * symT - g.x), to_f64(uh[m].y * symT - g.y));
     if (m == 0 || m == h) r.y = 0.0;
     res1[hs + m] = r;
     if (SOLVE) {
