@@ -177,8 +177,10 @@ __global__ void k_axpy1d(const Inst1d* __restrict__ insts, const double* __restr
 }
 
 // Orszag's 2/3 rule on a new time level: the modes |j| > n/3 of zeta = eta - h, of U and
-// (if u is non-null) of u are set to zero, one field after the other in the CTA's buffer.
-// Transforms in T: float64, or double-float on the mixed path.
+// (if u is non-null) of u are set to zero.  zeta and U share one complex transform
+// (zeta + i U): the mask is symmetric in j and n - j, so masking the packed spectrum masks
+// both fields exactly, and a projection does not amplify the shared rounding.  u takes a
+// second transform.  Transforms in T: float64, or double-float on the mixed path.
 template <typename T, int NT, int MAXB>
 __global__ void __launch_bounds__(NT, 1) k_dealias1d(const Inst1d* __restrict__ insts,
                                                   const int* __restrict__ ids,
@@ -194,13 +196,14 @@ __global__ void __launch_bounds__(NT, 1) k_dealias1d(const Inst1d* __restrict__ 
   const Inst1d I = insts[ids[blockIdx.x]];
   const int n = I.n;
   const double inv_n = 1.0 / n, third = n / 3.0;
-  double* fields[3] = {eta_all, U_all, u_all};
-  for (int q = 0; q < 3; ++q) {
-    double* f = fields[q];
-    if (!f) continue;
-    const double* h = q == 0 ? h_all + I.off : nullptr;
+  const double* h = h_all + I.off;
+  double* eta = eta_all + I.off;
+  double* U = U_all + I.off;
+  for (int pass = 0; pass < 2; ++pass) {
+    double* f = pass == 0 ? eta : (u_all ? u_all + I.off : nullptr);
+    if (!f) break;
     for (int j = threadIdx.x; j < n; j += NT)
-      buf[j] = mk(num<T>(f[I.off + j] - (h ? h[j] : 0.0)), num<T>(0.0));
+      buf[j] = pass == 0 ? mk(num<T>(f[j] - h[j]), num<T>(U[j])) : mk(num<T>(f[j]), num<T>(0.0));
     __syncthreads();
     cta_fft<T, NT, MAXB>(buf, n, I.log2n, false, tw);
     for (int j = threadIdx.x; j < n; j += NT) {
@@ -209,9 +212,15 @@ __global__ void __launch_bounds__(NT, 1) k_dealias1d(const Inst1d* __restrict__ 
     }
     __syncthreads();
     cta_fft<T, NT, MAXB>(buf, n, I.log2n, true, tw);
-    for (int j = threadIdx.x; j < n; j += NT)
-      f[I.off + j] = to_f64(buf[j].x) * inv_n + (h ? h[j] : 0.0);
-    __syncthreads();                                    // buf is reused by the next field
+    for (int j = threadIdx.x; j < n; j += NT) {
+      if (pass == 0) {
+        f[j] = to_f64(buf[j].x) * inv_n + h[j];
+        U[j] = to_f64(buf[j].y) * inv_n;
+      } else {
+        f[j] = to_f64(buf[j].x) * inv_n;
+      }
+    }
+    __syncthreads();                                    // buf is reused by the next pass
   }
 }
 
