@@ -314,10 +314,11 @@ struct CoefFor<df> {
 // One SBDF2 velocity update in one launch, transforms in T (float64, or double-float for
 // the mixed path):
 //   res1^ = (sigma + alpha k^2) u^ - (G u - U)^           stored as a half spectrum (float64)
-//   u    <- F^{-1}[(c1 res1^ + c0 res0^) / (sigma + alpha k^2)]   (SOLVE only)
-// u is read at the start and, with SOLVE, overwritten at the end by the same CTA, so the
-// caller's buffer takes the new level in place.  Without SOLVE (the start-up level) only
-// res1^ is produced.  The per-mode combinations run in float64.
+//   u_out <- F^{-1}[(c1 res1^ + c0 res0^) / (sigma + alpha k^2)]   (SOLVE only)
+// u_out may be u itself (the CTA reads u before it writes).  Without SOLVE (the start-up
+// level) only res1^ is produced.  With ux_out set, u_x (which the matvec's packed inverse
+// transform yields for free) is stored there in T, where the right-hand side of the same
+// level takes it instead of transforming u again.
 template <typename T, int NT, int MAXB, bool SOLVE>
 __global__ void __launch_bounds__(NT, 1) k_linimp_step1d(const Inst1d* __restrict__ insts,
                                                       const int* __restrict__ ids,
@@ -331,7 +332,9 @@ __global__ void __launch_bounds__(NT, 1) k_linimp_step1d(const Inst1d* __restric
                                                       const cplx<double>* __restrict__ res0,
                                                       cplx<double>* __restrict__ res1,
                                                       double c1, double c0,
-                                                      cplx<double>* __restrict__ ws) {
+                                                      cplx<double>* __restrict__ ws,
+                                                      double* __restrict__ u_out,
+                                                      void* __restrict__ ux_out) {
   extern __shared__ __align__(16) unsigned char smem[];
   cplx<T>* buf = big ? reinterpret_cast<cplx<T>*>(big + ((size_t)blockIdx.x << kMaxLog1d))
                      : reinterpret_cast<cplx<T>*>(smem);
@@ -354,7 +357,8 @@ __global__ void __launch_bounds__(NT, 1) k_linimp_step1d(const Inst1d* __restric
   const Spec<T> sp = make_spec<T>(n, I.L, sigma, alpha);
   spectral_matvec<T, NT, MAXB>(
       buf, sp, I.log2n, [&](int m) { return uh[m]; },
-      typename CoefFor<T>::type{eta_all + I.off, hx_all + I.off}, nullptr, tw, U_all + I.off);
+      typename CoefFor<T>::type{eta_all + I.off, hx_all + I.off}, nullptr, tw, U_all + I.off,
+      ux_out ? static_cast<T*>(ux_out) + I.off : nullptr);
   // mode m owns buf[m] and buf[n - m]: it reads both (gv_mode) before writing both
   for (int m = threadIdx.x; m <= h; m += NT) {
     const double k = (m == h) ? 0.0 : kunit * (double)m;
@@ -376,7 +380,7 @@ __global__ void __launch_bounds__(NT, 1) k_linimp_step1d(const Inst1d* __restric
   __syncthreads();
   cta_fft<T, NT, MAXB>(buf, n, I.log2n, true, tw);
   const double inv_n = 1.0 / n;
-  for (int j = threadIdx.x; j < n; j += NT) u_all[I.off + j] = to_f64(buf[j].x) * inv_n;
+  for (int j = threadIdx.x; j < n; j += NT) u_out[I.off + j] = to_f64(buf[j].x) * inv_n;
 }
 
 }  // namespace
@@ -510,7 +514,8 @@ cudaError_t launch_linimp_step1d(const Layout1d& lay, const void* tw64, const vo
                                  int precision, const SolveRec* A, const double* eta,
                                  const double* hx, double* u, const double* U,
                                  const void* res0_hat, void* res1_hat, double c1, double c0,
-                                 bool solve, void* ws, cudaStream_t s) {
+                                 bool solve, void* ws, double* u_out, void* ux_out,
+                                 cudaStream_t s) {
   const bool dfp = precision == SGN_PREC_MIXED;
   const void* twT = dfp ? static_cast<const void*>(static_cast<const char*>(tw32) + kTw32Bytes)
                         : tw64;
@@ -525,7 +530,7 @@ cudaError_t launch_linimp_step1d(const Layout1d& lay, const void* tw64, const vo
       kern<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, big, twp, A, eta, hx, u, U,
                                static_cast<const cplx<double>*>(res0_hat),
                                static_cast<cplx<double>*>(res1_hat), c1, c0,
-                               static_cast<cplx<double>*>(ws));
+                               static_cast<cplx<double>*>(ws), u_out ? u_out : u, ux_out);
       return cudaGetLastError();
     };
     auto twd = static_cast<const cplx<double>*>(twT);

@@ -124,11 +124,14 @@ __device__ __forceinline__ Spec<T> make_spec(int n, double L, double sigma, doub
 // ---------------------------------------------------------------------------------------
 // Inverse FFT of Z (already in buf), pointwise coefficients, forward FFT.
 // With wsub set, w - wsub is transformed instead of w, so the result is (G v - wsub)^.
+// With vxout set, the input's derivative v_x (the imaginary part of the packed inverse) is
+// stored there too, in T.
 template <typename T, int NT, int MAXB, typename Coef>
 __device__ __forceinline__ void matvec_core(cplx<T>* buf, int n, int log2n, const Coef& coef,
                                             double* __restrict__ vout,
                                             const cplx<T>* __restrict__ tw,
-                                            const double* __restrict__ wsub = nullptr) {
+                                            const double* __restrict__ wsub = nullptr,
+                                            T* __restrict__ vxout = nullptr) {
   cta_fft<T, NT, MAXB>(buf, n, log2n, true, tw);
   const T inv_n = num<T>(1.0 / (double)n);
   for (int j = threadIdx.x; j < n; j += NT) {
@@ -137,6 +140,7 @@ __device__ __forceinline__ void matvec_core(cplx<T>* buf, int n, int log2n, cons
     T c1, c2, c3;
     coef(j, c1, c2, c3);
     if (vout) vout[j] = to_f64(v);
+    if (vxout) vxout[j] = vx;
     T w = c1 * v + c2 * vx;
     if (wsub) w = w - num<T>(wsub[j]);
     buf[j] = mk(w, c2 * v + c3 * vx);
@@ -149,7 +153,8 @@ template <typename T, int NT, int MAXB, typename Get, typename Coef>
 __device__ __forceinline__ void spectral_matvec(cplx<T>* buf, const Spec<T>& sp, int log2n,
                                                 Get get, Coef coef, double* __restrict__ vout,
                                                 const cplx<T>* __restrict__ tw,
-                                                const double* __restrict__ wsub = nullptr) {
+                                                const double* __restrict__ wsub = nullptr,
+                                                T* __restrict__ vxout = nullptr) {
   const int n = sp.n, h = sp.h;
   const T one = from_int<T>(1);
   for (int m = threadIdx.x; m <= h; m += NT) {
@@ -161,7 +166,7 @@ __device__ __forceinline__ void spectral_matvec(cplx<T>* buf, const Spec<T>& sp,
     if (m > 0 && m < h) buf[n - m] = conj(v) * (one + k);
   }
   __syncthreads();
-  matvec_core<T, NT, MAXB>(buf, n, log2n, coef, vout, tw, wsub);
+  matvec_core<T, NT, MAXB>(buf, n, log2n, coef, vout, tw, wsub, vxout);
 }
 
 // (G v)_m = w_m - i k_m q_m = ((1 - k) Y_m + (1 + k) conj(Y_{n-m})) / 2

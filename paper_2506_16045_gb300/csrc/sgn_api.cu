@@ -1443,12 +1443,14 @@ extern "C" sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nstep
   const long long P = st->P, V = d * P;
   const bool one_d = st->lay->dim == 1;
   // 1d: the residual and the A-solve run as one launch (transforms in double-float on the
-  // mixed path) that writes the new u in place; 2d: residual and solve launches.
+  // mixed path) that writes the new u into u_s and hands u_x to the right-hand side of the
+  // same level; 2d: residual and solve launches.
   auto res_of = [&](const double* eta, const double* u, const double* U, void* out) -> sgn_status {
     cudaError_t e =
         one_d ? sgn::launch_linimp_step1d(st->lay->l1, ctx->tw64, ctx->tw32, st->prec,
                                           st->A_fixed, eta, st->gradh, const_cast<double*>(u),
-                                          U, nullptr, out, 0.0, 0.0, false, st->lay->ws, s)
+                                          U, nullptr, out, 0.0, 0.0, false, st->lay->ws,
+                                          nullptr, nullptr, s)
               : sgn::launch_linimp_res2d(st->lay->l2, ctx->tw64, st->A_fixed, eta, st->gradh, u,
                                          U, out, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "linimp residual");
@@ -1466,16 +1468,25 @@ extern "C" sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nstep
       st->hist = HIST_SBDF2;
       continue;
     }
-    // f_{n+1} into he[1] (before u is overwritten), then res_{n+1} into res1 and, in 1d, the
-    // new u in place
-    SGN_TRY(rhs_at(st, st->eta, st->u, st->he[1], st->hU[1], s));
+    // res_{n+1} into res1 and (1d) u_{n+2} into u_s with u_x handed over, then f_{n+1} into
+    // he[1] from the same level (2d: f_{n+1}, then the residual)
     if (one_d) {
-      cudaError_t e = sgn::launch_linimp_step1d(st->lay->l1, ctx->tw64, ctx->tw32, st->prec,
+      sgn_layout* lay = st->lay;
+      cudaError_t e = sgn::launch_linimp_step1d(lay->l1, ctx->tw64, ctx->tw32, st->prec,
                                                 st->A_fixed, st->eta, st->gradh, st->u, st->U,
-                                                st->res0, st->res1, 2.0, -1.0, true,
-                                                st->lay->ws, s);
+                                                st->res0, st->res1, 2.0, -1.0, true, lay->ws,
+                                                st->u_s, lay->scratch, s);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "linimp step");
+      {
+        ProfScope prof(ctx, s, 1);
+        e = sgn::launch_rhs1d_ux(lay->l1, ctx->tw64, ctx->tw32, st->prec, lay->grids[0].g,
+                                 st->eta, st->u, st->h, st->gradh, st->he[1], st->hU[1],
+                                 lay->scratch, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "rhs launch");
+      }
+      SGN_TRY(force_at(st, st->he[1], st->hU[1], 0.0, s));
     } else {
+      SGN_TRY(rhs_at(st, st->eta, st->u, st->he[1], st->hU[1], s));
       SGN_TRY(res_of(st->eta, st->u, st->U, st->res1));
     }
     SGN_TRY(lincomb(st, st->eta_s, {{st->eta, 4.0 / 3.0}, {st->eta_p, -1.0 / 3.0}},
@@ -1486,8 +1497,8 @@ extern "C" sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nstep
       cudaError_t e = sgn::launch_linimp_solve2d(st->lay->l2, ctx->tw64, st->A_fixed, st->res1,
                                                  st->res0, 2.0, -1.0, st->u_s, s);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "linimp solve");
-      SGN_TRY(copy_field(st, st->u, st->u_s, V, s));
     }
+    SGN_TRY(copy_field(st, st->u, st->u_s, V, s));
     SGN_TRY(copy_field(st, st->eta_p, st->eta, P, s));
     SGN_TRY(copy_field(st, st->U_p, st->U, V, s));
     SGN_TRY(copy_field(st, st->eta, st->eta_s, P, s));

@@ -121,12 +121,14 @@ cudaError_t launch_rhs_nc1d(const Layout1d& lay, const void* tw64, const void* t
                             double* scratch, cudaStream_t s);
 // SBDF2 velocity update in one launch (transforms in float64, or double-float for
 // SGN_PREC_MIXED): res1_hat = (sigma + alpha k^2) u_hat - (G u - U)_hat, and with `solve`
-// u <- A^{-1} iFFT(c1 res1_hat + c0 res0_hat) in place.
+// u_out <- A^{-1} iFFT(c1 res1_hat + c0 res0_hat) (u_out null: u in place).  ux_out
+// (nullable): u_x in the transforms' precision, as the solve's u_x hand-off stores it.
 cudaError_t launch_linimp_step1d(const Layout1d& lay, const void* tw64, const void* tw32,
                                  int precision, const SolveRec* A, const double* eta,
                                  const double* hx, double* u, const double* U,
                                  const void* res0_hat, void* res1_hat, double c1, double c0,
-                                 bool solve, void* ws, cudaStream_t s);
+                                 bool solve, void* ws, double* u_out, void* ux_out,
+                                 cudaStream_t s);
 
 struct Layout2d;
 
