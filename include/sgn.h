@@ -103,7 +103,9 @@ const char* sgn_status_string(sgn_status s);
 
 /* Packs `count` instances (host array `grids`).  count > 1 needs dim = 1 for every grid;
  * 2d layouts hold exactly one instance.  Allocates the layout's device descriptors and
- * spectral workspace. */
+ * spectral workspace.  Every call on a layout (and on the states bound to it) uses that
+ * workspace, so calls on one layout must be ordered: issue them on one stream, or order
+ * the streams; independent work runs concurrently on separate layouts. */
 sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid* grids, sgn_layout** out);
 void sgn_layout_destroy(sgn_layout* lay);
 /* Total packed points P (per component). */
