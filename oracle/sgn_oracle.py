@@ -22,7 +22,10 @@ Serre-Green-Naghdi Equations") in float64 numpy:
     option besides PCG;
   * the right-hand side of the DAE form (Eq:DAE_DSWE, §5) with the forcing F (Def:bigF);
   * RK4 (Eq:ERK, §5.1), Adams-Bashforth 2-4 (Eq:AB, Table 1, §5.2) and the linearly
-    implicit SBDF2 step (Eq:MM, §5.3).
+    implicit SBDF2 step (Eq:MM, §5.3);
+  * the manufactured solution of §6.4 Test 1 and its forcing;
+  * the 2/3-rule projection used as dealiasing (§6.4, Test 2 remark), and the
+    non-constraint form (Eq:dswe, Eq:MomEq) with its RK4 stepper (the remark of §5).
 
 Readings of the paper that the code takes (each one is listed with its reason in the
 design notes of the repository):
@@ -37,6 +40,7 @@ design notes of the repository):
   R8  time-stepping solves warm-start from the most recent velocity.
   R9  AB_s and SBDF2 take RK4 steps of the same dt for their start-up levels.
   R10 the SBDF2 preconditioner A is fixed from the initial data (§6.5).
+  R18 GMRES runs in the A^{-1} inner product, so it minimises the residual measure of R7.
   R19 optional dealiasing: Orszag's 2/3 rule applied to every new time level (zeta and U
       before u is solved from them; u too in SBDF2, where it is not solved from U); in 2d the
       tensor product of the 1d projections.
