@@ -566,9 +566,10 @@ def bench_shelf(sgn, ctx, torch, steps=2000):
     """1d shelf (N = 4096, L = 200, a = 0.3, ramp of width 5 at x = 60), whole 2000-step runs:
     AB4 with PCG (float64, and mixed refined to the same rtol 1e-12) against the linearly
     implicit SBDF2 step (float64 and mixed), each at its own stable step (AB4 dt 0.004, SBDF2
-    dt 0.002), and SBDF2 with 2/3-rule dealiasing over 4000 steps to t = 8, which it
-    reaches only with dealiasing.  Each run is timed with CUDA events from its initial state,
-    start-up steps included, after a short untimed run of the same kind."""
+    dt 0.002), SBDF2 with 2/3-rule dealiasing over 4000 steps to t = 8, which it reaches
+    only with dealiasing, and RK4 on the constraint and on the non-constraint form (mixed,
+    dt 0.004).  Each run is timed with CUDA events from its initial state, start-up steps
+    included, after a short untimed run of the same kind."""
     import numpy as np
 
     from paper_2506_16045_gb300 import inputs as I
@@ -578,11 +579,13 @@ def bench_shelf(sgn, ctx, torch, steps=2000):
                 ("ab4_mixed", "ab4", sgn.PREC_MIXED, 1e-12),
                 ("sbdf2_fp64", "sbdf2", sgn.PREC_FP64, 1e-12),
                 ("sbdf2_mixed", "sbdf2", sgn.PREC_MIXED, 1e-12),
-                ("sbdf2_mixed_dealiased_to_t8", "sbdf2", sgn.PREC_MIXED, 1e-12))
+                ("sbdf2_mixed_dealiased_to_t8", "sbdf2", sgn.PREC_MIXED, 1e-12),
+                ("rk4_mixed", "rk4", sgn.PREC_MIXED, 1e-12),
+                ("rk4_nc_mixed", "rk4_nc", sgn.PREC_MIXED, 1e-12))
     res, final = {}, {}
     for name, scheme, prec, rtol in variants:
         dealias = "dealiased" in name
-        dt = I.SHELF_DT[scheme]
+        dt = I.SHELF_DT.get(scheme, I.SHELF_DT["ab4"])
         nsteps = 2 * steps if dealias else steps          # the dealiased SBDF2 run goes to t = 8
         for k in (8, nsteps):
             eta, u, h = (torch.as_tensor(a, dtype=torch.float64, device="cuda")
@@ -596,6 +599,10 @@ def bench_shelf(sgn, ctx, torch, steps=2000):
             e0.record()
             if scheme == "sbdf2":
                 st.linimp(dt, k, rtol=rtol, maxit=4000, prec=prec)
+            elif scheme == "rk4":
+                st.rk4(dt, k, rtol=rtol, maxit=4000, prec=prec)
+            elif scheme == "rk4_nc":
+                st.rk4_nc(dt, k, rtol=rtol, maxit=4000, prec=prec)
             else:
                 st.abk(4, dt, k, rtol=rtol, maxit=4000, prec=prec)
             e1.record()
@@ -615,8 +622,12 @@ def bench_shelf(sgn, ctx, torch, steps=2000):
         (zm, um), (z6, u6) = final[s_ + "_mixed"], final[s_ + "_fp64"]
         res[s_ + "_mixed"]["rel_l2_zeta_vs_fp64"] = rel(zm, z6)
         res[s_ + "_mixed"]["rel_l2_u_vs_fp64"] = rel(um, u6)
-    return {"workload": f"1d shelf N=4096 L=200, {steps} steps per run (AB4 dt 0.004 to "
-                        f"t = {steps * 0.004:g}; SBDF2 dt 0.002 to t = {steps * 0.002:g}; "
+    # the constraint and non-constraint RK4 runs differ by their time discretisations only
+    (zc, uc), (zn, un) = final["rk4_mixed"], final["rk4_nc_mixed"]
+    res["rk4_nc_mixed"]["rel_l2_zeta_vs_rk4"] = rel(zn, zc)
+    res["rk4_nc_mixed"]["rel_l2_u_vs_rk4"] = rel(un, uc)
+    return {"workload": f"1d shelf N=4096 L=200, {steps} steps per run (AB4 and RK4 dt 0.004 "
+                        f"to t = {steps * 0.004:g}; SBDF2 dt 0.002 to t = {steps * 0.002:g}; "
                         f"dealiased SBDF2 dt 0.002 to t = {2 * steps * 0.002:g})",
             "unit": UNIT, **res}
 
