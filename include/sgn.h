@@ -256,7 +256,8 @@ sgn_status sgn_step_abk(sgn_state* st, int order, const double* dt, int nsteps,
  * G_{eta,h} u_t = M, where M collects the u_t-free terms of Eq:MomEq
  * (M = -eta (u.grad)u - g eta grad zeta + grad(eta^3 Q/3 + eta^2 S/2)
  *  - grad h (eta^2 Q/2 + eta S), Q = u.grad(div u) - (div u)^2, S = u.grad(grad h.u)),
- * solved by the PCG of sgn_pcg with the options (warm start from the previous u_t).
+ * solved by the PCG of sgn_pcg with the options (warm start from the previous u_t; the
+ * stage at c = 1 from 2 u_t(c = 1/2) - u_t(c = 0)).
  * U = G u is refreshed after every step, so other steppers can continue from the state.
  * Right-hand side transforms: 1d in float64, or double-float on the mixed path; 2d in
  * float64.  SGN_ERR_INVALID_ARG for a state with a forcing or dealiasing set. */

@@ -659,7 +659,7 @@ def rk4_nc_step(st: State, dt, rtol=1e-12, maxit=2000):
     """One RK4 step (Eq:ERK tableau) of the non-constraint form on (eta, u) (the remark of §5
     that the same time discretisations apply to Eq:dswe): each stage takes
     k = (f_eta, u_t) with G_{eta_i,h} u_t = M(eta_i, u_i) solved by PCG (warm start from the
-    previous stage's u_t).  U = G u is refreshed at the end so the state stays consistent.
+    previous stage's u_t; stage 4 from 2 u_t^(3) - u_t^(1), as R8's stage-4 start).  U = G u is refreshed at the end so the state stays consistent.
     1d and 2d, without forcing or dealiasing."""
     grid = st.grid
     if st.forcing is not None or st.dealias:
@@ -676,6 +676,8 @@ def rk4_nc_step(st: State, dt, rtol=1e-12, maxit=2000):
         eta_i = eta_n + dt * sum(RK4_A[i][j] * fe[j] for j in range(i))
         u_i = u_n + dt * sum(RK4_A[i][j] * ut[j] for j in range(i))
         f_eta, M = rhs_nc(eta_i, u_i)
+        if i == 3:                       # c = 1: extrapolate from c = 0 and c = 1/2
+            ut_prev = 2.0 * ut[2] - ut[0]
         ut_prev = _solve(st, eta_i, M, ut_prev, rtol, maxit)
         fe.append(f_eta)
         ut.append(ut_prev)

@@ -1545,7 +1545,11 @@ sgn_status rk4_nc_once(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
                                        st->gradh, st->fe[i], st->fU[i], s);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "non-constraint rhs launch");
     }
-    SGN_TRY(copy_field(st, st->hU[i], i == 0 ? st->ut : st->hU[i - 1], V, s));
+    // warm start: the previous u_t; stage 4 (c = 1) from 2 u_t^(3) - u_t^(1) (c = 1/2, 0)
+    if (i == 3)
+      SGN_TRY(lincomb(st, st->hU[3], {{st->hU[2], 2.0}, {st->hU[0], -1.0}}, {}, d, s));
+    else
+      SGN_TRY(copy_field(st, st->hU[i], i == 0 ? st->ut : st->hU[i - 1], V, s));
     SGN_TRY(solve_at(st, eta_i, st->fU[i], st->hU[i], o, s));
   }
   const double b0 = 1.0 / 6.0, b1 = 1.0 / 3.0;
