@@ -28,7 +28,10 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ("sgn_apply_operator", "sgn_precond_solve", "sgn_pcg", "sgn_step_rk4",
                  "sgn_step_abk", "sgn_step_linimp", "sgn_precond_coeffs", "sgn_rhs",
-                 "sgn_spectral_grad"):
+                 "sgn_spectral_grad", "sgn_gmres", "sgn_step_rk4_nc", "sgn_state_set_dealias",
+                 "sgn_state_set_forcing", "sgn_layout_set_forms", "sgn_state_autotune",
+                 "sgn_server_create", "sgn_batch_submit", "sgn_batch_poll",
+                 "sgn_pcg1d_noalloc"):
         assert must in names
 
 
