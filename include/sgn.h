@@ -232,6 +232,12 @@ typedef struct {
                                      float32) for SGN_PREC_MIXED */
   long long refinements;          /* SGN_PREC_MIXED: float32 inner solves (refinement passes
                                      less one per solve) since init; 0 for FP64 */
+  long long sbdf2_stability_warnings; /* SBDF2 instance-steps whose eta_max had grown past
+                                     (4/3)^(1/3) of its value at sgn_state_init: A is fixed
+                                     from the initial data (§6.5), and the generalised
+                                     eigenvalues of A^{-1} G then may leave SBDF2's
+                                     zero-stability interval (0, 4/3) (§5.4).  A warning, not
+                                     an error: re-initialise the state to refresh A */
 } sgn_state_stats;
 
 /* Binds caller-owned packed arrays: eta [P], U (vector), u (vector), h [P], gradh (vector,

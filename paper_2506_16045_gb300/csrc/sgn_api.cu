@@ -126,7 +126,31 @@ struct DevStats {
   double flops32;        // algorithmic float32 flops of the PCG solves
   double flops64;        // algorithmic float64 flops of the PCG solves
   long long refinements; // float32 inner solves (mixed)
+  long long sbdf2_warn;  // SBDF2 instance-steps whose eta_max left the fixed A's stable range
 };
+
+// SBDF2 guard (reading R10): A is fixed from the initial data; the generalised eigenvalues
+// of A^{-1} G grow like (eta_max / eta_max,0)^3, and SBDF2's zero-stability needs them below
+// 4/3.  One block per instance takes the level's eta_max and counts the instances past
+// that ratio.  (1d: insts; 2d: one instance of P points.)
+__global__ void k_sbdf2_guard(const Inst1d* __restrict__ insts, long long P,
+                              const double* __restrict__ eta, const SolveRec* __restrict__ A,
+                              DevStats* __restrict__ stats) {
+  __shared__ double red[32];
+  const long long off = insts ? insts[blockIdx.x].off : 0;
+  const long long n = insts ? insts[blockIdx.x].n : P;
+  double m = -1e300;
+  for (long long j = threadIdx.x; j < n; j += blockDim.x) m = fmax(m, eta[off + j]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    m = fmax(m, red[0]);
+    const double r = m / A[blockIdx.x].eta_max;
+    if (!(r * r * r < 4.0 / 3.0)) atomicAdd(reinterpret_cast<unsigned long long*>(&stats->sbdf2_warn), 1ull);
+  }
+}
 
 // Algorithmic flop model of one solve on n points (complex FFT of length n: 5 n log2 n):
 //   inner iteration: 2 FFTs + pointwise/vector work = 10 n log2 n + 26 n
@@ -1504,6 +1528,9 @@ extern "C" sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nstep
     SGN_TRY(copy_field(st, st->eta, st->eta_s, P, s));
     SGN_TRY(copy_field(st, st->U, st->U_s, V, s));
     SGN_TRY(dealias_at(st, st->eta, st->U, st->u, s));
+    k_sbdf2_guard<<<st->lay->count, 256, 0, s>>>(one_d ? st->lay->l1.d_inst : nullptr, st->P,
+                                                 st->eta, st->A_fixed, st->stats);
+    SGN_CUDA(ctx, cudaGetLastError());
     std::swap(st->he[0], st->he[1]);
     std::swap(st->hU[0], st->hU[1]);
     std::swap(st->res0, st->res1);
@@ -1734,6 +1761,7 @@ extern "C" sgn_status sgn_state_get_stats(sgn_state* st, sgn_state_stats* out) {
   out->flops32 = h.flops32;
   out->flops64 = h.flops64;
   out->refinements = h.refinements;
+  out->sbdf2_stability_warnings = h.sbdf2_warn;
   return SGN_OK;
 }
 

@@ -50,7 +50,7 @@ class SgnStateStats(C.Structure):
     _fields_ = [("solves", C.c_longlong), ("iterations", C.c_longlong), ("max_iters", C.c_int),
                 ("status", C.c_int), ("t", C.c_double), ("step", C.c_longlong),
                 ("flops32", C.c_double), ("flops64", C.c_double),
-                ("refinements", C.c_longlong)]
+                ("refinements", C.c_longlong), ("sbdf2_stability_warnings", C.c_longlong)]
 
 
 class SgnRequest(C.Structure):
@@ -449,7 +449,8 @@ class State:
                            "sgn_state_get_stats")
         return dict(solves=st.solves, iterations=st.iterations, max_iters=st.max_iters,
                     status=st.status, t=st.t, step=st.step, flops32=st.flops32,
-                    flops64=st.flops64, refinements=st.refinements)
+                    flops64=st.flops64, refinements=st.refinements,
+                    sbdf2_stability_warnings=st.sbdf2_stability_warnings)
 
     def close(self):
         if self.h:

@@ -349,3 +349,28 @@ def test_rk4_graph_replay_equals_direct_launches(S, prec):
     (ea, ua, ia, sa, ta), (eb, ub, ib, sb, tb) = outs
     assert np.array_equal(ea, eb) and np.array_equal(ua, ub)
     assert (ia, sa) == (ib, sb) and ta == tb
+
+
+def test_sbdf2_guard_counts_levels_past_the_fixed_A(S):
+    """SBDF2 keeps the A of the initial data (§6.5); the state counts the instance-steps
+    whose eta_max has grown past (4/3)^(1/3) of the initial one (the zero-stability bound of
+    §5.4 for the generalised eigenvalues).  A shelf run stays clear of it; a depth raised by
+    20% after init (ratio^3 = 1.73) is counted at every SBDF2 step."""
+    sgn, ctx = S
+    c = I.shelf_case(n=512, L=200.0, a=0.3, x0=40.0, r=0.5, xs=45.0, dt=0.02)
+    lay = sgn.Layout(ctx, [sgn.Grid(1, c.n, c.L, g=c.g), sgn.Grid(1, 256, 100.0, g=9.81)])
+    s2 = I.solitary_case()
+    for scale, want in ((1.0, 0), (1.2, 5)):
+        eta = dev(pack([c.eta, s2.eta]))
+        u = dev(pack([c.u, s2.u]))
+        h = dev(pack([c.h, s2.h]))
+        U, gh = torch.zeros_like(eta), torch.zeros_like(eta)
+        st = sgn.State(lay, eta, U, u, h, gh)
+        st.init()
+        if scale != 1.0:
+            eta[:c.n] *= scale                 # instance 0 only; A stays the initial one
+        st.linimp([c.dt, s2.dt], 6, rtol=1e-12, maxit=4000, prec=sgn.PREC_FP64)
+        stats = st.stats()
+        st.close()
+        # six steps: one RK4 start-up step, then five SBDF2 steps, each checked
+        assert stats["sbdf2_stability_warnings"] == want, (scale, stats)
