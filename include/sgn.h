@@ -173,6 +173,18 @@ sgn_status sgn_pcg(sgn_ctx* ctx, const sgn_layout* lay, const double* eta, const
                    const sgn_precond* P, const double* b, double* x, double rtol, int maxit,
                    sgn_precision prec, sgn_pcg_info* info, sgn_stream stream);
 
+/* The solve of sgn_pcg without any host synchronisation: the report goes to DEVICE
+ * memory.  The preconditioner coefficients are the optimal ones (Eq:Optcoeff, §4), computed
+ * per instance on the device, as the time steppers use them.  info: DEVICE array [count]
+ * of sgn_pcg_info, written on `stream` after the solve; read it once the stream (or an
+ * event recorded on it after this call) has completed.  Returns SGN_OK when the work was
+ * issued; each instance's outcome (SGN_ERR_NOT_CONVERGED, SGN_ERR_BREAKDOWN,
+ * SGN_ERR_NONPOSITIVE_DEPTH) is in its info.status.  A 2d solve on a stream that is being
+ * captured takes the host-driven path, which synchronises. */
+sgn_status sgn_pcg_async(sgn_ctx* ctx, const sgn_layout* lay, const double* eta,
+                         const double* gradh, const double* b, double* x, double rtol, int maxit,
+                         sgn_precision prec, sgn_pcg_info* info, sgn_stream stream);
+
 /* Restarted GMRES(restart) for G_{eta,h} x = b, right-preconditioned by the A of §4: the
  * Krylov option besides sgn_pcg.  G is symmetric positive definite, where PCG (§3.2) is the
  * paper's method and the cheaper one; GMRES is the solver for a non-symmetric variant of
@@ -396,7 +408,11 @@ double sgn_clock(void);
  *
  * Works on the current device.  The first call on a device does a one-time set-up (symbol
  * address lookups and the twiddle-table kernel) and synchronises the stream; make that
- * first call before any stream capture.  Every call shares the same static scratch, which
+ * first call before any stream capture.  Under CUDA's default lazy module loading that
+ * first call is also where the driver loads this library's kernels and places the static
+ * arrays in device memory, so a caller whose memory is frozen after start-up must make
+ * the first call during start-up, before the freeze: "no allocation" holds from the
+ * second call on.  Every call shares the same static scratch, which
  * keeps the last call's contents (the solve writes each scratch slot before reading it,
  * and clears the solve record itself): calls that overlap on the GPU (different streams,
  * or different host threads on one device) race with each other and must be serialised

@@ -42,12 +42,27 @@ struct DevicePtrs {
   float* coef_df = nullptr;
 };
 
+// Writes this call's instance descriptor (from launch arguments, so nothing is read from
+// host memory) and the constant instance index, and clears the solve record so that a
+// failed launch cannot report the previous call's result.
+__global__ void k_noalloc_prepare(sgn::Inst1d* inst, int* ids, sgn::SolveRec* rec, int n,
+                                  int log2n, double L) {
+  inst->n = n;
+  inst->log2n = log2n;
+  inst->L = L;
+  inst->off = 0;
+  inst->ws = 0;
+  ids[0] = 0;
+  *rec = sgn::SolveRec{};
+}
+
 constexpr int kMaxDevices = 64;
 DevicePtrs g_ptrs[kMaxDevices];
 std::mutex g_mu;
 
-// Once per device, with that device current: look up the symbol addresses, write the
-// constant instance index and fill the twiddle tables, then wait for that work.
+// Once per device, with that device current: look up the symbol addresses and fill the
+// twiddle tables, then wait for that work.  Under CUDA's lazy module loading the first
+// lookup is also where the driver loads this module and places its static arrays.
 sgn_status setup_device(int dev, cudaStream_t s) {
   DevicePtrs& P = g_ptrs[dev];
   if (P.ready) return SGN_OK;
@@ -61,9 +76,7 @@ sgn_status setup_device(int dev, cudaStream_t s) {
     cudaGetLastError();
     return SGN_ERR_CUDA;
   }
-  const int zero = 0;
-  if (cudaMemcpyAsync(P.ids, &zero, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      sgn::twiddles_init(P.tw64, P.tw32, s) != cudaSuccess ||
+  if (sgn::twiddles_init(P.tw64, P.tw32, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
     return SGN_ERR_CUDA;
@@ -98,19 +111,8 @@ extern "C" sgn_status sgn_pcg1d_noalloc(int n, double L, const double* eta, cons
     if (st != SGN_OK) return st;
     P = g_ptrs[dev];
   }
-  // This call's instance descriptor; the solve record starts cleared so that a failed
-  // launch cannot report the previous call's result.
-  sgn::Inst1d I;
-  I.n = n;
-  I.log2n = log2n;
-  I.L = L;
-  I.off = 0;
-  I.ws = 0;
-  if (cudaMemcpyAsync(P.inst, &I, sizeof(I), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemsetAsync(P.rec, 0, sizeof(sgn::SolveRec), s) != cudaSuccess) {
-    cudaGetLastError();
-    return SGN_ERR_CUDA;
-  }
+  k_noalloc_prepare<<<1, 1, 0, s>>>(P.inst, P.ids, P.rec, n, log2n, L);
+  if (cudaGetLastError() != cudaSuccess) return SGN_ERR_CUDA;
   sgn::Layout1d lay;
   lay.count = 1;
   lay.points = n;
