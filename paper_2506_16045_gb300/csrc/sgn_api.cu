@@ -792,6 +792,41 @@ extern "C" sgn_status sgn_pcg(sgn_ctx* ctx, const sgn_layout* lay_c, const doubl
   return SGN_OK;
 }
 
+namespace {
+
+// The solve report of every instance in the ABI's sgn_pcg_info form, on the device.
+__global__ void k_pcg_info(const SolveRec* __restrict__ rec, sgn_pcg_info* __restrict__ info,
+                           int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const SolveRec r = rec[i];
+  sgn_pcg_info o;
+  o.iters = r.iters;
+  o.refinements = r.refinements;
+  o.rel_resid_Ainv = r.ratio;
+  o.status = r.status;
+  info[i] = o;
+}
+
+}  // namespace
+
+extern "C" sgn_status sgn_pcg_async(sgn_ctx* ctx, const sgn_layout* lay_c, const double* eta,
+                                    const double* gradh, const double* b, double* x, double rtol,
+                                    int maxit, sgn_precision prec, sgn_pcg_info* info,
+                                    sgn_stream stream) {
+  sgn_layout* lay = const_cast<sgn_layout*>(lay_c);
+  if (!ctx || check_layout(lay) || !eta || !gradh || !b || !x || !info || !(rtol > 0.0) ||
+      maxit < 0 || (prec != SGN_PREC_FP64 && prec != SGN_PREC_MIXED))
+    return fail(ctx, SGN_ERR_INVALID_ARG, "pcg_async args");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  sgn_status st = run_pcg(lay, eta, gradh, nullptr, SGN_COEF_OPT, b, x, rtol, maxit, prec, 0.0, 0, s);
+  if (st) return st;
+  k_pcg_info<<<(lay->count + 127) / 128, 128, 0, s>>>(lay->rec, info, lay->count);
+  SGN_CUDA(ctx, cudaGetLastError());
+  return SGN_OK;
+}
+
 extern "C" sgn_status sgn_gmres(sgn_ctx* ctx, const sgn_layout* lay_c, const double* eta,
                                 const double* gradh, const sgn_precond* P, const double* b,
                                 double* x, double rtol, int restart, int maxit,

@@ -91,6 +91,8 @@ SIGNATURES = [
     ("sgn_precond_solve", C.c_int, [_VP, _VP, C.POINTER(SgnPrecond), _DP, _DP, _VP]),
     ("sgn_pcg", C.c_int, [_VP, _VP, _DP, _DP, C.POINTER(SgnPrecond), _DP, _DP, C.c_double,
                           C.c_int, C.c_int, C.POINTER(SgnPcgInfo), _VP]),
+    ("sgn_pcg_async", C.c_int, [_VP, _VP, _DP, _DP, _DP, _DP, C.c_double, C.c_int, C.c_int,
+                                _VP, _VP]),
     ("sgn_gmres", C.c_int, [_VP, _VP, _DP, _DP, C.POINTER(SgnPrecond), _DP, _DP, C.c_double,
                             C.c_int, C.c_int, C.POINTER(SgnPcgInfo), _VP]),
     ("sgn_rhs", C.c_int, [_VP, _VP, _DP, _DP, _DP, _DP, _DP, _DP, _VP]),
@@ -154,6 +156,13 @@ def _ptr(t):
         return None
     if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
         raise ValueError("expected a contiguous CUDA float64 tensor")
+    return t.data_ptr()
+
+
+def _vptr(t):
+    """Device address of a contiguous CUDA tensor of any dtype (raw byte buffers)."""
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
     return t.data_ptr()
 
 
@@ -326,6 +335,26 @@ def pcg(lay: Layout, eta, gradh, b, x, rtol=1e-12, maxit=1000, prec=PREC_FP64, P
         return None
     return [dict(iters=i.iters, refinements=i.refinements, ratio=i.rel_resid_Ainv,
                  status=i.status) for i in inf]
+
+
+PCG_INFO_BYTES = C.sizeof(SgnPcgInfo)
+
+
+def pcg_async(lay: Layout, eta, gradh, b, x, info_dev, rtol=1e-12, maxit=1000, prec=PREC_FP64,
+              stream=None):
+    """sgn_pcg_async: the solve with optimal coefficients and its report written to device
+    memory `info_dev` (count * PCG_INFO_BYTES bytes, e.g. a uint8 CUDA tensor); nothing
+    synchronises.  Decode the bytes with pcg_info_from_bytes once the stream has finished."""
+    lay.ctx.check(lay.ctx.lib.sgn_pcg_async(lay.ctx.h, lay.h, _ptr(eta), _ptr(gradh), _ptr(b),
+                                            _ptr(x), rtol, maxit, prec, _vptr(info_dev),
+                                            _stream(stream)), "sgn_pcg_async")
+
+
+def pcg_info_from_bytes(raw: bytes, count: int):
+    """The per-instance sgn_pcg_info records in `raw` (host bytes) as dicts."""
+    arr = (SgnPcgInfo * count).from_buffer_copy(raw[:count * PCG_INFO_BYTES])
+    return [dict(iters=i.iters, refinements=i.refinements, ratio=i.rel_resid_Ainv,
+                 status=i.status) for i in arr]
 
 
 def gmres(lay: Layout, eta, gradh, b, x, rtol=1e-10, restart=30, maxit=1000, P=None,

@@ -31,7 +31,7 @@ def test_header_declares_the_boundary():
                  "sgn_spectral_grad", "sgn_gmres", "sgn_step_rk4_nc", "sgn_state_set_dealias",
                  "sgn_state_set_forcing", "sgn_layout_set_forms", "sgn_state_autotune",
                  "sgn_server_create", "sgn_batch_submit", "sgn_batch_poll",
-                 "sgn_pcg1d_noalloc"):
+                 "sgn_pcg1d_noalloc", "sgn_pcg_async"):
         assert must in names
 
 

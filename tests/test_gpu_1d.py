@@ -374,3 +374,44 @@ def test_sbdf2_guard_counts_levels_past_the_fixed_A(S):
         st.close()
         # six steps: one RK4 start-up step, then five SBDF2 steps, each checked
         assert stats["sbdf2_stability_warnings"] == want, (scale, stats)
+
+
+def test_pcg_async_writes_device_info_after_event(S):
+    """sgn_pcg_async: the solve of sgn_pcg whose report lands in device memory; read after an
+    event recorded on the stream, it equals sgn_pcg's report and the oracle's solution."""
+    sgn, ctx = S
+    cases = [(512, 1.0, 1.0), (2048, 4.0, 1.0), (8192, 1.0, 4.0)]
+    prob = [I.testproblem_1d(n, e0, hv) for n, e0, hv in cases]
+    hxs = [O.deriv(p[1], 1.0) for p in prob]
+    lay = sgn.Layout(ctx, [sgn.Grid(1, n, 1.0) for n, _, _ in cases])
+    eta, hx, b = dev(pack([p[2] for p in prob])), dev(pack(hxs)), dev(pack([p[3] for p in prob]))
+    for prec, rtol, tol in ((sgn.PREC_FP64, 1e-12, 1e-10), (sgn.PREC_MIXED, 1e-11, 1e-9)):
+        x_ref = torch.zeros(lay.points, dtype=torch.float64, device="cuda")
+        info_ref = sgn.pcg(lay, eta, hx, b, x_ref, rtol=rtol, maxit=5000, prec=prec)
+        s = torch.cuda.Stream()
+        x = torch.zeros(lay.points, dtype=torch.float64, device="cuda")
+        info_dev = torch.full((len(cases) * sgn.PCG_INFO_BYTES,), 255, dtype=torch.uint8,
+                              device="cuda")
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            sgn.pcg_async(lay, eta, hx, b, x, info_dev, rtol=rtol, maxit=5000, prec=prec,
+                          stream=s)
+            done = torch.cuda.Event()
+            done.record(s)
+        done.synchronize()
+        info = sgn.pcg_info_from_bytes(bytes(info_dev.cpu().numpy().tobytes()), len(cases))
+        assert info == info_ref
+        xs = unpack(x.cpu().numpy(), lay.offsets)
+        assert np.array_equal(x.cpu().numpy(), x_ref.cpu().numpy())
+        for i, (n, _, _) in enumerate(cases):
+            assert info[i]["status"] == 0 and info[i]["ratio"] <= rtol
+            ref = O.solve_G(prob[i][2], hxs[i], prob[i][3], O.make_grid(1, n, 1.0, 1.0),
+                            rtol=1e-14, maxit=5000)[0]
+            assert rel(xs[i], ref) < tol
+    # a breakdown-free failure is reported through the device record, not the return value
+    x = torch.zeros(lay.points, dtype=torch.float64, device="cuda")
+    info_dev = torch.zeros((len(cases) * sgn.PCG_INFO_BYTES,), dtype=torch.uint8, device="cuda")
+    sgn.pcg_async(lay, eta, hx, b, x, info_dev, rtol=1e-14, maxit=2, prec=sgn.PREC_FP64)
+    torch.cuda.synchronize()
+    info = sgn.pcg_info_from_bytes(bytes(info_dev.cpu().numpy().tobytes()), len(cases))
+    assert all(i["status"] == 5 for i in info)
