@@ -38,6 +38,13 @@ FP32_PEAK = 152 * 128 * 2 * 2.07e9          # FMA lanes x 2 flops x max SM clock
 # 11 float32 operations and a multiply 7, so a butterfly costs about 9.6 times its float32 form
 DF_COST = 9.6
 RTOL = 1e-10
+# What the mixed path computes in which arithmetic (the line's accuracy block gives the
+# measured effect against the float64 path and the oracle)
+PRECISION_MIXED = ("mixed: float32 inner PCG (FFTs, matvecs, Krylov vectors; float32 "
+                   "per-thread dot partials reduced across the CTA in double-float); refinement "
+                   "residual b - G x and its dot r.A^-1 r in double-float (pairs of float32, "
+                   "~48-bit significand); right-hand side in double-float (2d: double-float "
+                   "transforms, float64 pointwise terms); float64 state and stage sums")
 
 
 def parse():
@@ -51,8 +58,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the shelf/2d/serving sections after the headline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--only-config", choices=["shelf_1d", "bump_2d", "serving", "robustness",
-                                              "manufactured"],
+    ap.add_argument("--only-config", choices=["solitary_1d", "shelf_1d", "bump_2d", "serving",
+                                              "robustness", "manufactured"],
                     help="run only this extra configuration and print its result as one JSON "
                          "line (for profiling one workload; not the headline)")
     ap.add_argument("--n2d", type=int, default=512, choices=[128, 256, 512, 1024],
@@ -472,7 +479,7 @@ def gpu_arm(args, world, rank, local, pg):
         "config": {"workload": "ensemble256-1d-rk4: 256 uneven 1d shelf instances, n in "
                                "{512..8192}, RK4 + mixed PCG, rtol 1e-10",
                    "instances": args.count, "points_per_gpu": E.points, "scheme": "RK4",
-                   "precision": "mixed (f32 inner PCG, f64 refinement/dots/stage sums/RHS)",
+                   "precision": PRECISION_MIXED,
                    "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas",
                    "autotuned_ctas_per_instance": E.forms},
         "e2e": {"value": total_points / (e2e_ms * 1e-3) if world == 1 else None, "unit": UNIT,
@@ -497,7 +504,8 @@ def gpu_arm(args, world, rank, local, pg):
     if rank == 0 and world == 1 and not args.no_extra:
         E.st.close()
         extra = {}
-        for name, fn in (("shelf_1d", bench_shelf), ("bump_2d", bench_2d),
+        for name, fn in (("solitary_1d", bench_solitary), ("shelf_1d", bench_shelf),
+                         ("bump_2d", bench_2d),
                          ("serving", bench_serving), ("robustness", bench_robustness),
                          ("manufactured", bench_manufactured)):
             try:
@@ -510,6 +518,54 @@ def gpu_arm(args, world, rank, local, pg):
     if rank == 0:
         print(json.dumps(line))
     E.st.close()
+
+
+def bench_solitary(sgn, ctx, torch, steps=500):
+    """Flat-bottom solitary wave (L = 100, n = 256, a = 0.2 at x = 25, g = 9.81), float64 RK4
+    with PCG at rtol 1e-12, dt = 0.01, the whole 500-step run; the same run in mixed precision
+    beside it.  Timed with CUDA events from the initial state after a short untimed run of the
+    same kind; the error against the closed-form translate at t = 5 (which carries the
+    periodic-image tail, ~1e-7 at L = 100) and the mass drift."""
+    import numpy as np
+
+    from paper_2506_16045_gb300 import inputs as I
+    c = I.solitary_case()
+    lay = sgn.Layout(ctx, [sgn.Grid(1, c.n, c.L, g=c.g)])
+    dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda")
+    x = I.grid_1d(c.n, c.L)
+    ee, ue = I.solitary_wave_1d(x, c.L, 1.0, 0.2, 25.0, c.g, t=steps * c.dt)
+    out = {}
+    for prec in (sgn.PREC_FP64, sgn.PREC_MIXED):
+        for k in (5, steps):
+            eta, u, h = dev(c.eta), dev(c.u), dev(c.h)
+            U, gh = torch.zeros_like(eta), torch.zeros_like(eta)
+            st = sgn.State(lay, eta, U, u, h, gh)
+            st.init()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            st.rk4(c.dt, k, rtol=1e-12, maxit=2000, prec=prec)
+            e1.record()
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) * 1e-3
+            stats = st.stats()
+            st.close()
+        out[prec] = (sec, eta.cpu().numpy(), u.cpu().numpy(), stats)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    t6, e6, u6, s6 = out[sgn.PREC_FP64]
+    tm, em, um, _ = out[sgn.PREC_MIXED]
+    m0 = float(np.sum(c.eta - c.h))
+    return {"workload": "solitary_1d: flat-bottom solitary wave L=100, n=256, a=0.2, g=9.81, "
+                        f"float64 RK4 + PCG rtol 1e-12, dt 0.01, {steps} steps",
+            "steps": steps, "value": c.n * steps / t6, "unit": UNIT, "dtype": "f64",
+            "seconds": round(t6, 4), "ms_per_step": 1e3 * t6 / steps,
+            "mixed_value": c.n * steps / tm,
+            "rel_linf_eta_vs_closed_form": float(np.abs(e6 - ee).max() / np.abs(ee - 1.0).max()),
+            "rel_l2_u_vs_closed_form": rel(u6, ue),
+            "rel_l2_eta_mixed_vs_fp64": rel(em, e6), "rel_l2_u_mixed_vs_fp64": rel(um, u6),
+            "mass_drift_rel": abs(float(np.sum(e6 - c.h)) - m0) / abs(m0),
+            "iterations_per_solve": s6["iterations"] / max(1, s6["solves"]),
+            "status": s6["status"]}
 
 
 def bench_2d(sgn, ctx, torch, steps=300, n=512):
@@ -943,7 +999,8 @@ def main():
 
         from paper_2506_16045_gb300 import sgn
         ctx = sgn.Context(0)
-        fn = {"shelf_1d": lambda *a: bench_shelf(*a, steps=args.shelf_steps),
+        fn = {"solitary_1d": bench_solitary,
+              "shelf_1d": lambda *a: bench_shelf(*a, steps=args.shelf_steps),
               "bump_2d": lambda *a: bench_2d(*a, n=args.n2d),
               "serving": bench_serving, "robustness": bench_robustness,
               "manufactured": bench_manufactured}
