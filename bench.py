@@ -62,6 +62,8 @@ def parse():
                                               "robustness", "manufactured"],
                     help="run only this extra configuration and print its result as one JSON "
                          "line (for profiling one workload; not the headline)")
+    ap.add_argument("--serving-requests", type=int, default=240,
+                    help="requests of the serving stream (2000: the whole workload)")
     ap.add_argument("--n2d", type=int, default=512, choices=[128, 256, 512, 1024],
                     help="grid side of the bump_2d configuration")
     ap.add_argument("--shelf-steps", type=int, default=2000,
@@ -864,7 +866,7 @@ def bench_manufactured(sgn, ctx, torch, n=256, t_final=1.0):
             "runs": runs, "observed_order": orders}
 
 
-def bench_serving(sgn, ctx, torch, nreq=120, rate=200.0, seed=16045, baseline_sample=8):
+def bench_serving(sgn, ctx, torch, nreq=240, rate=200.0, seed=16045, baseline_sample=8):
     """Poisson stream of SGN runs (RK4, 20-200 steps) and constraint solves (half 1d, half
     2d), host inputs.  A solve's right-hand side is b = G u_s for the solitary-wave velocity
     u_s (formed with sgn_apply_operator before the stream starts), so its answer is known."""
@@ -934,6 +936,14 @@ def bench_serving(sgn, ctx, torch, nreq=120, rate=200.0, seed=16045, baseline_sa
     lat = np.array([1e3 * (done[t]["t_done"] - done[t]["t_submit"]) for t, *_ in tickets])
     solve_lat = np.array([1e3 * (done[t]["t_done"] - done[t]["t_submit"])
                           for t, k, *_ in tickets if k == sgn.REQ_SOLVE])
+    by_kind = {}
+    for name, kk, dd in (("solve_1d", sgn.REQ_SOLVE, 1), ("solve_2d", sgn.REQ_SOLVE, 2),
+                         ("run_1d", sgn.REQ_RUN, 1), ("run_2d", sgn.REQ_RUN, 2)):
+        v = np.array([1e3 * (done[t]["t_done"] - done[t]["t_submit"])
+                      for t, k, p, ns, st, i in tickets if k == kk and reqs[i][1].dim == dd])
+        if v.size:
+            by_kind[name] = {"n": int(v.size), "p50_ms": float(np.percentile(v, 50)),
+                             "p99_ms": float(np.percentile(v, 99))}
     t0 = min(done[t]["t_submit"] for t, *_ in tickets)
     t1 = max(done[t]["t_done"] for t, *_ in tickets)
     work = sum(p * max(k, 1) for t, kind, p, k, *_ in tickets)    # a solve counts one step
@@ -982,6 +992,11 @@ def bench_serving(sgn, ctx, torch, nreq=120, rate=200.0, seed=16045, baseline_sa
             "p99_ms": float(np.percentile(lat, 99)),
             "solve_p50_ms": float(np.percentile(solve_lat, 50)) if solve_lat.size else None,
             "solve_p99_ms": float(np.percentile(solve_lat, 99)) if solve_lat.size else None,
+            "latency_by_kind": by_kind,
+            "sample_reason": None if nreq >= 2000 else
+            f"{nreq} of the workload's 2000 requests: the 2d runs (up to 1024^2 x 200 RK4 steps) "
+            "share one lane, and the whole stream takes minutes; --serving-requests 2000 runs "
+            "all of it",
             "throughput": work / (t1 - t0), "unit": UNIT,
             "plain_fp64_sequential": wsum / tsum,
             "plain_sample": f"{len(idx)} requests of the same stream run one at a time"}
@@ -1002,7 +1017,8 @@ def main():
         fn = {"solitary_1d": bench_solitary,
               "shelf_1d": lambda *a: bench_shelf(*a, steps=args.shelf_steps),
               "bump_2d": lambda *a: bench_2d(*a, n=args.n2d),
-              "serving": bench_serving, "robustness": bench_robustness,
+              "serving": lambda *a: bench_serving(*a, nreq=args.serving_requests),
+              "robustness": bench_robustness,
               "manufactured": bench_manufactured}
         print(json.dumps({args.only_config: fn[args.only_config](sgn, ctx, torch)}))
         ctx.close()

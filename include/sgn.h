@@ -101,8 +101,13 @@ void sgn_destroy(sgn_ctx* ctx);
 const char* sgn_last_error(const sgn_ctx* ctx);
 const char* sgn_status_string(sgn_status s);
 
-/* Packs `count` instances (host array `grids`).  count > 1 needs dim = 1 for every grid;
- * 2d layouts hold exactly one instance.  Allocates the layout's device descriptors and
+/* Packs `count` instances (host array `grids`).  1d batches may mix sizes.  A 2d layout of
+ * count > 1 (at most 32) is a batch of instances on one grid (every sgn_grid equal); it
+ * serves sgn_spectral_grad, sgn_precond_coeffs, sgn_apply_operator, sgn_precond_solve,
+ * sgn_pcg and sgn_pcg_async, whose mixed-precision solves advance the float32 inner PCG of
+ * every instance in one persistent launch per refinement pass; sgn_gmres, sgn_rhs and
+ * states take single 2d instances (SGN_ERR_INVALID_ARG).  Allocates the layout's device
+ * descriptors and
  * spectral workspace.  Every call on a layout (and on the states bound to it) uses that
  * workspace, so calls on one layout must be ordered: issue them on one stream, or order
  * the streams; independent work runs concurrently on separate layouts. */
@@ -128,6 +133,17 @@ sgn_status sgn_layout_get_form(const sgn_layout* lay, int log2n, int* ctas);
 sgn_status sgn_layout_set_forms(sgn_layout* lay, int log2n, int solve_ctas, int rhs_ctas);
 sgn_status sgn_layout_get_forms(const sgn_layout* lay, int log2n, int* solve_ctas,
                                 int* rhs_ctas);
+
+/* Kernel form of a 2d layout's float32 inner solves (the mixed-precision PCG).
+ * inner = 0: one persistent cooperative launch per inner solve, whose CTAs run the column
+ * passes, the row passes with the pointwise step and the vector updates behind grid-wide
+ * barriers (the default); inner = 1: four kernels per inner iteration inside a device-side
+ * loop.  tile_width: half-spectrum columns per column tile of the persistent form (1, 2 or
+ * 4; 0 picks the widest that still gives every CTA a tile).  Both forms run the same PCG
+ * (§3.2) and agree up to rounding.  SGN_ERR_INVALID_ARG on a 1d layout or bad arguments,
+ * SGN_ERR_UNSUPPORTED_SIZE for a tile too wide for ny. */
+sgn_status sgn_layout_set_form2d(sgn_layout* lay, int inner, int tile_width);
+sgn_status sgn_layout_get_form2d(const sgn_layout* lay, int* inner, int* tile_width);
 
 /* offsets[0..count]: start of each instance in a packed scalar array (host array). */
 sgn_status sgn_layout_offsets(const sgn_layout* lay, long long* offsets);
@@ -431,6 +447,15 @@ sgn_status sgn_pcg1d_noalloc(int n, double L, const double* eta, const double* g
 sgn_status sgn_profile_enable(sgn_ctx* ctx, int on);
 sgn_status sgn_profile_read(sgn_ctx* ctx, double* pcg_ms, long long* pcg_calls, double* rhs_ms,
                             long long* rhs_calls);
+/* Profiling of a 2d layout's persistent inner solves.  Reports what was recorded since the
+ * previous call (the summed device milliseconds of the persistent launches, their number,
+ * and the inner PCG iterations they ran), synchronising those events, then starts (on = 1)
+ * or stops (on = 0) recording.  While recording, mixed solves on the layout take the
+ * host-driven refinement loop (a stream synchronisation per pass) so that every persistent
+ * launch is bracketed by CUDA events on the solve's stream; results are unchanged.
+ * SGN_ERR_INVALID_ARG on a 1d layout. */
+sgn_status sgn_profile_inner2d(sgn_layout* lay, int on, double* ms, long long* launches,
+                               long long* iterations);
 
 #ifdef __cplusplus
 }

@@ -17,180 +17,13 @@
 #include <cstdio>
 #include <vector>
 
-#include "sgn_1d_dev.cuh"
-#include "sgn_2d.h"
+#include "sgn_2d_dev.cuh"
 
 namespace sgn {
 
-// device-resident scalars of one 2d solve
-struct Scal2d {
-  double bb;           // b.A^{-1}b (high precision problem)
-  double rz;           // inner r.z
-  double rz64;         // refinement residual r.A^{-1}r
-  double alpha, beta;
-  double tol;          // inner absolute tolerance on sqrt(r.z)
-  int done;            // inner loop finished
-  int iters;           // inner iterations (this solve)
-  int cap;             // iteration cap
-  int status;
-  unsigned int ticket; // last-block counter
-  double sigma, alpha_A, kappa_ub, eta_min, eta_max;
-  int flat;
-  // float32 copies for the inner solve's kernels, written where the doubles are: on this
-  // part a float64 instruction costs 62 float32 ones, so per-mode work stays in float32
-  float sigf, alphaAf, isigf;   // sigma, alpha of A and 1 / sigma
-  float alphaf, betaf;          // CG alpha, beta
-  // device-driven solve (the cached solve graph): options, and the refinement loop's state
-  double rtol, rtol_in;         // outer tolerance; inner tolerance (<= 0: adaptive)
-  double rn;                    // ||r||_{A^{-1}} of the last refinement residual
-  int maxit, max_refine, kind;
-  int refinements, it_before;
-};
+using namespace d2;
 
 namespace {
-
-using d1::kPi;
-using d1::kLambdaPlus;
-using d1::kLambdaMinus;
-using d1::kFlatSlope;
-
-constexpr int kRowNT = 256;
-constexpr int kColNT = 512;
-constexpr int kMaxParts = 2048;
-
-// ---- mode helpers --------------------------------------------------------------------
-struct Modes2d {
-  int nx, ny, H;
-  double kxu, kyu;     // 2 pi / Lx, 2 pi / Ly
-  __device__ __forceinline__ double kx(int c) const { return c == (nx >> 1) ? 0.0 : kxu * c; }
-  __device__ __forceinline__ double ky(int y) const { return kyu * wave_index(y, ny); }
-  __device__ __forceinline__ double weight(int c) const {
-    return (c == 0 || c == (nx >> 1)) ? 1.0 : 2.0;
-  }
-};
-
-__host__ Modes2d modes_of(const Layout2d& L) {
-  Modes2d M;
-  M.nx = L.nx;
-  M.ny = L.ny;
-  M.H = L.nx / 2 + 1;
-  M.kxu = 2.0 * kPi / L.Lx;
-  M.kyu = 2.0 * kPi / L.Ly;
-  return M;
-}
-
-template <typename T>
-__device__ __forceinline__ cplx<T> mul_ik(cplx<T> a, T k) {   // i k a
-  return mk(-(a.y * k), a.x * k);
-}
-
-template <typename T>
-__device__ __forceinline__ cplx<T> ld_c(const void* base, long long i) {
-  return reinterpret_cast<const cplx<T>*>(base)[i];
-}
-template <typename T>
-__device__ __forceinline__ void st_c(void* base, long long i, cplx<T> v) {
-  reinterpret_cast<cplx<T>*>(base)[i] = v;
-}
-
-// the twiddle table of each precision
-template <typename T>
-struct Tw;
-template <>
-struct Tw<double> {
-  static __device__ __forceinline__ const cplx<double>* get(const void* t64, const void* t32) {
-    return static_cast<const cplx<double>*>(t64);
-  }
-};
-template <>
-struct Tw<float> {
-  static __device__ __forceinline__ const cplx<float>* get(const void* t64, const void* t32) {
-    return static_cast<const cplx<float>*>(t32);
-  }
-};
-template <>
-struct Tw<df> {
-  static __device__ __forceinline__ const cplx<df>* get(const void* t64, const void* t32) {
-    return reinterpret_cast<const cplx<df>*>(static_cast<const char*>(t32) + kTw32Bytes);
-  }
-};
-
-// ---- per-mode arithmetic in the working precision ---------------------------------------
-// float32 for the float32 kernels of the inner solve, float64 otherwise.
-template <typename T>
-struct WorkP {
-  using type = double;
-};
-template <>
-struct WorkP<float> {
-  using type = float;
-};
-
-template <typename TP>
-struct ModesT {
-  TP kxu, kyu;
-  int nx, ny;
-  __device__ __forceinline__ explicit ModesT(const Modes2d& M)
-      : kxu((TP)M.kxu), kyu((TP)M.kyu), nx(M.nx), ny(M.ny) {}
-  __device__ __forceinline__ TP kx(int c) const { return c == (nx >> 1) ? TP(0) : kxu * (TP)c; }
-  __device__ __forceinline__ TP ky(int y) const { return kyu * (TP)wave_index(y, ny); }
-  __device__ __forceinline__ TP weight(int c) const {
-    return (c == 0 || c == (nx >> 1)) ? TP(1) : TP(2);
-  }
-};
-
-// z = A^{-1} r per mode (Sherman-Morrison of sigma I + alpha k k^T)
-template <typename TP>
-struct AinvT {
-  TP sigma, alpha, isig;
-  __device__ __forceinline__ void apply(TP kx, TP ky, cplx<TP> r1, cplx<TP> r2, cplx<TP>& z1,
-                                        cplx<TP>& z2) const {
-    const TP f = alpha * recip(sigma + alpha * (kx * kx + ky * ky));
-    const cplx<TP> kr = r1 * kx + r2 * ky;
-    z1 = (r1 - kr * (f * kx)) * isig;
-    z2 = (r2 - kr * (f * ky)) * isig;
-  }
-};
-__device__ __forceinline__ AinvT<float> ainv_of(const Scal2d* sc, float) {
-  return AinvT<float>{sc->sigf, sc->alphaAf, sc->isigf};
-}
-__device__ __forceinline__ AinvT<double> ainv_of(const Scal2d* sc, double) {
-  return AinvT<double>{sc->sigma, sc->alpha_A, 1.0 / sc->sigma};
-}
-__device__ __forceinline__ float cg_alpha(const Scal2d* sc, float) { return sc->alphaf; }
-__device__ __forceinline__ double cg_alpha(const Scal2d* sc, double) { return sc->alpha; }
-__device__ __forceinline__ float cg_beta(const Scal2d* sc, float) { return sc->betaf; }
-__device__ __forceinline__ double cg_beta(const Scal2d* sc, double) { return sc->beta; }
-
-// 2^-e in T (exact), for the 1 / (nx ny) of the inverse transforms
-template <typename T>
-__device__ __forceinline__ T pow2_inv(int e) {
-  const float f = __int_as_float((127 - e) << 23);
-  if constexpr (std::is_same<T, df>::value) return df(f, 0.0f);
-  else return (T)f;
-}
-
-// wavenumber of column c (x) or row y in the number type T of a kernel's data
-template <typename T, typename TP>
-__device__ __forceinline__ T mode_k(const ModesT<TP>& MT, int i, bool xdir) {
-  const TP k = xdir ? MT.kx(i) : MT.ky(i);
-  if constexpr (std::is_same<T, df>::value) return df((double)k);
-  else return (T)k;
-}
-
-// high-precision value -> working precision, and back, without float64 where T is float
-template <typename T>
-__device__ __forceinline__ T to_work(double v) { return (T)v; }
-template <typename T>
-__device__ __forceinline__ T to_work(df v) { return (T)to_f64(v); }
-template <>
-__device__ __forceinline__ float to_work<float>(df v) { return v.hi + v.lo; }
-template <typename TH>
-__device__ __forceinline__ TH widen(float v) { return (TH)v; }
-template <>
-__device__ __forceinline__ df widen<df>(float v) { return df(v, 0.0f); }
-template <typename TH>
-__device__ __forceinline__ TH widen(double v) { return num<TH>(v); }
 
 // ---- last-block reduction ------------------------------------------------------------
 // Each block writes its partial sum; the last block to arrive sums them in a fixed order
@@ -403,39 +236,6 @@ __global__ void __launch_bounds__(kColNT, 1) k2_cols(Modes2d M, int log2ny, cons
 // =======================================================================================
 // Row passes.  Two rows per block (y0 = 2b, y1 = 2b + 1).
 // =======================================================================================
-
-// C2R of one packed pair: buf <- A + i B over the full row from two half rows, iFFT.
-template <typename T>
-__device__ __forceinline__ void load_c2r_pair(cplx<T>* z, const cplx<T>* A, const cplx<T>* B,
-                                              int nx, int NT) {
-  const int h = nx >> 1;
-  for (int m = threadIdx.x; m < nx; m += NT) {
-    cplx<T> a, b;
-    if (m <= h) {
-      a = A[m];
-      b = B[m];
-    } else {
-      a = conj(A[nx - m]);
-      b = conj(B[nx - m]);
-    }
-    // a + i b
-    z[m] = mk(a.x - b.y, a.y + b.x);
-  }
-}
-
-// R2C split of a packed FFT row Y = FFT(a + i b): A[m] = (Y_m + conj Y_{n-m})/2,
-// B[m] = (Y_m - conj Y_{n-m})/(2i), m = 0..nx/2.
-template <typename T>
-__device__ __forceinline__ void split_r2c_pair(const cplx<T>* Y, cplx<T>* A, cplx<T>* B, int nx,
-                                               int NT) {
-  const int h = nx >> 1;
-  for (int m = threadIdx.x; m <= h; m += NT) {
-    cplx<T> y = Y[m], yc = conj(Y[(nx - m) & (nx - 1)]);
-    cplx<T> s = y + yc, d = mul_mi(y - yc);
-    A[m] = mk(half(s.x), half(s.y));
-    B[m] = mk(half(d.x), half(d.y));
-  }
-}
 
 // coefficient planes: c11 = eta(1+hx^2), c12 = eta hx hy, c22 = eta(1+hy^2),
 // c13 = eta^2 hx/2, c23 = eta^2 hy/2, c33 = eta^3/3 (Def:MatrixM); hi in float, the
@@ -746,11 +546,16 @@ __global__ void __launch_bounds__(256) k2_bnorm(Modes2d M, const void* b1, const
 }
 
 // coefficient planes (Def:MatrixM) from eta, grad h
+// (and float32 eta, h_x, h_y for the persistent inner solve, which forms its coefficients
+// from them)
 __global__ void k2_coef_planes(long long P, const double* eta, const double* gh, float* hi,
-                               float* lo) {
+                               float* lo, float* ehh) {
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < P;
        j += (long long)gridDim.x * blockDim.x) {
     const double e = eta[j], hx = gh[j], hy = gh[P + j];
+    ehh[j] = (float)e;
+    ehh[P + j] = (float)hx;
+    ehh[2 * P + j] = (float)hy;
     const double c[6] = {e * (1.0 + hx * hx), e * hx * hy, e * (1.0 + hy * hy), 0.5 * e * e * hx,
                          0.5 * e * e * hy, e * e * e / 3.0};
 #pragma unroll
@@ -1190,6 +995,29 @@ cudaError_t matvec(const Layout2d& L, const void* t64, const void* t32, const vo
 // Layout
 // =======================================================================================
 
+namespace {
+
+// The persistent inner solve's view of one instance: correction d^ (slots 8-9), r^ (4-5),
+// p^ (6-7) and the first three transform planes, as float32 half planes.
+PInst2d pinst_of(const Layout2d& L) {
+  PInst2d pi;
+  auto fp = [&](int q) { return reinterpret_cast<cplx<float>*>(slot(L, q)); };
+  pi.x[0] = fp(8);
+  pi.x[1] = fp(9);
+  pi.r[0] = fp(4);
+  pi.r[1] = fp(5);
+  pi.p[0] = fp(6);
+  pi.p[1] = fp(7);
+  for (int q = 0; q < 3; ++q) pi.t[q] = reinterpret_cast<cplx<float>*>(tplane(L, q));
+  pi.ehh = L.ehh;
+  pi.sc = L.sc;
+  pi.kxu = 2.0 * kPi / L.Lx;
+  pi.kyu = 2.0 * kPi / L.Ly;
+  return pi;
+}
+
+}  // namespace
+
 cudaError_t layout2d_create(Layout2d& L, const sgn_grid& g) {
   L.nx = g.nx;
   L.ny = g.ny;
@@ -1213,10 +1041,49 @@ cudaError_t layout2d_create(Layout2d& L, const sgn_grid& g) {
   if ((e = cudaMalloc(&L.stage, sizeof(double) * 7 * L.P))) return e;
   if ((e = cudaMalloc(&L.stage_rec, sizeof(SolveRec) * 2))) return e;
   if ((e = cudaMemset(L.sc, 0, sizeof(Scal2d)))) return e;
+  // persistent inner solve
+  if ((e = persist2d_grid(L.nx, L.ny, 1, &L.p_grid))) return e;
+  L.p_tw = persist2d_tile_width(L.nx, L.ny, 1, L.p_grid);
+  const int cu = L.H, ru = L.ny / 2;   // partial-sum slots for the narrowest tiles
+  if ((e = cudaMalloc(&L.ehh, sizeof(float) * 3 * L.P))) return e;
+  if ((e = cudaMalloc(&L.pinst, sizeof(PInst2d)))) return e;
+  if ((e = cudaMalloc(&L.pparts, sizeof(double) * (cu + ru)))) return e;
+  if ((e = cudaMalloc(&L.pbar, 2 * sizeof(unsigned)))) return e;
+  const PInst2d pi = pinst_of(L);
+  if ((e = cudaMemcpy(L.pinst, &pi, sizeof(pi), cudaMemcpyHostToDevice))) return e;
   return cudaSuccess;
 }
 
+namespace {
+
+PersistArgs2d persist_args(const Layout2d& L, const void* tw32) {
+  PersistArgs2d a;
+  a.inst = static_cast<const PInst2d*>(L.pinst);
+  a.B = 1;
+  a.nx = L.nx;
+  a.ny = L.ny;
+  a.H = L.H;
+  a.lognx = L.lx;
+  a.logny = L.ly;
+  a.tw = L.p_tw;
+  a.col_units = (L.H + L.p_tw - 1) / L.p_tw;
+  a.row_units = L.ny / 2;
+  a.parts = L.pparts;
+  a.bar = L.pbar;
+  a.err = reinterpret_cast<int*>(L.pbar + 1);
+  a.tw32 = tw32;
+  return a;
+}
+
+}  // namespace
+
 void layout2d_destroy(Layout2d& L) {
+  if (L.prof) {
+    for (auto v : L.prof->a) cudaEventDestroy(v);
+    for (auto v : L.prof->b) cudaEventDestroy(v);
+    delete L.prof;
+    L.prof = nullptr;
+  }
   for (auto& row : L.solve_exec)
     for (auto& ex : row) {
       if (ex) cudaGraphExecDestroy(ex);
@@ -1233,11 +1100,31 @@ void layout2d_destroy(Layout2d& L) {
   cudaFree(L.parts);
   cudaFree(L.sc);
   cudaFree(L.rhs_w);
+  cudaFree(L.ehh);
+  cudaFree(L.pinst);
+  cudaFree(L.pparts);
+  cudaFree(L.pbar);
+  L.ehh = nullptr;
+  L.pinst = nullptr;
+  L.pparts = nullptr;
+  L.pbar = nullptr;
   L.vec = L.tp = nullptr;
   L.coef = L.coef_lo = nullptr;
   L.parts = nullptr;
   L.sc = nullptr;
   L.rhs_w = nullptr;
+}
+
+cudaError_t layout2d_set_inner_form(Layout2d& L, int form, int tile_width) {
+  if (form == L.inner_form && tile_width == L.p_tw) return cudaSuccess;
+  for (auto& row : L.solve_exec)
+    for (auto& ex : row) {
+      if (ex) cudaGraphExecDestroy(ex);
+      ex = nullptr;
+    }
+  L.inner_form = form;
+  L.p_tw = tile_width;
+  return cudaSuccess;
 }
 
 size_t layout2d_res_bytes(const Layout2d& L) { return (size_t)16 * 2 * (L.HP > 0 ? L.HP : 1); }
@@ -1411,7 +1298,7 @@ cudaError_t launch_coeffs2d(const Layout2d& L, const double* eta, const double* 
 
 cudaError_t launch_apply_G2d(const Layout2d& L, const void* tw64, const double* eta,
                              const double* gradh, const double* u, double* Gu, cudaStream_t s) {
-  k2_coef_planes<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, eta, gradh, L.coef, L.coef_lo);
+  k2_coef_planes<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, eta, gradh, L.coef, L.coef_lo, L.ehh);
   cudaError_t e = cudaGetLastError();
   if (e) return e;
   if ((e = r2c_vec<double>(L, tw64, nullptr, u, slot(L, 0), slot(L, 1), s))) return e;
@@ -1623,7 +1510,7 @@ cudaError_t build_solve_graph(const Layout2d& L, const void* tw64, const void* t
     } else {
       k2_coeffs<<<grid_for(P, 256), 256, 0, cs[0]>>>(P, eta, gh, -1, L.parts, L.sc, nullptr);
     }
-    k2_coef_planes<<<grid_for(P, 256), 256, 0, cs[0]>>>(P, eta, gh, L.coef, L.coef_lo);
+    k2_coef_planes<<<grid_for(P, 256), 256, 0, cs[0]>>>(P, eta, gh, L.coef, L.coef_lo, L.ehh);
     e = cudaGetLastError();
   }
   if (mixed) {
@@ -1649,18 +1536,25 @@ cudaError_t build_solve_graph(const Layout2d& L, const void* tw64, const void* t
     }
     if (!e) e = add_while(cs[0], hout, &body);
     // refinement pass: inner solve of G d = r / ||r||, x^ += ||r|| d, next residual, decide
+    // the inner solve: one persistent launch, or a while node over the four-kernel iteration
+    const bool persist = L.inner_form == 0;
     if (!e) e = begin(1, body);
-    if (!e) e = cudaGraphConditionalHandleCreate(&hin, body, 0, 0);
+    if (!e && !persist) e = cudaGraphConditionalHandleCreate(&hin, body, 0, 0);
     if (!e) {
       k2_inner_start<df, float><<<blocks, 256, 0, cs[1]>>>(
           M, slot(L, 10), slot(L, 11), 1.0, slot(L, 4), slot(L, 5), slot(L, 8), slot(L, 9),
-          slot(L, 6), slot(L, 7), L.sc, L.parts, 1, hin, 1);
+          slot(L, 6), slot(L, 7), L.sc, L.parts, 1, persist ? cudaGraphConditionalHandle{} : hin,
+          persist ? 0 : 1);
       e = cudaGetLastError();
     }
-    if (!e) e = add_while(cs[1], hin, &ibody);
-    if (!e) e = begin(2, ibody);
-    if (!e) e = inner_loop(float(0), cs[2], hin);
-    if (!e) e = end(2);
+    if (persist) {
+      if (!e) e = launch_pcg2d_persist(persist_args(L, tw32), L.p_grid, cs[1]);
+    } else {
+      if (!e) e = add_while(cs[1], hin, &ibody);
+      if (!e) e = begin(2, ibody);
+      if (!e) e = inner_loop(float(0), cs[2], hin);
+      if (!e) e = end(2);
+    }
     if (!e) {
       k2_after_inner<<<1, 1, 0, cs[1]>>>(L.sc);
       k2_accumulate<df, float><<<blocks, 256, 0, cs[1]>>>(M, slot(L, 2), slot(L, 3), slot(L, 8),
@@ -1738,7 +1632,7 @@ cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, 
   cudaError_t e;
   // ---- device-driven: one graph launch between staging copies
   cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
-  if (!L.solve_graph_off && cudaStreamIsCapturing(s, &cst) == cudaSuccess &&
+  if (!L.solve_graph_off && !L.prof && cudaStreamIsCapturing(s, &cst) == cudaSuccess &&
       cst == cudaStreamCaptureStatusNone) {
     const int mi = precision == SGN_PREC_MIXED ? 1 : 0, gi = given ? 1 : 0;
     cudaGraphExec_t& ex = L.solve_exec[mi][gi];
@@ -1774,7 +1668,7 @@ cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, 
   } else {
     k2_coeffs<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, eta, gradh, kind, L.parts, L.sc, nullptr);
   }
-  k2_coef_planes<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, eta, gradh, L.coef, L.coef_lo);
+  k2_coef_planes<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, eta, gradh, L.coef, L.coef_lo, L.ehh);
   if ((e = cudaGetLastError())) return e;
   Scal2d h{};
   if ((e = cudaMemcpyAsync(&h, L.sc, sizeof(Scal2d), cudaMemcpyDeviceToHost, s))) return e;
@@ -1856,7 +1750,16 @@ cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, 
         slot(L, 6), slot(L, 7), L.sc, L.parts, 0, cudaGraphConditionalHandle{}, 0);
     if ((e = cudaGetLastError())) return e;
     const int it_before = h.iters;
-    if ((e = inner_pcg<float>(L, tw64, tw32, maxit, s))) return e;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (L.prof && L.inner_form == 0) {
+      for (auto& v : ev)
+        if ((e = cudaEventCreate(&v))) return e;
+      cudaEventRecord(ev[0], s);
+    }
+    if ((e = L.inner_form == 0 ? launch_pcg2d_persist(persist_args(L, tw32), L.p_grid, s)
+                               : inner_pcg<float>(L, tw64, tw32, maxit, s)))
+      return e;
+    if (ev[1]) cudaEventRecord(ev[1], s);
     {
       // a float32 breakdown after some progress keeps the correction (see the 1d solve)
       Scal2d hs{};
@@ -1864,6 +1767,11 @@ cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, 
       if ((e = cudaStreamSynchronize(s))) return e;
       if (hs.status == SGN_ERR_BREAKDOWN && hs.iters > it_before)
         k2_set_status<<<1, 1, 0, s>>>(L.sc, SGN_OK);
+      if (ev[1]) {
+        L.prof->a.push_back(ev[0]);
+        L.prof->b.push_back(ev[1]);
+        L.prof->iters.push_back(hs.iters - it_before);
+      }
     }
     k2_accumulate<df, float><<<grid_for(L.HP, 256), 256, 0, s>>>(M, slot(L, 2), slot(L, 3),
                                                                   slot(L, 8), slot(L, 9), rn,
@@ -1872,6 +1780,230 @@ cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, 
     ++refinements;
   }
   k2_report<<<1, 1, 0, s>>>(L.sc, rec, refinements);
+  return cudaGetLastError();
+}
+
+// =======================================================================================
+// Batches of 2d instances on one grid
+// =======================================================================================
+
+cudaError_t batch2d_create(Batch2d& Bt, Layout2d& first, const sgn_grid& g, int B) {
+  Bt.B = B;
+  Bt.more.resize(B - 1);
+  cudaError_t e;
+  for (auto& L : Bt.more)
+    if ((e = layout2d_create(L, g))) return e;
+  const long long P = first.P;
+  if ((e = cudaMalloc(&Bt.stage, sizeof(double) * 7 * P * B))) return e;
+  if ((e = persist2d_grid(first.nx, first.ny, B, &Bt.p_grid))) return e;
+  Bt.p_tw = persist2d_tile_width(first.nx, first.ny, B, Bt.p_grid);
+  if ((e = cudaMalloc(&Bt.pinst, sizeof(PInst2d) * B))) return e;
+  if ((e = cudaMalloc(&Bt.pparts, sizeof(double) * B * (first.H + first.ny / 2)))) return e;
+  if ((e = cudaMalloc(&Bt.pbar, 2 * sizeof(unsigned)))) return e;
+  std::vector<PInst2d> pi(B);
+  for (int b = 0; b < B; ++b) pi[b] = pinst_of(Bt.inst(first, b));
+  return cudaMemcpy(Bt.pinst, pi.data(), sizeof(PInst2d) * B, cudaMemcpyHostToDevice);
+}
+
+void batch2d_destroy(Batch2d& Bt) {
+  for (auto& L : Bt.more) layout2d_destroy(L);
+  Bt.more.clear();
+  cudaFree(Bt.stage);
+  cudaFree(Bt.pinst);
+  cudaFree(Bt.pparts);
+  cudaFree(Bt.pbar);
+  Bt.stage = nullptr;
+  Bt.pinst = nullptr;
+  Bt.pparts = nullptr;
+  Bt.pbar = nullptr;
+  Bt.B = 0;
+}
+
+cudaError_t batch2d_stage_in(const Layout2d& L, double* st, int b, long long Ptot,
+                             const double* scal, const double* vec0, const double* vec1,
+                             const double* vec2, cudaStream_t s) {
+  const long long P = L.P;
+  const size_t n = sizeof(double) * P;
+  cudaError_t e;
+  if (scal && (e = cudaMemcpyAsync(st, scal + b * P, n, cudaMemcpyDeviceToDevice, s))) return e;
+  const double* v[3] = {vec0, vec1, vec2};
+  for (int q = 0; q < 3; ++q) {
+    if (!v[q]) continue;
+    double* d = st + (1 + 2 * q) * P;
+    if ((e = cudaMemcpyAsync(d, v[q] + b * P, n, cudaMemcpyDeviceToDevice, s)) ||
+        (e = cudaMemcpyAsync(d + P, v[q] + Ptot + b * P, n, cudaMemcpyDeviceToDevice, s)))
+      return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t batch2d_stage_out(const Layout2d& L, const double* stvec, int b, long long Ptot,
+                              double* vec, cudaStream_t s) {
+  const long long P = L.P;
+  const size_t n = sizeof(double) * P;
+  cudaError_t e = cudaMemcpyAsync(vec + b * P, stvec, n, cudaMemcpyDeviceToDevice, s);
+  if (e) return e;
+  return cudaMemcpyAsync(vec + Ptot + b * P, stvec + P, n, cudaMemcpyDeviceToDevice, s);
+}
+
+namespace {
+__global__ void k2_mark_done(Scal2d* sc) { sc->done = 1; }
+}  // namespace
+
+cudaError_t launch_pcg2d_batch(Layout2d& first, Batch2d& Bt, const void* tw64, const void* tw32,
+                               int precision, const double* eta, const double* gradh,
+                               const double* b, double* x, const SolveRec* given, int kind,
+                               double rtol, double rtol_inner, int maxit, int max_refine,
+                               SolveRec* rec, cudaStream_t s) {
+  const int B = Bt.B;
+  const long long P = first.P, Ptot = P * B;
+  cudaError_t e;
+  auto st_of = [&](int i) { return Bt.stage + 7 * P * i; };
+  for (int i = 0; i < B; ++i)
+    if ((e = batch2d_stage_in(first, st_of(i), i, Ptot, eta, gradh, b, x, s))) return e;
+  if (precision != SGN_PREC_MIXED) {
+    // float64: each instance through the single-instance solve
+    for (int i = 0; i < B; ++i) {
+      double* st = st_of(i);
+      if ((e = launch_pcg2d(Bt.inst(first, i), tw64, tw32, precision, st, st + P, st + 3 * P,
+                            st + 5 * P, given ? given + i : nullptr, kind, rtol, rtol_inner,
+                            maxit, max_refine, rec + i, s)) ||
+          (e = batch2d_stage_out(first, st + 5 * P, i, Ptot, x, s)))
+        return e;
+    }
+    return cudaSuccess;
+  }
+  // mixed: double-float refinement of every instance around one persistent launch per pass
+  std::vector<Scal2d> h(B);
+  auto fetch = [&]() {
+    for (int i = 0; i < B; ++i) {
+      cudaError_t r = cudaMemcpyAsync(&h[i], Bt.inst(first, i).sc, sizeof(Scal2d),
+                                      cudaMemcpyDeviceToHost, s);
+      if (r) return r;
+    }
+    return cudaStreamSynchronize(s);
+  };
+  for (int i = 0; i < B; ++i) {
+    Layout2d& L = Bt.inst(first, i);
+    const Modes2d M = modes_of(L);
+    const double* st = st_of(i);
+    k2_reset<<<1, 1, 0, s>>>(L.sc);
+    if (given) {
+      k2_set_given<<<1, 1, 0, s>>>(L.sc, given + i);
+    } else {
+      k2_coeffs<<<grid_for(P, 256), 256, 0, s>>>(P, st, st + P, kind, L.parts, L.sc, nullptr);
+    }
+    k2_coef_planes<<<grid_for(P, 256), 256, 0, s>>>(P, st, st + P, L.coef, L.coef_lo, L.ehh);
+    if ((e = cudaGetLastError()) ||
+        (e = r2c_vec<df>(L, tw64, tw32, st + 3 * P, slot(L, 0), slot(L, 1), s)) ||
+        (e = r2c_vec<df>(L, tw64, tw32, st + 5 * P, slot(L, 2), slot(L, 3), s)))
+      return e;
+    k2_bnorm<df><<<grid_for(L.HP, 256), 256, 0, s>>>(M, slot(L, 0), slot(L, 1), L.sc, L.parts);
+    if ((e = cudaGetLastError())) return e;
+  }
+  if ((e = fetch())) return e;
+  // per instance: 0 refining, 1 finished
+  std::vector<int> fin(B, 0), refinements(B, 0), it_before(B, 0), pass(B, 0);
+  std::vector<double> bnorm(B, 0.0), rn(B, 0.0);
+  for (int i = 0; i < B; ++i) {
+    bnorm[i] = sqrt(fmax(h[i].bb, 0.0));
+    if (h[i].status != SGN_OK) {
+      fin[i] = 1;
+    } else if (!(bnorm[i] > 0.0)) {
+      if ((e = cudaMemsetAsync(st_of(i) + 5 * P, 0, sizeof(double) * 2 * P, s))) return e;
+      fin[i] = 1;
+    }
+  }
+  const PersistArgs2d pa = [&] {
+    PersistArgs2d a;
+    a.inst = static_cast<const PInst2d*>(Bt.pinst);
+    a.B = B;
+    a.nx = first.nx;
+    a.ny = first.ny;
+    a.H = first.H;
+    a.lognx = first.lx;
+    a.logny = first.ly;
+    a.tw = Bt.p_tw;
+    a.col_units = (first.H + Bt.p_tw - 1) / Bt.p_tw;
+    a.row_units = first.ny / 2;
+    a.parts = Bt.pparts;
+    a.bar = Bt.pbar;
+    a.err = reinterpret_cast<int*>(Bt.pbar + 1);
+    a.tw32 = tw32;
+    return a;
+  }();
+  for (;;) {
+    for (int i = 0; i < B; ++i) {
+      if (fin[i]) continue;
+      Layout2d& L = Bt.inst(first, i);
+      if ((e = matvec<df>(L, tw64, tw32, slot(L, 2), slot(L, 3), slot(L, 10), slot(L, 11),
+                          nullptr, nullptr, slot(L, 0), slot(L, 1), 1, st_of(i) + 5 * P, L.sc,
+                          0, 0, nullptr, nullptr, nullptr, nullptr, s)))
+        return e;
+    }
+    if ((e = fetch())) return e;
+    bool any = false;
+    for (int i = 0; i < B; ++i) {
+      Layout2d& L = Bt.inst(first, i);
+      pass[i] = 0;
+      if (!fin[i]) {
+        const double ratio = sqrt(fmax(h[i].rz64, 0.0)) / bnorm[i];
+        if (ratio <= rtol || h[i].status != SGN_OK) {
+          fin[i] = 1;
+        } else if (refinements[i] >= max_refine || h[i].iters >= maxit) {
+          k2_set_status<<<1, 1, 0, s>>>(L.sc, SGN_ERR_NOT_CONVERGED);
+          fin[i] = 1;
+        } else {
+          const Modes2d M = modes_of(L);
+          rn[i] = sqrt(h[i].rz64);
+          const double tin =
+              rtol_inner > 0.0 ? rtol_inner : fmin(0.1, fmax(1e-6, 0.3 * rtol / ratio));
+          k2_set_inner<float><<<1, 1, 0, s>>>(L.sc, tin, maxit);
+          k2_inner_start<df, float><<<grid_for(L.HP, 256), 256, 0, s>>>(
+              M, slot(L, 10), slot(L, 11), 1.0 / rn[i], slot(L, 4), slot(L, 5), slot(L, 8),
+              slot(L, 9), slot(L, 6), slot(L, 7), L.sc, L.parts, 0, cudaGraphConditionalHandle{},
+              0);
+          it_before[i] = h[i].iters;
+          pass[i] = 1;
+          any = true;
+        }
+      }
+      if (!pass[i]) k2_mark_done<<<1, 1, 0, s>>>(L.sc);
+    }
+    if ((e = cudaGetLastError())) return e;
+    if (!any) break;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (first.prof) {
+      for (auto& v : ev)
+        if ((e = cudaEventCreate(&v))) return e;
+      cudaEventRecord(ev[0], s);
+    }
+    if ((e = launch_pcg2d_persist(pa, Bt.p_grid, s))) return e;
+    if (ev[1]) cudaEventRecord(ev[1], s);
+    if ((e = fetch())) return e;
+    long long its = 0;
+    for (int i = 0; i < B; ++i) {
+      if (!pass[i]) continue;
+      Layout2d& L = Bt.inst(first, i);
+      its += h[i].iters - it_before[i];
+      // a float32 breakdown after some progress keeps the correction (see the 1d solve)
+      if (h[i].status == SGN_ERR_BREAKDOWN && h[i].iters > it_before[i])
+        k2_set_status<<<1, 1, 0, s>>>(L.sc, SGN_OK);
+      k2_accumulate<df, float><<<grid_for(L.HP, 256), 256, 0, s>>>(
+          modes_of(L), slot(L, 2), slot(L, 3), slot(L, 8), slot(L, 9), rn[i], nullptr);
+      ++refinements[i];
+    }
+    if ((e = cudaGetLastError())) return e;
+    if (ev[1]) {
+      first.prof->a.push_back(ev[0]);
+      first.prof->b.push_back(ev[1]);
+      first.prof->iters.push_back(its);
+    }
+  }
+  for (int i = 0; i < B; ++i) {
+    k2_report<<<1, 1, 0, s>>>(Bt.inst(first, i).sc, rec + i, refinements[i]);
+    if ((e = batch2d_stage_out(first, st_of(i) + 5 * P, i, Ptot, x, s))) return e;
+  }
   return cudaGetLastError();
 }
 
@@ -1966,7 +2098,7 @@ cudaError_t launch_linimp_res2d(const Layout2d& L, const void* tw64, const Solve
                                 const double* eta, const double* gradh, const double* u,
                                 const double* U, void* res_hat, cudaStream_t s) {
   // res^ = A u^ - (G u)^ + U^, float64, stored as two half planes in res_hat
-  k2_coef_planes<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, eta, gradh, L.coef, L.coef_lo);
+  k2_coef_planes<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, eta, gradh, L.coef, L.coef_lo, L.ehh);
   cudaError_t e = cudaGetLastError();
   if (e) return e;
   if ((e = r2c_vec<double>(L, tw64, nullptr, u, slot(L, 0), slot(L, 1), s))) return e;

@@ -2,11 +2,22 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "sgn_internal.h"
 
 namespace sgn {
 
 struct Scal2d;   // device-resident scalars of one 2d solve (sgn_2d.cu)
+
+constexpr int kMaxBatch2dAbi = 32;   // instances of one 2d layout (a persistent launch's limit)
+
+// Events around the persistent inner-solve launches of a layout while profiling is on, and
+// the inner iterations each launch ran.
+struct Prof2d {
+  std::vector<cudaEvent_t> a, b;
+  std::vector<long long> iters;
+};
 
 // One 2d instance: fields [ny][nx] row-major; vector fields are two planes of P = nx ny.
 // Spectra are half spectra [ny][H], H = nx/2 + 1; every half-plane buffer has 16 bytes
@@ -32,11 +43,64 @@ struct Layout2d {
   mutable bool solve_graph_off = false;   // building one failed: host-driven solves
   double* stage = nullptr;
   SolveRec* stage_rec = nullptr;
+  // Persistent float32 inner solve (sgn_2d_pcg.cu): float32 eta, h_x, h_y (3 planes of P),
+  // its instance descriptor (device), per-unit partial sums, the barrier words, the column
+  // tile width and the cooperative grid.  inner_form 1 runs the inner iteration as four
+  // kernels per iteration instead (k2_cols, k2_rows_matvec, k2_cols, k2_update).
+  float* ehh = nullptr;
+  void* pinst = nullptr;
+  double* pparts = nullptr;
+  unsigned* pbar = nullptr;
+  int p_tw = 0, p_grid = 0;
+  int inner_form = 0;
+  // non-null while profiling: mixed solves take the host-driven path and bracket each
+  // persistent launch with events
+  Prof2d* prof = nullptr;
+};
+
+// A batch of B >= 2 instances on one grid: B single-instance layouts (instance 0 is the
+// layout's own Layout2d, `more` holds instances 1..B-1), per-instance staging of the
+// caller's batch-packed fields into the single-instance packing (eta [P], grad h [2P],
+// b [2P], x [2P]), and the buffers of the persistent inner solve that advances every
+// instance's float32 inner PCG in one launch.
+struct Batch2d {
+  int B = 0;
+  std::vector<Layout2d> more;
+  double* stage = nullptr;        // B x 7P
+  void* pinst = nullptr;          // d2::PInst2d [B]
+  double* pparts = nullptr;       // B (H + ny/2)
+  unsigned* pbar = nullptr;
+  int p_grid = 0, p_tw = 0;
+  Layout2d& inst(Layout2d& first, int b) { return b == 0 ? first : more[b - 1]; }
 };
 
 cudaError_t layout2d_create(Layout2d& L, const sgn_grid& g);
+cudaError_t batch2d_create(Batch2d& Bt, Layout2d& first, const sgn_grid& g, int B);
+void batch2d_destroy(Batch2d& Bt);
+// Batched constraint solves of the B instances (fields packed as the ABI's batches: scalar
+// instance b at [b P, b P + P), vector components at [b P, ...) and [Ptot + b P, ...)).
+// given (nullable): [B] coefficients; rec: [B] reports.  The mixed path runs a host-driven
+// refinement loop (two stream synchronisations per pass) around one persistent inner-solve
+// launch for every instance that needs a pass; the float64 path solves instance by instance.
+cudaError_t launch_pcg2d_batch(Layout2d& first, Batch2d& Bt, const void* tw64, const void* tw32,
+                               int precision, const double* eta, const double* gradh,
+                               const double* b, double* x, const SolveRec* given, int kind,
+                               double rtol, double rtol_inner, int maxit, int max_refine,
+                               SolveRec* rec, cudaStream_t s);
+// Copies instance b of batch-packed fields into / out of its staging block.
+cudaError_t batch2d_stage_in(const Layout2d& L, double* st, int b, long long Ptot,
+                             const double* scal, const double* vec0, const double* vec1,
+                             const double* vec2, cudaStream_t s);
+cudaError_t batch2d_stage_out(const Layout2d& L, const double* stvec, int b, long long Ptot,
+                              double* vec, cudaStream_t s);
 void layout2d_destroy(Layout2d& L);
 size_t layout2d_res_bytes(const Layout2d& L);
+// Inner-solve form: 0 the persistent inner solve (default), 1 four kernels per inner
+// iteration; tile_width: columns per column tile of the persistent form.  Drops the cached
+// solve graphs.
+cudaError_t layout2d_set_inner_form(Layout2d& L, int form, int tile_width);
+int persist2d_tile_width(int nx, int ny, int B, int grid);
+bool persist2d_tile_ok(int nx, int ny, int tile_width);
 
 cudaError_t launch_grad2d(const Layout2d& L, const void* tw64, const double* f, double* gradf,
                           cudaStream_t s);

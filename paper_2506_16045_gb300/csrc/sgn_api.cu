@@ -109,6 +109,7 @@ struct sgn_layout {
   long long points = 0;
   Layout1d l1;
   sgn::Layout2d l2;
+  sgn::Batch2d b2;                  // 2d layouts of count > 1: instances 1.. and batch buffers
   void* ws = nullptr;               // spectral workspace
   double* scratch = nullptr;        // 5 P doubles (rhs intermediates)
   float* coef_df = nullptr;         // 6 P floats (double-float coefficients, high and low parts)
@@ -127,7 +128,47 @@ struct DevStats {
   double flops64;        // algorithmic float64 flops of the PCG solves
   long long refinements; // float32 inner solves (mixed)
   long long sbdf2_warn;  // SBDF2 instance-steps whose eta_max left the fixed A's stable range
+  unsigned long long guard_max;   // 2d guard: running eta_max (order-preserving bits)
+  unsigned int guard_ticket;      // 2d guard: blocks done
 };
+
+// Order-preserving unsigned image of a double (for atomicMax over doubles of any sign).
+__device__ __forceinline__ unsigned long long ordered_bits(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double from_ordered(unsigned long long o) {
+  return __longlong_as_double((long long)((o >> 63) ? (o & 0x7fffffffffffffffull) : ~o));
+}
+
+// The SBDF2 guard of a 2d state (reading R10, below) over many blocks: each block's eta_max
+// goes to one atomicMax; the last block to finish compares it with the fixed A's eta_max,
+// counts a warning, and resets the running maximum for the next step.
+__global__ void __launch_bounds__(256) k_sbdf2_guard2d(long long P, const double* __restrict__ eta,
+                                                       const SolveRec* __restrict__ A,
+                                                       DevStats* __restrict__ stats) {
+  __shared__ double red[8];
+  __shared__ bool last;
+  double m = -1e300;
+  for (long long j = blockIdx.x * 256ll + threadIdx.x; j < P; j += (long long)gridDim.x * 256)
+    m = fmax(m, eta[j]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) m = fmax(m, red[w]);
+    m = fmax(m, red[0]);
+    atomicMax(&stats->guard_max, ordered_bits(m));
+    __threadfence();
+    last = atomicAdd(&stats->guard_ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  const double mx = from_ordered(atomicExch(&stats->guard_max, 0ull));
+  stats->guard_ticket = 0;
+  const double r = mx / A->eta_max;
+  if (!(r * r * r < 4.0 / 3.0)) atomicAdd(reinterpret_cast<unsigned long long*>(&stats->sbdf2_warn), 1ull);
+}
 
 // SBDF2 guard (reading R10): A is fixed from the initial data; the generalised eigenvalues
 // of A^{-1} G grow like (eta_max / eta_max,0)^3, and SBDF2's zero-stability needs them below
@@ -388,6 +429,38 @@ extern "C" sgn_status sgn_profile_enable(sgn_ctx* ctx, int on) {
   return SGN_OK;
 }
 
+extern "C" sgn_status sgn_profile_inner2d(sgn_layout* lay, int on, double* ms,
+                                          long long* launches, long long* iterations) {
+  if (check_layout(lay) || lay->dim != 2) return SGN_ERR_INVALID_ARG;
+  DeviceGuard g(lay->device);
+  sgn::Layout2d& L = lay->l2;
+  double t = 0.0;
+  long long n = 0, it = 0;
+  if (L.prof) {
+    for (size_t i = 0; i < L.prof->a.size(); ++i) {
+      float f = 0.0f;
+      if (cudaEventSynchronize(L.prof->b[i]) != cudaSuccess ||
+          cudaEventElapsedTime(&f, L.prof->a[i], L.prof->b[i]) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(lay->ctx, SGN_ERR_CUDA, "profile event");
+      }
+      t += f;
+      n += 1;
+      it += L.prof->iters[i];
+      cudaEventDestroy(L.prof->a[i]);
+      cudaEventDestroy(L.prof->b[i]);
+    }
+    delete L.prof;
+    L.prof = nullptr;
+  }
+  if (on) L.prof = new (std::nothrow) sgn::Prof2d();
+  if (on && !L.prof) return fail(lay->ctx, SGN_ERR_NOMEM, "profile record");
+  if (ms) *ms = t;
+  if (launches) *launches = n;
+  if (iterations) *iterations = it;
+  return SGN_OK;
+}
+
 extern "C" sgn_status sgn_profile_read(sgn_ctx* ctx, double* pcg_ms, long long* pcg_calls,
                                        double* rhs_ms, long long* rhs_calls) {
   if (!ctx) return SGN_ERR_INVALID_ARG;
@@ -440,7 +513,12 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
   *out = nullptr;
   const int dim = grids[0].dim;
   if (dim != 1 && dim != 2) return fail(ctx, SGN_ERR_INVALID_ARG, "dim must be 1 or 2");
-  if (dim == 2 && count != 1) return fail(ctx, SGN_ERR_INVALID_ARG, "2d layouts hold one instance");
+  if (dim == 2 && count > sgn::kMaxBatch2dAbi)
+    return fail(ctx, SGN_ERR_INVALID_ARG, "too many 2d instances in one layout");
+  for (int i = 1; dim == 2 && i < count; ++i)
+    if (grids[i].nx != grids[0].nx || grids[i].ny != grids[0].ny || grids[i].Lx != grids[0].Lx ||
+        grids[i].Ly != grids[0].Ly || grids[i].g != grids[0].g)
+      return fail(ctx, SGN_ERR_INVALID_ARG, "a 2d batch needs one grid for every instance");
   for (int i = 0; i < count; ++i) {
     const sgn_grid& g = grids[i];
     if (g.dim != dim || !(g.Lx > 0.0) || (dim == 2 && !(g.Ly > 0.0)))
@@ -546,12 +624,13 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
     }
   } else {
     cudaError_t e = sgn::layout2d_create(lay->l2, grids[0]);
+    if (e == cudaSuccess && count > 1) e = sgn::batch2d_create(lay->b2, lay->l2, grids[0], count);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return cleanup(e == cudaErrorMemoryAllocation ? SGN_ERR_NOMEM : SGN_ERR_CUDA, "2d layout");
     }
-    if (cudaMalloc(&lay->rec, sizeof(SolveRec)) != cudaSuccess ||
-        cudaMalloc(&lay->given, sizeof(SolveRec)) != cudaSuccess) {
+    if (cudaMalloc(&lay->rec, sizeof(SolveRec) * count) != cudaSuccess ||
+        cudaMalloc(&lay->given, sizeof(SolveRec) * count) != cudaSuccess) {
       cudaGetLastError();
       return cleanup(SGN_ERR_NOMEM, "layout allocation");
     }
@@ -572,6 +651,7 @@ extern "C" void sgn_layout_destroy(sgn_layout* lay) {
   cudaFree(lay->l1.big);
   cudaFree(lay->l1.d_ids);
   delete[] lay->l1.h_inst;
+  sgn::batch2d_destroy(lay->b2);
   sgn::layout2d_destroy(lay->l2);
   cudaFree(lay->ws);
   cudaFree(lay->scratch);
@@ -620,10 +700,24 @@ extern "C" sgn_status sgn_layout_get_form(const sgn_layout* lay, int log2n, int*
   return sgn_layout_get_forms(lay, log2n, ctas, &r);
 }
 
-namespace {
+extern "C" sgn_status sgn_layout_set_form2d(sgn_layout* lay, int inner, int tile_width) {
+  if (check_layout(lay) || lay->dim != 2 || (inner != 0 && inner != 1) ||
+      (tile_width != 0 && tile_width != 1 && tile_width != 2 && tile_width != 4))
+    return fail(lay ? lay->ctx : nullptr, SGN_ERR_INVALID_ARG, "set_form2d args");
+  sgn::Layout2d& L = lay->l2;
+  const int tw = tile_width ? tile_width : sgn::persist2d_tile_width(L.nx, L.ny, 1, L.p_grid);
+  if (!sgn::persist2d_tile_ok(L.nx, L.ny, tw))
+    return fail(lay->ctx, SGN_ERR_UNSUPPORTED_SIZE, "tile width too wide for this grid");
+  SGN_CUDA(lay->ctx, sgn::layout2d_set_inner_form(L, inner, tw));
+  return SGN_OK;
+}
 
-}  // namespace
-
+extern "C" sgn_status sgn_layout_get_form2d(const sgn_layout* lay, int* inner, int* tile_width) {
+  if (check_layout(lay) || lay->dim != 2 || !inner || !tile_width) return SGN_ERR_INVALID_ARG;
+  *inner = lay->l2.inner_form;
+  *tile_width = lay->l2.p_tw;
+  return SGN_OK;
+}
 
 extern "C" sgn_status sgn_layout_offsets(const sgn_layout* lay, long long* offsets) {
   if (!lay || !offsets) return SGN_ERR_INVALID_ARG;
@@ -666,13 +760,46 @@ sgn_status fetch_recs(sgn_layout* lay, std::vector<SolveRec>& h, cudaStream_t s)
 
 }  // namespace
 
-extern "C" sgn_status sgn_spectral_grad(sgn_ctx* ctx, const sgn_layout* lay, const double* f,
+namespace {
+
+bool is_batch2d(const sgn_layout* lay) { return lay->dim == 2 && lay->count > 1; }
+
+// A single-instance 2d operation over every instance of a 2d batch: instance b's fields are
+// staged into its block st (eta [P], vector 0 [2P], vector 1 [2P], output [2P], in the
+// single-instance packing), op(L_b, st, b) runs, and the output vector goes back to `out`.
+template <typename Op>
+cudaError_t each_instance2d(sgn_layout* lay, const double* scal, const double* v0,
+                            const double* v1, double* out, cudaStream_t s, Op op) {
+  sgn::Batch2d& Bt = lay->b2;
+  const long long P = lay->l2.P, Ptot = lay->points;
+  cudaError_t e;
+  for (int b = 0; b < Bt.B; ++b) {
+    double* st = Bt.stage + 7 * P * b;
+    sgn::Layout2d& L = Bt.inst(lay->l2, b);
+    if ((e = sgn::batch2d_stage_in(L, st, b, Ptot, scal, v0, v1, nullptr, s)) ||
+        (e = op(L, st, b)))
+      return e;
+    if (out && (e = sgn::batch2d_stage_out(L, st + 5 * P, b, Ptot, out, s))) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" sgn_status sgn_spectral_grad(sgn_ctx* ctx, const sgn_layout* lay_c, const double* f,
                                         double* gradf, sgn_stream stream) {
+  sgn_layout* lay = const_cast<sgn_layout*>(lay_c);
   if (!ctx || check_layout(lay) || !f || !gradf) return fail(ctx, SGN_ERR_INVALID_ARG, "grad");
   DeviceGuard g(ctx->device);
-  cudaError_t e = lay->dim == 1
-                      ? sgn::launch_deriv1d(lay->l1, ctx->tw64, f, gradf, as_stream(stream))
-                      : sgn::launch_grad2d(lay->l2, ctx->tw64, f, gradf, as_stream(stream));
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e =
+      lay->dim == 1 ? sgn::launch_deriv1d(lay->l1, ctx->tw64, f, gradf, s)
+      : is_batch2d(lay)
+          ? each_instance2d(lay, f, nullptr, nullptr, gradf, s,
+                            [&](sgn::Layout2d& L, double* st, int) {
+                              return sgn::launch_grad2d(L, ctx->tw64, st, st + 5 * L.P, s);
+                            })
+          : sgn::launch_grad2d(lay->l2, ctx->tw64, f, gradf, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sgn_spectral_grad");
   return SGN_OK;
 }
@@ -685,9 +812,14 @@ extern "C" sgn_status sgn_precond_coeffs(sgn_ctx* ctx, const sgn_layout* lay_c, 
     return fail(ctx, SGN_ERR_INVALID_ARG, "coeffs");
   DeviceGuard g(ctx->device);
   cudaStream_t s = as_stream(stream);
-  cudaError_t e = lay->dim == 1
-                      ? sgn::launch_coeffs1d(lay->l1, eta, gradh, kind, lay->rec, s)
-                      : sgn::launch_coeffs2d(lay->l2, eta, gradh, kind, lay->rec, s);
+  cudaError_t e =
+      lay->dim == 1 ? sgn::launch_coeffs1d(lay->l1, eta, gradh, kind, lay->rec, s)
+      : is_batch2d(lay)
+          ? each_instance2d(lay, eta, gradh, nullptr, nullptr, s,
+                            [&](sgn::Layout2d& L, double* st, int b) {
+                              return sgn::launch_coeffs2d(L, st, st + L.P, kind, lay->rec + b, s);
+                            })
+          : sgn::launch_coeffs2d(lay->l2, eta, gradh, kind, lay->rec, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sgn_precond_coeffs");
   std::vector<SolveRec> h;
   sgn_status st = fetch_recs(lay, h, s);
@@ -704,16 +836,24 @@ extern "C" sgn_status sgn_precond_coeffs(sgn_ctx* ctx, const sgn_layout* lay_c, 
   return SGN_OK;
 }
 
-extern "C" sgn_status sgn_apply_operator(sgn_ctx* ctx, const sgn_layout* lay, const double* eta,
+extern "C" sgn_status sgn_apply_operator(sgn_ctx* ctx, const sgn_layout* lay_c, const double* eta,
                                          const double* gradh, const double* u, double* Gu,
                                          sgn_stream stream) {
+  sgn_layout* lay = const_cast<sgn_layout*>(lay_c);
   if (!ctx || check_layout(lay) || !eta || !gradh || !u || !Gu)
     return fail(ctx, SGN_ERR_INVALID_ARG, "apply_operator");
   DeviceGuard g(ctx->device);
+  cudaStream_t s = as_stream(stream);
   cudaError_t e =
-      lay->dim == 1
-          ? sgn::launch_apply_G1d(lay->l1, ctx->tw64, eta, gradh, u, Gu, as_stream(stream))
-          : sgn::launch_apply_G2d(lay->l2, ctx->tw64, eta, gradh, u, Gu, as_stream(stream));
+      lay->dim == 1 ? sgn::launch_apply_G1d(lay->l1, ctx->tw64, eta, gradh, u, Gu, s)
+      : is_batch2d(lay)
+          ? each_instance2d(lay, eta, gradh, u, Gu, s,
+                            [&](sgn::Layout2d& L, double* st, int) {
+                              const long long P = L.P;
+                              return sgn::launch_apply_G2d(L, ctx->tw64, st, st + P, st + 3 * P,
+                                                           st + 5 * P, s);
+                            })
+          : sgn::launch_apply_G2d(lay->l2, ctx->tw64, eta, gradh, u, Gu, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sgn_apply_operator");
   return SGN_OK;
 }
@@ -728,9 +868,15 @@ extern "C" sgn_status sgn_precond_solve(sgn_ctx* ctx, const sgn_layout* lay_c,
   cudaStream_t s = as_stream(stream);
   sgn_status st = upload_given(lay, P, s);
   if (st) return st;
-  cudaError_t e = lay->dim == 1
-                      ? sgn::launch_precond1d(lay->l1, ctx->tw64, lay->given, r, z, s)
-                      : sgn::launch_precond2d(lay->l2, ctx->tw64, lay->given, r, z, s);
+  cudaError_t e =
+      lay->dim == 1 ? sgn::launch_precond1d(lay->l1, ctx->tw64, lay->given, r, z, s)
+      : is_batch2d(lay)
+          ? each_instance2d(lay, nullptr, nullptr, r, z, s,
+                            [&](sgn::Layout2d& L, double* st, int b) {
+                              return sgn::launch_precond2d(L, ctx->tw64, lay->given + b,
+                                                           st + 3 * L.P, st + 5 * L.P, s);
+                            })
+          : sgn::launch_precond2d(lay->l2, ctx->tw64, lay->given, r, z, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sgn_precond_solve");
   return SGN_OK;
 }
@@ -748,6 +894,9 @@ sgn_status run_pcg(sgn_layout* lay, const double* eta, const double* gradh, cons
   if (lay->dim == 1) {
     e = sgn::launch_pcg1d(lay->l1, ctx->tw64, ctx->tw32, prec, eta, gradh, b, x, given, kind, rtol,
                           rtol_inner, maxit, max_refine, lay->rec, lay->ws, lay->coef_df, s);
+  } else if (lay->count > 1) {
+    e = sgn::launch_pcg2d_batch(lay->l2, lay->b2, ctx->tw64, ctx->tw32, prec, eta, gradh, b, x,
+                                given, kind, rtol, rtol_inner, maxit, max_refine, lay->rec, s);
   } else {
     e = sgn::launch_pcg2d(lay->l2, ctx->tw64, ctx->tw32, prec, eta, gradh, b, x, given, kind, rtol,
                           rtol_inner, maxit, max_refine, lay->rec, s);
@@ -835,6 +984,7 @@ extern "C" sgn_status sgn_gmres(sgn_ctx* ctx, const sgn_layout* lay_c, const dou
   if (!ctx || check_layout(lay) || !eta || !gradh || !b || !x || !(rtol > 0.0) || maxit < 0 ||
       restart < 1 || restart > SGN_GMRES_MAX_RESTART)
     return fail(ctx, SGN_ERR_INVALID_ARG, "gmres args");
+  if (is_batch2d(lay)) return fail(ctx, SGN_ERR_INVALID_ARG, "gmres on a 2d batch");
   DeviceGuard g(ctx->device);
   cudaStream_t s = as_stream(stream);
   sgn::GmresArgs a;
@@ -888,6 +1038,7 @@ extern "C" sgn_status sgn_rhs(sgn_ctx* ctx, const sgn_layout* lay, const double*
                               double* f_eta, double* f_U, sgn_stream stream) {
   if (!ctx || check_layout(lay) || !eta || !u || !h || !gradh || !f_eta || !f_U)
     return fail(ctx, SGN_ERR_INVALID_ARG, "rhs args");
+  if (is_batch2d(lay)) return fail(ctx, SGN_ERR_INVALID_ARG, "rhs on a 2d batch");
   DeviceGuard g(ctx->device);
   const double grav = lay->grids[0].g;
   ProfScope prof(ctx, as_stream(stream), 1);
@@ -1223,6 +1374,7 @@ extern "C" sgn_status sgn_state_create(sgn_ctx* ctx, const sgn_layout* lay, doub
                                        sgn_state** out) {
   if (!ctx || check_layout(lay) || !eta || !U || !u || !h || !gradh || !out)
     return fail(ctx, SGN_ERR_INVALID_ARG, "state args");
+  if (is_batch2d(lay)) return fail(ctx, SGN_ERR_INVALID_ARG, "states on a 2d batch");
   *out = nullptr;
   DeviceGuard g(ctx->device);
   sgn_state* st = new (std::nothrow) sgn_state();
@@ -1563,8 +1715,13 @@ extern "C" sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nstep
     SGN_TRY(copy_field(st, st->eta, st->eta_s, P, s));
     SGN_TRY(copy_field(st, st->U, st->U_s, V, s));
     SGN_TRY(dealias_at(st, st->eta, st->U, st->u, s));
-    k_sbdf2_guard<<<st->lay->count, 256, 0, s>>>(one_d ? st->lay->l1.d_inst : nullptr, st->P,
-                                                 st->eta, st->A_fixed, st->stats);
+    if (one_d) {
+      k_sbdf2_guard<<<st->lay->count, 256, 0, s>>>(st->lay->l1.d_inst, st->P, st->eta,
+                                                   st->A_fixed, st->stats);
+    } else {
+      const long long nb = std::min<long long>(1024, (st->P + 255) / 256);
+      k_sbdf2_guard2d<<<(int)nb, 256, 0, s>>>(st->P, st->eta, st->A_fixed, st->stats);
+    }
     SGN_CUDA(ctx, cudaGetLastError());
     std::swap(st->he[0], st->he[1]);
     std::swap(st->hU[0], st->hU[1]);

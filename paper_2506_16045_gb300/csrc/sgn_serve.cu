@@ -1,16 +1,24 @@
 // Serving: continuous batching of SGN constraint solves and runs on one GPU.
 //
-// A worker thread owns a stream and a private sgn_ctx.  Submissions copy their arrays to
-// the device and queue; the worker admits queued requests in arrival order while their
-// memory footprint fits the budget (a later, smaller request may pass a blocked larger
-// one), then repeatedly:
-//   * runs all admitted 1d solves as one batched PCG launch group;
-//   * advances all admitted 1d RK4 runs together by a chunk of steps through one batched
-//     layout (per-instance dt), gathering and scattering their device state around it;
-//   * advances 2d and multistep runs, and runs 2d solves, per request;
-//   * completes finished requests and frees their workspace.
+// A worker thread owns a private sgn_ctx and a set of CUDA streams ("lanes").  Submissions
+// copy their arrays to the device and queue; the worker admits queued requests in arrival
+// order while their memory footprint fits the budget (a later, smaller request may pass a
+// blocked larger one) and keeps every admitted request moving without waiting on the GPU:
+//   * admitted 1d solves, grouped by options, run as one batched PCG per group on a
+//     high-priority solve lane, their reports written to device memory (sgn_pcg_async);
+//   * admitted 1d RK4 runs advance together, a chunk of steps at a time, through one batched
+//     layout (per-instance dt) on the batch lane, gathering and scattering their device
+//     state around each chunk;
+//   * 1d multistep runs (AB2-4, SBDF2) advance chunk by chunk on their own lanes;
+//   * 2d solves and 2d runs share the 2d lane, which has the highest priority: their
+//     inner solves are cooperative persistent launches, which must not wait on one another;
+//   * each piece of work ends with an event; the worker polls the events, completes the
+//     finished requests and issues the next chunk, so the lanes' work overlaps on the device.
+// Work that frees device memory (cudaFree waits for the whole device) is deferred until no
+// lane is busy, or until the deferred bytes pass a threshold.
 // RK4 is a one-step method and every instance of a batched launch is computed by its own
-// CTAs, so a request's result does not depend on which requests shared its launches.
+// CTAs, and a 2d or multistep request runs on its own layout and state, so a request's
+// result does not depend on which requests ran beside it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,6 +42,8 @@ sgn_status state_attach(sgn_state* st, cudaStream_t s);
 namespace {
 
 constexpr int kChunk = 16;           // RUN steps per scheduling round
+constexpr int kSolveLanes = 2;       // high-priority lanes of the 1d solve groups
+constexpr size_t kReapBytes = (size_t)2 << 30;   // deferred frees forced past this many bytes
 
 struct Req {
   uint64_t ticket = 0;
@@ -51,12 +61,29 @@ struct Req {
   // per-request objects (2d / multistep runs, 2d solves)
   sgn_layout* lay = nullptr;
   sgn_state* st = nullptr;
+  cudaEvent_t ready = nullptr;        // the request's set-up work (grad h, U = G u) is done
+  cudaStream_t own = nullptr;         // 1d multistep runs: their own lane
+  bool busy = false;                  // a job of this request is in flight
+  double last_issue = 0.0;            // when its last job was issued (2d lane turns)
   int remaining = 0;
   bool admitted = false, done = false;
   sgn_status status = SGN_OK;
   sgn_pcg_info info{};
   long long iters = 0;
   double t_submit = 0, t_admit = 0, t_done = 0;
+};
+
+// One piece of issued work: the requests it serves, its lane and its completion event.
+enum JobKind { JOB_SOLVES_1D = 0, JOB_RUN_BATCH = 1, JOB_SINGLE = 2 };
+struct Job {
+  JobKind kind;
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev = nullptr;
+  std::vector<Req*> reqs;
+  sgn_layout* lay = nullptr;          // a solve group's layout
+  int info_at = -1, info_n = 0;       // slots of the report pool
+  int K = 0;                          // steps of a run chunk
+  sgn_status err = SGN_OK;            // an issue-time failure
 };
 
 double now_s() {
@@ -71,8 +98,13 @@ bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1))
 struct sgn_server {
   int device = 0;
   sgn_ctx* ctx = nullptr;
-  cudaStream_t stream = nullptr;
-  cudaStream_t copy = nullptr;
+  cudaStream_t stream = nullptr;      // set-up work of admitted requests
+  cudaStream_t copy = nullptr;        // submissions' input copies
+  cudaStream_t lane_solve[kSolveLanes] = {};
+  cudaStream_t lane_batch = nullptr;
+  cudaStream_t lane_2d = nullptr;
+  int prio_lo = 0, prio_hi = 0;       // stream priority range (hi: the greatest)
+  int next_solve_lane = 0;
   size_t budget = 0, used = 0;
   std::mutex mu;
   std::condition_variable cv;
@@ -82,18 +114,30 @@ struct sgn_server {
   uint64_t next = 1;
   bool stop = false;
   std::thread worker;
+  std::vector<Job*> inflight;
+  std::vector<cudaEvent_t> events;    // completed jobs' events, reused
+  // reports of solve jobs: device slots and their pinned host copies
+  sgn_pcg_info* info_dev = nullptr;
+  sgn_pcg_info* info_host = nullptr;
+  std::vector<char> info_used;
+  // deferred frees (cudaFree waits for the device)
+  std::vector<Req*> reap_reqs;
+  std::vector<sgn_layout*> reap_lays;
+  std::vector<sgn_state*> reap_states;
+  size_t reap_bytes = 0;
   // cached batch objects for 1d RK4 runs
   std::vector<uint64_t> run_members;
+  bool batch_busy = false;
   sgn_layout* run_lay = nullptr;
   sgn_state* run_st = nullptr;
   double* pk = nullptr;               // packed eta, U, u, h, gh of the RK4 batch (5 x cap)
   long long pk_cap = 0;
-  double* pks = nullptr;              // packed eta, b, x, gh of a solve batch
-  long long pks_cap = 0;
   std::map<std::pair<int, double>, sgn_layout*> one1d;   // single-instance 1d layouts
 };
 
 namespace {
+
+constexpr int kInfoSlots = 8192;
 
 size_t footprint_of(int d, long long N) {
   const size_t io = (size_t)(2 + 3 * d) * 8 * N;          // eta, h, u/b, U, gradh
@@ -111,6 +155,10 @@ void free_req_work(Req* r) {
   cudaFree(r->gh);
   cudaFree(r->b);
   r->h = r->gh = r->b = nullptr;
+  if (r->ready) cudaEventDestroy(r->ready);
+  r->ready = nullptr;
+  if (r->own) cudaStreamDestroy(r->own);
+  r->own = nullptr;
 }
 
 void free_req_all(Req* r) {
@@ -119,6 +167,20 @@ void free_req_all(Req* r) {
   cudaFree(r->u);
   cudaFree(r->U);
   delete r;
+}
+
+// Frees deferred work, which waits for the device: only when no lane is busy, unless the
+// deferred memory has grown past kReapBytes.
+void reap(sgn_server* S, bool force) {
+  if (S->reap_reqs.empty() && S->reap_lays.empty() && S->reap_states.empty()) return;
+  if (!force && !S->inflight.empty() && S->reap_bytes < kReapBytes) return;
+  for (Req* r : S->reap_reqs) free_req_work(r);
+  for (sgn_state* st : S->reap_states) sgn_state_free(st);
+  for (sgn_layout* l : S->reap_lays) sgn_layout_destroy(l);
+  S->reap_reqs.clear();
+  S->reap_states.clear();
+  S->reap_lays.clear();
+  S->reap_bytes = 0;
 }
 
 sgn_layout* one_layout(sgn_server* S, const sgn_grid& g) {
@@ -131,13 +193,16 @@ sgn_layout* one_layout(sgn_server* S, const sgn_grid& g) {
   return lay;
 }
 
+// The request is finished: publish its result; its working memory is freed later.
 void finish(sgn_server* S, Req* r, sgn_status st) {
   const double t = now_s();
-  free_req_work(r);
+  S->reap_reqs.push_back(r);
+  S->reap_bytes += r->footprint;
   std::lock_guard<std::mutex> lk(S->mu);
   r->status = st;
   r->t_done = t;
   r->done = true;
+  r->busy = false;
   S->used -= r->footprint;
 }
 
@@ -145,100 +210,150 @@ bool is_batched_run(const Req* r) {
   return r->q.kind == SGN_REQ_RUN && r->d == 1 && r->q.scheme == SGN_SCHEME_RK4;
 }
 
-// Initialise an admitted request on the device.
+cudaEvent_t take_event(sgn_server* S) {
+  if (!S->events.empty()) {
+    cudaEvent_t e = S->events.back();
+    S->events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+int take_info(sgn_server* S, int n) {
+  for (int i = 0; i + n <= kInfoSlots; ++i) {
+    int j = 0;
+    while (j < n && !S->info_used[i + j]) ++j;
+    if (j == n) {
+      for (int k = 0; k < n; ++k) S->info_used[i + k] = 1;
+      return i;
+    }
+    i += j;
+  }
+  return -1;
+}
+
+void give_info(sgn_server* S, int at, int n) {
+  for (int k = 0; k < n; ++k) S->info_used[at + k] = 0;
+}
+
+// Initialise an admitted request on the device (the set-up stream); records r->ready.
 sgn_status start(sgn_server* S, Req* r) {
   const sgn_stream s = S->stream;
+  sgn_status e = SGN_OK;
   if (r->q.kind == SGN_REQ_RUN && is_batched_run(r)) {
     sgn_layout* lay = one_layout(S, r->q.grid);
     if (!lay) return SGN_ERR_NOMEM;
-    sgn_status e = sgn_spectral_grad(S->ctx, lay, r->h, r->gh, s);
-    if (e) return e;
-    return sgn_apply_operator(S->ctx, lay, r->eta, r->gh, r->u, r->U, s);
+    e = sgn_spectral_grad(S->ctx, lay, r->h, r->gh, s);
+    if (!e) e = sgn_apply_operator(S->ctx, lay, r->eta, r->gh, r->u, r->U, s);
+  } else if (r->q.kind == SGN_REQ_RUN) {
+    e = sgn_layout_create(S->ctx, 1, &r->q.grid, &r->lay);
+    if (!e) e = sgn_state_create(S->ctx, r->lay, r->eta, r->U, r->u, r->h, r->gh, &r->st);
+    if (!e) e = sgn_state_init(r->st, s);
+  } else if (r->d == 2) {
+    // SOLVE: grad h now (2d solves also get their layout here)
+    e = sgn_layout_create(S->ctx, 1, &r->q.grid, &r->lay);
+    if (!e) e = sgn_spectral_grad(S->ctx, r->lay, r->h, r->gh, s);
+  } else {
+    sgn_layout* lay = one_layout(S, r->q.grid);
+    if (!lay) return SGN_ERR_NOMEM;
+    e = sgn_spectral_grad(S->ctx, lay, r->h, r->gh, s);
   }
-  if (r->q.kind == SGN_REQ_RUN) {
-    sgn_status e = sgn_layout_create(S->ctx, 1, &r->q.grid, &r->lay);
-    if (e) return e;
-    if ((e = sgn_state_create(S->ctx, r->lay, r->eta, r->U, r->u, r->h, r->gh, &r->st))) return e;
-    return sgn_state_init(r->st, s);
-  }
-  // SOLVE: grad h now (2d solves also get their layout here)
-  if (r->d == 2) {
-    sgn_status e = sgn_layout_create(S->ctx, 1, &r->q.grid, &r->lay);
-    if (e) return e;
-    return sgn_spectral_grad(S->ctx, r->lay, r->h, r->gh, s);
-  }
-  sgn_layout* lay = one_layout(S, r->q.grid);
-  if (!lay) return SGN_ERR_NOMEM;
-  return sgn_spectral_grad(S->ctx, lay, r->h, r->gh, s);
-}
-
-// grow-only packed buffer of 5 P doubles
-sgn_status ensure_pack(double** buf, long long* cap, long long P) {
-  if (P <= *cap) return SGN_OK;
-  cudaFree(*buf);
-  *buf = nullptr;
-  if (cudaMalloc(buf, sizeof(double) * 5 * (size_t)P) != cudaSuccess) {
+  if (e) return e;
+  if (!(r->ready = take_event(S)) || cudaEventRecord(r->ready, S->stream) != cudaSuccess) {
     cudaGetLastError();
-    *cap = 0;
-    return SGN_ERR_NOMEM;
+    return SGN_ERR_CUDA;
   }
-  *cap = P;
   return SGN_OK;
 }
 
-// All admitted 1d solves as one batched PCG (grouped by options).
-void run_solves_1d(sgn_server* S, std::vector<Req*>& v) {
-  if (v.empty()) return;
-  std::vector<sgn_grid> grids;
-  for (Req* r : v) grids.push_back(r->q.grid);
-  sgn_layout* lay = nullptr;
-  sgn_status e = sgn_layout_create(S->ctx, (int)v.size(), grids.data(), &lay);
-  if (e) {
-    for (Req* r : v) finish(S, r, e);
-    return;
-  }
-  std::vector<long long> off(v.size() + 1);
-  sgn_layout_offsets(lay, off.data());
-  const long long P = off.back();
-  if ((e = ensure_pack(&S->pks, &S->pks_cap, P))) {
-    sgn_layout_destroy(lay);
-    for (Req* r : v) finish(S, r, e);
-    return;
-  }
-  double *pe = S->pks, *pb = S->pks + P, *px = S->pks + 2 * P, *pg = S->pks + 3 * P;
-  for (size_t i = 0; i < v.size(); ++i) {
-    const size_t bytes = sizeof(double) * (size_t)v[i]->N;
-    cudaMemcpyAsync(pe + off[i], v[i]->eta, bytes, cudaMemcpyDeviceToDevice, S->stream);
-    cudaMemcpyAsync(pb + off[i], v[i]->b, bytes, cudaMemcpyDeviceToDevice, S->stream);
-    cudaMemcpyAsync(pg + off[i], v[i]->gh, bytes, cudaMemcpyDeviceToDevice, S->stream);
-  }
-  cudaMemsetAsync(px, 0, sizeof(double) * P, S->stream);
-  const sgn_opts& o = v[0]->q.opts;
-  std::vector<sgn_pcg_info> info(v.size());
-  e = sgn_pcg(S->ctx, lay, pe, pg, nullptr, pb, px, o.rtol, o.maxit, o.prec, info.data(),
-              S->stream);
-  for (size_t i = 0; i < v.size(); ++i)
-    cudaMemcpyAsync(v[i]->u, px + off[i], sizeof(double) * (size_t)v[i]->N,
-                    cudaMemcpyDeviceToDevice, S->stream);
-  cudaStreamSynchronize(S->stream);
-  sgn_layout_destroy(lay);
-  for (size_t i = 0; i < v.size(); ++i) {
-    v[i]->info = info[i];
-    finish(S, v[i], e == SGN_ERR_CUDA ? e : (sgn_status)info[i].status);
-  }
+void wait_ready(cudaStream_t s, const std::vector<Req*>& v) {
+  for (Req* r : v)
+    if (r->ready) cudaStreamWaitEvent(s, r->ready, 0);
 }
 
-// Advance all admitted 1d RK4 runs together by K steps.
-void run_batch_rk4(sgn_server* S, std::vector<Req*>& v) {
-  if (v.empty()) return;
+// Ends an issued job with its event and puts it in flight (or fails its requests).
+void launch_job(sgn_server* S, Job* J) {
+  if (!J->err) {
+    J->ev = take_event(S);
+    if (!J->ev || cudaEventRecord(J->ev, J->s) != cudaSuccess) {
+      cudaGetLastError();
+      J->err = SGN_ERR_CUDA;
+    }
+  }
+  for (Req* r : J->reqs) r->busy = true;
+  S->inflight.push_back(J);
+}
+
+// All given 1d solves (one option set) as one batched PCG with device-side reports.
+void issue_solves_1d(sgn_server* S, std::vector<Req*>& v) {
+  Job* J = new Job();
+  J->kind = JOB_SOLVES_1D;
+  J->reqs = v;
+  J->s = S->lane_solve[S->next_solve_lane];
+  S->next_solve_lane = (S->next_solve_lane + 1) % kSolveLanes;
+  std::vector<sgn_grid> grids;
+  for (Req* r : v) grids.push_back(r->q.grid);
+  sgn_status e = sgn_layout_create(S->ctx, (int)v.size(), grids.data(), &J->lay);
+  if (!e && (J->info_at = take_info(S, (int)v.size())) < 0) e = SGN_ERR_NOMEM;
+  J->info_n = (int)v.size();
+  double* pk = nullptr;
+  long long P = 0;
+  std::vector<long long> off(v.size() + 1);
+  if (!e) {
+    sgn_layout_offsets(J->lay, off.data());
+    P = off.back();
+    // the packed arrays of the group live with its layout (stream-ordered allocation)
+    if (cudaMallocAsync(reinterpret_cast<void**>(&pk), sizeof(double) * 4 * (size_t)P, J->s) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      e = SGN_ERR_NOMEM;
+    }
+  }
+  if (!e) {
+    wait_ready(J->s, v);
+    double *pe = pk, *pb = pk + P, *px = pk + 2 * P, *pg = pk + 3 * P;
+    for (size_t i = 0; i < v.size(); ++i) {
+      const size_t bytes = sizeof(double) * (size_t)v[i]->N;
+      cudaMemcpyAsync(pe + off[i], v[i]->eta, bytes, cudaMemcpyDeviceToDevice, J->s);
+      cudaMemcpyAsync(pb + off[i], v[i]->b, bytes, cudaMemcpyDeviceToDevice, J->s);
+      cudaMemcpyAsync(pg + off[i], v[i]->gh, bytes, cudaMemcpyDeviceToDevice, J->s);
+    }
+    cudaMemsetAsync(px, 0, sizeof(double) * P, J->s);
+    const sgn_opts& o = v[0]->q.opts;
+    e = sgn_pcg_async(S->ctx, J->lay, pe, pg, pb, px, o.rtol, o.maxit, o.prec,
+                      S->info_dev + J->info_at, J->s);
+    for (size_t i = 0; i < v.size(); ++i)
+      cudaMemcpyAsync(v[i]->u, px + off[i], sizeof(double) * (size_t)v[i]->N,
+                      cudaMemcpyDeviceToDevice, J->s);
+    cudaMemcpyAsync(S->info_host + J->info_at, S->info_dev + J->info_at,
+                    sizeof(sgn_pcg_info) * v.size(), cudaMemcpyDeviceToHost, J->s);
+    cudaFreeAsync(pk, J->s);
+    if (cudaGetLastError() != cudaSuccess && !e) e = SGN_ERR_CUDA;
+  }
+  J->err = e;
+  launch_job(S, J);
+}
+
+// The next chunk of all given 1d RK4 runs (one option set), on the batch lane.
+void issue_run_batch(sgn_server* S, std::vector<Req*>& v) {
+  Job* J = new Job();
+  J->kind = JOB_RUN_BATCH;
+  J->reqs = v;
+  J->s = S->lane_batch;
   int K = kChunk;
   for (Req* r : v) K = std::min(K, r->remaining);
+  J->K = K;
   std::vector<uint64_t> members;
   for (Req* r : v) members.push_back(r->ticket);
   sgn_status e = SGN_OK;
   if (members != S->run_members) {
-    if (S->run_st) sgn_state_free(S->run_st);
-    if (S->run_lay) sgn_layout_destroy(S->run_lay);
+    if (S->run_st) S->reap_states.push_back(S->run_st);
+    if (S->run_lay) S->reap_lays.push_back(S->run_lay);
     S->run_st = nullptr;
     S->run_lay = nullptr;
     S->run_members.clear();
@@ -246,82 +361,169 @@ void run_batch_rk4(sgn_server* S, std::vector<Req*>& v) {
     for (Req* r : v) grids.push_back(r->q.grid);
     e = sgn_layout_create(S->ctx, (int)v.size(), grids.data(), &S->run_lay);
     long long P = e ? 0 : sgn_layout_points(S->run_lay);
-    if (!e) e = ensure_pack(&S->pk, &S->pk_cap, P);
+    if (!e && P > S->pk_cap) {
+      // the packed buffer may still be read by an earlier chunk on this lane: free it in order
+      if (S->pk) cudaFreeAsync(S->pk, J->s);
+      S->pk = nullptr;
+      S->pk_cap = 0;
+      if (cudaMallocAsync(reinterpret_cast<void**>(&S->pk), sizeof(double) * 5 * (size_t)P,
+                          J->s) != cudaSuccess) {
+        cudaGetLastError();
+        e = SGN_ERR_NOMEM;
+      } else {
+        S->pk_cap = P;
+      }
+    }
     if (!e)
       e = sgn_state_create(S->ctx, S->run_lay, S->pk, S->pk + P, S->pk + 2 * P, S->pk + 3 * P,
                            S->pk + 4 * P, &S->run_st);
-    if (e) {
-      for (Req* r : v) finish(S, r, e);
-      return;
+    if (!e) S->run_members = members;
+  }
+  if (!e) {
+    sgn_layout* lay = S->run_lay;
+    std::vector<long long> off(v.size() + 1);
+    sgn_layout_offsets(lay, off.data());
+    const long long P = off.back();
+    double* F[5] = {S->pk, S->pk + P, S->pk + 2 * P, S->pk + 3 * P, S->pk + 4 * P};
+    wait_ready(J->s, v);
+    for (size_t i = 0; i < v.size(); ++i) {
+      double* src[5] = {v[i]->eta, v[i]->U, v[i]->u, v[i]->h, v[i]->gh};
+      for (int f = 0; f < 5; ++f)
+        cudaMemcpyAsync(F[f] + off[i], src[f], sizeof(double) * (size_t)v[i]->N,
+                        cudaMemcpyDeviceToDevice, J->s);
     }
-    S->run_members = members;
-  }
-  sgn_layout* lay = S->run_lay;
-  std::vector<long long> off(v.size() + 1);
-  sgn_layout_offsets(lay, off.data());
-  const long long P = off.back();
-  double* F[5] = {S->pk, S->pk + P, S->pk + 2 * P, S->pk + 3 * P, S->pk + 4 * P};
-  for (size_t i = 0; i < v.size(); ++i) {
-    double* src[5] = {v[i]->eta, v[i]->U, v[i]->u, v[i]->h, v[i]->gh};
-    for (int f = 0; f < 5; ++f)
-      cudaMemcpyAsync(F[f] + off[i], src[f], sizeof(double) * (size_t)v[i]->N,
-                      cudaMemcpyDeviceToDevice, S->stream);
-  }
-  std::vector<double> dts;
-  for (Req* r : v) dts.push_back(r->q.dt);
-  e = sgn::state_attach(S->run_st, S->stream);
-  const sgn_opts& o = v[0]->q.opts;
-  if (!e) e = sgn_step_rk4(S->run_st, dts.data(), K, &o, S->stream);
-  for (size_t i = 0; i < v.size(); ++i) {
-    double* dst[3] = {v[i]->eta, v[i]->U, v[i]->u};
-    for (int f = 0; f < 3; ++f)
-      cudaMemcpyAsync(dst[f], F[f] + off[i], sizeof(double) * (size_t)v[i]->N,
-                      cudaMemcpyDeviceToDevice, S->stream);
-  }
-  sgn_state_stats stt{};
-  if (!e) e = sgn_state_get_stats(S->run_st, &stt);
-  cudaStreamSynchronize(S->stream);
-  for (Req* r : v) {
-    r->remaining -= K;
-    r->iters += stt.iterations / (long long)v.size();   // shared launches: mean per request
-    if (e || stt.status != SGN_OK) {
-      finish(S, r, e ? e : (sgn_status)stt.status);
-    } else if (r->remaining <= 0) {
-      r->info.iters = (int)r->iters;
-      finish(S, r, SGN_OK);
+    std::vector<double> dts;
+    for (Req* r : v) dts.push_back(r->q.dt);
+    e = sgn::state_attach(S->run_st, J->s);
+    const sgn_opts& o = v[0]->q.opts;
+    if (!e) e = sgn_step_rk4(S->run_st, dts.data(), K, &o, J->s);
+    for (size_t i = 0; i < v.size(); ++i) {
+      double* dst[3] = {v[i]->eta, v[i]->U, v[i]->u};
+      for (int f = 0; f < 3; ++f)
+        cudaMemcpyAsync(dst[f], F[f] + off[i], sizeof(double) * (size_t)v[i]->N,
+                        cudaMemcpyDeviceToDevice, J->s);
     }
+    if (cudaGetLastError() != cudaSuccess && !e) e = SGN_ERR_CUDA;
   }
+  J->err = e;
+  S->batch_busy = true;
+  launch_job(S, J);
 }
 
-void run_single(sgn_server* S, Req* r) {
+// A 2d solve, or the next chunk of a 2d or multistep run, on the request's lane.
+void issue_single(sgn_server* S, Req* r) {
+  Job* J = new Job();
+  J->kind = JOB_SINGLE;
+  J->reqs = {r};
+  J->s = (r->d == 2) ? S->lane_2d : r->own;
+  r->last_issue = now_s();
   sgn_status e = SGN_OK;
-  if (r->q.kind == SGN_REQ_SOLVE) {
-    cudaMemsetAsync(r->u, 0, sizeof(double) * r->d * (size_t)r->N, S->stream);
-    sgn_pcg_info info{};
-    const sgn_opts& o = r->q.opts;
-    e = sgn_pcg(S->ctx, r->lay, r->eta, r->gh, nullptr, r->b, r->u, o.rtol, o.maxit, o.prec,
-                &info, S->stream);
-    r->info = info;
-    finish(S, r, e == SGN_ERR_CUDA ? e : (sgn_status)info.status);
-    return;
-  }
-  const int K = std::min(kChunk, r->remaining);
+  wait_ready(J->s, J->reqs);
   const sgn_opts& o = r->q.opts;
-  const double dt = r->q.dt;
-  switch (r->q.scheme) {
-    case SGN_SCHEME_RK4: e = sgn_step_rk4(r->st, &dt, K, &o, S->stream); break;
-    case SGN_SCHEME_LINIMP: e = sgn_step_linimp(r->st, &dt, K, &o, S->stream); break;
-    default: e = sgn_step_abk(r->st, (int)r->q.scheme, &dt, K, &o, S->stream); break;
+  if (r->q.kind == SGN_REQ_SOLVE) {
+    if ((J->info_at = take_info(S, 1)) < 0) e = SGN_ERR_NOMEM;
+    J->info_n = 1;
+    if (!e) {
+      cudaMemsetAsync(r->u, 0, sizeof(double) * r->d * (size_t)r->N, J->s);
+      e = sgn_pcg_async(S->ctx, r->lay, r->eta, r->gh, r->b, r->u, o.rtol, o.maxit, o.prec,
+                        S->info_dev + J->info_at, J->s);
+      cudaMemcpyAsync(S->info_host + J->info_at, S->info_dev + J->info_at, sizeof(sgn_pcg_info),
+                      cudaMemcpyDeviceToHost, J->s);
+    }
+  } else {
+    const int K = std::min(kChunk, r->remaining);
+    J->K = K;
+    const double dt = r->q.dt;
+    switch (r->q.scheme) {
+      case SGN_SCHEME_RK4: e = sgn_step_rk4(r->st, &dt, K, &o, J->s); break;
+      case SGN_SCHEME_LINIMP: e = sgn_step_linimp(r->st, &dt, K, &o, J->s); break;
+      default: e = sgn_step_abk(r->st, (int)r->q.scheme, &dt, K, &o, J->s); break;
+    }
   }
-  sgn_state_stats stt{};
-  if (!e) e = sgn_state_get_stats(r->st, &stt);
-  r->remaining -= K;
-  if (e || stt.status != SGN_OK) {
-    finish(S, r, e ? e : (sgn_status)stt.status);
-  } else if (r->remaining <= 0) {
-    r->info.iters = (int)stt.iterations;
-    finish(S, r, SGN_OK);
+  if (cudaGetLastError() != cudaSuccess && !e) e = SGN_ERR_CUDA;
+  J->err = e;
+  launch_job(S, J);
+}
+
+// A job whose event has fired (or that failed when issued): update its requests.
+void complete(sgn_server* S, Job* J) {
+  if (J->kind == JOB_SOLVES_1D) {
+    for (size_t i = 0; i < J->reqs.size(); ++i) {
+      Req* r = J->reqs[i];
+      if (J->err) {
+        finish(S, r, J->err);
+        continue;
+      }
+      r->info = S->info_host[J->info_at + i];
+      finish(S, r, (sgn_status)r->info.status);
+    }
+    if (J->lay) {
+      S->reap_lays.push_back(J->lay);
+      S->reap_bytes += 1 << 20;
+    }
+  } else if (J->kind == JOB_RUN_BATCH) {
+    S->batch_busy = false;
+    sgn_state_stats stt{};
+    sgn_status e = J->err;
+    if (!e) e = sgn_state_get_stats(S->run_st, &stt);     // the lane has finished: no wait
+    for (Req* r : J->reqs) {
+      r->busy = false;
+      r->remaining -= J->K;
+      r->iters += stt.iterations / (long long)J->reqs.size();   // shared launches: mean
+      if (e || stt.status != SGN_OK) {
+        finish(S, r, e ? e : (sgn_status)stt.status);
+      } else if (r->remaining <= 0) {
+        r->info.iters = (int)r->iters;
+        finish(S, r, SGN_OK);
+      }
+    }
+  } else {
+    Req* r = J->reqs[0];
+    r->busy = false;
+    if (r->q.kind == SGN_REQ_SOLVE) {
+      if (J->err) {
+        finish(S, r, J->err);
+      } else {
+        r->info = S->info_host[J->info_at];
+        finish(S, r, (sgn_status)r->info.status);
+      }
+    } else {
+      sgn_state_stats stt{};
+      sgn_status e = J->err;
+      if (!e) e = sgn_state_get_stats(r->st, &stt);
+      r->remaining -= J->K;
+      if (e || stt.status != SGN_OK) {
+        finish(S, r, e ? e : (sgn_status)stt.status);
+      } else if (r->remaining <= 0) {
+        r->info.iters = (int)stt.iterations;
+        finish(S, r, SGN_OK);
+      }
+    }
   }
+  if (J->info_at >= 0) give_info(S, J->info_at, J->info_n);
+  if (J->ev) S->events.push_back(J->ev);
+  delete J;
+}
+
+// Completes every job whose event has fired; returns how many.
+int poll_jobs(sgn_server* S) {
+  int n = 0;
+  for (size_t i = 0; i < S->inflight.size();) {
+    Job* J = S->inflight[i];
+    const cudaError_t q = J->err ? cudaSuccess : cudaEventQuery(J->ev);
+    if (q == cudaErrorNotReady) {
+      ++i;
+      continue;
+    }
+    if (q != cudaSuccess) {
+      cudaGetLastError();
+      J->err = SGN_ERR_CUDA;
+    }
+    S->inflight.erase(S->inflight.begin() + i);
+    complete(S, J);
+    ++n;
+  }
+  return n;
 }
 
 void worker_main(sgn_server* S) {
@@ -330,9 +532,7 @@ void worker_main(sgn_server* S) {
     std::vector<Req*> admit_now;
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      S->cv.wait_for(lk, std::chrono::milliseconds(2),
-                     [&] { return S->stop || !S->pending.empty() || !S->active.empty(); });
-      if (S->stop && S->pending.empty() && S->active.empty()) break;
+      if (S->stop && S->pending.empty() && S->active.empty() && S->inflight.empty()) break;
       for (auto it = S->pending.begin(); it != S->pending.end();) {
         Req* r = *it;
         if (S->used + r->footprint <= S->budget) {
@@ -352,44 +552,81 @@ void worker_main(sgn_server* S) {
         finish(S, r, e);
         continue;
       }
+      if (r->d == 1 && r->q.kind == SGN_REQ_RUN && !is_batched_run(r) &&
+          cudaStreamCreateWithPriority(&r->own, cudaStreamNonBlocking, S->prio_lo) !=
+              cudaSuccess) {
+        cudaGetLastError();
+        finish(S, r, SGN_ERR_CUDA);
+        continue;
+      }
       std::lock_guard<std::mutex> lk(S->mu);
       S->active.push_back(r);
     }
+    const int completed = poll_jobs(S);
     std::vector<Req*> act;
     {
       std::lock_guard<std::mutex> lk(S->mu);
+      S->active.erase(std::remove_if(S->active.begin(), S->active.end(),
+                                     [](Req* r) { return r->done; }),
+                      S->active.end());
       act = S->active;
     }
-    if (act.empty()) continue;
+    // issue work for every idle request
     std::vector<Req*> solves1d, runs1d, singles;
     for (Req* r : act) {
-      if (r->done) continue;
+      if (r->done || r->busy) continue;
       if (r->q.kind == SGN_REQ_SOLVE && r->d == 1) solves1d.push_back(r);
       else if (is_batched_run(r)) runs1d.push_back(r);
       else singles.push_back(r);
     }
-    // 1d solves grouped by identical options, batched
+    int issued = 0;
     while (!solves1d.empty()) {
       const sgn_opts o = solves1d[0]->q.opts;
       std::vector<Req*> grp, rest;
       for (Req* r : solves1d)
         (memcmp(&r->q.opts, &o, sizeof(o)) == 0 ? grp : rest).push_back(r);
-      run_solves_1d(S, grp);
+      issue_solves_1d(S, grp);
+      ++issued;
       solves1d.swap(rest);
     }
-    while (!runs1d.empty()) {
+    if (!S->batch_busy && !runs1d.empty()) {
+      // one option set per chunk; the others wait for the batch lane
       const sgn_opts o = runs1d[0]->q.opts;
-      std::vector<Req*> grp, rest;
-      for (Req* r : runs1d) (memcmp(&r->q.opts, &o, sizeof(o)) == 0 ? grp : rest).push_back(r);
-      run_batch_rk4(S, grp);
-      runs1d.swap(rest);
+      std::vector<Req*> grp;
+      for (Req* r : runs1d)
+        if (memcmp(&r->q.opts, &o, sizeof(o)) == 0) grp.push_back(r);
+      issue_run_batch(S, grp);
+      ++issued;
     }
-    for (Req* r : singles) run_single(S, r);
-    std::lock_guard<std::mutex> lk(S->mu);
-    S->active.erase(std::remove_if(S->active.begin(), S->active.end(),
-                                   [](Req* r) { return r->done; }),
-                    S->active.end());
+    // 2d work shares one lane, one job at a time, so two requests' persistent inner solves
+    // never wait on each other's CTAs.  Its turn goes to a waiting 2d solve first (short),
+    // else to the 2d run served longest ago.
+    bool busy2d = false;
+    for (Job* J : S->inflight)
+      if (J->kind == JOB_SINGLE && J->reqs[0]->d == 2) busy2d = true;
+    Req* next2d = nullptr;
+    for (Req* r : singles) {
+      if (r->d == 2) {
+        const bool better = !next2d ||
+                            (r->q.kind == SGN_REQ_SOLVE && next2d->q.kind != SGN_REQ_SOLVE) ||
+                            (r->q.kind == next2d->q.kind && r->last_issue < next2d->last_issue);
+        if (better) next2d = r;
+        continue;
+      }
+      issue_single(S, r);
+      ++issued;
+    }
+    if (next2d && !busy2d) {
+      issue_single(S, next2d);
+      ++issued;
+    }
+    reap(S, S->reap_bytes >= kReapBytes);
+    if (!completed && !issued) {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv.wait_for(lk, std::chrono::microseconds(50), [&] { return S->stop || !S->pending.empty(); });
+    }
   }
+  reap(S, true);
 }
 
 }  // namespace
@@ -413,14 +650,33 @@ extern "C" sgn_status sgn_server_create(sgn_ctx* ctx, double budget_fraction, sg
     return e;
   }
   size_t fr = 0, tot = 0;
-  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking) != cudaSuccess) {
+  bool ok = cudaMemGetInfo(&fr, &tot) == cudaSuccess &&
+            cudaDeviceGetStreamPriorityRange(&S->prio_lo, &S->prio_hi) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking) == cudaSuccess;
+  // priorities (numerically lower is higher): 2d lane highest (its cooperative launches
+  // must get every SM soon), then the 1d solve groups, then the run batch
+  const int mid = S->prio_hi + 1 < S->prio_lo ? S->prio_hi + 1 : S->prio_lo;
+  for (auto& l : S->lane_solve)
+    ok = ok && cudaStreamCreateWithPriority(&l, cudaStreamNonBlocking, mid) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithPriority(&S->lane_2d, cudaStreamNonBlocking, S->prio_hi) ==
+                 cudaSuccess;
+  ok = ok && cudaStreamCreateWithPriority(&S->lane_batch, cudaStreamNonBlocking, S->prio_lo) ==
+                 cudaSuccess;
+  ok = ok && cudaMalloc(&S->info_dev, sizeof(sgn_pcg_info) * kInfoSlots) == cudaSuccess;
+  ok = ok && cudaMallocHost(&S->info_host, sizeof(sgn_pcg_info) * kInfoSlots) == cudaSuccess;
+  if (!ok) {
     cudaGetLastError();
+    for (cudaStream_t t : {S->stream, S->copy, S->lane_solve[0], S->lane_solve[1], S->lane_2d,
+                           S->lane_batch})
+      if (t) cudaStreamDestroy(t);
+    cudaFree(S->info_dev);
+    cudaFreeHost(S->info_host);
     sgn_destroy(S->ctx);
     delete S;
     return SGN_ERR_CUDA;
   }
+  S->info_used.assign(kInfoSlots, 0);
   const double f = budget_fraction > 0.0 ? budget_fraction : 0.8;
   S->budget = (size_t)(f * (double)tot);
   S->worker = std::thread(worker_main, S);
@@ -539,9 +795,12 @@ extern "C" void sgn_server_destroy(sgn_server* S) {
   if (S->run_lay) sgn_layout_destroy(S->run_lay);
   for (auto& kv : S->one1d) sgn_layout_destroy(kv.second);
   cudaFree(S->pk);
-  cudaFree(S->pks);
-  cudaStreamDestroy(S->stream);
-  cudaStreamDestroy(S->copy);
+  for (cudaEvent_t e : S->events) cudaEventDestroy(e);
+  for (cudaStream_t t : {S->stream, S->copy, S->lane_solve[0], S->lane_solve[1], S->lane_2d,
+                         S->lane_batch})
+    cudaStreamDestroy(t);
+  cudaFree(S->info_dev);
+  cudaFreeHost(S->info_host);
   sgn_destroy(S->ctx);
   delete S;
 }

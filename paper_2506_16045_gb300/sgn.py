@@ -85,6 +85,8 @@ SIGNATURES = [
     ("sgn_layout_get_form", C.c_int, [_VP, C.c_int, C.POINTER(C.c_int)]),
     ("sgn_layout_set_forms", C.c_int, [_VP, C.c_int, C.c_int, C.c_int]),
     ("sgn_layout_get_forms", C.c_int, [_VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    ("sgn_layout_set_form2d", C.c_int, [_VP, C.c_int, C.c_int]),
+    ("sgn_layout_get_form2d", C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("sgn_spectral_grad", C.c_int, [_VP, _VP, _DP, _DP, _VP]),
     ("sgn_precond_coeffs", C.c_int, [_VP, _VP, _DP, _DP, C.c_int, C.POINTER(SgnPrecond), _VP]),
     ("sgn_apply_operator", C.c_int, [_VP, _VP, _DP, _DP, _DP, _DP, _VP]),
@@ -122,6 +124,8 @@ SIGNATURES = [
     ("sgn_profile_enable", C.c_int, [_VP, C.c_int]),
     ("sgn_profile_read", C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                                    C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+    ("sgn_profile_inner2d", C.c_int, [_VP, C.c_int, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
 ]
 
 _lib = None
@@ -280,6 +284,27 @@ class Layout:
         self.ctx.check(self.ctx.lib.sgn_layout_get_forms(self.h, log2n, C.byref(a), C.byref(b)),
                        "sgn_layout_get_forms")
         return a.value, b.value
+
+    def set_form2d(self, inner, tile_width=0):
+        """sgn_layout_set_form2d: inner 0 = persistent inner solve, 1 = four kernels per
+        inner iteration; tile_width 0 = automatic, else 1, 2 or 4 columns per tile."""
+        self.ctx.check(self.ctx.lib.sgn_layout_set_form2d(self.h, inner, tile_width),
+                       "sgn_layout_set_form2d")
+
+    def profile_inner2d(self, on):
+        """sgn_profile_inner2d: (ms, launches, inner iterations) recorded since the last
+        call; then recording on or off."""
+        ms, n, it = C.c_double(), C.c_longlong(), C.c_longlong()
+        self.ctx.check(self.ctx.lib.sgn_profile_inner2d(self.h, 1 if on else 0, C.byref(ms),
+                                                        C.byref(n), C.byref(it)),
+                       "sgn_profile_inner2d")
+        return ms.value, n.value, it.value
+
+    def form2d(self):
+        i, t = C.c_int(), C.c_int()
+        self.ctx.check(self.ctx.lib.sgn_layout_get_form2d(self.h, C.byref(i), C.byref(t)),
+                       "sgn_layout_get_form2d")
+        return i.value, t.value
 
     def close(self):
         if self.h:

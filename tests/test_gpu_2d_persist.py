@@ -1,0 +1,128 @@
+"""The persistent 2d inner solve (one cooperative launch per float32 inner PCG) against the
+oracle and against the four-kernel inner iteration it replaces.
+
+Mixed-precision solves are refined in double-float to the requested rtol, so both inner
+forms must reach the same solution within the refinement's tolerance; at sizes the oracle's
+dense solve cannot reach, the right-hand side is b = G u* for a known smooth u* (the oracle's
+matrix-free operator forms it) and the solve must return u*.
+"""
+import numpy as np
+import pytest
+
+from oracle import sgn_oracle as O
+from paper_2506_16045_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2506_16045_gb300 import sgn
+    ctx = sgn.Context(0)
+    yield sgn, ctx
+    ctx.close()
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64).ravel(), device="cuda")
+
+
+def bump_problem(nx, ny, Lx, Ly, H=0.5, R=None, seed=0):
+    """Gaussian-bump depth with a wave on it, and b = G u* for a smooth u* (the oracle's
+    operator)."""
+    X, Y = I.grid_2d(nx, ny, Lx, Ly)
+    R = R if R is not None else min(Lx, Ly) / 8
+    h = I.gaussian_bump_2d(X, Y, Lx, Ly, H, R, Lx / 2, Ly / 2)
+    eta = h + 0.2 * np.exp(np.cos(2 * np.pi * X / Lx) - 1)
+    gh = O.grad(h, (Lx, Ly))
+    us = np.stack([0.3 * np.sin(2 * np.pi * X / Lx) * np.cos(4 * np.pi * Y / Ly),
+                   0.2 * np.cos(2 * np.pi * X / Lx) + 0.1 * np.sin(2 * np.pi * Y / Ly)])
+    grid = O.make_grid(2, nx, Lx, 9.81, ny=ny, Ly=Ly)
+    b = O.apply_G(eta, gh, us, grid)
+    return eta, gh, b, us, grid
+
+
+@pytest.mark.parametrize("n,a,b", [(32, 1.0, 1.0), (64, 1.0, 20.0), (128, 1.0, 1.0)])
+def test_persistent_inner_solve_matches_oracle(S, n, a, b):
+    """Eq:ellipticalbump (§6.3): mixed solve with the persistent inner form at every tile
+    width equals the oracle's float64 solution."""
+    sgn, ctx = S
+    _, _, h, eta, rhs = I.elliptical_bump_2d(n, a, b)
+    gh = O.grad(h, (1.0, 1.0))
+    grid = O.make_grid(2, n, 1.0, 1.0, ny=n, Ly=1.0)
+    ref = O.solve_G(eta, gh, rhs, grid, rtol=1e-14, maxit=4000)[0]
+    lay = sgn.Layout(ctx, [sgn.Grid(2, n, 1.0, ny=n, Ly=1.0)])
+    assert lay.form2d()[0] == 0                     # persistent by default
+    for tw in (1, 2, 4):
+        lay.set_form2d(0, tw)
+        x = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+        info = sgn.pcg(lay, dev(eta), dev(gh), dev(rhs), x, rtol=1e-12, maxit=4000,
+                       prec=sgn.PREC_MIXED)[0]
+        assert info["status"] == 0 and info["ratio"] <= 1e-12
+        assert rel(x.cpu().numpy().reshape(2, n, n), ref) < 1e-9
+
+
+@pytest.mark.parametrize("nx,ny,Lx,Ly", [(8, 8, 1.0, 1.0), (16, 8, 2.0, 1.0), (256, 64, 80.0, 20.0),
+                                         (512, 512, 80.0, 80.0), (1024, 256, 80.0, 20.0),
+                                         (1024, 1024, 80.0, 80.0)])
+def test_persistent_equals_four_kernel_form(S, nx, ny, Lx, Ly):
+    """Both inner forms refine to the same solution (within the tolerance), which is the
+    known u*; the persistent form repeats bitwise (fixed-order reductions)."""
+    sgn, ctx = S
+    eta, gh, b, us, _ = bump_problem(nx, ny, Lx, Ly)
+    lay = sgn.Layout(ctx, [sgn.Grid(2, nx, Lx, ny=ny, Ly=Ly, g=9.81)])
+    out = {}
+    for form in (1, 0, 0):
+        lay.set_form2d(form, 0)
+        x = torch.zeros(2 * nx * ny, dtype=torch.float64, device="cuda")
+        info = sgn.pcg(lay, dev(eta), dev(gh), dev(b), x, rtol=1e-11, maxit=4000,
+                       prec=sgn.PREC_MIXED)[0]
+        assert info["status"] == 0 and info["ratio"] <= 1e-11, (form, info)
+        if form in out:
+            assert torch.equal(out[form][0], x)               # repeatable bitwise
+        out[form] = (x, info)
+    x1, x0 = out[1][0].cpu().numpy(), out[0][0].cpu().numpy()
+    assert rel(x0, x1) < 1e-9
+    assert rel(x0.reshape(2, ny, nx), us) < 1e-8
+    # same method, so the inner iteration counts stay close
+    i0, i1 = out[0][1]["iters"], out[1][1]["iters"]
+    assert abs(i0 - i1) <= max(2, 0.1 * i1), (i0, i1)
+
+
+def test_persistent_inner_solve_edge_cases(S):
+    """A zero right-hand side, an exact warm start, too small an iteration budget and a
+    non-positive depth behave as in the four-kernel form."""
+    sgn, ctx = S
+    n = 32
+    _, _, h, eta, rhs = I.elliptical_bump_2d(n, 1.0, 1.0)
+    gh = O.grad(h, (1.0, 1.0))
+    lay = sgn.Layout(ctx, [sgn.Grid(2, n, 1.0, ny=n, Ly=1.0)])
+    p = sgn.PREC_MIXED
+    x = dev(np.ones(2 * n * n))
+    info = sgn.pcg(lay, dev(eta), dev(gh), dev(np.zeros(2 * n * n)), x, prec=p)[0]
+    assert info["status"] == 0 and info["iters"] == 0 and torch.all(x == 0.0)
+    ref = np.linalg.solve(O.dense_G_2d(eta, gh, 1.0, 1.0), rhs.ravel())
+    x = dev(ref)
+    info = sgn.pcg(lay, dev(eta), dev(gh), dev(rhs), x, rtol=1e-8, prec=p)[0]
+    assert info["status"] == 0 and info["iters"] == 0
+    x = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+    info = sgn.pcg(lay, dev(eta), dev(gh), dev(rhs), x, rtol=1e-14, maxit=2, prec=p,
+                   check=False)[0]
+    assert info["status"] == 5 and info["iters"] <= 3
+    bad = eta.copy()
+    bad[3, 5] = -0.5
+    x = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+    info = sgn.pcg(lay, dev(bad), dev(gh), dev(rhs), x, prec=p, check=False)[0]
+    assert info["status"] == 7
+    with pytest.raises(sgn.SgnError):
+        lay.set_form2d(2, 0)
+    with pytest.raises(sgn.SgnError):
+        lay.set_form2d(0, 3)

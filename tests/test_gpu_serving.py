@@ -184,3 +184,45 @@ def test_admission_budget_and_rejection(S):
     res = wait(srv, tickets)
     assert all(r["status"] == 0 for r in res.values())
     srv.close()
+
+
+def test_short_solve_overlaps_a_long_2d_run(S):
+    """Work of admitted requests overlaps on the device: a short 1d solve submitted while a
+    2d run's chunk of steps is in flight finishes before that chunk, and the 2d run's result
+    is bitwise the run alone."""
+    sgn, ctx = S
+    n2 = 512
+    c2 = I.bump2d_case(n=n2, L=80.0, a=0.2, x0=20.0, H=0.5, R=3.0, dt=0.02)
+    g2 = sgn.Grid(2, n2, 80.0, g=9.81, ny=n2, Ly=80.0)
+    nsteps = 16                                   # one chunk of the server
+    srv = sgn.Server(ctx)
+    st, t_run = srv.submit(sgn.REQ_RUN, g2, dev(c2["eta"]), dev(c2["u"]), dev(c2["h"]),
+                           scheme=sgn.SCHEME_RK4, dt=0.02, nsteps=nsteps, rtol=1e-10,
+                           prec=sgn.PREC_MIXED)
+    assert st == 0
+    time.sleep(0.03)                              # the chunk is on the device by now
+    _, h, eta, b = I.testproblem_1d(1024, 1.0, 1.0)
+    st, t_sol = srv.submit(sgn.REQ_SOLVE, sgn.Grid(1, 1024, 1.0), dev(eta), dev(b), dev(h),
+                           rtol=1e-10, prec=sgn.PREC_MIXED)
+    assert st == 0
+    res = wait(srv, [t_run, t_sol])
+    rr, rs = res[t_run], res[t_sol]
+    assert rr["status"] == 0 and rs["status"] == 0
+    # the solve was admitted and finished while the run's only chunk was still running
+    assert rr["t_admit"] < rs["t_admit"] and rs["t_done"] < rr["t_done"], (rr, rs)
+    # the 2d run equals the same run alone
+    eta_a, u_a, h_a = dev(c2["eta"]), dev(c2["u"]), dev(c2["h"])
+    U_a = torch.zeros(2 * n2 * n2, dtype=torch.float64, device="cuda")
+    gh_a = torch.zeros_like(U_a)
+    lay = sgn.Layout(ctx, [g2])
+    sta = sgn.State(lay, eta_a, U_a, u_a, h_a, gh_a)
+    sta.init()
+    sta.rk4(0.02, nsteps, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
+    torch.cuda.synchronize()
+    eg = sgn.device_array(rr["eta"], n2 * n2).cpu().numpy()
+    ug = sgn.device_array(rr["u"], 2 * n2 * n2).cpu().numpy()
+    assert np.array_equal(eg, eta_a.cpu().numpy()) and np.array_equal(ug, u_a.cpu().numpy())
+    sta.close()
+    for t in (t_run, t_sol):
+        srv.release(t)
+    srv.close()
