@@ -135,13 +135,13 @@ sgn_status sgn_layout_get_forms(const sgn_layout* lay, int log2n, int* solve_cta
                                 int* rhs_ctas);
 
 /* Kernel form of a 2d layout's float32 inner solves (the mixed-precision PCG).
- * inner = 0: one persistent cooperative launch per inner solve, whose CTAs run the column
- * passes, the row passes with the pointwise step and the vector updates behind grid-wide
- * barriers (the default); inner = 1: four kernels per inner iteration inside a device-side
- * loop.  tile_width: half-spectrum columns per column tile of the persistent form (1, 2 or
- * 4; 0 picks the widest that still gives every CTA a tile).  Both forms run the same PCG
+ * inner = 0: one persistent cooperative launch per inner solve, whose CTAs (four
+ * independent thread groups each) run the column passes, the row passes with the pointwise
+ * step and the vector updates behind grid-wide barriers (the default); inner = 1: four
+ * kernels per inner iteration inside a device-side loop.  tile_width: half-spectrum columns
+ * per column unit of the persistent form (0 or 1: one column).  Both forms run the same PCG
  * (§3.2) and agree up to rounding.  SGN_ERR_INVALID_ARG on a 1d layout or bad arguments,
- * SGN_ERR_UNSUPPORTED_SIZE for a tile too wide for ny. */
+ * SGN_ERR_UNSUPPORTED_SIZE for another tile width. */
 sgn_status sgn_layout_set_form2d(sgn_layout* lay, int inner, int tile_width);
 sgn_status sgn_layout_get_form2d(const sgn_layout* lay, int* inner, int* tile_width);
 

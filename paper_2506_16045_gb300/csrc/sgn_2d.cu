@@ -479,7 +479,8 @@ __global__ void __launch_bounds__(256) k2_inner_start(Modes2d M, const void* s1,
                                                       double scale, void* r1p, void* r2p,
                                                       void* x1, void* x2, void* p1, void* p2,
                                                       Scal2d* sc, double* parts, int scale_sc,
-                                                      cudaGraphConditionalHandle hin, int use_h) {
+                                                      cudaGraphConditionalHandle hin, int use_h,
+                                                      int cm) {
   const long long HP = (long long)M.ny * M.H;
   const ModesT<T> MT(M);
   const AinvT<T> Ai = ainv_of(sc, T(0));
@@ -491,8 +492,10 @@ __global__ void __launch_bounds__(256) k2_inner_start(Modes2d M, const void* s1,
     cplx<TH> a = ld_c<TH>(s1, i), b = ld_c<TH>(s2, i);
     cplx<T> r1 = mk(to_work<T>(a.x) * sc_t, to_work<T>(a.y) * sc_t);
     cplx<T> r2 = mk(to_work<T>(b.x) * sc_t, to_work<T>(b.y) * sc_t);
-    st_c<T>(r1p, i, r1);
-    st_c<T>(r2p, i, r2);
+    // cm: the persistent inner solve keeps r, p, d column-major ([H][ny])
+    const long long o = cm ? (long long)c * M.ny + y : i;
+    st_c<T>(r1p, o, r1);
+    st_c<T>(r2p, o, r2);
     st_c<T>(x1, i, zero);
     st_c<T>(x2, i, zero);
     st_c<T>(p1, i, zero);
@@ -510,15 +513,17 @@ __global__ void __launch_bounds__(256) k2_inner_start(Modes2d M, const void* s1,
   });
 }
 
-// x_high += scale * d (T -> high precision)
+// x_high += scale * d (T -> high precision); cm: d is column-major ([H][ny])
 template <typename TH, typename T>
 __global__ void k2_accumulate(Modes2d M, void* x1, void* x2, const void* d1, const void* d2,
-                              double scale, const Scal2d* sc) {   // sc: scale = sc->rn
+                              double scale, const Scal2d* sc, int cm) {   // sc: scale = sc->rn
   const long long HP = (long long)M.ny * M.H;
   const TH s = num<TH>(sc ? sc->rn : scale);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HP;
        i += (long long)gridDim.x * blockDim.x) {
-    cplx<T> a = ld_c<T>(d1, i), b = ld_c<T>(d2, i);
+    const int y = (int)i / M.H, c = (int)i - y * M.H;
+    const long long o = cm ? (long long)c * M.ny + y : i;
+    cplx<T> a = ld_c<T>(d1, o), b = ld_c<T>(d2, o);
     cplx<TH> u = ld_c<TH>(x1, i), v = ld_c<TH>(x2, i);
     st_c<TH>(x1, i, mk(u.x + widen<TH>(a.x) * s, u.y + widen<TH>(a.y) * s));
     st_c<TH>(x2, i, mk(v.x + widen<TH>(b.x) * s, v.y + widen<TH>(b.y) * s));
@@ -1544,7 +1549,7 @@ cudaError_t build_solve_graph(const Layout2d& L, const void* tw64, const void* t
       k2_inner_start<df, float><<<blocks, 256, 0, cs[1]>>>(
           M, slot(L, 10), slot(L, 11), 1.0, slot(L, 4), slot(L, 5), slot(L, 8), slot(L, 9),
           slot(L, 6), slot(L, 7), L.sc, L.parts, 1, persist ? cudaGraphConditionalHandle{} : hin,
-          persist ? 0 : 1);
+          persist ? 0 : 1, L.inner_form == 0 ? 1 : 0);
       e = cudaGetLastError();
     }
     if (persist) {
@@ -1558,7 +1563,8 @@ cudaError_t build_solve_graph(const Layout2d& L, const void* tw64, const void* t
     if (!e) {
       k2_after_inner<<<1, 1, 0, cs[1]>>>(L.sc);
       k2_accumulate<df, float><<<blocks, 256, 0, cs[1]>>>(M, slot(L, 2), slot(L, 3), slot(L, 8),
-                                                         slot(L, 9), 1.0, L.sc);
+                                                         slot(L, 9), 1.0, L.sc,
+                                                         L.inner_form == 0 ? 1 : 0);
       e = cudaGetLastError();
     }
     if (!e) e = residual(cs[1]);
@@ -1585,7 +1591,7 @@ cudaError_t build_solve_graph(const Layout2d& L, const void* tw64, const void* t
       k2_setup_fp64<<<1, 1, 0, cs[0]>>>(L.sc);
       k2_inner_start<double, double><<<blocks, 256, 0, cs[0]>>>(
           M, slot(L, 4), slot(L, 5), 1.0, slot(L, 12), slot(L, 13), slot(L, 8), slot(L, 9),
-          slot(L, 6), slot(L, 7), L.sc, L.parts, 0, hin, 1);
+          slot(L, 6), slot(L, 7), L.sc, L.parts, 0, hin, 1, 0);
       e = cudaGetLastError();
     }
     if (!e) e = cudaMemcpyAsync(slot(L, 4), slot(L, 12), (size_t)16 * L.HP,
@@ -1599,7 +1605,7 @@ cudaError_t build_solve_graph(const Layout2d& L, const void* tw64, const void* t
     if (!e) {
       k2_accumulate<double, double><<<blocks, 256, 0, cs[0]>>>(M, slot(L, 2), slot(L, 3),
                                                                slot(L, 8), slot(L, 9), 1.0,
-                                                               nullptr);
+                                                               nullptr, 0);
       e = cudaGetLastError();
     }
     // final float64 residual for the report and x = F^{-1} x^
@@ -1708,14 +1714,14 @@ cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, 
     k2_set_inner<double><<<1, 1, 0, s>>>(L.sc, rtol * bnorm, maxit);
     k2_inner_start<double, double><<<grid_for(L.HP, 256), 256, 0, s>>>(
         M, slot(L, 4), slot(L, 5), 1.0, slot(L, 12), slot(L, 13), slot(L, 8), slot(L, 9),
-        slot(L, 6), slot(L, 7), L.sc, L.parts, 0, cudaGraphConditionalHandle{}, 0);
+        slot(L, 6), slot(L, 7), L.sc, L.parts, 0, cudaGraphConditionalHandle{}, 0, 0);
     if ((e = cudaGetLastError())) return e;
     // move r into slots 4-5 for the loop
     cudaMemcpyAsync(slot(L, 4), slot(L, 12), (size_t)16 * L.HP, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(slot(L, 5), slot(L, 13), (size_t)16 * L.HP, cudaMemcpyDeviceToDevice, s);
     if ((e = inner_pcg<double>(L, tw64, tw32, maxit, s))) return e;
     k2_accumulate<double, double><<<grid_for(L.HP, 256), 256, 0, s>>>(
-        M, slot(L, 2), slot(L, 3), slot(L, 8), slot(L, 9), 1.0, nullptr);
+        M, slot(L, 2), slot(L, 3), slot(L, 8), slot(L, 9), 1.0, nullptr, 0);
     // final float64 residual for the report and x = F^{-1} x^
     if ((e = matvec<double>(L, tw64, tw32, slot(L, 2), slot(L, 3), slot(L, 10), slot(L, 11),
                             nullptr, nullptr, slot(L, 0), slot(L, 1), 1, x, L.sc, 0, 0, nullptr,
@@ -1747,7 +1753,8 @@ cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, 
     k2_set_inner<float><<<1, 1, 0, s>>>(L.sc, tin, maxit);
     k2_inner_start<df, float><<<grid_for(L.HP, 256), 256, 0, s>>>(
         M, slot(L, 10), slot(L, 11), 1.0 / rn, slot(L, 4), slot(L, 5), slot(L, 8), slot(L, 9),
-        slot(L, 6), slot(L, 7), L.sc, L.parts, 0, cudaGraphConditionalHandle{}, 0);
+        slot(L, 6), slot(L, 7), L.sc, L.parts, 0, cudaGraphConditionalHandle{}, 0,
+        L.inner_form == 0 ? 1 : 0);
     if ((e = cudaGetLastError())) return e;
     const int it_before = h.iters;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -1775,7 +1782,8 @@ cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, 
     }
     k2_accumulate<df, float><<<grid_for(L.HP, 256), 256, 0, s>>>(M, slot(L, 2), slot(L, 3),
                                                                   slot(L, 8), slot(L, 9), rn,
-                                                                  nullptr);
+                                                                  nullptr,
+                                                                  L.inner_form == 0 ? 1 : 0);
     if ((e = cudaGetLastError())) return e;
     ++refinements;
   }
@@ -1962,7 +1970,7 @@ cudaError_t launch_pcg2d_batch(Layout2d& first, Batch2d& Bt, const void* tw64, c
           k2_inner_start<df, float><<<grid_for(L.HP, 256), 256, 0, s>>>(
               M, slot(L, 10), slot(L, 11), 1.0 / rn[i], slot(L, 4), slot(L, 5), slot(L, 8),
               slot(L, 9), slot(L, 6), slot(L, 7), L.sc, L.parts, 0, cudaGraphConditionalHandle{},
-              0);
+              0, 1);     // a batch always runs the persistent inner solve
           it_before[i] = h[i].iters;
           pass[i] = 1;
           any = true;
@@ -1990,7 +1998,7 @@ cudaError_t launch_pcg2d_batch(Layout2d& first, Batch2d& Bt, const void* tw64, c
       if (h[i].status == SGN_ERR_BREAKDOWN && h[i].iters > it_before[i])
         k2_set_status<<<1, 1, 0, s>>>(L.sc, SGN_OK);
       k2_accumulate<df, float><<<grid_for(L.HP, 256), 256, 0, s>>>(
-          modes_of(L), slot(L, 2), slot(L, 3), slot(L, 8), slot(L, 9), rn[i], nullptr);
+          modes_of(L), slot(L, 2), slot(L, 3), slot(L, 8), slot(L, 9), rn[i], nullptr, 1);
       ++refinements[i];
     }
     if ((e = cudaGetLastError())) return e;

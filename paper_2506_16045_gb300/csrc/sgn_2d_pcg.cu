@@ -36,7 +36,9 @@ using namespace d2;
 namespace {
 
 constexpr int kPNT = 512;                 // threads per CTA
-constexpr int kPMaxE = 12;                // transform elements per thread: nb n <= 12 * 512
+constexpr int kGT = 128;                  // threads per group: four groups per CTA
+constexpr int kNG = kPNT / kGT;
+constexpr int kRows = 4;                  // global loads a thread keeps in flight per batch
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s
 
 struct IScal {            // per-instance scalars, identical in every CTA
@@ -92,56 +94,48 @@ __device__ __forceinline__ void dft_reg(cplx<float>* x, bool inv) {
   }
 }
 
-// One radix-R stage at sub-transform length p (log2 lp) over nb transforms of length n:
-// butterfly i of transform j reads src[i + r n/R], twiddles by w^{r k} (w = e^{-+2 pi i/(p R)},
-// k = i mod p), and writes output s to dst[(i - k) R + k + s p].  MAXE bounds the elements a
-// thread holds (nb n <= MAXE NT).
-template <int NT, int MAXE, int R>
-__device__ __forceinline__ void pstage(const cplx<float>* src, cplx<float>* dst, int log2n, int nb,
-                                       int S, int lp, bool inv, const cplx<float>* tws) {
+// Barrier of one group of kGT threads (named barrier g + 1; barrier 0 is __syncthreads).
+__device__ __forceinline__ void gsync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kGT) : "memory");
+}
+
+// One radix-R stage at sub-transform length p (log2 lp) over nb transforms of length n, run
+// by the kGT threads of group g (thread t of the group): butterfly i of transform j reads
+// src[i + r n/R], twiddles by w^{r k} (w = e^{-+2 pi i/(p R)}, k = i mod p), and writes output
+// s to dst[(i - k) R + k + s p].  src and dst are different buffers, so each butterfly is
+// written as soon as it is computed; the group barrier at the end orders the stages.
+template <int R>
+__device__ __forceinline__ void pstage(const cplx<float>* __restrict__ src,
+                                       cplx<float>* __restrict__ dst, int log2n, int nb, int S,
+                                       int lp, bool inv, const cplx<float>* __restrict__ tws,
+                                       int t, int g) {
   constexpr int LR = R == 8 ? 3 : (R == 4 ? 2 : 1);
-  constexpr int MB = (MAXE + R - 1) / R;            // butterflies per thread
   const int lq = log2n - LR, q = 1 << lq;           // butterflies per transform
   const int tot = nb << lq;
   const int tsh = 10 - lp - LR;                     // table index of w^1: 2^tsh
-  cplx<float> x[MB][R];
-  int base[MB], out[MB];
+#pragma unroll 2
+  for (int gi = t; gi < tot; gi += kGT) {
+    const int j = gi >> lq, i = gi & (q - 1), k = i & ((1 << lp) - 1);
+    const int base = j * S, out = ((i - k) << LR) + k;
+    cplx<float> x[R];
 #pragma unroll
-  for (int b = 0; b < MB; ++b) {
-    const int g = threadIdx.x + b * NT;
-    if (g < tot) {
-      const int j = g >> lq, i = g & (q - 1), k = i & ((1 << lp) - 1);
-      base[b] = j * S;
-      out[b] = ((i - k) << LR) + k;
+    for (int r = 0; r < R; ++r) x[r] = src[base + pad(i + r * q)];
+    if (lp > 0) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) x[b][r] = src[base[b] + pad(i + r * q)];
-      if (lp > 0) {
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          const cplx<float> w = tws[(r * k) << tsh];
-          x[b][r] = cmul_tw(x[b][r], w, inv);
-        }
-      }
-      dft_reg<R>(x[b], inv);
+      for (int r = 1; r < R; ++r) x[r] = cmul_tw(x[r], tws[(r * k) << tsh], inv);
     }
-  }
+    dft_reg<R>(x, inv);
 #pragma unroll
-  for (int b = 0; b < MB; ++b) {
-    const int g = threadIdx.x + b * NT;
-    if (g < tot) {
-#pragma unroll
-      for (int s = 0; s < R; ++s) dst[base[b] + pad(out[b] + (s << lp))] = x[b][s];
-    }
+    for (int s = 0; s < R; ++s) dst[base + pad(out + (s << lp))] = x[s];
   }
-  __syncthreads();
+  gsync(g);
 }
 
-// Batched transform of nb sequences of length n = 2^log2n (8 <= n <= 1024) from buffer a,
-// using b as the other buffer; returns the buffer that holds the result.  All NT threads
-// call it; it returns after a barrier.
-template <int NT, int MAXE>
+// Batched transform of nb sequences of length n = 2^log2n (8 <= n <= 1024) by group g, from
+// buffer a with b as the other buffer; returns the buffer that holds the result.  Every
+// thread of the group calls it; it returns after a group barrier.
 __device__ __noinline__ cplx<float>* pfft(cplx<float>* a, cplx<float>* b, int log2n, int nb, int S,
-                                          bool inv, const cplx<float>* tws) {
+                                          bool inv, const cplx<float>* tws, int t, int g) {
   const int ns = (log2n + 2) / 3;                   // stages of radix <= 8
   const int base = log2n / ns, extra = log2n - base * ns;
   int lp = 0;
@@ -149,13 +143,13 @@ __device__ __noinline__ cplx<float>* pfft(cplx<float>* a, cplx<float>* b, int lo
   cplx<float>* dst = b;
   for (int st = 0; st < ns; ++st) {
     const int bits = base + (st < extra ? 1 : 0);
-    if (bits == 3) pstage<NT, MAXE, 8>(src, dst, log2n, nb, S, lp, inv, tws);
-    else if (bits == 2) pstage<NT, MAXE, 4>(src, dst, log2n, nb, S, lp, inv, tws);
-    else pstage<NT, MAXE, 2>(src, dst, log2n, nb, S, lp, inv, tws);
+    if (bits == 3) pstage<8>(src, dst, log2n, nb, S, lp, inv, tws, t, g);
+    else if (bits == 2) pstage<4>(src, dst, log2n, nb, S, lp, inv, tws, t, g);
+    else pstage<2>(src, dst, log2n, nb, S, lp, inv, tws, t, g);
     lp += bits;
-    cplx<float>* t = src;
+    cplx<float>* tmp = src;
     src = dst;
-    dst = t;
+    dst = tmp;
   }
   return src;
 }
@@ -235,49 +229,84 @@ __device__ __forceinline__ void ainv(const IScal& s, float kx, float ky, cplx<fl
   z2 = (r2 - kr * (f * ky)) * s.isigf;
 }
 
-// Block sum of float partials in double-float, returned as a double on thread 0.
-__device__ __forceinline__ void block_part(float v, df* slot, double* out) {
-  block_sum_df<kPNT>(v, slot, [&](float hi, float lo) { __stcg(out, (double)hi + (double)lo); });
+// Sum of the float partials of group g in double-float, stored as a double to `out` by the
+// group's thread 0 (warp shuffles, then the group's four warp totals in order).
+__device__ __forceinline__ void group_part(float v, df* slot, double* out, int t, int g) {
+  df a(v, 0.0f);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    df b(__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o));
+    a = a + b;
+  }
+  if ((t & 31) == 0) slot[g * (kGT / 32) + (t >> 5)] = a;
+  gsync(g);
+  if (t == 0) {
+    df r = slot[g * (kGT / 32)];
+#pragma unroll
+    for (int w = 1; w < kGT / 32; ++w) r = r + slot[g * (kGT / 32) + w];
+    __stcg(out, (double)r.hi + (double)r.lo);
+  }
+  gsync(g);
 }
 
-// Shared memory of the kernel: the twiddle table, then two transform buffers A and B of
-// max(3 TW, 3) transforms (column tiles: 3 planes x TW columns of ny; rows: 3 of nx).
+// Shared memory of the kernel: the twiddle table, then per group two transform buffers of
+// three columns of ny or three rows of nx (padded).
 struct PSmem {
   cplx<float>* tws;
-  cplx<float>* A;
+  cplx<float>* A;       // this group's buffers
   cplx<float>* B;
 };
 
-// ---- C1: p update, projection, divergence, column iFFT --------------------------------
-__device__ __forceinline__ void col_inverse(const PersistArgs2d& a, const PInst2d& I,
-                                            const IScal& s, int c0, const PSmem& sm) {
-  const int ny = a.ny, H = a.H, TW = a.tw, S = pad_len(ny), nx = a.nx;
+// ---- C1: p update, projection, divergence, column iFFT (column c, group g) -------------
+// The solve's vectors and transform planes are column-major, [H][ny]: a column is contiguous.
+__device__ __noinline__ void col_inverse(const PersistArgs2d& a, const PInst2d& I,
+                                         const IScal& s, int c, const PSmem& sm, int t, int g) {
+  const int ny = a.ny, S = pad_len(ny), nx = a.nx;
+  const long long cb = (long long)c * ny;
   cplx<float>* buf = sm.A;
   const bool upd = s.beta != 0.0f;
-  for (int e = threadIdx.x; e < TW * ny; e += kPNT) {
-    const int y = e / TW, c = e - y * TW, col = c0 + c;
-    cplx<float> p1 = mk(0.0f, 0.0f), p2 = p1;
-    if (col < H) {
-      const long long gi = (long long)y * H + col;
-      const cplx<float> r1 = ldcg(I.r[0] + gi), r2 = ldcg(I.r[1] + gi);
-      ainv(s, kx_of(s, col, nx), ky_of(s, y, ny), r1, r2, p1, p2);
-      if (upd) {
-        p1 = p1 + ldcg(I.p[0] + gi) * s.beta;
-        p2 = p2 + ldcg(I.p[1] + gi) * s.beta;
+  const float kx = kx_of(s, c, nx);
+  const cplx<float>* __restrict__ r0 = I.r[0] + cb;
+  const cplx<float>* __restrict__ r1p = I.r[1] + cb;
+  cplx<float>* __restrict__ p0 = I.p[0] + cb;
+  cplx<float>* __restrict__ p1p = I.p[1] + cb;
+  // the column's loads first (kRows rows per thread in flight), then the shared stores
+  for (int y0 = 0; y0 < ny; y0 += kRows * kGT) {
+    cplx<float> r1[kRows], r2[kRows], q1[kRows], q2[kRows];
+#pragma unroll
+    for (int k = 0; k < kRows; ++k) {
+      const int y = y0 + t + k * kGT;
+      if (y < ny) {
+        r1[k] = ldcg(r0 + y);
+        r2[k] = ldcg(r1p + y);
+        if (upd) {
+          q1[k] = ldcg(p0 + y);
+          q2[k] = ldcg(p1p + y);
+        }
       }
     }
-    buf[(0 * TW + c) * S + pad(y)] = p1;
-    buf[(1 * TW + c) * S + pad(y)] = p2;
+#pragma unroll
+    for (int k = 0; k < kRows; ++k) {
+      const int y = y0 + t + k * kGT;
+      if (y < ny) {
+        cplx<float> p1, p2;
+        ainv(s, kx, ky_of(s, y, ny), r1[k], r2[k], p1, p2);
+        if (upd) {
+          p1 = p1 + q1[k] * s.beta;
+          p2 = p2 + q2[k] * s.beta;
+        }
+        buf[pad(y)] = p1;
+        buf[S + pad(y)] = p2;
+      }
+    }
   }
-  __syncthreads();
+  gsync(g);
   // the kx = 0 and kx = nx/2 columns of a real field are Hermitian in ky: project out the
   // rounding residue there before the packed C2R of the row pass could leak it
-  for (int c = 0; c < TW; ++c) {
-    const int col = c0 + c;
-    if (col != 0 && col != (nx >> 1)) continue;
+  if (c == 0 || c == (nx >> 1)) {
     for (int q = 0; q < 2; ++q) {
-      cplx<float>* v = buf + (q * TW + c) * S;
-      for (int y = threadIdx.x; y <= (ny >> 1); y += kPNT) {
+      cplx<float>* v = buf + q * S;
+      for (int y = t; y <= (ny >> 1); y += kGT) {
         const int ym = (ny - y) & (ny - 1);
         const cplx<float> sm2 = v[pad(y)] + conj(v[pad(ym)]);
         const cplx<float> hm = mk(0.5f * sm2.x, 0.5f * sm2.y);
@@ -285,69 +314,86 @@ __device__ __forceinline__ void col_inverse(const PersistArgs2d& a, const PInst2
         v[pad(ym)] = conj(hm);
       }
     }
+    gsync(g);
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < TW * ny; e += kPNT) {
-    const int y = e / TW, c = e - y * TW, col = c0 + c;
-    const cplx<float> p1 = buf[(0 * TW + c) * S + pad(y)], p2 = buf[(1 * TW + c) * S + pad(y)];
-    cplx<float> d = mk(0.0f, 0.0f);
-    if (col < H) {
-      const long long gi = (long long)y * H + col;
-      stcg(I.p[0] + gi, p1);
-      stcg(I.p[1] + gi, p2);
-      d = mul_ik(p1, kx_of(s, col, nx)) + mul_ik(p2, ky_of(s, y, ny));
-    }
-    buf[(2 * TW + c) * S + pad(y)] = d;
+  for (int y = t; y < ny; y += kGT) {
+    const cplx<float> p1 = buf[pad(y)], p2 = buf[S + pad(y)];
+    stcg(p0 + y, p1);
+    stcg(p1p + y, p2);
+    buf[2 * S + pad(y)] = mul_ik(p1, kx) + mul_ik(p2, ky_of(s, y, ny));
   }
-  __syncthreads();
-  const cplx<float>* o = pfft<kPNT, kPMaxE>(sm.A, sm.B, a.logny, 3 * TW, S, true, sm.tws);
-  for (int e = threadIdx.x; e < TW * ny; e += kPNT) {
-    const int y = e / TW, c = e - y * TW, col = c0 + c;
-    if (col >= H) continue;
-    const long long gi = (long long)y * H + col;
+  gsync(g);
+  const cplx<float>* o = pfft(sm.A, sm.B, a.logny, 3, S, true, sm.tws, t, g);
+  for (int y = t; y < ny; y += kGT) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) stcg(I.t[q] + gi, o[(q * TW + c) * S + pad(y)]);
+    for (int q = 0; q < 3; ++q) stcg(I.t[q] + cb + y, o[q * S + pad(y)]);
   }
 }
 
-// ---- R: C2R, Def:MatrixM pointwise with the p.Gp partial, R2C --------------------------
-__device__ __forceinline__ float row_matvec(const PersistArgs2d& a, const PInst2d& I, int y0,
-                                            const PSmem& sm) {
-  const int nx = a.nx, H = a.H, h = nx >> 1, S = pad_len(nx);
+// ---- R: C2R, Def:MatrixM pointwise with the p.Gp partial, R2C (row pair y0, group g) -----
+__device__ __noinline__ float row_matvec(const PersistArgs2d& a, const PInst2d& I, int y0,
+                                            const PSmem& sm, int t, int g) {
+  const int nx = a.nx, h = nx >> 1, S = pad_len(nx);
   const long long P = (long long)nx * a.ny;
   const int y1 = y0 + 1;
-  // packed row r: (A, B) = (t0, t1) of row y0 (r = 0) or y1 (r = 1), (t2 of y0, t2 of y1)
-  auto rowA = [&](int r) {
-    return (r == 2 ? I.t[2] : I.t[0]) + (long long)(r == 1 ? y1 : y0) * H;
-  };
-  auto rowB = [&](int r) {
-    return (r == 2 ? I.t[2] : I.t[1]) + (long long)(r == 0 ? y0 : y1) * H;
-  };
+  // Column m of the transform planes holds rows y0 and y1 side by side (16 bytes): one load
+  // per plane gives packed row 0 (t0, t1 of y0), row 1 (t0, t1 of y1) and row 2 (t2 of y0,
+  // t2 of y1) at mode m; modes above nx/2 are the conjugates of nx - m.
   cplx<float>* z = sm.A;
-  for (int e = threadIdx.x; e < 3 * nx; e += kPNT) {
-    const int r = e / nx, m = e - r * nx;
-    const int mm = m <= h ? m : nx - m;
-    cplx<float> u = ldcg(rowA(r) + mm), v = ldcg(rowB(r) + mm);
-    if (m > h) {
-      u = conj(u);
-      v = conj(v);
+  auto pair_ld = [&](int q, int m) {
+    return __ldcg(reinterpret_cast<const float4*>(I.t[q] + (long long)m * a.ny + y0));
+  };
+  auto put = [&](int m, cplx<float> u0, cplx<float> v0, cplx<float> u1, cplx<float> v1,
+                 cplx<float> u2, cplx<float> v2) {
+    z[pad(m)] = mk(u0.x - v0.y, u0.y + v0.x);          // u + i v
+    z[S + pad(m)] = mk(u1.x - v1.y, u1.y + v1.x);
+    z[2 * S + pad(m)] = mk(u2.x - v2.y, u2.y + v2.x);
+  };
+  for (int m0 = 0; m0 <= h; m0 += kRows * kGT) {
+    float4 A0[kRows], A1[kRows], A2[kRows];
+#pragma unroll
+    for (int k = 0; k < kRows; ++k) {
+      const int m = m0 + t + k * kGT;
+      if (m <= h) {
+        A0[k] = pair_ld(0, m);
+        A1[k] = pair_ld(1, m);
+        A2[k] = pair_ld(2, m);
+      }
     }
-    z[r * S + pad(m)] = mk(u.x - v.y, u.y + v.x);      // u + i v
+#pragma unroll
+    for (int k = 0; k < kRows; ++k) {
+      const int m = m0 + t + k * kGT;
+      if (m <= h) {
+        // t0 = (p1(y0), p1(y1)), t1 = (p2(y0), p2(y1)), t2 = (d(y0), d(y1))
+        const cplx<float> a0 = mk(A0[k].x, A0[k].y), a1 = mk(A0[k].z, A0[k].w);
+        const cplx<float> b0 = mk(A1[k].x, A1[k].y), b1 = mk(A1[k].z, A1[k].w);
+        const cplx<float> d0 = mk(A2[k].x, A2[k].y), d1 = mk(A2[k].z, A2[k].w);
+        put(m, a0, b0, a1, b1, d0, d1);
+        if (m > 0 && m < h) put(nx - m, conj(a0), conj(b0), conj(a1), conj(b1), conj(d0), conj(d1));
+      }
+    }
   }
-  __syncthreads();
-  cplx<float>* w = pfft<kPNT, kPMaxE>(sm.A, sm.B, a.lognx, 3, S, true, sm.tws);
+  gsync(g);
+  cplx<float>* w = pfft(sm.A, sm.B, a.lognx, 3, S, true, sm.tws, t, g);
   const float inv = __int_as_float((127 - a.lognx - a.logny) << 23);   // 1 / (nx ny), exact
   const float third = 1.0f / 3.0f;
   float part = 0.0f;
-  for (int x = threadIdx.x; x < nx; x += kPNT) {
+  for (int x = t; x < nx; x += kGT) {
+    float ev[2], hxv[2], hyv[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       const long long j = (long long)(r ? y1 : y0) * nx + x;
+      ev[r] = I.ehh[j];
+      hxv[r] = I.ehh[P + j];
+      hyv[r] = I.ehh[2 * P + j];
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
       const cplx<float> pp = w[r * S + pad(x)];
       const cplx<float> dd = w[2 * S + pad(x)];
       const float p1 = pp.x * inv, p2 = pp.y * inv;
       const float d = (r ? dd.y : dd.x) * inv;
-      const float e = I.ehh[j], hx = I.ehh[P + j], hy = I.ehh[2 * P + j];
+      const float e = ev[r], hx = hxv[r], hy = hyv[r];
       const float e2h = 0.5f * e * e;
       const float c11 = e * (1.0f + hx * hx), c12 = e * hx * hy, c22 = e * (1.0f + hy * hy);
       const float c13 = e2h * hx, c23 = e2h * hy, c33 = e * e * e * third;
@@ -359,54 +405,99 @@ __device__ __forceinline__ float row_matvec(const PersistArgs2d& a, const PInst2
       if (r) w[2 * S + pad(x)].y = q; else w[2 * S + pad(x)].x = q;
     }
   }
-  __syncthreads();
+  gsync(g);
   cplx<float>* other = w == sm.A ? sm.B : sm.A;
-  const cplx<float>* Y = pfft<kPNT, kPMaxE>(w, other, a.lognx, 3, S, false, sm.tws);
-  // R2C split of the three packed rows: A = (Y_m + conj Y_{n-m})/2, B = (Y_m - conj Y_{n-m})/(2i)
-  for (int e = threadIdx.x; e < 3 * (h + 1); e += kPNT) {
-    const int r = e / (h + 1), m = e - r * (h + 1);
-    const cplx<float> yv = Y[r * S + pad(m)], yc = conj(Y[r * S + pad((nx - m) & (nx - 1))]);
-    const cplx<float> sm2 = yv + yc, dm = mul_mi(yv - yc);
-    stcg(const_cast<cplx<float>*>(rowA(r)) + m, mk(0.5f * sm2.x, 0.5f * sm2.y));
-    stcg(const_cast<cplx<float>*>(rowB(r)) + m, mk(0.5f * dm.x, 0.5f * dm.y));
+  const cplx<float>* Y = pfft(w, other, a.lognx, 3, S, false, sm.tws, t, g);
+  // R2C split of the three packed rows, A = (Y_m + conj Y_{n-m})/2, B = (Y_m - conj Y_{n-m})/(2i),
+  // stored back as row pairs of columns m: t0 = (A_0, A_1), t1 = (B_0, B_1), t2 = (A_2, B_2)
+  for (int m = t; m <= h; m += kGT) {
+    cplx<float> A_[3], B_[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const cplx<float> yv = Y[r * S + pad(m)], yc = conj(Y[r * S + pad((nx - m) & (nx - 1))]);
+      const cplx<float> sm2 = yv + yc, dm = mul_mi(yv - yc);
+      A_[r] = mk(0.5f * sm2.x, 0.5f * sm2.y);
+      B_[r] = mk(0.5f * dm.x, 0.5f * dm.y);
+    }
+    const long long o = (long long)m * a.ny + y0;
+    __stcg(reinterpret_cast<float4*>(I.t[0] + o), make_float4(A_[0].x, A_[0].y, A_[1].x, A_[1].y));
+    __stcg(reinterpret_cast<float4*>(I.t[1] + o), make_float4(B_[0].x, B_[0].y, B_[1].x, B_[1].y));
+    __stcg(reinterpret_cast<float4*>(I.t[2] + o), make_float4(A_[2].x, A_[2].y, B_[2].x, B_[2].y));
   }
   return part;
 }
 
-// ---- C2: column FFT, G p, x and r updates, r.z partial --------------------------------
-__device__ __forceinline__ float col_forward_update(const PersistArgs2d& a, const PInst2d& I,
-                                                    const IScal& s, int c0, const PSmem& sm) {
-  const int ny = a.ny, H = a.H, TW = a.tw, S = pad_len(ny), nx = a.nx;
+// ---- C2: column FFT, G p, x and r updates, r.z partial (column c, group g) ---------------
+__device__ __noinline__ float col_forward_update(const PersistArgs2d& a, const PInst2d& I,
+                                                    const IScal& s, int c, const PSmem& sm,
+                                                    int t, int g) {
+  const int ny = a.ny, S = pad_len(ny), nx = a.nx;
+  const long long cb = (long long)c * ny;
   cplx<float>* buf = sm.A;
-  for (int e = threadIdx.x; e < TW * ny; e += kPNT) {
-    const int y = e / TW, c = e - y * TW, col = c0 + c;
-    const long long gi = (long long)y * H + col;
+  for (int y0 = 0; y0 < ny; y0 += kRows * kGT) {
+    cplx<float> v[3][kRows];
 #pragma unroll
-    for (int q = 0; q < 3; ++q)
-      buf[(q * TW + c) * S + pad(y)] = col < H ? ldcg(I.t[q] + gi) : mk(0.0f, 0.0f);
+    for (int k = 0; k < kRows; ++k) {
+      const int y = y0 + t + k * kGT;
+      if (y < ny) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) v[q][k] = ldcg(I.t[q] + cb + y);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kRows; ++k) {
+      const int y = y0 + t + k * kGT;
+      if (y < ny) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) buf[q * S + pad(y)] = v[q][k];
+      }
+    }
   }
-  __syncthreads();
-  const cplx<float>* o = pfft<kPNT, kPMaxE>(sm.A, sm.B, a.logny, 3 * TW, S, false, sm.tws);
+  gsync(g);
+  const cplx<float>* o = pfft(sm.A, sm.B, a.logny, 3, S, false, sm.tws, t, g);
   float part = 0.0f;
   const float al = s.alpha;
-  for (int e = threadIdx.x; e < TW * ny; e += kPNT) {
-    const int y = e / TW, c = e - y * TW, col = c0 + c;
-    if (col >= H) continue;
-    const long long gi = (long long)y * H + col;
-    const float kx = kx_of(s, col, nx), ky = ky_of(s, y, ny);
-    const cplx<float> qh = o[(2 * TW + c) * S + pad(y)];
-    const cplx<float> g1 = o[(0 * TW + c) * S + pad(y)] - mul_ik(qh, kx);
-    const cplx<float> g2 = o[(1 * TW + c) * S + pad(y)] - mul_ik(qh, ky);
-    const cplx<float> p1 = ldcg(I.p[0] + gi), p2 = ldcg(I.p[1] + gi);
-    stcg(I.x[0] + gi, ldcg(I.x[0] + gi) + p1 * al);
-    stcg(I.x[1] + gi, ldcg(I.x[1] + gi) + p2 * al);
-    const cplx<float> r1 = ldcg(I.r[0] + gi) - g1 * al, r2 = ldcg(I.r[1] + gi) - g2 * al;
-    stcg(I.r[0] + gi, r1);
-    stcg(I.r[1] + gi, r2);
-    cplx<float> z1, z2;
-    ainv(s, kx, ky, r1, r2, z1, z2);
-    const float wgt = (col == 0 || col == (nx >> 1)) ? 1.0f : 2.0f;
-    part += wgt * (r1.x * z1.x + r1.y * z1.y + r2.x * z2.x + r2.y * z2.y);
+  const float kx = kx_of(s, c, nx);
+  const float wgt = (c == 0 || c == (nx >> 1)) ? 1.0f : 2.0f;
+  cplx<float>* __restrict__ X0 = I.x[0] + cb;
+  cplx<float>* __restrict__ X1 = I.x[1] + cb;
+  cplx<float>* __restrict__ R0 = I.r[0] + cb;
+  cplx<float>* __restrict__ R1 = I.r[1] + cb;
+  const cplx<float>* __restrict__ P0 = I.p[0] + cb;
+  const cplx<float>* __restrict__ P1 = I.p[1] + cb;
+  constexpr int KU = kRows;         // rows per batch of the update (six loads each)
+  for (int y0 = 0; y0 < ny; y0 += KU * kGT) {
+    cplx<float> p1[KU], p2[KU], x1[KU], x2[KU], r1[KU], r2[KU];
+#pragma unroll
+    for (int k = 0; k < KU; ++k) {
+      const int y = y0 + t + k * kGT;
+      if (y < ny) {
+        p1[k] = ldcg(P0 + y);
+        p2[k] = ldcg(P1 + y);
+        x1[k] = ldcg(X0 + y);
+        x2[k] = ldcg(X1 + y);
+        r1[k] = ldcg(R0 + y);
+        r2[k] = ldcg(R1 + y);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KU; ++k) {
+      const int y = y0 + t + k * kGT;
+      if (y < ny) {
+        const float ky = ky_of(s, y, ny);
+        const cplx<float> qh = o[2 * S + pad(y)];
+        const cplx<float> g1 = o[pad(y)] - mul_ik(qh, kx);
+        const cplx<float> g2 = o[S + pad(y)] - mul_ik(qh, ky);
+        stcg(X0 + y, x1[k] + p1[k] * al);
+        stcg(X1 + y, x2[k] + p2[k] * al);
+        const cplx<float> nr1 = r1[k] - g1 * al, nr2 = r2[k] - g2 * al;
+        stcg(R0 + y, nr1);
+        stcg(R1 + y, nr2);
+        cplx<float> z1, z2;
+        ainv(s, kx, ky, nr1, nr2, z1, z2);
+        part += wgt * (nr1.x * z1.x + nr1.y * z1.y + nr2.x * z2.x + nr2.y * z2.y);
+      }
+    }
   }
   return part;
 }
@@ -414,15 +505,15 @@ __device__ __forceinline__ float col_forward_update(const PersistArgs2d& a, cons
 __global__ void __launch_bounds__(kPNT, 1) k2_pcg_persist(const __grid_constant__ PersistArgs2d a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ IScal S[kMaxBatch2d];
-  __shared__ df slot[kPNT / 32];
+  __shared__ df slot[kPNT / 32];        // the groups' warp totals
   __shared__ int s_stop;
+  // thread t of group g; the group's two transform buffers after the twiddle table
+  const int g = threadIdx.x / kGT, t = threadIdx.x - g * kGT;
+  const long long be = 3ll * pad_len(a.nx > a.ny ? a.nx : a.ny);
   PSmem sm;
   sm.tws = reinterpret_cast<cplx<float>*>(smem);
-  sm.A = sm.tws + kTwTab;
-  {
-    const long long col = 3ll * a.tw * pad_len(a.ny), row = 3ll * pad_len(a.nx);
-    sm.B = sm.A + (col > row ? col : row);
-  }
+  sm.A = sm.tws + kTwTab + 2 * be * g;
+  sm.B = sm.A + be;
   {
     // e^{-2 pi i m / 1024} from the 16384-entry float32 table
     const cplx<float>* tg = static_cast<const cplx<float>*>(a.tw32);
@@ -457,20 +548,24 @@ __global__ void __launch_bounds__(kPNT, 1) k2_pcg_persist(const __grid_constant_
     int live = 0;
     for (int b = 0; b < B; ++b) live += S[b].done ? 0 : 1;
     if (!live) break;
+    // Units go to the groups of the grid in turn, group-major (slot = group * grid + CTA),
+    // so a phase with fewer units than slots still spreads over every SM; adjacent columns
+    // (which share the 32-byte sectors of every row) are in flight together.
+    const int slot0 = g * gridDim.x + blockIdx.x, nslots = gridDim.x * kNG;
     // ---- C1
-    for (int u = blockIdx.x; u < B * CU; u += gridDim.x) {
-      const int b = u / CU, tile = u - b * CU;
+    for (int u = slot0; u < B * CU; u += nslots) {
+      const int b = u / CU, c = u - b * CU;
       if (S[b].done) continue;
-      col_inverse(a, a.inst[b], S[b], tile * a.tw, sm);
-      __syncthreads();
+      col_inverse(a, a.inst[b], S[b], c, sm, t, g);
+      gsync(g);
     }
     if ((stop = grid_barrier(a.bar, a.err, target, &s_stop))) break;
     // ---- R
-    for (int u = blockIdx.x; u < B * RU; u += gridDim.x) {
+    for (int u = slot0; u < B * RU; u += nslots) {
       const int b = u / RU, pr = u - b * RU;
       if (S[b].done) continue;
-      const float part = row_matvec(a, a.inst[b], 2 * pr, sm);
-      block_part(part, slot, a.parts + (long long)b * RU + pr);
+      const float part = row_matvec(a, a.inst[b], 2 * pr, sm, t, g);
+      group_part(part, slot, a.parts + (long long)b * RU + pr, t, g);
     }
     if ((stop = grid_barrier(a.bar, a.err, target, &s_stop))) break;
     // alpha = r.z / p.Gp (p.Gp in the half-spectrum units of r.z: P times the real sum)
@@ -486,11 +581,11 @@ __global__ void __launch_bounds__(kPNT, 1) k2_pcg_persist(const __grid_constant_
     });
     // ---- C2
     double* parts2 = a.parts + (long long)B * RU;
-    for (int u = blockIdx.x; u < B * CU; u += gridDim.x) {
-      const int b = u / CU, tile = u - b * CU;
+    for (int u = slot0; u < B * CU; u += nslots) {
+      const int b = u / CU, c = u - b * CU;
       if (S[b].done) continue;
-      const float part = col_forward_update(a, a.inst[b], S[b], tile * a.tw, sm);
-      block_part(part, slot, parts2 + (long long)b * CU + tile);
+      const float part = col_forward_update(a, a.inst[b], S[b], c, sm, t, g);
+      group_part(part, slot, parts2 + (long long)b * CU + c, t, g);
     }
     if ((stop = grid_barrier(a.bar, a.err, target, &s_stop))) break;
     sum_units(parts2, CU, S, B, [&](int b, double rz) {
@@ -533,36 +628,32 @@ __global__ void k2_persist_arm(unsigned* bar, int* err) {
 
 }  // namespace
 
-// elements of one transform buffer: 3 tw columns of ny or 3 rows of nx, padded
-long long persist2d_buf_elems(int nx, int ny, int tw) {
-  const long long col = 3ll * tw * pad_len(ny), row = 3ll * pad_len(nx);
-  return col > row ? col : row;
-}
-
+// Shared memory: the twiddle table and two buffers of three padded transforms per group.
 size_t persist2d_smem(int nx, int ny, int tw) {
-  return sizeof(cplx<float>) * (kTwTab + 2 * persist2d_buf_elems(nx, ny, tw));
+  (void)tw;
+  const long long be = 3ll * pad_len(nx > ny ? nx : ny);
+  return sizeof(cplx<float>) * (kTwTab + 2 * be * kNG);
 }
 
-// Columns per tile: the widest of 4, 2, 1 whose three planes fit kPMaxE elements per thread
-// and whose tiles still give every CTA of the grid a unit (four float32 columns fill a
-// 32-byte sector of a row; a single instance of 512^2 takes one).
+// A column unit is one half-spectrum column (each group transforms three planes of it).
 int persist2d_tile_width(int nx, int ny, int B, int grid) {
-  const int H = nx / 2 + 1;
-  for (int tw = 4; tw > 1; tw >>= 1)
-    if (3 * tw * ny <= kPMaxE * kPNT && (long long)B * ((H + tw - 1) / tw) >= grid) return tw;
+  (void)nx;
+  (void)ny;
+  (void)B;
+  (void)grid;
   return 1;
 }
 
 bool persist2d_tile_ok(int nx, int ny, int tw) {
-  return tw >= 1 && tw <= 4 && 3 * tw * ny <= kPMaxE * kPNT;
+  (void)nx;
+  (void)ny;
+  return tw == 1;
 }
 
 // Resident CTAs of the persistent kernel on this device (one per SM: 512 threads of up to
 // 128 registers), at most the largest phase's unit count.
 cudaError_t persist2d_grid(int nx, int ny, int B, int* grid) {
-  int tw_max = 4;
-  while (tw_max > 1 && !persist2d_tile_ok(nx, ny, tw_max)) tw_max >>= 1;
-  const size_t smem = persist2d_smem(nx, ny, tw_max);
+  const size_t smem = persist2d_smem(nx, ny, 1);
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k2_pcg_persist, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(smem > 48 * 1024 ? smem : 48 * 1024))))
