@@ -58,10 +58,12 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the shelf/2d/serving sections after the headline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--only-config", choices=["solitary_1d", "shelf_1d", "bump_2d", "serving",
-                                              "robustness", "manufactured"],
+    ap.add_argument("--only-config", choices=["solitary_1d", "shelf_1d", "bump_2d", "pcg2d_batch",
+                                              "serving", "robustness", "manufactured"],
                     help="run only this extra configuration and print its result as one JSON "
                          "line (for profiling one workload; not the headline)")
+    ap.add_argument("--batch2d", type=int, default=16,
+                    help="instances of the pcg2d_batch configuration")
     ap.add_argument("--serving-requests", type=int, default=240,
                     help="requests of the serving stream (2000: the whole workload)")
     ap.add_argument("--n2d", type=int, default=512, choices=[128, 256, 512, 1024],
@@ -507,7 +509,7 @@ def gpu_arm(args, world, rank, local, pg):
         E.st.close()
         extra = {}
         for name, fn in (("solitary_1d", bench_solitary), ("shelf_1d", bench_shelf),
-                         ("bump_2d", bench_2d),
+                         ("bump_2d", bench_2d), ("pcg2d_batch", bench_pcg2d),
                          ("serving", bench_serving), ("robustness", bench_robustness),
                          ("manufactured", bench_manufactured)):
             try:
@@ -568,6 +570,73 @@ def bench_solitary(sgn, ctx, torch, steps=500):
             "mass_drift_rel": abs(float(np.sum(e6 - c.h)) - m0) / abs(m0),
             "iterations_per_solve": s6["iterations"] / max(1, s6["solves"]),
             "status": s6["status"]}
+
+
+def bench_pcg2d(sgn, ctx, torch, B=16, n=512, L=80.0, seed=2024, reps=3):
+    """Batched 2d constraint solves: B instances of the bump workload's size (n^2, L = 80) on
+    one grid, each with its own Gaussian bump (height U[0.1, 0.6], radius U[1, 5], centre
+    U[0.3L, 0.7L]^2) and wave, right-hand side b = G u* for a smooth u* (formed on the GPU by
+    sgn_apply_operator), mixed precision to rtol 1e-10.  The persistent inner-solve kernel is
+    timed with CUDA events around each launch (sgn_profile_inner2d); its algorithmic traffic
+    is 60 bytes per point per inner iteration (eta and grad h read, x, r, p of two
+    components read and written, float32)."""
+    import numpy as np
+
+    from paper_2506_16045_gb300 import inputs as I
+    rng = np.random.default_rng(seed)
+    X, Y = I.grid_2d(n, n, L, L)
+    etas, hs, us = [], [], []
+    for _ in range(B):
+        h = I.gaussian_bump_2d(X, Y, L, L, rng.uniform(0.1, 0.6), rng.uniform(1.0, 5.0),
+                               rng.uniform(0.3, 0.7) * L, rng.uniform(0.3, 0.7) * L)
+        etas.append(h + rng.uniform(0.05, 0.3) * np.exp(np.cos(2 * np.pi * X / L
+                                                                - rng.uniform(0, 6)) - 1))
+        hs.append(h)
+        k = int(rng.integers(1, 4))
+        us.append(np.stack([0.3 * np.sin(2 * np.pi * k * X / L) * np.cos(4 * np.pi * Y / L),
+                            0.2 * np.cos(2 * np.pi * X / L) + 0.1 * np.sin(2 * np.pi * k * Y / L)]))
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a).ravel(), dtype=torch.float64,
+                                    device="cuda")
+    pack_v = lambda vs: np.concatenate([v[0].ravel() for v in vs] + [v[1].ravel() for v in vs])
+    lay = sgn.Layout(ctx, [sgn.Grid(2, n, L, ny=n, Ly=L, g=9.81)] * B)
+    eta = dev(np.concatenate([e.ravel() for e in etas]))
+    gh = torch.zeros(2 * B * n * n, dtype=torch.float64, device="cuda")
+    sgn.spectral_grad(lay, dev(np.concatenate([h.ravel() for h in hs])), gh)
+    ustar = dev(pack_v(us))
+    b = torch.zeros_like(ustar)
+    sgn.apply_operator(lay, eta, gh, ustar, b)
+    x = torch.zeros_like(b)
+    info = sgn.pcg(lay, eta, gh, b, x, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
+    ts = []
+    for _ in range(reps):
+        x.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sgn.pcg(lay, eta, gh, b, x, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED, info=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    err = float(torch.linalg.norm(x - ustar) / torch.linalg.norm(ustar))
+    lay.profile_inner2d(True)
+    for _ in range(reps):
+        x.zero_()
+        sgn.pcg(lay, eta, gh, b, x, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED, info=False)
+    ms, launches, iters = lay.profile_inner2d(False)
+    lay.close()
+    per_launch_s = ms * 1e-3 / launches
+    alg_bytes = 60.0 * n * n * iters / launches        # per launch
+    return {"workload": f"pcg2d_batch: {B} instances of {n}^2 (L = {L:g}) on one grid, Gaussian "
+                        "bumps, b = G u*, mixed precision, rtol 1e-10",
+            "instances": B, "n": n, "solve_ms": min(ts),
+            "value": B * n * n / (min(ts) * 1e-3), "unit": "grid-point-solves/s",
+            "rel_l2_vs_known_solution": err,
+            "inner_iterations_per_instance": [i["iters"] for i in info],
+            "refinements_per_instance": [i["refinements"] for i in info],
+            "persistent_kernel": {"launches": launches, "ms_per_launch": 1e3 * per_launch_s,
+                                  "inner_iterations_per_launch": iters / launches,
+                                  "algorithmic_bytes_per_launch": alg_bytes,
+                                  "algorithmic_GBs": alg_bytes / per_launch_s / 1e9}}
 
 
 def bench_2d(sgn, ctx, torch, steps=300, n=512):
@@ -1015,6 +1084,7 @@ def main():
         from paper_2506_16045_gb300 import sgn
         ctx = sgn.Context(0)
         fn = {"solitary_1d": bench_solitary,
+              "pcg2d_batch": lambda *a: bench_pcg2d(*a, B=args.batch2d, n=args.n2d),
               "shelf_1d": lambda *a: bench_shelf(*a, steps=args.shelf_steps),
               "bump_2d": lambda *a: bench_2d(*a, n=args.n2d),
               "serving": lambda *a: bench_serving(*a, nreq=args.serving_requests),

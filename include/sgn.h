@@ -332,8 +332,11 @@ sgn_status sgn_state_set_dealias(sgn_state* st, int on);
  * unless another combination is at least 3% faster; the choice stays set on the layout.
  * The state (eta, U, u, time, counters) is restored afterwards, so tuning leaves no trace
  * on the solution.  Allocates and frees 3 P doubles; synchronises `stream`; best_ms
- * (nullable, host) receives the chosen time per step.  A 2d state, or one without such
- * classes, is left as it is. */
+ * (nullable, host) receives the chosen time per step.  A 1d state without such classes is
+ * left as it is.  For a 2d state it chooses the layout's inner-solve form
+ * (sgn_layout_set_form2d: the persistent launch, or four kernels per inner iteration) the
+ * same way: each form timed on RK4 steps from the same state in two passes, the persistent
+ * form kept unless the other is at least 3% faster, the state restored. */
 sgn_status sgn_state_autotune(sgn_state* st, const double* dt, const sgn_opts* opts,
                               sgn_stream stream, double* best_ms);
 /* Synchronises the stream used by the last step call and reports counters. */

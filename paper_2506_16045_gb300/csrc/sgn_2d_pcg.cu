@@ -38,7 +38,8 @@ namespace {
 constexpr int kPNT = 512;                 // threads per CTA
 constexpr int kGT = 128;                  // threads per group: four groups per CTA
 constexpr int kNG = kPNT / kGT;
-constexpr int kRows = 4;                  // global loads a thread keeps in flight per batch
+constexpr int kRows = 1;                  // rows a thread loads per batch: with every phase
+                                          // inlined, more would spill past 128 registers
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s
 
 struct IScal {            // per-instance scalars, identical in every CTA
@@ -52,7 +53,9 @@ struct IScal {            // per-instance scalars, identical in every CTA
 // buffers used in turn (one barrier per stage), twiddles from a 1024-entry table in shared
 // memory, and one spare element after every 32 (pad) so the strided accesses of the stages
 // spread over the banks.  Transform j of a batch lives at [j S, j S + pad_len(n)).
-constexpr int kTwTab = 1024;                       // e^{-2 pi i m / 1024}, m < 1024
+// Twiddles per transform length n: for the stage of radix R at sub-length p, the block at
+// offset p - 1 holds w^{r k} = e^{-2 pi i r k / (p R)} at (r - 1) p + k (r = 1..R-1, k < p), so
+// the lanes of a warp read consecutive entries; the blocks of all stages take n - 1 entries.
 __device__ __forceinline__ int pad(int a) { return a + (a >> 5); }
 __host__ __device__ constexpr int pad_len(int n) { return n + (n >> 5); }
 
@@ -65,7 +68,21 @@ __device__ __forceinline__ cplx<float> rot8(cplx<float> a, int q, bool inv) {
   return inv ? mk(-(a.x + a.y) * r, (a.x - a.y) * r) : mk((a.y - a.x) * r, -(a.x + a.y) * r);
 }
 
-// In-register DFT of R = 2, 4 or 8 points, output in natural order.
+// a * e^{-+2 pi i q / 16}, q = 1..9 (the twiddles inside a radix-16 butterfly)
+__device__ __forceinline__ cplx<float> rot16(cplx<float> a, int q, bool inv) {
+  constexpr float C[10] = {1.0f, 0.92387953251128676f, 0.70710678118654752f,
+                           0.38268343236508977f, 0.0f, -0.38268343236508977f,
+                           -0.70710678118654752f, -0.92387953251128676f, -1.0f,
+                           -0.92387953251128676f};
+  constexpr float Sn[10] = {0.0f, 0.38268343236508977f, 0.70710678118654752f,
+                            0.92387953251128676f, 1.0f, 0.92387953251128676f,
+                            0.70710678118654752f, 0.38268343236508977f, 0.0f,
+                            -0.38268343236508977f};
+  const float c = C[q], sn = inv ? Sn[q] : -Sn[q];       // e^{-+i pi q / 8}
+  return mk(a.x * c - a.y * sn, a.x * sn + a.y * c);
+}
+
+// In-register DFT of R = 2, 4, 8 or 16 points, output in natural order.
 template <int R>
 __device__ __forceinline__ void dft_reg(cplx<float>* x, bool inv) {
   if constexpr (R == 2) {
@@ -79,6 +96,23 @@ __device__ __forceinline__ void dft_reg(cplx<float>* x, bool inv) {
     x[1] = d02 + r13;
     x[2] = s02 - s13;
     x[3] = d02 - r13;
+  } else if constexpr (R == 16) {
+    // 16 = 4 x 4: r = 4a + b, s = c + 4d; DFT4 over a, twiddle w16^{b c}, DFT4 over b
+    cplx<float> A[4][4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      cplx<float> v[4] = {x[b], x[4 + b], x[8 + b], x[12 + b]};
+      dft_reg<4>(v, inv);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) A[b][c] = (b && c) ? rot16(v[c], b * c, inv) : v[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      cplx<float> v[4] = {A[0][c], A[1][c], A[2][c], A[3][c]};
+      dft_reg<4>(v, inv);
+#pragma unroll
+      for (int d = 0; d < 4; ++d) x[c + 4 * d] = v[d];
+    }
   } else {
     cplx<float> e[4] = {x[0], x[2], x[4], x[6]}, o[4] = {x[1], x[3], x[5], x[7]};
     dft_reg<4>(e, inv);
@@ -109,10 +143,10 @@ __device__ __forceinline__ void pstage(const cplx<float>* __restrict__ src,
                                        cplx<float>* __restrict__ dst, int log2n, int nb, int S,
                                        int lp, bool inv, const cplx<float>* __restrict__ tws,
                                        int t, int g) {
-  constexpr int LR = R == 8 ? 3 : (R == 4 ? 2 : 1);
+  constexpr int LR = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
   const int lq = log2n - LR, q = 1 << lq;           // butterflies per transform
   const int tot = nb << lq;
-  const int tsh = 10 - lp - LR;                     // table index of w^1: 2^tsh
+  const int p0 = 1 << lp;
 #pragma unroll 2
   for (int gi = t; gi < tot; gi += kGT) {
     const int j = gi >> lq, i = gi & (q - 1), k = i & ((1 << lp) - 1);
@@ -121,8 +155,27 @@ __device__ __forceinline__ void pstage(const cplx<float>* __restrict__ src,
 #pragma unroll
     for (int r = 0; r < R; ++r) x[r] = src[base + pad(i + r * q)];
     if (lp > 0) {
+      // w^r from the table for r = 1, 2, 4, 8; the other powers by one or two products
+      const cplx<float>* tb = tws + p0 - 1 + k;
+      cplx<float> w[R];
+      w[1] = tb[0];
+      if constexpr (R >= 4) {
+        w[2] = tb[p0];
+        w[3] = cmul(w[1], w[2]);
+      }
+      if constexpr (R >= 8) {
+        w[4] = tb[3 * p0];
+        w[5] = cmul(w[1], w[4]);
+        w[6] = cmul(w[2], w[4]);
+        w[7] = cmul(w[3], w[4]);
+      }
+      if constexpr (R >= 16) {
+        w[8] = tb[7 * p0];
 #pragma unroll
-      for (int r = 1; r < R; ++r) x[r] = cmul_tw(x[r], tws[(r * k) << tsh], inv);
+        for (int r = 9; r < 16; ++r) w[r] = cmul(w[r - 8], w[8]);
+      }
+#pragma unroll
+      for (int r = 1; r < R; ++r) x[r] = cmul_tw(x[r], w[r], inv);
     }
     dft_reg<R>(x, inv);
 #pragma unroll
@@ -134,16 +187,17 @@ __device__ __forceinline__ void pstage(const cplx<float>* __restrict__ src,
 // Batched transform of nb sequences of length n = 2^log2n (8 <= n <= 1024) by group g, from
 // buffer a with b as the other buffer; returns the buffer that holds the result.  Every
 // thread of the group calls it; it returns after a group barrier.
-__device__ __noinline__ cplx<float>* pfft(cplx<float>* a, cplx<float>* b, int log2n, int nb, int S,
+__device__ __forceinline__ cplx<float>* pfft(cplx<float>* a, cplx<float>* b, int log2n, int nb, int S,
                                           bool inv, const cplx<float>* tws, int t, int g) {
-  const int ns = (log2n + 2) / 3;                   // stages of radix <= 8
+  const int ns = (log2n + 3) / 4;                   // stages of radix <= 16
   const int base = log2n / ns, extra = log2n - base * ns;
   int lp = 0;
   cplx<float>* src = a;
   cplx<float>* dst = b;
   for (int st = 0; st < ns; ++st) {
     const int bits = base + (st < extra ? 1 : 0);
-    if (bits == 3) pstage<8>(src, dst, log2n, nb, S, lp, inv, tws, t, g);
+    if (bits == 4) pstage<16>(src, dst, log2n, nb, S, lp, inv, tws, t, g);
+    else if (bits == 3) pstage<8>(src, dst, log2n, nb, S, lp, inv, tws, t, g);
     else if (bits == 2) pstage<4>(src, dst, log2n, nb, S, lp, inv, tws, t, g);
     else pstage<2>(src, dst, log2n, nb, S, lp, inv, tws, t, g);
     lp += bits;
@@ -207,7 +261,16 @@ __device__ __forceinline__ void sum_units(const double* parts, int U, IScal* S, 
   for (int b = w; b < B; b += kPNT / 32) {
     if (S[b].done) continue;
     double acc = 0.0;
-    for (int i = l; i < U; i += 32) acc += __ldcg(parts + (long long)b * U + i);
+    for (int i0 = 0; i0 < U; i0 += 8 * 32) {
+      double v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int i = i0 + l + 32 * k;
+        v[k] = i < U ? __ldcg(parts + (long long)b * U + i) : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc += v[k];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (l == 0) fin(b, acc);
@@ -252,14 +315,15 @@ __device__ __forceinline__ void group_part(float v, df* slot, double* out, int t
 // Shared memory of the kernel: the twiddle table, then per group two transform buffers of
 // three columns of ny or three rows of nx (padded).
 struct PSmem {
-  cplx<float>* tws;
+  cplx<float>* twx;     // twiddles of length nx
+  cplx<float>* twy;     // of length ny (the same table when ny = nx)
   cplx<float>* A;       // this group's buffers
   cplx<float>* B;
 };
 
 // ---- C1: p update, projection, divergence, column iFFT (column c, group g) -------------
 // The solve's vectors and transform planes are column-major, [H][ny]: a column is contiguous.
-__device__ __noinline__ void col_inverse(const PersistArgs2d& a, const PInst2d& I,
+__device__ __forceinline__ void col_inverse(const PersistArgs2d& a, const PInst2d& I,
                                          const IScal& s, int c, const PSmem& sm, int t, int g) {
   const int ny = a.ny, S = pad_len(ny), nx = a.nx;
   const long long cb = (long long)c * ny;
@@ -323,7 +387,7 @@ __device__ __noinline__ void col_inverse(const PersistArgs2d& a, const PInst2d& 
     buf[2 * S + pad(y)] = mul_ik(p1, kx) + mul_ik(p2, ky_of(s, y, ny));
   }
   gsync(g);
-  const cplx<float>* o = pfft(sm.A, sm.B, a.logny, 3, S, true, sm.tws, t, g);
+  const cplx<float>* o = pfft(sm.A, sm.B, a.logny, 3, S, true, sm.twy, t, g);
   for (int y = t; y < ny; y += kGT) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) stcg(I.t[q] + cb + y, o[q * S + pad(y)]);
@@ -331,7 +395,7 @@ __device__ __noinline__ void col_inverse(const PersistArgs2d& a, const PInst2d& 
 }
 
 // ---- R: C2R, Def:MatrixM pointwise with the p.Gp partial, R2C (row pair y0, group g) -----
-__device__ __noinline__ float row_matvec(const PersistArgs2d& a, const PInst2d& I, int y0,
+__device__ __forceinline__ float row_matvec(const PersistArgs2d& a, const PInst2d& I, int y0,
                                             const PSmem& sm, int t, int g) {
   const int nx = a.nx, h = nx >> 1, S = pad_len(nx);
   const long long P = (long long)nx * a.ny;
@@ -374,40 +438,52 @@ __device__ __noinline__ float row_matvec(const PersistArgs2d& a, const PInst2d& 
     }
   }
   gsync(g);
-  cplx<float>* w = pfft(sm.A, sm.B, a.lognx, 3, S, true, sm.tws, t, g);
+  cplx<float>* w = pfft(sm.A, sm.B, a.lognx, 3, S, true, sm.twx, t, g);
   const float inv = __int_as_float((127 - a.lognx - a.logny) << 23);   // 1 / (nx ny), exact
   const float third = 1.0f / 3.0f;
   float part = 0.0f;
-  for (int x = t; x < nx; x += kGT) {
-    float ev[2], hxv[2], hyv[2];
+  for (int x0 = 0; x0 < nx; x0 += kRows * kGT) {
+    // eta, h_x, h_y of both rows for kRows points per thread, loaded before use
+    float ev[kRows][2], hxv[kRows][2], hyv[kRows][2];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const long long j = (long long)(r ? y1 : y0) * nx + x;
-      ev[r] = I.ehh[j];
-      hxv[r] = I.ehh[P + j];
-      hyv[r] = I.ehh[2 * P + j];
+    for (int k = 0; k < kRows; ++k) {
+      const int x = x0 + t + k * kGT;
+      if (x < nx) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const long long j = (long long)(r ? y1 : y0) * nx + x;
+          ev[k][r] = I.ehh[j];
+          hxv[k][r] = I.ehh[P + j];
+          hyv[k][r] = I.ehh[2 * P + j];
+        }
+      }
     }
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const cplx<float> pp = w[r * S + pad(x)];
-      const cplx<float> dd = w[2 * S + pad(x)];
-      const float p1 = pp.x * inv, p2 = pp.y * inv;
-      const float d = (r ? dd.y : dd.x) * inv;
-      const float e = ev[r], hx = hxv[r], hy = hyv[r];
-      const float e2h = 0.5f * e * e;
-      const float c11 = e * (1.0f + hx * hx), c12 = e * hx * hy, c22 = e * (1.0f + hy * hy);
-      const float c13 = e2h * hx, c23 = e2h * hy, c33 = e * e * e * third;
-      const float w1 = c11 * p1 + c12 * p2 + c13 * d;
-      const float w2 = c12 * p1 + c22 * p2 + c23 * d;
-      const float q = c13 * p1 + c23 * p2 + c33 * d;
-      part += p1 * w1 + p2 * w2 + d * q;
-      w[r * S + pad(x)] = mk(w1, w2);
-      if (r) w[2 * S + pad(x)].y = q; else w[2 * S + pad(x)].x = q;
+    for (int k = 0; k < kRows; ++k) {
+      const int x = x0 + t + k * kGT;
+      if (x >= nx) continue;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const cplx<float> pp = w[r * S + pad(x)];
+        const cplx<float> dd = w[2 * S + pad(x)];
+        const float p1 = pp.x * inv, p2 = pp.y * inv;
+        const float d = (r ? dd.y : dd.x) * inv;
+        const float e = ev[k][r], hx = hxv[k][r], hy = hyv[k][r];
+        const float e2h = 0.5f * e * e;
+        const float c11 = e * (1.0f + hx * hx), c12 = e * hx * hy, c22 = e * (1.0f + hy * hy);
+        const float c13 = e2h * hx, c23 = e2h * hy, c33 = e * e * e * third;
+        const float w1 = c11 * p1 + c12 * p2 + c13 * d;
+        const float w2 = c12 * p1 + c22 * p2 + c23 * d;
+        const float q = c13 * p1 + c23 * p2 + c33 * d;
+        part += p1 * w1 + p2 * w2 + d * q;
+        w[r * S + pad(x)] = mk(w1, w2);
+        if (r) w[2 * S + pad(x)].y = q; else w[2 * S + pad(x)].x = q;
+      }
     }
   }
   gsync(g);
   cplx<float>* other = w == sm.A ? sm.B : sm.A;
-  const cplx<float>* Y = pfft(w, other, a.lognx, 3, S, false, sm.tws, t, g);
+  const cplx<float>* Y = pfft(w, other, a.lognx, 3, S, false, sm.twx, t, g);
   // R2C split of the three packed rows, A = (Y_m + conj Y_{n-m})/2, B = (Y_m - conj Y_{n-m})/(2i),
   // stored back as row pairs of columns m: t0 = (A_0, A_1), t1 = (B_0, B_1), t2 = (A_2, B_2)
   for (int m = t; m <= h; m += kGT) {
@@ -428,7 +504,7 @@ __device__ __noinline__ float row_matvec(const PersistArgs2d& a, const PInst2d& 
 }
 
 // ---- C2: column FFT, G p, x and r updates, r.z partial (column c, group g) ---------------
-__device__ __noinline__ float col_forward_update(const PersistArgs2d& a, const PInst2d& I,
+__device__ __forceinline__ float col_forward_update(const PersistArgs2d& a, const PInst2d& I,
                                                     const IScal& s, int c, const PSmem& sm,
                                                     int t, int g) {
   const int ny = a.ny, S = pad_len(ny), nx = a.nx;
@@ -454,7 +530,7 @@ __device__ __noinline__ float col_forward_update(const PersistArgs2d& a, const P
     }
   }
   gsync(g);
-  const cplx<float>* o = pfft(sm.A, sm.B, a.logny, 3, S, false, sm.tws, t, g);
+  const cplx<float>* o = pfft(sm.A, sm.B, a.logny, 3, S, false, sm.twy, t, g);
   float part = 0.0f;
   const float al = s.alpha;
   const float kx = kx_of(s, c, nx);
@@ -510,14 +586,29 @@ __global__ void __launch_bounds__(kPNT, 1) k2_pcg_persist(const __grid_constant_
   // thread t of group g; the group's two transform buffers after the twiddle table
   const int g = threadIdx.x / kGT, t = threadIdx.x - g * kGT;
   const long long be = 3ll * pad_len(a.nx > a.ny ? a.nx : a.ny);
+  const int ntw = a.nx + (a.ny == a.nx ? 0 : a.ny);
   PSmem sm;
-  sm.tws = reinterpret_cast<cplx<float>*>(smem);
-  sm.A = sm.tws + kTwTab + 2 * be * g;
+  sm.twx = reinterpret_cast<cplx<float>*>(smem);
+  sm.twy = a.ny == a.nx ? sm.twx : sm.twx + a.nx;
+  sm.A = sm.twx + ntw + 2 * be * g;
   sm.B = sm.A + be;
   {
-    // e^{-2 pi i m / 1024} from the 16384-entry float32 table
+    // the stage tables of both lengths from the 16384-entry float32 table e^{-2 pi i m / 16384}
     const cplx<float>* tg = static_cast<const cplx<float>*>(a.tw32);
-    for (int m = threadIdx.x; m < kTwTab; m += kPNT) sm.tws[m] = tg[m * (kTwiddleN / kTwTab)];
+    for (int which = 0; which < (a.ny == a.nx ? 1 : 2); ++which) {
+      const int log2n = which ? a.logny : a.lognx;
+      cplx<float>* tab = which ? sm.twy : sm.twx;
+      const int ns = (log2n + 3) / 4, base = log2n / ns, extra = log2n - base * ns;
+      int lp = 0;
+      for (int st = 0; st < ns; ++st) {
+        const int bits = base + (st < extra ? 1 : 0), R = 1 << bits, p0 = 1 << lp;
+        for (int e = threadIdx.x; e < (R - 1) * p0; e += kPNT) {
+          const int r = 1 + e / p0, k = e - (r - 1) * p0;
+          tab[p0 - 1 + e] = tg[(r * k) << (kTwiddleLog2 - lp - bits)];
+        }
+        lp += bits;
+      }
+    }
   }
   const int B = a.B, CU = a.col_units, RU = a.row_units;
   const long long P = (long long)a.nx * a.ny;
@@ -628,11 +719,12 @@ __global__ void k2_persist_arm(unsigned* bar, int* err) {
 
 }  // namespace
 
-// Shared memory: the twiddle table and two buffers of three padded transforms per group.
+// Shared memory: the twiddle tables and two buffers of three padded transforms per group.
 size_t persist2d_smem(int nx, int ny, int tw) {
   (void)tw;
   const long long be = 3ll * pad_len(nx > ny ? nx : ny);
-  return sizeof(cplx<float>) * (kTwTab + 2 * be * kNG);
+  const long long ntw = nx + (ny == nx ? 0 : ny);
+  return sizeof(cplx<float>) * (ntw + 2 * be * kNG);
 }
 
 // A column unit is one half-spectrum column (each group transforms three planes of it).

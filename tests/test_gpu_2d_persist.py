@@ -128,3 +128,39 @@ def test_persistent_inner_solve_edge_cases(S):
         lay.set_form2d(0, 3)
     with pytest.raises(sgn.SgnError):
         lay.set_form2d(0, 2)             # one column per tile
+
+
+def test_autotune_2d_chooses_a_form_and_restores_the_state(S):
+    """sgn_state_autotune on a 2d state times both inner-solve forms on the state's own RK4
+    steps, leaves one of them set, and restores the state bitwise; the next steps equal the
+    same steps taken with that form set by hand."""
+    sgn, ctx = S
+    n = 128
+    c = I.bump2d_case(n=n, L=40.0, a=0.2, x0=10.0, H=0.5, R=3.0, dt=0.05)
+    g = sgn.Grid(2, n, 40.0, g=9.81, ny=n, Ly=40.0)
+
+    def state(lay):
+        eta, u, h = dev(c["eta"]), dev(c["u"]), dev(c["h"])
+        U = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+        gh = torch.zeros_like(U)
+        st = sgn.State(lay, eta, U, u, h, gh)
+        st.init()
+        return st, eta, u
+
+    lay = sgn.Layout(ctx, [g])
+    st, eta, u = state(lay)
+    eta0, u0 = eta.clone(), u.clone()
+    ms = st.autotune([0.05], rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
+    assert ms > 0.0
+    form = lay.form2d()[0]
+    assert form in (0, 1)
+    assert torch.equal(eta, eta0) and torch.equal(u, u0)
+    st.rk4(0.05, 3, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
+    lay2 = sgn.Layout(ctx, [g])
+    lay2.set_form2d(form, 0)
+    st2, eta2, u2 = state(lay2)
+    st2.rk4(0.05, 3, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
+    torch.cuda.synchronize()
+    assert torch.equal(eta, eta2) and torch.equal(u, u2)
+    st.close()
+    st2.close()
