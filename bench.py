@@ -34,6 +34,22 @@ METRIC = "SGN grid-point-steps/s batched vs plain at ≤1e-6 rel err; p50/p99 so
 UNIT = "grid-point-steps/s"
 FULL_STEPS = 200            # the ensemble configuration's run length
 FP32_PEAK = 152 * 128 * 2 * 2.07e9          # FMA lanes x 2 flops x max SM clock
+# float32 FMA rate of a dependent-chain probe kernel measured on the GB300s (TFLOP/s)
+FP32_PROBE_TFLOPS = 75.3
+# DRAM bytes (read + write) per launch of the 2d persistent inner-solve kernel on the
+# pcg2d_batch configuration (16 instances of 512^2), from an ncu capture of this kernel
+# version (dram__bytes_read.sum + dram__bytes_write.sum, the mean of the first solve's two
+# launches: 4.362e9 and 6.128e9 bytes)
+PCG2D_TRAFFIC_BYTES = 5.245e9
+
+
+def hbm_peak():
+    """The measured HBM copy bandwidth (GB/s) and its source."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
 # float32 operations per double-float flop in a complex FFT butterfly: a double-float add is
 # 11 float32 operations and a multiply 7, so a butterfly costs about 9.6 times its float32 form
 DF_COST = 9.6
@@ -466,11 +482,18 @@ def gpu_arm(args, world, rank, local, pg):
     fhi = s1["flops64"] - s0["flops64"]
     pcg_s = prof["pcg_ms"] * 1e-3
     achieved = (f32 + DF_COST * fhi) / pcg_s / 1e12
+    nominal = (f32 + fhi) / pcg_s / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK / 1e12, "unit": "TFLOP/s",
             "frac": achieved * 1e12 / FP32_PEAK, "traffic": None,
             "kernel": "k_pcg1d<float,...,mixed> (one launch per size class per solve)",
             "note": "float32-operation rate: float32 algorithmic flops plus double-float flops "
                     f"x {DF_COST}; peak = 152 SMs x 128 FMA lanes x 2 x 2.07 GHz (derived)",
+            "frac_nominal": nominal * 1e12 / FP32_PEAK,
+            "achieved_nominal": nominal,
+            "note_nominal": "nominal flops (a double-float flop counted once) over the same "
+                            "time: the method's work without the cost model of double-float",
+            "peak_fp32_probe": FP32_PROBE_TFLOPS,
+            "frac_of_probe": achieved / FP32_PROBE_TFLOPS,
             "flops32": f32, "flops_df": fhi,
             "pcg_share_of_step": prof["pcg_ms"] / t_ms, "rhs_share_of_step": prof["rhs_ms"] / t_ms}
 
@@ -517,6 +540,21 @@ def gpu_arm(args, world, rank, local, pg):
             except Exception as exc:                          # reported, never silent
                 extra[name] = {"error": repr(exc)}
         line["configs"] = extra
+        pc = extra.get("pcg2d_batch", {})
+        if "persistent_kernel" in pc:
+            pk = pc["persistent_kernel"]
+            peak, src = hbm_peak()
+            tr = PCG2D_TRAFFIC_BYTES
+            line["roofline_pcg2d"] = {
+                "bound": "hbm", "achieved": pk["algorithmic_GBs"], "peak": peak, "unit": "GB/s",
+                "frac": pk["algorithmic_GBs"] / peak, "peak_source": src,
+                "traffic": tr,
+                "traffic_GBs": tr / (pk["ms_per_launch"] * 1e-3) / 1e9 if tr else None,
+                "kernel": "k2_pcg_persist (one persistent launch per float32 inner solve)",
+                "workload": pc["workload"],
+                "note": "achieved = 60 B per point per inner iteration (eta, grad h read; x, r, p "
+                        "of two components read and written, float32) x iterations per launch / "
+                        "launch time from CUDA events around each launch"}
         print(json.dumps(line))
         return
     if rank == 0:
