@@ -40,7 +40,7 @@ extern "C" {
 typedef enum {
   SGN_OK = 0,
   SGN_ERR_INVALID_ARG = 1,        /* null pointer, bad count, inconsistent grids */
-  SGN_ERR_UNSUPPORTED_SIZE = 2,   /* n not a power of two or outside the supported range */
+  SGN_ERR_UNSUPPORTED_SIZE = 2,   /* a size outside the supported set (sgn_layout_create) */
   SGN_ERR_NOMEM = 3,              /* device allocation failed */
   SGN_ERR_CUDA = 4,               /* a CUDA runtime call failed (message in sgn_last_error) */
   SGN_ERR_NOT_CONVERGED = 5,      /* PCG hit maxit (or the refinement cap) before rtol */
@@ -101,7 +101,14 @@ void sgn_destroy(sgn_ctx* ctx);
 const char* sgn_last_error(const sgn_ctx* ctx);
 const char* sgn_status_string(sgn_status s);
 
-/* Packs `count` instances (host array `grids`).  1d batches may mix sizes.  A 2d layout of
+/* Packs `count` instances (host array `grids`).  1d batches may mix sizes.  1d sizes: a
+ * power of two with 8 <= n <= 16384, or n = 2^a 3^b 5^c (a >= 1) with 6 <= n <= 6144 (the
+ * grids of §6.1 at sizes such as 96, 384 or 1536).  The latter run on generic kernels (one
+ * CTA per instance, a mixed-radix transform in shared memory) for the spectral gradient,
+ * the coefficients, G, A^{-1}, PCG (both precisions), GMRES, the right-hand side and the
+ * RK4 / Adams-Bashforth steppers; dealiasing, SBDF2 (sgn_step_linimp), the non-constraint
+ * stepper and sgn_pcg1d_noalloc take powers of two only (SGN_ERR_UNSUPPORTED_SIZE).  2d
+ * grids: powers of two, 8 <= nx, ny <= 1024.  Other sizes: SGN_ERR_UNSUPPORTED_SIZE.  A 2d layout of
  * count > 1 (at most 32) is a batch of instances on one grid (every sgn_grid equal); it
  * serves sgn_spectral_grad, sgn_precond_coeffs, sgn_apply_operator, sgn_precond_solve,
  * sgn_pcg and sgn_pcg_async, whose mixed-precision solves advance the float32 inner PCG of

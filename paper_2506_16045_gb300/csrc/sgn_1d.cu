@@ -409,6 +409,8 @@ cudaError_t launch_deriv1d(const Layout1d& lay, const void* tw64, const double* 
     if (e) return e;
     k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, big, tw, f, fx);
     return cudaGetLastError();
+  }, [&](int first, int num, cudaStream_t s) {
+    return mr_launch_deriv(lay, first, num, f, fx, s);
   });
 }
 
@@ -425,6 +427,8 @@ cudaError_t launch_apply_G1d(const Layout1d& lay, const void* tw64, const double
     if (e) return e;
     k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, big, tw, eta, hx, u, Gu);
     return cudaGetLastError();
+  }, [&](int first, int num, cudaStream_t s) {
+    return mr_launch_apply_G(lay, first, num, eta, hx, u, Gu, s);
   });
 }
 
@@ -447,6 +451,8 @@ cudaError_t launch_precond1d(const Layout1d& lay, const void* tw64, const SolveR
     if (e) return e;
     k<<<num, NT, sm, s>>>(lay.d_inst, lay.d_ids + first, big, tw, rec, r, z);
     return cudaGetLastError();
+  }, [&](int first, int num, cudaStream_t s) {
+    return mr_launch_precond(lay, first, num, rec, r, z, s);
   });
 }
 

@@ -259,15 +259,20 @@ using IC = std::integral_constant<int, V>;
 // One launch per size class.  When a layout holds several classes they run concurrently on
 // the layout's side streams (event fork from `s`, join back into `s`; largest class first),
 // so a class that occupies few SMs does not leave the rest of the GPU idle.
-// call(l, first, num, stream) launches class l = log2 n.
+// call(l, first, num, stream) launches class l = log2 n (kGenericClass: the sizes that are
+// not powers of two).
 template <typename Call>
 cudaError_t fan_classes(const Layout1d& lay, cudaStream_t s, Call&& call) {
   int ncls = 0;
-  for (int l = 3; l <= kMaxLog1d; ++l) ncls += lay.class_end[l] > lay.class_begin[l];
+  for (int i = 0; i < kNumClassSlots; ++i) {
+    const int l = class_at(i);
+    ncls += lay.class_end[l] > lay.class_begin[l];
+  }
   const bool fan = ncls > 1 && lay.side[0] != nullptr;
   if (fan && cudaEventRecord(lay.fork, s) != cudaSuccess) return cudaGetLastError();
   int ci = 0;
-  for (int l = kMaxLog1d; l >= 3; --l) {
+  for (int i = 0; i < kNumClassSlots; ++i) {
+    const int l = class_at(i);
     const int b = lay.class_begin[l], e = lay.class_end[l];
     if (e <= b) continue;
     cudaStream_t cs = s;
@@ -287,13 +292,21 @@ cudaError_t fan_classes(const Layout1d& lay, cudaStream_t s, Call&& call) {
   return cudaSuccess;
 }
 
+// The generic class's launch of an operation that has no generic kernel (the API rejects
+// such layouts first).
+struct NoGeneric {
+  cudaError_t operator()(int, int, cudaStream_t) const { return cudaErrorNotSupported; }
+};
+
 // Size-class dispatch for the cta_fft kernels: NT = clamp(n/8, 32, 512) threads, MAXB =
 // n/(4 NT) butterflies per thread per radix-4 stage (n = 16384: 1024 threads, and the
-// transform buffer in the layout's global scratch instead of shared memory).
-template <typename Fn>
-cudaError_t for_each_class(const Layout1d& lay, cudaStream_t s, Fn&& fn) {
+// transform buffer in the layout's global scratch instead of shared memory).  gen(first,
+// num, stream) launches the generic class.
+template <typename Fn, typename Gen = NoGeneric>
+cudaError_t for_each_class(const Layout1d& lay, cudaStream_t s, Fn&& fn, Gen&& gen = Gen{}) {
   return fan_classes(lay, s, [&](int l, int b, int num, cudaStream_t cs) -> cudaError_t {
     switch (l) {
+      case kGenericClass: return gen(b, num, cs);
       case 3: case 4: case 5: case 6: case 7: return fn(IC<32>{}, IC<1>{}, l, b, num, cs);
       case 8: return fn(IC<32>{}, IC<2>{}, l, b, num, cs);
       case 9: return fn(IC<64>{}, IC<2>{}, l, b, num, cs);
@@ -307,11 +320,12 @@ cudaError_t for_each_class(const Layout1d& lay, cudaStream_t s, Fn&& fn) {
   });
 }
 
-// Size-class dispatch for the register-FFT kernels, templated on log2 n.
-template <typename Fn>
-cudaError_t for_each_size(const Layout1d& lay, cudaStream_t s, Fn&& fn) {
+// Size-class dispatch for the register-FFT kernels, templated on log2 n; gen as above.
+template <typename Fn, typename Gen = NoGeneric>
+cudaError_t for_each_size(const Layout1d& lay, cudaStream_t s, Fn&& fn, Gen&& gen = Gen{}) {
   return fan_classes(lay, s, [&](int l, int b, int num, cudaStream_t cs) -> cudaError_t {
     switch (l) {
+      case kGenericClass: return gen(b, num, cs);
       case 3: return fn(IC<3>{}, b, num, cs);
       case 4: return fn(IC<4>{}, b, num, cs);
       case 5: return fn(IC<5>{}, b, num, cs);

@@ -129,6 +129,9 @@ cudaError_t launch_pcg1d(const Layout1d& lay, const void* tw64, const void* tw32
                              rtol_inner, maxit, max_refine, rec, ws, coef_df);
   return d1::for_each_size(lay, s, [&](auto Lc, int first, int num, cudaStream_t cs) {
     return launch_form<decltype(Lc)::value>(lay, a, first, num, cs, PcgKernels{});
+  }, [&](int first, int num, cudaStream_t cs) {
+    return mr_launch_pcg(lay, first, num, precision, eta, hx, b, x, given, kind, rtol,
+                         rtol_inner, maxit, max_refine, rec, ws, cs);
   });
 }
 
@@ -140,8 +143,12 @@ cudaError_t launch_pcg1d_ux(const Layout1d& lay, const void* tw64, const void* t
   PcgArgs a = pcg_args(lay, tw64, tw32, precision, eta, hx, b, x, nullptr, kind, rtol,
                        rtol_inner, maxit, max_refine, rec, ws, coef_df);
   a.ux = scratch;
+  // the generic kernels take no u_x hand-off: their right-hand side derives u itself
   return d1::for_each_size(lay, s, [&](auto Lc, int first, int num, cudaStream_t cs) {
     return launch_form<decltype(Lc)::value>(lay, a, first, num, cs, PcgKernels{});
+  }, [&](int first, int num, cudaStream_t cs) {
+    return mr_launch_pcg(lay, first, num, precision, eta, hx, b, x, nullptr, kind, rtol,
+                         rtol_inner, maxit, max_refine, rec, ws, cs);
   });
 }
 
@@ -152,6 +159,8 @@ cudaError_t launch_rhs1d(const Layout1d& lay, const void* tw64, const void* tw32
   const RhsArgs a = rhs_args(lay, tw64, tw32, precision, g, eta, u, h, hx, f_eta, f_U, scratch);
   return d1::for_each_size(lay, s, [&](auto Lc, int first, int num, cudaStream_t cs) {
     return launch_form<decltype(Lc)::value>(lay, a, first, num, cs, RhsKernels{});
+  }, [&](int first, int num, cudaStream_t cs) {
+    return mr_launch_rhs(lay, first, num, precision, g, eta, u, h, hx, f_eta, f_U, scratch, cs);
   });
 }
 
@@ -163,6 +172,8 @@ cudaError_t launch_rhs1d_ux(const Layout1d& lay, const void* tw64, const void* t
   a.ux_given = 1;
   return d1::for_each_size(lay, s, [&](auto Lc, int first, int num, cudaStream_t cs) {
     return launch_form<decltype(Lc)::value>(lay, a, first, num, cs, RhsKernels{});
+  }, [&](int first, int num, cudaStream_t cs) {
+    return mr_launch_rhs(lay, first, num, precision, g, eta, u, h, hx, f_eta, f_U, scratch, cs);
   });
 }
 

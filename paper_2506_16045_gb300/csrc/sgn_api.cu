@@ -222,7 +222,9 @@ __global__ void k_accum(const SolveRec* __restrict__ rec, const Inst1d* __restri
     atomicMax(&st->status, rec[i].status);
     double f32, f64;
     const double n = insts ? (double)insts[i].n : (double)n2d;
-    const double lg = insts ? (double)insts[i].log2n : (double)log2n2d;
+    // log2 n (the generic sizes, log2n = 0: the real logarithm)
+    const double lg = insts ? (insts[i].log2n ? (double)insts[i].log2n : log2((double)insts[i].n))
+                            : (double)log2n2d;
     solve_flops(n, lg, rec[i].iters, rec[i].refinements, mixed, f32, f64);
     atomicAdd(&st->flops32, f32);
     atomicAdd(&st->flops64, f64);
@@ -342,6 +344,12 @@ sgn_status cuda_fail(sgn_ctx* ctx, cudaError_t e, const char* where) {
   } while (0)
 
 inline cudaStream_t as_stream(sgn_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// a 1d layout holding sizes that are not powers of two (the generic kernels)
+bool has_generic(const sgn_layout* lay) {
+  return lay->dim == 1 &&
+         lay->l1.class_end[sgn::kGenericClass] > lay->l1.class_begin[sgn::kGenericClass];
+}
 
 int ilog2_exact(int n) {
   if (n <= 0 || (n & (n - 1))) return -1;
@@ -525,8 +533,9 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
       return fail(ctx, SGN_ERR_INVALID_ARG, "grid fields");
     if (dim == 1 && g.ny != 1) return fail(ctx, SGN_ERR_INVALID_ARG, "1d grid needs ny = 1");
     const int lx = ilog2_exact(g.nx);
-    if (dim == 1 && (lx < 3 || lx > sgn::kMaxLog1d))
-      return fail(ctx, SGN_ERR_UNSUPPORTED_SIZE, "1d nx must be a power of two in [8, 16384]");
+    if (dim == 1 && (lx < 3 || lx > sgn::kMaxLog1d) && !(lx < 0 && sgn::mr_size_ok(g.nx)))
+      return fail(ctx, SGN_ERR_UNSUPPORTED_SIZE,
+                  "1d nx must be a power of two in [8, 16384] or 2^a 3^b 5^c (a >= 1) in [6, 6144]");
     if (dim == 2) {
       const int ly = ilog2_exact(g.ny);
       if (lx < 3 || ly < 3 || lx > 10 || ly > 10)
@@ -566,16 +575,48 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
         if (ilog2_exact(grids[i].nx) == l) ids.push_back(i);
       L.class_end[l] = (int)ids.size();
     }
+    L.class_begin[sgn::kGenericClass] = (int)ids.size();
+    for (int i = 0; i < count; ++i)
+      if (ilog2_exact(grids[i].nx) < 0) ids.push_back(i);
+    L.class_end[sgn::kGenericClass] = (int)ids.size();
+    std::vector<std::pair<int, long long>> tables;   // generic n and its twiddles' offset
     for (int i = 0; i < count; ++i) {
       Inst1d& I = L.h_inst[i];
       I.n = grids[i].nx;
-      I.log2n = ilog2_exact(I.n);
+      I.log2n = ilog2_exact(I.n) < 0 ? 0 : ilog2_exact(I.n);
       I.L = grids[i].Lx;
       I.off = lay->offsets[i];
       I.ws = ws;
+      I.tw = 0;
       ws += (long long)sgn::kWsVectors * (I.n / 2 + 1);
+      L.maxn = std::max(L.maxn, I.n);
+      if (I.log2n == 0) {
+        auto it = std::find_if(tables.begin(), tables.end(),
+                               [&](const std::pair<int, long long>& t) { return t.first == I.n; });
+        if (it == tables.end()) {
+          tables.emplace_back(I.n, L.mr_tw_len);
+          I.tw = L.mr_tw_len;
+          L.mr_tw_len += sgn::mr_twiddle_len(I.n);
+        } else {
+          I.tw = it->second;
+        }
+        L.mr_maxn = std::max(L.mr_maxn, I.n);
+      }
     }
+    L.mr_tw_len += L.mr_tw_len & 1;                 // the double-float table 16-byte aligned
     L.ws_cplx = ws;
+    if (!tables.empty()) {
+      // float64, float32 and double-float complex entries: 16 + 8 + 16 bytes each
+      if (cudaMalloc(&L.mr_tw, (size_t)40 * L.mr_tw_len) != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(SGN_ERR_NOMEM, "layout allocation");
+      }
+      for (const auto& t : tables)
+        if (sgn::mr_twiddles_init(t.first, t.second, L, nullptr) != cudaSuccess)
+          return cleanup(SGN_ERR_CUDA, "twiddle tables");
+      if (cudaStreamSynchronize(nullptr) != cudaSuccess)
+        return cleanup(SGN_ERR_CUDA, "twiddle tables");
+    }
     const int nbig = L.class_end[sgn::kMaxLog1d] - L.class_begin[sgn::kMaxLog1d];
     if (nbig > 0 &&
         cudaMalloc(&L.big, sizeof(double) * 2 * ((size_t)nbig << sgn::kMaxLog1d)) != cudaSuccess) {
@@ -600,7 +641,10 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
       return cleanup(SGN_ERR_CUDA, "layout upload");
     }
     int ncls = 0;
-    for (int l = 3; l <= sgn::kMaxLog1d; ++l) ncls += L.class_end[l] > L.class_begin[l];
+    for (int i = 0; i < sgn::kNumClassSlots; ++i) {
+      const int l = sgn::class_at(i);
+      ncls += L.class_end[l] > L.class_begin[l];
+    }
     if (ncls > 1) {
       if (cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming) != cudaSuccess)
         return cleanup(SGN_ERR_CUDA, "layout events");
@@ -650,6 +694,7 @@ extern "C" void sgn_layout_destroy(sgn_layout* lay) {
   cudaFree(lay->l1.d_inst);
   cudaFree(lay->l1.big);
   cudaFree(lay->l1.d_ids);
+  cudaFree(lay->l1.mr_tw);
   delete[] lay->l1.h_inst;
   sgn::batch2d_destroy(lay->b2);
   sgn::layout2d_destroy(lay->l2);
@@ -1182,9 +1227,7 @@ sgn_status lincomb(sgn_state* st, double* out, Terms xs, Terms fs, int component
   const LinComb lc = make_lincomb(xs, fs), lc2 = make_lincomb(xs2, fs2);
   if (st->lay->dim == 1) {
     const sgn::Layout1d& L = st->lay->l1;
-    int maxn = 8;
-    for (int l = 3; l <= sgn::kMaxLog1d; ++l)
-      if (L.class_end[l] > L.class_begin[l]) maxn = 1 << l;
+    const int maxn = L.maxn;
     LinJobs J{};
     J.j[0] = LinJob{out, lc, components};
     J.j[1] = LinJob{out2, lc2, components2};
@@ -1208,9 +1251,7 @@ sgn_status force_at(sgn_state* st, double* fe, double* fU, double c, cudaStream_
   int maxn = 8;
   long long n2d = 0;
   if (d1) {
-    const sgn::Layout1d& L = st->lay->l1;
-    for (int l = 3; l <= sgn::kMaxLog1d; ++l)
-      if (L.class_end[l] > L.class_begin[l]) maxn = 1 << l;
+    maxn = st->lay->l1.maxn;
   } else {
     n2d = st->P;
   }
@@ -1642,6 +1683,8 @@ extern "C" sgn_status sgn_step_linimp(sgn_state* st, const double* dt, int nstep
                                       const sgn_opts* opts, sgn_stream stream) {
   if (!st || !dt || nsteps < 0) return SGN_ERR_INVALID_ARG;
   sgn_ctx* ctx = st->lay->ctx;
+  if (has_generic(st->lay))
+    return fail(ctx, SGN_ERR_UNSUPPORTED_SIZE, "SBDF2 takes power-of-two sizes");
   DeviceGuard g(ctx->device);
   cudaStream_t s = as_stream(stream);
   SGN_TRY(check_opts(st, opts));
@@ -1792,6 +1835,9 @@ sgn_status rk4_nc_once(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
 extern "C" sgn_status sgn_step_rk4_nc(sgn_state* st, const double* dt, int nsteps,
                                       const sgn_opts* opts, sgn_stream stream) {
   if (!st || !dt || nsteps < 0) return SGN_ERR_INVALID_ARG;
+  if (has_generic(st->lay))
+    return fail(st->lay->ctx, SGN_ERR_UNSUPPORTED_SIZE,
+                "the non-constraint stepper takes power-of-two sizes");
   if (st->force.K > 0 || st->dealias)
     return fail(st->lay->ctx, SGN_ERR_INVALID_ARG,
                 "the non-constraint stepper takes states without forcing or dealiasing");
@@ -1831,6 +1877,8 @@ extern "C" sgn_status sgn_state_set_forcing(sgn_state* st, int nterms, const dou
 
 extern "C" sgn_status sgn_state_set_dealias(sgn_state* st, int on) {
   if (!st) return SGN_ERR_INVALID_ARG;
+  if (on && has_generic(st->lay))
+    return fail(st->lay->ctx, SGN_ERR_UNSUPPORTED_SIZE, "dealiasing takes power-of-two sizes");
   st->dealias = on ? 1 : 0;
   graph_drop(st);                   // a captured step holds the previous setting
   return SGN_OK;

@@ -20,10 +20,11 @@ constexpr size_t kTwDfBytes = (size_t)16 * kTwiddleN;
 // ws (in units of complex doubles) and holds kWsVectors half spectra of n/2 + 1 modes.
 struct Inst1d {
   int n;
-  int log2n;
+  int log2n;             // log2 n, or 0 for a size that is not a power of two
   double L;
   long long off;
   long long ws;
+  long long tw;          // sizes that are not powers of two: first entry of the n's twiddles
 };
 
 // Preconditioner coefficients and solve report per instance (device resident).
@@ -40,16 +41,26 @@ constexpr int kWsVectors = 6;          // half-spectrum vectors per instance in 
 constexpr int kMaxLog1d = 14;          // 1d n <= 16384 (n = 16384: two-CTA clusters)
 constexpr int kSmemLog1d = 13;         // largest 1d n whose float64 transform fits in one CTA
 constexpr int kClusterLog1d = 12;      // smallest 1d log2 n with a two-CTA cluster form
+constexpr int kGenericClass = 0;       // size class of the 1d n that are not powers of two
+// The size classes in launch order: the largest power of two first, the generic class last.
+constexpr int kNumClassSlots = kMaxLog1d - 3 + 2;
+inline int class_at(int i) { return i <= kMaxLog1d - 3 ? kMaxLog1d - i : kGenericClass; }
 
 struct Layout1d {
   int count = 0;
   long long points = 0;                // sum of n
+  int maxn = 0;                        // largest n
   long long ws_cplx = 0;               // workspace size in complex doubles
   Inst1d* d_inst = nullptr;            // device copy
   Inst1d* h_inst = nullptr;            // host copy
   int* d_ids = nullptr;                // instance ids grouped by size class
-  int class_begin[16] = {0};           // per log2n: [begin, end) into ids
-  int class_end[16] = {0};
+  int class_begin[16] = {0};           // per log2n: [begin, end) into ids; class
+  int class_end[16] = {0};             // kGenericClass: the sizes that are not powers of two
+  // sizes n = 2^a 3^b 5^c that are not powers of two (the generic kernels): their twiddle
+  // tables (float64, float32, double-float, mr_tw_len entries each) and the largest such n
+  void* mr_tw = nullptr;
+  long long mr_tw_len = 0;
+  int mr_maxn = 0;
   // float64 transform buffers (n complex doubles per instance) of the cta_fft kernels for
   // the instances above kSmemLog1d, indexed by position in their size class
   void* big = nullptr;
@@ -129,6 +140,27 @@ cudaError_t launch_linimp_step1d(const Layout1d& lay, const void* tw64, const vo
                                  const void* res0_hat, void* res1_hat, double c1, double c0,
                                  bool solve, void* ws, double* u_out, void* ux_out,
                                  cudaStream_t s);
+
+// Sizes n = 2^a 3^b 5^c (a >= 1) that are not powers of two, 6 <= n <= 6144: one CTA per
+// instance with a mixed-radix transform in shared memory (sgn_1d_mr.cu).  Each launches the
+// generic instances ids[first, first + num) of the layout.
+bool mr_size_ok(int n);
+long long mr_twiddle_len(int n);
+cudaError_t mr_twiddles_init(int n, long long off, const Layout1d& lay, cudaStream_t s);
+cudaError_t mr_launch_deriv(const Layout1d& lay, int first, int num, const double* f,
+                            double* fx, cudaStream_t s);
+cudaError_t mr_launch_apply_G(const Layout1d& lay, int first, int num, const double* eta,
+                              const double* hx, const double* u, double* Gu, cudaStream_t s);
+cudaError_t mr_launch_precond(const Layout1d& lay, int first, int num, const SolveRec* rec,
+                              const double* r, double* z, cudaStream_t s);
+cudaError_t mr_launch_pcg(const Layout1d& lay, int first, int num, int precision,
+                          const double* eta, const double* hx, const double* b, double* x,
+                          const SolveRec* given, int kind, double rtol, double rtol_inner,
+                          int maxit, int max_refine, SolveRec* rec, void* ws, cudaStream_t s);
+cudaError_t mr_launch_rhs(const Layout1d& lay, int first, int num, int precision, double g,
+                          const double* eta, const double* u, const double* h,
+                          const double* hx, double* f_eta, double* f_U, double* scratch,
+                          cudaStream_t s);
 
 struct Layout2d;
 

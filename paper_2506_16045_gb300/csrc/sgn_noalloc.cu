@@ -52,6 +52,7 @@ __global__ void k_noalloc_prepare(sgn::Inst1d* inst, int* ids, sgn::SolveRec* re
   inst->L = L;
   inst->off = 0;
   inst->ws = 0;
+  inst->tw = 0;
   ids[0] = 0;
   *rec = sgn::SolveRec{};
 }

@@ -67,6 +67,10 @@ struct Req {
   double last_issue = 0.0;            // when its last job was issued (2d lane turns)
   int remaining = 0;
   bool admitted = false, done = false;
+  // ownership after `done` (under the server's mutex): the worker frees the request's
+  // working memory (reaped); the client gives up its result (released).  Whichever comes
+  // second deletes the request.
+  bool reaped = false, released = false;
   sgn_status status = SGN_OK;
   sgn_pcg_info info{};
   long long iters = 0;
@@ -170,11 +174,21 @@ void free_req_all(Req* r) {
 }
 
 // Frees deferred work, which waits for the device: only when no lane is busy, unless the
-// deferred memory has grown past kReapBytes.
+// deferred memory has grown past kReapBytes.  A request the client has already released
+// is deleted here; otherwise sgn_result_release deletes it later.
 void reap(sgn_server* S, bool force) {
   if (S->reap_reqs.empty() && S->reap_lays.empty() && S->reap_states.empty()) return;
   if (!force && !S->inflight.empty() && S->reap_bytes < kReapBytes) return;
-  for (Req* r : S->reap_reqs) free_req_work(r);
+  for (Req* r : S->reap_reqs) {
+    free_req_work(r);
+    bool gone;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      r->reaped = true;
+      gone = r->released;
+    }
+    if (gone) free_req_all(r);
+  }
   for (sgn_state* st : S->reap_states) sgn_state_free(st);
   for (sgn_layout* l : S->reap_lays) sgn_layout_destroy(l);
   S->reap_reqs.clear();
@@ -775,6 +789,11 @@ extern "C" sgn_status sgn_result_release(sgn_server* S, uint64_t ticket) {
     if (!it->second->done) return SGN_ERR_PENDING;
     r = it->second;
     S->all.erase(it);
+    // the worker still holds the request in its deferred frees: it deletes it there
+    if (!r->reaped) {
+      r->released = true;
+      return SGN_OK;
+    }
   }
   cudaSetDevice(S->device);
   free_req_all(r);

@@ -211,7 +211,7 @@ def test_pcg_edge_cases(S):
     info = sgn.pcg(lay, dev(eta), dev(hx), dev(b), x, rtol=1e-14, maxit=2, check=False)[0]
     assert info["status"] == 5
     with pytest.raises(sgn.SgnError):
-        sgn.Layout(ctx, [sgn.Grid(1, 96, 1.0)])
+        sgn.Layout(ctx, [sgn.Grid(1, 98, 1.0)])          # 2 7^2: no transform for radix 7
 
 
 def test_rhs_shelf_and_flat(S):

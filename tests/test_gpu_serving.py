@@ -226,3 +226,35 @@ def test_short_solve_overlaps_a_long_2d_run(S):
     for t in (t_run, t_sol):
         srv.release(t)
     srv.close()
+
+
+def test_release_while_other_work_is_in_flight(S):
+    """Results released as soon as they are done, while a 2d run keeps the server busy (so
+    their working memory is still queued for the deferred frees): the server frees each
+    request exactly once, a released ticket is gone, and later requests still finish."""
+    sgn, ctx = S
+    n2 = 256
+    c2 = I.bump2d_case(n=n2, L=80.0, a=0.2, x0=20.0, H=0.5, R=3.0, dt=0.02)
+    g2 = sgn.Grid(2, n2, 80.0, g=9.81, ny=n2, Ly=80.0)
+    srv = sgn.Server(ctx)
+    st, t_run = srv.submit(sgn.REQ_RUN, g2, dev(c2["eta"]), dev(c2["u"]), dev(c2["h"]),
+                           scheme=sgn.SCHEME_RK4, dt=0.02, nsteps=48, rtol=1e-10,
+                           prec=sgn.PREC_MIXED)
+    assert st == 0
+    for wave in range(3):
+        tickets = []
+        for n in (256, 512, 1024, 2048):
+            _, h, eta, b = I.testproblem_1d(n, 1.0, 1.0)
+            st, t = srv.submit(sgn.REQ_SOLVE, sgn.Grid(1, n, 1.0), eta, b, h, rtol=1e-10,
+                               prec=sgn.PREC_MIXED, host=True)
+            assert st == 0
+            tickets.append(t)
+        res = wait(srv, tickets)
+        for t in tickets:
+            assert res[t]["status"] == 0
+            assert srv.release(t) == 0
+            assert srv.release(t) == 1                 # gone: SGN_ERR_INVALID_ARG
+    res = wait(srv, [t_run])
+    assert res[t_run]["status"] == 0
+    srv.release(t_run)
+    srv.close()

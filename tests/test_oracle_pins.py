@@ -20,7 +20,8 @@ GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper
 
 # ---------------------------------------------------------------------------- D (§6.1)
 
-@pytest.mark.parametrize("n,L", [(8, 1.0), (16, 3.7), (64, 100.0), (128, 2 * math.pi)])
+@pytest.mark.parametrize("n,L", [(8, 1.0), (16, 3.7), (64, 100.0), (128, 2 * math.pi),
+                                 (6, 1.0), (12, 2.0), (30, 5.0), (96, 80.0), (120, 1.5)])
 def test_derivative_fft_equals_cotangent_matrix(n, L):
     """D built from the DFT definition equals the closed-form periodic cotangent matrix."""
     Df = O.diff_matrix_fft(n, L)
@@ -29,7 +30,7 @@ def test_derivative_fft_equals_cotangent_matrix(n, L):
     assert np.abs(Dc + Dc.T).max() == 0.0           # real antisymmetric
 
 
-@pytest.mark.parametrize("n,L", [(16, 1.0), (64, 7.5)])
+@pytest.mark.parametrize("n,L", [(16, 1.0), (64, 7.5), (30, 2.0), (96, 7.5), (384, 80.0)])
 def test_derivative_exact_on_trig_and_nyquist(n, L):
     x = I.grid_1d(n, L)
     for m in range(1, n // 2):
@@ -144,7 +145,7 @@ def test_lambda_pm_printed_values():
 
 @pytest.mark.parametrize("eta0", [0.5, 1.0, 4.0])
 @pytest.mark.parametrize("hvar", [0.0, 0.5, 1.0, 4.0])
-@pytest.mark.parametrize("n", [16, 64])
+@pytest.mark.parametrize("n", [16, 64, 24, 40])
 def test_theorem_4_1_eigenvalue_interval_1d(n, eta0, hvar):
     """Generalized eigenvalues of (G, A) lie in [1/kappa_ub, 1] (Eq:EigValueBound)."""
     _, h, eta, _ = I.testproblem_1d(n, eta0, hvar)
