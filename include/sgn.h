@@ -102,9 +102,10 @@ const char* sgn_last_error(const sgn_ctx* ctx);
 const char* sgn_status_string(sgn_status s);
 
 /* Packs `count` instances (host array `grids`).  1d batches may mix sizes.  1d sizes: a
- * power of two with 8 <= n <= 16384, or n = 2^a 3^b 5^c (a >= 1) with 6 <= n <= 6144 (the
- * grids of §6.1 at sizes such as 96, 384 or 1536).  The latter run on generic kernels (one
- * CTA per instance, a mixed-radix transform in shared memory) for the spectral gradient,
+ * power of two with 8 <= n <= 16384, or n = 2^a 3^b 5^c (a >= 1) with 6 <= n <= 16384
+ * (the grids of §6.1 at sizes such as 96, 384, 1536 or 12288).  The latter run on generic
+ * kernels (one CTA per instance, a mixed-radix transform in shared memory up to n = 6144,
+ * in a global buffer of the layout above) for the spectral gradient,
  * the coefficients, G, A^{-1}, PCG (both precisions), GMRES, the right-hand side and the
  * RK4 / Adams-Bashforth steppers; dealiasing, SBDF2 (sgn_step_linimp), the non-constraint
  * stepper and sgn_pcg1d_noalloc take powers of two only (SGN_ERR_UNSUPPORTED_SIZE).  2d

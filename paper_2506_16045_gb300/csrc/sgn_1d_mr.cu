@@ -20,7 +20,9 @@ namespace {
 
 using d1::kPi;
 constexpr int kMrNT = 256;
-constexpr int kMrMaxN = 6144;        // two transform buffers of 16-byte entries: 192 KB
+constexpr int kMrMaxN = 16384;       // largest generic n
+constexpr int kMrSmemN = 6144;       // largest n whose two transform buffers (192 KB) are in
+                                     // shared memory; above it they are in global memory
 constexpr int kMrMaxStages = 16;
 
 // ---- plan: radices in order (8 ... 8, then 4 or 2, then 5 ... 5, then 3 ... 3) ------------
@@ -187,6 +189,7 @@ __device__ __forceinline__ const cplx<df>* tw_of<df>(const MrTw& t) { return t.h
 struct MrArgs {
   const Inst1d* insts;
   const int* ids;          // the generic instances' ids
+  cplx<double>* big;       // global transform buffers of the instances above kMrSmemN
   const cplx<double>* tw64;
   const cplx<float>* tw32;
   const cplx<df>* twdf;
@@ -196,10 +199,14 @@ __device__ __forceinline__ MrTw mr_tw(const MrArgs& A, const Inst1d& I) {
   return MrTw{A.tw64 + I.tw, A.tw32 + I.tw, A.twdf + I.tw};
 }
 
+// The instance's two transform buffers (n entries of 16 bytes each): shared memory, or its
+// slot of the layout's global buffer (I.gbuf >= 0, n > kMrSmemN; the CTA's own L2-resident
+// copy, written and read by this CTA only, ordered by the same barriers).
 template <typename T>
-__device__ __forceinline__ cplx<T>* smem_buf(int which, int n) {
+__device__ __forceinline__ cplx<T>* tbuf(const MrArgs& A, const Inst1d& I, int which) {
   extern __shared__ __align__(16) unsigned char smem[];
-  return reinterpret_cast<cplx<T>*>(smem) + (size_t)which * n;
+  unsigned char* base = I.gbuf >= 0 ? reinterpret_cast<unsigned char*>(A.big + I.gbuf) : smem;
+  return reinterpret_cast<cplx<T>*>(base + (size_t)which * 16 * I.n);
 }
 
 // f_x of the real fields a + i b packed in buf (transform, i k / n, inverse): re / im
@@ -220,8 +227,8 @@ __global__ void __launch_bounds__(kMrNT) k_mr_deriv(const MrArgs A, const double
   const Inst1d I = A.insts[A.ids[blockIdx.x]];
   MrPlan P;
   mr_plan(I.n, P);
-  cplx<double>* a = smem_buf<double>(0, I.n);
-  cplx<double>* b = smem_buf<double>(1, I.n);
+  cplx<double>* a = tbuf<double>(A, I, 0);
+  cplx<double>* b = tbuf<double>(A, I, 1);
   for (int j = threadIdx.x; j < I.n; j += kMrNT) a[j] = mk(f[I.off + j], 0.0);
   __syncthreads();
   const cplx<double>* o = mr_deriv_pair<double>(a, b, P, 2.0 * kPi / I.L, mr_tw(A, I).d);
@@ -278,8 +285,8 @@ __global__ void __launch_bounds__(kMrNT) k_mr_apply_G(const MrArgs A, const doub
   MrPlan P;
   mr_plan(I.n, P);
   const int n = I.n, h = n / 2;
-  cplx<double>* a = smem_buf<double>(0, n);
-  cplx<double>* b = smem_buf<double>(1, n);
+  cplx<double>* a = tbuf<double>(A, I, 0);
+  cplx<double>* b = tbuf<double>(A, I, 1);
   const cplx<double>* tw = mr_tw(A, I).d;
   const double kunit = 2.0 * kPi / I.L;
   for (int j = threadIdx.x; j < n; j += kMrNT) a[j] = mk(u[I.off + j], 0.0);
@@ -305,8 +312,8 @@ __global__ void __launch_bounds__(kMrNT) k_mr_precond(const MrArgs A, const Solv
   MrPlan P;
   mr_plan(I.n, P);
   const int n = I.n;
-  cplx<double>* a = smem_buf<double>(0, n);
-  cplx<double>* b = smem_buf<double>(1, n);
+  cplx<double>* a = tbuf<double>(A, I, 0);
+  cplx<double>* b = tbuf<double>(A, I, 1);
   const cplx<double>* tw = mr_tw(A, I).d;
   const double kunit = 2.0 * kPi / I.L, sigma = rec[id].sigma, alpha = rec[id].alpha;
   for (int j = threadIdx.x; j < n; j += kMrNT) a[j] = mk(r[I.off + j], 0.0);
@@ -409,8 +416,8 @@ __global__ void __launch_bounds__(kMrNT) k_mr_pcg(const MrArgs A, const MrPcgArg
   auto wgt = [&](int m) { return (m == 0 || m == h) ? 1.0 : 2.0; };
   cplx<double>* ws = a.ws + I.ws;
   // ---- b^ and x0^ from one transform of b + i x0 (float64)
-  cplx<double>* d0 = smem_buf<double>(0, n);
-  cplx<double>* d1 = smem_buf<double>(1, n);
+  cplx<double>* d0 = tbuf<double>(A, I, 0);
+  cplx<double>* d1 = tbuf<double>(A, I, 1);
   for (int j = threadIdx.x; j < n; j += kMrNT) d0[j] = mk(a.b[I.off + j], a.x[I.off + j]);
   __syncthreads();
   cplx<double>* Y = mr_fft<double>(d0, d1, P, false, tws.d);
@@ -509,10 +516,10 @@ __global__ void __launch_bounds__(kMrNT) k_mr_pcg(const MrArgs A, const MrPcgArg
       Xd[m] = mk(df(xh.x), df(xh.y));
     }
     __syncthreads();
-    cplx<df>* h0 = smem_buf<df>(0, n);
-    cplx<df>* h1 = smem_buf<df>(1, n);
-    cplx<float>* f0 = smem_buf<float>(0, n);
-    cplx<float>* f1 = smem_buf<float>(1, n);
+    cplx<df>* h0 = tbuf<df>(A, I, 0);
+    cplx<df>* h1 = tbuf<df>(A, I, 1);
+    cplx<float>* f0 = tbuf<float>(A, I, 0);
+    cplx<float>* f1 = tbuf<float>(A, I, 1);
     const CoefDf cdf{eta, hx};
     const Coef32 c32{eta, hx};
     const float sigf = (float)sigma, alf = (float)alpha, kf = (float)kunit;
@@ -637,8 +644,8 @@ __global__ void __launch_bounds__(kMrNT) k_mr_rhs(const MrArgs A, double g, cons
   const long long o = I.off;
   const double kunit = 2.0 * kPi / I.L;
   const cplx<T>* tw = tw_of<T>(mr_tw(A, I));
-  cplx<T>* b0 = smem_buf<T>(0, n);
-  cplx<T>* b1 = smem_buf<T>(1, n);
+  cplx<T>* b0 = tbuf<T>(A, I, 0);
+  cplx<T>* b1 = tbuf<T>(A, I, 1);
   // planes of Ptot 8-byte values (float64 or double-float), indexed by point
   T* D = reinterpret_cast<T*>(scr);                 // d, then Psi
   T* M = reinterpret_cast<T*>(scr + Ptot);          // m
@@ -725,6 +732,7 @@ MrArgs mr_args(const Layout1d& lay, int first) {
   MrArgs A;
   A.insts = lay.d_inst;
   A.ids = lay.d_ids + first;
+  A.big = static_cast<cplx<double>*>(lay.mr_big);
   const long long len = lay.mr_tw_len;
   const char* base = static_cast<const char*>(lay.mr_tw);
   A.tw64 = reinterpret_cast<const cplx<double>*>(base);
@@ -733,10 +741,10 @@ MrArgs mr_args(const Layout1d& lay, int first) {
   return A;
 }
 
-// two transform buffers of the layout's largest generic n, 16 bytes per entry.  The tables
+// two transform buffers of the layout's largest generic n up to kMrSmemN, 16 bytes per entry.  The tables
 // lie back to back (float64, float32, double-float; mr_tw_len entries each, an even count
 // so that the double-float table starts on a 16-byte boundary).
-size_t mr_smem(const Layout1d& lay) { return (size_t)2 * 16 * lay.mr_maxn; }
+size_t mr_smem(const Layout1d& lay) { return (size_t)2 * 16 * lay.mr_smem_n; }
 
 template <typename K>
 cudaError_t mr_attr(K k, size_t sm) {
@@ -744,6 +752,8 @@ cudaError_t mr_attr(K k, size_t sm) {
 }
 
 }  // namespace
+
+bool mr_in_smem(int n) { return n <= kMrSmemN; }
 
 bool mr_size_ok(int n) {
   MrPlan P;

@@ -535,7 +535,7 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
     const int lx = ilog2_exact(g.nx);
     if (dim == 1 && (lx < 3 || lx > sgn::kMaxLog1d) && !(lx < 0 && sgn::mr_size_ok(g.nx)))
       return fail(ctx, SGN_ERR_UNSUPPORTED_SIZE,
-                  "1d nx must be a power of two in [8, 16384] or 2^a 3^b 5^c (a >= 1) in [6, 6144]");
+                  "1d nx must be a power of two in [8, 16384] or 2^a 3^b 5^c (a >= 1) in [6, 16384]");
     if (dim == 2) {
       const int ly = ilog2_exact(g.ny);
       if (lx < 3 || ly < 3 || lx > 10 || ly > 10)
@@ -580,6 +580,7 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
       if (ilog2_exact(grids[i].nx) < 0) ids.push_back(i);
     L.class_end[sgn::kGenericClass] = (int)ids.size();
     std::vector<std::pair<int, long long>> tables;   // generic n and its twiddles' offset
+    long long gbuf = 0;                              // global transform buffers (complex)
     for (int i = 0; i < count; ++i) {
       Inst1d& I = L.h_inst[i];
       I.n = grids[i].nx;
@@ -588,6 +589,7 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
       I.off = lay->offsets[i];
       I.ws = ws;
       I.tw = 0;
+      I.gbuf = -1;
       ws += (long long)sgn::kWsVectors * (I.n / 2 + 1);
       L.maxn = std::max(L.maxn, I.n);
       if (I.log2n == 0) {
@@ -600,14 +602,20 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
         } else {
           I.tw = it->second;
         }
-        L.mr_maxn = std::max(L.mr_maxn, I.n);
+        if (sgn::mr_in_smem(I.n)) {
+          L.mr_smem_n = std::max(L.mr_smem_n, I.n);
+        } else {
+          I.gbuf = gbuf;
+          gbuf += 2LL * I.n;
+        }
       }
     }
     L.mr_tw_len += L.mr_tw_len & 1;                 // the double-float table 16-byte aligned
     L.ws_cplx = ws;
     if (!tables.empty()) {
       // float64, float32 and double-float complex entries: 16 + 8 + 16 bytes each
-      if (cudaMalloc(&L.mr_tw, (size_t)40 * L.mr_tw_len) != cudaSuccess) {
+      if (cudaMalloc(&L.mr_tw, (size_t)40 * L.mr_tw_len) != cudaSuccess ||
+          (gbuf > 0 && cudaMalloc(&L.mr_big, (size_t)16 * gbuf) != cudaSuccess)) {
         cudaGetLastError();
         return cleanup(SGN_ERR_NOMEM, "layout allocation");
       }
@@ -695,6 +703,7 @@ extern "C" void sgn_layout_destroy(sgn_layout* lay) {
   cudaFree(lay->l1.big);
   cudaFree(lay->l1.d_ids);
   cudaFree(lay->l1.mr_tw);
+  cudaFree(lay->l1.mr_big);
   delete[] lay->l1.h_inst;
   sgn::batch2d_destroy(lay->b2);
   sgn::layout2d_destroy(lay->l2);

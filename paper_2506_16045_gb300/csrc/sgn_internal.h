@@ -25,6 +25,8 @@ struct Inst1d {
   long long off;
   long long ws;
   long long tw;          // sizes that are not powers of two: first entry of the n's twiddles
+  long long gbuf;        // and, above the shared-memory limit, their global transform
+                         // buffers' offset (complex doubles; -1: shared memory)
 };
 
 // Preconditioner coefficients and solve report per instance (device resident).
@@ -60,7 +62,8 @@ struct Layout1d {
   // tables (float64, float32, double-float, mr_tw_len entries each) and the largest such n
   void* mr_tw = nullptr;
   long long mr_tw_len = 0;
-  int mr_maxn = 0;
+  int mr_smem_n = 0;                   // largest such n with shared-memory buffers
+  void* mr_big = nullptr;              // global transform buffers of the larger ones
   // float64 transform buffers (n complex doubles per instance) of the cta_fft kernels for
   // the instances above kSmemLog1d, indexed by position in their size class
   void* big = nullptr;
@@ -141,10 +144,12 @@ cudaError_t launch_linimp_step1d(const Layout1d& lay, const void* tw64, const vo
                                  bool solve, void* ws, double* u_out, void* ux_out,
                                  cudaStream_t s);
 
-// Sizes n = 2^a 3^b 5^c (a >= 1) that are not powers of two, 6 <= n <= 6144: one CTA per
-// instance with a mixed-radix transform in shared memory (sgn_1d_mr.cu).  Each launches the
-// generic instances ids[first, first + num) of the layout.
+// Sizes n = 2^a 3^b 5^c (a >= 1) that are not powers of two, 6 <= n <= 16384: one CTA per
+// instance with a mixed-radix transform in shared memory (n <= 6144; above, in global
+// memory) (sgn_1d_mr.cu).  Each launches the generic instances ids[first, first + num) of
+// the layout.
 bool mr_size_ok(int n);
+bool mr_in_smem(int n);
 long long mr_twiddle_len(int n);
 cudaError_t mr_twiddles_init(int n, long long off, const Layout1d& lay, cudaStream_t s);
 cudaError_t mr_launch_deriv(const Layout1d& lay, int first, int num, const double* f,

@@ -53,6 +53,7 @@ __global__ void k_noalloc_prepare(sgn::Inst1d* inst, int* ids, sgn::SolveRec* re
   inst->off = 0;
   inst->ws = 0;
   inst->tw = 0;
+  inst->gbuf = -1;
   ids[0] = 0;
   *rec = sgn::SolveRec{};
 }

@@ -1,5 +1,6 @@
 """1d sizes that are not powers of two, n = 2^a 3^b 5^c (the grids of §6.1 at n = 96, 384,
-1536, 6144, ...), on the generic kernels (mixed-radix transforms in shared memory), against
+1536, 6144, 12288, ...), on the generic kernels (mixed-radix transforms in shared memory, or
+in global memory above n = 6144), against
 the oracle: gradient, G, the preconditioner, PCG in both precisions, GMRES, the right-hand
 side and the RK4 / Adams-Bashforth steppers, alone and in ragged batches with powers of two.
 
@@ -50,7 +51,8 @@ def unpack(v, offs):
 
 # generic sizes (every radix: 2, 4, 8, 3, 5), with powers of two mixed in
 RAGGED = [(96, 80.0), (384, 200.0), (1536, 200.0), (6144, 400.0), (6, 1.0), (30, 5.0),
-          (120, 10.0), (3000, 300.0), (64, 7.5), (512, 3.0), (360, 36.0), (2400, 100.0)]
+          (120, 10.0), (3000, 300.0), (64, 7.5), (512, 3.0), (360, 36.0), (2400, 100.0),
+          (12288, 800.0), (15360, 900.0)]
 
 
 def fields(n, L, seed):
@@ -110,7 +112,7 @@ def test_generic_operator_matches_dense_weak_form(S, n):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("n,eta0,hvar", [(96, 1.0, 1.0), (384, 4.0, 1.0), (1536, 1.0, 4.0),
-                                         (6144, 1.0, 1.0), (30, 1.0, 1.0)])
+                                         (6144, 1.0, 1.0), (30, 1.0, 1.0), (12288, 1.0, 1.0)])
 def test_generic_pcg_testproblem(S, prec, n, eta0, hvar):
     """Eq:Testproblem (§6.2) at generic n: the CUDA solve equals the oracle's solution, and
     the float64 iteration count is the oracle's."""
@@ -289,7 +291,7 @@ def test_generic_rk4_solitary_wave_and_mixed_precision(S):
 
 def test_generic_size_rejections(S):
     sgn, ctx = S
-    for n in (7, 14, 98, 4, 12288, 15, 10240):
+    for n in (7, 14, 98, 4, 15, 18432, 32768):
         with pytest.raises(sgn.SgnError) as e:
             sgn.Layout(ctx, [sgn.Grid(1, n, 1.0)])
         assert e.value.status == 2, n
