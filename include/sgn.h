@@ -24,8 +24,10 @@
  *    is row-major [ny][nx] (x fastest).
  *  - Grid (§6.1): x_j = j Lx/nx; spectral derivatives D = F^{-1}(iK)F with
  *    k_j = 2 pi j/L, j = -n/2+1..n/2-1, and the n/2 wavenumber set to 0.
- *    nx, ny must be powers of two; 1d needs 8 <= nx <= 16384 (nx = 16384 runs each solve
- *    and right-hand side on a thread-block cluster of two CTAs), 2d 8 <= nx, ny <= 1024.
+ *    Sizes: a power of two (1d 8 <= nx <= 16384, where nx = 16384 runs each solve and
+ *    right-hand side on a thread-block cluster of two CTAs; 2d 8 <= nx, ny <= 1024), or
+ *    n = 2^a 3^b 5^c with a >= 1 (1d 6 <= nx <= 16384; 2d 6 <= nx, ny <= 1024) on generic
+ *    kernels (see sgn_layout_create for what they serve).
  */
 #ifndef SGN_H
 #define SGN_H
@@ -109,7 +111,13 @@ const char* sgn_status_string(sgn_status s);
  * the coefficients, G, A^{-1}, PCG (both precisions), GMRES, the right-hand side and the
  * RK4 / Adams-Bashforth steppers; dealiasing, SBDF2 (sgn_step_linimp), the non-constraint
  * stepper and sgn_pcg1d_noalloc take powers of two only (SGN_ERR_UNSUPPORTED_SIZE).  2d
- * grids: powers of two, 8 <= nx, ny <= 1024.  Other sizes: SGN_ERR_UNSUPPORTED_SIZE.  A 2d layout of
+ * sides: powers of two with 8 <= n <= 1024, or n = 2^a 3^b 5^c (a >= 1) with
+ * 6 <= n <= 1024 (such as 384 x 240).  A 2d grid with a side that is not a power of two
+ * runs on generic kernels (full complex spectra, mixed-radix row and column passes) for
+ * the same calls as the 1d generic sizes, with host-driven solves (one stream
+ * synchronisation per PCG iteration) and float64 right-hand sides; it takes no batches, no
+ * inner-solve forms (sgn_layout_set_form2d, sgn_profile_inner2d) and the same power-of-two
+ * options as 1d.  Other sizes: SGN_ERR_UNSUPPORTED_SIZE.  A 2d layout of
  * count > 1 (at most 32) is a batch of instances on one grid (every sgn_grid equal); it
  * serves sgn_spectral_grad, sgn_precond_coeffs, sgn_apply_operator, sgn_precond_solve,
  * sgn_pcg and sgn_pcg_async, whose mixed-precision solves advance the float32 inner PCG of

@@ -369,8 +369,7 @@ cudaError_t launch_clustered(void (*kernel)(P...), int num, int threads, size_t 
 
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return raise_smem(kernel, bytes);
 }
 
 }  // namespace d1

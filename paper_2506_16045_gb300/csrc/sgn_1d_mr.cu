@@ -14,157 +14,19 @@
 #include <vector>
 
 #include "sgn_1d_dev.cuh"
+#include "sgn_mr_fft.cuh"
 
 namespace sgn {
 namespace {
 
 using d1::kPi;
+using mr::MrPlan;
+using mr::mr_plan;
+using mr::k_mr_twiddles;
 constexpr int kMrNT = 256;
 constexpr int kMrMaxN = 16384;       // largest generic n
 constexpr int kMrSmemN = 6144;       // largest n whose two transform buffers (192 KB) are in
                                      // shared memory; above it they are in global memory
-constexpr int kMrMaxStages = 16;
-
-// ---- plan: radices in order (8 ... 8, then 4 or 2, then 5 ... 5, then 3 ... 3) ------------
-struct MrPlan {
-  int n, ns;
-  int n8, r42, n5;       // radix-8 stages, the 4 or 2 stage (0: none), radix-5 stages
-  __host__ __device__ int radix(int st) const {
-    if (st < n8) return 8;
-    st -= n8;
-    if (r42) {
-      if (st == 0) return r42;
-      --st;
-    }
-    return st < n5 ? 5 : 3;
-  }
-};
-
-__host__ __device__ inline bool mr_plan(int n, MrPlan& P) {
-  int a = 0, b = 0, c = 0, m = n;
-  while (m % 2 == 0) { m /= 2; ++a; }
-  while (m % 3 == 0) { m /= 3; ++b; }
-  while (m % 5 == 0) { m /= 5; ++c; }
-  if (m != 1 || a < 1) return false;
-  P.n = n;
-  P.n8 = a / 3;
-  P.r42 = a % 3 == 2 ? 4 : (a % 3 == 1 ? 2 : 0);
-  P.n5 = c;
-  P.ns = P.n8 + (P.r42 != 0) + c + b;
-  return P.ns <= kMrMaxStages;
-}
-
-// ---- small DFTs in registers, natural order --------------------------------------------
-template <typename T>
-__device__ __forceinline__ cplx<T> mul_i(cplx<T> a, bool inv) {   // * (-+i)
-  return inv ? mul_pi(a) : mul_mi(a);
-}
-
-template <typename T, int R>
-__device__ __forceinline__ void mr_dft(cplx<T>* x, bool inv) {
-  if constexpr (R == 2) {
-    const cplx<T> a = x[0], b = x[1];
-    x[0] = a + b;
-    x[1] = a - b;
-  } else if constexpr (R == 4) {
-    const cplx<T> s02 = x[0] + x[2], d02 = x[0] - x[2], s13 = x[1] + x[3], d13 = x[1] - x[3];
-    const cplx<T> r13 = mul_i(d13, inv);
-    x[0] = s02 + s13;
-    x[1] = d02 + r13;
-    x[2] = s02 - s13;
-    x[3] = d02 - r13;
-  } else if constexpr (R == 3) {
-    // y1,2 = x0 - (x1 + x2)/2 -+ i (sqrt3/2)(x1 - x2)
-    const T h3 = num<T>(0.86602540378443864676);
-    const cplx<T> s = x[1] + x[2], d = x[1] - x[2];
-    const cplx<T> m = x[0] - mk(half(s.x), half(s.y));
-    const cplx<T> t = mul_i(d, inv) * h3;
-    x[0] = x[0] + s;
-    x[1] = m + t;
-    x[2] = m - t;
-  } else if constexpr (R == 5) {
-    // y_s = sum_r x_r w^{r s}, w = e^{-+2 pi i / 5}, pairing r and 5 - r
-    const T c1 = num<T>(0.30901699437494742410), c2 = num<T>(-0.80901699437494742410);
-    const T s1 = num<T>(0.95105651629515357212), s2 = num<T>(0.58778525229247312917);
-    const cplx<T> a1 = x[1] + x[4], b1 = x[1] - x[4], a2 = x[2] + x[3], b2 = x[2] - x[3];
-    const cplx<T> m1 = x[0] + a1 * c1 + a2 * c2, m2 = x[0] + a1 * c2 + a2 * c1;
-    // -+i (s1 b1 + s2 b2) and -+i (s2 b1 - s1 b2)
-    const cplx<T> t1 = mul_i(b1 * s1 + b2 * s2, inv), t2 = mul_i(b1 * s2 - b2 * s1, inv);
-    x[0] = x[0] + a1 + a2;
-    x[1] = m1 + t1;
-    x[4] = m1 - t1;
-    x[2] = m2 + t2;
-    x[3] = m2 - t2;
-  } else {
-    // 8 = 2 x 4
-    cplx<T> e[4] = {x[0], x[2], x[4], x[6]}, o[4] = {x[1], x[3], x[5], x[7]};
-    mr_dft<T, 4>(e, inv);
-    mr_dft<T, 4>(o, inv);
-    const T r = num<T>(0.70710678118654752440);
-    const cplx<T> o1 = o[1], o3 = o[3];
-    const cplx<T> w1 = inv ? mk((o1.x - o1.y) * r, (o1.x + o1.y) * r)
-                           : mk((o1.x + o1.y) * r, (o1.y - o1.x) * r);
-    const cplx<T> w2 = mul_i(o[2], inv);
-    const cplx<T> w3 = inv ? mk(-(o3.x + o3.y) * r, (o3.x - o3.y) * r)
-                           : mk((o3.y - o3.x) * r, -(o3.x + o3.y) * r);
-    x[0] = e[0] + o[0];
-    x[4] = e[0] - o[0];
-    x[1] = e[1] + w1;
-    x[5] = e[1] - w1;
-    x[2] = e[2] + w2;
-    x[6] = e[2] - w2;
-    x[3] = e[3] + w3;
-    x[7] = e[3] - w3;
-  }
-}
-
-// One radix-R Stockham stage at sub-length p: butterfly i reads src[i + r n/R], twiddles by
-// w^{r k} (k = i mod p, table block at p - 1: entry (r - 1) p + k), writes output s to
-// dst[(i - k) R + k + s p].
-template <typename T, int R>
-__device__ __forceinline__ void mr_stage(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst,
-                                         int n, int p, bool inv, const cplx<T>* __restrict__ tw) {
-  const int q = n / R;
-  for (int i = threadIdx.x; i < q; i += kMrNT) {
-    const int k = i % p;
-    cplx<T> x[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = src[i + r * q];
-    if (p > 1) {
-#pragma unroll
-      for (int r = 1; r < R; ++r) x[r] = cmul_tw(x[r], tw[p - 1 + (r - 1) * p + k], inv);
-    }
-    mr_dft<T, R>(x, inv);
-    const int o = (i - k) * R + k;
-#pragma unroll
-    for (int s = 0; s < R; ++s) dst[o + s * p] = x[s];
-  }
-  __syncthreads();
-}
-
-// The transform of a (length n, natural order) with b as the other buffer; returns the
-// buffer holding the result.  Forward: X_m = sum_j x_j e^{-2 pi i j m / n}; inverse without
-// the 1/n.  Callers synchronise before it; it returns after a barrier.
-template <typename T>
-__device__ cplx<T>* mr_fft(cplx<T>* a, cplx<T>* b, const MrPlan& P, bool inv,
-                           const cplx<T>* tw) {
-  cplx<T>* src = a;
-  cplx<T>* dst = b;
-  int p = 1;
-  for (int st = 0; st < P.ns; ++st) {
-    const int R = P.radix(st);
-    if (R == 8) mr_stage<T, 8>(src, dst, P.n, p, inv, tw);
-    else if (R == 4) mr_stage<T, 4>(src, dst, P.n, p, inv, tw);
-    else if (R == 2) mr_stage<T, 2>(src, dst, P.n, p, inv, tw);
-    else if (R == 5) mr_stage<T, 5>(src, dst, P.n, p, inv, tw);
-    else mr_stage<T, 3>(src, dst, P.n, p, inv, tw);
-    p *= R;
-    cplx<T>* t = src;
-    src = dst;
-    dst = t;
-  }
-  return src;
-}
 
 // wavenumber of mode m (Nyquist 0), in T
 template <typename T>
@@ -214,11 +76,11 @@ template <typename T>
 __device__ __forceinline__ cplx<T>* mr_deriv_pair(cplx<T>* A, cplx<T>* B, const MrPlan& P,
                                                   double kunit, const cplx<T>* tw) {
   const int n = P.n;
-  cplx<T>* F = mr_fft<T>(A, B, P, false, tw);
+  cplx<T>* F = mr::mr_fft<T, kMrNT>(A, B, P, false, tw);
   const double inv_n = 1.0 / n;
   for (int m = threadIdx.x; m < n; m += kMrNT) F[m] = mul_pi(F[m]) * num<T>(kunit * wave_index(m, n) * inv_n);
   __syncthreads();
-  return mr_fft<T>(F, F == A ? B : A, P, true, tw);
+  return mr::mr_fft<T, kMrNT>(F, F == A ? B : A, P, true, tw);
 }
 
 // ---- operators (float64) ----------------------------------------------------------------
@@ -247,7 +109,7 @@ __device__ void mr_matvec(cplx<T>* a, cplx<T>* b, const MrPlan& P, double kunit,
   // a holds V (full spectrum); form (1 - k) V in place
   for (int m = threadIdx.x; m < n; m += kMrNT) a[m] = a[m] * (num<T>(1.0) - mr_k<T>(m, n, kunit));
   __syncthreads();
-  cplx<T>* z = mr_fft<T>(a, b, P, true, tw);
+  cplx<T>* z = mr::mr_fft<T, kMrNT>(a, b, P, true, tw);
   const T inv_n = num<T>(1.0 / n);
   for (int j = threadIdx.x; j < n; j += kMrNT) {
     const T v = z[j].x * inv_n, vx = z[j].y * inv_n;
@@ -256,7 +118,7 @@ __device__ void mr_matvec(cplx<T>* a, cplx<T>* b, const MrPlan& P, double kunit,
     z[j] = mk(c1 * v + c2 * vx, c2 * v + c3 * vx);
   }
   __syncthreads();
-  cplx<T>* Y = mr_fft<T>(z, z == a ? b : a, P, false, tw);
+  cplx<T>* Y = mr::mr_fft<T, kMrNT>(z, z == a ? b : a, P, false, tw);
   for (int m = threadIdx.x; m <= h; m += kMrNT) {
     const T k = mr_k<T>(m, n, kunit);
     const cplx<T> y = Y[m], ym = conj(Y[(n - m) % n]);
@@ -291,7 +153,7 @@ __global__ void __launch_bounds__(kMrNT) k_mr_apply_G(const MrArgs A, const doub
   const double kunit = 2.0 * kPi / I.L;
   for (int j = threadIdx.x; j < n; j += kMrNT) a[j] = mk(u[I.off + j], 0.0);
   __syncthreads();
-  cplx<double>* V = mr_fft<double>(a, b, P, false, tw);
+  cplx<double>* V = mr::mr_fft<double, kMrNT>(a, b, P, false, tw);
   cplx<double>* o = V == a ? b : a;
   // (G u)^ of modes 0..n/2 into V itself: mode m is read and written only by the thread
   // that computes it (its mirror n - m is above n/2 and never written)
@@ -300,7 +162,7 @@ __global__ void __launch_bounds__(kMrNT) k_mr_apply_G(const MrArgs A, const doub
   for (int m = threadIdx.x; m < h; m += kMrNT)
     if (m > 0) V[n - m] = conj(V[m]);
   __syncthreads();
-  const cplx<double>* x = mr_fft<double>(V, o, P, true, tw);
+  const cplx<double>* x = mr::mr_fft<double, kMrNT>(V, o, P, true, tw);
   for (int j = threadIdx.x; j < n; j += kMrNT) Gu[I.off + j] = x[j].x / n;
 }
 
@@ -318,13 +180,13 @@ __global__ void __launch_bounds__(kMrNT) k_mr_precond(const MrArgs A, const Solv
   const double kunit = 2.0 * kPi / I.L, sigma = rec[id].sigma, alpha = rec[id].alpha;
   for (int j = threadIdx.x; j < n; j += kMrNT) a[j] = mk(r[I.off + j], 0.0);
   __syncthreads();
-  cplx<double>* F = mr_fft<double>(a, b, P, false, tw);
+  cplx<double>* F = mr::mr_fft<double, kMrNT>(a, b, P, false, tw);
   for (int m = threadIdx.x; m < n; m += kMrNT) {
     const double k = kunit * wave_index(m, n);
     F[m] = F[m] * (1.0 / ((sigma + alpha * k * k) * (double)n));
   }
   __syncthreads();
-  const cplx<double>* x = mr_fft<double>(F, F == a ? b : a, P, true, tw);
+  const cplx<double>* x = mr::mr_fft<double, kMrNT>(F, F == a ? b : a, P, true, tw);
   for (int j = threadIdx.x; j < n; j += kMrNT) z[I.off + j] = x[j].x;
 }
 
@@ -420,7 +282,7 @@ __global__ void __launch_bounds__(kMrNT) k_mr_pcg(const MrArgs A, const MrPcgArg
   cplx<double>* d1 = tbuf<double>(A, I, 1);
   for (int j = threadIdx.x; j < n; j += kMrNT) d0[j] = mk(a.b[I.off + j], a.x[I.off + j]);
   __syncthreads();
-  cplx<double>* Y = mr_fft<double>(d0, d1, P, false, tws.d);
+  cplx<double>* Y = mr::mr_fft<double, kMrNT>(d0, d1, P, false, tws.d);
   cplx<double>* Bh = ws;            // float64 path: b^, x^, r^, p^, (G p)^ in slots 0..4
   cplx<double>* Xh = ws + S;
   double bb = 0.0;
@@ -496,7 +358,7 @@ __global__ void __launch_bounds__(kMrNT) k_mr_pcg(const MrArgs A, const MrPcgArg
     R.ratio = sqrt(rz) / bnorm;
     __syncthreads();
     mr_full<double>(d0, Xh, n);
-    const cplx<double>* x = mr_fft<double>(d0, d1, P, true, tws.d);
+    const cplx<double>* x = mr::mr_fft<double, kMrNT>(d0, d1, P, true, tws.d);
     for (int j = threadIdx.x; j < n; j += kMrNT) a.x[I.off + j] = x[j].x / n;
   } else {
     // double-float refinement: b^ and x^ (slots 0, 1) and the residual (slot 4) in
@@ -616,7 +478,7 @@ __global__ void __launch_bounds__(kMrNT) k_mr_pcg(const MrArgs A, const MrPcgArg
     R.ratio = ratio;
     __syncthreads();
     mr_full<df>(h0, Xd, n);
-    const cplx<df>* x = mr_fft<df>(h0, h1, P, true, tws.h);
+    const cplx<df>* x = mr::mr_fft<df, kMrNT>(h0, h1, P, true, tws.h);
     const df inv_n(1.0 / n);
     for (int j = threadIdx.x; j < n; j += kMrNT) a.x[I.off + j] = to_f64(x[j].x * inv_n);
   }
@@ -705,28 +567,6 @@ __global__ void __launch_bounds__(kMrNT) k_mr_rhs(const MrArgs A, double g, cons
   }
 }
 
-// e^{-2 pi i r k / (p R)} of every stage of n's plan, in float64, float32 and double-float
-__global__ void k_mr_twiddles(int n, cplx<double>* t64, cplx<float>* t32, cplx<df>* tdf) {
-  MrPlan P;
-  mr_plan(n, P);
-  int p = 1;
-  for (int st = 0; st < P.ns; ++st) {
-    const int R = P.radix(st);
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < (R - 1) * p;
-         e += gridDim.x * blockDim.x) {
-      const int r = 1 + e / p, k = e - (r - 1) * p;
-      // the angle -2 r k / (p R) in units of pi, reduced exactly: (r k mod pR) / (pR)
-      const long long num_ = (long long)r * k % ((long long)p * R);
-      double sn, cs;
-      sincospi(-2.0 * (double)num_ / (double)(p * R), &sn, &cs);
-      t64[p - 1 + e] = mk(cs, sn);
-      t32[p - 1 + e] = mk((float)cs, (float)sn);
-      tdf[p - 1 + e] = mk(df(cs), df(sn));
-    }
-    p *= R;
-  }
-}
-
 // ---- launchers (one launch over the generic instances ids[first, first + num)) ---------
 MrArgs mr_args(const Layout1d& lay, int first) {
   MrArgs A;
@@ -741,14 +581,14 @@ MrArgs mr_args(const Layout1d& lay, int first) {
   return A;
 }
 
-// two transform buffers of the layout's largest generic n up to kMrSmemN, 16 bytes per entry.  The tables
-// lie back to back (float64, float32, double-float; mr_tw_len entries each, an even count
-// so that the double-float table starts on a 16-byte boundary).
+// Two transform buffers of the layout's largest generic n up to kMrSmemN, 16 bytes per
+// entry.  The twiddle tables lie back to back (float64, float32, double-float; mr_tw_len
+// entries each, an even count so that the double-float table starts on a 16-byte boundary).
 size_t mr_smem(const Layout1d& lay) { return (size_t)2 * 16 * lay.mr_smem_n; }
 
 template <typename K>
 cudaError_t mr_attr(K k, size_t sm) {
-  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  return raise_smem(k, sm);
 }
 
 }  // namespace

@@ -794,8 +794,7 @@ __global__ void k2_axpby(long long HP, void* o1, void* o2, const void* a1, const
 
 template <typename K>
 cudaError_t smem_attr(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return raise_smem(kernel, bytes);
 }
 
 // Columns per CTA for this layout: 2, or 4 for float32 planes when 2-column tiles would not
@@ -1023,6 +1022,21 @@ PInst2d pinst_of(const Layout2d& L) {
 
 }  // namespace
 
+namespace {
+
+// The cached solve graphs and their source graphs (kept until the executable graph goes).
+void drop_solve_graphs(const Layout2d& L) {
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      if (L.solve_exec[i][j]) cudaGraphExecDestroy(L.solve_exec[i][j]);
+      if (L.solve_graph[i][j]) cudaGraphDestroy(L.solve_graph[i][j]);
+      L.solve_exec[i][j] = nullptr;
+      L.solve_graph[i][j] = nullptr;
+    }
+}
+
+}  // namespace
+
 cudaError_t layout2d_create(Layout2d& L, const sgn_grid& g) {
   L.nx = g.nx;
   L.ny = g.ny;
@@ -1036,6 +1050,13 @@ cudaError_t layout2d_create(Layout2d& L, const sgn_grid& g) {
   L.H = g.nx / 2 + 1;
   L.HP = (long long)g.ny * L.H;
   cudaError_t e;
+  if ((1 << L.lx) != g.nx || (1 << L.ly) != g.ny) {
+    // a side that is not a power of two: the generic kernels (coefficients use parts, sc)
+    if ((e = cudaMalloc(&L.parts, sizeof(double) * 5 * kMaxParts))) return e;
+    if ((e = cudaMalloc(&L.sc, sizeof(Scal2d)))) return e;
+    if ((e = cudaMemset(L.sc, 0, sizeof(Scal2d)))) return e;
+    return mr2d_create(L);
+  }
   if ((e = cudaMalloc(&L.vec, (size_t)16 * L.HP * 14))) return e;
   if ((e = cudaMalloc(&L.tp, (size_t)16 * L.HP * 4))) return e;
   if ((e = cudaMalloc(&L.coef, sizeof(float) * 6 * L.P))) return e;
@@ -1083,17 +1104,14 @@ PersistArgs2d persist_args(const Layout2d& L, const void* tw32) {
 }  // namespace
 
 void layout2d_destroy(Layout2d& L) {
+  mr2d_destroy(L);
   if (L.prof) {
     for (auto v : L.prof->a) cudaEventDestroy(v);
     for (auto v : L.prof->b) cudaEventDestroy(v);
     delete L.prof;
     L.prof = nullptr;
   }
-  for (auto& row : L.solve_exec)
-    for (auto& ex : row) {
-      if (ex) cudaGraphExecDestroy(ex);
-      ex = nullptr;
-    }
+  drop_solve_graphs(L);
   cudaFree(L.stage);
   cudaFree(L.stage_rec);
   L.stage = nullptr;
@@ -1121,12 +1139,9 @@ void layout2d_destroy(Layout2d& L) {
 }
 
 cudaError_t layout2d_set_inner_form(Layout2d& L, int form, int tile_width) {
+  if (L.mr) return cudaErrorNotSupported;            // no persistent form
   if (form == L.inner_form && tile_width == L.p_tw) return cudaSuccess;
-  for (auto& row : L.solve_exec)
-    for (auto& ex : row) {
-      if (ex) cudaGraphExecDestroy(ex);
-      ex = nullptr;
-    }
+  drop_solve_graphs(L);
   L.inner_form = form;
   L.p_tw = tile_width;
   return cudaSuccess;
@@ -1140,6 +1155,7 @@ size_t layout2d_res_bytes(const Layout2d& L) { return (size_t)16 * 2 * (L.HP > 0
 
 cudaError_t launch_grad2d(const Layout2d& L, const void* tw64, const double* f, double* gradf,
                           cudaStream_t s) {
+  if (L.mr) return mr2d_grad(L, f, gradf, s);
   // forward transform of f (paired with zero), i k, inverse of both components
   cudaError_t e = rows_r2c<double>(L, tw64, nullptr, f, nullptr, nullptr, nullptr,
                                    tplane(L, 0), tplane(L, 3), nullptr, nullptr, 1, s);
@@ -1183,6 +1199,7 @@ __global__ void k2_sub(long long P, const double* a, const double* b, double* ou
 
 cudaError_t launch_dealias2d(const Layout2d& L, const void* tw64, const double* h, double* eta,
                              double* U, double* u, cudaStream_t s) {
+  if (L.mr) return cudaErrorNotSupported;
   const Modes2d M = modes_of(L);
   double* zs = L.rhs_w;                        // zeta = eta - h (a free real plane here)
   k2_sub<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, eta, h, zs, -1.0);
@@ -1268,6 +1285,7 @@ __global__ void k2_nc_c(long long P, const double* __restrict__ phx, const doubl
 cudaError_t launch_rhs_nc2d(const Layout2d& L, const void* tw64, double g, const double* eta,
                             const double* u, const double* h, const double* gradh, double* f_eta,
                             double* M, cudaStream_t s) {
+  if (L.mr) return cudaErrorNotSupported;
   const long long P = L.P;
   double* w = L.rhs_w;                          // free real planes here
   auto pl = [&](int k) { return w + (long long)k * P; };
@@ -1303,6 +1321,7 @@ cudaError_t launch_coeffs2d(const Layout2d& L, const double* eta, const double* 
 
 cudaError_t launch_apply_G2d(const Layout2d& L, const void* tw64, const double* eta,
                              const double* gradh, const double* u, double* Gu, cudaStream_t s) {
+  if (L.mr) return mr2d_apply_G(L, eta, gradh, u, Gu, s);
   k2_coef_planes<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, eta, gradh, L.coef, L.coef_lo, L.ehh);
   cudaError_t e = cudaGetLastError();
   if (e) return e;
@@ -1316,6 +1335,7 @@ cudaError_t launch_apply_G2d(const Layout2d& L, const void* tw64, const double* 
 
 cudaError_t launch_precond2d(const Layout2d& L, const void* tw64, const SolveRec* rec,
                              const double* r, double* z, cudaStream_t s) {
+  if (L.mr) return mr2d_precond(L, rec, r, z, s);
   cudaError_t e = r2c_vec<double>(L, tw64, nullptr, r, slot(L, 0), slot(L, 1), s);
   if (e) return e;
   const Modes2d M = modes_of(L);
@@ -1469,7 +1489,7 @@ cudaError_t add_while(cudaStream_t cs, cudaGraphConditionalHandle h, cudaGraph_t
 // conditions k2_decide, k2_inner_start and k2_update set.  Inputs come from L.stage,
 // options from sc (k2_set_opts), the report goes to L.stage_rec[1].
 cudaError_t build_solve_graph(const Layout2d& L, const void* tw64, const void* tw32, bool mixed,
-                              bool given, cudaGraphExec_t* out) {
+                              bool given, cudaGraphExec_t* out, cudaGraph_t* src) {
   const Modes2d M = modes_of(L);
   const long long P = L.P;
   const double* eta = L.stage;
@@ -1622,9 +1642,13 @@ cudaError_t build_solve_graph(const Layout2d& L, const void* tw64, const void* t
   for (int i = 2; i >= 0; --i)
     if (capturing & (1 << i)) end(i);          // a failed build: close its captures
   if (!e) e = cudaGraphInstantiate(out, g, 0);
-  if (g) cudaGraphDestroy(g);
   for (auto& c : cs)
     if (c) cudaStreamDestroy(c);
+  // the source graph lives as long as its executable graph (both go in drop_solve_graphs).
+  // A graph whose build failed is left alone: destroying one whose capture into a
+  // conditional node's body had failed crashed the driver.  The layout then solves on the
+  // host-driven path, so this happens at most once per layout.
+  if (!e) *src = g;
   return e;
 }
 
@@ -1634,6 +1658,9 @@ cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, 
                          const double* eta, const double* gradh, const double* b, double* x,
                          const SolveRec* given, int kind, double rtol, double rtol_inner,
                          int maxit, int max_refine, SolveRec* rec, cudaStream_t s) {
+  if (L.mr)
+    return mr2d_pcg(L, precision, eta, gradh, b, x, given, kind, rtol, rtol_inner, maxit,
+                    max_refine, rec, s);
   const Modes2d M = modes_of(L);
   cudaError_t e;
   // ---- device-driven: one graph launch between staging copies
@@ -1642,7 +1669,8 @@ cudaError_t launch_pcg2d(const Layout2d& L, const void* tw64, const void* tw32, 
       cst == cudaStreamCaptureStatusNone) {
     const int mi = precision == SGN_PREC_MIXED ? 1 : 0, gi = given ? 1 : 0;
     cudaGraphExec_t& ex = L.solve_exec[mi][gi];
-    if (!ex && build_solve_graph(L, tw64, tw32, mi == 1, gi == 1, &ex) != cudaSuccess) {
+    if (!ex && build_solve_graph(L, tw64, tw32, mi == 1, gi == 1, &ex,
+                                 &L.solve_graph[mi][gi]) != cudaSuccess) {
       cudaGetLastError();
       ex = nullptr;
       L.solve_graph_off = true;
@@ -2075,6 +2103,7 @@ cudaError_t rhs2d(const Layout2d& L, const void* tw64, const void* tw32, double 
 cudaError_t launch_rhs2d(const Layout2d& L, const void* tw64, const void* tw32, int precision,
                          double g, const double* eta, const double* u, const double* h,
                          const double* gradh, double* f_eta, double* f_U, cudaStream_t s) {
+  if (L.mr) return mr2d_rhs(L, g, eta, u, h, gradh, f_eta, f_U, s);
   return precision == SGN_PREC_MIXED
              ? rhs2d<df>(L, tw64, tw32, g, eta, u, h, gradh, f_eta, f_U, s)
              : rhs2d<double>(L, tw64, tw32, g, eta, u, h, gradh, f_eta, f_U, s);
@@ -2105,6 +2134,7 @@ cudaError_t launch_lincomb2d(const Layout2d& L, const double* dt, double* out,
 cudaError_t launch_linimp_res2d(const Layout2d& L, const void* tw64, const SolveRec* A,
                                 const double* eta, const double* gradh, const double* u,
                                 const double* U, void* res_hat, cudaStream_t s) {
+  if (L.mr) return cudaErrorNotSupported;
   // res^ = A u^ - (G u)^ + U^, float64, stored as two half planes in res_hat
   k2_coef_planes<<<grid_for(L.P, 256), 256, 0, s>>>(L.P, eta, gradh, L.coef, L.coef_lo, L.ehh);
   cudaError_t e = cudaGetLastError();
@@ -2126,6 +2156,7 @@ cudaError_t launch_linimp_res2d(const Layout2d& L, const void* tw64, const Solve
 cudaError_t launch_linimp_solve2d(const Layout2d& L, const void* tw64, const SolveRec* A,
                                   const void* res1_hat, const void* res0_hat, double c1,
                                   double c0, double* u, cudaStream_t s) {
+  if (L.mr) return cudaErrorNotSupported;
   const char* r1 = static_cast<const char*>(res1_hat);
   const char* r0 = static_cast<const char*>(res0_hat);
   const size_t off = (size_t)16 * L.HP;

@@ -40,6 +40,7 @@ struct Layout2d {
   // first use, and the buffers its kernels address: staged eta [P], grad h [2P], b [2P],
   // x [2P], and two solve records (given coefficients in, report out).
   mutable cudaGraphExec_t solve_exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  mutable cudaGraph_t solve_graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // sources
   mutable bool solve_graph_off = false;   // building one failed: host-driven solves
   double* stage = nullptr;
   SolveRec* stage_rec = nullptr;
@@ -56,6 +57,15 @@ struct Layout2d {
   // non-null while profiling: mixed solves take the host-driven path and bracket each
   // persistent launch with events
   Prof2d* prof = nullptr;
+  // Grids whose nx or ny is not a power of two (sgn_2d_mr.cu): full complex spectra,
+  // host-driven solves.  Of the buffers above only parts and sc are allocated.
+  bool mr = false;
+  void* mr_twx = nullptr;      // twiddles of nx: float64, float32, double-float tables
+  void* mr_twy = nullptr;      // of ny
+  long long mr_lenx = 0, mr_leny = 0;   // entries per table (even)
+  void* mr_w = nullptr;        // kMr2dPlanes complex-double planes of P
+  double* mr_dev = nullptr;    // dot-product partials and results
+  double* mr_host = nullptr;   // pinned copies of the results
 };
 
 // A batch of B >= 2 instances on one grid: B single-instance layouts (instance 0 is the
@@ -75,6 +85,24 @@ struct Batch2d {
 };
 
 cudaError_t layout2d_create(Layout2d& L, const sgn_grid& g);
+
+// ---- grids with a side that is not a power of two (sgn_2d_mr.cu) --------------------------
+// A side n = 2^a 3^b 5^c (a >= 1) with 6 <= n <= 1024.
+bool mr2d_side_ok(int n);
+cudaError_t mr2d_create(Layout2d& L);
+void mr2d_destroy(Layout2d& L);
+cudaError_t mr2d_grad(const Layout2d& L, const double* f, double* gradf, cudaStream_t s);
+cudaError_t mr2d_apply_G(const Layout2d& L, const double* eta, const double* gradh,
+                         const double* u, double* Gu, cudaStream_t s);
+cudaError_t mr2d_precond(const Layout2d& L, const SolveRec* rec, const double* r, double* z,
+                         cudaStream_t s);
+cudaError_t mr2d_pcg(const Layout2d& L, int precision, const double* eta, const double* gradh,
+                     const double* b, double* x, const SolveRec* given, int kind, double rtol,
+                     double rtol_inner, int maxit, int max_refine, SolveRec* rec,
+                     cudaStream_t s);
+cudaError_t mr2d_rhs(const Layout2d& L, double g, const double* eta, const double* u,
+                     const double* h, const double* gradh, double* f_eta, double* f_U,
+                     cudaStream_t s);
 cudaError_t batch2d_create(Batch2d& Bt, Layout2d& first, const sgn_grid& g, int B);
 void batch2d_destroy(Batch2d& Bt);
 // Batched constraint solves of the B instances (fields packed as the ABI's batches: scalar

@@ -747,9 +747,7 @@ bool persist2d_tile_ok(int nx, int ny, int tw) {
 cudaError_t persist2d_grid(int nx, int ny, int B, int* grid) {
   const size_t smem = persist2d_smem(nx, ny, 1);
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k2_pcg_persist, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(smem > 48 * 1024 ? smem : 48 * 1024))))
-    return e;
+  if ((e = raise_smem(k2_pcg_persist, smem))) return e;
   int dev = 0, sms = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev))) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;

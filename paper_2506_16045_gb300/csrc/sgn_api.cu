@@ -345,10 +345,10 @@ sgn_status cuda_fail(sgn_ctx* ctx, cudaError_t e, const char* where) {
 
 inline cudaStream_t as_stream(sgn_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// a 1d layout holding sizes that are not powers of two (the generic kernels)
+// a layout holding sizes that are not powers of two (the generic kernels)
 bool has_generic(const sgn_layout* lay) {
-  return lay->dim == 1 &&
-         lay->l1.class_end[sgn::kGenericClass] > lay->l1.class_begin[sgn::kGenericClass];
+  if (lay->dim == 2) return lay->l2.mr;
+  return lay->l1.class_end[sgn::kGenericClass] > lay->l1.class_begin[sgn::kGenericClass];
 }
 
 int ilog2_exact(int n) {
@@ -440,6 +440,7 @@ extern "C" sgn_status sgn_profile_enable(sgn_ctx* ctx, int on) {
 extern "C" sgn_status sgn_profile_inner2d(sgn_layout* lay, int on, double* ms,
                                           long long* launches, long long* iterations) {
   if (check_layout(lay) || lay->dim != 2) return SGN_ERR_INVALID_ARG;
+  if (lay->l2.mr) return SGN_ERR_UNSUPPORTED_SIZE;    // no persistent inner solve
   DeviceGuard g(lay->device);
   sgn::Layout2d& L = lay->l2;
   double t = 0.0;
@@ -538,8 +539,13 @@ extern "C" sgn_status sgn_layout_create(sgn_ctx* ctx, int count, const sgn_grid*
                   "1d nx must be a power of two in [8, 16384] or 2^a 3^b 5^c (a >= 1) in [6, 16384]");
     if (dim == 2) {
       const int ly = ilog2_exact(g.ny);
-      if (lx < 3 || ly < 3 || lx > 10 || ly > 10)
-        return fail(ctx, SGN_ERR_UNSUPPORTED_SIZE, "2d nx, ny must be powers of two in [8, 1024]");
+      auto side = [](int n, int l) { return (l >= 3 && l <= 10) || sgn::mr2d_side_ok(n); };
+      if (!side(g.nx, lx) || !side(g.ny, ly))
+        return fail(ctx, SGN_ERR_UNSUPPORTED_SIZE,
+                    "2d nx, ny must be powers of two in [8, 1024] or 2^a 3^b 5^c (a >= 1) "
+                    "in [6, 1024]");
+      if (count > 1 && (lx < 0 || ly < 0))
+        return fail(ctx, SGN_ERR_UNSUPPORTED_SIZE, "2d batches take power-of-two grids");
     }
   }
   sgn_layout* lay = new (std::nothrow) sgn_layout();
@@ -759,6 +765,7 @@ extern "C" sgn_status sgn_layout_set_form2d(sgn_layout* lay, int inner, int tile
       (tile_width != 0 && tile_width != 1 && tile_width != 2 && tile_width != 4))
     return fail(lay ? lay->ctx : nullptr, SGN_ERR_INVALID_ARG, "set_form2d args");
   sgn::Layout2d& L = lay->l2;
+  if (L.mr) return fail(lay->ctx, SGN_ERR_UNSUPPORTED_SIZE, "no inner-solve forms on this grid");
   const int tw = tile_width ? tile_width : sgn::persist2d_tile_width(L.nx, L.ny, 1, L.p_grid);
   if (!sgn::persist2d_tile_ok(L.nx, L.ny, tw))
     return fail(lay->ctx, SGN_ERR_UNSUPPORTED_SIZE, "tile width too wide for this grid");
@@ -1978,6 +1985,7 @@ extern "C" sgn_status sgn_state_autotune(sgn_state* st, const double* dt, const 
     cudaStream_t s = as_stream(stream);
     SGN_TRY(check_opts(st, opts));
     SGN_TRY(upload_dt(st, dt, s));
+    if (lay->l2.mr) return SGN_OK;                 // one form: nothing to choose
     return autotune_2d(st, opts, s, best_ms);
   }
   sgn_ctx* ctx = lay->ctx;

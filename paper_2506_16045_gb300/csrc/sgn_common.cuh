@@ -15,6 +15,27 @@
 
 namespace sgn {
 
+// Raises a kernel's dynamic shared-memory limit to the most the device allows it (the opt-in
+// maximum less the kernel's static shared memory) when a launch needs more than the default
+// 48 KB.  Every caller writes the same value for a kernel, so layouts of different sizes
+// (and threads) never lower the limit under one another's launches: a limit set to each
+// layout's own size let a smaller layout's setting make a larger layout's later launch fail.
+template <typename K>
+cudaError_t raise_smem(K kernel, size_t bytes) {
+  if (bytes == 0) return cudaSuccess;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e) return e;
+  if (fa.sharedSizeBytes + bytes <= 48 * 1024) return cudaSuccess;   // the default limit
+  int dev = 0, optin = 0;
+  if ((e = cudaGetDevice(&dev)) ||
+      (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)))
+    return e;
+  const long long lim = (long long)optin - (long long)fa.sharedSizeBytes;
+  if (lim < (long long)bytes) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+}
+
 // -------------------------------------------------------------------------------------
 // Double-float number: value = hi + lo with |lo| <= ulp(hi)/2, ~48-bit significand, built
 // from float32 operations only (error-free transformations: Knuth's two-sum and the

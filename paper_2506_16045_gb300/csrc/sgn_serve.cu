@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "../../include/sgn.h"
+#include "sgn_2d.h"
 #include "sgn_internal.h"
 
 namespace sgn {
@@ -146,7 +147,7 @@ constexpr int kInfoSlots = 8192;
 size_t footprint_of(int d, long long N) {
   const size_t io = (size_t)(2 + 3 * d) * 8 * N;          // eta, h, u/b, U, gradh
   const size_t work = d == 1 ? (size_t)260 * N : (size_t)816 * N;
-  const size_t big = (d == 1 && N > 8192) ? (size_t)16 * N : 0;   // global transform buffer
+  const size_t big = (d == 1 && N > 6144) ? (size_t)32 * N : 0;   // global transform buffers
   return io + work + big + (1 << 16);
 }
 
@@ -702,10 +703,12 @@ extern "C" sgn_status sgn_batch_submit(sgn_server* S, const sgn_request* q, uint
   if (!S || !q || !ticket || !q->eta || !q->u_or_b || !q->h) return SGN_ERR_INVALID_ARG;
   const sgn_grid& g = q->grid;
   const int d = g.dim;
+  auto side2 = [](int n) { return pow2_in(n, 8, 1024) || sgn::mr2d_side_ok(n); };
   if (d == 1) {
-    if (g.ny != 1 || !pow2_in(g.nx, 8, 16384)) return SGN_ERR_UNSUPPORTED_SIZE;
+    if (g.ny != 1 || !(pow2_in(g.nx, 8, 16384) || sgn::mr_size_ok(g.nx)))
+      return SGN_ERR_UNSUPPORTED_SIZE;
   } else if (d == 2) {
-    if (!pow2_in(g.nx, 8, 1024) || !pow2_in(g.ny, 8, 1024)) return SGN_ERR_UNSUPPORTED_SIZE;
+    if (!side2(g.nx) || !side2(g.ny)) return SGN_ERR_UNSUPPORTED_SIZE;
   } else {
     return SGN_ERR_INVALID_ARG;
   }

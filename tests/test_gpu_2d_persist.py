@@ -164,3 +164,20 @@ def test_autotune_2d_chooses_a_form_and_restores_the_state(S):
     assert torch.equal(eta, eta2) and torch.equal(u, u2)
     st.close()
     st2.close()
+
+
+def test_layouts_of_other_sizes_leave_a_larger_layout_usable(S):
+    """A layout created after a larger one (a smaller persistent-kernel shared-memory need)
+    must not break the larger layout's later solves: both solve to their known u*."""
+    sgn, ctx = S
+    big = sgn.Layout(ctx, [sgn.Grid(2, 512, 80.0, ny=512, Ly=80.0, g=9.81)])
+    small = sgn.Layout(ctx, [sgn.Grid(2, 64, 20.0, ny=64, Ly=20.0, g=9.81)])
+    for lay, (n, L) in ((big, (512, 80.0)), (small, (64, 20.0)), (big, (512, 80.0))):
+        eta, gh, b, us, _ = bump_problem(n, n, L, L)
+        x = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+        info = sgn.pcg(lay, dev(eta), dev(gh), dev(b), x, rtol=1e-10, maxit=4000,
+                       prec=sgn.PREC_MIXED)[0]
+        assert info["status"] == 0 and info["ratio"] <= 1e-10
+        assert rel(x.cpu().numpy().reshape(2, n, n), us) < 1e-7
+    big.close()
+    small.close()

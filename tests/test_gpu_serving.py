@@ -258,3 +258,38 @@ def test_release_while_other_work_is_in_flight(S):
     assert res[t_run]["status"] == 0
     srv.release(t_run)
     srv.close()
+
+
+def test_2d_runs_and_solves_of_several_sizes(S):
+    """2d solves and 2d runs of several grid sizes interleaved on the 2d lane (each request's
+    layout builds its own solve graph while layouts of other sizes come and go): every
+    request finishes with status 0 and every solve returns its known solution."""
+    sgn, ctx = S
+    srv = sgn.Server(ctx)
+    sizes = [256, 64, 128, 32, 256, 64]
+    tickets, known = [], {}
+    for i, n in enumerate(sizes):
+        c = I.bump2d_case(n=n, L=40.0, a=0.2, x0=10.0, H=0.5, R=3.0, dt=0.05 * 64 / n)
+        g2 = sgn.Grid(2, n, 40.0, g=9.81, ny=n, Ly=40.0)
+        if i % 2 == 0:
+            st, t = srv.submit(sgn.REQ_RUN, g2, dev(c["eta"]), dev(c["u"]), dev(c["h"]),
+                               scheme=sgn.SCHEME_RK4, dt=0.05 * 64 / n, nsteps=20, rtol=1e-10,
+                               prec=sgn.PREC_MIXED)
+        else:
+            gh = O.grad(c["h"], (40.0, 40.0))
+            grid = O.make_grid(2, n, 40.0, 9.81, ny=n, Ly=40.0)
+            b = O.apply_G(c["eta"], gh, c["u"], grid)
+            st, t = srv.submit(sgn.REQ_SOLVE, g2, dev(c["eta"]), dev(b), dev(c["h"]),
+                               rtol=1e-10, prec=sgn.PREC_MIXED)
+            known[t] = (n, c["u"])
+        assert st == 0
+        tickets.append(t)
+    res = wait(srv, tickets, timeout=300.0)
+    for t in tickets:
+        assert res[t]["status"] == 0, res[t]
+        if t in known:
+            n, u = known[t]
+            x = sgn.device_array(res[t]["u"], 2 * n * n).cpu().numpy().reshape(2, n, n)
+            assert np.linalg.norm(x - u) / np.linalg.norm(u) < 1e-8
+        srv.release(t)
+    srv.close()
