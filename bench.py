@@ -75,7 +75,8 @@ def parse():
                     help="skip the shelf/2d/serving sections after the headline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--only-config", choices=["solitary_1d", "shelf_1d", "bump_2d", "pcg2d_batch",
-                                              "serving", "robustness", "manufactured"],
+                                              "generic_sizes", "serving", "robustness",
+                                              "manufactured"],
                     help="run only this extra configuration and print its result as one JSON "
                          "line (for profiling one workload; not the headline)")
     ap.add_argument("--batch2d", type=int, default=16,
@@ -533,6 +534,7 @@ def gpu_arm(args, world, rank, local, pg):
         extra = {}
         for name, fn in (("solitary_1d", bench_solitary), ("shelf_1d", bench_shelf),
                          ("bump_2d", bench_2d), ("pcg2d_batch", bench_pcg2d),
+                         ("generic_sizes", bench_generic),
                          ("serving", bench_serving), ("robustness", bench_robustness),
                          ("manufactured", bench_manufactured)):
             try:
@@ -725,6 +727,69 @@ def bench_2d(sgn, ctx, torch, steps=300, n=512):
                                "fp64": abs(mass(e6) - m0) / abs(m0)},
             "max_zeta": float(np.abs(em - c["h"]).max()),
             "iterations_per_solve": sm["iterations"] / max(1, sm["solves"]), "status": sm["status"]}
+
+
+def bench_generic(sgn, ctx, torch, count=128, steps=20):
+    """Sizes that are not powers of two on the generic kernels: a 1d ensemble with n drawn
+    from {768, 1536, 3072, 6144} (RK4, mixed, rtol 1e-10) against the same-seed ensemble at
+    the power-of-two sizes {512, 1024, 2048, 4096}, and a 2d bump at 384 x 240 (RK4, mixed)
+    against 512 x 256."""
+    import numpy as np
+
+    from paper_2506_16045_gb300 import inputs as I
+    out = {}
+    for name, sizes in (("generic_1d", [768, 1536, 3072, 6144]),
+                        ("pow2_1d", [512, 1024, 2048, 4096])):
+        ens = I.ensemble_1d(count=count, seed=2507, sizes=sizes)
+        E = Ensemble(sgn, ctx, ens, torch)
+        E.reset()
+        E.step(sgn.PREC_MIXED, 2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        E.step(sgn.PREC_MIXED, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        stt = E.st.stats()
+        out[name] = {"sizes": sizes, "instances": count, "points": E.points,
+                     "ms_per_step": ms / steps, "value": E.points * steps / (ms * 1e-3),
+                     "unit": UNIT, "status": stt["status"]}
+        E.st.close()
+        E.lay.close()
+    for name, (nx, ny) in (("generic_2d", (384, 240)), ("pow2_2d", (512, 256))):
+        Lx, Ly = 80.0, 50.0
+        X, Y = I.grid_2d(nx, ny, Lx, Ly)
+        h = I.gaussian_bump_2d(X, Y, Lx, Ly, 0.4, 3.0, Lx / 2, Ly / 2)
+        eta, u = I.solitary_wave_2d(X, Y, Lx, Ly, 1.0, 0.2, 0.25 * Lx, 9.81)
+        eta = h + (eta - 1.0)
+        dt = 0.25 * (Lx / nx) / np.sqrt(9.81 * 1.2)
+        lay = sgn.Layout(ctx, [sgn.Grid(2, nx, Lx, g=9.81, ny=ny, Ly=Ly)])
+        dev = lambda a: torch.as_tensor(np.ascontiguousarray(a).ravel(), dtype=torch.float64,
+                                        device="cuda")
+        E_, u_, h_ = dev(eta), dev(u), dev(h)
+        U_ = torch.zeros(2 * nx * ny, dtype=torch.float64, device="cuda")
+        st = sgn.State(lay, E_, U_, u_, h_, torch.zeros_like(U_))
+        st.init()
+        st.rk4(dt, 2, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st.rk4(dt, 10, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        stt = st.stats()
+        out[name] = {"grid": f"{nx}x{ny}", "ms_per_step": ms / 10,
+                     "value": nx * ny * 10 / (ms * 1e-3), "unit": UNIT,
+                     "iterations_per_solve": stt["iterations"] / max(1, stt["solves"]),
+                     "status": stt["status"]}
+        st.close()
+        lay.close()
+    out["workload"] = ("generic sizes: 1d ensemble of 128 shelf instances, n from {768, 1536, "
+                       "3072, 6144}, RK4 mixed rtol 1e-10, 20 steps; 2d bump at 384x240, RK4 "
+                       "mixed, 10 steps; each beside its power-of-two neighbour")
+    return out
 
 
 def bench_shelf(sgn, ctx, torch, steps=2000):
@@ -1127,6 +1192,7 @@ def main():
               "bump_2d": lambda *a: bench_2d(*a, n=args.n2d),
               "serving": lambda *a: bench_serving(*a, nreq=args.serving_requests),
               "robustness": bench_robustness,
+              "generic_sizes": bench_generic,
               "manufactured": bench_manufactured}
         print(json.dumps({args.only_config: fn[args.only_config](sgn, ctx, torch)}))
         ctx.close()

@@ -179,18 +179,20 @@ SHELF_DT = {"ab4": 0.004, "sbdf2": 0.002}
 
 
 def ensemble_1d(count=256, seed=2506, kmin=9, kmax=13, L=200.0, g=9.81,
-                cfl=0.25) -> list[Instance1d]:
-    """Batched ensemble: n = 2^k with k ~ U{kmin..kmax}, a ~ U[0.05, 0.4],
-    shelf start x_s ~ U[0.3L, 0.7L], depth ratio r ~ U[0.4, 0.8], w = 5, W = 0.4L,
-    crest 20 units before the shelf, dt = cfl * dx / sqrt(g (1 + a))."""
+                cfl=0.25, sizes=None) -> list[Instance1d]:
+    """Batched ensemble: n = 2^k with k ~ U{kmin..kmax} (or n drawn uniformly from `sizes`),
+    a ~ U[0.05, 0.4], shelf start x_s ~ U[0.3L, 0.7L], depth ratio r ~ U[0.4, 0.8], w = 5,
+    W = 0.4L, crest 20 units before the shelf, dt = cfl * dx / sqrt(g (1 + a))."""
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(count):
-        k = int(rng.integers(kmin, kmax + 1))
+        if sizes is None:
+            n = 2 ** int(rng.integers(kmin, kmax + 1))
+        else:
+            n = int(sizes[int(rng.integers(0, len(sizes)))])
         a = float(rng.uniform(0.05, 0.4))
         xs = float(rng.uniform(0.3 * L, 0.7 * L))
         r = float(rng.uniform(0.4, 0.8))
-        n = 2 ** k
         x0 = xs - 20.0
         dt = cfl * (L / n) / math.sqrt(g * (1.0 + a))
         inst = shelf_case(n=n, L=L, a=a, x0=x0, r=r, xs=xs, w=5.0, g=g, dt=dt)
