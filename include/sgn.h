@@ -114,8 +114,8 @@ const char* sgn_status_string(sgn_status s);
  * sides: powers of two with 8 <= n <= 1024, or n = 2^a 3^b 5^c (a >= 1) with
  * 6 <= n <= 1024 (such as 384 x 240).  A 2d grid with a side that is not a power of two
  * runs on generic kernels (full complex spectra, mixed-radix row and column passes) for
- * the same calls as the 1d generic sizes, with host-driven solves (one stream
- * synchronisation per PCG iteration) and float64 right-hand sides; it takes no batches, no
+ * the same calls as the 1d generic sizes, with device-driven solves (one cached graph per
+ * precision) and float64 right-hand sides; it takes no batches, no
  * inner-solve forms (sgn_layout_set_form2d, sgn_profile_inner2d) and the same power-of-two
  * options as 1d.  Other sizes: SGN_ERR_UNSUPPORTED_SIZE.  A 2d layout of
  * count > 1 (at most 32) is a batch of instances on one grid (every sgn_grid equal); it

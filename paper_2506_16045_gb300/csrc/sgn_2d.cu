@@ -1022,8 +1022,6 @@ PInst2d pinst_of(const Layout2d& L) {
 
 }  // namespace
 
-namespace {
-
 // The cached solve graphs and their source graphs (kept until the executable graph goes).
 void drop_solve_graphs(const Layout2d& L) {
   for (int i = 0; i < 2; ++i)
@@ -1035,7 +1033,28 @@ void drop_solve_graphs(const Layout2d& L) {
     }
 }
 
-}  // namespace
+// Appends a while node after the work captured so far on `cs` (which keeps capturing after
+// it) and returns the node's body graph.
+cudaError_t capture_add_while(cudaStream_t cs, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(cs, &st, nullptr, &g, &deps, &edges, &nd);
+  if (e) return e;
+  if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, g, deps, edges, nd, &p))) return e;
+  *body = p.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1,
+                                             cudaStreamSetCaptureDependencies);
+}
 
 cudaError_t layout2d_create(Layout2d& L, const sgn_grid& g) {
   L.nx = g.nx;
@@ -1461,29 +1480,6 @@ __global__ void k2_finalize(const Scal2d* sc, double* x, long long n) {
 
 namespace {
 
-// Appends a while node after the work captured so far on `cs` (which keeps capturing after
-// it) and returns the node's body graph.
-cudaError_t add_while(cudaStream_t cs, cudaGraphConditionalHandle h, cudaGraph_t* body) {
-  cudaStreamCaptureStatus st;
-  cudaGraph_t g = nullptr;
-  const cudaGraphNode_t* deps = nullptr;
-  const cudaGraphEdgeData* edges = nullptr;
-  size_t nd = 0;
-  cudaError_t e = cudaStreamGetCaptureInfo(cs, &st, nullptr, &g, &deps, &edges, &nd);
-  if (e) return e;
-  if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
-  cudaGraphNodeParams p = {};
-  p.type = cudaGraphNodeTypeConditional;
-  p.conditional.handle = h;
-  p.conditional.type = cudaGraphCondTypeWhile;
-  p.conditional.size = 1;
-  cudaGraphNode_t node;
-  if ((e = cudaGraphAddNode(&node, g, deps, edges, nd, &p))) return e;
-  *body = p.conditional.phGraph_out[0];
-  return cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1,
-                                             cudaStreamSetCaptureDependencies);
-}
-
 // The solve of launch_pcg2d's host-driven path, with every host decision moved into the
 // graph: the refinement loop (mixed) and the inner PCG loop become while nodes whose
 // conditions k2_decide, k2_inner_start and k2_update set.  Inputs come from L.stage,
@@ -1559,7 +1555,7 @@ cudaError_t build_solve_graph(const Layout2d& L, const void* tw64, const void* t
       k2_decide<<<1, 1, 0, cs[0]>>>(L.sc, hout);
       e = cudaGetLastError();
     }
-    if (!e) e = add_while(cs[0], hout, &body);
+    if (!e) e = capture_add_while(cs[0], hout, &body);
     // refinement pass: inner solve of G d = r / ||r||, x^ += ||r|| d, next residual, decide
     // the inner solve: one persistent launch, or a while node over the four-kernel iteration
     const bool persist = L.inner_form == 0;
@@ -1575,7 +1571,7 @@ cudaError_t build_solve_graph(const Layout2d& L, const void* tw64, const void* t
     if (persist) {
       if (!e) e = launch_pcg2d_persist(persist_args(L, tw32), L.p_grid, cs[1]);
     } else {
-      if (!e) e = add_while(cs[1], hin, &ibody);
+      if (!e) e = capture_add_while(cs[1], hin, &ibody);
       if (!e) e = begin(2, ibody);
       if (!e) e = inner_loop(float(0), cs[2], hin);
       if (!e) e = end(2);
@@ -1618,7 +1614,7 @@ cudaError_t build_solve_graph(const Layout2d& L, const void* tw64, const void* t
                                 cudaMemcpyDeviceToDevice, cs[0]);
     if (!e) e = cudaMemcpyAsync(slot(L, 5), slot(L, 13), (size_t)16 * L.HP,
                                 cudaMemcpyDeviceToDevice, cs[0]);
-    if (!e) e = add_while(cs[0], hin, &ibody);
+    if (!e) e = capture_add_while(cs[0], hin, &ibody);
     if (!e) e = begin(1, ibody);
     if (!e) e = inner_loop(double(0), cs[1], hin);
     if (!e) e = end(1);

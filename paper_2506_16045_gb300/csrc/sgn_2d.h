@@ -66,6 +66,7 @@ struct Layout2d {
   void* mr_w = nullptr;        // kMr2dPlanes complex-double planes of P
   double* mr_dev = nullptr;    // dot-product partials and results
   double* mr_host = nullptr;   // pinned copies of the results
+  void* mr_sc = nullptr;       // the device-driven solve's scalars
 };
 
 // A batch of B >= 2 instances on one grid: B single-instance layouts (instance 0 is the
@@ -85,6 +86,11 @@ struct Batch2d {
 };
 
 cudaError_t layout2d_create(Layout2d& L, const sgn_grid& g);
+// Appends a while node (condition handle h) after the work captured so far on the capturing
+// stream cs, which keeps capturing after the node; returns the node's body graph.
+cudaError_t capture_add_while(cudaStream_t cs, cudaGraphConditionalHandle h, cudaGraph_t* body);
+// Destroys a layout's cached solve graphs (executable and source).
+void drop_solve_graphs(const Layout2d& L);
 
 // ---- grids with a side that is not a power of two (sgn_2d_mr.cu) --------------------------
 // A side n = 2^a 3^b 5^c (a >= 1) with 6 <= n <= 1024.

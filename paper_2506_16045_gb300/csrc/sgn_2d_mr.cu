@@ -16,8 +16,8 @@
 //   PCG                   (§3.2 with the stopping rule sqrt(r.A^{-1}r) <= rtol sqrt(b.A^{-1}b);
 //                          float64, or float32 inner solves inside float64 refinement)
 //   right-hand side       (Eq:DAE_DSWE with Def:bigF in 2d, float64)
-// The solves are host-driven: each PCG iteration reads its scalars back (one stream
-// synchronisation per iteration).
+// A solve runs as one cached graph whose loops are while nodes driven by device-side
+// decisions (build_mr_graph); under stream capture the same steps run host-driven.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -25,6 +25,7 @@
 
 #include "../../include/sgn.h"
 #include "sgn_2d.h"
+#include "sgn_2d_dev.cuh"
 #include "sgn_mr_fft.cuh"
 
 namespace sgn {
@@ -283,6 +284,209 @@ __global__ void k2m_report(SolveRec* rec, int iters, int refinements, double rat
   rec->status = status;
 }
 
+// ---- device-driven solve: scalars and decisions -------------------------------------------
+// The cached solve graph keeps every decision on the device: the while nodes' conditions are
+// set by the kernels below from these scalars (options written before each launch).
+struct MrScal {
+  double rtol, rtol_in;       // options
+  int maxit, max_refine, kind;
+  double bb, rz, rzn, pq, alpha, beta, tol, nr, scale, ratio;
+  int iters, refinements, status, st_in, it0, skip, zero_x, nofit;
+};
+
+__global__ void k2m_opts(MrScal* S, double rtol, double rtol_in, int maxit, int max_refine) {
+  S->rtol = rtol;
+  S->rtol_in = rtol_in;
+  S->maxit = maxit;
+  S->max_refine = max_refine;
+}
+
+// after the coefficients (rec) and b.A^{-1}b: start the solve, or finish it at once
+__global__ void k2m_begin(MrScal* S, const SolveRec* rec) {
+  S->iters = 0;
+  S->refinements = 0;
+  S->ratio = 0.0;
+  S->st_in = SGN_OK;
+  S->skip = 0;
+  S->zero_x = 0;
+  S->nofit = 0;
+  S->status = rec->status;
+  if (S->status != SGN_OK) {         // reported by the coefficients; x untouched
+    S->skip = 1;
+    S->nofit = 1;
+    return;
+  }
+  const double bb = S->bb;
+  if (!(bb > 0.0)) {                 // x = 0: b = 0 solves exactly, a non-finite b breaks down
+    S->zero_x = 1;
+    S->skip = 1;
+    S->status = bb == 0.0 ? SGN_OK : SGN_ERR_BREAKDOWN;
+  }
+}
+
+// float64 PCG: after r.z of the first residual; the loop runs while sqrt(rz) > tol
+__global__ void k2m_init64(MrScal* S, cudaGraphConditionalHandle h) {
+  unsigned go = 0u;
+  if (!S->skip) {
+    S->tol = S->rtol * sqrt(S->bb);
+    if (sqrt(S->rz) > S->tol) {
+      if (S->iters >= S->maxit) S->status = SGN_ERR_NOT_CONVERGED;
+      else go = 1u;
+    }
+  }
+  cudaGraphSetConditional(h, go);
+}
+
+// alpha = rz / p.Gp, or a breakdown (skip marks the rest of the iteration)
+__global__ void k2m_alpha(MrScal* S, int inner) {
+  if (S->skip) return;
+  const double pq = S->pq;
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    if (inner) S->st_in = SGN_ERR_BREAKDOWN;
+    else S->status = SGN_ERR_BREAKDOWN;
+    S->skip = 1;
+    return;
+  }
+  S->alpha = S->rz / pq;
+}
+
+// beta = rz_new / rz and the loop condition (float64 PCG: tol; inner PCG: tin)
+__global__ void k2m_beta(MrScal* S, int inner, cudaGraphConditionalHandle h) {
+  unsigned go = 0u;
+  if (!S->skip) {
+    S->iters += 1;
+    const double rzn = S->rzn;
+    if (!isfinite(rzn)) {
+      if (inner) S->st_in = SGN_ERR_BREAKDOWN;
+      else S->status = SGN_ERR_BREAKDOWN;
+      S->skip = 1;
+    } else {
+      S->beta = rzn / S->rz;
+      S->rz = rzn;
+      if (sqrt(rzn) > S->tol) {
+        if (S->iters >= S->maxit) {
+          if (inner) S->st_in = SGN_ERR_NOT_CONVERGED;
+          else S->status = SGN_ERR_NOT_CONVERGED;
+        } else {
+          go = 1u;
+        }
+      }
+    }
+  }
+  cudaGraphSetConditional(h, go);
+}
+
+// mixed: after a refinement residual's r.A^{-1}r (in rz): done, out of budget, or the next
+// inner solve (its tolerance and the scale of r)
+__global__ void k2m_decide(MrScal* S, cudaGraphConditionalHandle h) {
+  unsigned go = 0u;
+  if (!S->zero_x && !S->nofit) {
+    const double nr = sqrt(fmax(S->rz, 0.0));
+    S->ratio = nr / sqrt(S->bb);
+    if (S->ratio <= S->rtol) {
+      S->status = SGN_OK;
+    } else if (S->status != SGN_OK) {
+      // a float32 breakdown without progress ended the solve
+    } else if (!isfinite(nr)) {
+      S->status = SGN_ERR_BREAKDOWN;
+    } else if (S->refinements >= S->max_refine || S->iters >= S->maxit) {
+      S->status = SGN_ERR_NOT_CONVERGED;
+    } else {
+      S->nr = nr;
+      S->scale = 1.0 / nr;
+      S->tol = S->rtol_in > 0.0 ? S->rtol_in : fmin(0.1, fmax(1e-6, 0.3 * S->rtol / S->ratio));
+      go = 1u;
+    }
+  }
+  cudaGraphSetConditional(h, go);
+}
+
+// mixed: the inner solve starts from d = 0 with r.z in rz
+__global__ void k2m_inner_init(MrScal* S, cudaGraphConditionalHandle h) {
+  S->it0 = S->iters;
+  S->st_in = SGN_OK;
+  S->skip = 0;
+  unsigned go = 0u;
+  if (sqrt(fmax(S->rz, 0.0)) > S->tol) {
+    if (S->iters >= S->maxit) S->st_in = SGN_ERR_NOT_CONVERGED;
+    else go = 1u;
+  }
+  cudaGraphSetConditional(h, go);
+}
+
+// mixed: after an inner solve; a float32 breakdown without progress ends the solve
+__global__ void k2m_after_inner(MrScal* S) {
+  if (S->st_in == SGN_ERR_BREAKDOWN && S->iters == S->it0) S->status = SGN_ERR_BREAKDOWN;
+  S->refinements += 1;
+  S->skip = 0;
+}
+
+// y += sign alpha x, p = z + beta p, x += nr d, out = scale r: the loop's vector updates with
+// their scalars read on the device (skipped after a breakdown in the same iteration)
+template <typename Sv>
+__global__ void k2m_axpy_s(long long n, const MrScal* S, double sign, const Sv* __restrict__ x,
+                           Sv* __restrict__ y) {
+  if (S->skip) return;
+  const double a = sign * S->alpha;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = (Sv)((double)y[i] + a * (double)x[i]);
+}
+
+template <typename Sv>
+__global__ void k2m_xpby_s(long long n, const MrScal* S, const Sv* __restrict__ z,
+                           Sv* __restrict__ p) {
+  if (S->skip) return;
+  const double b = S->beta;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] = (Sv)((double)z[i] + b * (double)p[i]);
+}
+
+__global__ void k2m_correct_s(long long n, const MrScal* S, const float* __restrict__ d,
+                              double* __restrict__ x) {
+  const double s = S->nr;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] += s * (double)d[i];
+}
+
+__global__ void k2m_scale_s(long long n, const MrScal* S, const double* __restrict__ r,
+                            float* __restrict__ out) {
+  const double s = S->scale;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)(s * r[i]);
+}
+
+// the report into rec (coefficients kept); x = 0 when b was zero (or not finite)
+__global__ void k2m_finish(const MrScal* S, SolveRec* rec, double* __restrict__ x, long long n,
+                           int mixed) {
+  if (S->zero_x) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+      x[i] = 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    rec->iters = S->iters;
+    rec->refinements = S->refinements;
+    rec->status = S->status;
+    rec->ratio = (S->zero_x || S->nofit)
+                     ? 0.0
+                     : (mixed ? S->ratio : sqrt(fmax(S->rz, 0.0)) / sqrt(S->bb));
+  }
+}
+
+// the coefficient kind of the captured coefficient step (k2_coeffs reads it from sc)
+__global__ void k2m_kind(Scal2d* sc, int kind) { sc->kind = kind; }
+
+// given coefficients: rec = given with status OK
+__global__ void k2m_given(const SolveRec* given, SolveRec* rec) {
+  SolveRec r = *given;
+  r.status = SGN_OK;
+  *rec = r;
+}
+
 // ---- right-hand side (Eq:DAE_DSWE with Def:bigF, 2d; reading R6) -------------------------
 // products whose divergence or gradient the right-hand side takes
 __global__ void k2m_rhs_pre(long long P, const double* __restrict__ eta,
@@ -524,6 +728,9 @@ cudaError_t mr2d_create(Layout2d& L) {
   if ((e = cudaMalloc(&L.mr_w, (size_t)16 * L.P * kMr2dPlanes))) return e;
   if ((e = cudaMalloc(&L.mr_dev, sizeof(double) * (kRedBlocks + kScal)))) return e;
   if ((e = cudaMallocHost(&L.mr_host, sizeof(double) * kScal))) return e;
+  if ((e = cudaMalloc(&L.mr_sc, sizeof(MrScal)))) return e;
+  if ((e = cudaMalloc(&L.stage, sizeof(double) * 7 * L.P))) return e;
+  if ((e = cudaMalloc(&L.stage_rec, sizeof(SolveRec) * 2))) return e;
   return cudaStreamSynchronize(nullptr);          // the tables (legacy stream)
 }
 
@@ -532,6 +739,8 @@ void mr2d_destroy(Layout2d& L) {
   cudaFree(L.mr_twy);
   cudaFree(L.mr_w);
   cudaFree(L.mr_dev);
+  cudaFree(L.mr_sc);
+  L.mr_sc = nullptr;
   if (L.mr_host) cudaFreeHost(L.mr_host);
   L.mr_twx = L.mr_twy = L.mr_w = nullptr;
   L.mr_dev = L.mr_host = nullptr;
@@ -554,6 +763,182 @@ cudaError_t mr2d_precond(const Layout2d& L, const SolveRec* rec, const double* r
   return ainv<double, double>(M, rec, r, z, s);
 }
 
+namespace {
+
+// The solve as one graph (inputs from L.stage, options from the scalars, the report to
+// L.stage_rec[1]): the float64 PCG loop, or the refinement loop around the float32 inner
+// loop, as while nodes whose conditions the decision kernels set.
+cudaError_t build_mr_graph(const Layout2d& L, bool mixed, bool given, cudaGraphExec_t* out,
+                           cudaGraph_t* src) {
+  const Mr M(L);
+  const long long P = L.P, V = 2 * P;
+  const int nb = blocks_for(V);
+  MrScal* S = static_cast<MrScal*>(L.mr_sc);
+  const double* eta = L.stage;
+  const double* gh = L.stage + P;
+  const double* b = L.stage + 3 * P;
+  double* x = L.stage + 5 * P;
+  SolveRec* rec = L.stage_rec + 1;
+  double* r = M.rp(0);
+  double* p = M.rp(2);
+  double* z = M.rp(4);
+  double* q = M.rp(6);
+  double* l = M.rp(8);
+  float* rf = M.fp(10);
+  float* pf = M.fp(11);
+  float* zf = M.fp(12);
+  float* qf = M.fp(13);
+  float* df_ = M.fp(14);
+  float* lf = M.fp(15);
+  cudaStream_t cs[3] = {nullptr, nullptr, nullptr};
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaSuccess;
+  int capturing = 0;
+  for (auto& c : cs)
+    if (!e) e = cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking);
+  if (!e) e = cudaGraphCreate(&g, 0);
+  auto begin = [&](int i, cudaGraph_t into) {
+    cudaError_t r_ = cudaStreamBeginCaptureToGraph(cs[i], into, nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeRelaxed);
+    if (!r_) capturing |= 1 << i;
+    return r_;
+  };
+  auto end = [&](int i) {
+    cudaGraph_t dummy;
+    capturing &= ~(1 << i);
+    cudaError_t r_ = cudaStreamEndCapture(cs[i], &dummy);
+    return r_ ? r_ : cudaGetLastError();
+  };
+  auto last = [&]() { return cudaGetLastError(); };
+  // r = b - G x, z = A^{-1} r, rz = r.z (float64) on stream st
+  auto residual64 = [&](cudaStream_t st) -> cudaError_t {
+    cudaError_t r_ = applyG<double, double>(M, eta, gh, x, q, l, st);
+    if (r_) return r_;
+    k2m_sub_scale<double><<<nb, 256, 0, st>>>(V, b, q, 1.0, r);
+    if ((r_ = last()) || (r_ = ainv<double, double>(M, rec, r, z, st))) return r_;
+    k2m_dot1<double><<<kRedBlocks, 256, 0, st>>>(V, r, z, L.mr_dev);
+    k2m_dot2<<<1, 256, 0, st>>>(L.mr_dev, &S->rz);
+    return last();
+  };
+  if (!e) e = begin(0, g);
+  if (!e) {
+    if (given) k2m_given<<<1, 1, 0, cs[0]>>>(L.stage_rec, rec);
+    e = last();
+    if (!e && !given) e = launch_coeffs2d(L, eta, gh, -1, rec, cs[0]);
+  }
+  // b.A^{-1}b, then the start decisions
+  if (!e) e = ainv<double, double>(M, rec, b, z, cs[0]);
+  if (!e) {
+    k2m_dot1<double><<<kRedBlocks, 256, 0, cs[0]>>>(V, b, z, L.mr_dev);
+    k2m_dot2<<<1, 256, 0, cs[0]>>>(L.mr_dev, &S->bb);
+    k2m_begin<<<1, 1, 0, cs[0]>>>(S, rec);
+    e = last();
+  }
+  if (!mixed) {
+    cudaGraphConditionalHandle hin;
+    cudaGraph_t body = nullptr;
+    if (!e) e = residual64(cs[0]);
+    if (!e) e = cudaMemcpyAsync(p, z, sizeof(double) * V, cudaMemcpyDeviceToDevice, cs[0]);
+    if (!e) e = cudaGraphConditionalHandleCreate(&hin, g, 0, 0);
+    if (!e) {
+      k2m_init64<<<1, 1, 0, cs[0]>>>(S, hin);
+      e = last();
+    }
+    if (!e) e = capture_add_while(cs[0], hin, &body);
+    if (!e) e = begin(1, body);
+    if (!e) e = applyG<double, double>(M, eta, gh, p, q, l, cs[1]);
+    if (!e) {
+      k2m_dot1<double><<<kRedBlocks, 256, 0, cs[1]>>>(V, p, q, L.mr_dev);
+      k2m_dot2<<<1, 256, 0, cs[1]>>>(L.mr_dev, &S->pq);
+      k2m_alpha<<<1, 1, 0, cs[1]>>>(S, 0);
+      k2m_axpy_s<double><<<nb, 256, 0, cs[1]>>>(V, S, 1.0, p, x);
+      k2m_axpy_s<double><<<nb, 256, 0, cs[1]>>>(V, S, -1.0, q, r);
+      e = last();
+    }
+    if (!e) e = ainv<double, double>(M, rec, r, z, cs[1]);
+    if (!e) {
+      k2m_dot1<double><<<kRedBlocks, 256, 0, cs[1]>>>(V, r, z, L.mr_dev);
+      k2m_dot2<<<1, 256, 0, cs[1]>>>(L.mr_dev, &S->rzn);
+      k2m_beta<<<1, 1, 0, cs[1]>>>(S, 0, hin);
+      k2m_xpby_s<double><<<nb, 256, 0, cs[1]>>>(V, S, z, p);
+      e = last();
+    }
+    if (!e) e = end(1);
+  } else {
+    cudaGraphConditionalHandle hout, hin;
+    cudaGraph_t body = nullptr, ibody = nullptr;
+    if (!e) e = residual64(cs[0]);
+    if (!e) e = cudaGraphConditionalHandleCreate(&hout, g, 0, 0);
+    if (!e) {
+      k2m_decide<<<1, 1, 0, cs[0]>>>(S, hout);
+      e = last();
+    }
+    if (!e) e = capture_add_while(cs[0], hout, &body);
+    if (!e) e = begin(1, body);
+    // the inner solve of G d = r / ||r|| from d = 0
+    if (!e) {
+      k2m_scale_s<<<nb, 256, 0, cs[1]>>>(V, S, r, rf);
+      e = last();
+    }
+    if (!e) e = cudaMemsetAsync(df_, 0, sizeof(float) * V, cs[1]);
+    if (!e) e = ainv<float, float>(M, rec, rf, zf, cs[1]);
+    if (!e) e = cudaMemcpyAsync(pf, zf, sizeof(float) * V, cudaMemcpyDeviceToDevice, cs[1]);
+    if (!e) e = cudaGraphConditionalHandleCreate(&hin, body, 0, 0);
+    if (!e) {
+      k2m_dot1<float><<<kRedBlocks, 256, 0, cs[1]>>>(V, rf, zf, L.mr_dev);
+      k2m_dot2<<<1, 256, 0, cs[1]>>>(L.mr_dev, &S->rz);
+      k2m_inner_init<<<1, 1, 0, cs[1]>>>(S, hin);
+      e = last();
+    }
+    if (!e) e = capture_add_while(cs[1], hin, &ibody);
+    if (!e) e = begin(2, ibody);
+    if (!e) e = applyG<float, float>(M, eta, gh, pf, qf, lf, cs[2]);
+    if (!e) {
+      k2m_dot1<float><<<kRedBlocks, 256, 0, cs[2]>>>(V, pf, qf, L.mr_dev);
+      k2m_dot2<<<1, 256, 0, cs[2]>>>(L.mr_dev, &S->pq);
+      k2m_alpha<<<1, 1, 0, cs[2]>>>(S, 1);
+      k2m_axpy_s<float><<<nb, 256, 0, cs[2]>>>(V, S, 1.0, pf, df_);
+      k2m_axpy_s<float><<<nb, 256, 0, cs[2]>>>(V, S, -1.0, qf, rf);
+      e = last();
+    }
+    if (!e) e = ainv<float, float>(M, rec, rf, zf, cs[2]);
+    if (!e) {
+      k2m_dot1<float><<<kRedBlocks, 256, 0, cs[2]>>>(V, rf, zf, L.mr_dev);
+      k2m_dot2<<<1, 256, 0, cs[2]>>>(L.mr_dev, &S->rzn);
+      k2m_beta<<<1, 1, 0, cs[2]>>>(S, 1, hin);
+      k2m_xpby_s<float><<<nb, 256, 0, cs[2]>>>(V, S, zf, pf);
+      e = last();
+    }
+    if (!e) e = end(2);
+    if (!e) {
+      k2m_after_inner<<<1, 1, 0, cs[1]>>>(S);
+      k2m_correct_s<<<nb, 256, 0, cs[1]>>>(V, S, df_, x);
+      e = last();
+    }
+    if (!e) e = residual64(cs[1]);
+    if (!e) {
+      k2m_decide<<<1, 1, 0, cs[1]>>>(S, hout);
+      e = last();
+    }
+    if (!e) e = end(1);
+  }
+  if (!e) {
+    k2m_finish<<<nb, 256, 0, cs[0]>>>(S, rec, x, V, mixed ? 1 : 0);
+    e = last();
+  }
+  if (!e) e = end(0);
+  for (int i = 2; i >= 0; --i)
+    if (capturing & (1 << i)) end(i);          // a failed build: close its captures
+  if (!e) e = cudaGraphInstantiate(out, g, 0);
+  for (auto& c : cs)
+    if (c) cudaStreamDestroy(c);
+  // as for the power-of-two solve graphs: a graph whose build failed is left alone
+  if (!e) *src = g;
+  return e;
+}
+
+}  // namespace
+
 cudaError_t mr2d_pcg(const Layout2d& L, int precision, const double* eta, const double* gradh,
                      const double* b, double* x, const SolveRec* given, int kind, double rtol,
                      double rtol_inner, int maxit, int max_refine, SolveRec* rec,
@@ -562,6 +947,39 @@ cudaError_t mr2d_pcg(const Layout2d& L, int precision, const double* eta, const 
   const long long P = L.P, V = 2 * P;
   const int nb = blocks_for(V);
   cudaError_t e;
+  // ---- device-driven: one graph launch between staging copies
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  if (!L.solve_graph_off && cudaStreamIsCapturing(s, &cst) == cudaSuccess &&
+      cst == cudaStreamCaptureStatusNone) {
+    const int mi = precision == SGN_PREC_MIXED ? 1 : 0, gi = given ? 1 : 0;
+    cudaGraphExec_t& ex = L.solve_exec[mi][gi];
+    if (!ex && build_mr_graph(L, mi == 1, gi == 1, &ex, &L.solve_graph[mi][gi]) != cudaSuccess) {
+      cudaGetLastError();
+      ex = nullptr;
+      L.solve_graph_off = true;
+    }
+    if (ex) {
+      const size_t d = sizeof(double);
+      if ((e = cudaMemcpyAsync(L.stage, eta, d * P, cudaMemcpyDeviceToDevice, s)) ||
+          (e = cudaMemcpyAsync(L.stage + P, gradh, d * V, cudaMemcpyDeviceToDevice, s)) ||
+          (e = cudaMemcpyAsync(L.stage + 3 * P, b, d * V, cudaMemcpyDeviceToDevice, s)) ||
+          (e = cudaMemcpyAsync(L.stage + 5 * P, x, d * V, cudaMemcpyDeviceToDevice, s)))
+        return e;
+      if (given && (e = cudaMemcpyAsync(L.stage_rec, given, sizeof(SolveRec),
+                                        cudaMemcpyDeviceToDevice, s)))
+        return e;
+      k2m_opts<<<1, 1, 0, s>>>(static_cast<MrScal*>(L.mr_sc), rtol, rtol_inner, maxit,
+                               max_refine > 0 ? max_refine : 12);
+      k2m_kind<<<1, 1, 0, s>>>(L.sc, kind);
+      if ((e = cudaGetLastError()) || (e = cudaGraphLaunch(ex, s))) return e;
+      if ((e = cudaMemcpyAsync(x, L.stage + 5 * P, d * V, cudaMemcpyDeviceToDevice, s)) ||
+          (e = cudaMemcpyAsync(rec, L.stage_rec + 1, sizeof(SolveRec), cudaMemcpyDeviceToDevice,
+                               s)))
+        return e;
+      return cudaSuccess;
+    }
+  }
+  // ---- host-driven
   // a1: the coefficients (or the caller's) into rec
   if (given) {
     if ((e = cudaMemcpyAsync(rec, given, sizeof(SolveRec), cudaMemcpyDeviceToDevice, s)))
