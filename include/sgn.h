@@ -160,6 +160,14 @@ sgn_status sgn_layout_get_forms(const sgn_layout* lay, int log2n, int* solve_cta
  * SGN_ERR_UNSUPPORTED_SIZE for another tile width. */
 sgn_status sgn_layout_set_form2d(sgn_layout* lay, int inner, int tile_width);
 sgn_status sgn_layout_get_form2d(const sgn_layout* lay, int* inner, int* tile_width);
+/* Radix plan of the persistent 2d inner solve's transforms (§6.1 D by FFT): the stages of a
+ * length-2^k transform have radices up to max_radix (16, the default, or 8), split as evenly
+ * as possible (1024 = 16 x 8 x 8 with 16; 8 x 8 x 4 x 4 with 8).  Both plans compute the
+ * same transform and agree up to rounding.  0 restores the default.  SGN_ERR_INVALID_ARG on
+ * a 1d layout or another value, SGN_ERR_UNSUPPORTED_SIZE on a grid with a side that is not a
+ * power of two.  sgn_state_autotune times the plans with the inner-solve forms. */
+sgn_status sgn_layout_set_radix2d(sgn_layout* lay, int max_radix);
+sgn_status sgn_layout_get_radix2d(const sgn_layout* lay, int* max_radix);
 
 /* offsets[0..count]: start of each instance in a packed scalar array (host array). */
 sgn_status sgn_layout_offsets(const sgn_layout* lay, long long* offsets);
@@ -349,10 +357,12 @@ sgn_status sgn_state_set_dealias(sgn_state* st, int on);
  * The state (eta, U, u, time, counters) is restored afterwards, so tuning leaves no trace
  * on the solution.  Allocates and frees 3 P doubles; synchronises `stream`; best_ms
  * (nullable, host) receives the chosen time per step.  A 1d state without such classes is
- * left as it is.  For a 2d state it chooses the layout's inner-solve form
- * (sgn_layout_set_form2d: the persistent launch, or four kernels per inner iteration) the
- * same way: each form timed on RK4 steps from the same state in two passes, the persistent
- * form kept unless the other is at least 3% faster, the state restored. */
+ * left as it is.  For a 2d state it chooses the layout's inner-solve form and radix plan
+ * (sgn_layout_set_form2d and sgn_layout_set_radix2d: the persistent launch with radix-16 or
+ * radix-8 stages, or four kernels per inner iteration) the same way: each candidate timed
+ * on RK4 steps from the same state in two passes, the default (persistent, radix 16) kept
+ * unless another is at least 3% faster, the state restored.  A 2d grid with a side that is
+ * not a power of two has one form: nothing to choose. */
 sgn_status sgn_state_autotune(sgn_state* st, const double* dt, const sgn_opts* opts,
                               sgn_stream stream, double* best_ms);
 /* Synchronises the stream used by the last step call and reports counters. */

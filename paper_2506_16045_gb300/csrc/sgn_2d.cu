@@ -1111,6 +1111,7 @@ PersistArgs2d persist_args(const Layout2d& L, const void* tw32) {
   a.lognx = L.lx;
   a.logny = L.ly;
   a.tw = L.p_tw;
+  a.maxb = L.p_maxb;
   a.col_units = (L.H + L.p_tw - 1) / L.p_tw;
   a.row_units = L.ny / 2;
   a.parts = L.pparts;
@@ -1163,6 +1164,14 @@ cudaError_t layout2d_set_inner_form(Layout2d& L, int form, int tile_width) {
   drop_solve_graphs(L);
   L.inner_form = form;
   L.p_tw = tile_width;
+  return cudaSuccess;
+}
+
+cudaError_t layout2d_set_radix(Layout2d& L, int maxb) {
+  if (L.mr || (maxb != 3 && maxb != 4)) return cudaErrorInvalidValue;
+  if (maxb == L.p_maxb) return cudaSuccess;
+  drop_solve_graphs(L);
+  L.p_maxb = maxb;
   return cudaSuccess;
 }
 
@@ -1956,6 +1965,7 @@ cudaError_t launch_pcg2d_batch(Layout2d& first, Batch2d& Bt, const void* tw64, c
     a.lognx = first.lx;
     a.logny = first.ly;
     a.tw = Bt.p_tw;
+    a.maxb = first.p_maxb;
     a.col_units = (first.H + Bt.p_tw - 1) / Bt.p_tw;
     a.row_units = first.ny / 2;
     a.parts = Bt.pparts;

@@ -231,6 +231,7 @@ struct PersistArgs2d {
   int B;
   int nx, ny, H, lognx, logny;
   int tw;                 // columns per column tile
+  int maxb;               // log2 of the largest radix of the transforms' stages (3 or 4)
   int col_units, row_units;    // per instance: column tiles, row pairs
   double* parts;          // B (row_units + col_units) per-unit partial sums
   unsigned* bar;          // arrival counter of the grid barriers

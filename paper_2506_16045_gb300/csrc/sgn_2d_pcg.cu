@@ -186,10 +186,14 @@ __device__ __forceinline__ void pstage(const cplx<float>* __restrict__ src,
 
 // Batched transform of nb sequences of length n = 2^log2n (8 <= n <= 1024) by group g, from
 // buffer a with b as the other buffer; returns the buffer that holds the result.  Every
-// thread of the group calls it; it returns after a group barrier.
+// thread of the group calls it; it returns after a group barrier.  The stages have radices
+// up to 2^maxb (maxb = 4: radix 16, 3: radix 8), split as evenly as possible.
+__device__ __forceinline__ int pfft_stages(int log2n, int maxb) { return (log2n + maxb - 1) / maxb; }
+
 __device__ __forceinline__ cplx<float>* pfft(cplx<float>* a, cplx<float>* b, int log2n, int nb, int S,
-                                          bool inv, const cplx<float>* tws, int t, int g) {
-  const int ns = (log2n + 3) / 4;                   // stages of radix <= 16
+                                          bool inv, const cplx<float>* tws, int t, int g,
+                                          int maxb) {
+  const int ns = pfft_stages(log2n, maxb);
   const int base = log2n / ns, extra = log2n - base * ns;
   int lp = 0;
   cplx<float>* src = a;
@@ -387,7 +391,7 @@ __device__ __forceinline__ void col_inverse(const PersistArgs2d& a, const PInst2
     buf[2 * S + pad(y)] = mul_ik(p1, kx) + mul_ik(p2, ky_of(s, y, ny));
   }
   gsync(g);
-  const cplx<float>* o = pfft(sm.A, sm.B, a.logny, 3, S, true, sm.twy, t, g);
+  const cplx<float>* o = pfft(sm.A, sm.B, a.logny, 3, S, true, sm.twy, t, g, a.maxb);
   for (int y = t; y < ny; y += kGT) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) stcg(I.t[q] + cb + y, o[q * S + pad(y)]);
@@ -438,7 +442,7 @@ __device__ __forceinline__ float row_matvec(const PersistArgs2d& a, const PInst2
     }
   }
   gsync(g);
-  cplx<float>* w = pfft(sm.A, sm.B, a.lognx, 3, S, true, sm.twx, t, g);
+  cplx<float>* w = pfft(sm.A, sm.B, a.lognx, 3, S, true, sm.twx, t, g, a.maxb);
   const float inv = __int_as_float((127 - a.lognx - a.logny) << 23);   // 1 / (nx ny), exact
   const float third = 1.0f / 3.0f;
   float part = 0.0f;
@@ -483,7 +487,7 @@ __device__ __forceinline__ float row_matvec(const PersistArgs2d& a, const PInst2
   }
   gsync(g);
   cplx<float>* other = w == sm.A ? sm.B : sm.A;
-  const cplx<float>* Y = pfft(w, other, a.lognx, 3, S, false, sm.twx, t, g);
+  const cplx<float>* Y = pfft(w, other, a.lognx, 3, S, false, sm.twx, t, g, a.maxb);
   // R2C split of the three packed rows, A = (Y_m + conj Y_{n-m})/2, B = (Y_m - conj Y_{n-m})/(2i),
   // stored back as row pairs of columns m: t0 = (A_0, A_1), t1 = (B_0, B_1), t2 = (A_2, B_2)
   for (int m = t; m <= h; m += kGT) {
@@ -530,7 +534,7 @@ __device__ __forceinline__ float col_forward_update(const PersistArgs2d& a, cons
     }
   }
   gsync(g);
-  const cplx<float>* o = pfft(sm.A, sm.B, a.logny, 3, S, false, sm.twy, t, g);
+  const cplx<float>* o = pfft(sm.A, sm.B, a.logny, 3, S, false, sm.twy, t, g, a.maxb);
   float part = 0.0f;
   const float al = s.alpha;
   const float kx = kx_of(s, c, nx);
@@ -598,7 +602,7 @@ __global__ void __launch_bounds__(kPNT, 1) k2_pcg_persist(const __grid_constant_
     for (int which = 0; which < (a.ny == a.nx ? 1 : 2); ++which) {
       const int log2n = which ? a.logny : a.lognx;
       cplx<float>* tab = which ? sm.twy : sm.twx;
-      const int ns = (log2n + 3) / 4, base = log2n / ns, extra = log2n - base * ns;
+      const int ns = pfft_stages(log2n, a.maxb), base = log2n / ns, extra = log2n - base * ns;
       int lp = 0;
       for (int st = 0; st < ns; ++st) {
         const int bits = base + (st < extra ? 1 : 0), R = 1 << bits, p0 = 1 << lp;

@@ -773,6 +773,20 @@ extern "C" sgn_status sgn_layout_set_form2d(sgn_layout* lay, int inner, int tile
   return SGN_OK;
 }
 
+extern "C" sgn_status sgn_layout_set_radix2d(sgn_layout* lay, int max_radix) {
+  if (check_layout(lay) || lay->dim != 2 || (max_radix != 0 && max_radix != 8 && max_radix != 16))
+    return fail(lay ? lay->ctx : nullptr, SGN_ERR_INVALID_ARG, "set_radix2d args");
+  if (lay->l2.mr) return fail(lay->ctx, SGN_ERR_UNSUPPORTED_SIZE, "no radix plans on this grid");
+  SGN_CUDA(lay->ctx, sgn::layout2d_set_radix(lay->l2, max_radix == 8 ? 3 : 4));
+  return SGN_OK;
+}
+
+extern "C" sgn_status sgn_layout_get_radix2d(const sgn_layout* lay, int* max_radix) {
+  if (check_layout(lay) || lay->dim != 2 || !max_radix) return SGN_ERR_INVALID_ARG;
+  *max_radix = 1 << lay->l2.p_maxb;
+  return SGN_OK;
+}
+
 extern "C" sgn_status sgn_layout_get_form2d(const sgn_layout* lay, int* inner, int* tile_width) {
   if (check_layout(lay) || lay->dim != 2 || !inner || !tile_width) return SGN_ERR_INVALID_ARG;
   *inner = lay->l2.inner_form;
@@ -1942,11 +1956,16 @@ sgn_status autotune_2d(sgn_state* st, const sgn_opts* opts, cudaStream_t s, doub
     r = fail(ctx, SGN_ERR_CUDA, "autotune events");
   }
   constexpr int kTimed = 2;
-  float t_of[2] = {0.0f, 0.0f};
+  // candidates: the persistent form with radix-16 stages (the default), with radix-8 stages,
+  // and the four-kernel form
+  constexpr int kCand = 3;
+  const int cform[kCand] = {0, 0, 1}, cmaxb[kCand] = {4, 3, 4};
+  float t_of[kCand] = {0.0f, 0.0f, 0.0f};
   const int tw = L.p_tw;
   for (int pass = 0; pass < 2 && !r; ++pass) {
-    for (int form = 0; form < 2 && !r; ++form) {
-      if (sgn::layout2d_set_inner_form(L, form, tw) != cudaSuccess)
+    for (int c = 0; c < kCand && !r; ++c) {
+      if (sgn::layout2d_set_inner_form(L, cform[c], tw) != cudaSuccess ||
+          sgn::layout2d_set_radix(L, cmaxb[c]) != cudaSuccess)
         r = cuda_fail(ctx, cudaGetLastError(), "autotune form");
       if (!r) r = rk4_step(st, opts, s);              // untimed: builds the solve graph
       if (!r) r = copy_state(false);
@@ -1958,11 +1977,14 @@ sgn_status autotune_2d(sgn_state* st, const sgn_opts* opts, cudaStream_t s, doub
                  cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
         r = cuda_fail(ctx, cudaGetLastError(), "autotune timing");
       if (!r) r = copy_state(false);
-      if (!r && (pass == 0 || ms < t_of[form])) t_of[form] = ms;
+      if (!r && (pass == 0 || ms < t_of[c])) t_of[c] = ms;
     }
   }
-  const int best = (t_of[1] < 0.97f * t_of[0]) ? 1 : 0;
-  sgn::layout2d_set_inner_form(L, best, tw);
+  int best = 0;
+  for (int c = 1; c < kCand; ++c)
+    if (t_of[c] < 0.97f * t_of[0] && t_of[c] < t_of[best]) best = c;
+  sgn::layout2d_set_inner_form(L, cform[best], tw);
+  sgn::layout2d_set_radix(L, cmaxb[best]);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaStreamSynchronize(s);

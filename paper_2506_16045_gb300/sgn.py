@@ -87,6 +87,8 @@ SIGNATURES = [
     ("sgn_layout_get_forms", C.c_int, [_VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("sgn_layout_set_form2d", C.c_int, [_VP, C.c_int, C.c_int]),
     ("sgn_layout_get_form2d", C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    ("sgn_layout_set_radix2d", C.c_int, [_VP, C.c_int]),
+    ("sgn_layout_get_radix2d", C.c_int, [_VP, C.POINTER(C.c_int)]),
     ("sgn_spectral_grad", C.c_int, [_VP, _VP, _DP, _DP, _VP]),
     ("sgn_precond_coeffs", C.c_int, [_VP, _VP, _DP, _DP, C.c_int, C.POINTER(SgnPrecond), _VP]),
     ("sgn_apply_operator", C.c_int, [_VP, _VP, _DP, _DP, _DP, _DP, _VP]),
@@ -287,7 +289,7 @@ class Layout:
 
     def set_form2d(self, inner, tile_width=0):
         """sgn_layout_set_form2d: inner 0 = persistent inner solve, 1 = four kernels per
-        inner iteration; tile_width 0 = automatic, else 1, 2 or 4 columns per tile."""
+        inner iteration; tile_width 0 = automatic (one column per tile), or 1."""
         self.ctx.check(self.ctx.lib.sgn_layout_set_form2d(self.h, inner, tile_width),
                        "sgn_layout_set_form2d")
 
@@ -299,6 +301,18 @@ class Layout:
                                                         C.byref(n), C.byref(it)),
                        "sgn_profile_inner2d")
         return ms.value, n.value, it.value
+
+    def set_radix2d(self, max_radix):
+        """sgn_layout_set_radix2d: the persistent inner solve's transform stages up to radix
+        16 (default, also 0) or 8."""
+        self.ctx.check(self.ctx.lib.sgn_layout_set_radix2d(self.h, max_radix),
+                       "sgn_layout_set_radix2d")
+
+    def radix2d(self):
+        r = C.c_int()
+        self.ctx.check(self.ctx.lib.sgn_layout_get_radix2d(self.h, C.byref(r)),
+                       "sgn_layout_get_radix2d")
+        return r.value
 
     def form2d(self):
         i, t = C.c_int(), C.c_int()

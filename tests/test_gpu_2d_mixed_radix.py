@@ -1,6 +1,6 @@
 """2d grids with a side that is not a power of two (n = 2^a 3^b 5^c; the §6.1 grids at sizes
 such as 384 x 240) on the generic kernels (full complex spectra, mixed-radix row and column
-passes, host-driven solves), against the oracle: gradient, G, the preconditioner, PCG in
+passes, solves as one cached graph), against the oracle: gradient, G, the preconditioner, PCG in
 both precisions, GMRES, the right-hand side and the RK4 / Adams-Bashforth steppers.
 
 Tolerances as for the power-of-two 2d path: float64 operators <= 1e-12 relative L2, solves
@@ -243,6 +243,8 @@ def test_generic_2d_rejections(S):
     lay = sgn.Layout(ctx, [sgn.Grid(2, nx, 12.0, ny=ny, Ly=9.0, g=9.81)])
     with pytest.raises(sgn.SgnError):
         lay.set_form2d(1, 0)
+    with pytest.raises(sgn.SgnError):
+        lay.set_radix2d(8)
     eta, u, h = dev(c["eta"]), dev(c["u"]), dev(c["h"])
     U = torch.zeros(2 * nx * ny, dtype=torch.float64, device="cuda")
     st = sgn.State(lay, eta, U, u, h, torch.zeros_like(U))

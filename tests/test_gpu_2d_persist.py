@@ -80,8 +80,11 @@ def test_persistent_equals_four_kernel_form(S, nx, ny, Lx, Ly):
     eta, gh, b, us, _ = bump_problem(nx, ny, Lx, Ly)
     lay = sgn.Layout(ctx, [sgn.Grid(2, nx, Lx, ny=ny, Ly=Ly, g=9.81)])
     out = {}
-    for form in (1, 0, 0):
-        lay.set_form2d(form, 0)
+    # the four-kernel form, the persistent form (twice: bitwise repeatable), and the
+    # persistent form with radix-8 stages
+    for form in (1, 0, 0, 2):
+        lay.set_form2d(1 if form == 1 else 0, 0)
+        lay.set_radix2d(8 if form == 2 else 16)
         x = torch.zeros(2 * nx * ny, dtype=torch.float64, device="cuda")
         info = sgn.pcg(lay, dev(eta), dev(gh), dev(b), x, rtol=1e-11, maxit=4000,
                        prec=sgn.PREC_MIXED)[0]
@@ -89,9 +92,12 @@ def test_persistent_equals_four_kernel_form(S, nx, ny, Lx, Ly):
         if form in out:
             assert torch.equal(out[form][0], x)               # repeatable bitwise
         out[form] = (x, info)
-    x1, x0 = out[1][0].cpu().numpy(), out[0][0].cpu().numpy()
-    assert rel(x0, x1) < 1e-9
+    x1, x0, x8 = out[1][0].cpu().numpy(), out[0][0].cpu().numpy(), out[2][0].cpu().numpy()
+    assert rel(x0, x1) < 1e-9 and rel(x8, x0) < 1e-9
     assert rel(x0.reshape(2, ny, nx), us) < 1e-8
+    assert lay.radix2d() == 8
+    lay.set_radix2d(0)
+    assert lay.radix2d() == 16
     # same method, so the inner iteration counts stay close
     i0, i1 = out[0][1]["iters"], out[1][1]["iters"]
     assert abs(i0 - i1) <= max(2, 0.1 * i1), (i0, i1)
@@ -128,6 +134,8 @@ def test_persistent_inner_solve_edge_cases(S):
         lay.set_form2d(0, 3)
     with pytest.raises(sgn.SgnError):
         lay.set_form2d(0, 2)             # one column per tile
+    with pytest.raises(sgn.SgnError):
+        lay.set_radix2d(4)
 
 
 def test_autotune_2d_chooses_a_form_and_restores_the_state(S):
@@ -153,11 +161,13 @@ def test_autotune_2d_chooses_a_form_and_restores_the_state(S):
     ms = st.autotune([0.05], rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
     assert ms > 0.0
     form = lay.form2d()[0]
-    assert form in (0, 1)
+    radix = lay.radix2d()
+    assert form in (0, 1) and radix in (8, 16)
     assert torch.equal(eta, eta0) and torch.equal(u, u0)
     st.rk4(0.05, 3, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
     lay2 = sgn.Layout(ctx, [g])
     lay2.set_form2d(form, 0)
+    lay2.set_radix2d(radix)
     st2, eta2, u2 = state(lay2)
     st2.rk4(0.05, 3, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
     torch.cuda.synchronize()

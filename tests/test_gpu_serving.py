@@ -293,3 +293,58 @@ def test_2d_runs_and_solves_of_several_sizes(S):
             assert np.linalg.norm(x - u) / np.linalg.norm(u) < 1e-8
         srv.release(t)
     srv.close()
+
+
+def test_generic_sizes_are_served(S):
+    """Requests on sizes that are not powers of two (1d n = 384 and 1536, 2d 96 x 60) are
+    admitted and finish, each equal to the same request run alone through the direct API."""
+    sgn, ctx = S
+    srv = sgn.Server(ctx)
+    tickets, spec = [], {}
+    for n in (384, 1536):
+        _, h, eta, b = I.testproblem_1d(n, 1.0, 1.0)
+        st, t = srv.submit(sgn.REQ_SOLVE, sgn.Grid(1, n, 1.0), dev(eta), dev(b), dev(h),
+                           rtol=1e-11, prec=sgn.PREC_MIXED)
+        assert st == 0
+        tickets.append(t)
+        spec[t] = ("solve1", n, h, eta, b)
+    c = I.ensemble_1d(count=1, seed=5, sizes=[768])[0]
+    st, t = srv.submit(sgn.REQ_RUN, sgn.Grid(1, c.n, c.L, g=c.g), dev(c.eta), dev(c.u), dev(c.h),
+                       scheme=sgn.SCHEME_RK4, dt=c.dt, nsteps=6, rtol=1e-10, prec=sgn.PREC_MIXED)
+    assert st == 0
+    tickets.append(t)
+    spec[t] = ("run1", c)
+    nx, ny, Lx, Ly = 96, 60, 24.0, 15.0
+    X, Y = I.grid_2d(nx, ny, Lx, Ly)
+    h2 = I.gaussian_bump_2d(X, Y, Lx, Ly, 0.4, 3.0, Lx / 2, Ly / 2)
+    eta2 = h2 + 0.2 * np.exp(np.cos(2 * np.pi * X / Lx) - 1)
+    us = np.stack([0.3 * np.sin(2 * np.pi * X / Lx), 0.2 * np.cos(2 * np.pi * Y / Ly)])
+    grid = O.make_grid(2, nx, Lx, 9.81, ny=ny, Ly=Ly)
+    b2 = O.apply_G(eta2, O.grad(h2, (Lx, Ly)), us, grid)
+    st, t = srv.submit(sgn.REQ_SOLVE, sgn.Grid(2, nx, Lx, g=9.81, ny=ny, Ly=Ly), dev(eta2),
+                       dev(b2), dev(h2), rtol=1e-11, prec=sgn.PREC_MIXED)
+    assert st == 0
+    tickets.append(t)
+    spec[t] = ("solve2", us)
+    res = wait(srv, tickets)
+    for t in tickets:
+        r = res[t]
+        assert r["status"] == 0, (spec[t][0], r)
+        kind = spec[t][0]
+        if kind == "solve1":
+            _, n, h, eta, b = spec[t]
+            x = sgn.device_array(r["u"], n).cpu().numpy()
+            ref = O.solve_G(eta, O.deriv(h, 1.0), b, O.make_grid(1, n, 1.0, 1.0), rtol=1e-14,
+                            maxit=4000)[0]
+            assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < 1e-9
+        elif kind == "run1":
+            c = spec[t][1]
+            ea, ua, Ua = alone_run(sgn, ctx, c, sgn.SCHEME_RK4, 6, 1e-10, sgn.PREC_MIXED)
+            eg = sgn.device_array(r["eta"], c.n).cpu().numpy()
+            ug = sgn.device_array(r["u"], c.n).cpu().numpy()
+            assert np.array_equal(eg, ea) and np.array_equal(ug, ua)
+        else:
+            x = sgn.device_array(r["u"], 2 * nx * ny).cpu().numpy().reshape(2, ny, nx)
+            assert np.linalg.norm(x - spec[t][1]) / np.linalg.norm(spec[t][1]) < 1e-8
+        srv.release(t)
+    srv.close()
