@@ -612,7 +612,7 @@ def bench_solitary(sgn, ctx, torch, steps=500):
             "status": s6["status"]}
 
 
-def bench_pcg2d(sgn, ctx, torch, B=16, n=512, L=80.0, seed=2024, reps=3):
+def bench_pcg2d(sgn, ctx, torch, B=16, n=512, L=80.0, seed=2024, reps=3, radix=16):
     """Batched 2d constraint solves: B instances of the bump workload's size (n^2, L = 80) on
     one grid, each with its own Gaussian bump (height U[0.1, 0.6], radius U[1, 5], centre
     U[0.3L, 0.7L]^2) and wave, right-hand side b = G u* for a smooth u* (formed on the GPU by
@@ -639,6 +639,7 @@ def bench_pcg2d(sgn, ctx, torch, B=16, n=512, L=80.0, seed=2024, reps=3):
                                     device="cuda")
     pack_v = lambda vs: np.concatenate([v[0].ravel() for v in vs] + [v[1].ravel() for v in vs])
     lay = sgn.Layout(ctx, [sgn.Grid(2, n, L, ny=n, Ly=L, g=9.81)] * B)
+    lay.set_radix2d(radix)
     eta = dev(np.concatenate([e.ravel() for e in etas]))
     gh = torch.zeros(2 * B * n * n, dtype=torch.float64, device="cuda")
     sgn.spectral_grad(lay, dev(np.concatenate([h.ravel() for h in hs])), gh)
@@ -668,7 +669,7 @@ def bench_pcg2d(sgn, ctx, torch, B=16, n=512, L=80.0, seed=2024, reps=3):
     alg_bytes = 60.0 * n * n * iters / launches        # per launch
     return {"workload": f"pcg2d_batch: {B} instances of {n}^2 (L = {L:g}) on one grid, Gaussian "
                         "bumps, b = G u*, mixed precision, rtol 1e-10",
-            "instances": B, "n": n, "solve_ms": min(ts),
+            "instances": B, "n": n, "max_radix": radix, "solve_ms": min(ts),
             "value": B * n * n / (min(ts) * 1e-3), "unit": "grid-point-solves/s",
             "rel_l2_vs_known_solution": err,
             "inner_iterations_per_instance": [i["iters"] for i in info],
