@@ -612,7 +612,7 @@ def bench_solitary(sgn, ctx, torch, steps=500):
             "status": s6["status"]}
 
 
-def bench_pcg2d(sgn, ctx, torch, B=16, n=512, L=80.0, seed=2024, reps=3, radix=16):
+def bench_pcg2d(sgn, ctx, torch, B=16, n=512, L=80.0, seed=2024, reps=3, radix=8):
     """Batched 2d constraint solves: B instances of the bump workload's size (n^2, L = 80) on
     one grid, each with its own Gaussian bump (height U[0.1, 0.6], radius U[1, 5], centre
     U[0.3L, 0.7L]^2) and wave, right-hand side b = G u* for a smooth u* (formed on the GPU by

@@ -161,8 +161,8 @@ sgn_status sgn_layout_get_forms(const sgn_layout* lay, int log2n, int* solve_cta
 sgn_status sgn_layout_set_form2d(sgn_layout* lay, int inner, int tile_width);
 sgn_status sgn_layout_get_form2d(const sgn_layout* lay, int* inner, int* tile_width);
 /* Radix plan of the persistent 2d inner solve's transforms (§6.1 D by FFT): the stages of a
- * length-2^k transform have radices up to max_radix (16, the default, or 8), split as evenly
- * as possible (1024 = 16 x 8 x 8 with 16; 8 x 8 x 4 x 4 with 8).  Both plans compute the
+ * length-2^k transform have radices up to max_radix (8, the default, or 16), split as evenly
+ * as possible (1024 = 8 x 8 x 4 x 4 with 8; 16 x 8 x 8 with 16).  Both plans compute the
  * same transform and agree up to rounding.  0 restores the default.  SGN_ERR_INVALID_ARG on
  * a 1d layout or another value, SGN_ERR_UNSUPPORTED_SIZE on a grid with a side that is not a
  * power of two.  sgn_state_autotune times the plans with the inner-solve forms. */
@@ -360,7 +360,7 @@ sgn_status sgn_state_set_dealias(sgn_state* st, int on);
  * left as it is.  For a 2d state it chooses the layout's inner-solve form and radix plan
  * (sgn_layout_set_form2d and sgn_layout_set_radix2d: the persistent launch with radix-16 or
  * radix-8 stages, or four kernels per inner iteration) the same way: each candidate timed
- * on RK4 steps from the same state in two passes, the default (persistent, radix 16) kept
+ * on RK4 steps from the same state in two passes, the default (persistent, radix 8) kept
  * unless another is at least 3% faster, the state restored.  A 2d grid with a side that is
  * not a power of two has one form: nothing to choose. */
 sgn_status sgn_state_autotune(sgn_state* st, const double* dt, const sgn_opts* opts,

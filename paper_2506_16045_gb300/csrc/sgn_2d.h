@@ -53,7 +53,7 @@ struct Layout2d {
   double* pparts = nullptr;
   unsigned* pbar = nullptr;
   int p_tw = 0, p_grid = 0;
-  int p_maxb = 4;           // the persistent form's transforms: stages up to radix 2^p_maxb
+  int p_maxb = 3;           // the persistent form's transforms: stages up to radix 2^p_maxb
   int inner_form = 0;
   // non-null while profiling: mixed solves take the host-driven path and bracket each
   // persistent launch with events

@@ -777,7 +777,7 @@ extern "C" sgn_status sgn_layout_set_radix2d(sgn_layout* lay, int max_radix) {
   if (check_layout(lay) || lay->dim != 2 || (max_radix != 0 && max_radix != 8 && max_radix != 16))
     return fail(lay ? lay->ctx : nullptr, SGN_ERR_INVALID_ARG, "set_radix2d args");
   if (lay->l2.mr) return fail(lay->ctx, SGN_ERR_UNSUPPORTED_SIZE, "no radix plans on this grid");
-  SGN_CUDA(lay->ctx, sgn::layout2d_set_radix(lay->l2, max_radix == 8 ? 3 : 4));
+  SGN_CUDA(lay->ctx, sgn::layout2d_set_radix(lay->l2, max_radix == 16 ? 4 : 3));
   return SGN_OK;
 }
 
@@ -1956,10 +1956,10 @@ sgn_status autotune_2d(sgn_state* st, const sgn_opts* opts, cudaStream_t s, doub
     r = fail(ctx, SGN_ERR_CUDA, "autotune events");
   }
   constexpr int kTimed = 2;
-  // candidates: the persistent form with radix-16 stages (the default), with radix-8 stages,
+  // candidates: the persistent form with radix-8 stages (the default), with radix-16 stages,
   // and the four-kernel form
   constexpr int kCand = 3;
-  const int cform[kCand] = {0, 0, 1}, cmaxb[kCand] = {4, 3, 4};
+  const int cform[kCand] = {0, 0, 1}, cmaxb[kCand] = {3, 4, 3};
   float t_of[kCand] = {0.0f, 0.0f, 0.0f};
   const int tw = L.p_tw;
   for (int pass = 0; pass < 2 && !r; ++pass) {

@@ -304,7 +304,7 @@ class Layout:
 
     def set_radix2d(self, max_radix):
         """sgn_layout_set_radix2d: the persistent inner solve's transform stages up to radix
-        16 (default, also 0) or 8."""
+        8 (default, also 0) or 16."""
         self.ctx.check(self.ctx.lib.sgn_layout_set_radix2d(self.h, max_radix),
                        "sgn_layout_set_radix2d")
 

@@ -81,10 +81,10 @@ def test_persistent_equals_four_kernel_form(S, nx, ny, Lx, Ly):
     lay = sgn.Layout(ctx, [sgn.Grid(2, nx, Lx, ny=ny, Ly=Ly, g=9.81)])
     out = {}
     # the four-kernel form, the persistent form (twice: bitwise repeatable), and the
-    # persistent form with radix-8 stages
+    # persistent form with radix-16 stages
     for form in (1, 0, 0, 2):
         lay.set_form2d(1 if form == 1 else 0, 0)
-        lay.set_radix2d(8 if form == 2 else 16)
+        lay.set_radix2d(16 if form == 2 else 8)
         x = torch.zeros(2 * nx * ny, dtype=torch.float64, device="cuda")
         info = sgn.pcg(lay, dev(eta), dev(gh), dev(b), x, rtol=1e-11, maxit=4000,
                        prec=sgn.PREC_MIXED)[0]
@@ -95,9 +95,9 @@ def test_persistent_equals_four_kernel_form(S, nx, ny, Lx, Ly):
     x1, x0, x8 = out[1][0].cpu().numpy(), out[0][0].cpu().numpy(), out[2][0].cpu().numpy()
     assert rel(x0, x1) < 1e-9 and rel(x8, x0) < 1e-9
     assert rel(x0.reshape(2, ny, nx), us) < 1e-8
-    assert lay.radix2d() == 8
-    lay.set_radix2d(0)
     assert lay.radix2d() == 16
+    lay.set_radix2d(0)                  # the default
+    assert lay.radix2d() == 8
     # same method, so the inner iteration counts stay close
     i0, i1 = out[0][1]["iters"], out[1][1]["iters"]
     assert abs(i0 - i1) <= max(2, 0.1 * i1), (i0, i1)
