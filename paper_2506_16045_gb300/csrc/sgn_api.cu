@@ -1154,6 +1154,10 @@ struct sgn_state {
   double* eta_p = nullptr;          // SBDF2 previous level
   double* U_p = nullptr;
   double* ut = nullptr;             // non-constraint form: the last u_t (next warm start)
+  // RK4 history for the first stage solve's starting point: u at the start of the last RK4
+  // step (u_prev) and the u that step returned (u_last; NaN when there is none)
+  double* u_prev = nullptr;
+  double* u_last = nullptr;
   void* res0 = nullptr;             // SBDF2 residual spectra (previous / current)
   void* res1 = nullptr;
   double* dt_dev = nullptr;
@@ -1202,11 +1206,18 @@ sgn_status alloc_state(sgn_state* st) {
   }
   if (!(st->eta_s = get(P)) || !(st->U_s = get(V)) || !(st->u_s = get(V)) ||
       !(st->eta_p = get(P)) || !(st->U_p = get(V)) || !(st->ut = get(V)) ||
+      !(st->u_prev = get(V)) || !(st->u_last = get(V)) ||
       !(st->dt_dev = get(st->lay->count)) || !(st->t_dev = get(st->lay->count)))
     return SGN_ERR_NOMEM;
   const size_t res_bytes = st->lay->dim == 1 ? sizeof(double) * 2 * (size_t)(st->lay->l1.ws_cplx /
                                                                             sgn::kWsVectors)
                                              : sgn::layout2d_res_bytes(st->lay->l2);
+  // no RK4 history yet: NaN compares unequal to every u
+  if (cudaMemset(st->u_last, 0xff, sizeof(double) * (size_t)std::max<long long>(V, 1)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return SGN_ERR_NOMEM;
+  }
   if (cudaMalloc(&st->res0, res_bytes) != cudaSuccess ||
       cudaMalloc(&st->res1, res_bytes) != cudaSuccess ||
       cudaMalloc(&st->A_fixed, sizeof(SolveRec) * st->lay->count) != cudaSuccess ||
@@ -1247,6 +1258,21 @@ LinComb make_lincomb(Terms xs, Terms fs) {
     ++lc.nf;
   }
   return lc;
+}
+
+// Starting point of the first RK4 stage solve (c = 1/2, reading R8): at every point where u
+// is still the value the last RK4 step of this state returned, u + (u - u_prev) / 2, the
+// linear extrapolation to t + dt/2 from that step's start (an O(dt^2) guess in place of
+// O(dt)); elsewhere (no history, or u changed since) u itself.  Only the solve's starting
+// point depends on it; its stopping rule is unchanged.
+__global__ void k_rk4_guess(long long n, const double* __restrict__ u,
+                            const double* __restrict__ u_last, const double* __restrict__ u_prev,
+                            double* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = u[i];
+    out[i] = v == u_last[i] ? 1.5 * v - 0.5 * u_prev[i] : v;
+  }
 }
 
 // out = sum a_t x_t + dt sum c_t f_t for scalar (components=1) or vector fields; with out2
@@ -1406,7 +1432,12 @@ sgn_status rk4_once(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
   const long long P = st->P, V = d * P;
   static const double a[4] = {0.0, 0.5, 0.5, 1.0};
   SGN_TRY(rhs_at(st, st->eta, st->u, st->fe[0], st->fU[0], s));
-  SGN_TRY(copy_field(st, st->u_s, st->u, V, s));
+  {
+    const long long nb = std::min<long long>((V + 255) / 256, 4096);
+    k_rk4_guess<<<(int)std::max<long long>(nb, 1), 256, 0, s>>>(V, st->u, st->u_last,
+                                                                  st->u_prev, st->u_s);
+    SGN_CUDA(st->lay->ctx, cudaGetLastError());
+  }
   for (int i = 1; i < 4; ++i) {
     SGN_TRY(lincomb(st, st->eta_s, {{st->eta, 1.0}}, {{st->fe[i - 1], a[i]}}, 1, s, st->U_s,
                     {{st->U, 1.0}}, {{st->fU[i - 1], a[i]}}, d));
@@ -1421,8 +1452,10 @@ sgn_status rk4_once(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
                   st->U, {{st->U, 1.0}},
                   {{st->fU[0], b0}, {st->fU[1], b1}, {st->fU[2], b1}, {st->fU[3], b0}}, d));
   SGN_TRY(dealias_at(st, st->eta, st->U, nullptr, s));
+  SGN_TRY(copy_field(st, st->u_prev, st->u, V, s));        // u at this step's start
   SGN_TRY(copy_field(st, st->u, st->u_s, V, s));
   SGN_TRY(solve_at(st, st->eta, st->U, st->u, o, s));
+  SGN_TRY(copy_field(st, st->u_last, st->u, V, s));        // the u this step returns
   SGN_TRY(advance_time(st, s));
   (void)P;
   st->t += st->dt_last[0];
@@ -1483,6 +1516,8 @@ extern "C" sgn_status sgn_state_init(sgn_state* st, sgn_stream stream) {
   SGN_CUDA(ctx, cudaMemsetAsync(st->stats, 0, sizeof(DevStats), s));
   SGN_CUDA(ctx, cudaMemsetAsync(st->t_dev, 0, sizeof(double) * st->lay->count, s));
   SGN_CUDA(ctx, cudaMemsetAsync(st->ut, 0, sizeof(double) * st->d * st->P, s));
+  // the RK4 history starts over (NaN compares unequal to every u)
+  SGN_CUDA(ctx, cudaMemsetAsync(st->u_last, 0xff, sizeof(double) * st->d * st->P, s));
   st->hist = HIST_NONE;
   st->levels = 0;
   st->t = 0.0;
@@ -1495,6 +1530,11 @@ extern "C" sgn_status sgn_state_init(sgn_state* st, sgn_stream stream) {
 // gradh and U were computed earlier, for example per request before packing into a
 // batch); clear counters and multistep history only.
 namespace sgn {
+// The RK4 history arrays of a state (d P doubles each; see k_rk4_guess), for callers that
+// pack a request's state into a shared batched state and back (the server).
+double* state_rk4_prev(sgn_state* st) { return st->u_prev; }
+double* state_rk4_last(sgn_state* st) { return st->u_last; }
+
 sgn_status state_attach(sgn_state* st, cudaStream_t s) {
   if (!st) return SGN_ERR_INVALID_ARG;
   DeviceGuard g(st->lay->device);

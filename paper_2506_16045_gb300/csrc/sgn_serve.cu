@@ -38,6 +38,8 @@
 
 namespace sgn {
 sgn_status state_attach(sgn_state* st, cudaStream_t s);
+double* state_rk4_prev(sgn_state* st);
+double* state_rk4_last(sgn_state* st);
 }
 
 namespace {
@@ -59,6 +61,7 @@ struct Req {
   double* h = nullptr;
   double* U = nullptr;
   double* gh = nullptr;
+  double* hist = nullptr;             // batched 1d RK4 runs: the RK4 history (u_prev, u_last)
   // per-request objects (2d / multistep runs, 2d solves)
   sgn_layout* lay = nullptr;
   sgn_state* st = nullptr;
@@ -145,7 +148,7 @@ namespace {
 constexpr int kInfoSlots = 8192;
 
 size_t footprint_of(int d, long long N) {
-  const size_t io = (size_t)(2 + 3 * d) * 8 * N;          // eta, h, u/b, U, gradh
+  const size_t io = (size_t)(2 + 3 * d) * 8 * N + (d == 1 ? 16 * N : 0);   // + RK4 history
   const size_t work = d == 1 ? (size_t)260 * N : (size_t)816 * N;
   const size_t big = (d == 1 && N > 6144) ? (size_t)32 * N : 0;   // global transform buffers
   return io + work + big + (1 << 16);
@@ -159,7 +162,8 @@ void free_req_work(Req* r) {
   cudaFree(r->h);
   cudaFree(r->gh);
   cudaFree(r->b);
-  r->h = r->gh = r->b = nullptr;
+  cudaFree(r->hist);
+  r->h = r->gh = r->b = r->hist = nullptr;
   if (r->ready) cudaEventDestroy(r->ready);
   r->ready = nullptr;
   if (r->own) cudaStreamDestroy(r->own);
@@ -263,6 +267,14 @@ sgn_status start(sgn_server* S, Req* r) {
   if (r->q.kind == SGN_REQ_RUN && is_batched_run(r)) {
     sgn_layout* lay = one_layout(S, r->q.grid);
     if (!lay) return SGN_ERR_NOMEM;
+    // the request's own RK4 history travels with it through the batched state, so its
+    // result does not depend on the requests beside it (no history yet: NaN)
+    if (cudaMalloc(&r->hist, sizeof(double) * 2 * (size_t)r->N) != cudaSuccess ||
+        cudaMemsetAsync(r->hist + r->N, 0xff, sizeof(double) * (size_t)r->N, S->stream) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return SGN_ERR_NOMEM;
+    }
     e = sgn_spectral_grad(S->ctx, lay, r->h, r->gh, s);
     if (!e) e = sgn_apply_operator(S->ctx, lay, r->eta, r->gh, r->u, r->U, s);
   } else if (r->q.kind == SGN_REQ_RUN) {
@@ -401,11 +413,15 @@ void issue_run_batch(sgn_server* S, std::vector<Req*>& v) {
     const long long P = off.back();
     double* F[5] = {S->pk, S->pk + P, S->pk + 2 * P, S->pk + 3 * P, S->pk + 4 * P};
     wait_ready(J->s, v);
+    double* Hp = sgn::state_rk4_prev(S->run_st);
+    double* Hl = sgn::state_rk4_last(S->run_st);
     for (size_t i = 0; i < v.size(); ++i) {
       double* src[5] = {v[i]->eta, v[i]->U, v[i]->u, v[i]->h, v[i]->gh};
+      const size_t bytes = sizeof(double) * (size_t)v[i]->N;
       for (int f = 0; f < 5; ++f)
-        cudaMemcpyAsync(F[f] + off[i], src[f], sizeof(double) * (size_t)v[i]->N,
-                        cudaMemcpyDeviceToDevice, J->s);
+        cudaMemcpyAsync(F[f] + off[i], src[f], bytes, cudaMemcpyDeviceToDevice, J->s);
+      cudaMemcpyAsync(Hp + off[i], v[i]->hist, bytes, cudaMemcpyDeviceToDevice, J->s);
+      cudaMemcpyAsync(Hl + off[i], v[i]->hist + v[i]->N, bytes, cudaMemcpyDeviceToDevice, J->s);
     }
     std::vector<double> dts;
     for (Req* r : v) dts.push_back(r->q.dt);
@@ -414,9 +430,11 @@ void issue_run_batch(sgn_server* S, std::vector<Req*>& v) {
     if (!e) e = sgn_step_rk4(S->run_st, dts.data(), K, &o, J->s);
     for (size_t i = 0; i < v.size(); ++i) {
       double* dst[3] = {v[i]->eta, v[i]->U, v[i]->u};
+      const size_t bytes = sizeof(double) * (size_t)v[i]->N;
       for (int f = 0; f < 3; ++f)
-        cudaMemcpyAsync(dst[f], F[f] + off[i], sizeof(double) * (size_t)v[i]->N,
-                        cudaMemcpyDeviceToDevice, J->s);
+        cudaMemcpyAsync(dst[f], F[f] + off[i], bytes, cudaMemcpyDeviceToDevice, J->s);
+      cudaMemcpyAsync(v[i]->hist, Hp + off[i], bytes, cudaMemcpyDeviceToDevice, J->s);
+      cudaMemcpyAsync(v[i]->hist + v[i]->N, Hl + off[i], bytes, cudaMemcpyDeviceToDevice, J->s);
     }
     if (cudaGetLastError() != cudaSuccess && !e) e = SGN_ERR_CUDA;
   }
