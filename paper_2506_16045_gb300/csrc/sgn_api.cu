@@ -2027,6 +2027,8 @@ sgn_status autotune_2d(sgn_state* st, const sgn_opts* opts, cudaStream_t s, doub
   sgn::layout2d_set_radix(L, cmaxb[best]);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
+  // the state is as it was before tuning, with no RK4 history (as after sgn_state_init)
+  cudaMemsetAsync(st->u_last, 0xff, sizeof(double) * st->d * st->P, s);
   cudaStreamSynchronize(s);
   cudaFree(save);
   st->last = s;
@@ -2137,6 +2139,8 @@ extern "C" sgn_status sgn_state_autotune(sgn_state* st, const double* dt, const 
   L.gen += 1;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
+  // the state is as it was before tuning, with no RK4 history (as after sgn_state_init)
+  cudaMemsetAsync(st->u_last, 0xff, sizeof(double) * st->d * st->P, s);
   cudaStreamSynchronize(s);
   cudaFree(save);
   st->last = s;
