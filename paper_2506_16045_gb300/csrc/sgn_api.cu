@@ -1260,18 +1260,19 @@ LinComb make_lincomb(Terms xs, Terms fs) {
   return lc;
 }
 
-// Starting point of the first RK4 stage solve (c = 1/2, reading R8): at every point where u
-// is still the value the last RK4 step of this state returned, u + (u - u_prev) / 2, the
-// linear extrapolation to t + dt/2 from that step's start (an O(dt^2) guess in place of
-// O(dt)); elsewhere (no history, or u changed since) u itself.  Only the solve's starting
-// point depends on it; its stopping rule is unchanged.
-__global__ void k_rk4_guess(long long n, const double* __restrict__ u,
-                            const double* __restrict__ u_last, const double* __restrict__ u_prev,
-                            double* __restrict__ out) {
+// Starting point of a time step's first solve (reading R8): at every point where u is still
+// the value the last step of this state returned, u + c (u - u_prev), the linear
+// extrapolation from that step's start (c = 1/2: the RK4 stage at t + dt/2; c = 1: the AB
+// solve at t + dt), an O(dt^2) guess in place of u's O(dt); elsewhere (no history, or u
+// changed since) u itself.  Only the solve's starting point depends on it; its stopping
+// rule is unchanged.
+__global__ void k_step_guess(long long n, double c, const double* __restrict__ u,
+                             const double* __restrict__ u_last,
+                             const double* __restrict__ u_prev, double* __restrict__ out) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const double v = u[i];
-    out[i] = v == u_last[i] ? 1.5 * v - 0.5 * u_prev[i] : v;
+    out[i] = v == u_last[i] ? v + c * (v - u_prev[i]) : v;
   }
 }
 
@@ -1427,17 +1428,22 @@ sgn_status stage_at(sgn_state* st, const double* eta, const double* U, double* u
 }
 
 // One RK4 step (Eq:ERK): stages with a_{i,i-1} = 1/2, 1/2, 1 and weights 1/6, 1/3, 1/3, 1/6.
+// u_s = the first solve's starting point (k_step_guess, c as there)
+sgn_status step_guess(sgn_state* st, double c, double* out, cudaStream_t s) {
+  const long long V = (long long)st->d * st->P;
+  const long long nb = std::min<long long>((V + 255) / 256, 4096);
+  k_step_guess<<<(int)std::max<long long>(nb, 1), 256, 0, s>>>(V, c, st->u, st->u_last,
+                                                                st->u_prev, out);
+  SGN_CUDA(st->lay->ctx, cudaGetLastError());
+  return SGN_OK;
+}
+
 sgn_status rk4_once(sgn_state* st, const sgn_opts* o, cudaStream_t s) {
   const int d = st->d;
   const long long P = st->P, V = d * P;
   static const double a[4] = {0.0, 0.5, 0.5, 1.0};
   SGN_TRY(rhs_at(st, st->eta, st->u, st->fe[0], st->fU[0], s));
-  {
-    const long long nb = std::min<long long>((V + 255) / 256, 4096);
-    k_rk4_guess<<<(int)std::max<long long>(nb, 1), 256, 0, s>>>(V, st->u, st->u_last,
-                                                                  st->u_prev, st->u_s);
-    SGN_CUDA(st->lay->ctx, cudaGetLastError());
-  }
+  SGN_TRY(step_guess(st, 0.5, st->u_s, s));
   for (int i = 1; i < 4; ++i) {
     SGN_TRY(lincomb(st, st->eta_s, {{st->eta, 1.0}}, {{st->fe[i - 1], a[i]}}, 1, s, st->U_s,
                     {{st->U, 1.0}}, {{st->fU[i - 1], a[i]}}, d));
@@ -1734,8 +1740,14 @@ extern "C" sgn_status sgn_step_abk(sgn_state* st, int order, const double* dt, i
       // above were launched with the current history pointers, so rotating is safe)
       make_room();
       SGN_TRY(advance_time(st, s));          // the new level's right-hand side is at t_{n+1}
+      // the solve starts from u extrapolated from the last step (reading R8)
+      const long long V = (long long)d * st->P;
+      SGN_TRY(step_guess(st, 1.0, st->u_s, s));
+      SGN_TRY(copy_field(st, st->u_prev, st->u, V, s));
+      SGN_TRY(copy_field(st, st->u, st->u_s, V, s));
       SGN_TRY(stage_at(st, st->eta, st->U, st->u, st->he[st->levels], st->hU[st->levels], opts,
                        s, 0.0));
+      SGN_TRY(copy_field(st, st->u_last, st->u, V, s));
       st->levels += 1;
       st->t += st->dt_last[0];
       st->step += 1;
