@@ -560,10 +560,15 @@ class State:
         self.dealias = False       # 2/3-rule projection of every new level (reading R19)
         self.solves = 0
         self.iterations = 0
+        # the last step's starting u and the u it returned (reading R8's first-solve guess)
+        self.u_prev = None
+        self.u_last = None
 
     def copy(self):
         s = State(self.eta, self.U, self.u, self.h, self.gradh, self.grid, self.t, self.forcing)
         s.solves, s.iterations, s.dealias = self.solves, self.iterations, self.dealias
+        s.u_prev = None if self.u_prev is None else self.u_prev.copy()
+        s.u_last = None if self.u_last is None else self.u_last.copy()
         return s
 
 
@@ -627,6 +632,18 @@ def _rhs_t(st: State, eta, u, t):
     return a, b
 
 
+def _step_guess(st: State, c):
+    """Reading R8: the first solve of a step starts, at every point where u is still the value
+    the last step returned, from u + c (u - u_prev), the linear extrapolation from that step's
+    start (c = 1/2 for the RK4 stage at t + dt/2, c = 1 for the AB solve at t + dt); elsewhere
+    (no history, or u changed since) from u itself."""
+    u = st.u
+    if st.u_last is None:
+        return u.copy()
+    same = u == st.u_last
+    return np.where(same, u + c * (u - st.u_prev), u)
+
+
 def _solve(st: State, eta, U, x0, rtol, maxit):
     x, it, _, _ = solve_G(eta, st.gradh, U, st.grid, x0=x0, rtol=rtol, maxit=maxit)
     st.solves += 1
@@ -636,21 +653,30 @@ def _solve(st: State, eta, U, x0, rtol, maxit):
 
 def rk4_step(st: State, dt, rtol=1e-12, maxit=2000):
     """One classical RK4 step of Eq:ERK with one constraint solve per stage 2..4 and one
-    for u_{n+1} (readings R2, R8)."""
-    eta_n, U_n = st.eta, st.U
+    for u_{n+1} (readings R2, R8: the stage at c = 1/2 starts from the extrapolated guess of
+    _step_guess, the stage at c = 1 from 2 u^(3) - u_n, the others from the previous
+    stage's u)."""
+    eta_n, U_n, u_n = st.eta, st.U, st.u
     fe, fU = [], []
-    eta_i, U_i, u_i = eta_n, U_n, st.u
+    eta_i, U_i, u_i = eta_n, U_n, u_n
     for i in range(4):
         if i > 0:
             eta_i = eta_n + dt * sum(RK4_A[i][j] * fe[j] for j in range(i))
             U_i = U_n + dt * sum(RK4_A[i][j] * fU[j] for j in range(i))
-            u_i = _solve(st, eta_i, U_i, u_i, rtol, maxit)
+            if i == 1:
+                x0 = _step_guess(st, 0.5)
+            elif i == 3:
+                x0 = 2.0 * u_i - u_n
+            else:
+                x0 = u_i
+            u_i = _solve(st, eta_i, U_i, x0, rtol, maxit)
         a, b = _rhs_t(st, eta_i, u_i, st.t + dt * sum(RK4_A[i]))
         fe.append(a)
         fU.append(b)
     st.eta, st.U = _new_level(st, eta_n + dt * sum(RK4_B[j] * fe[j] for j in range(4)),
                               U_n + dt * sum(RK4_B[j] * fU[j] for j in range(4)))
     st.u = _solve(st, st.eta, st.U, u_i, rtol, maxit)
+    st.u_prev, st.u_last = u_n.copy(), st.u.copy()
     st.t += dt
     return st
 
@@ -716,7 +742,9 @@ def run_ab(st: State, order, dt, nsteps, rtol=1e-12):
         fe = sum(b[j] * hist[j][0] for j in range(s))
         fU = sum(b[j] * hist[j][1] for j in range(s))
         st.eta, st.U = _new_level(st, st.eta + dt * fe, st.U + dt * fU)
-        st.u = _solve(st, st.eta, st.U, st.u, rtol, 2000)
+        u_n = st.u
+        st.u = _solve(st, st.eta, st.U, _step_guess(st, 1.0), rtol, 2000)
+        st.u_prev, st.u_last = u_n.copy(), st.u.copy()
         st.t += dt
         done += 1
         hist = hist[1:] + [_rhs_t(st, st.eta, st.u, st.t)]
