@@ -452,8 +452,8 @@ double sgn_clock(void);
  * when non-NULL the call synchronises the stream and returns the instance status.
  *
  * Works on the current device.  The first call on a device does a one-time set-up (symbol
- * address lookups and the twiddle-table kernel) and synchronises the stream; make that
- * first call before any stream capture.  Under CUDA's default lazy module loading that
+ * address lookups and the twiddle-table kernel) and synchronises the stream.  Under
+ * CUDA's default lazy module loading that
  * first call is also where the driver loads this library's kernels and places the static
  * arrays in device memory, so a caller whose memory is frozen after start-up must make
  * the first call during start-up, before the freeze: "no allocation" holds from the
