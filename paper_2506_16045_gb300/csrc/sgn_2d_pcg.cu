@@ -21,7 +21,10 @@
 // loop together; no scalar goes through the host.
 //
 // Data produced by other CTAs inside the launch (transform planes, Krylov vectors, partial
-// sums) is read with ld.global.cg (L2, never a stale L1 line).  Each barrier waits at most
+// sums) is read with ld.global.cg or copied to shared memory with cp.async.cg (both from L2,
+// never a stale L1 line).  Where the shared memory allows (sides up to 512), the staged form
+// gives each group a third buffer and issues all of a unit's input copies at once, so a
+// unit waits for memory once instead of once per batch of rows.  Each barrier waits at most
 // kBarrierTimeoutNs; a CTA that gives up sets the error word, every CTA then leaves the
 // loop at its next barrier, and the solve reports SGN_ERR_TIMEOUT.  The launch is
 // cooperative, so every CTA of the grid is resident at once.
@@ -229,6 +232,13 @@ __device__ __forceinline__ cplx<float> ldcg(const cplx<float>* p) {
 __device__ __forceinline__ void stcg(cplx<float>* p, cplx<float> v) {
   __stcg(reinterpret_cast<float2*>(p), make_float2(v.x, v.y));
 }
+// Asynchronous 16-byte copy global -> shared that bypasses L1 (cp.async.cg), and the wait
+// for all of this thread's copies; both addresses 16-byte aligned.
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Grid-wide barrier on a monotone arrival counter: the k-th barrier of the launch waits for
 // k * gridDim.x arrivals.  Returns true when the launch must stop (a wait gave up here or
@@ -317,16 +327,33 @@ __device__ __forceinline__ void group_part(float v, df* slot, double* out, int t
 }
 
 // Shared memory of the kernel: the twiddle table, then per group two transform buffers of
-// three columns of ny or three rows of nx (padded).
+// three columns of ny or three rows of nx (padded) and, in the staged form, a third buffer
+// C that receives a unit's global inputs by asynchronous copies.
 struct PSmem {
   cplx<float>* twx;     // twiddles of length nx
   cplx<float>* twy;     // of length ny (the same table when ny = nx)
   cplx<float>* A;       // this group's buffers
   cplx<float>* B;
+  cplx<float>* C;       // staged form only
 };
+
+// Sizes in complex float32 entries, both even (16-byte aligned buffers).  A and B each hold
+// three padded transforms; staged, B also takes the raw row pairs of a row unit (6 (nx/2 + 1)
+// entries).  C holds the largest unit input: six columns of ny (the C2 update vectors) or
+// three planes' float32 coefficients of two rows (3 nx entries).
+__host__ __device__ inline int persist_be(int nx, int ny, bool stg) {
+  int be = 3 * pad_len(nx > ny ? nx : ny);
+  if (stg && be < 6 * (nx / 2 + 1)) be = 6 * (nx / 2 + 1);
+  return (be + 1) & ~1;
+}
+__host__ __device__ inline int persist_bc(int nx, int ny, bool stg) {
+  if (!stg) return 0;
+  return 6 * ny > 3 * nx ? 6 * ny : 3 * nx;
+}
 
 // ---- C1: p update, projection, divergence, column iFFT (column c, group g) -------------
 // The solve's vectors and transform planes are column-major, [H][ny]: a column is contiguous.
+template <bool STG>
 __device__ __forceinline__ void col_inverse(const PersistArgs2d& a, const PInst2d& I,
                                          const IScal& s, int c, const PSmem& sm, int t, int g) {
   const int ny = a.ny, S = pad_len(ny), nx = a.nx;
@@ -338,6 +365,29 @@ __device__ __forceinline__ void col_inverse(const PersistArgs2d& a, const PInst2
   const cplx<float>* __restrict__ r1p = I.r[1] + cb;
   cplx<float>* __restrict__ p0 = I.p[0] + cb;
   cplx<float>* __restrict__ p1p = I.p[1] + cb;
+  if constexpr (STG) {
+    // every load of the unit in flight at once: r1, r2 (and p1, p2 when beta != 0) into C as
+    // 16-byte copies, then p = A^{-1} r + beta p from shared memory
+    cplx<float>* Cb = sm.C;
+    const int lch = a.logny - 1, nch = (upd ? 4 : 2) << lch;
+    for (int i = t; i < nch; i += kGT) {
+      const int q = i >> lch, e = (i - (q << lch)) << 1;
+      const cplx<float>* src = q == 0 ? r0 : (q == 1 ? r1p : (q == 2 ? p0 : p1p));
+      cp16(Cb + q * ny + e, src + e);
+    }
+    cp_wait_all();
+    gsync(g);
+    for (int y = t; y < ny; y += kGT) {
+      cplx<float> p1, p2;
+      ainv(s, kx, ky_of(s, y, ny), Cb[y], Cb[ny + y], p1, p2);
+      if (upd) {
+        p1 = p1 + Cb[2 * ny + y] * s.beta;
+        p2 = p2 + Cb[3 * ny + y] * s.beta;
+      }
+      buf[pad(y)] = p1;
+      buf[S + pad(y)] = p2;
+    }
+  } else {
   // the column's loads first (kRows rows per thread in flight), then the shared stores
   for (int y0 = 0; y0 < ny; y0 += kRows * kGT) {
     cplx<float> r1[kRows], r2[kRows], q1[kRows], q2[kRows];
@@ -367,6 +417,7 @@ __device__ __forceinline__ void col_inverse(const PersistArgs2d& a, const PInst2
         buf[S + pad(y)] = p2;
       }
     }
+  }
   }
   gsync(g);
   // the kx = 0 and kx = nx/2 columns of a real field are Hermitian in ky: project out the
@@ -399,6 +450,7 @@ __device__ __forceinline__ void col_inverse(const PersistArgs2d& a, const PInst2
 }
 
 // ---- R: C2R, Def:MatrixM pointwise with the p.Gp partial, R2C (row pair y0, group g) -----
+template <bool STG>
 __device__ __forceinline__ float row_matvec(const PersistArgs2d& a, const PInst2d& I, int y0,
                                             const PSmem& sm, int t, int g) {
   const int nx = a.nx, h = nx >> 1, S = pad_len(nx);
@@ -417,6 +469,33 @@ __device__ __forceinline__ float row_matvec(const PersistArgs2d& a, const PInst2
     z[S + pad(m)] = mk(u1.x - v1.y, u1.y + v1.x);
     z[2 * S + pad(m)] = mk(u2.x - v2.y, u2.y + v2.x);
   };
+  // staged: the raw row pairs of the three planes go to B (16-byte entries [q (h + 1) + m])
+  // and the six coefficient rows (eta, h_x, h_y of rows y0, y1) to C ([(2 j + r) nx + x]),
+  // all copies in flight at once; the packing then reads shared memory
+  const float* ef = reinterpret_cast<const float*>(sm.C);
+  if constexpr (STG) {
+    float4* raw = reinterpret_cast<float4*>(sm.B);
+    const int hp = h + 1;
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      for (int m = t; m <= h; m += kGT) cp16(raw + q * hp + m, I.t[q] + (long long)m * a.ny + y0);
+    float* ed = reinterpret_cast<float*>(sm.C);
+    const int lc = a.lognx - 2, nch = 6 << lc;
+    for (int i = t; i < nch; i += kGT) {
+      const int row = i >> lc, e = (i - (row << lc)) << 2, j = row >> 1, r = row & 1;
+      cp16(ed + row * nx + e, I.ehh + j * P + (long long)(y0 + r) * nx + e);
+    }
+    cp_wait_all();
+    gsync(g);
+    for (int m = t; m <= h; m += kGT) {
+      const float4 A0 = raw[m], A1 = raw[hp + m], A2 = raw[2 * hp + m];
+      const cplx<float> a0 = mk(A0.x, A0.y), a1 = mk(A0.z, A0.w);
+      const cplx<float> b0 = mk(A1.x, A1.y), b1 = mk(A1.z, A1.w);
+      const cplx<float> d0 = mk(A2.x, A2.y), d1 = mk(A2.z, A2.w);
+      put(m, a0, b0, a1, b1, d0, d1);
+      if (m > 0 && m < h) put(nx - m, conj(a0), conj(b0), conj(a1), conj(b1), conj(d0), conj(d1));
+    }
+  } else
   for (int m0 = 0; m0 <= h; m0 += kRows * kGT) {
     float4 A0[kRows], A1[kRows], A2[kRows];
 #pragma unroll
@@ -455,10 +534,16 @@ __device__ __forceinline__ float row_matvec(const PersistArgs2d& a, const PInst2
       if (x < nx) {
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-          const long long j = (long long)(r ? y1 : y0) * nx + x;
-          ev[k][r] = I.ehh[j];
-          hxv[k][r] = I.ehh[P + j];
-          hyv[k][r] = I.ehh[2 * P + j];
+          if constexpr (STG) {
+            ev[k][r] = ef[r * nx + x];
+            hxv[k][r] = ef[(2 + r) * nx + x];
+            hyv[k][r] = ef[(4 + r) * nx + x];
+          } else {
+            const long long j = (long long)(r ? y1 : y0) * nx + x;
+            ev[k][r] = I.ehh[j];
+            hxv[k][r] = I.ehh[P + j];
+            hyv[k][r] = I.ehh[2 * P + j];
+          }
         }
       }
     }
@@ -508,12 +593,37 @@ __device__ __forceinline__ float row_matvec(const PersistArgs2d& a, const PInst2
 }
 
 // ---- C2: column FFT, G p, x and r updates, r.z partial (column c, group g) ---------------
+template <bool STG>
 __device__ __forceinline__ float col_forward_update(const PersistArgs2d& a, const PInst2d& I,
                                                     const IScal& s, int c, const PSmem& sm,
                                                     int t, int g) {
   const int ny = a.ny, S = pad_len(ny), nx = a.nx;
   const long long cb = (long long)c * ny;
   cplx<float>* buf = sm.A;
+  const cplx<float>* Cb = sm.C;
+  if constexpr (STG) {
+    // every load of the unit in flight at once: the three plane columns to B (unpadded) and
+    // p1, p2, x1, x2, r1, r2 to C, as 16-byte copies; then the planes are spread into A's
+    // padded transform layout
+    cplx<float>* Bb = sm.B;
+    cplx<float>* Cw = sm.C;
+    const int lch = a.logny - 1;
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      for (int e = 2 * t; e < ny; e += 2 * kGT) cp16(Bb + q * ny + e, I.t[q] + cb + e);
+    const int nch = 6 << lch;
+    for (int i = t; i < nch; i += kGT) {
+      const int q = i >> lch, e = (i - (q << lch)) << 1;
+      const cplx<float>* src = q < 2 ? I.p[q] : (q < 4 ? I.x[q - 2] : I.r[q - 4]);
+      cp16(Cw + q * ny + e, src + cb + e);
+    }
+    cp_wait_all();
+    gsync(g);
+    for (int y = t; y < ny; y += kGT) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) buf[q * S + pad(y)] = Bb[q * ny + y];
+    }
+  } else
   for (int y0 = 0; y0 < ny; y0 += kRows * kGT) {
     cplx<float> v[3][kRows];
 #pragma unroll
@@ -552,12 +662,21 @@ __device__ __forceinline__ float col_forward_update(const PersistArgs2d& a, cons
     for (int k = 0; k < KU; ++k) {
       const int y = y0 + t + k * kGT;
       if (y < ny) {
-        p1[k] = ldcg(P0 + y);
-        p2[k] = ldcg(P1 + y);
-        x1[k] = ldcg(X0 + y);
-        x2[k] = ldcg(X1 + y);
-        r1[k] = ldcg(R0 + y);
-        r2[k] = ldcg(R1 + y);
+        if constexpr (STG) {
+          p1[k] = Cb[y];
+          p2[k] = Cb[ny + y];
+          x1[k] = Cb[2 * ny + y];
+          x2[k] = Cb[3 * ny + y];
+          r1[k] = Cb[4 * ny + y];
+          r2[k] = Cb[5 * ny + y];
+        } else {
+          p1[k] = ldcg(P0 + y);
+          p2[k] = ldcg(P1 + y);
+          x1[k] = ldcg(X0 + y);
+          x2[k] = ldcg(X1 + y);
+          r1[k] = ldcg(R0 + y);
+          r2[k] = ldcg(R1 + y);
+        }
       }
     }
 #pragma unroll
@@ -582,20 +701,24 @@ __device__ __forceinline__ float col_forward_update(const PersistArgs2d& a, cons
   return part;
 }
 
+// STG: the staged form (a third shared buffer per group takes each unit's global inputs
+// by asynchronous copies, all in flight at once); otherwise loads go through registers.
+template <bool STG>
 __global__ void __launch_bounds__(kPNT, 1) k2_pcg_persist(const __grid_constant__ PersistArgs2d a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ IScal S[kMaxBatch2d];
   __shared__ df slot[kPNT / 32];        // the groups' warp totals
   __shared__ int s_stop;
-  // thread t of group g; the group's two transform buffers after the twiddle table
+  // thread t of group g; the group's buffers after the twiddle table
   const int g = threadIdx.x / kGT, t = threadIdx.x - g * kGT;
-  const long long be = 3ll * pad_len(a.nx > a.ny ? a.nx : a.ny);
+  const int be = persist_be(a.nx, a.ny, STG), bc = persist_bc(a.nx, a.ny, STG);
   const int ntw = a.nx + (a.ny == a.nx ? 0 : a.ny);
   PSmem sm;
   sm.twx = reinterpret_cast<cplx<float>*>(smem);
   sm.twy = a.ny == a.nx ? sm.twx : sm.twx + a.nx;
-  sm.A = sm.twx + ntw + 2 * be * g;
+  sm.A = sm.twx + ntw + (2 * be + bc) * g;
   sm.B = sm.A + be;
+  sm.C = sm.B + be;
   {
     // the stage tables of both lengths from the 16384-entry float32 table e^{-2 pi i m / 16384}
     const cplx<float>* tg = static_cast<const cplx<float>*>(a.tw32);
@@ -651,7 +774,7 @@ __global__ void __launch_bounds__(kPNT, 1) k2_pcg_persist(const __grid_constant_
     for (int u = slot0; u < B * CU; u += nslots) {
       const int b = u / CU, c = u - b * CU;
       if (S[b].done) continue;
-      col_inverse(a, a.inst[b], S[b], c, sm, t, g);
+      col_inverse<STG>(a, a.inst[b], S[b], c, sm, t, g);
       gsync(g);
     }
     if ((stop = grid_barrier(a.bar, a.err, target, &s_stop))) break;
@@ -659,7 +782,7 @@ __global__ void __launch_bounds__(kPNT, 1) k2_pcg_persist(const __grid_constant_
     for (int u = slot0; u < B * RU; u += nslots) {
       const int b = u / RU, pr = u - b * RU;
       if (S[b].done) continue;
-      const float part = row_matvec(a, a.inst[b], 2 * pr, sm, t, g);
+      const float part = row_matvec<STG>(a, a.inst[b], 2 * pr, sm, t, g);
       group_part(part, slot, a.parts + (long long)b * RU + pr, t, g);
     }
     if ((stop = grid_barrier(a.bar, a.err, target, &s_stop))) break;
@@ -679,7 +802,7 @@ __global__ void __launch_bounds__(kPNT, 1) k2_pcg_persist(const __grid_constant_
     for (int u = slot0; u < B * CU; u += nslots) {
       const int b = u / CU, c = u - b * CU;
       if (S[b].done) continue;
-      const float part = col_forward_update(a, a.inst[b], S[b], c, sm, t, g);
+      const float part = col_forward_update<STG>(a, a.inst[b], S[b], c, sm, t, g);
       group_part(part, slot, parts2 + (long long)b * CU + c, t, g);
     }
     if ((stop = grid_barrier(a.bar, a.err, target, &s_stop))) break;
@@ -723,12 +846,30 @@ __global__ void k2_persist_arm(unsigned* bar, int* err) {
 
 }  // namespace
 
-// Shared memory: the twiddle tables and two buffers of three padded transforms per group.
+// Shared memory: the twiddle tables and, per group, two buffers of three padded transforms
+// (and the staged form's input buffer).
+static size_t persist_smem(int nx, int ny, bool stg) {
+  const long long ntw = nx + (ny == nx ? 0 : ny);
+  const long long per = 2ll * persist_be(nx, ny, stg) + persist_bc(nx, ny, stg);
+  return sizeof(cplx<float>) * (ntw + per * kNG);
+}
+
 size_t persist2d_smem(int nx, int ny, int tw) {
   (void)tw;
-  const long long be = 3ll * pad_len(nx > ny ? nx : ny);
-  const long long ntw = nx + (ny == nx ? 0 : ny);
-  return sizeof(cplx<float>) * (ntw + 2 * be * kNG);
+  return persist_smem(nx, ny, false);
+}
+
+// The staged form runs where its shared memory (with the kernel's static part) fits one
+// CTA on this device: sides up to 512 on a 227 KB part.
+static cudaError_t persist_staged(int nx, int ny, bool* stg) {
+  int dev = 0, optin = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev))) return e;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, k2_pcg_persist<true>))) return e;
+  *stg = fa.sharedSizeBytes + persist_smem(nx, ny, true) <= (size_t)optin;
+  return cudaSuccess;
 }
 
 // A column unit is one half-spectrum column (each group transforms three planes of it).
@@ -749,13 +890,19 @@ bool persist2d_tile_ok(int nx, int ny, int tw) {
 // Resident CTAs of the persistent kernel on this device (one per SM: 512 threads of up to
 // 128 registers), at most the largest phase's unit count.
 cudaError_t persist2d_grid(int nx, int ny, int B, int* grid) {
-  const size_t smem = persist2d_smem(nx, ny, 1);
+  bool stg = false;
   cudaError_t e;
-  if ((e = raise_smem(k2_pcg_persist, smem))) return e;
+  if ((e = persist_staged(nx, ny, &stg))) return e;
+  const size_t smem = persist_smem(nx, ny, stg);
+  if ((e = stg ? raise_smem(k2_pcg_persist<true>, smem) : raise_smem(k2_pcg_persist<false>, smem)))
+    return e;
   int dev = 0, sms = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev))) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2_pcg_persist, kPNT, smem)))
+  if ((e = stg ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2_pcg_persist<true>,
+                                                               kPNT, smem)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2_pcg_persist<false>,
+                                                               kPNT, smem)))
     return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int H = nx / 2 + 1;
@@ -770,7 +917,9 @@ cudaError_t launch_pcg2d_persist(const PersistArgs2d& args, int grid, cudaStream
   k2_persist_arm<<<1, 1, 0, s>>>(args.bar, args.err);
   cudaError_t e = cudaGetLastError();
   if (e) return e;
-  const size_t smem = persist2d_smem(args.nx, args.ny, args.tw);
+  bool stg = false;
+  if ((e = persist_staged(args.nx, args.ny, &stg))) return e;
+  const size_t smem = persist_smem(args.nx, args.ny, stg);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kPNT);
@@ -781,7 +930,8 @@ cudaError_t launch_pcg2d_persist(const PersistArgs2d& args, int grid, cudaStream
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k2_pcg_persist, args);
+  return stg ? cudaLaunchKernelEx(&cfg, k2_pcg_persist<true>, args)
+             : cudaLaunchKernelEx(&cfg, k2_pcg_persist<false>, args);
 }
 
 }  // namespace sgn
