@@ -150,13 +150,17 @@ __device__ __forceinline__ void pstage(const cplx<float>* __restrict__ src,
   const int lq = log2n - LR, q = 1 << lq;           // butterflies per transform
   const int tot = nb << lq;
   const int p0 = 1 << lp;
+  // The padded addresses split into a per-butterfly part and per-stage constants that stay
+  // out of the loop: pad(i + r q) = pad(i) + pad(r q) and, with k = i mod p,
+  // pad((i - k) R + k + s p) = pad((i - k) R) + pad(k) + pad(s p) (q, p powers of two).
 #pragma unroll 2
   for (int gi = t; gi < tot; gi += kGT) {
     const int j = gi >> lq, i = gi & (q - 1), k = i & ((1 << lp) - 1);
-    const int base = j * S, out = ((i - k) << LR) + k;
+    const cplx<float>* __restrict__ sb = src + j * S + pad(i);
+    cplx<float>* __restrict__ db = dst + j * S + pad((i - k) << LR) + pad(k);
     cplx<float> x[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = src[base + pad(i + r * q)];
+    for (int r = 0; r < R; ++r) x[r] = sb[pad(r << lq)];
     if (lp > 0) {
       // w^r from the table for r = 1, 2, 4, 8; the other powers by one or two products
       const cplx<float>* tb = tws + p0 - 1 + k;
@@ -182,7 +186,7 @@ __device__ __forceinline__ void pstage(const cplx<float>* __restrict__ src,
     }
     dft_reg<R>(x, inv);
 #pragma unroll
-    for (int s = 0; s < R; ++s) dst[base + pad(out + (s << lp))] = x[s];
+    for (int s = 0; s < R; ++s) db[pad(s << lp)] = x[s];
   }
   gsync(g);
 }
