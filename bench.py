@@ -38,9 +38,10 @@ FP32_PEAK = 152 * 128 * 2 * 2.07e9          # FMA lanes x 2 flops x max SM clock
 FP32_PROBE_TFLOPS = 75.3
 # DRAM bytes (read + write) per launch of the 2d persistent inner-solve kernel on the
 # pcg2d_batch configuration (16 instances of 512^2), from an ncu capture of this kernel
-# version, the staged form (dram__bytes_read.sum + dram__bytes_write.sum, the mean of the
-# first solve's two launches: 4.373e9 and 6.148e9 bytes)
-PCG2D_TRAFFIC_BYTES = 5.261e9
+# version, the staged form with split transform addresses (dram__bytes_read.sum +
+# dram__bytes_write.sum, the mean of the first solve's two launches: 4.368e9 and 6.134e9
+# bytes)
+PCG2D_TRAFFIC_BYTES = 5.251e9
 
 
 def hbm_peak():
