@@ -168,6 +168,16 @@ sgn_status sgn_layout_get_form2d(const sgn_layout* lay, int* inner, int* tile_wi
  * power of two.  sgn_state_autotune times the plans with the inner-solve forms. */
 sgn_status sgn_layout_set_radix2d(sgn_layout* lay, int max_radix);
 sgn_status sgn_layout_get_radix2d(const sgn_layout* lay, int* max_radix);
+/* Threads per unit of the persistent 2d inner solve (a unit is one half-spectrum column or
+ * one pair of rows, whose three transforms one thread group computes): 128 (four groups per
+ * CTA), 256 (two groups per CTA: each unit in about half the time, half as many units in
+ * flight), or 0, the default: 256 when the solve's largest phase has at most one unit per
+ * 256-thread group of the grid (a single 512^2 instance), else 128.  Every choice runs the
+ * same PCG (§3.2) and the results agree up to rounding.  The getter returns the setting (0
+ * for the default).  SGN_ERR_INVALID_ARG on a 1d layout or another value,
+ * SGN_ERR_UNSUPPORTED_SIZE on a grid with a side that is not a power of two. */
+sgn_status sgn_layout_set_unit_threads2d(sgn_layout* lay, int threads);
+sgn_status sgn_layout_get_unit_threads2d(const sgn_layout* lay, int* threads);
 
 /* offsets[0..count]: start of each instance in a packed scalar array (host array). */
 sgn_status sgn_layout_offsets(const sgn_layout* lay, long long* offsets);
@@ -357,10 +367,12 @@ sgn_status sgn_state_set_dealias(sgn_state* st, int on);
  * The state (eta, U, u, time, counters) is restored afterwards, so tuning leaves no trace
  * on the solution.  Allocates and frees 3 P doubles; synchronises `stream`; best_ms
  * (nullable, host) receives the chosen time per step.  A 1d state without such classes is
- * left as it is.  For a 2d state it chooses the layout's inner-solve form and radix plan
- * (sgn_layout_set_form2d and sgn_layout_set_radix2d: the persistent launch with radix-16 or
- * radix-8 stages, or four kernels per inner iteration) the same way: each candidate timed
- * on RK4 steps from the same state in two passes, the default (persistent, radix 8) kept
+ * left as it is.  For a 2d state it chooses the layout's inner-solve form, radix plan and
+ * threads per unit (sgn_layout_set_form2d, sgn_layout_set_radix2d and
+ * sgn_layout_set_unit_threads2d: the persistent launch with radix-8 stages and units sized
+ * by their count, with 128 or with 256 threads per unit, with radix-16 stages, or four
+ * kernels per inner iteration) the same way: each candidate timed on RK4 steps from the same
+ * state in two passes, the default (persistent, radix 8, units sized by their count) kept
  * unless another is at least 3% faster, the state restored.  A 2d grid with a side that is
  * not a power of two has one form: nothing to choose. */
 sgn_status sgn_state_autotune(sgn_state* st, const double* dt, const sgn_opts* opts,

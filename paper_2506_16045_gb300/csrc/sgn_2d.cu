@@ -1112,6 +1112,7 @@ PersistArgs2d persist_args(const Layout2d& L, const void* tw32) {
   a.logny = L.ly;
   a.tw = L.p_tw;
   a.maxb = L.p_maxb;
+  a.gt = L.p_gt;
   a.col_units = (L.H + L.p_tw - 1) / L.p_tw;
   a.row_units = L.ny / 2;
   a.parts = L.pparts;
@@ -1172,6 +1173,14 @@ cudaError_t layout2d_set_radix(Layout2d& L, int maxb) {
   if (maxb == L.p_maxb) return cudaSuccess;
   drop_solve_graphs(L);
   L.p_maxb = maxb;
+  return cudaSuccess;
+}
+
+cudaError_t layout2d_set_unit_threads(Layout2d& L, int threads) {
+  if (L.mr || (threads != 0 && threads != 128 && threads != 256)) return cudaErrorInvalidValue;
+  if (threads == L.p_gt) return cudaSuccess;
+  drop_solve_graphs(L);
+  L.p_gt = threads;
   return cudaSuccess;
 }
 
@@ -1966,6 +1975,7 @@ cudaError_t launch_pcg2d_batch(Layout2d& first, Batch2d& Bt, const void* tw64, c
     a.logny = first.ly;
     a.tw = Bt.p_tw;
     a.maxb = first.p_maxb;
+    a.gt = first.p_gt;
     a.col_units = (first.H + Bt.p_tw - 1) / Bt.p_tw;
     a.row_units = first.ny / 2;
     a.parts = Bt.pparts;

@@ -54,6 +54,7 @@ struct Layout2d {
   unsigned* pbar = nullptr;
   int p_tw = 0, p_grid = 0;
   int p_maxb = 3;           // the persistent form's transforms: stages up to radix 2^p_maxb
+  int p_gt = 0;             // the persistent form's threads per unit (0: by the unit count)
   int inner_form = 0;
   // non-null while profiling: mixed solves take the host-driven path and bracket each
   // persistent launch with events
@@ -137,6 +138,7 @@ cudaError_t layout2d_set_inner_form(Layout2d& L, int form, int tile_width);
 // Largest radix of the persistent form's transform stages, log2 (3: radix 8, 4: radix 16).
 // Drops the cached solve graphs when it changes.
 cudaError_t layout2d_set_radix(Layout2d& L, int maxb);
+cudaError_t layout2d_set_unit_threads(Layout2d& L, int threads);
 int persist2d_tile_width(int nx, int ny, int B, int grid);
 bool persist2d_tile_ok(int nx, int ny, int tile_width);
 

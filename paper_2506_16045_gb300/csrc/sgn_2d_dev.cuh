@@ -232,6 +232,7 @@ struct PersistArgs2d {
   int nx, ny, H, lognx, logny;
   int tw;                 // columns per column tile
   int maxb;               // log2 of the largest radix of the transforms' stages (3 or 4)
+  int gt;                 // threads per unit: 128, 256, or 0 (chosen by the unit count)
   int col_units, row_units;    // per instance: column tiles, row pairs
   double* parts;          // B (row_units + col_units) per-unit partial sums
   unsigned* bar;          // arrival counter of the grid barriers

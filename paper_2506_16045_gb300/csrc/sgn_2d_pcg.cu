@@ -39,8 +39,8 @@ using namespace d2;
 namespace {
 
 constexpr int kPNT = 512;                 // threads per CTA
-constexpr int kGT = 128;                  // threads per group: four groups per CTA
-constexpr int kNG = kPNT / kGT;
+// Threads per group (GT): 128 (four groups per CTA, the default) or 256 (two groups, for
+// solves with fewer units per phase than a grid's 128-thread groups).
 constexpr int kRows = 1;                  // rows a thread loads per batch: with every phase
                                           // inlined, more would spill past 128 registers
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s
@@ -131,17 +131,18 @@ __device__ __forceinline__ void dft_reg(cplx<float>* x, bool inv) {
   }
 }
 
-// Barrier of one group of kGT threads (named barrier g + 1; barrier 0 is __syncthreads).
+// Barrier of one group of GT threads (named barrier g + 1; barrier 0 is __syncthreads).
+template <int GT>
 __device__ __forceinline__ void gsync(int g) {
-  asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kGT) : "memory");
+  asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(GT) : "memory");
 }
 
 // One radix-R stage at sub-transform length p (log2 lp) over nb transforms of length n, run
-// by the kGT threads of group g (thread t of the group): butterfly i of transform j reads
+// by the GT threads of group g (thread t of the group): butterfly i of transform j reads
 // src[i + r n/R], twiddles by w^{r k} (w = e^{-+2 pi i/(p R)}, k = i mod p), and writes output
 // s to dst[(i - k) R + k + s p].  src and dst are different buffers, so each butterfly is
 // written as soon as it is computed; the group barrier at the end orders the stages.
-template <int R>
+template <int R, int GT>
 __device__ __forceinline__ void pstage(const cplx<float>* __restrict__ src,
                                        cplx<float>* __restrict__ dst, int log2n, int nb, int S,
                                        int lp, bool inv, const cplx<float>* __restrict__ tws,
@@ -154,7 +155,7 @@ __device__ __forceinline__ void pstage(const cplx<float>* __restrict__ src,
   // out of the loop: pad(i + r q) = pad(i) + pad(r q) and, with k = i mod p,
   // pad((i - k) R + k + s p) = pad((i - k) R) + pad(k) + pad(s p) (q, p powers of two).
 #pragma unroll 2
-  for (int gi = t; gi < tot; gi += kGT) {
+  for (int gi = t; gi < tot; gi += GT) {
     const int j = gi >> lq, i = gi & (q - 1), k = i & ((1 << lp) - 1);
     const cplx<float>* __restrict__ sb = src + j * S + pad(i);
     cplx<float>* __restrict__ db = dst + j * S + pad((i - k) << LR) + pad(k);
@@ -188,7 +189,7 @@ __device__ __forceinline__ void pstage(const cplx<float>* __restrict__ src,
 #pragma unroll
     for (int s = 0; s < R; ++s) db[pad(s << lp)] = x[s];
   }
-  gsync(g);
+  gsync<GT>(g);
 }
 
 // Batched transform of nb sequences of length n = 2^log2n (8 <= n <= 1024) by group g, from
@@ -197,6 +198,7 @@ __device__ __forceinline__ void pstage(const cplx<float>* __restrict__ src,
 // up to 2^maxb (maxb = 4: radix 16, 3: radix 8), split as evenly as possible.
 __device__ __forceinline__ int pfft_stages(int log2n, int maxb) { return (log2n + maxb - 1) / maxb; }
 
+template <int GT>
 __device__ __forceinline__ cplx<float>* pfft(cplx<float>* a, cplx<float>* b, int log2n, int nb, int S,
                                           bool inv, const cplx<float>* tws, int t, int g,
                                           int maxb) {
@@ -207,10 +209,10 @@ __device__ __forceinline__ cplx<float>* pfft(cplx<float>* a, cplx<float>* b, int
   cplx<float>* dst = b;
   for (int st = 0; st < ns; ++st) {
     const int bits = base + (st < extra ? 1 : 0);
-    if (bits == 4) pstage<16>(src, dst, log2n, nb, S, lp, inv, tws, t, g);
-    else if (bits == 3) pstage<8>(src, dst, log2n, nb, S, lp, inv, tws, t, g);
-    else if (bits == 2) pstage<4>(src, dst, log2n, nb, S, lp, inv, tws, t, g);
-    else pstage<2>(src, dst, log2n, nb, S, lp, inv, tws, t, g);
+    if (bits == 4) pstage<16, GT>(src, dst, log2n, nb, S, lp, inv, tws, t, g);
+    else if (bits == 3) pstage<8, GT>(src, dst, log2n, nb, S, lp, inv, tws, t, g);
+    else if (bits == 2) pstage<4, GT>(src, dst, log2n, nb, S, lp, inv, tws, t, g);
+    else pstage<2, GT>(src, dst, log2n, nb, S, lp, inv, tws, t, g);
     lp += bits;
     cplx<float>* tmp = src;
     src = dst;
@@ -312,6 +314,7 @@ __device__ __forceinline__ void ainv(const IScal& s, float kx, float ky, cplx<fl
 
 // Sum of the float partials of group g in double-float, stored as a double to `out` by the
 // group's thread 0 (warp shuffles, then the group's four warp totals in order).
+template <int GT>
 __device__ __forceinline__ void group_part(float v, df* slot, double* out, int t, int g) {
   df a(v, 0.0f);
 #pragma unroll
@@ -319,15 +322,15 @@ __device__ __forceinline__ void group_part(float v, df* slot, double* out, int t
     df b(__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o));
     a = a + b;
   }
-  if ((t & 31) == 0) slot[g * (kGT / 32) + (t >> 5)] = a;
-  gsync(g);
+  if ((t & 31) == 0) slot[g * (GT / 32) + (t >> 5)] = a;
+  gsync<GT>(g);
   if (t == 0) {
-    df r = slot[g * (kGT / 32)];
+    df r = slot[g * (GT / 32)];
 #pragma unroll
-    for (int w = 1; w < kGT / 32; ++w) r = r + slot[g * (kGT / 32) + w];
+    for (int w = 1; w < GT / 32; ++w) r = r + slot[g * (GT / 32) + w];
     __stcg(out, (double)r.hi + (double)r.lo);
   }
-  gsync(g);
+  gsync<GT>(g);
 }
 
 // Shared memory of the kernel: the twiddle table, then per group two transform buffers of
@@ -357,7 +360,7 @@ __host__ __device__ inline int persist_bc(int nx, int ny, bool stg) {
 
 // ---- C1: p update, projection, divergence, column iFFT (column c, group g) -------------
 // The solve's vectors and transform planes are column-major, [H][ny]: a column is contiguous.
-template <bool STG>
+template <bool STG, int GT>
 __device__ __forceinline__ void col_inverse(const PersistArgs2d& a, const PInst2d& I,
                                          const IScal& s, int c, const PSmem& sm, int t, int g) {
   const int ny = a.ny, S = pad_len(ny), nx = a.nx;
@@ -374,14 +377,14 @@ __device__ __forceinline__ void col_inverse(const PersistArgs2d& a, const PInst2
     // 16-byte copies, then p = A^{-1} r + beta p from shared memory
     cplx<float>* Cb = sm.C;
     const int lch = a.logny - 1, nch = (upd ? 4 : 2) << lch;
-    for (int i = t; i < nch; i += kGT) {
+    for (int i = t; i < nch; i += GT) {
       const int q = i >> lch, e = (i - (q << lch)) << 1;
       const cplx<float>* src = q == 0 ? r0 : (q == 1 ? r1p : (q == 2 ? p0 : p1p));
       cp16(Cb + q * ny + e, src + e);
     }
     cp_wait_all();
-    gsync(g);
-    for (int y = t; y < ny; y += kGT) {
+    gsync<GT>(g);
+    for (int y = t; y < ny; y += GT) {
       cplx<float> p1, p2;
       ainv(s, kx, ky_of(s, y, ny), Cb[y], Cb[ny + y], p1, p2);
       if (upd) {
@@ -393,11 +396,11 @@ __device__ __forceinline__ void col_inverse(const PersistArgs2d& a, const PInst2
     }
   } else {
   // the column's loads first (kRows rows per thread in flight), then the shared stores
-  for (int y0 = 0; y0 < ny; y0 += kRows * kGT) {
+  for (int y0 = 0; y0 < ny; y0 += kRows * GT) {
     cplx<float> r1[kRows], r2[kRows], q1[kRows], q2[kRows];
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
-      const int y = y0 + t + k * kGT;
+      const int y = y0 + t + k * GT;
       if (y < ny) {
         r1[k] = ldcg(r0 + y);
         r2[k] = ldcg(r1p + y);
@@ -409,7 +412,7 @@ __device__ __forceinline__ void col_inverse(const PersistArgs2d& a, const PInst2
     }
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
-      const int y = y0 + t + k * kGT;
+      const int y = y0 + t + k * GT;
       if (y < ny) {
         cplx<float> p1, p2;
         ainv(s, kx, ky_of(s, y, ny), r1[k], r2[k], p1, p2);
@@ -423,13 +426,13 @@ __device__ __forceinline__ void col_inverse(const PersistArgs2d& a, const PInst2
     }
   }
   }
-  gsync(g);
+  gsync<GT>(g);
   // the kx = 0 and kx = nx/2 columns of a real field are Hermitian in ky: project out the
   // rounding residue there before the packed C2R of the row pass could leak it
   if (c == 0 || c == (nx >> 1)) {
     for (int q = 0; q < 2; ++q) {
       cplx<float>* v = buf + q * S;
-      for (int y = t; y <= (ny >> 1); y += kGT) {
+      for (int y = t; y <= (ny >> 1); y += GT) {
         const int ym = (ny - y) & (ny - 1);
         const cplx<float> sm2 = v[pad(y)] + conj(v[pad(ym)]);
         const cplx<float> hm = mk(0.5f * sm2.x, 0.5f * sm2.y);
@@ -437,24 +440,24 @@ __device__ __forceinline__ void col_inverse(const PersistArgs2d& a, const PInst2
         v[pad(ym)] = conj(hm);
       }
     }
-    gsync(g);
+    gsync<GT>(g);
   }
-  for (int y = t; y < ny; y += kGT) {
+  for (int y = t; y < ny; y += GT) {
     const cplx<float> p1 = buf[pad(y)], p2 = buf[S + pad(y)];
     stcg(p0 + y, p1);
     stcg(p1p + y, p2);
     buf[2 * S + pad(y)] = mul_ik(p1, kx) + mul_ik(p2, ky_of(s, y, ny));
   }
-  gsync(g);
-  const cplx<float>* o = pfft(sm.A, sm.B, a.logny, 3, S, true, sm.twy, t, g, a.maxb);
-  for (int y = t; y < ny; y += kGT) {
+  gsync<GT>(g);
+  const cplx<float>* o = pfft<GT>(sm.A, sm.B, a.logny, 3, S, true, sm.twy, t, g, a.maxb);
+  for (int y = t; y < ny; y += GT) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) stcg(I.t[q] + cb + y, o[q * S + pad(y)]);
   }
 }
 
 // ---- R: C2R, Def:MatrixM pointwise with the p.Gp partial, R2C (row pair y0, group g) -----
-template <bool STG>
+template <bool STG, int GT>
 __device__ __forceinline__ float row_matvec(const PersistArgs2d& a, const PInst2d& I, int y0,
                                             const PSmem& sm, int t, int g) {
   const int nx = a.nx, h = nx >> 1, S = pad_len(nx);
@@ -482,16 +485,16 @@ __device__ __forceinline__ float row_matvec(const PersistArgs2d& a, const PInst2
     const int hp = h + 1;
 #pragma unroll
     for (int q = 0; q < 3; ++q)
-      for (int m = t; m <= h; m += kGT) cp16(raw + q * hp + m, I.t[q] + (long long)m * a.ny + y0);
+      for (int m = t; m <= h; m += GT) cp16(raw + q * hp + m, I.t[q] + (long long)m * a.ny + y0);
     float* ed = reinterpret_cast<float*>(sm.C);
     const int lc = a.lognx - 2, nch = 6 << lc;
-    for (int i = t; i < nch; i += kGT) {
+    for (int i = t; i < nch; i += GT) {
       const int row = i >> lc, e = (i - (row << lc)) << 2, j = row >> 1, r = row & 1;
       cp16(ed + row * nx + e, I.ehh + j * P + (long long)(y0 + r) * nx + e);
     }
     cp_wait_all();
-    gsync(g);
-    for (int m = t; m <= h; m += kGT) {
+    gsync<GT>(g);
+    for (int m = t; m <= h; m += GT) {
       const float4 A0 = raw[m], A1 = raw[hp + m], A2 = raw[2 * hp + m];
       const cplx<float> a0 = mk(A0.x, A0.y), a1 = mk(A0.z, A0.w);
       const cplx<float> b0 = mk(A1.x, A1.y), b1 = mk(A1.z, A1.w);
@@ -500,11 +503,11 @@ __device__ __forceinline__ float row_matvec(const PersistArgs2d& a, const PInst2
       if (m > 0 && m < h) put(nx - m, conj(a0), conj(b0), conj(a1), conj(b1), conj(d0), conj(d1));
     }
   } else
-  for (int m0 = 0; m0 <= h; m0 += kRows * kGT) {
+  for (int m0 = 0; m0 <= h; m0 += kRows * GT) {
     float4 A0[kRows], A1[kRows], A2[kRows];
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
-      const int m = m0 + t + k * kGT;
+      const int m = m0 + t + k * GT;
       if (m <= h) {
         A0[k] = pair_ld(0, m);
         A1[k] = pair_ld(1, m);
@@ -513,7 +516,7 @@ __device__ __forceinline__ float row_matvec(const PersistArgs2d& a, const PInst2
     }
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
-      const int m = m0 + t + k * kGT;
+      const int m = m0 + t + k * GT;
       if (m <= h) {
         // t0 = (p1(y0), p1(y1)), t1 = (p2(y0), p2(y1)), t2 = (d(y0), d(y1))
         const cplx<float> a0 = mk(A0[k].x, A0[k].y), a1 = mk(A0[k].z, A0[k].w);
@@ -524,17 +527,17 @@ __device__ __forceinline__ float row_matvec(const PersistArgs2d& a, const PInst2
       }
     }
   }
-  gsync(g);
-  cplx<float>* w = pfft(sm.A, sm.B, a.lognx, 3, S, true, sm.twx, t, g, a.maxb);
+  gsync<GT>(g);
+  cplx<float>* w = pfft<GT>(sm.A, sm.B, a.lognx, 3, S, true, sm.twx, t, g, a.maxb);
   const float inv = __int_as_float((127 - a.lognx - a.logny) << 23);   // 1 / (nx ny), exact
   const float third = 1.0f / 3.0f;
   float part = 0.0f;
-  for (int x0 = 0; x0 < nx; x0 += kRows * kGT) {
+  for (int x0 = 0; x0 < nx; x0 += kRows * GT) {
     // eta, h_x, h_y of both rows for kRows points per thread, loaded before use
     float ev[kRows][2], hxv[kRows][2], hyv[kRows][2];
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
-      const int x = x0 + t + k * kGT;
+      const int x = x0 + t + k * GT;
       if (x < nx) {
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
@@ -553,7 +556,7 @@ __device__ __forceinline__ float row_matvec(const PersistArgs2d& a, const PInst2
     }
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
-      const int x = x0 + t + k * kGT;
+      const int x = x0 + t + k * GT;
       if (x >= nx) continue;
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
@@ -574,12 +577,12 @@ __device__ __forceinline__ float row_matvec(const PersistArgs2d& a, const PInst2
       }
     }
   }
-  gsync(g);
+  gsync<GT>(g);
   cplx<float>* other = w == sm.A ? sm.B : sm.A;
-  const cplx<float>* Y = pfft(w, other, a.lognx, 3, S, false, sm.twx, t, g, a.maxb);
+  const cplx<float>* Y = pfft<GT>(w, other, a.lognx, 3, S, false, sm.twx, t, g, a.maxb);
   // R2C split of the three packed rows, A = (Y_m + conj Y_{n-m})/2, B = (Y_m - conj Y_{n-m})/(2i),
   // stored back as row pairs of columns m: t0 = (A_0, A_1), t1 = (B_0, B_1), t2 = (A_2, B_2)
-  for (int m = t; m <= h; m += kGT) {
+  for (int m = t; m <= h; m += GT) {
     cplx<float> A_[3], B_[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -597,7 +600,7 @@ __device__ __forceinline__ float row_matvec(const PersistArgs2d& a, const PInst2
 }
 
 // ---- C2: column FFT, G p, x and r updates, r.z partial (column c, group g) ---------------
-template <bool STG>
+template <bool STG, int GT>
 __device__ __forceinline__ float col_forward_update(const PersistArgs2d& a, const PInst2d& I,
                                                     const IScal& s, int c, const PSmem& sm,
                                                     int t, int g) {
@@ -614,25 +617,25 @@ __device__ __forceinline__ float col_forward_update(const PersistArgs2d& a, cons
     const int lch = a.logny - 1;
 #pragma unroll
     for (int q = 0; q < 3; ++q)
-      for (int e = 2 * t; e < ny; e += 2 * kGT) cp16(Bb + q * ny + e, I.t[q] + cb + e);
+      for (int e = 2 * t; e < ny; e += 2 * GT) cp16(Bb + q * ny + e, I.t[q] + cb + e);
     const int nch = 6 << lch;
-    for (int i = t; i < nch; i += kGT) {
+    for (int i = t; i < nch; i += GT) {
       const int q = i >> lch, e = (i - (q << lch)) << 1;
       const cplx<float>* src = q < 2 ? I.p[q] : (q < 4 ? I.x[q - 2] : I.r[q - 4]);
       cp16(Cw + q * ny + e, src + cb + e);
     }
     cp_wait_all();
-    gsync(g);
-    for (int y = t; y < ny; y += kGT) {
+    gsync<GT>(g);
+    for (int y = t; y < ny; y += GT) {
 #pragma unroll
       for (int q = 0; q < 3; ++q) buf[q * S + pad(y)] = Bb[q * ny + y];
     }
   } else
-  for (int y0 = 0; y0 < ny; y0 += kRows * kGT) {
+  for (int y0 = 0; y0 < ny; y0 += kRows * GT) {
     cplx<float> v[3][kRows];
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
-      const int y = y0 + t + k * kGT;
+      const int y = y0 + t + k * GT;
       if (y < ny) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) v[q][k] = ldcg(I.t[q] + cb + y);
@@ -640,15 +643,15 @@ __device__ __forceinline__ float col_forward_update(const PersistArgs2d& a, cons
     }
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
-      const int y = y0 + t + k * kGT;
+      const int y = y0 + t + k * GT;
       if (y < ny) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) buf[q * S + pad(y)] = v[q][k];
       }
     }
   }
-  gsync(g);
-  const cplx<float>* o = pfft(sm.A, sm.B, a.logny, 3, S, false, sm.twy, t, g, a.maxb);
+  gsync<GT>(g);
+  const cplx<float>* o = pfft<GT>(sm.A, sm.B, a.logny, 3, S, false, sm.twy, t, g, a.maxb);
   float part = 0.0f;
   const float al = s.alpha;
   const float kx = kx_of(s, c, nx);
@@ -660,11 +663,11 @@ __device__ __forceinline__ float col_forward_update(const PersistArgs2d& a, cons
   const cplx<float>* __restrict__ P0 = I.p[0] + cb;
   const cplx<float>* __restrict__ P1 = I.p[1] + cb;
   constexpr int KU = kRows;         // rows per batch of the update (six loads each)
-  for (int y0 = 0; y0 < ny; y0 += KU * kGT) {
+  for (int y0 = 0; y0 < ny; y0 += KU * GT) {
     cplx<float> p1[KU], p2[KU], x1[KU], x2[KU], r1[KU], r2[KU];
 #pragma unroll
     for (int k = 0; k < KU; ++k) {
-      const int y = y0 + t + k * kGT;
+      const int y = y0 + t + k * GT;
       if (y < ny) {
         if constexpr (STG) {
           p1[k] = Cb[y];
@@ -685,7 +688,7 @@ __device__ __forceinline__ float col_forward_update(const PersistArgs2d& a, cons
     }
 #pragma unroll
     for (int k = 0; k < KU; ++k) {
-      const int y = y0 + t + k * kGT;
+      const int y = y0 + t + k * GT;
       if (y < ny) {
         const float ky = ky_of(s, y, ny);
         const cplx<float> qh = o[2 * S + pad(y)];
@@ -707,14 +710,14 @@ __device__ __forceinline__ float col_forward_update(const PersistArgs2d& a, cons
 
 // STG: the staged form (a third shared buffer per group takes each unit's global inputs
 // by asynchronous copies, all in flight at once); otherwise loads go through registers.
-template <bool STG>
+template <bool STG, int GT>
 __global__ void __launch_bounds__(kPNT, 1) k2_pcg_persist(const __grid_constant__ PersistArgs2d a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ IScal S[kMaxBatch2d];
   __shared__ df slot[kPNT / 32];        // the groups' warp totals
   __shared__ int s_stop;
   // thread t of group g; the group's buffers after the twiddle table
-  const int g = threadIdx.x / kGT, t = threadIdx.x - g * kGT;
+  const int g = threadIdx.x / GT, t = threadIdx.x - g * GT;
   const int be = persist_be(a.nx, a.ny, STG), bc = persist_bc(a.nx, a.ny, STG);
   const int ntw = a.nx + (a.ny == a.nx ? 0 : a.ny);
   PSmem sm;
@@ -773,21 +776,21 @@ __global__ void __launch_bounds__(kPNT, 1) k2_pcg_persist(const __grid_constant_
     // Units go to the groups of the grid in turn, group-major (slot = group * grid + CTA),
     // so a phase with fewer units than slots still spreads over every SM; adjacent columns
     // (which share the 32-byte sectors of every row) are in flight together.
-    const int slot0 = g * gridDim.x + blockIdx.x, nslots = gridDim.x * kNG;
+    const int slot0 = g * gridDim.x + blockIdx.x, nslots = gridDim.x * (kPNT / GT);
     // ---- C1
     for (int u = slot0; u < B * CU; u += nslots) {
       const int b = u / CU, c = u - b * CU;
       if (S[b].done) continue;
-      col_inverse<STG>(a, a.inst[b], S[b], c, sm, t, g);
-      gsync(g);
+      col_inverse<STG, GT>(a, a.inst[b], S[b], c, sm, t, g);
+      gsync<GT>(g);
     }
     if ((stop = grid_barrier(a.bar, a.err, target, &s_stop))) break;
     // ---- R
     for (int u = slot0; u < B * RU; u += nslots) {
       const int b = u / RU, pr = u - b * RU;
       if (S[b].done) continue;
-      const float part = row_matvec<STG>(a, a.inst[b], 2 * pr, sm, t, g);
-      group_part(part, slot, a.parts + (long long)b * RU + pr, t, g);
+      const float part = row_matvec<STG, GT>(a, a.inst[b], 2 * pr, sm, t, g);
+      group_part<GT>(part, slot, a.parts + (long long)b * RU + pr, t, g);
     }
     if ((stop = grid_barrier(a.bar, a.err, target, &s_stop))) break;
     // alpha = r.z / p.Gp (p.Gp in the half-spectrum units of r.z: P times the real sum)
@@ -806,8 +809,8 @@ __global__ void __launch_bounds__(kPNT, 1) k2_pcg_persist(const __grid_constant_
     for (int u = slot0; u < B * CU; u += nslots) {
       const int b = u / CU, c = u - b * CU;
       if (S[b].done) continue;
-      const float part = col_forward_update<STG>(a, a.inst[b], S[b], c, sm, t, g);
-      group_part(part, slot, parts2 + (long long)b * CU + c, t, g);
+      const float part = col_forward_update<STG, GT>(a, a.inst[b], S[b], c, sm, t, g);
+      group_part<GT>(part, slot, parts2 + (long long)b * CU + c, t, g);
     }
     if ((stop = grid_barrier(a.bar, a.err, target, &s_stop))) break;
     sum_units(parts2, CU, S, B, [&](int b, double rz) {
@@ -850,30 +853,46 @@ __global__ void k2_persist_arm(unsigned* bar, int* err) {
 
 }  // namespace
 
-// Shared memory: the twiddle tables and, per group, two buffers of three padded transforms
-// (and the staged form's input buffer).
-static size_t persist_smem(int nx, int ny, bool stg) {
+// Shared memory: the twiddle tables and, per group of gt threads, two buffers of three
+// padded transforms (and the staged form's input buffer).
+static size_t persist_smem(int nx, int ny, bool stg, int gt) {
   const long long ntw = nx + (ny == nx ? 0 : ny);
   const long long per = 2ll * persist_be(nx, ny, stg) + persist_bc(nx, ny, stg);
-  return sizeof(cplx<float>) * (ntw + per * kNG);
+  return sizeof(cplx<float>) * (ntw + per * (kPNT / gt));
 }
 
 size_t persist2d_smem(int nx, int ny, int tw) {
   (void)tw;
-  return persist_smem(nx, ny, false);
+  return persist_smem(nx, ny, false, 128);
+}
+
+using PersistKernel = void (*)(PersistArgs2d);
+static PersistKernel persist_kernel(bool stg, int gt) {
+  if (gt == 256) return stg ? k2_pcg_persist<true, 256> : k2_pcg_persist<false, 256>;
+  return stg ? k2_pcg_persist<true, 128> : k2_pcg_persist<false, 128>;
 }
 
 // The staged form runs where its shared memory (with the kernel's static part) fits one
-// CTA on this device: sides up to 512 on a 227 KB part.
-static cudaError_t persist_staged(int nx, int ny, bool* stg) {
+// CTA on this device: with 128-thread groups sides up to 512, with 256-thread groups up to
+// 1024, on a 227 KB part.
+static cudaError_t persist_staged(int nx, int ny, int gt, bool* stg) {
   int dev = 0, optin = 0;
   cudaError_t e;
   if ((e = cudaGetDevice(&dev))) return e;
   if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
   cudaFuncAttributes fa;
-  if ((e = cudaFuncGetAttributes(&fa, k2_pcg_persist<true>))) return e;
-  *stg = fa.sharedSizeBytes + persist_smem(nx, ny, true) <= (size_t)optin;
+  if ((e = cudaFuncGetAttributes(&fa, persist_kernel(true, gt)))) return e;
+  *stg = fa.sharedSizeBytes + persist_smem(nx, ny, true, gt) <= (size_t)optin;
   return cudaSuccess;
+}
+
+// Threads per unit: the layout's choice, else 256 when the largest phase has at most one
+// unit per 256-thread group of the grid (each unit then finishes in about half the time and
+// no group waits for a second round), else 128.
+static int persist_gt(const PersistArgs2d& a, int grid) {
+  if (a.gt == 128 || a.gt == 256) return a.gt;
+  const long long units = (long long)a.B * (a.col_units > a.row_units ? a.col_units : a.row_units);
+  return units <= 2ll * grid ? 256 : 128;
 }
 
 // A column unit is one half-spectrum column (each group transforms three planes of it).
@@ -894,20 +913,24 @@ bool persist2d_tile_ok(int nx, int ny, int tw) {
 // Resident CTAs of the persistent kernel on this device (one per SM: 512 threads of up to
 // 128 registers), at most the largest phase's unit count.
 cudaError_t persist2d_grid(int nx, int ny, int B, int* grid) {
-  bool stg = false;
   cudaError_t e;
-  if ((e = persist_staged(nx, ny, &stg))) return e;
-  const size_t smem = persist_smem(nx, ny, stg);
-  if ((e = stg ? raise_smem(k2_pcg_persist<true>, smem) : raise_smem(k2_pcg_persist<false>, smem)))
-    return e;
+  PersistKernel k128 = nullptr;
+  size_t smem128 = 0;
+  for (int gt : {128, 256}) {
+    bool stg = false;
+    if ((e = persist_staged(nx, ny, gt, &stg))) return e;
+    const size_t smem = persist_smem(nx, ny, stg, gt);
+    if ((e = raise_smem(persist_kernel(stg, gt), smem))) return e;
+    if (gt == 128) {
+      k128 = persist_kernel(stg, gt);
+      smem128 = smem;
+    }
+  }
+  // the 128-thread form holds the most shared memory: its residency bounds both forms
   int dev = 0, sms = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev))) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
-  if ((e = stg ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2_pcg_persist<true>,
-                                                               kPNT, smem)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2_pcg_persist<false>,
-                                                               kPNT, smem)))
-    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k128, kPNT, smem128))) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int H = nx / 2 + 1;
   const long long units = (long long)B * (H > ny / 2 ? H : ny / 2);
@@ -921,9 +944,10 @@ cudaError_t launch_pcg2d_persist(const PersistArgs2d& args, int grid, cudaStream
   k2_persist_arm<<<1, 1, 0, s>>>(args.bar, args.err);
   cudaError_t e = cudaGetLastError();
   if (e) return e;
+  const int gt = persist_gt(args, grid);
   bool stg = false;
-  if ((e = persist_staged(args.nx, args.ny, &stg))) return e;
-  const size_t smem = persist_smem(args.nx, args.ny, stg);
+  if ((e = persist_staged(args.nx, args.ny, gt, &stg))) return e;
+  const size_t smem = persist_smem(args.nx, args.ny, stg, gt);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kPNT);
@@ -934,8 +958,7 @@ cudaError_t launch_pcg2d_persist(const PersistArgs2d& args, int grid, cudaStream
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return stg ? cudaLaunchKernelEx(&cfg, k2_pcg_persist<true>, args)
-             : cudaLaunchKernelEx(&cfg, k2_pcg_persist<false>, args);
+  return cudaLaunchKernelEx(&cfg, persist_kernel(stg, gt), args);
 }
 
 }  // namespace sgn

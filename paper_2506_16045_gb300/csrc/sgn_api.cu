@@ -781,6 +781,20 @@ extern "C" sgn_status sgn_layout_set_radix2d(sgn_layout* lay, int max_radix) {
   return SGN_OK;
 }
 
+extern "C" sgn_status sgn_layout_set_unit_threads2d(sgn_layout* lay, int threads) {
+  if (check_layout(lay) || lay->dim != 2 || (threads != 0 && threads != 128 && threads != 256))
+    return fail(lay ? lay->ctx : nullptr, SGN_ERR_INVALID_ARG, "set_unit_threads2d args");
+  if (lay->l2.mr) return fail(lay->ctx, SGN_ERR_UNSUPPORTED_SIZE, "no persistent solve on this grid");
+  SGN_CUDA(lay->ctx, sgn::layout2d_set_unit_threads(lay->l2, threads));
+  return SGN_OK;
+}
+
+extern "C" sgn_status sgn_layout_get_unit_threads2d(const sgn_layout* lay, int* threads) {
+  if (check_layout(lay) || lay->dim != 2 || !threads) return SGN_ERR_INVALID_ARG;
+  *threads = lay->l2.p_gt;
+  return SGN_OK;
+}
+
 extern "C" sgn_status sgn_layout_get_radix2d(const sgn_layout* lay, int* max_radix) {
   if (check_layout(lay) || lay->dim != 2 || !max_radix) return SGN_ERR_INVALID_ARG;
   *max_radix = 1 << lay->l2.p_maxb;
@@ -2008,16 +2022,19 @@ sgn_status autotune_2d(sgn_state* st, const sgn_opts* opts, cudaStream_t s, doub
     r = fail(ctx, SGN_ERR_CUDA, "autotune events");
   }
   constexpr int kTimed = 2;
-  // candidates: the persistent form with radix-8 stages (the default), with radix-16 stages,
-  // and the four-kernel form
-  constexpr int kCand = 3;
-  const int cform[kCand] = {0, 0, 1}, cmaxb[kCand] = {3, 4, 3};
-  float t_of[kCand] = {0.0f, 0.0f, 0.0f};
+  // candidates: the persistent form with radix-8 stages and units sized by their count (the
+  // default), the same with 128 and with 256 threads per unit, with radix-16 stages, and the
+  // four-kernel form
+  constexpr int kCand = 5;
+  const int cform[kCand] = {0, 0, 0, 0, 1}, cmaxb[kCand] = {3, 3, 3, 4, 3};
+  const int cgt[kCand] = {0, 128, 256, 0, 0};
+  float t_of[kCand] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
   const int tw = L.p_tw;
   for (int pass = 0; pass < 2 && !r; ++pass) {
     for (int c = 0; c < kCand && !r; ++c) {
       if (sgn::layout2d_set_inner_form(L, cform[c], tw) != cudaSuccess ||
-          sgn::layout2d_set_radix(L, cmaxb[c]) != cudaSuccess)
+          sgn::layout2d_set_radix(L, cmaxb[c]) != cudaSuccess ||
+          sgn::layout2d_set_unit_threads(L, cgt[c]) != cudaSuccess)
         r = cuda_fail(ctx, cudaGetLastError(), "autotune form");
       if (!r) r = rk4_step(st, opts, s);              // untimed: builds the solve graph
       if (!r) r = copy_state(false);
@@ -2037,6 +2054,7 @@ sgn_status autotune_2d(sgn_state* st, const sgn_opts* opts, cudaStream_t s, doub
     if (t_of[c] < 0.97f * t_of[0] && t_of[c] < t_of[best]) best = c;
   sgn::layout2d_set_inner_form(L, cform[best], tw);
   sgn::layout2d_set_radix(L, cmaxb[best]);
+  sgn::layout2d_set_unit_threads(L, cgt[best]);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   // the state is as it was before tuning, with no RK4 history (as after sgn_state_init)

@@ -89,6 +89,8 @@ SIGNATURES = [
     ("sgn_layout_get_form2d", C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("sgn_layout_set_radix2d", C.c_int, [_VP, C.c_int]),
     ("sgn_layout_get_radix2d", C.c_int, [_VP, C.POINTER(C.c_int)]),
+    ("sgn_layout_set_unit_threads2d", C.c_int, [_VP, C.c_int]),
+    ("sgn_layout_get_unit_threads2d", C.c_int, [_VP, C.POINTER(C.c_int)]),
     ("sgn_spectral_grad", C.c_int, [_VP, _VP, _DP, _DP, _VP]),
     ("sgn_precond_coeffs", C.c_int, [_VP, _VP, _DP, _DP, C.c_int, C.POINTER(SgnPrecond), _VP]),
     ("sgn_apply_operator", C.c_int, [_VP, _VP, _DP, _DP, _DP, _DP, _VP]),
@@ -307,6 +309,18 @@ class Layout:
         8 (default, also 0) or 16."""
         self.ctx.check(self.ctx.lib.sgn_layout_set_radix2d(self.h, max_radix),
                        "sgn_layout_set_radix2d")
+
+    def set_unit_threads2d(self, threads):
+        """sgn_layout_set_unit_threads2d: threads per unit of the persistent 2d inner solve
+        (128, 256, or 0: chosen by the unit count)."""
+        self.ctx.check(self.ctx.lib.sgn_layout_set_unit_threads2d(self.h, threads),
+                       "sgn_layout_set_unit_threads2d")
+
+    def unit_threads2d(self):
+        r = C.c_int()
+        self.ctx.check(self.ctx.lib.sgn_layout_get_unit_threads2d(self.h, C.byref(r)),
+                       "sgn_layout_get_unit_threads2d")
+        return r.value
 
     def radix2d(self):
         r = C.c_int()

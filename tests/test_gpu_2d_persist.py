@@ -103,6 +103,37 @@ def test_persistent_equals_four_kernel_form(S, nx, ny, Lx, Ly):
     assert abs(i0 - i1) <= max(2, 0.1 * i1), (i0, i1)
 
 
+@pytest.mark.parametrize("nx,ny,L", [(16, 16, 10.0), (64, 128, 20.0), (512, 512, 80.0),
+                                     (1024, 1024, 160.0)])
+def test_unit_threads_agree_and_default_follows_the_unit_count(S, nx, ny, L):
+    """128 and 256 threads per unit solve to the known u* and agree within the tolerance;
+    the default takes 256 when the largest phase has at most one unit per 256-thread group
+    of the grid (one instance up to 512^2 on 152 SMs) and 128 otherwise (1024^2), and
+    equals that choice bitwise."""
+    sgn, ctx = S
+    eta, gh, b, us, _ = bump_problem(nx, ny, L, L * ny / nx)
+    lay = sgn.Layout(ctx, [sgn.Grid(2, nx, L, ny=ny, Ly=L * ny / nx, g=9.81)])
+    out = {}
+    for gt in (128, 256, 0):
+        lay.set_unit_threads2d(gt)
+        assert lay.unit_threads2d() == gt
+        x = torch.zeros(2 * nx * ny, dtype=torch.float64, device="cuda")
+        info = sgn.pcg(lay, dev(eta), dev(gh), dev(b), x, rtol=1e-11, maxit=4000,
+                       prec=sgn.PREC_MIXED)[0]
+        assert info["status"] == 0 and info["ratio"] <= 1e-11, (gt, info)
+        out[gt] = x
+    x128, x256 = out[128].cpu().numpy(), out[256].cpu().numpy()
+    assert rel(x128, x256) < 1e-9
+    assert rel(x256.reshape(2, ny, nx), us) < 1e-8
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    units = max(nx // 2 + 1, ny // 2)
+    chosen = 256 if units <= 2 * min(sms, units) else 128
+    assert torch.equal(out[0], out[chosen])
+    with pytest.raises(sgn.SgnError):
+        lay.set_unit_threads2d(64)
+    lay.close()
+
+
 def test_persistent_inner_solve_edge_cases(S):
     """A zero right-hand side, an exact warm start, too small an iteration budget and a
     non-positive depth behave as in the four-kernel form."""
@@ -139,9 +170,9 @@ def test_persistent_inner_solve_edge_cases(S):
 
 
 def test_autotune_2d_chooses_a_form_and_restores_the_state(S):
-    """sgn_state_autotune on a 2d state times both inner-solve forms on the state's own RK4
-    steps, leaves one of them set, and restores the state bitwise; the next steps equal the
-    same steps taken with that form set by hand."""
+    """sgn_state_autotune on a 2d state times the inner-solve forms, radix plans and unit
+    widths on the state's own RK4 steps, leaves one of them set, and restores the state
+    bitwise; the next steps equal the same steps taken with that choice set by hand."""
     sgn, ctx = S
     n = 128
     c = I.bump2d_case(n=n, L=40.0, a=0.2, x0=10.0, H=0.5, R=3.0, dt=0.05)
@@ -162,12 +193,14 @@ def test_autotune_2d_chooses_a_form_and_restores_the_state(S):
     assert ms > 0.0
     form = lay.form2d()[0]
     radix = lay.radix2d()
-    assert form in (0, 1) and radix in (8, 16)
+    gt = lay.unit_threads2d()
+    assert form in (0, 1) and radix in (8, 16) and gt in (0, 128, 256)
     assert torch.equal(eta, eta0) and torch.equal(u, u0)
     st.rk4(0.05, 3, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
     lay2 = sgn.Layout(ctx, [g])
     lay2.set_form2d(form, 0)
     lay2.set_radix2d(radix)
+    lay2.set_unit_threads2d(gt)
     st2, eta2, u2 = state(lay2)
     st2.rk4(0.05, 3, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
     torch.cuda.synchronize()
