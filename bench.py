@@ -716,6 +716,24 @@ def bench_2d(sgn, ctx, torch, steps=300, n=512):
         out[prec] = (sec, eta.cpu().numpy().reshape(n, n), u.cpu().numpy(), stats)
     tm, em, um, sm = out[sgn.PREC_MIXED]
     t6, e6, u6, _ = out[sgn.PREC_FP64]
+    # where a mixed step's time goes: 20 more steps with the library's launch-group events on
+    # (the solves and the right-hand sides), after the timed runs
+    eta, u, h = dev(c["eta"]), dev(c["u"]), dev(c["h"])
+    U = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+    st = sgn.State(lay, eta, U, u, h, torch.zeros_like(U))
+    st.init()
+    st.rk4(c["dt"], 2, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st.rk4(c["dt"], 20, rtol=1e-10, maxit=4000, prec=sgn.PREC_MIXED)
+    e1.record()
+    torch.cuda.synchronize()
+    ctx.profile(False)
+    prof = ctx.profile_read()
+    st.close()
+    seg_ms = e0.elapsed_time(e1)
     rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
     mass = lambda e: float(np.sum(e - c["h"]))
     m0 = float(np.sum(zeta0))
@@ -728,7 +746,14 @@ def bench_2d(sgn, ctx, torch, steps=300, n=512):
             "mass_drift_rel": {"mixed": abs(mass(em) - m0) / abs(m0),
                                "fp64": abs(mass(e6) - m0) / abs(m0)},
             "max_zeta": float(np.abs(em - c["h"]).max()),
-            "iterations_per_solve": sm["iterations"] / max(1, sm["solves"]), "status": sm["status"]}
+            "iterations_per_solve": sm["iterations"] / max(1, sm["solves"]), "status": sm["status"],
+            "mixed_step_split": {"steps": 20, "ms_per_step": seg_ms / 20,
+                                 "solve_ms_per_step": prof["pcg_ms"] / 20,
+                                 "rhs_ms_per_step": prof["rhs_ms"] / 20,
+                                 "solve_share": prof["pcg_ms"] / seg_ms,
+                                 "rhs_share": prof["rhs_ms"] / seg_ms,
+                                 "note": "CUDA events of the library's profiling hooks around "
+                                         "each solve and each right-hand side"}}
 
 
 def bench_generic(sgn, ctx, torch, count=128, steps=20):
