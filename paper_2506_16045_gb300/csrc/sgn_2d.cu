@@ -172,8 +172,9 @@ __global__ void __launch_bounds__(kColNT, 1) k2_cols(Modes2d M, int log2ny, cons
     __syncthreads();
   }
   const bool inverse = (MODE == COL_INV || MODE == COL_MATVEC_IN);
-  for (int q = 0; q < nplanes; ++q)
-    cta_fft_batch<T, kColNT, MAXB>(buf + q * TW * stride, ny, log2ny, TW, stride, inverse, tw);
+  // the planes' columns lie at one stride (sequence q TW + c): one batched transform of all
+  // of them, so every stage's butterflies spread over the whole CTA
+  cta_fft_batch<T, kColNT, MAXB>(buf, ny, log2ny, nplanes * TW, stride, inverse, tw);
 
   // ---- store / epilogue
   if constexpr (MODE == COL_MATVEC_OUT) {
@@ -816,7 +817,8 @@ size_t row_smem(const Layout2d& L, int nrows) {
   return (size_t)nrows * L.nx * sizeof(cplx<T>);
 }
 
-// column pass launcher: MAXB from ny (TW columns x ny/4 butterflies over 512 threads)
+// column pass launcher: MAXB from the K planes' TW columns x ny/4 butterflies per radix-4
+// stage over kColNT threads
 template <typename T, int TW, int MODE>
 cudaError_t cols_tw(const Layout2d& L, const void* t64, const void* t32, const ColArgs& a,
                     cudaStream_t s) {
@@ -824,8 +826,9 @@ cudaError_t cols_tw(const Layout2d& L, const void* t64, const void* t32, const C
   const int tiles = (M.H + TW - 1) / TW;
   const int K = (MODE == COL_MATVEC_IN || MODE == COL_MATVEC_OUT) ? 3 : a.K;
   const size_t sm = (size_t)K * TW * (L.ny + 1) * sizeof(cplx<T>);
-  // TW * ny / 4 butterflies per radix-4 stage; MAXB = ceil(that / 512)
-  const int need = (TW * L.ny / 4 + kColNT - 1) / kColNT;
+  // K TW ny / 4 butterflies per radix-4 stage; MAXB = ceil(that / kColNT): at most 4, or 8
+  // for the four float32 columns of the widest grids
+  const int need = (K * TW * L.ny / 4 + kColNT - 1) / kColNT;
   cudaError_t e;
   if (need <= 1) {
     auto k = k2_cols<T, TW, 1, MODE>;
@@ -835,10 +838,16 @@ cudaError_t cols_tw(const Layout2d& L, const void* t64, const void* t32, const C
     auto k = k2_cols<T, TW, 2, MODE>;
     if ((e = smem_attr(k, sm))) return e;
     k<<<tiles, kColNT, sm, s>>>(M, L.ly, t64, t32, a);
-  } else {
+  } else if (need <= 4 || TW < 4) {
     auto k = k2_cols<T, TW, 4, MODE>;
     if ((e = smem_attr(k, sm))) return e;
     k<<<tiles, kColNT, sm, s>>>(M, L.ly, t64, t32, a);
+  } else {
+    if constexpr (TW == 4) {
+      auto k = k2_cols<T, TW, 8, MODE>;
+      if ((e = smem_attr(k, sm))) return e;
+      k<<<tiles, kColNT, sm, s>>>(M, L.ly, t64, t32, a);
+    }
   }
   return cudaGetLastError();
 }
