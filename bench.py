@@ -418,7 +418,8 @@ def gpu_arm(args, world, rank, local, pg):
                  "sample": f"{len(pick)} size-stratified instances, 1 RK4 step each, one "
                            "instance per launch"}
 
-    # ---- end to end through host buffers: H2D of the state, one step, D2H of (eta, u)
+    # ---- end to end through host buffers: the state lives on the host; every step uploads
+    # (eta, U, u), steps, and downloads the new (eta, U, u)
     E.reset()
     torch.cuda.synchronize()
     P = E.points
@@ -436,6 +437,7 @@ def gpu_arm(args, world, rank, local, pg):
         E.u.copy_(h_u, non_blocking=True)
         E.step(sgn.PREC_MIXED)
         h_eta.copy_(E.eta, non_blocking=True)
+        h_U.copy_(E.U, non_blocking=True)
         h_u.copy_(E.u, non_blocking=True)
 
     # untimed warm-up: the steps above ran with profiling on, which is part of the step
@@ -512,7 +514,7 @@ def gpu_arm(args, world, rank, local, pg):
                    "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas",
                    "autotuned_ctas_per_instance": E.forms},
         "e2e": {"value": total_points / (e2e_ms * 1e-3) if world == 1 else None, "unit": UNIT,
-                "h2d_bytes_per_step": 3 * 8 * P, "d2h_bytes_per_step": 2 * 8 * P},
+                "h2d_bytes_per_step": 3 * 8 * P, "d2h_bytes_per_step": 3 * 8 * P},
         "gpu_launches": E.launches_per_step() * args.steps,
         "clocks": clocks,
         "roofline": roof,
