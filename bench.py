@@ -310,7 +310,10 @@ class Ensemble:
 
     def launches_per_step(self):
         c = len(self.classes)
-        return 4 * c + 4 * c + 8 + 4          # rhs, pcg per size class; stage sums; counters
+        # per RK4 step: 4 right-hand sides and 4 solves per size class, 5 stage combinations,
+        # the first stage's starting point, 4 counter updates and the time update (the field
+        # copies are memcpy nodes, not kernels)
+        return 4 * c + 4 * c + 5 + 1 + 4 + 1
 
 
 def gpu_arm(args, world, rank, local, pg):
