@@ -418,6 +418,35 @@ __global__ void k2_spec(Modes2d M, const void* in0, const void* in1, void* out0,
   }
 }
 
+// Spectral combinations of the 2d right-hand side (i k multiplies by the wavenumber, the
+// Nyquist wavenumbers being 0):
+//   RHS_DIVD: out0 = d^ = i kx in0 + i ky in1 (d = div u), out1 = i kx in2 + i ky in3
+//             (m = div(eta u)), out2 = i kx d^, out3 = i ky d^ (grad d);
+//   RHS_DIV2: out0 = i kx in0 + i ky in1, out1 = i kx in1 + i ky in2 (the two components of
+//             div(eta u (x) u) from eta u u, eta u v, eta v v).
+enum RhsSpec { RHS_DIVD = 0, RHS_DIV2 = 1 };
+template <typename T, int MODE>
+__global__ void k2_spec_rhs(Modes2d M, const void* in0, const void* in1, const void* in2,
+                            const void* in3, void* out0, void* out1, void* out2, void* out3) {
+  const long long HP = (long long)M.ny * M.H;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HP;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)i / M.H, c = (int)i - y * M.H;   // half planes < 2^31 elements
+    const T kx = num<T>(M.kx(c)), ky = num<T>(M.ky(y));
+    const cplx<T> a = ld_c<T>(in0, i), b = ld_c<T>(in1, i), e = ld_c<T>(in2, i);
+    if constexpr (MODE == RHS_DIVD) {
+      const cplx<T> dh = mul_ik(a, kx) + mul_ik(b, ky);
+      st_c<T>(out0, i, dh);
+      st_c<T>(out1, i, mul_ik(e, kx) + mul_ik(ld_c<T>(in3, i), ky));
+      st_c<T>(out2, i, mul_ik(dh, kx));
+      st_c<T>(out3, i, mul_ik(dh, ky));
+    } else {
+      st_c<T>(out0, i, mul_ik(a, kx) + mul_ik(b, ky));
+      st_c<T>(out1, i, mul_ik(b, kx) + mul_ik(e, ky));
+    }
+  }
+}
+
 // Inner PCG update: x += alpha p; r -= alpha g; rz = r.A^{-1}r; last block forms beta and
 // the stopping decision.
 // In a solve graph (use_h) it also sets the inner loop's condition: 0 once done, which
@@ -727,15 +756,11 @@ __global__ void k2_rhs_stage(int stage, long long P, double g, const double* eta
       w[4 * P + j] = to_f64(e * uu * uu);                  // eta u u
       w[5 * P + j] = to_f64(e * uu * vv);                  // eta u v
       w[6 * P + j] = to_f64(e * vv * vv);                  // eta v v
-    } else if (stage == 1) {
-      // derivatives available: 10 u_x, 11 u_y, 12 v_x, 13 v_y, 14 (eta u)_x, 15 (eta u)_y,
-      // 16 (eta v)_x, 17 (eta v)_y; d = u_x + v_y -> plane 7
-      w[7 * P + j] = w[10 * P + j] + w[13 * P + j];
     } else {
-      // 18 zeta_x, 19 zeta_y, 20 s_x, 21 s_y, 22 d_x, 23 d_y, 24 (euu)_x, 25 (euu)_y,
-      // 26 (euv)_x, 27 (euv)_y, 28 (evv)_x, 29 (evv)_y; Phi -> 8, Psi -> 9
+      // 7 d = div u, 14 m = div(eta u), 18 zeta_x, 19 zeta_y, 20 s_x, 21 s_y, 22 d_x, 23 d_y,
+      // 24 and 26 the x and y components of div(eta u (x) u); Phi -> 8, Psi -> 9
       const T d = num<T>(w[7 * P + j]);
-      const T m = num<T>(w[14 * P + j]) + num<T>(w[17 * P + j]);
+      const T m = num<T>(w[14 * P + j]);
       const T s = hx * uu + hy * vv;
       const T Sv = uu * num<T>(w[20 * P + j]) + vv * num<T>(w[21 * P + j]);
       const T Q = uu * num<T>(w[22 * P + j]) + vv * num<T>(w[23 * P + j]) - d * d;
@@ -749,9 +774,9 @@ __global__ void k2_rhs_stage(int stage, long long P, double g, const double* eta
         const T gT = num<T>(g);
         f_eta[j] = -to_f64(m);
         const T fx = num<T>(w[30 * P + j]) - gT * e * num<T>(w[18 * P + j]) -
-                     num<T>(w[24 * P + j]) - num<T>(w[27 * P + j]) - hx * Psi;
+                     num<T>(w[24 * P + j]) - hx * Psi;
         const T fy = num<T>(w[31 * P + j]) - gT * e * num<T>(w[19 * P + j]) -
-                     num<T>(w[26 * P + j]) - num<T>(w[29 * P + j]) - hy * Psi;
+                     num<T>(w[26 * P + j]) - hy * Psi;
         f_U[j] = to_f64(fx);
         f_U[P + j] = to_f64(fy);
       }
@@ -2070,9 +2095,12 @@ cudaError_t launch_pcg2d_batch(Layout2d& first, Batch2d& Bt, const void* tw64, c
 
 namespace {
 
-// Right-hand side with six derivative pairs (see k2_rhs_stage for plane indices).  The
-// transforms run in T (float64, or double-float for the mixed path); the pointwise stages
-// and the intermediate planes are float64.
+// Right-hand side (Def:bigF) in four transform passes (see k2_rhs_stage for plane indices):
+// div u, div(eta u) and grad(div u) from one pass of (u, v, eta u, eta v); grad zeta and
+// grad s; the two components of div(eta u (x) u); grad Phi.  Sums of derivatives are formed
+// in spectral space, so only the twelve planes the pointwise stages read are transformed
+// back.  The transforms run in T (float64, or double-float for the mixed path); the
+// pointwise stages and the intermediate planes are float64.
 template <typename T>
 cudaError_t rhs2d(const Layout2d& L, const void* tw64, const void* tw32, double g,
                   const double* eta, const double* u, const double* h, const double* gradh,
@@ -2107,15 +2135,48 @@ cudaError_t rhs2d(const Layout2d& L, const void* tw64, const void* tw32, double 
     return rows_c2r<T>(L, tw64, tw32, slot(L, 0), slot(L, 1), slot(L, 2), slot(L, 3), ax,
                             ay, bx, by, 2, s);
   };
+  // Pass of four real fields through the forward transform, a spectral combination and the
+  // inverse transform of nout planes (written to out[0..nout) as real planes).
+  auto combo = [&](const double* a, const double* b, const double* c, const double* d, int K,
+                   int mode, int nout, double* const* out) -> cudaError_t {
+    cudaError_t r = rows_r2c<T>(L, tw64, tw32, a, b, c, d, tplane(L, 0), tplane(L, 1),
+                                tplane(L, 2), tplane(L, 3), (K + 1) / 2, s);
+    if (r) return r;
+    ColArgs cf{};
+    for (int q = 0; q < 4; ++q) cf.planes[q] = tplane(L, q);
+    cf.K = K;
+    if ((r = cols<T, COL_FWD>(L, tw64, tw32, cf, s))) return r;
+    const Modes2d M = modes_of(L);
+    if (mode == RHS_DIVD)
+      k2_spec_rhs<T, RHS_DIVD><<<grid_for(L.HP, 256), 256, 0, s>>>(
+          M, tplane(L, 0), tplane(L, 1), tplane(L, 2), tplane(L, 3), slot(L, 0), slot(L, 1),
+          slot(L, 2), slot(L, 3));
+    else
+      k2_spec_rhs<T, RHS_DIV2><<<grid_for(L.HP, 256), 256, 0, s>>>(
+          M, tplane(L, 0), tplane(L, 1), tplane(L, 2), nullptr, slot(L, 0), slot(L, 1), nullptr,
+          nullptr);
+    if ((r = cudaGetLastError())) return r;
+    ColArgs ci{};
+    for (int q = 0; q < 4; ++q) ci.planes[q] = slot(L, q);
+    ci.K = nout;
+    if ((r = cols<T, COL_INV>(L, tw64, tw32, ci, s))) return r;
+    return rows_c2r<T>(L, tw64, tw32, slot(L, 0), slot(L, 1), slot(L, 2), slot(L, 3), out[0],
+                       out[1], nout > 2 ? out[2] : nullptr, nout > 2 ? out[3] : nullptr,
+                       nout / 2, s);
+  };
   k2_rhs_stage<double><<<gb, 256, 0, s>>>(0, P, g, eta, u, h, gradh, w, f_eta, f_U);
   if ((e = cudaGetLastError())) return e;
-  if ((e = grad_pair(u, u + P, W(10), W(11), W(12), W(13)))) return e;
-  if ((e = grad_pair(W(0), W(1), W(14), W(15), W(16), W(17)))) return e;
-  if ((e = grad_pair(W(2), W(3), W(18), W(19), W(20), W(21)))) return e;
-  k2_rhs_stage<double><<<gb, 256, 0, s>>>(1, P, g, eta, u, h, gradh, w, f_eta, f_U);
-  if ((e = cudaGetLastError())) return e;
-  if ((e = grad_pair(W(7), W(4), W(22), W(23), W(24), W(25)))) return e;
-  if ((e = grad_pair(W(5), W(6), W(26), W(27), W(28), W(29)))) return e;
+  // d = div u, m = div(eta u), grad d from one pass of (u, v, eta u, eta v)
+  {
+    double* out[4] = {W(7), W(14), W(22), W(23)};
+    if ((e = combo(u, u + P, W(0), W(1), 4, RHS_DIVD, 4, out))) return e;
+  }
+  if ((e = grad_pair(W(2), W(3), W(18), W(19), W(20), W(21)))) return e;   // grad zeta, grad s
+  // div(eta u (x) u) from (eta u u, eta u v, eta v v)
+  {
+    double* out[4] = {W(24), W(26), nullptr, nullptr};
+    if ((e = combo(W(4), W(5), W(6), nullptr, 3, RHS_DIV2, 2, out))) return e;
+  }
   k2_rhs_stage<double><<<gb, 256, 0, s>>>(2, P, g, eta, u, h, gradh, w, f_eta, f_U);
   if ((e = cudaGetLastError())) return e;
   if ((e = grad_pair(W(8), nullptr, W(30), W(31), nullptr, nullptr))) return e;
