@@ -243,7 +243,6 @@ struct PersistArgs2d {
 }  // namespace d2
 
 // Launchers of the persistent inner solve (sgn_2d_pcg.cu).
-size_t persist2d_smem(int nx, int ny, int tw);
 // CTAs of the cooperative grid: every SM's resident CTAs, at most the largest phase's units
 cudaError_t persist2d_grid(int nx, int ny, int B, int* grid);
 // Zeroes the barrier words, then runs the inner solves of args.inst[0..B) to completion.

@@ -861,11 +861,6 @@ static size_t persist_smem(int nx, int ny, bool stg, int gt) {
   return sizeof(cplx<float>) * (ntw + per * (kPNT / gt));
 }
 
-size_t persist2d_smem(int nx, int ny, int tw) {
-  (void)tw;
-  return persist_smem(nx, ny, false, 128);
-}
-
 using PersistKernel = void (*)(PersistArgs2d);
 static PersistKernel persist_kernel(bool stg, int gt) {
   if (gt == 256) return stg ? k2_pcg_persist<true, 256> : k2_pcg_persist<false, 256>;
