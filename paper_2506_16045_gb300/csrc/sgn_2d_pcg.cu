@@ -22,9 +22,10 @@
 //
 // Data produced by other CTAs inside the launch (transform planes, Krylov vectors, partial
 // sums) is read with ld.global.cg or copied to shared memory with cp.async.cg (both from L2,
-// never a stale L1 line).  Where the shared memory allows (sides up to 512), the staged form
-// gives each group a third buffer and issues all of a unit's input copies at once, so a
-// unit waits for memory once instead of once per batch of rows.  Each barrier waits at most
+// never a stale L1 line).  Where the shared memory allows (sides up to 512 with 128-thread
+// groups, up to 1024 with 256-thread groups), the staged form gives each group a third
+// buffer and issues all of a unit's input copies at once, so a unit waits for memory once
+// instead of once per batch of rows.  Each barrier waits at most
 // kBarrierTimeoutNs; a CTA that gives up sets the error word, every CTA then leaves the
 // loop at its next barrier, and the solve reports SGN_ERR_TIMEOUT.  The launch is
 // cooperative, so every CTA of the grid is resident at once.
