@@ -113,11 +113,7 @@ __device__ __forceinline__ void mr_stage(const cplx<T>* __restrict__ src, cplx<T
                                          int n, int p, bool inv, const cplx<T>* __restrict__ tw,
                                          int nb) {
   const int q = n / R;
-  for (int t = threadIdx.x; t < q * nb; t += NT) {
-    const int sq = t / q, i = t - sq * q;
-    const cplx<T>* sr = src + (size_t)sq * n;
-    cplx<T>* ds = dst + (size_t)sq * n;
-    const int k = i % p;
+  auto butterfly = [&](const cplx<T>* __restrict__ sr, cplx<T>* __restrict__ ds, int i, int k) {
     cplx<T> x[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) x[r] = sr[i + r * q];
@@ -129,6 +125,22 @@ __device__ __forceinline__ void mr_stage(const cplx<T>* __restrict__ src, cplx<T
     const int o = (i - k) * R + k;
 #pragma unroll
     for (int s = 0; s < R; ++s) ds[o + s * p] = x[s];
+  };
+  if (nb == 1) {
+    // one sequence: butterfly i = t, and k = i mod p carried from one butterfly of this
+    // thread to its next (i grows by NT) instead of a division each time
+    const int step = NT % p;
+    int k = threadIdx.x % p;
+    for (int i = threadIdx.x; i < q; i += NT) {
+      butterfly(src, dst, i, k);
+      k += step;
+      if (k >= p) k -= p;
+    }
+  } else {
+    for (int t = threadIdx.x; t < q * nb; t += NT) {
+      const int sq = t / q, i = t - sq * q;
+      butterfly(src + (size_t)sq * n, dst + (size_t)sq * n, i, i % p);
+    }
   }
   __syncthreads();
 }
